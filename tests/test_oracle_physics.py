@@ -1,0 +1,118 @@
+"""Physics pins for the oracle: product states, the rotated Heisenberg bond,
+the classical Ising model against Onsager/Yang, brute-force patch
+contractions, and derivatives (CPU only)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import qrctm_oracle as o
+import qrctm_inputs as qi
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")))
+
+
+def test_rotated_bond_closed_form():
+    # exp(i pi sigma^y / 2) on one site flips sigma^x and sigma^z
+    X = np.array([[0, 1], [1, 0]])
+    Y = np.array([[0, -1j], [1j, 0]])
+    Z = np.diag([1, -1])
+    ref = (-np.kron(X, X) + np.kron(Y, Y) - np.kron(Z, Z)).real / 4
+    assert np.abs(o.rotated_heisenberg_bond() - ref).max() < 1e-15
+    # singlet energy -3/4 for the plain bond
+    assert abs(np.linalg.eigvalsh(o.heisenberg_bond()).min() + 0.75) < 1e-15
+
+
+@pytest.mark.parametrize("method", ["qr", "eigen"])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_product_state_D1_energy_exact(method, seed):
+    v = np.random.default_rng(seed).standard_normal(2)
+    A = (v / np.linalg.norm(v)).reshape(2, 1, 1, 1, 1)
+    C, T, _ = o.ctmrg(A, 4, method, tol=1e-14, max_iter=5)
+    g = GOLD["product_state_energy"]
+    for J2 in (0.0, 0.5):
+        E = o.energy(C, T, A, 1.0, J2)
+        assert abs(E - (g["value_J1"] + J2 * g["value_J2"])) < 1e-14
+
+
+@pytest.mark.parametrize("method", ["qr", "eigen"])
+def test_product_state_embedded_D2(method):
+    # rank-deficient reduced corner (R_jj = 0), exact energies survive
+    v = np.array([0.6, -0.8])
+    A = np.zeros((2, 2, 2, 2, 2))
+    A[:, 0, 0, 0, 0] = v
+    C, T, _ = o.ctmrg(A, 8, method, tol=1e-14, max_iter=10)
+    assert abs(o.energy(C, T, A, 1.0, 0.5) - (-0.5 + 0.25)) < 1e-13
+    rho = o.rdm_nn(C, T, A)
+    pv = np.einsum("a,b,c,d->abcd", v, v, v, v)
+    assert np.abs(rho / np.trace(np.trace(rho, axis1=0, axis2=1)) - pv).max() < 1e-13
+
+
+def test_onsager_quadrature_at_critical_point():
+    g = GOLD["ising_critical_free_energy"]["value"]
+    bc = GOLD["ising_beta_c"]["value"]
+    assert abs(o.onsager_free_energy(bc, n=4096) - g) < 1e-6
+
+
+def onsager_nn_correlation(beta, n=512):
+    """<s s>_NN = (1/2) d(-beta f)/d beta, differentiated under the integral."""
+    t = 2 * np.pi * np.arange(n) / n
+    c = np.cos(t)[:, None] + np.cos(t)[None, :]
+    ch, sh = np.cosh(2 * beta), np.sinh(2 * beta)
+    arg = ch ** 2 - sh * c
+    darg = 4 * ch * sh - 2 * ch * c
+    return 0.5 * 0.5 * np.mean(darg / arg)
+
+
+@pytest.mark.parametrize("method", ["qr", "eigen"])
+@pytest.mark.parametrize("beta", [0.3, 0.6])
+def test_ising_against_onsager_and_yang(method, beta):
+    # Discussion: QR-CTMRG applies to classical partition functions
+    A = o.ising_A(beta)
+    a = o.double_layer(A)
+    env = o.init_env(A, fixed_phys=0) if beta > GOLD["ising_beta_c"]["value"] else None
+    C, T, _ = o.ctmrg(A, 16, method, tol=1e-12, max_iter=300, env=env)
+    assert abs(np.log(o.ising_kappa(C, T, a)) - o.onsager_free_energy(beta)) < 1e-11
+    M = o.ising_kappa(C, T, a, o.ising_observable_layer(A))
+    assert abs(abs(M) - o.yang_magnetization(beta)) < 1e-9
+    # nearest-neighbour correlation from the 2x1 reduced density matrix
+    rho = o.rdm_nn(C, T, A)
+    p = np.einsum("aabb->ab", rho)
+    p = p / p.sum()
+    s = np.array([1.0, -1.0])
+    assert abs(s @ p @ s - onsager_nn_correlation(beta)) < 1e-9
+
+
+def test_rdm_nnn_by_brute_force_patch():
+    # the 2x2 patch written out tensor by tensor (4 C, 8 T, 4 sites), no
+    # quadrant symmetry used
+    rng = np.random.default_rng(3)
+    A = o.normalized_input(qi.raw_tensor(2, 2, 4))
+    C, T = o.sym_norm(rng.standard_normal((3, 3)), rng.standard_normal((3, 4, 3)))
+    a = o.double_layer(A)
+    aO = o.double_layer_open(A)
+    ops = [
+        C, [0, 1], T, [1, 2, 3], T, [3, 4, 5], C, [5, 6],          # top row
+        T, [0, 7, 8], aO, [40, 41, 2, 7, 9, 10], a, [4, 10, 11, 12], T, [6, 12, 13],
+        T, [8, 14, 15], a, [9, 14, 16, 17], aO, [42, 43, 11, 17, 18, 19], T, [13, 19, 20],
+        C, [15, 21], T, [21, 16, 22], T, [22, 18, 23], C, [23, 20],  # bottom row
+    ]
+    ref = np.einsum(*ops, [40, 41, 42, 43], optimize="greedy")
+    got = o.rdm_nnn(C, T, A)
+    assert np.abs(ref - got).max() < 1e-14 * np.abs(ref).max()
+
+
+def test_rdm_nn_by_brute_force_patch():
+    rng = np.random.default_rng(5)
+    A = o.normalized_input(qi.raw_tensor(2, 2, 6))
+    C, T = o.sym_norm(rng.standard_normal((3, 3)), rng.standard_normal((3, 4, 3)))
+    aO = o.double_layer_open(A)
+    ops = [
+        C, [0, 1], T, [1, 2, 3], T, [3, 4, 5], C, [5, 6],
+        T, [0, 7, 8], aO, [40, 41, 2, 7, 9, 10], aO, [42, 43, 4, 10, 11, 12], T, [6, 12, 13],
+        C, [8, 14], T, [14, 9, 15], T, [15, 11, 16], C, [16, 13],
+    ]
+    ref = np.einsum(*ops, [40, 41, 42, 43], optimize="greedy")
+    got = o.rdm_nn(C, T, A)
+    assert np.abs(ref - got).max() < 1e-14 * np.abs(ref).max()
