@@ -1,0 +1,169 @@
+/*
+ * qrctm.h -- C ABI of the B300 (sm_103a) QR-CTMRG library.
+ *
+ * The library contracts a C4v-symmetric infinite PEPS made of one real
+ * rank-5 tensor A[s,u,l,d,r] (physical dimension d, bond dimension D) with
+ * the corner transfer matrix renormalisation group in which the isometry
+ * comes from an unpivoted QR decomposition of the reduced corner
+ * ct = C T (Zhang, Yang, Corboz, arXiv 2505.00494: QR-CTMRG paragraph and
+ * Fig. 1(e,f)), and evaluates the Heisenberg / J1-J2 energy per site and its
+ * gradient with respect to A (Results paragraphs; Automatic differentiation
+ * paragraph; fixed-point differentiation as in the Discussion).
+ *
+ * Conventions (all arrays row-major, FP64, on the device unless stated):
+ *   A   [d][D][D][D][D]       legs (s, up, left, down, right)
+ *   C   [chi][chi]            corner, symmetric, unit Frobenius norm
+ *   T   [chi][D*D][chi]       edge, T[a][k][b] = T[b][k][a], unit norm;
+ *                             inner leg k = x*D + x' (ket-major)
+ * Every call returns a qrctm_status.  No exception or abort crosses the ABI.
+ * All device work is queued on the stream given in the configuration; calls
+ * that return host scalars synchronise that stream.  The caller owns every
+ * pointer it passes; the library never frees them.  The library allocates no
+ * device memory: all scratch lives in the caller's workspace.
+ */
+#ifndef QRCTM_H
+#define QRCTM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QRCTM_OK = 0,
+  QRCTM_ERR_INVALID_ARG = 1,   /* bad size, null pointer, unsupported option   */
+  QRCTM_ERR_CUDA = 2,          /* a CUDA runtime call failed (see last_error)  */
+  QRCTM_ERR_NOT_CONVERGED = 3, /* max_iter reached; the context stays usable   */
+  QRCTM_ERR_NUMERIC = 4,       /* NaN/Inf or a zero norm met in a kernel       */
+  QRCTM_ERR_NOT_SYMMETRIC = 5, /* A is not C4v symmetric (rel. tol 1e-12)      */
+  QRCTM_ERR_WORKSPACE = 6,     /* workspace smaller than required              */
+  QRCTM_ERR_TIMEOUT = 7,       /* a bounded device-side wait ran out           */
+  QRCTM_ERR_STATE = 8          /* call out of order (e.g. step before init)    */
+} qrctm_status;
+
+typedef enum { QRCTM_FP64 = 0, QRCTM_SPLIT = 1 } qrctm_precision;
+typedef enum { QRCTM_LAYERS_AUTO = 0, QRCTM_LAYERS_DOUBLE = 1, QRCTM_LAYERS_SPLIT = 2 } qrctm_layers;
+typedef enum { QRCTM_GRAD_IMPLICIT = 0, QRCTM_GRAD_UNROLL = 1 } qrctm_grad_mode;
+
+typedef struct {
+  int d;              /* physical dimension (>= 1)                               */
+  int D;              /* virtual bond dimension (>= 1)                           */
+  int chi;            /* environment bond dimension (D*D .. 1024)                */
+  int precision;      /* qrctm_precision: FP64 everywhere, or split TF32x3
+                         contractions on the tensor cores with FP64 QR panels,
+                         normalisation, spectrum and energy traces               */
+  int layers;         /* qrctm_layers: AUTO picks SPLIT (ket and bra layers
+                         absorbed one after the other) when 2*d < D*D            */
+  int warmup_steps;   /* standard-CTMRG steps in qrctm_init_env (0 = automatic:
+                         max(2, steps needed to grow chi from D^2); -1 = none,
+                         i.e. keep the bulk-initialised boundary, chi = D^2)     */
+  int check_every;    /* convergence test every this many steps (>= 1)          */
+  double tol;         /* default convergence tolerance on the corner spectrum   */
+  int max_iter;       /* default iteration cap                                  */
+  int grad_max_iter;  /* cap on adjoint fixed-point iterations (0 = 200)        */
+  double grad_tol;    /* adjoint fixed-point tolerance (0 = 1e-12)              */
+  int with_nnn;       /* 1: reserve workspace for the J2 (2x2 patch) energy term */
+  int with_grad;      /* 1: reserve workspace for qrctm_energy_grad              */
+  void* stream;       /* cudaStream_t; NULL = legacy default stream             */
+} qrctm_config;
+
+typedef struct {
+  double J1;          /* nearest-neighbour coupling (sublattice-rotated bond)    */
+  double J2;          /* next-nearest-neighbour coupling (plain bond)            */
+} qrctm_model;
+
+typedef struct qrctm_ctx qrctm_ctx;
+
+/* Bytes of device workspace needed for `cfg` (0 if cfg is invalid).  Host
+ * only; no CUDA call. */
+size_t qrctm_workspace_bytes(const qrctm_config* cfg);
+
+/* Create a context over a caller-owned device workspace of `bytes` bytes
+ * (256-byte aligned).  The workspace must stay valid until qrctm_destroy.
+ * Errors: INVALID_ARG (bad cfg, null or misaligned pointer), WORKSPACE (too
+ * small; both checked before any CUDA call). */
+qrctm_status qrctm_create(const qrctm_config* cfg, void* workspace, size_t bytes,
+                          qrctm_ctx** out);
+void qrctm_destroy(qrctm_ctx* ctx);
+
+/* Set the iPEPS tensor and initialise the environment (QR-CTMRG paragraph:
+ * a few standard steps first, growing chi to the target).
+ * A: device, d*D^4 doubles, must be C4v symmetric (checked, NOT_SYMMETRIC
+ *    otherwise); copied into the workspace.
+ * C0, T0: optional device environment (chi*chi and chi*D^2*chi).  If both are
+ *    given they are symmetrised, normalised and used as is (no warm-up).  If
+ *    both are NULL the boundary is built from A (contracting the ket and bra
+ *    legs on the open boundary, footnote of the Standard CTMRG paragraph) and
+ *    grown to chi by `warmup_steps` standard steps whose isometry spans the
+ *    dominant-|eigenvalue| subspace of the enlarged corner (block subspace
+ *    iteration, Fig. 1(d)). */
+qrctm_status qrctm_init_env(qrctm_ctx* ctx, const double* A, const double* C0, const double* T0);
+
+/* Run n_steps QR-CTMRG steps (Fig. 1(e,f)).  If delta_out is non-NULL the
+ * corner spectrum change since the previous test is computed and returned
+ * (host double; synchronises). */
+qrctm_status qrctm_step(qrctm_ctx* ctx, int n_steps, double* delta_out);
+
+/* Step until the change of the sorted, normalised |eig(C)| between two
+ * tests (every check_every steps) is below tol, or max_iter steps ("repeated
+ * until convergence", Standard CTMRG paragraph).  iters_out / delta_out:
+ * host, may be NULL.  Returns NOT_CONVERGED at max_iter (environment kept). */
+qrctm_status qrctm_run_to_convergence(qrctm_ctx* ctx, double tol, int max_iter, int* iters_out,
+                                      double* delta_out);
+
+/* Energy per site 2 J1 <h~>_nn + 2 J2 <h>_nnn of the current environment
+ * (Results paragraphs: Heisenberg bond with the sublattice rotation
+ * exp(i pi sigma^y / 2) on one sublattice for nearest neighbours; plain
+ * bond for next-nearest neighbours).  d must be 2; J2 != 0 needs with_nnn.
+ * e_out: host. */
+qrctm_status qrctm_energy(qrctm_ctx* ctx, const qrctm_model* model, double* e_out);
+
+/* Energy and its gradient with respect to A at the converged environment
+ * (Automatic differentiation paragraph; fixed-point AD, Discussion).
+ * mode IMPLICIT: adjoint fixed point of two QR-CTMRG steps at the current
+ * environment (the map's fixed point up to the sign gauge it alternates);
+ * mode UNROLL: backpropagation through k_unroll steps started from the
+ * current (detached) environment.  grad: device, d*D^4 doubles, the
+ * C4v-projected gradient.  e_out: host.  Needs with_grad. */
+qrctm_status qrctm_energy_grad(qrctm_ctx* ctx, const qrctm_model* model, int mode, int k_unroll,
+                               double* grad, double* e_out);
+
+/* Copy the environment out: C (chi*chi), T (chi*D^2*chi) on the device (may be
+ * NULL); spectrum_host: chi doubles, sorted |eig(C)| (may be NULL). */
+qrctm_status qrctm_get_env(qrctm_ctx* ctx, double* C, double* T, double* spectrum_host);
+
+/* Steps run since qrctm_init_env. */
+int qrctm_iterations(const qrctm_ctx* ctx);
+
+/* Text of the last error on this context ("" if none). */
+const char* qrctm_last_error(const qrctm_ctx* ctx);
+
+/* ----- standalone operations (no context) --------------------------------- */
+
+/* Y = sym(X), the mean over the 8 C4v operations on the virtual legs (iPEPS
+ * paragraph; n(D) free parameters per its footnote); if normalize,
+ * Y /= ||Y||_F.  X, Y: device, d*D^4 doubles, distinct.  workspace:
+ * qrctm_c4v_symmetrize_workspace_bytes() device bytes (only for normalize).
+ * stream: cudaStream_t or NULL.  Synchronises when normalize is set. */
+size_t qrctm_c4v_symmetrize_workspace_bytes(void);
+qrctm_status qrctm_c4v_symmetrize(int d, int D, const double* X, double* Y, int normalize,
+                                  void* workspace, size_t bytes, void* stream);
+
+/* Unpivoted Householder QR with diag(R) >= 0 (QR-CTMRG paragraph) of a
+ * column-major m x n device matrix M (m >= n >= 1).  Q: m x n column-major,
+ * R: n x n row-major (upper triangular).  workspace: 256-byte aligned,
+ * qrctm_qr_workspace_bytes(m, n) bytes, zero-filled before its first use
+ * (the call leaves its control words zero again).  Synchronises. */
+size_t qrctm_qr_workspace_bytes(int m, int n);
+qrctm_status qrctm_householder_qr(int m, int n, const double* M, double* Q, double* R,
+                                  void* workspace, size_t bytes, void* stream);
+
+/* Library version string. */
+const char* qrctm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QRCTM_H */

@@ -1,0 +1,253 @@
+"""Python binding of the B300 QR-CTMRG library (libqrctm.so).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libqrctm.so``.  PyTorch supplies device memory (the workspace and
+the caller's tensors) and the CUDA stream.  If the shared library is missing
+this module raises at import time; there is no CPU fallback.
+
+The functions mirror the C ABI in ``include/qrctm.h``:
+
+    ctx = QRCTM(d=2, D=6, chi=144, precision="split")
+    ctx.init_env(A)                      # A: cuda float64, C4v symmetric
+    iters, delta = ctx.run_to_convergence(tol=1e-10, max_iter=500)
+    E = ctx.energy(J1=1.0, J2=0.0)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+__all__ = ["QRCTM", "QRCTMError", "lib", "c4v_symmetrize", "householder_qr", "LIB_PATH"]
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libqrctm.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -m paper_2505_00494_b300.build` "
+        "(nvcc, sm_103a). There is no CPU fallback.")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+STATUS = {
+    0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "NOT_CONVERGED", 4: "NUMERIC",
+    5: "NOT_SYMMETRIC", 6: "WORKSPACE", 7: "TIMEOUT", 8: "STATE",
+}
+PRECISION = {"fp64": 0, "split": 1}
+LAYERS = {"auto": 0, "double": 1, "split": 2}
+GRAD_MODE = {"implicit": 0, "unroll": 1}
+
+
+class QRCTMError(RuntimeError):
+    def __init__(self, code, where, msg=""):
+        self.code = code
+        self.status = STATUS.get(code, str(code))
+        super().__init__(f"{where}: {self.status}" + (f" ({msg})" if msg else ""))
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_int), ("D", ctypes.c_int), ("chi", ctypes.c_int),
+        ("precision", ctypes.c_int), ("layers", ctypes.c_int),
+        ("warmup_steps", ctypes.c_int), ("check_every", ctypes.c_int),
+        ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+        ("grad_max_iter", ctypes.c_int), ("grad_tol", ctypes.c_double),
+        ("with_nnn", ctypes.c_int), ("with_grad", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class Model(ctypes.Structure):
+    _fields_ = [("J1", ctypes.c_double), ("J2", ctypes.c_double)]
+
+
+_vp, _dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+_sig = {
+    "qrctm_version": ([], ctypes.c_char_p),
+    "qrctm_workspace_bytes": ([ctypes.POINTER(Config)], ctypes.c_size_t),
+    "qrctm_create": ([ctypes.POINTER(Config), _vp, ctypes.c_size_t, ctypes.POINTER(_vp)],
+                     ctypes.c_int),
+    "qrctm_destroy": ([_vp], None),
+    "qrctm_init_env": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+    "qrctm_step": ([_vp, ctypes.c_int, _dp], ctypes.c_int),
+    "qrctm_run_to_convergence": ([_vp, ctypes.c_double, ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_int), _dp], ctypes.c_int),
+    "qrctm_energy": ([_vp, ctypes.POINTER(Model), _dp], ctypes.c_int),
+    "qrctm_energy_grad": ([_vp, ctypes.POINTER(Model), ctypes.c_int, ctypes.c_int, _vp, _dp],
+                          ctypes.c_int),
+    "qrctm_get_env": ([_vp, _vp, _vp, _dp], ctypes.c_int),
+    "qrctm_iterations": ([_vp], ctypes.c_int),
+    "qrctm_last_error": ([_vp], ctypes.c_char_p),
+    "qrctm_c4v_symmetrize": ([ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp,
+                              ctypes.c_size_t, _vp], ctypes.c_int),
+    "qrctm_c4v_symmetrize_workspace_bytes": ([], ctypes.c_size_t),
+    "qrctm_qr_workspace_bytes": ([ctypes.c_int, ctypes.c_int], ctypes.c_size_t),
+    "qrctm_householder_qr": ([ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_size_t,
+                              _vp], ctypes.c_int),
+}
+for _name, (_args, _ret) in _sig.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = _ret
+
+EXPORTED = sorted(_sig)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError("expected a CUDA float64 tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _workspace(nbytes, device, zero=False):
+    torch = _torch()
+    alloc = torch.zeros if zero else torch.empty
+    ws = alloc(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+    if ws.data_ptr() % 256 != 0:
+        raise RuntimeError("workspace not 256-byte aligned")
+    return ws
+
+
+class QRCTM:
+    """A QR-CTMRG context over a torch-allocated device workspace."""
+
+    def __init__(self, d, D, chi, precision="fp64", layers="auto", warmup_steps=0,
+                 check_every=1, tol=1e-10, max_iter=500, grad_max_iter=0, grad_tol=0.0,
+                 with_nnn=False, with_grad=False, stream=None, device="cuda"):
+        torch = _torch()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.cfg = Config(d, D, chi, PRECISION[precision], LAYERS[layers], warmup_steps,
+                          check_every, tol, max_iter, grad_max_iter, grad_tol, int(with_nnn),
+                          int(with_grad), ctypes.c_void_p(self.stream.cuda_stream))
+        nbytes = lib.qrctm_workspace_bytes(ctypes.byref(self.cfg))
+        if nbytes == 0:
+            raise QRCTMError(1, "qrctm_workspace_bytes", "invalid configuration")
+        self.workspace_bytes = nbytes
+        self.ws = _workspace(nbytes, device)
+        self.d, self.D, self.chi = d, D, chi
+        h = ctypes.c_void_p()
+        self.h = None
+        self._check(lib.qrctm_create(ctypes.byref(self.cfg), ctypes.c_void_p(self.ws.data_ptr()),
+                                     nbytes, ctypes.byref(h)), "qrctm_create")
+        self.h = h
+
+    def _check(self, code, where):
+        if code != 0:
+            msg = lib.qrctm_last_error(self.h).decode() if self.h else ""
+            raise QRCTMError(code, where, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.qrctm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def init_env(self, A, C0=None, T0=None):
+        self.A = A
+        self._check(lib.qrctm_init_env(self.h, _ptr(A), _ptr(C0), _ptr(T0)), "qrctm_init_env")
+
+    def step(self, n=1, want_delta=True):
+        dlt = ctypes.c_double(0.0)
+        self._check(lib.qrctm_step(self.h, n, ctypes.byref(dlt) if want_delta else None),
+                    "qrctm_step")
+        return dlt.value if want_delta else None
+
+    def run_to_convergence(self, tol=0.0, max_iter=0, raise_on_max=False):
+        it = ctypes.c_int(0)
+        dlt = ctypes.c_double(0.0)
+        code = lib.qrctm_run_to_convergence(self.h, tol, max_iter, ctypes.byref(it),
+                                            ctypes.byref(dlt))
+        if code == 3 and not raise_on_max:
+            return it.value, dlt.value
+        self._check(code, "qrctm_run_to_convergence")
+        return it.value, dlt.value
+
+    def energy(self, J1=1.0, J2=0.0):
+        e = ctypes.c_double(0.0)
+        m = Model(J1, J2)
+        self._check(lib.qrctm_energy(self.h, ctypes.byref(m), ctypes.byref(e)), "qrctm_energy")
+        return e.value
+
+    def energy_grad(self, J1=1.0, J2=0.0, mode="implicit", k_unroll=20, grad=None):
+        torch = _torch()
+        if grad is None:
+            grad = torch.empty((self.d,) + (self.D,) * 4, dtype=torch.float64, device="cuda")
+        e = ctypes.c_double(0.0)
+        m = Model(J1, J2)
+        self._check(lib.qrctm_energy_grad(self.h, ctypes.byref(m), GRAD_MODE[mode], k_unroll,
+                                          _ptr(grad), ctypes.byref(e)), "qrctm_energy_grad")
+        return e.value, grad
+
+    def get_env(self, spectrum=True):
+        torch = _torch()
+        import numpy as np
+        D2 = self.D * self.D
+        C = torch.empty((self.chi, self.chi), dtype=torch.float64, device="cuda")
+        T = torch.empty((self.chi, D2, self.chi), dtype=torch.float64, device="cuda")
+        s = np.zeros(self.chi) if spectrum else None
+        sp = s.ctypes.data_as(_dp) if spectrum else None
+        self._check(lib.qrctm_get_env(self.h, _ptr(C), _ptr(T), sp), "qrctm_get_env")
+        return C, T, s
+
+    @property
+    def iterations(self):
+        return lib.qrctm_iterations(self.h)
+
+
+def c4v_symmetrize(X, normalize=True, stream=None):
+    """Y = sym(X) (optionally / ||.||_F) on the device."""
+    torch = _torch()
+    d, D = X.shape[0], X.shape[1]
+    Y = torch.empty_like(X)
+    nb = lib.qrctm_c4v_symmetrize_workspace_bytes()
+    ws = _workspace(nb, X.device)
+    code = lib.qrctm_c4v_symmetrize(d, D, _ptr(X), _ptr(Y), int(normalize),
+                                    ctypes.c_void_p(ws.data_ptr()), nb, _stream_ptr(stream))
+    if code != 0:
+        raise QRCTMError(code, "qrctm_c4v_symmetrize")
+    return Y
+
+
+def householder_qr(M, stream=None, workspace=None):
+    """Q, R of an m x n float64 CUDA matrix M (a row-major torch tensor).
+
+    The library works on column-major storage, so M is passed as the storage
+    of M^T; Q comes back the same way and is returned as an (m, n) view."""
+    torch = _torch()
+    m, n = M.shape
+    Mcm = M.t().contiguous()
+    Qcm = torch.empty((n, m), dtype=torch.float64, device=M.device)
+    R = torch.empty((n, n), dtype=torch.float64, device=M.device)
+    nb = lib.qrctm_qr_workspace_bytes(m, n)
+    ws = workspace if workspace is not None else _workspace(nb, M.device, zero=True)
+    code = lib.qrctm_householder_qr(m, n, _ptr(Mcm), _ptr(Qcm), _ptr(R),
+                                    ctypes.c_void_p(ws.data_ptr()), nb, _stream_ptr(stream))
+    if code != 0:
+        raise QRCTMError(code, "qrctm_householder_qr")
+    return Qcm.t(), R

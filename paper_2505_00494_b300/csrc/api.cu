@@ -1,0 +1,408 @@
+// C ABI of the QR-CTMRG library (declared in include/qrctm.h).
+//
+// The context never allocates device memory: every buffer is a region of
+// the caller's workspace, laid out by make_plan().  Errors are reported as
+// status codes plus a per-context message; kernel-side failures raise bits
+// of a device error word that the host reads at every synchronisation.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ctx.cuh"
+
+using namespace qrctm;
+
+namespace {
+
+inline size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool cfg_valid(const qrctm_config& c) {
+  if (c.d < 1 || c.D < 1 || c.chi < 1 || c.chi > 1024) return false;
+  if (c.precision != QRCTM_FP64 && c.precision != QRCTM_SPLIT) return false;
+  if (c.layers < 0 || c.layers > 2) return false;
+  if (c.check_every < 0 || c.warmup_steps < -1) return false;
+  const long long D2 = (long long)c.D * c.D;
+  if (D2 > 4096 || (long long)c.chi * D2 > (1ll << 20)) return false;
+  if (c.chi < D2) return false;
+  return true;
+}
+
+qrctm_status set_err(qrctm_ctx* c, qrctm_status s, const char* msg) {
+  if (c) c->last_error = msg;
+  return s;
+}
+
+qrctm_status cuda_fail(qrctm_ctx* c, cudaError_t e, const char* where) {
+  if (c) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+    c->last_error = buf;
+  }
+  return QRCTM_ERR_CUDA;
+}
+
+// Synchronise the stream and translate the device error word.
+qrctm_status sync_check(qrctm_ctx* c, const char* where) {
+  cudaError_t e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return cuda_fail(c, e, where);
+  int flag = 0;
+  e = cudaMemcpy(&flag, c->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, where);
+  if (flag) {
+    cudaMemsetAsync(c->err, 0, sizeof(int), c->st);
+    cudaStreamSynchronize(c->st);
+    if (flag & ERRF_TIMEOUT) return set_err(c, QRCTM_ERR_TIMEOUT, "device wait timed out");
+    if (flag & ERRF_NUMERIC) return set_err(c, QRCTM_ERR_NUMERIC, "NaN/Inf or zero norm");
+    return set_err(c, QRCTM_ERR_NUMERIC, "device size check failed");
+  }
+  return QRCTM_OK;
+}
+
+}  // namespace
+
+namespace qrctm {
+
+// Regions in a fixed order; the same function sizes and carves.
+size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
+  const size_t d = cfg.d, D = cfg.D, D2 = D * D, chi = cfg.chi, m = chi * D2;
+  const bool split = (cfg.layers == QRCTM_LAYERS_SPLIT) ||
+                     (cfg.layers == QRCTM_LAYERS_AUTO && 2 * d < D2);
+  size_t off = 0;
+  auto take = [&](double** dst, size_t n_doubles) {
+    size_t o = off;
+    off += al(sizeof(double) * (n_doubles > 0 ? n_doubles : 1));
+    if (carve && dst) *dst = reinterpret_cast<double*>(c->ws + o);
+  };
+  auto P = [&](double*& ref) { return carve ? &ref : nullptr; };
+  static double* dummy;
+  qrctm_ctx* cc = carve ? c : nullptr;
+#define R_(field) P(cc ? cc->field : dummy)
+  const size_t nA = d * D2 * D2, nC = chi * chi, nT = chi * D2 * chi;
+  take(R_(A), nA);
+  take(R_(tmpA), nA);
+  take(R_(C), nC);
+  take(R_(T), nT);
+  take(R_(Cn), nC);
+  take(R_(Tn), nT);
+  take(R_(Craw), nC);
+  take(R_(Traw), nT);
+  take(R_(Mcm), m * chi);
+  take(R_(Q), m * chi);
+  take(R_(R), nC);
+  take(R_(X1), m * m);
+  take(R_(Z), m * m * d);
+  take(R_(X2), m * m);
+  take(R_(Y2), m * chi);
+  take(R_(Xs), m * chi);
+  take(R_(Yw), m * chi);
+  take(R_(spec_work), nC + 8 * chi);
+  take(R_(s_cur), chi);
+  take(R_(s_prev), chi);
+  take(R_(delta_d), 8);
+  take(R_(partials), 1024);
+  take(R_(a), split ? 1 : D2 * D2 * D2 * D2);
+  take(R_(E1), d * d * m * m);
+  take(R_(E2), d * d * m * chi);
+  if (cfg.with_nnn) take(R_(E3), d * d * m * m);
+  else if (carve) c->E3 = nullptr;
+  take(R_(rho), 64);
+  take(R_(e_d), 8);
+#undef R_
+  {
+    size_t o = off;
+    off += al(qr_work_bytes((int)m, (int)chi));
+    if (carve) c->qrw = qr_carve(c->ws + o, (int)m, (int)chi);
+  }
+  {
+    size_t o = off;
+    off += 256;
+    if (carve) c->err = reinterpret_cast<int*>(c->ws + o);
+  }
+  if (cfg.with_grad) {
+    size_t gb = grad_bytes((int)d, (int)D, (int)chi);
+    size_t o = off;
+    off += al(gb);
+    if (carve) { c->G = c->ws + o; c->G_bytes = gb; }
+  } else if (carve) {
+    c->G = nullptr; c->G_bytes = 0;
+  }
+  if (carve) c->split_layers = split;
+  return off;
+}
+
+size_t grad_bytes(int, int, int) { return 256; }
+
+}  // namespace qrctm
+
+extern "C" {
+
+const char* qrctm_version(void) { return "qrctm-b300 0.1 (sm_103a)"; }
+
+size_t qrctm_workspace_bytes(const qrctm_config* cfg) {
+  if (!cfg || !cfg_valid(*cfg)) return 0;
+  return make_plan(*cfg, false, nullptr);
+}
+
+qrctm_status qrctm_create(const qrctm_config* cfg, void* workspace, size_t bytes,
+                          qrctm_ctx** out) {
+  if (!cfg || !out || !workspace) return QRCTM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!cfg_valid(*cfg)) return QRCTM_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return QRCTM_ERR_INVALID_ARG;
+  const size_t need = qrctm_workspace_bytes(cfg);
+  if (bytes < need) return QRCTM_ERR_WORKSPACE;
+  qrctm_ctx* c = new (std::nothrow) qrctm_ctx();
+  if (!c) return QRCTM_ERR_INVALID_ARG;
+  c->cfg = *cfg;
+  if (c->cfg.check_every <= 0) c->cfg.check_every = 1;
+  if (c->cfg.grad_max_iter <= 0) c->cfg.grad_max_iter = 200;
+  if (c->cfg.grad_tol <= 0) c->cfg.grad_tol = 1e-12;
+  c->st = reinterpret_cast<cudaStream_t>(cfg->stream);
+  c->d = cfg->d; c->D = cfg->D; c->D2 = cfg->D * cfg->D; c->chi = cfg->chi;
+  c->chi_cur = 0;
+  c->split_prec = cfg->precision == QRCTM_SPLIT;
+  c->ws = static_cast<char*>(workspace);
+  c->ws_bytes = bytes;
+  make_plan(c->cfg, true, c);
+  c->iters = 0;
+  c->last_delta = INFINITY;
+  c->have_env = false;
+  c->spec_valid = false;
+  // zero the control words (error flag, QR grid barrier)
+  cudaError_t e = cudaMemsetAsync(c->err, 0, 256, c->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->qrw.bar, 0, sizeof(GridBar), c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) { delete c; return QRCTM_ERR_CUDA; }
+  c->qrw.err = c->err;   // QR kernels report through the context's error word
+  *out = c;
+  return QRCTM_OK;
+}
+
+void qrctm_destroy(qrctm_ctx* ctx) { delete ctx; }
+
+int qrctm_iterations(const qrctm_ctx* ctx) { return ctx ? ctx->iters : 0; }
+
+const char* qrctm_last_error(const qrctm_ctx* ctx) {
+  return ctx ? ctx->last_error.c_str() : "null context";
+}
+
+qrctm_status qrctm_init_env(qrctm_ctx* c, const double* A, const double* C0, const double* T0) {
+  if (!c || !A) return QRCTM_ERR_INVALID_ARG;
+  if ((C0 == nullptr) != (T0 == nullptr))
+    return set_err(c, QRCTM_ERR_INVALID_ARG, "C0 and T0 must both be given or both NULL");
+  const int d = c->d, D = c->D, D2 = c->D2;
+  const long long nA = (long long)d * D2 * D2;
+  c->have_env = false;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(c->A, A, sizeof(double) * nA, cudaMemcpyDeviceToDevice, c->st)) !=
+      cudaSuccess)
+    return cuda_fail(c, e, "copy A");
+  // C4v check: ||A - sym(A)|| <= 1e-12 ||A||
+  if ((e = c4v_symmetrize(d, D, c->A, c->tmpA, c->st)) != cudaSuccess)
+    return cuda_fail(c, e, "sym A");
+  if ((e = axpby(c->tmpA, c->A, 1.0, -1.0, nA, c->st)) != cudaSuccess)
+    return cuda_fail(c, e, "sym A");
+  if ((e = sum_squares_partials(c->tmpA, nA, c->partials, 64, c->st)) != cudaSuccess)
+    return cuda_fail(c, e, "sym A");
+  if ((e = sum_squares_partials(c->A, nA, c->partials + 64, 64, c->st)) != cudaSuccess)
+    return cuda_fail(c, e, "sym A");
+  {
+    double h[128];
+    if ((e = cudaMemcpyAsync(h, c->partials, sizeof(h), cudaMemcpyDeviceToHost, c->st)) !=
+        cudaSuccess)
+      return cuda_fail(c, e, "sym A");
+    if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(c, e, "sym A");
+    double dsym = 0, nrm = 0;
+    for (int i = 0; i < 64; ++i) { dsym += h[i]; nrm += h[64 + i]; }
+    if (!(nrm > 0) || !std::isfinite(nrm))
+      return set_err(c, QRCTM_ERR_NUMERIC, "A has zero or non-finite norm");
+    if (std::sqrt(dsym) > 1e-12 * std::sqrt(nrm))
+      return set_err(c, QRCTM_ERR_NOT_SYMMETRIC, "A is not C4v symmetric");
+  }
+  if (!c->split_layers) {
+    if ((e = double_layer_kernel(d, D, c->A, c->a, c->st)) != cudaSuccess)
+      return cuda_fail(c, e, "double layer");
+  }
+  c->iters = 0;
+  c->spec_valid = false;
+  if (C0 != nullptr) {
+    c->chi_cur = c->chi;
+    if ((e = sym_norm_env(C0, T0, c->C, c->T, c->chi, D2, c->partials, c->err, c->st)) !=
+        cudaSuccess)
+      return cuda_fail(c, e, "init env");
+  } else {
+    // boundary from the bulk tensor, chi0 = D^2 (<= chi, checked in cfg_valid)
+    if ((e = init_env_kernel(d, D, c->A, c->Craw, c->Traw, c->st)) != cudaSuccess)
+      return cuda_fail(c, e, "init env");
+    c->chi_cur = D2;
+    if ((e = sym_norm_env(c->Craw, c->Traw, c->C, c->T, D2, D2, c->partials, c->err, c->st)) !=
+        cudaSuccess)
+      return cuda_fail(c, e, "init env");
+    int nw = c->cfg.warmup_steps;
+    if (nw == 0) {
+      long long cc = c->chi_cur;
+      while (cc < c->chi && D2 > 1) { cc *= D2; ++nw; }
+      if (nw < 2) nw = 2;
+    }
+    for (int w = 0; w < nw; ++w) {
+      int ci = c->chi_cur;
+      int co = (int)std::min<long long>(c->chi, (long long)ci * D2);
+      if ((e = warmup_step(c, ci, co)) != cudaSuccess) return cuda_fail(c, e, "warm-up");
+    }
+  }
+  qrctm_status s = sync_check(c, "init env");
+  if (s != QRCTM_OK) return s;
+  if ((e = spectrum_check(c)) != cudaSuccess) return cuda_fail(c, e, "spectrum");
+  s = sync_check(c, "spectrum");
+  if (s != QRCTM_OK) return s;
+  c->spec_valid = true;
+  c->have_env = true;
+  return QRCTM_OK;
+}
+
+qrctm_status qrctm_step(qrctm_ctx* c, int n, double* delta_out) {
+  if (!c || n < 0) return QRCTM_ERR_INVALID_ARG;
+  if (!c->have_env) return set_err(c, QRCTM_ERR_STATE, "qrctm_init_env not called");
+  cudaError_t e;
+  for (int i = 0; i < n; ++i)
+    if ((e = qr_step(c)) != cudaSuccess) return cuda_fail(c, e, "qr step");
+  if (delta_out) {
+    if ((e = spectrum_check(c)) != cudaSuccess) return cuda_fail(c, e, "spectrum");
+    qrctm_status s = sync_check(c, "step");
+    if (s != QRCTM_OK) return s;
+    double dlt;
+    if ((e = cudaMemcpy(&dlt, c->delta_d, sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(c, e, "delta");
+    c->last_delta = dlt;
+    *delta_out = dlt;
+    return QRCTM_OK;
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "step");
+  return QRCTM_OK;
+}
+
+qrctm_status qrctm_run_to_convergence(qrctm_ctx* c, double tol, int max_iter, int* iters_out,
+                                      double* delta_out) {
+  if (!c) return QRCTM_ERR_INVALID_ARG;
+  if (!c->have_env) return set_err(c, QRCTM_ERR_STATE, "qrctm_init_env not called");
+  if (tol <= 0) tol = c->cfg.tol > 0 ? c->cfg.tol : 1e-10;
+  if (max_iter <= 0) max_iter = c->cfg.max_iter > 0 ? c->cfg.max_iter : 500;
+  const int ce = c->cfg.check_every;
+  int done = 0;
+  double dlt = INFINITY;
+  qrctm_status s = QRCTM_OK;
+  while (done < max_iter) {
+    int n = std::min(ce, max_iter - done);
+    s = qrctm_step(c, n, &dlt);
+    if (s != QRCTM_OK) break;
+    done += n;
+    if (dlt < tol) break;
+  }
+  if (iters_out) *iters_out = done;
+  if (delta_out) *delta_out = dlt;
+  if (s != QRCTM_OK) return s;
+  if (!(dlt < tol)) return set_err(c, QRCTM_ERR_NOT_CONVERGED, "max_iter reached");
+  return QRCTM_OK;
+}
+
+qrctm_status qrctm_energy(qrctm_ctx* c, const qrctm_model* model, double* e_out) {
+  if (!c || !model || !e_out) return QRCTM_ERR_INVALID_ARG;
+  if (!c->have_env) return set_err(c, QRCTM_ERR_STATE, "qrctm_init_env not called");
+  if (c->d != 2) return set_err(c, QRCTM_ERR_INVALID_ARG, "the spin-1/2 energy needs d = 2");
+  if (model->J2 != 0.0 && c->E3 == nullptr)
+    return set_err(c, QRCTM_ERR_INVALID_ARG, "J2 != 0 needs with_nnn = 1");
+  cudaError_t e = energy_fp64(c, model->J1, model->J2);
+  if (e != cudaSuccess) return cuda_fail(c, e, "energy");
+  qrctm_status s = sync_check(c, "energy");
+  if (s != QRCTM_OK) return s;
+  double h;
+  if ((e = cudaMemcpy(&h, c->e_d, sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(c, e, "energy");
+  *e_out = h;
+  return QRCTM_OK;
+}
+
+qrctm_status qrctm_energy_grad(qrctm_ctx* c, const qrctm_model*, int, int, double*, double*) {
+  if (!c) return QRCTM_ERR_INVALID_ARG;
+  return set_err(c, QRCTM_ERR_INVALID_ARG, "energy gradient not available in this build");
+}
+
+qrctm_status qrctm_get_env(qrctm_ctx* c, double* C, double* T, double* spectrum_host) {
+  if (!c) return QRCTM_ERR_INVALID_ARG;
+  if (!c->have_env) return set_err(c, QRCTM_ERR_STATE, "qrctm_init_env not called");
+  cudaError_t e;
+  const long long nC = (long long)c->chi_cur * c->chi_cur;
+  const long long nT = (long long)c->chi_cur * c->D2 * c->chi_cur;
+  if (C && (e = cudaMemcpyAsync(C, c->C, sizeof(double) * nC, cudaMemcpyDeviceToDevice, c->st)) !=
+               cudaSuccess)
+    return cuda_fail(c, e, "get env");
+  if (T && (e = cudaMemcpyAsync(T, c->T, sizeof(double) * nT, cudaMemcpyDeviceToDevice, c->st)) !=
+               cudaSuccess)
+    return cuda_fail(c, e, "get env");
+  if (spectrum_host) {
+    if ((e = spectrum_check(c)) != cudaSuccess) return cuda_fail(c, e, "spectrum");
+    qrctm_status s = sync_check(c, "spectrum");
+    if (s != QRCTM_OK) return s;
+    if ((e = cudaMemcpy(spectrum_host, c->s_cur, sizeof(double) * c->chi_cur,
+                        cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(c, e, "spectrum");
+  }
+  return sync_check(c, "get env");
+}
+
+size_t qrctm_c4v_symmetrize_workspace_bytes(void) { return 256 * sizeof(double); }
+
+qrctm_status qrctm_c4v_symmetrize(int d, int D, const double* X, double* Y, int normalize,
+                                  void* workspace, size_t bytes, void* stream) {
+  if (d < 1 || D < 1 || !X || !Y || X == Y) return QRCTM_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (normalize && (!workspace || bytes < qrctm_c4v_symmetrize_workspace_bytes()))
+    return QRCTM_ERR_WORKSPACE;
+  cudaError_t e = c4v_symmetrize(d, D, X, Y, s);
+  if (e != cudaSuccess) return QRCTM_ERR_CUDA;
+  if (normalize) {
+    double* parts = static_cast<double*>(workspace);
+    int* err = reinterpret_cast<int*>(parts + 128);
+    const long long n = (long long)d * D * D * D * D;
+    if ((e = cudaMemsetAsync(err, 0, sizeof(int), s)) != cudaSuccess) return QRCTM_ERR_CUDA;
+    if ((e = sum_squares_partials(Y, n, parts, 64, s)) != cudaSuccess) return QRCTM_ERR_CUDA;
+    if ((e = scale_by_inv_norm(Y, Y, n, parts, 64, err, s)) != cudaSuccess) return QRCTM_ERR_CUDA;
+    int flag = 0;
+    if ((e = cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      return QRCTM_ERR_CUDA;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return QRCTM_ERR_CUDA;
+    if (flag) return QRCTM_ERR_NUMERIC;
+  }
+  return QRCTM_OK;
+}
+
+size_t qrctm_qr_workspace_bytes(int m, int n) {
+  if (m < n || n < 1) return 0;
+  return qr_work_bytes(m, n);
+}
+
+qrctm_status qrctm_householder_qr(int m, int n, const double* M, double* Q, double* R,
+                                  void* workspace, size_t bytes, void* stream) {
+  if (m < n || n < 1 || !M || !Q || !R || !workspace) return QRCTM_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return QRCTM_ERR_INVALID_ARG;
+  if (bytes < qrctm_qr_workspace_bytes(m, n)) return QRCTM_ERR_WORKSPACE;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  QrWork w = qr_carve(workspace, m, n);
+  cudaError_t e = householder_qr_f64(m, n, M, Q, R, w, s);
+  if (e != cudaSuccess) return QRCTM_ERR_CUDA;
+  int flag = 0;
+  if ((e = cudaMemcpyAsync(&flag, w.err, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return QRCTM_ERR_CUDA;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return QRCTM_ERR_CUDA;
+  if (flag) {
+    cudaMemsetAsync(w.err, 0, sizeof(int), s);
+    cudaStreamSynchronize(s);
+    return (flag & ERRF_TIMEOUT) ? QRCTM_ERR_TIMEOUT : QRCTM_ERR_NUMERIC;
+  }
+  return QRCTM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,65 @@
+// Library context: configuration, workspace carving and the per-step
+// device buffers of the QR-CTMRG iteration.
+#pragma once
+
+#include <string>
+
+#include "qrctm.h"
+#include "qrctm_internal.cuh"
+
+struct qrctm_ctx {
+  qrctm_config cfg;
+  cudaStream_t st;
+  int d, D, D2, chi;   // chi = target environment bond
+  int chi_cur;         // current bond (< chi only if the warm-up could not grow it)
+  bool split_layers;
+  bool split_prec;
+  // workspace
+  char* ws;
+  size_t ws_bytes;
+  // state
+  double *A, *C, *T, *Cn, *Tn, *Craw, *Traw;
+  // step intermediates
+  double *Mcm, *Q, *R, *X1, *Z, *X2, *Y2;
+  // warm-up
+  double *Xs, *Yw;
+  // spectrum
+  double *spec_work, *s_cur, *s_prev, *delta_d;
+  double* partials;
+  double* tmpA;
+  double* a;           // double layer (only with DOUBLE layers)
+  // energy
+  double *E1, *E2, *E3, *rho, *e_d;
+  // gradient
+  char* G;             // gradient region base (carved by grad.cu)
+  size_t G_bytes;
+  qrctm::QrWork qrw;
+  int* err;
+  int iters;
+  double last_delta;
+  bool have_env;
+  bool spec_valid;
+  std::string last_error;
+};
+
+namespace qrctm {
+
+// Workspace plan (api.cu); 256-byte aligned regions.
+size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* ctx);
+
+// Steps (ctmrg.cu)
+cudaError_t reduced_corner(qrctm_ctx* c, const double* C, const double* T, int chi_in,
+                           double* Mcm);
+cudaError_t renorm_edge(qrctm_ctx* c, const double* P, int chi_out, const double* T,
+                        int chi_in, double* Tout);
+cudaError_t qr_step(qrctm_ctx* c);
+cudaError_t warmup_step(qrctm_ctx* c, int chi_in, int chi_out);
+cudaError_t spectrum_check(qrctm_ctx* c);
+
+// Energy (energy.cu)
+cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2);
+
+// Gradient (grad.cu)
+size_t grad_bytes(int d, int D, int chi);
+
+}  // namespace qrctm

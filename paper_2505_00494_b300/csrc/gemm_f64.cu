@@ -1,0 +1,108 @@
+// FP64 CUDA-core contraction engine (any layout, through mixed-radix maps).
+//
+// Used by the plain FP64 path of every contraction in the QR-CTMRG step
+// (QR-CTMRG paragraph, Fig. 1(e,f)), by the compact-WY updates of the
+// Householder QR and by the reduced density matrices.  On B300 the FP64 pipe
+// is narrow, so the kernel is arithmetic bound: a 64x64x16 shared-memory
+// tile with a 4x4 register block per thread is enough to keep it busy.
+#include "qrctm_internal.cuh"
+
+namespace qrctm {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+__global__ void __launch_bounds__(NT) gemm_f64_kernel(Gemm g) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  __shared__ long long aRow[BM], bCol[BN], aK[BK], bK[BK];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const long long m0 = (long long)blockIdx.x * BM;
+  const long long n0 = (long long)blockIdx.y * BN;
+
+  for (long long b = blockIdx.z; b < g.batch; b += gridDim.z) {
+    const long long aB = map_off(g.a_b, b), bB = map_off(g.b_b, b), cB = map_off(g.c_b, b);
+    __syncthreads();
+    if (tid < BM) {
+      long long m = m0 + tid;
+      aRow[tid] = (m < g.M) ? map_off(g.a_m, m) : -1;
+    } else if (tid < BM + BN) {
+      long long n = n0 + tid - BM;
+      bCol[tid - BM] = (n < g.N) ? map_off(g.b_n, n) : -1;
+    }
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+    for (long long k0 = 0; k0 < g.K; k0 += BK) {
+      if (tid < BK) {
+        long long k = k0 + tid;
+        aK[tid] = (k < g.K) ? map_off(g.a_k, k) : -1;
+      } else if (tid < 2 * BK) {
+        long long k = k0 + tid - BK;
+        bK[tid - BK] = (k < g.K) ? map_off(g.b_k, k) : -1;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < (BM * BK) / NT; ++q) {
+        int e = tid + NT * q;
+        int r = e % BM, kk = e / BM;
+        long long ro = aRow[r], ko = aK[kk];
+        As[kk][r] = (ro >= 0 && ko >= 0) ? g.A[aB + ro + ko] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < (BN * BK) / NT; ++q) {
+        int e = tid + NT * q;
+        int c = e % BN, kk = e / BN;
+        long long co = bCol[c], ko = bK[kk];
+        Bs[kk][c] = (co >= 0 && ko >= 0) ? g.B[bB + co + ko] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        double av[4], bv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      long long m = m0 + ty + 16 * i;
+      if (m >= g.M) continue;
+      long long ro = map_off(g.c_m, m);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        long long n = n0 + tx + 16 * j;
+        if (n >= g.N) continue;
+        double* p = g.C + cB + ro + map_off(g.c_n, n);
+        double v = g.alpha * acc[i][j];
+        if (g.beta != 0.0) v += g.beta * *p;
+        *p = v;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t gemm_f64(const Gemm& g, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+  long long gx = (g.M + BM - 1) / BM, gy = (g.N + BN - 1) / BN;
+  if (gx > 0x7fffffffll || gy > 65535) return cudaErrorInvalidValue;
+  int gz = g.batch < 65535 ? g.batch : 65535;
+  gemm_f64_kernel<<<dim3((unsigned)gx, (unsigned)gy, gz), NT, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+}  // namespace qrctm

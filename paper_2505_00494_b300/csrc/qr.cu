@@ -1,0 +1,317 @@
+// Blocked Householder QR of the reduced corner (QR-CTMRG paragraph: the
+// isometry Q of an unpivoted QR of ct replaces the eigenvectors U).
+//
+// Layout: the m x n input is column-major (each column of ct contiguous).
+// Panels of nb <= 32 columns are factored by one cooperative kernel spread
+// over the whole GPU (one bounded grid barrier per column, FP64 reductions);
+// the trailing matrix and the explicit Q are updated with the compact WY
+// form H_1...H_nb = I - V T V^T through the contraction engine.
+//
+// Reflector choice: H x = ||x|| e_1 with v = x - ||x|| e_1, whose first entry
+// is evaluated as -sigma / (x_0 + ||x||) when x_0 > 0 (Parlett's rearrangement,
+// no cancellation).  This yields diag(R) >= 0 directly, the sign convention
+// under which the thin QR of a full-rank matrix is unique.
+#include "qrctm_internal.cuh"
+
+#include <algorithm>
+
+namespace qrctm {
+
+namespace {
+
+constexpr int NB = 32;       // panel width (one warp lane per panel column)
+constexpr int PT = 256;      // threads per panel CTA (8 row lanes x 32 columns)
+constexpr int PMAX = 1024;   // upper bound on panel CTAs (scratch sizing)
+
+__host__ __device__ inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+__global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
+                                                      double* __restrict__ V,
+                                                      double* __restrict__ Tf,
+                                                      double* __restrict__ part, GridBar* bar,
+                                                      int* err, int m, int j0, int nb,
+                                                      int rows_per_cta) {
+  const int P = gridDim.x, b = blockIdx.x;
+  const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;   // wrp = row lane (0..7)
+  const long long r_begin = (long long)j0 + (long long)b * rows_per_cta;
+  const long long r_end = std::min<long long>(m, r_begin + rows_per_cta);
+  // scratch: psum[2][P][NB], rowb[2][NB], gram[P][NB*NB]
+  double* psum = part;
+  double* rowb = part + 2 * (size_t)P * NB;
+  double* gram = rowb + 2 * NB;
+  __shared__ double red[8][NB];
+  __shared__ double tot[NB];
+  __shared__ double sc[4];
+  __shared__ double tau_s[NB];
+
+  // partial sums for column j (slot 0: sum x_i^2 over i > c; slot t: sum x_i y_{c+t,i})
+  auto partials = [&](int j, int buf) {
+    const long long c = (long long)j0 + j;
+    const int nrem = nb - j - 1;
+    double acc = 0.0;
+    const long long i0 = std::max<long long>(r_begin, c + 1);
+    if (lane <= nrem) {
+      const double* xc = W + c * m;
+      const double* yc = W + (c + lane) * m;
+      for (long long i = i0 + wrp; i < r_end; i += 8) acc = fma(xc[i], yc[i], acc);
+    }
+    red[wrp][lane] = acc;
+    __syncthreads();
+    if (threadIdx.x < NB) {
+      double s = 0.0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
+      psum[((size_t)buf * P + b) * NB + threadIdx.x] = s;
+    }
+    // the owner of row c publishes row c (x_0 and the y_0 of the other columns)
+    if (c >= r_begin && c < r_end && (int)threadIdx.x <= nrem)
+      rowb[buf * NB + threadIdx.x] = W[(c + threadIdx.x) * m + c];
+    __syncthreads();
+  };
+
+  partials(0, 0);
+  if (!grid_barrier(bar, P, err)) return;
+
+  for (int j = 0; j < nb; ++j) {
+    const int buf = j & 1;
+    const long long c = (long long)j0 + j;
+    const int nrem = nb - j - 1;
+    if ((int)threadIdx.x <= nrem) {
+      double s = 0.0;
+      for (int q = 0; q < P; ++q) s += psum[((size_t)buf * P + q) * NB + threadIdx.x];
+      tot[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double x0 = rowb[buf * NB];
+      const double sigma = tot[0];
+      const double mu = sqrt(x0 * x0 + sigma);
+      double tau, inv_v0;
+      if (sigma == 0.0) {
+        tau = (x0 < 0.0) ? 2.0 : 0.0;      // v = e_1
+        inv_v0 = 0.0;
+      } else {
+        const double v0 = (x0 <= 0.0) ? (x0 - mu) : (-sigma / (x0 + mu));
+        tau = 2.0 * v0 * v0 / (sigma + v0 * v0);
+        inv_v0 = 1.0 / v0;
+      }
+      if (!(mu == mu) || isinf(mu)) atomicOr(err, ERRF_NUMERIC);
+      sc[0] = tau; sc[1] = inv_v0; sc[2] = mu;
+      tau_s[j] = tau;
+    }
+    __syncthreads();
+    const double tau = sc[0], inv_v0 = sc[1], mu = sc[2];
+    // coefficient of column c+t (t >= 1): tau * (y_0 + s_t / v_0)
+    double coef = 0.0;
+    if (lane >= 1 && lane <= nrem) coef = tau * (rowb[buf * NB + lane] + tot[lane] * inv_v0);
+    {
+      const long long i0 = std::max<long long>(r_begin, c + 1);
+      double* xc = W + c * m;
+      for (long long i = i0 + wrp; i < r_end; i += 8) {
+        const double v = xc[i] * inv_v0;
+        if (lane >= 1 && lane <= nrem) W[(c + lane) * m + i] -= coef * v;
+        __syncwarp();
+        if (lane == 0) { xc[i] = v; V[c * m + i] = v; }
+        __syncwarp();
+      }
+      // explicit reflector column: zeros above c inside the panel rows, 1 at c
+      for (long long i = r_begin + threadIdx.x; i < std::min<long long>(r_end, c + 1); i += PT)
+        V[c * m + i] = (i == c) ? 1.0 : 0.0;
+      // row c itself: the R entries
+      if (c >= r_begin && c < r_end) {
+        if (lane == 0 && wrp == 0) W[c * m + c] = mu;
+        if (wrp == 0 && lane >= 1 && lane <= nrem) W[(c + lane) * m + c] -= coef;
+      }
+    }
+    __syncthreads();
+    if (j + 1 < nb) partials(j + 1, buf ^ 1);
+    if (!grid_barrier(bar, P, err)) return;
+  }
+
+  // Gram matrix of the explicit reflectors for the compact-WY factor
+  for (int e = threadIdx.x; e < nb * nb; e += PT) {
+    const int p = e / nb, q = e % nb;
+    double s = 0.0;
+    if (q >= p) {
+      const long long i0 = std::max<long long>(r_begin, (long long)j0 + q);
+      for (long long i = i0; i < r_end; ++i)
+        s = fma(V[((long long)j0 + p) * m + i], V[((long long)j0 + q) * m + i], s);
+    }
+    gram[(size_t)b * NB * NB + e] = s;
+  }
+  if (!grid_barrier(bar, P, err)) return;
+  if (b != 0) return;
+  // T (upper triangular, nb x nb, row-major): T_jj = tau_j,
+  // T[0:j, j] = -tau_j T[0:j, 0:j] G[0:j, j]
+  __shared__ double Gs[NB][NB + 1];
+  __shared__ double Ts[NB][NB + 1];
+  for (int e = threadIdx.x; e < nb * nb; e += PT) {
+    double s = 0.0;
+    for (int q = 0; q < P; ++q) s += gram[(size_t)q * NB * NB + e];
+    Gs[e / nb][e % nb] = s;
+    Ts[e / nb][e % nb] = 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    double val = 0.0;
+    const int i = threadIdx.x;
+    if (i < j) {
+      for (int l = i; l < j; ++l) val = fma(Ts[i][l], Gs[l][j], val);
+      val *= -tau_s[j];
+    }
+    __syncthreads();
+    if (i < j) Ts[i][j] = val;
+    if (i == j) Ts[j][j] = tau_s[j];
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < nb * nb; e += PT) Tf[(e / nb) * NB + (e % nb)] = Ts[e / nb][e % nb];
+}
+
+__global__ void extract_r_kernel(const double* __restrict__ W, double* __restrict__ R, int m,
+                                 int n) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  int i = (int)(e / n), j = (int)(e % n);
+  R[e] = (j >= i) ? W[(long long)j * m + i] : 0.0;
+}
+
+__global__ void set_identity_cols_kernel(double* Q, int m, int n) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)m * n) return;
+  long long col = e / m, row = e % m;
+  Q[e] = (row == col) ? 1.0 : 0.0;
+}
+
+}  // namespace
+
+int qr_panel_grid(int mrows) {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+  }
+  int p = (mrows + 31) / 32;
+  return std::max(1, std::min(std::min(p, nsm), PMAX));
+}
+
+size_t qr_work_bytes(int m, int n) {
+  const int npan = (n + NB - 1) / NB;
+  size_t b = 0;
+  b += align_up(sizeof(double) * (size_t)m * n);            // W
+  b += align_up(sizeof(double) * (size_t)m * n);            // V
+  b += align_up(sizeof(double) * (size_t)NB * NB * npan);   // Tf
+  b += align_up(sizeof(double) * (size_t)NB * n);           // Y
+  b += align_up(sizeof(double) * (size_t)NB * n);           // Y2
+  b += align_up(sizeof(double) * ((size_t)2 * PMAX * NB + 2 * NB + (size_t)PMAX * NB * NB));
+  b += align_up(sizeof(GridBar));
+  b += align_up(sizeof(int));
+  return b;
+}
+
+QrWork qr_carve(void* base, int m, int n) {
+  const int npan = (n + NB - 1) / NB;
+  char* p = static_cast<char*>(base);
+  QrWork w;
+  w.W = reinterpret_cast<double*>(p); p += align_up(sizeof(double) * (size_t)m * n);
+  w.V = reinterpret_cast<double*>(p); p += align_up(sizeof(double) * (size_t)m * n);
+  w.Tf = reinterpret_cast<double*>(p); p += align_up(sizeof(double) * (size_t)NB * NB * npan);
+  w.Y = reinterpret_cast<double*>(p); p += align_up(sizeof(double) * (size_t)NB * n);
+  w.Y2 = reinterpret_cast<double*>(p); p += align_up(sizeof(double) * (size_t)NB * n);
+  w.part = reinterpret_cast<double*>(p);
+  p += align_up(sizeof(double) * ((size_t)2 * PMAX * NB + 2 * NB + (size_t)PMAX * NB * NB));
+  w.bar = reinterpret_cast<GridBar*>(p); p += align_up(sizeof(GridBar));
+  w.err = reinterpret_cast<int*>(p);
+  return w;
+}
+
+cudaError_t set_identity_cols(double* Q, int m, int n, cudaStream_t s) {
+  long long tot = (long long)m * n;
+  set_identity_cols_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Q, m, n);
+  return cudaGetLastError();
+}
+
+// M (m x n, column-major, m >= n) -> Q (m x n, column-major), R (n x n, row-major).
+// The grid barrier in `w` must be zero on entry; it is left zero on exit.
+cudaError_t householder_qr_f64(int m, int n, const double* M, double* Q, double* R,
+                               const QrWork& w, cudaStream_t s) {
+  if (m < n || n <= 0) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemcpyAsync(w.W, M, sizeof(double) * (size_t)m * n,
+                                  cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return e;
+  const int npan = (n + NB - 1) / NB;
+  for (int p = 0; p < npan; ++p) {
+    const int j0 = p * NB;
+    const int nbj = std::min(NB, n - j0);
+    const int mr = m - j0;
+    const int P = qr_panel_grid(mr);
+    int rpc = (mr + P - 1) / P;
+    double* Tp = w.Tf + (size_t)p * NB * NB;
+    double* W = w.W; double* V = w.V; double* part = w.part;
+    GridBar* bar = w.bar; int* err = w.err;
+    int m_ = m, j0_ = j0, nb_ = nbj;
+    void* args[] = {&W, &V, &Tp, &part, &bar, &err, &m_, &j0_, &nb_, &rpc};
+    e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel, dim3(P), dim3(PT), args, 0, s);
+    if (e != cudaSuccess) return e;
+    const int n2 = n - j0 - nbj;
+    if (n2 > 0) {
+      Gemm g = gemm_init();
+      // Y = V^T W2   (nbj x n2, K = mr)
+      g.M = nbj; g.N = n2; g.K = mr;
+      g.A = w.V + (size_t)j0 * m + j0; g.a_m = im1(m); g.a_k = im1(1);
+      g.B = w.W + (size_t)(j0 + nbj) * m + j0; g.b_k = im1(1); g.b_n = im1(m);
+      g.C = w.Y; g.c_m = im1(n2); g.c_n = im1(1);
+      if ((e = gemm_f64(g, s)) != cudaSuccess) return e;
+      // Y2 = T^T Y   (nbj x n2, K = nbj)
+      g.M = nbj; g.N = n2; g.K = nbj;
+      g.A = Tp; g.a_m = im1(1); g.a_k = im1(NB);
+      g.B = w.Y; g.b_k = im1(n2); g.b_n = im1(1);
+      g.C = w.Y2; g.c_m = im1(n2); g.c_n = im1(1);
+      if ((e = gemm_f64(g, s)) != cudaSuccess) return e;
+      // W2 -= V Y2   (mr x n2, K = nbj)
+      g.M = mr; g.N = n2; g.K = nbj;
+      g.A = w.V + (size_t)j0 * m + j0; g.a_m = im1(1); g.a_k = im1(m);
+      g.B = w.Y2; g.b_k = im1(n2); g.b_n = im1(1);
+      g.C = w.W + (size_t)(j0 + nbj) * m + j0; g.c_m = im1(1); g.c_n = im1(m);
+      g.alpha = -1.0; g.beta = 1.0;
+      if ((e = gemm_f64(g, s)) != cudaSuccess) return e;
+    }
+  }
+  {
+    long long tot = (long long)n * n;
+    extract_r_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(w.W, R, m, n);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // Q = H_1 ... H_n [I; 0], applying the panels in reverse order
+  if ((e = set_identity_cols(Q, m, n, s)) != cudaSuccess) return e;
+  for (int p = npan - 1; p >= 0; --p) {
+    const int j0 = p * NB;
+    const int nbj = std::min(NB, n - j0);
+    const int mr = m - j0, nq = n - j0;
+    const double* Tp = w.Tf + (size_t)p * NB * NB;
+    Gemm g = gemm_init();
+    // Y = V^T Qs   (nbj x nq, K = mr)
+    g.M = nbj; g.N = nq; g.K = mr;
+    g.A = w.V + (size_t)j0 * m + j0; g.a_m = im1(m); g.a_k = im1(1);
+    g.B = Q + (size_t)j0 * m + j0; g.b_k = im1(1); g.b_n = im1(m);
+    g.C = w.Y; g.c_m = im1(nq); g.c_n = im1(1);
+    if ((e = gemm_f64(g, s)) != cudaSuccess) return e;
+    // Y2 = T Y
+    g.M = nbj; g.N = nq; g.K = nbj;
+    g.A = Tp; g.a_m = im1(NB); g.a_k = im1(1);
+    g.B = w.Y; g.b_k = im1(nq); g.b_n = im1(1);
+    g.C = w.Y2; g.c_m = im1(nq); g.c_n = im1(1);
+    if ((e = gemm_f64(g, s)) != cudaSuccess) return e;
+    // Qs -= V Y2
+    g.M = mr; g.N = nq; g.K = nbj;
+    g.A = w.V + (size_t)j0 * m + j0; g.a_m = im1(1); g.a_k = im1(m);
+    g.B = w.Y2; g.b_k = im1(nq); g.b_n = im1(1);
+    g.C = Q + (size_t)j0 * m + j0; g.c_m = im1(1); g.c_n = im1(m);
+    g.alpha = -1.0; g.beta = 1.0;
+    if ((e = gemm_f64(g, s)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace qrctm

@@ -1,0 +1,168 @@
+// Internal declarations shared by the QR-CTMRG CUDA sources.
+//
+// Every contraction of the method is expressed as a (batched) matrix product
+// whose operands and result are addressed through mixed-radix index maps:
+// an index i is split into digits (innermost first) and each digit carries
+// its own element stride.  This lets one GEMM kernel read and write every
+// tensor layout of the step (reshape + permute folded into the addressing).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qrctm {
+
+// ---------------------------------------------------------------------------
+// Mixed-radix index map: offset(i) = sum_t digit_t(i) * str[t].
+// digit_0 = i % rad[0], digit_1 = (i / rad[0]) % rad[1], ...; the last used
+// digit takes the remaining quotient (its radix is ignored).
+// ---------------------------------------------------------------------------
+constexpr int kMaxDigits = 6;
+struct IdxMap {
+  int nd;
+  int rad[kMaxDigits];
+  long long str[kMaxDigits];
+};
+
+static inline IdxMap im0() { IdxMap m{}; m.nd = 1; m.rad[0] = 1; m.str[0] = 0; return m; }
+static inline IdxMap im1(long long s0) { IdxMap m{}; m.nd = 1; m.rad[0] = 1; m.str[0] = s0; return m; }
+static inline IdxMap im2(int r0, long long s0, long long s1) {
+  IdxMap m{}; m.nd = 2; m.rad[0] = r0; m.str[0] = s0; m.str[1] = s1; return m;
+}
+static inline IdxMap im3(int r0, int r1, long long s0, long long s1, long long s2) {
+  IdxMap m{}; m.nd = 3; m.rad[0] = r0; m.rad[1] = r1; m.str[0] = s0; m.str[1] = s1; m.str[2] = s2;
+  return m;
+}
+static inline IdxMap im4(int r0, int r1, int r2, long long s0, long long s1, long long s2,
+                         long long s3) {
+  IdxMap m{}; m.nd = 4; m.rad[0] = r0; m.rad[1] = r1; m.rad[2] = r2;
+  m.str[0] = s0; m.str[1] = s1; m.str[2] = s2; m.str[3] = s3; return m;
+}
+static inline IdxMap im5(int r0, int r1, int r2, int r3, long long s0, long long s1,
+                         long long s2, long long s3, long long s4) {
+  IdxMap m{}; m.nd = 5; m.rad[0] = r0; m.rad[1] = r1; m.rad[2] = r2; m.rad[3] = r3;
+  m.str[0] = s0; m.str[1] = s1; m.str[2] = s2; m.str[3] = s3; m.str[4] = s4; return m;
+}
+
+__host__ __device__ __forceinline__ long long map_off(const IdxMap& m, long long i) {
+  long long off = 0;
+#pragma unroll
+  for (int t = 0; t < kMaxDigits; ++t) {
+    if (t >= m.nd) break;
+    if (t == m.nd - 1) {
+      off += i * m.str[t];
+    } else {
+      long long q = i / m.rad[t];
+      off += (i - q * m.rad[t]) * m.str[t];
+      i = q;
+    }
+  }
+  return off;
+}
+
+// C[b](m,n) = alpha * sum_k A[b](m,k) B[b](k,n) + beta * C[b](m,n)
+struct Gemm {
+  long long M, N, K;
+  int batch;
+  const double* A; IdxMap a_m, a_k, a_b;
+  const double* B; IdxMap b_k, b_n, b_b;
+  double* C;       IdxMap c_m, c_n, c_b;
+  double alpha, beta;
+};
+
+static inline Gemm gemm_init() {
+  Gemm g{};
+  g.batch = 1;
+  g.a_b = im0(); g.b_b = im0(); g.c_b = im0();
+  g.alpha = 1.0; g.beta = 0.0;
+  return g;
+}
+
+// FP64 CUDA-core contraction (any layout).  Returns cudaGetLastError().
+cudaError_t gemm_f64(const Gemm& g, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Device-side error flag bits (written by kernels, read by the host).
+// ---------------------------------------------------------------------------
+enum : int {
+  ERRF_NUMERIC = 1,      // NaN/Inf or zero norm met
+  ERRF_TIMEOUT = 2,      // a bounded wait ran out
+  ERRF_BOUNDS = 4,       // a size check inside a kernel failed
+};
+
+// Grid-wide barrier for cooperative launches.  The spin is bounded; on
+// timeout the flag ERRF_TIMEOUT is raised and false is returned so that the
+// caller can leave the kernel.
+struct GridBar {
+  unsigned int count;
+  unsigned int gen;
+};
+
+__device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned int nblocks, int* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = &bar->gen;
+    unsigned int g = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == g) {
+        if (++spins > (1ll << 25)) { ok = 0; atomicOr(err, ERRF_TIMEOUT); break; }
+        __nanosleep(20);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Householder QR (unpivoted, diag(R) >= 0) of a column-major m x n matrix.
+// ---------------------------------------------------------------------------
+struct QrWork {
+  double* W;        // m x n working copy (column-major)
+  double* V;        // m x n explicit reflectors (column-major, unit diagonal)
+  double* Tf;       // nb x nb x npanel compact-WY factors
+  double* Y;        // nb x n scratch
+  double* Y2;       // nb x n scratch
+  double* part;     // partial sums of the panel kernel
+  GridBar* bar;
+  int* err;
+};
+size_t qr_work_bytes(int m, int n);
+QrWork qr_carve(void* base, int m, int n);
+int qr_panel_grid(int m);
+cudaError_t householder_qr_f64(int m, int n, const double* M, double* Q, double* R_rowmajor,
+                               const QrWork& w, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Elementwise / reduction kernels.
+// ---------------------------------------------------------------------------
+cudaError_t c4v_symmetrize(int d, int D, const double* X, double* Y, cudaStream_t s);
+cudaError_t sum_squares_partials(const double* x, long long n, double* partials, int nparts,
+                                 cudaStream_t s);
+cudaError_t scale_by_inv_norm(const double* x, double* y, long long n, const double* partials,
+                              int nparts, int* err, cudaStream_t s);
+// C <- (C + C^T)/2 and T[a,k,b] <- (T[a,k,b] + T[b,k,a])/2, then each / ||.||_F
+cudaError_t sym_norm_env(const double* Cin, const double* Tin, double* Cout, double* Tout,
+                         int chi, int D2, double* partials, int* err, cudaStream_t s);
+cudaError_t sym_edge(const double* Tin, double* Tout, int chi, int D2, cudaStream_t s);
+cudaError_t init_env_kernel(int d, int D, const double* A, double* C0, double* T0,
+                            cudaStream_t s);
+cudaError_t double_layer_kernel(int d, int D, const double* A, double* a, cudaStream_t s);
+cudaError_t set_identity_cols(double* Q, int m, int n, cudaStream_t s);
+cudaError_t corner_spectrum(const double* C, int chi, double* work, double* s_new,
+                            const double* s_old, int chi_old, double* delta, int* err,
+                            cudaStream_t s);
+cudaError_t fill_zero(double* p, long long n, cudaStream_t s);
+cudaError_t axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t s);
+
+}  // namespace qrctm

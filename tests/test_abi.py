@@ -1,0 +1,77 @@
+"""The C-ABI library loads and exports every symbol that include/qrctm.h
+declares; host-side planning and argument checks work without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+INCLUDE = os.path.join(ROOT, "include")
+
+
+def declared_functions():
+    names = set()
+    for f in os.listdir(INCLUDE):
+        if f.endswith(".h"):
+            text = re.sub(r"/\*.*?\*/", "", open(os.path.join(INCLUDE, f)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(qrctm_\w+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_2505_00494_b300 import build
+    build.build()
+    import paper_2505_00494_b300 as q
+    return q
+
+
+def test_every_declared_symbol_is_exported(q):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(q.lib, n), n
+    assert set(names) == set(q.EXPORTED)   # the binding covers the whole header
+
+
+def test_version(q):
+    assert b"sm_103a" in q.lib.qrctm_version()
+
+
+def cfg(q, d=2, D=6, chi=144, **kw):
+    c = q.Config(d, D, chi, 0, 0, 0, 1, 1e-10, 500, 0, 0.0, 0, 0, None)
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def test_workspace_planning_host_only(q):
+    c = cfg(q)
+    b1 = q.lib.qrctm_workspace_bytes(ctypes.byref(c))
+    assert b1 > 0 and b1 % 256 == 0
+    # at least X1, Z, X2 and the open-leg energy buffer (chi D^2)^2 (1 + d + 1 + d^2)
+    m = 144 * 36
+    assert b1 >= 8 * m * m * 8
+    c.with_nnn = 1
+    assert q.lib.qrctm_workspace_bytes(ctypes.byref(c)) > b1
+    for bad in (cfg(q, chi=0), cfg(q, chi=2000), cfg(q, chi=16), cfg(q, precision=7),
+                cfg(q, warmup_steps=-2)):
+        assert q.lib.qrctm_workspace_bytes(ctypes.byref(bad)) == 0
+    assert q.lib.qrctm_qr_workspace_bytes(10, 20) == 0
+    assert q.lib.qrctm_qr_workspace_bytes(5184, 144) > 2 * 5184 * 144 * 8
+
+
+def test_create_rejects_bad_arguments_without_gpu(q):
+    c = cfg(q, D=2, chi=16)
+    h = ctypes.c_void_p()
+    assert q.lib.qrctm_create(ctypes.byref(c), None, 0, ctypes.byref(h)) == 1
+    buf = ctypes.create_string_buffer(2048)
+    aligned = (ctypes.addressof(buf) + 255) // 256 * 256
+    assert q.lib.qrctm_create(ctypes.byref(c), ctypes.c_void_p(aligned + 8), 64,
+                              ctypes.byref(h)) == 1
+    assert q.lib.qrctm_create(ctypes.byref(c), ctypes.c_void_p(aligned), 256,
+                              ctypes.byref(h)) == 6
+    # null context calls fail cleanly
+    assert q.lib.qrctm_step(None, 1, None) == 1
+    assert q.lib.qrctm_householder_qr(4, 8, None, None, None, None, 0, None) == 1
