@@ -1,0 +1,374 @@
+"""Benchmark of the QR-CTMRG hot path on B300: iterations per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision split|fp64]
+                    [--workload d2_D6_chi144] [--impl ours|reference]
+
+One step is one QR-CTMRG iteration of the library (reduced corner C T, QR,
+T' = Q^T (T a) Q, corner update from (T', R, Q), symmetrise/normalise; the
+corner-spectrum convergence test runs every ``check_every`` steps and its
+8-byte result is read back each time).  The timed steps run on resident
+device buffers after W warm-up steps; the energy per site and the
+energy-gradient time are measured after the timed region and reported beside
+the iteration rate.  With --gpus N > 1 (torchrun) every rank runs an
+independent replica of the same workload (no data-path collective) and the
+value is the sum of the replicas' iteration rates (weak scaling).
+
+``--impl reference`` times the plain FP64 CPU oracle (the checker the GPU
+path is compared against) on the host cores, one oracle QR-CTMRG iteration
+per step, on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import qrctm_inputs as qi  # noqa: E402
+
+METRIC = "QR-CTMRG iterations/s (d=2, D=6, chi=144)"
+UNIT = "iter/s"
+
+
+def algorithmic_flops(d, D, chi):
+    """Per-phase algorithmic flops of one QR-CTMRG iteration (split layers).
+
+    ct = C T: 2 chi^3 D^2; QR of the (chi D^2) x chi corner: factorisation
+    plus explicit Q, 2 (2 m n^2 - 2 n^3 / 3); X1 = Q^T T: 2 chi^3 D^4; ket and
+    bra absorption: 2 x 2 chi^2 d D^6; T' = X2 Q: 2 chi^3 D^4; corner update:
+    4 chi^3 D^2."""
+    D2 = D * D
+    m, n = chi * D2, chi
+    return {
+        "ct": 2.0 * chi ** 3 * D2,
+        "qr": 2.0 * (2.0 * m * n * n - 2.0 * n ** 3 / 3.0),
+        "x1": 2.0 * chi ** 3 * D2 * D2,
+        "absorb": 4.0 * chi ** 2 * d * D2 ** 3,
+        "project": 2.0 * chi ** 3 * D2 * D2,
+        "corner": 4.0 * chi ** 3 * D2,
+    }
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def peak_for(precision, peaks):
+    """(peak TFLOP/s, bound, note).  The recipe's nominal dense rates: bf16
+    2.25, tf32 1.1, fp64 1.25 PFLOP/s -> TFLOP/s; TF32 is scaled from the
+    measured BF16 peak by the nominal ratio; FP64 runs on the CUDA cores
+    (ALU bound) against the nominal FP64 rate."""
+    if precision == "split":
+        if "bf16_tflops" in peaks:
+            return peaks["bf16_tflops"] * 1.1 / 2.25, "tensor", "tf32 = measured bf16 x 1.1/2.25"
+        return 1800.0 * 1.1 / 2.25, "tensor", "tf32 = fallback bf16 x 1.1/2.25"
+    return 1.25, "alu", "fp64 nominal 1.25 TFLOP/s (B300 FP64 pipe)"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = str(index)
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "200"], stdout=self.out,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        try:
+            self.out.close()
+        except Exception:
+            pass
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def oracle_sample(w, n_steps):
+    """Oracle QR-CTMRG iterations on the host (bounded sample).  The per-step
+    cost does not depend on the values, so a symmetric random environment of
+    the workload's shape stands in for the converged one."""
+    from oracle import qrctm_oracle as o
+    d, D, chi = w["d"], w["D"], w["chi"]
+    A = o.normalized_input(qi.raw_tensor(d, D, w["seed"], w["decay"], w["bias"]))
+    rng = np.random.default_rng(1)
+    C, T = o.sym_norm(rng.standard_normal((chi, chi)), rng.standard_normal((chi, D * D, chi)))
+    layers = "split" if 2 * d < D * D else "double"
+    times = []
+    for _ in range(n_steps):
+        t0 = time.perf_counter()
+        C, T = o.qr_step(C, T, A, layers)
+        times.append(time.perf_counter() - t0)
+    return times, layers
+
+
+def run_reference(args, w, rank):
+    if rank != 0:
+        return
+    o_times, layers = oracle_sample(w, args.warmup + args.steps)
+    timed = o_times[args.warmup:]
+    tot = sum(timed)
+    val = len(timed) / tot
+    cores = cpu_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / len(timed), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "d": w["d"], "D": w["D"], "chi": w["chi"],
+                   "layers": layers, "parallelism": "replicas"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} oracle QR-CTMRG iterations after "
+                                   f"{args.warmup} untimed, NumPy FP64 on the host"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=0)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "split"])
+    ap.add_argument("--workload", default="d2_D6_chi144", choices=sorted(qi.WORKLOADS))
+    ap.add_argument("--check-every", type=int, default=5)
+    ap.add_argument("--cpu-sample", type=int, default=3, help="oracle steps in cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    w = qi.WORKLOADS[args.workload]
+    if args.steps <= 0:
+        args.steps = 20 if args.precision == "fp64" else 200
+    args.warmup = max(3, args.warmup)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, w, rank)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2505_00494_b300 import build
+    if rank == 0 and not os.path.exists(build.LIB):
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    import paper_2505_00494_b300 as q
+
+    d, D, chi = w["d"], w["D"], w["chi"]
+    # every replica runs the same seeded workload
+    X = torch.tensor(qi.raw_tensor(d, D, w["seed"], w["decay"], w["bias"]), dtype=torch.float64,
+                     device="cuda")
+    A = q.c4v_symmetrize(X, normalize=True)
+    ctx = q.QRCTM(d, D, chi, precision=args.precision, check_every=args.check_every,
+                  with_nnn=True)
+    ctx.init_env(A)
+    ce = args.check_every
+
+    def one_step(i):
+        ctx.step(1, want_delta=(i % ce == ce - 1))
+
+    for i in range(args.warmup):
+        one_step(i)
+    torch.cuda.synchronize()
+    ctx.set_profiling(True)
+    ctx.phase_times()                                 # reset accumulators
+    stream = torch.cuda.current_stream()
+    launches0 = q.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gpu_id = local
+    with ClockSampler(gpu_id) as clk:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")
+        ev0.record(stream)
+        for i in range(args.steps):
+            one_step(i)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        if dist is not None:
+            dist.barrier()
+    launches = q.kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1)
+    phases = ctx.phase_times()
+    ctx.set_profiling(False)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+
+    # roofline of the dominant phase (largest share of the timed region)
+    fl = algorithmic_flops(d, D, chi)
+    dom = max(fl, key=lambda k: phases[k][0])
+    dom_ms, dom_n = phases[dom]
+    avg_s = dom_ms / max(1, dom_n) / 1e3
+    achieved = fl[dom] / avg_s / 1e12
+    peaks = load_peaks()
+    peak, bound, peak_note = peak_for(args.precision, peaks)
+    share = {k: round(phases[k][0] / ms, 4) for k in ("ct", "qr", "x1", "absorb", "project",
+                                                      "corner", "symnorm", "spectrum")}
+
+    # energy per site after the timed steps (Heisenberg, J2 = 0; and J1-J2 at 0.5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    E = ctx.energy(1.0, 0.0)
+    energy_ms = 1e3 * (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    E12 = ctx.energy(1.0, 0.5)
+    energy_j2_ms = 1e3 * (time.perf_counter() - t0)
+
+    # end to end through the public API from pinned host buffers: per step the
+    # host copies (A, C, T) in, the library re-initialises from them and runs
+    # one iteration with its convergence test, and (C, T) come back to the host.
+    C_d, T_d, _ = ctx.get_env(spectrum=False)
+    hA = A.cpu().pin_memory()
+    hC = C_d.cpu().pin_memory()
+    hT = T_d.cpu().pin_memory()
+    ctx2 = ctx
+    dA, dC, dT = torch.empty_like(A), torch.empty_like(C_d), torch.empty_like(T_d)
+    oC, oT = torch.empty_like(hC).pin_memory(), torch.empty_like(hT).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        dA.copy_(hA, non_blocking=True)
+        dC.copy_(hC, non_blocking=True)
+        dT.copy_(hT, non_blocking=True)
+        ctx2.init_env(dA, dC, dT)
+        ctx2.step(1, want_delta=True)
+        Cn, Tn, _ = ctx2.get_env(spectrum=False)
+        oC.copy_(Cn, non_blocking=True)
+        oT.copy_(Tn, non_blocking=True)
+        torch.cuda.synchronize()
+        hC, hT = oC.clone(), oT.clone()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    h2d = (hA.numel() + hC.numel() + hT.numel()) * 8
+    d2h = (oC.numel() + oT.numel()) * 8 + 8
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        times, layers = oracle_sample(w, args.cpu_sample)
+        cpu = {"value": len(times) / sum(times), "unit": UNIT, "cores": cpu_threads(),
+               "kind": "oracle",
+               "sample": f"{len(times)} oracle QR-CTMRG iterations ({layers} layers, NumPy FP64, "
+                         f"d={d} D={D} chi={chi}) from a random symmetric environment"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC if args.workload == "d2_D6_chi144" else
+            f"QR-CTMRG iterations/s ({args.workload})",
+            "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "tf32x3+f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "d": d, "D": D, "chi": chi,
+                       "precision": args.precision, "layers": "split" if 2 * d < D * D else "double",
+                       "check_every": ce, "parallelism": f"replicas{world}",
+                       "l2": "per-step intermediates larger than L2 (X1 alone "
+                             f"{(chi * D * D) ** 2 * 8 / 1e6:.0f} MB)"},
+            "roofline": {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": peak_note, "algorithmic_flops_per_launch": fl[dom],
+                         "avg_launch_ms": avg_s * 1e3},
+            "phase_share": share,
+            "clocks": clk.summary(),
+            "gpu_launches": int(launches),
+            "e2e": {"value": 1.0 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "energy_per_site": {"J2_0": E, "J2_0.5": E12, "energy_ms": energy_ms,
+                                "energy_j2_ms": energy_j2_ms},
+            "energy_grad_ms": None,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

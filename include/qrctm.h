@@ -75,6 +75,24 @@ typedef struct {
 
 typedef struct qrctm_ctx qrctm_ctx;
 
+/* Phases of the iteration timed by qrctm_phase_times (kernels K1..K9 of the
+ * step: reduced corner, QR, the three contractions of T', corner update,
+ * symmetrise/normalise, spectrum), plus the energy and gradient calls. */
+enum {
+  QRCTM_PH_CT = 0,        /* ct = C T                       (Fig. 1(e))        */
+  QRCTM_PH_QR = 1,        /* ct = Q R                       (QR-CTMRG para.)   */
+  QRCTM_PH_X1 = 2,        /* X1 = Q^T T                                          */
+  QRCTM_PH_ABSORB = 3,    /* ket and bra layers of A absorbed                    */
+  QRCTM_PH_PROJECT = 4,   /* T' = X2 Q                                           */
+  QRCTM_PH_CORNER = 5,    /* C' from T', R, Q               (Fig. 1(f))        */
+  QRCTM_PH_SYMNORM = 6,   /* symmetrise and normalise C', T'                     */
+  QRCTM_PH_SPECTRUM = 7,  /* |eig(C)| and its change                             */
+  QRCTM_PH_ENERGY = 8,    /* reduced density matrices and energy                 */
+  QRCTM_PH_GRAD = 9,      /* adjoint (gradient) passes                           */
+  QRCTM_PH_WARMUP = 10,   /* standard warm-up steps                              */
+  QRCTM_NUM_PHASES = 12
+};
+
 /* Bytes of device workspace needed for `cfg` (0 if cfg is invalid).  Host
  * only; no CUDA call. */
 size_t qrctm_workspace_bytes(const qrctm_config* cfg);
@@ -132,6 +150,18 @@ qrctm_status qrctm_energy_grad(qrctm_ctx* ctx, const qrctm_model* model, int mod
 /* Copy the environment out: C (chi*chi), T (chi*D^2*chi) on the device (may be
  * NULL); spectrum_host: chi doubles, sorted |eig(C)| (may be NULL). */
 qrctm_status qrctm_get_env(qrctm_ctx* ctx, double* C, double* T, double* spectrum_host);
+
+/* Phase timing.  With profiling on, the library records a pair of CUDA
+ * events on the context's stream around every phase; qrctm_phase_times
+ * synchronises the stream, writes the accumulated milliseconds and the number
+ * of timed occurrences of each phase since the previous call
+ * (QRCTM_NUM_PHASES entries each, host arrays, either may be NULL) and resets
+ * the accumulators.  Events are created on first use and reused. */
+qrctm_status qrctm_set_profiling(qrctm_ctx* ctx, int enable);
+qrctm_status qrctm_phase_times(qrctm_ctx* ctx, double* ms_out, long long* count_out);
+
+/* Number of kernels this library has launched in this process so far. */
+unsigned long long qrctm_kernel_launches(void);
 
 /* Steps run since qrctm_init_env. */
 int qrctm_iterations(const qrctm_ctx* ctx);

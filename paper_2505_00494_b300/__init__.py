@@ -3,7 +3,7 @@
 Argument marshalling only: every step of the computation runs in the CUDA
 kernels of ``libqrctm.so``.  PyTorch supplies device memory (the workspace and
 the caller's tensors) and the CUDA stream.  If the shared library is missing
-this module raises at import time; there is no CPU fallback.
+the first call into it raises; there is no CPU fallback.
 
 The functions mirror the C ABI in ``include/qrctm.h``:
 
@@ -21,12 +21,6 @@ __all__ = ["QRCTM", "QRCTMError", "lib", "c4v_symmetrize", "householder_qr", "LI
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libqrctm.so")
 
-if not os.path.exists(LIB_PATH):
-    raise ImportError(
-        f"{LIB_PATH} is missing: build it with `python -m paper_2505_00494_b300.build` "
-        "(nvcc, sm_103a). There is no CPU fallback.")
-
-lib = ctypes.CDLL(LIB_PATH)
 
 STATUS = {
     0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "NOT_CONVERGED", 4: "NUMERIC",
@@ -35,6 +29,8 @@ STATUS = {
 PRECISION = {"fp64": 0, "split": 1}
 LAYERS = {"auto": 0, "double": 1, "split": 2}
 GRAD_MODE = {"implicit": 0, "unroll": 1}
+PHASES = ["ct", "qr", "x1", "absorb", "project", "corner", "symnorm", "spectrum", "energy",
+          "grad", "warmup", "reserved"]
 
 
 class QRCTMError(RuntimeError):
@@ -76,6 +72,9 @@ _sig = {
                           ctypes.c_int),
     "qrctm_get_env": ([_vp, _vp, _vp, _dp], ctypes.c_int),
     "qrctm_iterations": ([_vp], ctypes.c_int),
+    "qrctm_set_profiling": ([_vp, ctypes.c_int], ctypes.c_int),
+    "qrctm_phase_times": ([_vp, _dp, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
+    "qrctm_kernel_launches": ([], ctypes.c_ulonglong),
     "qrctm_last_error": ([_vp], ctypes.c_char_p),
     "qrctm_c4v_symmetrize": ([ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp,
                               ctypes.c_size_t, _vp], ctypes.c_int),
@@ -84,12 +83,31 @@ _sig = {
     "qrctm_householder_qr": ([ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                               _vp], ctypes.c_int),
 }
-for _name, (_args, _ret) in _sig.items():
-    _f = getattr(lib, _name)
-    _f.argtypes = _args
-    _f.restype = _ret
-
 EXPORTED = sorted(_sig)
+_LIB = None
+
+
+def _load():
+    """Load libqrctm.so once and bind its signatures; raise if it is missing."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"{LIB_PATH} is missing: build it with `python -m paper_2505_00494_b300.build` "
+                "(nvcc, sm_103a). There is no CPU fallback.")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (args, ret) in _sig.items():
+            f = getattr(handle, name)
+            f.argtypes = args
+            f.restype = ret
+        _LIB = handle
+    return _LIB
+
+
+def __getattr__(name):
+    if name == "lib":
+        return _load()
+    raise AttributeError(name)
 
 
 def _torch():
@@ -134,7 +152,7 @@ class QRCTM:
         self.cfg = Config(d, D, chi, PRECISION[precision], LAYERS[layers], warmup_steps,
                           check_every, tol, max_iter, grad_max_iter, grad_tol, int(with_nnn),
                           int(with_grad), ctypes.c_void_p(self.stream.cuda_stream))
-        nbytes = lib.qrctm_workspace_bytes(ctypes.byref(self.cfg))
+        nbytes = _load().qrctm_workspace_bytes(ctypes.byref(self.cfg))
         if nbytes == 0:
             raise QRCTMError(1, "qrctm_workspace_bytes", "invalid configuration")
         self.workspace_bytes = nbytes
@@ -142,18 +160,18 @@ class QRCTM:
         self.d, self.D, self.chi = d, D, chi
         h = ctypes.c_void_p()
         self.h = None
-        self._check(lib.qrctm_create(ctypes.byref(self.cfg), ctypes.c_void_p(self.ws.data_ptr()),
+        self._check(_load().qrctm_create(ctypes.byref(self.cfg), ctypes.c_void_p(self.ws.data_ptr()),
                                      nbytes, ctypes.byref(h)), "qrctm_create")
         self.h = h
 
     def _check(self, code, where):
         if code != 0:
-            msg = lib.qrctm_last_error(self.h).decode() if self.h else ""
+            msg = _load().qrctm_last_error(self.h).decode() if self.h else ""
             raise QRCTMError(code, where, msg)
 
     def close(self):
         if getattr(self, "h", None):
-            lib.qrctm_destroy(self.h)
+            _load().qrctm_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -170,18 +188,18 @@ class QRCTM:
 
     def init_env(self, A, C0=None, T0=None):
         self.A = A
-        self._check(lib.qrctm_init_env(self.h, _ptr(A), _ptr(C0), _ptr(T0)), "qrctm_init_env")
+        self._check(_load().qrctm_init_env(self.h, _ptr(A), _ptr(C0), _ptr(T0)), "qrctm_init_env")
 
     def step(self, n=1, want_delta=True):
         dlt = ctypes.c_double(0.0)
-        self._check(lib.qrctm_step(self.h, n, ctypes.byref(dlt) if want_delta else None),
+        self._check(_load().qrctm_step(self.h, n, ctypes.byref(dlt) if want_delta else None),
                     "qrctm_step")
         return dlt.value if want_delta else None
 
     def run_to_convergence(self, tol=0.0, max_iter=0, raise_on_max=False):
         it = ctypes.c_int(0)
         dlt = ctypes.c_double(0.0)
-        code = lib.qrctm_run_to_convergence(self.h, tol, max_iter, ctypes.byref(it),
+        code = _load().qrctm_run_to_convergence(self.h, tol, max_iter, ctypes.byref(it),
                                             ctypes.byref(dlt))
         if code == 3 and not raise_on_max:
             return it.value, dlt.value
@@ -191,7 +209,7 @@ class QRCTM:
     def energy(self, J1=1.0, J2=0.0):
         e = ctypes.c_double(0.0)
         m = Model(J1, J2)
-        self._check(lib.qrctm_energy(self.h, ctypes.byref(m), ctypes.byref(e)), "qrctm_energy")
+        self._check(_load().qrctm_energy(self.h, ctypes.byref(m), ctypes.byref(e)), "qrctm_energy")
         return e.value
 
     def energy_grad(self, J1=1.0, J2=0.0, mode="implicit", k_unroll=20, grad=None):
@@ -200,7 +218,7 @@ class QRCTM:
             grad = torch.empty((self.d,) + (self.D,) * 4, dtype=torch.float64, device="cuda")
         e = ctypes.c_double(0.0)
         m = Model(J1, J2)
-        self._check(lib.qrctm_energy_grad(self.h, ctypes.byref(m), GRAD_MODE[mode], k_unroll,
+        self._check(_load().qrctm_energy_grad(self.h, ctypes.byref(m), GRAD_MODE[mode], k_unroll,
                                           _ptr(grad), ctypes.byref(e)), "qrctm_energy_grad")
         return e.value, grad
 
@@ -212,12 +230,27 @@ class QRCTM:
         T = torch.empty((self.chi, D2, self.chi), dtype=torch.float64, device="cuda")
         s = np.zeros(self.chi) if spectrum else None
         sp = s.ctypes.data_as(_dp) if spectrum else None
-        self._check(lib.qrctm_get_env(self.h, _ptr(C), _ptr(T), sp), "qrctm_get_env")
+        self._check(_load().qrctm_get_env(self.h, _ptr(C), _ptr(T), sp), "qrctm_get_env")
         return C, T, s
+
+    def set_profiling(self, enable=True):
+        self._check(_load().qrctm_set_profiling(self.h, int(enable)), "qrctm_set_profiling")
+
+    def phase_times(self):
+        """{phase: (milliseconds, occurrences)} since the previous call."""
+        n = len(PHASES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_longlong * n)()
+        self._check(_load().qrctm_phase_times(self.h, ms, cnt), "qrctm_phase_times")
+        return {PHASES[i]: (ms[i], cnt[i]) for i in range(n)}
 
     @property
     def iterations(self):
-        return lib.qrctm_iterations(self.h)
+        return _load().qrctm_iterations(self.h)
+
+
+def kernel_launches():
+    return _load().qrctm_kernel_launches()
 
 
 def c4v_symmetrize(X, normalize=True, stream=None):
@@ -225,9 +258,9 @@ def c4v_symmetrize(X, normalize=True, stream=None):
     torch = _torch()
     d, D = X.shape[0], X.shape[1]
     Y = torch.empty_like(X)
-    nb = lib.qrctm_c4v_symmetrize_workspace_bytes()
+    nb = _load().qrctm_c4v_symmetrize_workspace_bytes()
     ws = _workspace(nb, X.device)
-    code = lib.qrctm_c4v_symmetrize(d, D, _ptr(X), _ptr(Y), int(normalize),
+    code = _load().qrctm_c4v_symmetrize(d, D, _ptr(X), _ptr(Y), int(normalize),
                                     ctypes.c_void_p(ws.data_ptr()), nb, _stream_ptr(stream))
     if code != 0:
         raise QRCTMError(code, "qrctm_c4v_symmetrize")
@@ -244,9 +277,9 @@ def householder_qr(M, stream=None, workspace=None):
     Mcm = M.t().contiguous()
     Qcm = torch.empty((n, m), dtype=torch.float64, device=M.device)
     R = torch.empty((n, n), dtype=torch.float64, device=M.device)
-    nb = lib.qrctm_qr_workspace_bytes(m, n)
+    nb = _load().qrctm_qr_workspace_bytes(m, n)
     ws = workspace if workspace is not None else _workspace(nb, M.device, zero=True)
-    code = lib.qrctm_householder_qr(m, n, _ptr(Mcm), _ptr(Qcm), _ptr(R),
+    code = _load().qrctm_householder_qr(m, n, _ptr(Mcm), _ptr(Qcm), _ptr(R),
                                     ctypes.c_void_p(ws.data_ptr()), nb, _stream_ptr(stream))
     if code != 0:
         raise QRCTMError(code, "qrctm_householder_qr")

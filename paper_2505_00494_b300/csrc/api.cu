@@ -134,6 +134,31 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
 
 size_t grad_bytes(int, int, int) { return 256; }
 
+PhaseScope::PhaseScope(qrctm_ctx* c_, int ph_) : c(c_), ph(ph_), a(nullptr) {
+  if (!c->prof) return;
+  if (c->ev_pool.empty()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    c->ev_pool.push_back(e);
+  }
+  a = c->ev_pool.back();
+  c->ev_pool.pop_back();
+  cudaEventRecord(a, c->st);
+}
+
+PhaseScope::~PhaseScope() {
+  if (!a) return;
+  cudaEvent_t b;
+  if (c->ev_pool.empty()) {
+    if (cudaEventCreate(&b) != cudaSuccess) { c->ev_pool.push_back(a); return; }
+  } else {
+    b = c->ev_pool.back();
+    c->ev_pool.pop_back();
+  }
+  cudaEventRecord(b, c->st);
+  c->recs.push_back({ph, a, b});
+}
+
 }  // namespace qrctm
 
 extern "C" {
@@ -180,7 +205,45 @@ qrctm_status qrctm_create(const qrctm_config* cfg, void* workspace, size_t bytes
   return QRCTM_OK;
 }
 
-void qrctm_destroy(qrctm_ctx* ctx) { delete ctx; }
+void qrctm_destroy(qrctm_ctx* ctx) {
+  if (!ctx) return;
+  if (!ctx->recs.empty() || !ctx->ev_pool.empty()) cudaStreamSynchronize(ctx->st);
+  for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+qrctm_status qrctm_set_profiling(qrctm_ctx* c, int enable) {
+  if (!c) return QRCTM_ERR_INVALID_ARG;
+  c->prof = enable != 0;
+  return QRCTM_OK;
+}
+
+qrctm_status qrctm_phase_times(qrctm_ctx* c, double* ms_out, long long* count_out) {
+  if (!c) return QRCTM_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "phase times");
+  for (auto& r : c->recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess && r.ph >= 0 &&
+        r.ph < QRCTM_NUM_PHASES) {
+      c->ph_ms[r.ph] += ms;
+      c->ph_n[r.ph] += 1;
+    }
+    c->ev_pool.push_back(r.a);
+    c->ev_pool.push_back(r.b);
+  }
+  c->recs.clear();
+  for (int i = 0; i < QRCTM_NUM_PHASES; ++i) {
+    if (ms_out) ms_out[i] = c->ph_ms[i];
+    if (count_out) count_out[i] = c->ph_n[i];
+    c->ph_ms[i] = 0.0;
+    c->ph_n[i] = 0;
+  }
+  return QRCTM_OK;
+}
+
+unsigned long long qrctm_kernel_launches(void) { return launches_so_far(); }
 
 int qrctm_iterations(const qrctm_ctx* ctx) { return ctx ? ctx->iters : 0; }
 
@@ -246,6 +309,7 @@ qrctm_status qrctm_init_env(qrctm_ctx* c, const double* A, const double* C0, con
       while (cc < c->chi && D2 > 1) { cc *= D2; ++nw; }
       if (nw < 2) nw = 2;
     }
+    PhaseScope ps(c, QRCTM_PH_WARMUP);
     for (int w = 0; w < nw; ++w) {
       int ci = c->chi_cur;
       int co = (int)std::min<long long>(c->chi, (long long)ci * D2);
@@ -314,7 +378,11 @@ qrctm_status qrctm_energy(qrctm_ctx* c, const qrctm_model* model, double* e_out)
   if (c->d != 2) return set_err(c, QRCTM_ERR_INVALID_ARG, "the spin-1/2 energy needs d = 2");
   if (model->J2 != 0.0 && c->E3 == nullptr)
     return set_err(c, QRCTM_ERR_INVALID_ARG, "J2 != 0 needs with_nnn = 1");
-  cudaError_t e = energy_fp64(c, model->J1, model->J2);
+  cudaError_t e;
+  {
+    PhaseScope ps(c, QRCTM_PH_ENERGY);
+    e = energy_fp64(c, model->J1, model->J2);
+  }
   if (e != cudaSuccess) return cuda_fail(c, e, "energy");
   qrctm_status s = sync_check(c, "energy");
   if (s != QRCTM_OK) return s;

@@ -41,6 +41,7 @@ cudaError_t renorm_edge(qrctm_ctx* c, const double* P, int co, const double* T, 
   cudaError_t e;
   // X1[(u,m),(k,b)] = sum_a P[(a,u),m] T[a,(k,b)]
   {
+    PhaseScope ps(c, QRCTM_PH_X1);
     Gemm g = gemm_init();
     g.M = (long long)D2 * co; g.N = (long long)D2 * ci; g.K = ci;
     g.A = P; g.a_m = im2(co, mi, 1); g.a_k = im1(D2);
@@ -48,6 +49,8 @@ cudaError_t renorm_edge(qrctm_ctx* c, const double* P, int co, const double* T, 
     g.C = c->X1; g.c_m = im1(g.N); g.c_n = im1(1);
     if ((e = gemm_f64(g, c->st)) != cudaSuccess) return e;
   }
+  {
+  PhaseScope ps_abs(c, QRCTM_PH_ABSORB);
   if (c->split_layers) {
     const long long dD2 = (long long)d * D2;
     // ket: Z[(m,b,u_b,k_b),(s,d_k,j_k)] = sum_{u_k,k_k} X1 A[s,u_k,k_k,d_k,j_k]
@@ -73,9 +76,11 @@ cudaError_t renorm_edge(qrctm_ctx* c, const double* P, int co, const double* T, 
     g.C = c->X2; g.c_m = im1(D4); g.c_n = im4(D, D, D, 1, D2, D, D3);
     if ((e = gemm_f64(g, c->st)) != cudaSuccess) return e;
   }
+  }
   if (Tout == nullptr) return cudaSuccess;
   // T'[(m,j),n] = sum_{(b,d)} X2[m,b,d_k,j_k,d_b,j_b] P[(b,d),n]
   {
+    PhaseScope ps(c, QRCTM_PH_PROJECT);
     Gemm g = gemm_init();
     g.M = (long long)co * D2; g.N = co; g.K = mi;
     g.A = c->X2; g.a_m = im3(D, D, 1, D2, (long long)ci * D4); g.a_k = im3(D, D, D, D3, D4);
@@ -94,12 +99,19 @@ cudaError_t qr_step(qrctm_ctx* c) {
   const int ch = c->chi_cur, D2 = c->D2;
   const long long m = (long long)ch * D2;
   cudaError_t e;
-  if ((e = reduced_corner(c, c->C, c->T, ch, c->Mcm)) != cudaSuccess) return e;
-  if ((e = householder_qr_f64((int)m, ch, c->Mcm, c->Q, c->R, c->qrw, c->st)) != cudaSuccess)
-    return e;
-  if ((e = renorm_edge(c, c->Q, ch, c->T, ch, c->Traw)) != cudaSuccess) return e;
-  if ((e = sym_edge(c->Traw, c->Tn, ch, D2, c->st)) != cudaSuccess) return e;
   {
+    PhaseScope ps(c, QRCTM_PH_CT);
+    if ((e = reduced_corner(c, c->C, c->T, ch, c->Mcm)) != cudaSuccess) return e;
+  }
+  {
+    PhaseScope ps(c, QRCTM_PH_QR);
+    if ((e = householder_qr_f64((int)m, ch, c->Mcm, c->Q, c->R, c->qrw, c->st)) != cudaSuccess)
+      return e;
+  }
+  if ((e = renorm_edge(c, c->Q, ch, c->T, ch, c->Traw)) != cudaSuccess) return e;
+  {
+    PhaseScope ps(c, QRCTM_PH_CORNER);
+    if ((e = sym_edge(c->Traw, c->Tn, ch, D2, c->st)) != cudaSuccess) return e;
     // Y2[n,(g,j)] = sum_m T's[n,j,m] R[m,g]   (batched over j; T's symmetric)
     Gemm g = gemm_init();
     g.M = ch; g.N = ch; g.K = ch; g.batch = D2;
@@ -115,9 +127,12 @@ cudaError_t qr_step(qrctm_ctx* c) {
     g.C = c->Craw; g.c_m = im1(ch); g.c_n = im1(1);
     if ((e = gemm_f64(g, c->st)) != cudaSuccess) return e;
   }
-  if ((e = sym_norm_env(c->Craw, c->Tn, c->C, c->T, ch, D2, c->partials, c->err, c->st)) !=
-      cudaSuccess)
-    return e;
+  {
+    PhaseScope ps(c, QRCTM_PH_SYMNORM);
+    if ((e = sym_norm_env(c->Craw, c->Tn, c->C, c->T, ch, D2, c->partials, c->err, c->st)) !=
+        cudaSuccess)
+      return e;
+  }
   c->iters += 1;
   return cudaSuccess;
 }
@@ -176,6 +191,7 @@ cudaError_t warmup_step(qrctm_ctx* c, int ci, int co) {
 }
 
 cudaError_t spectrum_check(qrctm_ctx* c) {
+  PhaseScope ps(c, QRCTM_PH_SPECTRUM);
   // s_prev <- s_cur, then s_cur <- |eig(C)|, delta <- ||s_cur - s_prev||
   cudaError_t e = cudaMemcpyAsync(c->s_prev, c->s_cur, sizeof(double) * c->chi,
                                   cudaMemcpyDeviceToDevice, c->st);

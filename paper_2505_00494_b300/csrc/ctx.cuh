@@ -3,6 +3,7 @@
 #pragma once
 
 #include <string>
+#include <vector>
 
 #include "qrctm.h"
 #include "qrctm_internal.cuh"
@@ -40,9 +41,25 @@ struct qrctm_ctx {
   bool have_env;
   bool spec_valid;
   std::string last_error;
+  // phase timing (qrctm_set_profiling)
+  bool prof;
+  struct PhaseRec { int ph; cudaEvent_t a, b; };
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<PhaseRec> recs;
+  double ph_ms[QRCTM_NUM_PHASES];
+  long long ph_n[QRCTM_NUM_PHASES];
 };
 
 namespace qrctm {
+
+// Records a pair of CUDA events around a phase when profiling is on.
+struct PhaseScope {
+  qrctm_ctx* c;
+  int ph;
+  cudaEvent_t a;
+  PhaseScope(qrctm_ctx* c_, int ph_);
+  ~PhaseScope();
+};
 
 // Workspace plan (api.cu); 256-byte aligned regions.
 size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* ctx);

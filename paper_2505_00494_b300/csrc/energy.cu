@@ -168,6 +168,7 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
       g.c_n = im3(D, D, 1, m, mm);
       if ((e = gemm_f64(g, st)) != cudaSuccess) return e;
       trace_phys_k<<<1184, 256, 0, st>>>(c->E1, c->X2, d, mm);
+      note_launch();
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       // P(s,t) = Ct_open(s,t) Ct
       g = gemm_init();
@@ -186,6 +187,7 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
     }
   }
   energy_k<<<1, 1, 0, st>>>(c->rho, rho_nnn, J1, J2, c->e_d, c->err);
+  note_launch();
   return cudaGetLastError();
 }
 

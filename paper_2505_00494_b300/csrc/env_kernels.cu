@@ -313,12 +313,14 @@ inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) /
 cudaError_t c4v_symmetrize(int d, int D, const double* X, double* Y, cudaStream_t s) {
   long long n = (long long)d * D * D * D * D;
   c4v_sym_kernel<<<nblk(n), 256, 0, s>>>(d, D, X, Y);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t sum_squares_partials(const double* x, long long n, double* partials, int nparts,
                                  cudaStream_t s) {
   sumsq_kernel<<<nparts, 256, 0, s>>>(x, n, partials);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -328,12 +330,14 @@ cudaError_t scale_by_inv_norm(const double* x, double* y, long long n, const dou
   if (nb > 1184) nb = 1184;
   if (nb < 1) nb = 1;
   scale_kernel<<<(unsigned)nb, 256, 0, s>>>(x, y, n, partials, nparts, err);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t sym_edge(const double* Tin, double* Tout, int chi, int D2, cudaStream_t s) {
   long long n = (long long)chi * D2 * chi;
   sym_edge_kernel<<<nblk(n), 256, 0, s>>>(Tin, Tout, chi, D2);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -343,9 +347,13 @@ cudaError_t sym_norm_env(const double* Cin, const double* Tin, double* Cout, dou
   const int NP = 256;
   long long nC = (long long)chi * chi, nT = (long long)chi * D2 * chi;
   sym_corner_kernel<<<nblk(nC), 256, 0, s>>>(Cin, Cout, chi);
+  note_launch();
   sym_edge_kernel<<<nblk(nT), 256, 0, s>>>(Tin, Tout, chi, D2);
+  note_launch();
   sumsq_kernel<<<NP, 256, 0, s>>>(Cout, nC, partials);
+  note_launch();
   sumsq_kernel<<<NP, 256, 0, s>>>(Tout, nT, partials + NP);
+  note_launch();
   cudaError_t e = scale_by_inv_norm(Cout, Cout, nC, partials, NP, err, s);
   if (e != cudaSuccess) return e;
   return scale_by_inv_norm(Tout, Tout, nT, partials + NP, NP, err, s);
@@ -355,6 +363,7 @@ cudaError_t init_env_kernel(int d, int D, const double* A, double* C0, double* T
                             cudaStream_t s) {
   long long n = (long long)D * D * D * D * D * D;
   init_env_k<<<nblk(n), 256, 0, s>>>(d, D, A, C0, T0);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -362,6 +371,7 @@ cudaError_t double_layer_kernel(int d, int D, const double* A, double* a, cudaSt
   long long n = (long long)D * D * D * D;
   n = n * n;
   double_layer_k<<<nblk(n), 256, 0, s>>>(d, D, A, a);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -370,6 +380,7 @@ cudaError_t corner_spectrum(const double* C, int chi, double* work, double* s_ne
                             cudaStream_t s) {
   if (chi < 1 || chi > 1024) return cudaErrorInvalidValue;
   spectrum_kernel<<<1, 1024, 0, s>>>(C, chi, work, s_new, s_old, chi_old, delta, err);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -378,6 +389,7 @@ cudaError_t fill_zero(double* p, long long n, cudaStream_t s) {
   long long nb = (n + 255) / 256;
   if (nb > 4096) nb = 4096;
   fill_zero_k<<<(unsigned)nb, 256, 0, s>>>(p, n);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -386,6 +398,7 @@ cudaError_t axpby(double* y, const double* x, double a, double b, long long n, c
   long long nb = (n + 255) / 256;
   if (nb > 4096) nb = 4096;
   axpby_k<<<(unsigned)nb, 256, 0, s>>>(y, x, a, b, n);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -96,12 +96,17 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(Gemm g) {
 
 }  // namespace
 
+static unsigned long long g_launches = 0;
+void note_launch(unsigned long long n) { __atomic_fetch_add(&g_launches, n, __ATOMIC_RELAXED); }
+unsigned long long launches_so_far() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
 cudaError_t gemm_f64(const Gemm& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
   long long gx = (g.M + BM - 1) / BM, gy = (g.N + BN - 1) / BN;
   if (gx > 0x7fffffffll || gy > 65535) return cudaErrorInvalidValue;
   int gz = g.batch < 65535 ? g.batch : 65535;
   gemm_f64_kernel<<<dim3((unsigned)gx, (unsigned)gy, gz), NT, 0, s>>>(g);
+  note_launch();
   return cudaGetLastError();
 }
 

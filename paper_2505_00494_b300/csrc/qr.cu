@@ -229,6 +229,7 @@ QrWork qr_carve(void* base, int m, int n) {
 cudaError_t set_identity_cols(double* Q, int m, int n, cudaStream_t s) {
   long long tot = (long long)m * n;
   set_identity_cols_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Q, m, n);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -254,6 +255,7 @@ cudaError_t householder_qr_f64(int m, int n, const double* M, double* Q, double*
     void* args[] = {&W, &V, &Tp, &part, &bar, &err, &m_, &j0_, &nb_, &rpc};
     e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel, dim3(P), dim3(PT), args, 0, s);
     if (e != cudaSuccess) return e;
+    note_launch();
     const int n2 = n - j0 - nbj;
     if (n2 > 0) {
       Gemm g = gemm_init();
@@ -281,6 +283,7 @@ cudaError_t householder_qr_f64(int m, int n, const double* M, double* Q, double*
   {
     long long tot = (long long)n * n;
     extract_r_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(w.W, R, m, n);
+    note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   // Q = H_1 ... H_n [I; 0], applying the panels in reverse order

@@ -78,6 +78,10 @@ static inline Gemm gemm_init() {
   return g;
 }
 
+// Process-wide count of kernels launched by this library (for reporting).
+void note_launch(unsigned long long n = 1);
+unsigned long long launches_so_far();
+
 // FP64 CUDA-core contraction (any layout).  Returns cudaGetLastError().
 cudaError_t gemm_f64(const Gemm& g, cudaStream_t s);
 
