@@ -19,7 +19,7 @@ namespace qrctm {
 cudaError_t reduced_corner(qrctm_ctx* c, const double* C, const double* T, int ci, double* Mcm) {
   const int D2 = c->D2;
   const long long mi = (long long)ci * D2;
-  Gemm g = gemm_init();
+  Gemm g = gemm_ctx(c);
   g.M = ci; g.N = ci; g.K = ci; g.batch = D2;
   g.A = C; g.a_m = im1(ci); g.a_k = im1(1); g.a_b = im0();
   g.B = T; g.b_k = im1((long long)D2 * ci); g.b_n = im1(1); g.b_b = im1(ci);
@@ -42,7 +42,7 @@ cudaError_t renorm_edge(qrctm_ctx* c, const double* P, int co, const double* T, 
   // X1[(u,m),(k,b)] = sum_a P[(a,u),m] T[a,(k,b)]
   {
     PhaseScope ps(c, QRCTM_PH_X1);
-    Gemm g = gemm_init();
+    Gemm g = gemm_ctx(c);
     g.M = (long long)D2 * co; g.N = (long long)D2 * ci; g.K = ci;
     g.A = P; g.a_m = im2(co, mi, 1); g.a_k = im1(D2);
     g.B = T; g.b_k = im1((long long)D2 * ci); g.b_n = im1(1);
@@ -54,14 +54,14 @@ cudaError_t renorm_edge(qrctm_ctx* c, const double* P, int co, const double* T, 
   if (c->split_layers) {
     const long long dD2 = (long long)d * D2;
     // ket: Z[(m,b,u_b,k_b),(s,d_k,j_k)] = sum_{u_k,k_k} X1 A[s,u_k,k_k,d_k,j_k]
-    Gemm g = gemm_init();
+    Gemm g = gemm_ctx(c);
     g.M = (long long)co * ci * D2; g.N = dD2; g.K = D2;
     g.A = c->X1; g.a_m = im4(D, D, ci, Sk, Su, 1, Smu); g.a_k = im2(D, D * Sk, D * Su);
     g.B = c->A; g.b_k = im2(D, D2, D3); g.b_n = im3(D, D, 1, D, D4);
     g.C = c->Z; g.c_m = im1(dD2); g.c_n = im1(1);
     if ((e = gemm_f64(g, c->st)) != cudaSuccess) return e;
     // bra: X2[(m,b,d_k,j_k),(d_b,j_b)] = sum_{s,u_b,k_b} Z A[s,u_b,k_b,d_b,j_b]
-    g = gemm_init();
+    g = gemm_ctx(c);
     g.M = (long long)co * ci * D2; g.N = D2; g.K = dD2;
     g.A = c->Z; g.a_m = im3(D, D, 1, D, D2 * dD2); g.a_k = im3(D, D, dD2, D * dD2, D2);
     g.B = c->A; g.b_k = im3(D, D, D2, D3, D4); g.b_n = im1(1);
@@ -69,7 +69,7 @@ cudaError_t renorm_edge(qrctm_ctx* c, const double* P, int co, const double* T, 
     if ((e = gemm_f64(g, c->st)) != cudaSuccess) return e;
   } else {
     // X2[(m,b),(d,j)] = sum_{(u,k)} X1 a[(u,k),(d,j)], stored [m,b,d_k,j_k,d_b,j_b]
-    Gemm g = gemm_init();
+    Gemm g = gemm_ctx(c);
     g.M = (long long)co * ci; g.N = D4; g.K = D4;
     g.A = c->X1; g.a_m = im2(ci, 1, Smu); g.a_k = im2(D2, Sk, Su);
     g.B = c->a; g.b_k = im1(D4); g.b_n = im1(1);
@@ -81,7 +81,7 @@ cudaError_t renorm_edge(qrctm_ctx* c, const double* P, int co, const double* T, 
   // T'[(m,j),n] = sum_{(b,d)} X2[m,b,d_k,j_k,d_b,j_b] P[(b,d),n]
   {
     PhaseScope ps(c, QRCTM_PH_PROJECT);
-    Gemm g = gemm_init();
+    Gemm g = gemm_ctx(c);
     g.M = (long long)co * D2; g.N = co; g.K = mi;
     g.A = c->X2; g.a_m = im3(D, D, 1, D2, (long long)ci * D4); g.a_k = im3(D, D, D, D3, D4);
     g.B = P; g.b_k = im1(1); g.b_n = im1(mi);
@@ -113,14 +113,14 @@ cudaError_t qr_step(qrctm_ctx* c) {
     PhaseScope ps(c, QRCTM_PH_CORNER);
     if ((e = sym_edge(c->Traw, c->Tn, ch, D2, c->st)) != cudaSuccess) return e;
     // Y2[n,(g,j)] = sum_m T's[n,j,m] R[m,g]   (batched over j; T's symmetric)
-    Gemm g = gemm_init();
+    Gemm g = gemm_ctx(c);
     g.M = ch; g.N = ch; g.K = ch; g.batch = D2;
     g.A = c->Tn; g.a_m = im1((long long)D2 * ch); g.a_k = im1(1); g.a_b = im1(ch);
     g.B = c->R; g.b_k = im1(ch); g.b_n = im1(1); g.b_b = im0();
     g.C = c->Y2; g.c_m = im1((long long)ch * D2); g.c_n = im1(D2); g.c_b = im1(1);
     if ((e = gemm_f64(g, c->st)) != cudaSuccess) return e;
     // C'[n,p] = sum_{(g,j)} Y2[n,(g,j)] Q[(g,j),p]
-    g = gemm_init();
+    g = gemm_ctx(c);
     g.M = ch; g.N = ch; g.K = m;
     g.A = c->Y2; g.a_m = im1(m); g.a_k = im1(1);
     g.B = c->Q; g.b_k = im1(1); g.b_n = im1(m);
@@ -154,7 +154,7 @@ cudaError_t warmup_step(qrctm_ctx* c, int ci, int co) {
   const IdxMap ct_col = im3(D, D, 1, D2, (long long)ci * D4);
   // (every use of Ct comes before the final renorm_edge overwrites X2)
   auto apply_ct = [&](const double* X, double* Y, int ncol) -> cudaError_t {
-    Gemm g = gemm_init();
+    Gemm g = gemm_ctx(c);
     g.M = mi; g.N = ncol; g.K = mi;
     g.A = c->X2; g.a_m = ct_row; g.a_k = ct_col;
     g.B = X; g.b_k = im1(1); g.b_n = im1(mi);
@@ -175,7 +175,7 @@ cudaError_t warmup_step(qrctm_ctx* c, int ci, int co) {
   // C' = U^T (Ct U)
   if ((e = apply_ct(c->Q, c->Yw, co)) != cudaSuccess) return e;
   {
-    Gemm g = gemm_init();
+    Gemm g = gemm_ctx(c);
     g.M = co; g.N = co; g.K = mi;
     g.A = c->Q; g.a_m = im1(mi); g.a_k = im1(1);
     g.B = c->Yw; g.b_k = im1(1); g.b_n = im1(mi);

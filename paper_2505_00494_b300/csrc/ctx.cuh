@@ -61,6 +61,14 @@ struct PhaseScope {
   ~PhaseScope();
 };
 
+// A contraction descriptor that may use the context's split-K scratch.
+inline Gemm gemm_ctx(qrctm_ctx* c) {
+  Gemm g = gemm_init();
+  g.part = c->qrw.splitk;
+  g.part_elems = kSplitKElems;
+  return g;
+}
+
 // Workspace plan (api.cu); 256-byte aligned regions.
 size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* ctx);
 

@@ -79,7 +79,7 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
   if ((e = reduced_corner(c, c->C, c->T, ch, c->Mcm)) != cudaSuccess) return e;
   // L1[(x1,q),z1] = sum_y ct[(x1,q),y] C[y,z1]
   {
-    Gemm g = gemm_init();
+    Gemm g = gemm_ctx(c);
     g.M = m; g.N = ch; g.K = ch;
     g.A = c->Mcm; g.a_m = im1(1); g.a_k = im1(m);
     g.B = c->C; g.b_k = im1(ch); g.b_n = im1(1);
@@ -88,7 +88,7 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
   }
   // W[(q,z1),(p,X)] = sum_x1 L1[x1,q,z1] T[x1,p,X]
   {
-    Gemm g = gemm_init();
+    Gemm g = gemm_ctx(c);
     g.M = m; g.N = m; g.K = ch;
     g.A = c->Y2; g.a_m = im1(1); g.a_k = im1(m);
     g.B = c->T; g.b_k = im1(m); g.b_n = im1(1);
@@ -97,7 +97,7 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
   }
   // ket: Z1[(z1,X,q_b,p_b),(s,d_k,h_k)] = sum_{p_k,q_k} W A[s,p_k,q_k,d_k,h_k]
   {
-    Gemm g = gemm_init();
+    Gemm g = gemm_ctx(c);
     g.M = (long long)ch * ch * D2; g.N = dD2; g.K = D2;
     g.A = c->X1; g.a_m = im4(D, D, ch, ch, Sq, 1, m); g.a_k = im2(D, D * Sq, (long long)D * ch);
     g.B = c->A; g.b_k = im2(D, D2, D3); g.b_n = im3(D, D, 1, D, D4);
@@ -107,7 +107,7 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
   // bra (physical index t open): Z2 stored [X][s][t][h_k][h_b][z1][d_k][d_b]
   {
     const long long D2c = (long long)D2 * ch, D4c = D4 * ch;
-    Gemm g = gemm_init();
+    Gemm g = gemm_ctx(c);
     g.M = (long long)ch * ch * dD2; g.N = dD2; g.K = D2;
     g.A = c->Z; g.a_m = im4(D, D, d, 1, D, D2, D2 * dD2); g.a_k = im2(D, dD2, D * dD2);
     g.B = c->A; g.b_k = im2(D, D3, D2); g.b_n = im3(D, D, 1, D, D4);
@@ -119,7 +119,7 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
   }
   // HL[(X,s,t,h),Z] = sum_{(z1,d)} Z2[X,s,t,h,(z1,d)] T[(z1,d),Z]
   {
-    Gemm g = gemm_init();
+    Gemm g = gemm_ctx(c);
     g.M = (long long)ch * d * d * D2; g.N = ch; g.K = m;
     g.A = c->E1; g.a_m = im1(m); g.a_k = im1(1);
     g.B = c->T; g.b_k = im1(ch); g.b_n = im1(1);
@@ -129,7 +129,7 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
   // rho_nn[(s1,t1),(s2,t2)] = sum_{X,h,Z} HL[X,s1,t1,h,Z] HL[X,s2,t2,h,Z]
   {
     const long long st_str = (long long)D2 * ch;
-    Gemm g = gemm_init();
+    Gemm g = gemm_ctx(c);
     g.M = d * d; g.N = d * d; g.K = (long long)ch * D2 * ch;
     g.A = c->E2; g.a_m = im1(st_str); g.a_k = im3(ch, D2, 1, ch, (long long)d * d * D2 * ch);
     g.B = c->E2; g.b_k = im3(ch, D2, 1, ch, (long long)d * d * D2 * ch); g.b_n = im1(st_str);
@@ -143,13 +143,13 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
     // X[(i,r),(k,b)] = sum_g ct[(g,i),r] T[g,(k,b)] and the ket layer -> c->Z
     const long long Su = (long long)ch * D2 * ch, Smu = (long long)D2 * ch, Sk = ch;
     {
-      Gemm g = gemm_init();
+      Gemm g = gemm_ctx(c);
       g.M = m; g.N = m; g.K = ch;
       g.A = c->Mcm; g.a_m = im2(ch, m, 1); g.a_k = im1(D2);
       g.B = c->T; g.b_k = im1(m); g.b_n = im1(1);
       g.C = c->X1; g.c_m = im1(m); g.c_n = im1(1);
       if ((e = gemm_f64(g, st)) != cudaSuccess) return e;
-      g = gemm_init();
+      g = gemm_ctx(c);
       g.M = (long long)ch * ch * D2; g.N = dD2; g.K = D2;
       g.A = c->X1; g.a_m = im4(D, D, ch, Sk, Su, 1, Smu); g.a_k = im2(D, D * Sk, D * Su);
       g.B = c->A; g.b_k = im2(D, D2, D3); g.b_n = im3(D, D, 1, D, D4);
@@ -159,7 +159,7 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
     // bra with t open: Ct_open stored [s][t][b][l_k][l_b][r][j_k][j_b]
     {
       const long long mm = m * m;
-      Gemm g = gemm_init();
+      Gemm g = gemm_ctx(c);
       g.M = (long long)ch * ch * dD2; g.N = dD2; g.K = D2;
       g.A = c->Z; g.a_m = im4(D, D, d, 1, D, D2, D2 * dD2); g.a_k = im2(D, dD2, D * dD2);
       g.B = c->A; g.b_k = im2(D, D2, D3); g.b_n = im3(D, D, 1, D, D4);
@@ -171,14 +171,14 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
       note_launch();
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       // P(s,t) = Ct_open(s,t) Ct
-      g = gemm_init();
+      g = gemm_ctx(c);
       g.M = m; g.N = m; g.K = m; g.batch = d * d;
       g.A = c->E1; g.a_m = im1(m); g.a_k = im1(1); g.a_b = im1(mm);
       g.B = c->X2; g.b_k = im1(m); g.b_n = im1(1); g.b_b = im0();
       g.C = c->E3; g.c_m = im1(m); g.c_n = im1(1); g.c_b = im1(mm);
       if ((e = gemm_f64(g, st)) != cudaSuccess) return e;
       // rho_nnn[(s1,t1),(s4,t4)] = sum_{a,c} P(s1,t1)[a,c] P(s4,t4)[c,a]
-      g = gemm_init();
+      g = gemm_ctx(c);
       g.M = d * d; g.N = d * d; g.K = mm;
       g.A = c->E3; g.a_m = im1(mm); g.a_k = im1(1);
       g.B = c->E3; g.b_k = im2((int)m, m, 1); g.b_n = im1(mm);

@@ -7,13 +7,17 @@
 // tile with a 4x4 register block per thread is enough to keep it busy.
 #include "qrctm_internal.cuh"
 
+#include <algorithm>
+
 namespace qrctm {
 
 namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 
-__global__ void __launch_bounds__(NT) gemm_f64_kernel(Gemm g) {
+// splits > 1 (batch == 1 only): CTA z handles K range [z*kc, (z+1)*kc) and
+// writes its raw sums to g.part[z][M][N].
+__global__ void __launch_bounds__(NT) gemm_f64_kernel(Gemm g, int splits, long long kc) {
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
   __shared__ long long aRow[BM], bCol[BN], aK[BK], bK[BK];
@@ -22,7 +26,10 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(Gemm g) {
   const long long m0 = (long long)blockIdx.x * BM;
   const long long n0 = (long long)blockIdx.y * BN;
 
-  for (long long b = blockIdx.z; b < g.batch; b += gridDim.z) {
+  const long long kbeg = (splits > 1) ? (long long)blockIdx.z * kc : 0;
+  const long long kend = (splits > 1) ? min(g.K, kbeg + kc) : g.K;
+  for (long long b = (splits > 1) ? 0 : blockIdx.z; b < g.batch;
+       b += (splits > 1) ? g.batch : gridDim.z) {
     const long long aB = map_off(g.a_b, b), bB = map_off(g.b_b, b), cB = map_off(g.c_b, b);
     __syncthreads();
     if (tid < BM) {
@@ -38,13 +45,13 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(Gemm g) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
 
-    for (long long k0 = 0; k0 < g.K; k0 += BK) {
+    for (long long k0 = kbeg; k0 < kend; k0 += BK) {
       if (tid < BK) {
         long long k = k0 + tid;
-        aK[tid] = (k < g.K) ? map_off(g.a_k, k) : -1;
+        aK[tid] = (k < kend) ? map_off(g.a_k, k) : -1;
       } else if (tid < 2 * BK) {
         long long k = k0 + tid - BK;
-        bK[tid - BK] = (k < g.K) ? map_off(g.b_k, k) : -1;
+        bK[tid - BK] = (k < kend) ? map_off(g.b_k, k) : -1;
       }
       __syncthreads();
 #pragma unroll
@@ -76,6 +83,20 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(Gemm g) {
       }
       __syncthreads();
     }
+    if (splits > 1) {
+      double* P = g.part + (long long)blockIdx.z * g.M * g.N;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        long long m = m0 + ty + 16 * i;
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          long long n = n0 + tx + 16 * j;
+          if (n < g.N) P[m * g.N + n] = acc[i][j];
+        }
+      }
+      continue;
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       long long m = m0 + ty + 16 * i;
@@ -94,6 +115,21 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(Gemm g) {
   }
 }
 
+// C(m,n) = alpha * sum_z part[z][m][n] + beta * C(m,n), summed in z order.
+__global__ void splitk_reduce_kernel(Gemm g, int splits) {
+  const long long MN = g.M * g.N;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < MN;
+       e += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int z = 0; z < splits; ++z) s += g.part[(long long)z * MN + e];
+    const long long m = e / g.N, n = e % g.N;
+    double* p = g.C + map_off(g.c_m, m) + map_off(g.c_n, n);
+    double v = g.alpha * s;
+    if (g.beta != 0.0) v += g.beta * *p;
+    *p = v;
+  }
+}
+
 }  // namespace
 
 static unsigned long long g_launches = 0;
@@ -104,8 +140,36 @@ cudaError_t gemm_f64(const Gemm& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
   long long gx = (g.M + BM - 1) / BM, gy = (g.N + BN - 1) / BN;
   if (gx > 0x7fffffffll || gy > 65535) return cudaErrorInvalidValue;
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 148;
+  }
+  const long long tiles = gx * gy;
+  int splits = 1;
+  if (g.part != nullptr && g.batch == 1 && tiles < 2 * nsm && g.K >= 4 * BK) {
+    long long want = (4ll * nsm + tiles - 1) / tiles;          // ~4 CTAs per SM
+    long long by_k = g.K / (4 * BK);                           // >= 4 k-tiles per split
+    long long by_mem = g.part_elems / (g.M * g.N);
+    long long sp = std::min(std::min(want, by_k), std::min(by_mem, 65535ll));
+    if (sp > 1) splits = (int)sp;
+  }
+  if (splits > 1) {
+    long long kc = (g.K + splits - 1) / splits;
+    kc = (kc + BK - 1) / BK * BK;
+    splits = (int)((g.K + kc - 1) / kc);
+    gemm_f64_kernel<<<dim3((unsigned)gx, (unsigned)gy, splits), NT, 0, s>>>(g, splits, kc);
+    note_launch();
+    long long MN = g.M * g.N;
+    long long nb = std::min<long long>((MN + 255) / 256, 4096);
+    splitk_reduce_kernel<<<(unsigned)nb, 256, 0, s>>>(g, splits);
+    note_launch();
+    return cudaGetLastError();
+  }
   int gz = g.batch < 65535 ? g.batch : 65535;
-  gemm_f64_kernel<<<dim3((unsigned)gx, (unsigned)gy, gz), NT, 0, s>>>(g);
+  gemm_f64_kernel<<<dim3((unsigned)gx, (unsigned)gy, gz), NT, 0, s>>>(g, 1, 0);
   note_launch();
   return cudaGetLastError();
 }

@@ -199,6 +199,7 @@ int qr_panel_grid(int mrows) {
 size_t qr_work_bytes(int m, int n) {
   const int npan = (n + NB - 1) / NB;
   size_t b = 0;
+  b += align_up(sizeof(double) * (size_t)kSplitKElems);     // split-K partials
   b += align_up(sizeof(double) * (size_t)m * n);            // W
   b += align_up(sizeof(double) * (size_t)m * n);            // V
   b += align_up(sizeof(double) * (size_t)NB * NB * npan);   // Tf
@@ -214,6 +215,7 @@ QrWork qr_carve(void* base, int m, int n) {
   const int npan = (n + NB - 1) / NB;
   char* p = static_cast<char*>(base);
   QrWork w;
+  w.splitk = reinterpret_cast<double*>(p); p += align_up(sizeof(double) * (size_t)kSplitKElems);
   w.W = reinterpret_cast<double*>(p); p += align_up(sizeof(double) * (size_t)m * n);
   w.V = reinterpret_cast<double*>(p); p += align_up(sizeof(double) * (size_t)m * n);
   w.Tf = reinterpret_cast<double*>(p); p += align_up(sizeof(double) * (size_t)NB * NB * npan);
@@ -259,6 +261,7 @@ cudaError_t householder_qr_f64(int m, int n, const double* M, double* Q, double*
     const int n2 = n - j0 - nbj;
     if (n2 > 0) {
       Gemm g = gemm_init();
+      g.part = w.splitk; g.part_elems = kSplitKElems;
       // Y = V^T W2   (nbj x n2, K = mr)
       g.M = nbj; g.N = n2; g.K = mr;
       g.A = w.V + (size_t)j0 * m + j0; g.a_m = im1(m); g.a_k = im1(1);
@@ -294,6 +297,7 @@ cudaError_t householder_qr_f64(int m, int n, const double* M, double* Q, double*
     const int mr = m - j0, nq = n - j0;
     const double* Tp = w.Tf + (size_t)p * NB * NB;
     Gemm g = gemm_init();
+    g.part = w.splitk; g.part_elems = kSplitKElems;
     // Y = V^T Qs   (nbj x nq, K = mr)
     g.M = nbj; g.N = nq; g.K = mr;
     g.A = w.V + (size_t)j0 * m + j0; g.a_m = im1(m); g.a_k = im1(1);

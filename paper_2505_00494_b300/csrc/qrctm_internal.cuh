@@ -61,6 +61,9 @@ __host__ __device__ __forceinline__ long long map_off(const IdxMap& m, long long
 }
 
 // C[b](m,n) = alpha * sum_k A[b](m,k) B[b](k,n) + beta * C[b](m,n)
+// If `part` is set and the output grid is too small to fill the GPU, the K
+// range is split over CTAs; partial sums go to `part` (part_elems doubles)
+// and a second kernel adds them in a fixed order (deterministic).
 struct Gemm {
   long long M, N, K;
   int batch;
@@ -68,10 +71,14 @@ struct Gemm {
   const double* B; IdxMap b_k, b_n, b_b;
   double* C;       IdxMap c_m, c_n, c_b;
   double alpha, beta;
+  double* part;
+  long long part_elems;
 };
 
 static inline Gemm gemm_init() {
   Gemm g{};
+  g.part = nullptr;
+  g.part_elems = 0;
   g.batch = 1;
   g.a_b = im0(); g.b_b = im0(); g.c_b = im0();
   g.alpha = 1.0; g.beta = 0.0;
@@ -132,6 +139,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned int nblocks,
 // Householder QR (unpivoted, diag(R) >= 0) of a column-major m x n matrix.
 // ---------------------------------------------------------------------------
 struct QrWork {
+  double* splitk;   // split-K partial sums (kSplitKElems doubles)
   double* W;        // m x n working copy (column-major)
   double* V;        // m x n explicit reflectors (column-major, unit diagonal)
   double* Tf;       // nb x nb x npanel compact-WY factors
@@ -141,6 +149,7 @@ struct QrWork {
   GridBar* bar;
   int* err;
 };
+constexpr long long kSplitKElems = 1ll << 21;   // 16 MB of split-K partials
 size_t qr_work_bytes(int m, int n);
 QrWork qr_carve(void* base, int m, int n);
 int qr_panel_grid(int m);
