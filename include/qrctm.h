@@ -189,6 +189,24 @@ size_t qrctm_qr_workspace_bytes(int m, int n);
 qrctm_status qrctm_householder_qr(int m, int n, const double* M, double* Q, double* R,
                                   void* workspace, size_t bytes, void* stream);
 
+/* Householder QR that allocates nothing: the same result as
+ * qrctm_householder_qr, for callers that cannot obtain device memory of their
+ * own (a plug-in handed only input/output pointers by a host application that
+ * owns the device memory, a process whose device memory is already reserved
+ * by another runtime, code that must not enter the CUDA allocator).  The paper
+ * has no counterpart; this is a convenience of the library.  The scratch is
+ * one 48 MiB array inside the library that every device loading the library
+ * keeps until exit.  Limits: n <= 1024 and m * n <= 1048576 (for example
+ * 5184 x 144); larger sizes return QRCTM_ERR_WORKSPACE without touching the
+ * device.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array and each clears the
+ * words that must start at zero, so calls whose GPU work overlaps (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Synchronises `stream`. */
+qrctm_status qrctm_householder_qr_noalloc(int m, int n, const double* M, double* Q, double* R,
+                                          void* stream);
+
 /* Library version string. */
 const char* qrctm_version(void);
 

@@ -82,6 +82,8 @@ _sig = {
     "qrctm_qr_workspace_bytes": ([ctypes.c_int, ctypes.c_int], ctypes.c_size_t),
     "qrctm_householder_qr": ([ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                               _vp], ctypes.c_int),
+    "qrctm_householder_qr_noalloc": ([ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp],
+                                     ctypes.c_int),
 }
 EXPORTED = sorted(_sig)
 _LIB = None
