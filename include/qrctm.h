@@ -189,6 +189,19 @@ size_t qrctm_qr_workspace_bytes(int m, int n);
 qrctm_status qrctm_householder_qr(int m, int n, const double* M, double* Q, double* R,
                                   void* workspace, size_t bytes, void* stream);
 
+/* Split-precision matrix product on the tensor cores (the contraction engine
+ * of the QR-CTMRG split path):  C[m*ldc + n] = sum_k A[m*lda + k] B[n*ldb + k]
+ * for 0 <= m < M, 0 <= n < N, with A, B FP32 (device, K contiguous, lda and
+ * ldb multiples of 4, 16-byte aligned) and C FP64 (device, row-major).  Each
+ * operand is split into a TF32 head and an FP32 tail; the three products
+ * head*head + head*tail + tail*head accumulate in FP32 (about 2^-21 relative
+ * error per product).  err_word: device int (required) that the kernel sets
+ * if one of its bounded waits runs out; it is cleared first and read back, and
+ * a set word is returned as QRCTM_ERR_TIMEOUT.  Synchronises `stream`. */
+qrctm_status qrctm_gemm_tf32x3(int M, int N, int K, const float* A, long long lda, const float* B,
+                               long long ldb, double* C, long long ldc, int* err_word,
+                               void* stream);
+
 /* Householder QR that allocates nothing: the same result as
  * qrctm_householder_qr, for callers that cannot obtain device memory of their
  * own (a plug-in handed only input/output pointers by a host application that

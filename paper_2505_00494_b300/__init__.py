@@ -82,6 +82,8 @@ _sig = {
     "qrctm_qr_workspace_bytes": ([ctypes.c_int, ctypes.c_int], ctypes.c_size_t),
     "qrctm_householder_qr": ([ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                               _vp], ctypes.c_int),
+    "qrctm_gemm_tf32x3": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_longlong, _vp,
+                           ctypes.c_longlong, _vp, ctypes.c_longlong, _vp, _vp], ctypes.c_int),
     "qrctm_householder_qr_noalloc": ([ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp],
                                      ctypes.c_int),
 }
@@ -267,6 +269,25 @@ def c4v_symmetrize(X, normalize=True, stream=None):
     if code != 0:
         raise QRCTMError(code, "qrctm_c4v_symmetrize")
     return Y
+
+
+def gemm_tf32x3(A, B, stream=None):
+    """C = A @ B.T (C FP64) from FP32 CUDA matrices A (M x K), B (N x K) on the
+    tensor cores in split TF32x3 precision."""
+    torch = _torch()
+    M, K = A.shape
+    N = B.shape[0]
+    if A.dtype != torch.float32 or B.dtype != torch.float32:
+        raise TypeError("A and B must be float32")
+    C = torch.empty((M, N), dtype=torch.float64, device=A.device)
+    err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    code = _load().qrctm_gemm_tf32x3(M, N, K, ctypes.c_void_p(A.data_ptr()), A.stride(0),
+                                     ctypes.c_void_p(B.data_ptr()), B.stride(0),
+                                     ctypes.c_void_p(C.data_ptr()), N,
+                                     ctypes.c_void_p(err.data_ptr()), _stream_ptr(stream))
+    if code != 0:
+        raise QRCTMError(code, "qrctm_gemm_tf32x3")
+    return C
 
 
 def householder_qr(M, stream=None, workspace=None):

@@ -11,6 +11,7 @@
 #include <new>
 
 #include "ctx.cuh"
+#include "tc_gemm.cuh"
 
 using namespace qrctm;
 
@@ -444,6 +445,32 @@ qrctm_status qrctm_c4v_symmetrize(int d, int D, const double* X, double* Y, int 
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return QRCTM_ERR_CUDA;
     if (flag) return QRCTM_ERR_NUMERIC;
   }
+  return QRCTM_OK;
+}
+
+qrctm_status qrctm_gemm_tf32x3(int M, int N, int K, const float* A, long long lda, const float* B,
+                               long long ldb, double* C, long long ldc, int* err_word,
+                               void* stream) {
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !C || !err_word) return QRCTM_ERR_INVALID_ARG;
+  if (lda < K || ldb < K || ldc < N || (lda % 4) || (ldb % 4)) return QRCTM_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  TcGemm g{};
+  g.A = TcOperand{A, M, K, lda, 1, 0};
+  g.B = TcOperand{B, N, K, ldb, 1, 0};
+  g.M = M; g.N = N; g.K = K; g.batch = 1;
+  g.C = C; g.c_fp64 = true;
+  g.c_m = im1(ldc); g.c_n = im1(1); g.c_b = im0();
+  g.alpha = 1.0; g.beta = 0.0;
+  g.err = err_word;
+  if (cudaMemsetAsync(err_word, 0, sizeof(int), s) != cudaSuccess) return QRCTM_ERR_CUDA;
+  cudaError_t e = gemm_tc(g, s);
+  if (e == cudaErrorInvalidValue) return QRCTM_ERR_INVALID_ARG;
+  if (e != cudaSuccess) return QRCTM_ERR_CUDA;
+  int flag = 0;
+  if (cudaMemcpyAsync(&flag, err_word, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return QRCTM_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return QRCTM_ERR_CUDA;
+  if (flag) return (flag & ERRF_TIMEOUT) ? QRCTM_ERR_TIMEOUT : QRCTM_ERR_NUMERIC;
   return QRCTM_OK;
 }
 

@@ -1,0 +1,46 @@
+// Split-precision (TF32x3) contraction on tcgen05 tensor cores: interface.
+#pragma once
+
+#include "qrctm_internal.cuh"
+
+namespace qrctm {
+
+// A K-contiguous FP32 operand: element (b, r, k) at ptr[b*batch_stride + r*row_stride + k].
+// row_stride and batch_stride (elements) must be multiples of 4 (16 bytes)
+// and ptr 16-byte aligned (TMA rules).
+struct TcOperand {
+  const float* ptr;
+  long long rows;
+  long long K;
+  long long row_stride;
+  int batch;               // 1 = shared by every batch entry
+  long long batch_stride;
+};
+
+// D[b](m,n) = alpha * sum_k A[b](m,k) B[b](n,k) + beta * D[b](m,n), D stored
+// through index maps, FP32 or FP64.
+struct TcGemm {
+  TcOperand A, B;
+  long long M, N, K;
+  int batch;
+  void* C;
+  bool c_fp64;
+  IdxMap c_m, c_n, c_b;
+  double alpha, beta;
+  int* err;
+};
+
+// Kernel arguments (device side).
+struct TcArgs {
+  long long M, N, K;
+  void* C;
+  int c_fp64;
+  IdxMap c_m, c_n, c_b;
+  double alpha, beta;
+  int a_batched, b_batched;
+  int* err;
+};
+
+cudaError_t gemm_tc(const TcGemm& g, cudaStream_t s);
+
+}  // namespace qrctm
