@@ -195,12 +195,15 @@ qrctm_status qrctm_householder_qr(int m, int n, const double* M, double* Q, doub
  * ldb multiples of 4, 16-byte aligned) and C FP64 (device, row-major).  Each
  * operand is split into a TF32 head and an FP32 tail; the three products
  * head*head + head*tail + tail*head accumulate in FP32 (about 2^-21 relative
- * error per product).  err_word: device int (required) that the kernel sets
+ * error per product).  work: optional device scratch of work_elems floats; with
+ * it, K is cut into chunks of at most 512 (and more chunks when the M x N
+ * grid is small) whose FP32 partial sums are added in FP64; NULL = one pass
+ * over K.  err_word: device int (required) that the kernel sets
  * if one of its bounded waits runs out; it is cleared first and read back, and
  * a set word is returned as QRCTM_ERR_TIMEOUT.  Synchronises `stream`. */
 qrctm_status qrctm_gemm_tf32x3(int M, int N, int K, const float* A, long long lda, const float* B,
-                               long long ldb, double* C, long long ldc, int* err_word,
-                               void* stream);
+                               long long ldb, double* C, long long ldc, float* work,
+                               long long work_elems, int* err_word, void* stream);
 
 /* Householder QR that allocates nothing: the same result as
  * qrctm_householder_qr, for callers that cannot obtain device memory of their

@@ -83,7 +83,8 @@ _sig = {
     "qrctm_householder_qr": ([ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                               _vp], ctypes.c_int),
     "qrctm_gemm_tf32x3": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_longlong, _vp,
-                           ctypes.c_longlong, _vp, ctypes.c_longlong, _vp, _vp], ctypes.c_int),
+                           ctypes.c_longlong, _vp, ctypes.c_longlong, _vp, ctypes.c_longlong, _vp,
+                           _vp], ctypes.c_int),
     "qrctm_householder_qr_noalloc": ([ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp],
                                      ctypes.c_int),
 }
@@ -271,9 +272,10 @@ def c4v_symmetrize(X, normalize=True, stream=None):
     return Y
 
 
-def gemm_tf32x3(A, B, stream=None):
+def gemm_tf32x3(A, B, stream=None, split_k=True):
     """C = A @ B.T (C FP64) from FP32 CUDA matrices A (M x K), B (N x K) on the
-    tensor cores in split TF32x3 precision."""
+    tensor cores in split TF32x3 precision (K chunks summed in FP64 when
+    split_k)."""
     torch = _torch()
     M, K = A.shape
     N = B.shape[0]
@@ -281,9 +283,12 @@ def gemm_tf32x3(A, B, stream=None):
         raise TypeError("A and B must be float32")
     C = torch.empty((M, N), dtype=torch.float64, device=A.device)
     err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    nwork = (1 << 22) if split_k else 0
+    work = torch.empty(max(nwork, 1), dtype=torch.float32, device=A.device)
     code = _load().qrctm_gemm_tf32x3(M, N, K, ctypes.c_void_p(A.data_ptr()), A.stride(0),
                                      ctypes.c_void_p(B.data_ptr()), B.stride(0),
                                      ctypes.c_void_p(C.data_ptr()), N,
+                                     ctypes.c_void_p(work.data_ptr()) if nwork else None, nwork,
                                      ctypes.c_void_p(err.data_ptr()), _stream_ptr(stream))
     if code != 0:
         raise QRCTMError(code, "qrctm_gemm_tf32x3")

@@ -27,6 +27,7 @@ bool cfg_valid(const qrctm_config& c) {
   const long long D2 = (long long)c.D * c.D;
   if (D2 > 4096 || (long long)c.chi * D2 > (1ll << 20)) return false;
   if (c.chi < D2) return false;
+  if (c.precision == QRCTM_SPLIT && c.D < 2) return false;
   return true;
 }
 
@@ -111,6 +112,34 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
   take(R_(rho), 64);
   take(R_(e_d), 8);
 #undef R_
+  // split precision buffers (floats; carved as double regions of half size)
+  if (cfg.precision == QRCTM_SPLIT) {
+    auto p4 = [](size_t x) { return (x + 3) & ~size_t(3); };
+    const size_t chp = p4(chi), mp = p4(m), D2p = p4(D2), dD2p = p4(d * D2);
+    auto takef = [&](float** dst, size_t n_floats) {
+      size_t o = off;
+      off += al(sizeof(float) * (n_floats > 0 ? n_floats : 1));
+      if (carve) *dst = reinterpret_cast<float*>(c->ws + o);
+    };
+    static float* fdummy;
+    takef(carve ? &c->T32 : &fdummy, m * chp);
+    takef(carve ? &c->C32 : &fdummy, chi * chp);
+    takef(carve ? &c->Qt32 : &fdummy, m * chp);
+    takef(carve ? &c->Qc32 : &fdummy, chi * mp);
+    takef(carve ? &c->Ts32 : &fdummy, m * chp);
+    takef(carve ? &c->Rt32 : &fdummy, chi * chp);
+    takef(carve ? &c->Aket32 : &fdummy, d * D2 * D2p);
+    takef(carve ? &c->Abra32 : &fdummy, D2 * dD2p);
+    const size_t part = size_t(1) << 24;
+    takef(carve ? &c->tc_part : &fdummy, part);
+    if (carve) c->tc_part_elems = (long long)part;
+    // the FP32 intermediates X1, Z, X2, Y2 reuse the FP64 regions of the same
+    // names: for D >= 2 each needs at most as many bytes as its FP64 region
+  } else if (carve) {
+    c->T32 = c->C32 = c->Qt32 = c->Qc32 = c->Ts32 = c->Rt32 = c->Aket32 = c->Abra32 = nullptr;
+    c->tc_part = nullptr;
+    c->tc_part_elems = 0;
+  }
   {
     size_t o = off;
     off += al(qr_work_bytes((int)m, (int)chi));
@@ -289,6 +318,9 @@ qrctm_status qrctm_init_env(qrctm_ctx* c, const double* A, const double* C0, con
     if ((e = double_layer_kernel(d, D, c->A, c->a, c->st)) != cudaSuccess)
       return cuda_fail(c, e, "double layer");
   }
+  if (c->split_prec) {
+    if ((e = split_prepare_A(c)) != cudaSuccess) return cuda_fail(c, e, "split A");
+  }
   c->iters = 0;
   c->spec_valid = false;
   if (C0 != nullptr) {
@@ -332,7 +364,8 @@ qrctm_status qrctm_step(qrctm_ctx* c, int n, double* delta_out) {
   if (!c->have_env) return set_err(c, QRCTM_ERR_STATE, "qrctm_init_env not called");
   cudaError_t e;
   for (int i = 0; i < n; ++i)
-    if ((e = qr_step(c)) != cudaSuccess) return cuda_fail(c, e, "qr step");
+    if ((e = c->split_prec ? qr_step_split(c) : qr_step(c)) != cudaSuccess)
+      return cuda_fail(c, e, "qr step");
   if (delta_out) {
     if ((e = spectrum_check(c)) != cudaSuccess) return cuda_fail(c, e, "spectrum");
     qrctm_status s = sync_check(c, "step");
@@ -449,8 +482,8 @@ qrctm_status qrctm_c4v_symmetrize(int d, int D, const double* X, double* Y, int 
 }
 
 qrctm_status qrctm_gemm_tf32x3(int M, int N, int K, const float* A, long long lda, const float* B,
-                               long long ldb, double* C, long long ldc, int* err_word,
-                               void* stream) {
+                               long long ldb, double* C, long long ldc, float* work,
+                               long long work_elems, int* err_word, void* stream) {
   if (M < 1 || N < 1 || K < 1 || !A || !B || !C || !err_word) return QRCTM_ERR_INVALID_ARG;
   if (lda < K || ldb < K || ldc < N || (lda % 4) || (ldb % 4)) return QRCTM_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -462,6 +495,8 @@ qrctm_status qrctm_gemm_tf32x3(int M, int N, int K, const float* A, long long ld
   g.c_m = im1(ldc); g.c_n = im1(1); g.c_b = im0();
   g.alpha = 1.0; g.beta = 0.0;
   g.err = err_word;
+  g.part = work;
+  g.part_elems = work ? work_elems : 0;
   if (cudaMemsetAsync(err_word, 0, sizeof(int), s) != cudaSuccess) return QRCTM_ERR_CUDA;
   cudaError_t e = gemm_tc(g, s);
   if (e == cudaErrorInvalidValue) return QRCTM_ERR_INVALID_ARG;

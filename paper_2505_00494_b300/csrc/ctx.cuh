@@ -31,6 +31,10 @@ struct qrctm_ctx {
   double* a;           // double layer (only with DOUBLE layers)
   // energy
   double *E1, *E2, *E3, *rho, *e_d;
+  // split precision: FP32 operand copies (rows padded to 4 floats) and the
+  // tensor-core split-K partial sums
+  float *T32, *C32, *Qt32, *Qc32, *Ts32, *Rt32, *Aket32, *Abra32, *tc_part;
+  long long tc_part_elems;
   // gradient
   char* G;             // gradient region base (carved by grad.cu)
   size_t G_bytes;
@@ -80,6 +84,10 @@ cudaError_t renorm_edge(qrctm_ctx* c, const double* P, int chi_out, const double
 cudaError_t qr_step(qrctm_ctx* c);
 cudaError_t warmup_step(qrctm_ctx* c, int chi_in, int chi_out);
 cudaError_t spectrum_check(qrctm_ctx* c);
+
+// Split-precision step (split_step.cu)
+cudaError_t split_prepare_A(qrctm_ctx* c);
+cudaError_t qr_step_split(qrctm_ctx* c);
 
 // Energy (energy.cu)
 cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2);

@@ -145,7 +145,9 @@ struct Cfg {
   static constexpr int B_BYTES = BN * BK * 4;
   static constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);   // x and lo tiles
   static constexpr int STAGES = std::min(4, (210 * 1024) / STAGE_BYTES);
-  static constexpr int TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+  // main accumulator at column 0, correction accumulator at column HALF
+  static constexpr int HALF = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+  static constexpr int TMEM_COLS = 2 * HALF;
   static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + 1024 + BN * 8;
 };
 
@@ -174,9 +176,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long m0 = (long long)blockIdx.x * BM;
-  const int n0 = blockIdx.y * BN, z = blockIdx.z;
+  const int n0 = blockIdx.y * BN;
+  const int z = blockIdx.z / args.ksplit, kz = blockIdx.z % args.ksplit;
   int issued = 0;   // TMA k-blocks issued (producer lane only)
-  const int nkb = (args.K + BK - 1) / BK;
+  const int nkb_all = (int)((args.K + BK - 1) / BK);
+  const int kb0 = kz * args.kb_per_split;
+  const int nkb = max(0, min(nkb_all - kb0, args.kb_per_split));
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -209,8 +214,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int s = kb % S;
         if (kb >= S && !mbar_wait(empty0 + 8 * s, ((kb / S) - 1) & 1, abort_flag, args.err)) break;
         mbar_arrive_expect_tx(full0 + 8 * s, C::A_BYTES + C::B_BYTES);
-        tma_load(smem_u32(xA(s)), &tmA, kb * BK, (int)m0, za, full0 + 8 * s);
-        tma_load(smem_u32(xB(s)), &tmB, kb * BK, n0, zb, full0 + 8 * s);
+        tma_load(smem_u32(xA(s)), &tmA, (kb0 + kb) * BK, (int)m0, za, full0 + 8 * s);
+        tma_load(smem_u32(xB(s)), &tmB, (kb0 + kb) * BK, n0, zb, full0 + 8 * s);
         issued = kb + 1;
       }
     }
@@ -226,13 +231,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t ah = smem_u32(xA(s)), al = smem_u32(loA(s));
         const uint32_t bh = smem_u32(xB(s)), bl = smem_u32(loB(s));
+        // head*head into the main accumulator; the two head*tail terms into
+        // a separate one, so that the tensor core's truncating accumulation
+        // never adds ~2^-11-sized terms to the large running sum
 #pragma unroll
         for (int ks = 0; ks < BK / 8; ++ks) {
           const uint32_t off = ks * 32;   // 8 TF32 = 32 bytes along K
-          umma_tf32(tmem, desc_sw128(ah + off), desc_sw128(bh + off), idesc,
-                    (kb > 0 || ks > 0) ? 1u : 0u);
-          umma_tf32(tmem, desc_sw128(ah + off), desc_sw128(bl + off), idesc, 1u);
-          umma_tf32(tmem, desc_sw128(al + off), desc_sw128(bh + off), idesc, 1u);
+          const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
+          umma_tf32(tmem, desc_sw128(ah + off), desc_sw128(bh + off), idesc, acc);
+          umma_tf32(tmem + C::HALF, desc_sw128(ah + off), desc_sw128(bl + off), idesc, acc);
+          umma_tf32(tmem + C::HALF, desc_sw128(al + off), desc_sw128(bh + off), idesc, 1u);
         }
         umma_commit(empty0 + 8 * s);
       }
@@ -281,14 +289,29 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int row = q * 32 + lane;
       const long long m = (long long)m0 + row;
       const bool mvalid = m < args.M;
-      const long long base_off = map_off(args.c_b, z) + (mvalid ? map_off(args.c_m, m) : 0);
+      const bool split = args.ksplit > 1;
+      const long long base_off =
+          split ? (((long long)z * args.ksplit + kz) * args.M + (mvalid ? m : 0)) * args.N
+                : map_off(args.c_b, z) + (mvalid ? map_off(args.c_m, m) : 0);
 #pragma unroll 1
       for (int c = 0; c < (BN + 31) / 32; ++c) {
-        float v[32];
-        tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + c * 32, v);
+        float v[32], w[32];
+        const uint32_t ta = tmem + (static_cast<uint32_t>(q * 32) << 16) + c * 32;
+        tmem_ld32(ta, v);
+        tmem_ld32(ta + C::HALF, w);
         if (!mvalid) continue;
+        if (split) {
+          float* p = args.part + base_off + n0 + c * 32;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int jj = c * 32 + j;
+            if (jj < BN && (long long)n0 + jj < args.N) p[j] = v[j] + w[j];
+          }
+          continue;
+        }
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
+          v[j] += w[j];
           const int jj = c * 32 + j;
           if (jj >= BN || (long long)n0 + jj >= args.N) continue;
           const long long off = base_off + col_off[jj];
@@ -323,6 +346,30 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(C::TMEM_COLS)
                  : "memory");
+  }
+}
+
+// out(b,m,n) = alpha * sum_z part[b][z][m][n] (in z order, FP64) + beta * out
+__global__ void tc_splitk_reduce(const TcArgs a, int batch) {
+  const long long MN = a.M * a.N;
+  const long long tot = MN * batch;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long b = e / MN, r = e % MN, m = r / a.N, n = r % a.N;
+    double acc = 0.0;
+    const float* p = a.part + b * a.ksplit * MN + r;
+    for (int z = 0; z < a.ksplit; ++z) acc += static_cast<double>(p[(long long)z * MN]);
+    const long long off = map_off(a.c_b, b) + map_off(a.c_m, m) + map_off(a.c_n, n);
+    double v = a.alpha * acc;
+    if (a.c_fp64) {
+      double* o = static_cast<double*>(a.C) + off;
+      if (a.beta != 0.0) v += a.beta * *o;
+      *o = v;
+    } else {
+      float* o = static_cast<float*>(a.C) + off;
+      if (a.beta != 0.0) v += a.beta * static_cast<double>(*o);
+      *o = static_cast<float>(v);
+    }
   }
 }
 
@@ -387,10 +434,42 @@ cudaError_t launch_bn(const TcGemm& g, cudaStream_t s) {
   a.a_batched = g.A.batch > 1 ? 1 : 0;
   a.b_batched = g.B.batch > 1 ? 1 : 0;
   a.err = g.err;
+  // K chunks: at most 512 of K (16 blocks) per chunk, more chunks when the
+  // output grid alone cannot fill the GPU; partials are summed in FP64
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 148;
+  }
+  const long long tiles = ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN) * std::max(1, g.batch);
+  const int nkb = (int)((g.K + BK - 1) / BK);
+  int ksplit = 1, kbps = nkb;
+  if (g.part != nullptr && nkb > 2) {
+    long long want = std::max<long long>((nkb + 15) / 16, (2ll * nsm + tiles - 1) / tiles);
+    want = std::min<long long>(want, nkb / 2);
+    const long long cap = g.part_elems / (g.M * g.N * std::max(1, g.batch));
+    want = std::min<long long>(want, cap);
+    if (want > 1) {
+      kbps = (int)((nkb + want - 1) / want);
+      ksplit = (nkb + kbps - 1) / kbps;
+    }
+  }
+  a.ksplit = ksplit;
+  a.kb_per_split = kbps;
+  a.part = g.part;
+  if ((long long)std::max(1, g.batch) * ksplit > 65535) return cudaErrorInvalidValue;
   dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + BN - 1) / BN),
-            (unsigned)std::max(1, g.batch));
+            (unsigned)(std::max(1, g.batch) * ksplit));
   tc_tf32x3_kernel<BN><<<grid, NTHREADS, C::SMEM, s>>>(ta, tb, a);
   note_launch();
+  if (ksplit > 1) {
+    const long long tot = g.M * g.N * std::max(1, g.batch);
+    tc_splitk_reduce<<<(unsigned)std::min<long long>((tot + 255) / 256, 4096), 256, 0, s>>>(
+        a, std::max(1, g.batch));
+    note_launch();
+  }
   return cudaGetLastError();
 }
 

@@ -28,6 +28,10 @@ struct TcGemm {
   IdxMap c_m, c_n, c_b;
   double alpha, beta;
   int* err;
+  // optional split-K scratch (FP32 partial sums, part_elems floats); long K
+  // ranges are cut into chunks of at most 512 that are summed in FP64
+  float* part;
+  long long part_elems;
 };
 
 // Kernel arguments (device side).
@@ -39,6 +43,9 @@ struct TcArgs {
   double alpha, beta;
   int a_batched, b_batched;
   int* err;
+  int ksplit;          // K chunks per output tile (1 = no split)
+  int kb_per_split;    // 32-wide K blocks per chunk
+  float* part;         // ksplit > 1: partials [batch][ksplit][M][N]
 };
 
 cudaError_t gemm_tc(const TcGemm& g, cudaStream_t s);

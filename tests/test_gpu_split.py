@@ -1,0 +1,57 @@
+"""GPU parity of the split-precision path (TF32x3 tensor-core contractions,
+FP64 QR, normalisation and traces) against the FP64 CPU oracle.
+
+Tolerances: one step from the same environment, elementwise 2e-5 relative to
+the largest entry (TF32x3 products carry ~2^-21 relative error, FP32
+partial sums ~2^-24 per addition, and the QR of the reduced corner can
+amplify them by its conditioning); energy per site of converged
+environments |dE| <= 1e-7 (the split-path target)."""
+import numpy as np
+import pytest
+
+from oracle import qrctm_oracle as o
+import qrctm_inputs as qi
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch  # noqa: F401
+    from paper_2505_00494_b300 import build
+    build.build()
+    import paper_2505_00494_b300 as q
+    return q
+
+
+def cuda(x):
+    import torch
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+@pytest.mark.parametrize("D,chi,seed", [(2, 16, 3), (3, 27, 4), (4, 32, 5)])
+def test_split_single_step(q, D, chi, seed):
+    A = o.normalized_input(qi.raw_tensor(2, D, seed))
+    C, T = o.warmup(A, chi)
+    Cn, Tn = o.qr_step(C, T, A)
+    ctx = q.QRCTM(2, D, chi, precision="split")
+    ctx.init_env(cuda(A), cuda(C), cuda(T))
+    ctx.step(1, want_delta=False)
+    Cg, Tg, _ = ctx.get_env(spectrum=False)
+    Cg, Tg = Cg.cpu().numpy(), Tg.cpu().numpy()
+    assert np.abs(Cg - Cn).max() < 2e-5 * np.abs(Cn).max()
+    assert np.abs(Tg - Tn).max() < 2e-5 * np.abs(Tn).max()
+
+
+@pytest.mark.parametrize("D,chi,seed,decay", [(2, 16, 0, False), (3, 27, 1, True)])
+def test_split_converged_energy(q, D, chi, seed, decay):
+    A = o.normalized_input(qi.raw_tensor(2, D, seed, decay))
+    C, T = o.warmup(A, chi)
+    Co, To, info = o.ctmrg(A, chi, "qr", tol=1e-12, max_iter=400, init=(C, T))
+    Eo = o.energy(Co, To, A, 1.0, 0.5)
+    ctx = q.QRCTM(2, D, chi, precision="split", with_nnn=True, check_every=5)
+    ctx.init_env(cuda(A), cuda(C), cuda(T))
+    it, dlt = ctx.run_to_convergence(tol=1e-9, max_iter=400)
+    Eg = ctx.energy(1.0, 0.5)
+    print("split", D, chi, "iters", it, "delta", dlt, "dE", Eg - Eo)
+    assert abs(Eg - Eo) < 1e-7
