@@ -99,7 +99,7 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
   take(R_(Y2), m * chi);
   take(R_(Xs), m * chi);
   take(R_(Yw), m * chi);
-  take(R_(spec_work), nC + 8 * chi);
+  take(R_(spec_work), nC + 8 * chi + 16);
   take(R_(s_cur), chi);
   take(R_(s_prev), chi);
   take(R_(delta_d), 8);

@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(1024) spectrum_kernel(const double* __restrict
     dg[n - 1] = Am[(long long)(n - 1) * n + n - 1];
   }
   __syncthreads();
-  // squared off-diagonals into v, Gershgorin interval
+  // squared off-diagonals into v, Gershgorin interval into p[0..2]
   double lo_l = 1e300, hi_l = -1e300, amax = 0.0;
   for (int i = tid; i < n; i += nt) {
     double r = (i > 0 ? fabs(of[i - 1]) : 0.0) + (i + 1 < n ? fabs(of[i]) : 0.0);
@@ -269,22 +269,51 @@ __global__ void __launch_bounds__(1024) spectrum_kernel(const double* __restrict
   }
   if ((tid & 31) == 0) { mn[tid >> 5] = lo_l; mx[tid >> 5] = hi_l; am[tid >> 5] = amax; }
   __syncthreads();
-  double lo = 1e300, hi = -1e300, big = 0.0;
-  for (int w = 0; w < (nt >> 5); ++w) { lo = fmin(lo, mn[w]); hi = fmax(hi, mx[w]); big = fmax(big, am[w]); }
-  if (!(big == big) || isinf(big)) { if (tid == 0) atomicOr(err, ERRF_NUMERIC); }
-  const double pivmin = fmax(1e-300, big * 1e-300);
-  // bisection: thread i finds the i-th smallest eigenvalue
-  for (int i = tid; i < n; i += nt) {
-    double a = lo - 1e-14 * fabs(lo) - 1e-300, b = hi + 1e-14 * fabs(hi) + 1e-300;
-    for (int it = 0; it < 200; ++it) {
-      double mid = 0.5 * (a + b);
-      if (mid == a || mid == b) break;
-      if (sturm_count(dg, v, n, mid, pivmin) > i) b = mid; else a = mid;
-    }
-    ev[i] = 0.5 * (a + b);
+  if (tid == 0) {
+    double lo = 1e300, hi = -1e300, big = 0.0;
+    for (int w = 0; w < (nt >> 5); ++w) { lo = fmin(lo, mn[w]); hi = fmax(hi, mx[w]); big = fmax(big, am[w]); }
+    if (!(big == big) || isinf(big)) atomicOr(err, ERRF_NUMERIC);
+    p[0] = lo - 1e-14 * fabs(lo) - 1e-300;
+    p[1] = hi + 1e-14 * fabs(hi) + 1e-300;
+    p[2] = fmax(1e-300, big * 1e-300);       // pivot floor of the Sturm recurrence
   }
-  __syncthreads();
-  // sort |lambda| descending into s_new (rank by counting, ties by index)
+  (void)s_new; (void)s_old; (void)n_old; (void)delta;
+}
+
+// Eigenvalue i of the tridiagonal (dg, e^2) by multisection: one warp per
+// eigenvalue, the 32 lanes evaluate Sturm counts at 32 interior points of the
+// current bracket, which shrinks 33-fold per round until it stops shrinking.
+__global__ void bisect_kernel(const double* work, int n, double* ev_out) {
+  const double* dg = work + (size_t)n * n;
+  const double* v = dg + 3 * (size_t)n;       // e^2
+  const double* p = v + n;                    // lo, hi, pivmin
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= n) return;
+  double a = p[0], b = p[1];
+  const double pivmin = p[2];
+  for (int round = 0; round < 64; ++round) {
+    const double h = (b - a) / 33.0;
+    const double x = a + h * (lane + 1);
+    const bool above = (x > a && x < b) ? (sturm_count(dg, v, n, x, pivmin) > i) : (x >= b);
+    const unsigned mask = __ballot_sync(0xffffffffu, above);
+    // first lane whose point lies above eigenvalue i bounds it from above
+    const int first = mask ? __ffs(mask) - 1 : 32;
+    const double na = (first == 0) ? a : a + h * first;
+    const double nb = (first == 32) ? b : a + h * (first + 1);
+    if (!(nb < b || na > a)) break;          // no progress: bracket at resolution
+    a = na;
+    b = nb;
+    if (b - a <= 4e-16 * fmax(fabs(a), fabs(b))) break;
+  }
+  if (lane == 0) ev_out[i] = 0.5 * (a + b);
+}
+
+// sorted |lambda| (descending, ties by index) and the change to the previous
+__global__ void spectrum_finish_kernel(const double* ev, int n, double* s_new, const double* s_old,
+                                       int n_old, double* delta) {
+  __shared__ double red[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < n; i += nt) {
     double ai = fabs(ev[i]);
     int rank = 0;
@@ -298,9 +327,9 @@ __global__ void __launch_bounds__(1024) spectrum_kernel(const double* __restrict
   const int nm = n > n_old ? n : n_old;
   double acc = 0.0;
   for (int i = tid; i < nm; i += nt) {
-    double a = (i < n) ? s_new[i] : 0.0;
-    double b = (s_old != nullptr && i < n_old) ? s_old[i] : 0.0;
-    acc += (a - b) * (a - b);
+    double x = (i < n) ? s_new[i] : 0.0;
+    double y = (s_old != nullptr && i < n_old) ? s_old[i] : 0.0;
+    acc += (x - y) * (x - y);
   }
   double tot = block_sum(acc, red);
   if (tid == 0) *delta = sqrt(tot);
@@ -375,11 +404,18 @@ cudaError_t double_layer_kernel(int d, int D, const double* A, double* a, cudaSt
   return cudaGetLastError();
 }
 
+// work: chi*chi + 8*chi + 16 doubles: matrix, diagonal, off-diagonal, (unused),
+// squared off-diagonal, Gershgorin bracket + pivot floor, eigenvalues
 cudaError_t corner_spectrum(const double* C, int chi, double* work, double* s_new,
                             const double* s_old, int chi_old, double* delta, int* err,
                             cudaStream_t s) {
   if (chi < 1 || chi > 1024) return cudaErrorInvalidValue;
   spectrum_kernel<<<1, 1024, 0, s>>>(C, chi, work, s_new, s_old, chi_old, delta, err);
+  note_launch();
+  double* ev = work + (size_t)chi * chi + 5 * (size_t)chi + 8;
+  bisect_kernel<<<(chi + 3) / 4, 128, 0, s>>>(work, chi, ev);
+  note_launch();
+  spectrum_finish_kernel<<<1, 256, 0, s>>>(ev, chi, s_new, s_old, chi_old, delta);
   note_launch();
   return cudaGetLastError();
 }

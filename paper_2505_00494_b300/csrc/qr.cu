@@ -27,7 +27,7 @@ __host__ __device__ inline size_t align_up(size_t x) { return (x + 255) & ~size_
 
 __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
                                                       double* __restrict__ V,
-                                                      double* __restrict__ Tf,
+                                                      double* __restrict__ tau_out,
                                                       double* __restrict__ part, GridBar* bar,
                                                       int* err, int m, int j0, int nb,
                                                       int rows_per_cta) {
@@ -35,10 +35,9 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
   const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;   // wrp = row lane (0..7)
   const long long r_begin = (long long)j0 + (long long)b * rows_per_cta;
   const long long r_end = std::min<long long>(m, r_begin + rows_per_cta);
-  // scratch: psum[2][P][NB], rowb[2][NB], gram[P][NB*NB]
+  // scratch: psum[2][P][NB], rowb[2][NB]
   double* psum = part;
   double* rowb = part + 2 * (size_t)P * NB;
-  double* gram = rowb + 2 * NB;
   __shared__ double red[8][NB];
   __shared__ double tot[NB];
   __shared__ double sc[4];
@@ -76,9 +75,19 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     const int buf = j & 1;
     const long long c = (long long)j0 + j;
     const int nrem = nb - j - 1;
+    // cross-CTA reduction of the partial sums: lane = column slot, the 8 warps
+    // take every 8th CTA, then a fixed-order sum over the warps
+    {
+      double s = 0.0;
+      if (lane <= nrem)
+        for (int q = wrp; q < P; q += 8) s += psum[((size_t)buf * P + q) * NB + lane];
+      red[wrp][lane] = s;
+    }
+    __syncthreads();
     if ((int)threadIdx.x <= nrem) {
       double s = 0.0;
-      for (int q = 0; q < P; ++q) s += psum[((size_t)buf * P + q) * NB + threadIdx.x];
+#pragma unroll
+      for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
       tot[threadIdx.x] = s;
     }
     __syncthreads();
@@ -128,27 +137,18 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     if (!grid_barrier(bar, P, err)) return;
   }
 
-  // Gram matrix of the explicit reflectors for the compact-WY factor
-  for (int e = threadIdx.x; e < nb * nb; e += PT) {
-    const int p = e / nb, q = e % nb;
-    double s = 0.0;
-    if (q >= p) {
-      const long long i0 = std::max<long long>(r_begin, (long long)j0 + q);
-      for (long long i = i0; i < r_end; ++i)
-        s = fma(V[((long long)j0 + p) * m + i], V[((long long)j0 + q) * m + i], s);
-    }
-    gram[(size_t)b * NB * NB + e] = s;
-  }
-  if (!grid_barrier(bar, P, err)) return;
-  if (b != 0) return;
-  // T (upper triangular, nb x nb, row-major): T_jj = tau_j,
-  // T[0:j, j] = -tau_j T[0:j, 0:j] G[0:j, j]
+  // tau of the panel columns for the compact-WY factor (built after the kernel)
+  if (b == 0 && threadIdx.x < (unsigned)nb) tau_out[threadIdx.x] = tau_s[threadIdx.x];
+}
+
+// T (upper triangular, nb x nb, row stride NB): T_jj = tau_j,
+// T[0:j, j] = -tau_j T[0:j, 0:j] G[0:j, j], with G = V^T V of the panel.
+__global__ void qr_tfactor_kernel(const double* __restrict__ G, const double* __restrict__ tau,
+                                  double* __restrict__ Tf, int nb) {
   __shared__ double Gs[NB][NB + 1];
   __shared__ double Ts[NB][NB + 1];
-  for (int e = threadIdx.x; e < nb * nb; e += PT) {
-    double s = 0.0;
-    for (int q = 0; q < P; ++q) s += gram[(size_t)q * NB * NB + e];
-    Gs[e / nb][e % nb] = s;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    Gs[e / nb][e % nb] = G[(e / nb) * NB + (e % nb)];
     Ts[e / nb][e % nb] = 0.0;
   }
   __syncthreads();
@@ -157,14 +157,15 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     const int i = threadIdx.x;
     if (i < j) {
       for (int l = i; l < j; ++l) val = fma(Ts[i][l], Gs[l][j], val);
-      val *= -tau_s[j];
+      val *= -tau[j];
     }
     __syncthreads();
     if (i < j) Ts[i][j] = val;
-    if (i == j) Ts[j][j] = tau_s[j];
+    if (i == j) Ts[j][j] = tau[j];
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < nb * nb; e += PT) Tf[(e / nb) * NB + (e % nb)] = Ts[e / nb][e % nb];
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x)
+    Tf[(e / nb) * NB + (e % nb)] = Ts[e / nb][e % nb];
 }
 
 __global__ void extract_r_kernel(const double* __restrict__ W, double* __restrict__ R, int m,
@@ -252,12 +253,29 @@ cudaError_t householder_qr_f64(int m, int n, const double* M, double* Q, double*
     int rpc = (mr + P - 1) / P;
     double* Tp = w.Tf + (size_t)p * NB * NB;
     double* W = w.W; double* V = w.V; double* part = w.part;
+    // after the panel partial sums: G (NB x NB) and tau (NB) of this panel
+    double* Gp = w.part + 2 * (size_t)PMAX * NB + 2 * NB;
+    double* taup = Gp + NB * NB;
     GridBar* bar = w.bar; int* err = w.err;
     int m_ = m, j0_ = j0, nb_ = nbj;
-    void* args[] = {&W, &V, &Tp, &part, &bar, &err, &m_, &j0_, &nb_, &rpc};
+    void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc};
     e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel, dim3(P), dim3(PT), args, 0, s);
     if (e != cudaSuccess) return e;
     note_launch();
+    {
+      // G = V_p^T V_p over the panel rows (reflectors are zero above their
+      // unit diagonal), then T from G and tau
+      Gemm g = gemm_init();
+      g.part = w.splitk; g.part_elems = kSplitKElems;
+      g.M = nbj; g.N = nbj; g.K = mr;
+      g.A = w.V + (size_t)j0 * m + j0; g.a_m = im1(m); g.a_k = im1(1);
+      g.B = w.V + (size_t)j0 * m + j0; g.b_k = im1(1); g.b_n = im1(m);
+      g.C = Gp; g.c_m = im1(NB); g.c_n = im1(1);
+      if ((e = gemm_f64(g, s)) != cudaSuccess) return e;
+      qr_tfactor_kernel<<<1, NB, 0, s>>>(Gp, taup, Tp, nbj);
+      note_launch();
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     const int n2 = n - j0 - nbj;
     if (n2 > 0) {
       Gemm g = gemm_init();
