@@ -132,11 +132,13 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
     takef(carve ? &c->Abra32 : &fdummy, D2 * dD2p);
     const size_t part = size_t(1) << 24;
     takef(carve ? &c->tc_part : &fdummy, part);
+    takef(carve ? &c->qr32 : &fdummy, qr_split_floats((int)m, (int)chi));
     if (carve) c->tc_part_elems = (long long)part;
     // the FP32 intermediates X1, Z, X2, Y2 reuse the FP64 regions of the same
     // names: for D >= 2 each needs at most as many bytes as its FP64 region
   } else if (carve) {
     c->T32 = c->C32 = c->Qt32 = c->Qc32 = c->Ts32 = c->Rt32 = c->Aket32 = c->Abra32 = nullptr;
+    c->qr32 = nullptr;
     c->tc_part = nullptr;
     c->tc_part_elems = 0;
   }

@@ -33,7 +33,7 @@ struct qrctm_ctx {
   double *E1, *E2, *E3, *rho, *e_d;
   // split precision: FP32 operand copies (rows padded to 4 floats) and the
   // tensor-core split-K partial sums
-  float *T32, *C32, *Qt32, *Qc32, *Ts32, *Rt32, *Aket32, *Abra32, *tc_part;
+  float *T32, *C32, *Qt32, *Qc32, *Ts32, *Rt32, *Aket32, *Abra32, *tc_part, *qr32;
   long long tc_part_elems;
   // gradient
   char* G;             // gradient region base (carved by grad.cu)

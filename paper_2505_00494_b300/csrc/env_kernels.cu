@@ -10,6 +10,8 @@
 //   bisection, one CTA.
 #include "qrctm_internal.cuh"
 
+#include <algorithm>
+
 namespace qrctm {
 
 namespace {
@@ -174,18 +176,33 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
+// Number of eigenvalues of the symmetric tridiagonal (dg, e2 = offdiag^2)
+// below x: sign changes of the leading-minor sequence
+//   p_0 = 1, p_1 = d_0 - x, p_i = (d_{i-1} - x) p_{i-1} - e2_{i-2} p_{i-2},
+// i.e. negative pivots of T - x I (Sylvester's inertia).  No divisions: the
+// pair (p_{i-1}, p_i) is rescaled by an exact power of two when it leaves
+// [2^-400, 2^400]; an exact zero p_i is replaced by -pivmin * p_{i-1}.
 __device__ int sturm_count(const double* dg, const double* e2, int n, double x, double pivmin) {
   int cnt = 0;
-  double q = dg[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  if (q < 0) ++cnt;
+  double pm = 1.0, pc = dg[0] - x;
+  if (pc == 0.0) pc = -pivmin;
+  cnt += (pc < 0.0);
   for (int i = 1; i < n; ++i) {
-    q = dg[i] - x - e2[i - 1] / q;
-    if (fabs(q) < pivmin) q = -pivmin;
-    if (q < 0) ++cnt;
+    double pn = fma(dg[i] - x, pc, -e2[i - 1] * pm);
+    if (pn == 0.0) pn = -pivmin * pc;
+    cnt += ((pn < 0.0) != (pc < 0.0));
+    pm = pc;
+    pc = pn;
+    const double a = fabs(pc);
+    if (a > 0x1p400) { pc *= 0x1p-400; pm *= 0x1p-400; }
+    else if (a < 0x1p-400) { pc *= 0x1p400; pm *= 0x1p400; }
   }
   return cnt;
 }
+
+// Householder tridiagonalisation of (C + C^T)/2.  The matrix lives in shared
+// memory when it fits (n <= kSmemSpecMax), else in `work`.
+constexpr int kSmemSpecMax = 160;
 
 __global__ void __launch_bounds__(1024) spectrum_kernel(const double* __restrict__ C, int n,
                                                         double* work, double* s_new,
@@ -193,12 +210,14 @@ __global__ void __launch_bounds__(1024) spectrum_kernel(const double* __restrict
                                                         double* delta, int* err) {
   __shared__ double red[32];
   __shared__ double sc[2];
-  double* Am = work;                 // n x n
+  extern __shared__ double spec_smem[];
+  double* Am = (n <= kSmemSpecMax) ? spec_smem : work;   // n x n
   double* dg = work + (size_t)n * n; // n
   double* of = dg + n;               // n (off-diagonal)
   double* ev = of + n;               // n
-  double* v = ev + n;                // n
-  double* p = v + n;                 // n
+  double* v = ev + n;                // n (squared off-diagonal, after the loop)
+  double* p = v + n;                 // n (bracket, after the loop)
+  __shared__ double sv[1024], sp[1024];   // Householder vector and A v during the loop
   const int tid = threadIdx.x, nt = blockDim.x;
   for (long long e = tid; e < (long long)n * n; e += nt) {
     int i = (int)(e / n), j = (int)(e % n);
@@ -223,24 +242,33 @@ __global__ void __launch_bounds__(1024) spectrum_kernel(const double* __restrict
       __syncthreads();
       continue;
     }
-    if (tid < L) v[tid] = (tid == 0) ? sc[0] : xi;
+    if (tid < L) sv[tid] = (tid == 0) ? sc[0] : xi;
     __syncthreads();
-    double vv = block_sum((tid < L) ? v[tid] * v[tid] : 0.0, red);
+    double vv = block_sum((tid < L) ? sv[tid] * sv[tid] : 0.0, red);
     const double beta = 2.0 / vv;
-    // p = beta * A22 v  (A22 symmetric: read columns for coalescing)
+    // p = beta * A22 v  (A22 symmetric: read columns; four independent sums)
     if (tid < L) {
-      double acc = 0.0;
-      for (int j = 0; j < L; ++j) acc = fma(Am[(long long)(k + 1 + j) * n + k + 1 + tid], v[j], acc);
-      p[tid] = beta * acc;
+      const double* col = Am + (long long)(k + 1) * n + k + 1 + tid;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int j = 0;
+      for (; j + 4 <= L; j += 4) {
+        a0 = fma(col[(long long)j * n], sv[j], a0);
+        a1 = fma(col[(long long)(j + 1) * n], sv[j + 1], a1);
+        a2 = fma(col[(long long)(j + 2) * n], sv[j + 2], a2);
+        a3 = fma(col[(long long)(j + 3) * n], sv[j + 3], a3);
+      }
+      for (; j < L; ++j) a0 = fma(col[(long long)j * n], sv[j], a0);
+      sp[tid] = beta * ((a0 + a1) + (a2 + a3));
     }
     __syncthreads();
-    double pv = block_sum((tid < L) ? p[tid] * v[tid] : 0.0, red);
+    double pv = block_sum((tid < L) ? sp[tid] * sv[tid] : 0.0, red);
     const double K = 0.5 * beta * pv;
-    if (tid < L) p[tid] = p[tid] - K * v[tid];      // w
+    if (tid < L) sp[tid] = sp[tid] - K * sv[tid];      // w
     __syncthreads();
-    for (long long e = tid; e < (long long)L * L; e += nt) {
-      int i = (int)(e / L), j = (int)(e % L);
-      Am[(long long)(k + 1 + i) * n + k + 1 + j] -= v[i] * p[j] + p[i] * v[j];
+    for (int i = tid >> 5; i < L; i += nt >> 5) {
+      const double vi = sv[i], pi = sp[i];
+      double* row = Am + (long long)(k + 1 + i) * n + k + 1;
+      for (int j = tid & 31; j < L; j += 32) row[j] -= vi * sp[j] + pi * sv[j];
     }
     __syncthreads();
   }
@@ -337,7 +365,28 @@ __global__ void spectrum_finish_kernel(const double* ev, int n, double* s_new, c
 
 inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+__global__ void gather_f32_k(const double* __restrict__ in, float* __restrict__ out,
+                             long long nrows, int ncols, long long stride, IdxMap rmap,
+                             IdxMap cmap) {
+  const long long tot = nrows * ncols;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / ncols, c = e % ncols;
+    out[r * stride + c] = static_cast<float>(in[map_off(rmap, r) + map_off(cmap, c)]);
+  }
+}
+
 }  // namespace
+
+cudaError_t gather_f32(const double* in, float* out, long long nrows, int ncols, long long stride,
+                       IdxMap rmap, IdxMap cmap, cudaStream_t s) {
+  const long long tot = nrows * ncols;
+  if (tot <= 0) return cudaSuccess;
+  gather_f32_k<<<(unsigned)std::min<long long>((tot + 255) / 256, 8192), 256, 0, s>>>(
+      in, out, nrows, ncols, stride, rmap, cmap);
+  note_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t c4v_symmetrize(int d, int D, const double* X, double* Y, cudaStream_t s) {
   long long n = (long long)d * D * D * D * D;
@@ -410,7 +459,14 @@ cudaError_t corner_spectrum(const double* C, int chi, double* work, double* s_ne
                             const double* s_old, int chi_old, double* delta, int* err,
                             cudaStream_t s) {
   if (chi < 1 || chi > 1024) return cudaErrorInvalidValue;
-  spectrum_kernel<<<1, 1024, 0, s>>>(C, chi, work, s_new, s_old, chi_old, delta, err);
+  const size_t smem = (chi <= kSmemSpecMax) ? sizeof(double) * chi * chi : 0;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(spectrum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(double) * kSmemSpecMax * kSmemSpecMax));
+    attr = true;
+  }
+  spectrum_kernel<<<1, 1024, smem, s>>>(C, chi, work, s_new, s_old, chi_old, delta, err);
   note_launch();
   double* ev = work + (size_t)chi * chi + 5 * (size_t)chi + 8;
   bisect_kernel<<<(chi + 3) / 4, 128, 0, s>>>(work, chi, ev);

@@ -185,6 +185,42 @@ __global__ void set_identity_cols_kernel(double* Q, int m, int n) {
 
 }  // namespace
 
+// Factor panel p (columns j0..j0+nbj) of w.W in place: FP64 Householder
+// reflectors into w.V, tau and the Gram-based T factor into w.Tf (stride NB).
+// gram_tc: compute G = V^T V with the caller's contraction (nullptr = FP64).
+cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t s, double** G_out,
+                          double** tau_out) {
+  const int mr = m - j0;
+  const int P = qr_panel_grid(mr);
+  int rpc = (mr + P - 1) / P;
+  double* W = w.W; double* V = w.V; double* part = w.part;
+  double* Gp = w.part + 2 * (size_t)PMAX * NB + 2 * NB;
+  double* taup = Gp + NB * NB;
+  GridBar* bar = w.bar; int* err = w.err;
+  int m_ = m, j0_ = j0, nb_ = nbj;
+  void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc};
+  cudaError_t e =
+      cudaLaunchCooperativeKernel((const void*)qr_panel_kernel, dim3(P), dim3(PT), args, 0, s);
+  if (e != cudaSuccess) return e;
+  note_launch();
+  *G_out = Gp;
+  *tau_out = taup;
+  return cudaSuccess;
+}
+
+cudaError_t qr_tfactor(const double* G, const double* tau, double* Tp, int nbj, cudaStream_t s) {
+  qr_tfactor_kernel<<<1, NB, 0, s>>>(G, tau, Tp, nbj);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t qr_extract_r(const double* W, double* R, int m, int n, cudaStream_t s) {
+  long long tot = (long long)n * n;
+  extract_r_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(W, R, m, n);
+  note_launch();
+  return cudaGetLastError();
+}
+
 int qr_panel_grid(int mrows) {
   static int nsm = 0;
   if (nsm == 0) {

@@ -155,6 +155,21 @@ QrWork qr_carve(void* base, int m, int n);
 int qr_panel_grid(int m);
 cudaError_t householder_qr_f64(int m, int n, const double* M, double* Q, double* R_rowmajor,
                                const QrWork& w, cudaStream_t s);
+constexpr int kQrPanel = 32;   // panel width of the blocked QR
+cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t s, double** G_out,
+                          double** tau_out);
+cudaError_t qr_tfactor(const double* G, const double* tau, double* Tp, int nbj, cudaStream_t s);
+cudaError_t qr_extract_r(const double* W, double* R, int m, int n, cudaStream_t s);
+// Split-precision variant (tensor-core compact-WY products); f32 holds
+// qr_split_floats(m, n) floats, part the tensor-core split-K partial sums.
+size_t qr_split_floats(int m, int n);
+cudaError_t householder_qr_split(int m, int n, const double* M, double* Q, double* R,
+                                 const QrWork& w, float* f32, float* part, long long part_elems,
+                                 cudaStream_t s);
+
+// out[r * stride + c] = (float) in[map(rmap, r) + map(cmap, c)], 0 <= c < ncols
+cudaError_t gather_f32(const double* in, float* out, long long nrows, int ncols, long long stride,
+                       IdxMap rmap, IdxMap cmap, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Elementwise / reduction kernels.

@@ -24,29 +24,6 @@ namespace {
 
 inline long long pad4(long long x) { return (x + 3) & ~3ll; }
 
-// out[r * stride + c] = (float) in[map(rmap, r) + map(cmap, c)] for c < ncols,
-// 0 for ncols <= c < stride.
-__global__ void gather_f32_k(const double* __restrict__ in, float* __restrict__ out,
-                             long long nrows, int ncols, long long stride, IdxMap rmap,
-                             IdxMap cmap) {
-  const long long tot = nrows * stride;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long r = e / stride, c = e % stride;
-    out[e] = (c < ncols) ? static_cast<float>(in[map_off(rmap, r) + map_off(cmap, c)]) : 0.0f;
-  }
-}
-
-cudaError_t gather_f32(const double* in, float* out, long long nrows, int ncols, long long stride,
-                       IdxMap rmap, IdxMap cmap, cudaStream_t s) {
-  const long long tot = nrows * stride;
-  if (tot <= 0) return cudaSuccess;
-  gather_f32_k<<<(unsigned)std::min<long long>((tot + 255) / 256, 8192), 256, 0, s>>>(
-      in, out, nrows, ncols, stride, rmap, cmap);
-  note_launch();
-  return cudaGetLastError();
-}
-
 TcOperand op(const float* p, long long rows, long long K, long long stride, int batch = 1,
              long long bstride = 0) {
   return TcOperand{p, rows, K, stride, batch, bstride};
@@ -113,7 +90,8 @@ cudaError_t qr_step_split(qrctm_ctx* c) {
   }
   {
     PhaseScope ps(c, QRCTM_PH_QR);
-    if ((e = householder_qr_f64((int)m, ch, c->Mcm, c->Q, c->R, c->qrw, st)) != cudaSuccess)
+    if ((e = householder_qr_split((int)m, ch, c->Mcm, c->Q, c->R, c->qrw, c->qr32, c->tc_part,
+                                  c->tc_part_elems, st)) != cudaSuccess)
       return e;
     // Qt32[(mu,u)][a] = Q[(a,u),mu];  Qc32[n][(b,d)] = Q[(b,d),n]
     if ((e = gather_f32(c->Q, Qt32, m, ch, chp, im2(D2, 1, m), im1(D2), st)) != cudaSuccess)
