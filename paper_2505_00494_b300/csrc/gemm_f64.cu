@@ -115,13 +115,22 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(Gemm g, int splits, long l
   }
 }
 
-// C(m,n) = alpha * sum_z part[z][m][n] + beta * C(m,n), summed in z order.
+// C(m,n) = alpha * sum_z part[z][m][n] + beta * C(m,n); a fixed summation
+// order (four interleaved partial sums) keeps the result deterministic.
 __global__ void splitk_reduce_kernel(Gemm g, int splits) {
   const long long MN = g.M * g.N;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < MN;
        e += (long long)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int z = 0; z < splits; ++z) s += g.part[(long long)z * MN + e];
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int z = 0;
+    for (; z + 4 <= splits; z += 4) {
+      s0 += g.part[(long long)z * MN + e];
+      s1 += g.part[(long long)(z + 1) * MN + e];
+      s2 += g.part[(long long)(z + 2) * MN + e];
+      s3 += g.part[(long long)(z + 3) * MN + e];
+    }
+    for (; z < splits; ++z) s0 += g.part[(long long)z * MN + e];
+    const double s = (s0 + s1) + (s2 + s3);
     const long long m = e / g.N, n = e % g.N;
     double* p = g.C + map_off(g.c_m, m) + map_off(g.c_n, n);
     double v = g.alpha * s;

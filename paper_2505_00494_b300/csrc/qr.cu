@@ -25,6 +25,28 @@ constexpr int PMAX = 1024;   // upper bound on panel CTAs (scratch sizing)
 
 __host__ __device__ inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
+// FP64 reciprocal and square root by Newton's iteration from an FP32 seed
+// (quadratic convergence: 24 -> 48 -> 96 bits), avoiding the long-latency
+// IEEE double-precision divide and square-root sequences on the scalar path.
+__device__ __forceinline__ double rcp_nr(double x) {
+  const double ax = fabs(x);
+  if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;   // outside the FP32 seed range
+  double r = static_cast<double>(1.0f / static_cast<float>(x));
+  r = fma(r, fma(-x, r, 1.0), r);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return r;
+}
+__device__ __forceinline__ double sqrt_nr(double a) {
+  if (!(a > 1e-30 && a < 1e30)) return sqrt(a);   // zero, NaN or outside the seed range
+  // y ~ 1/sqrt(a); two Newton steps y <- y (3 - a y^2) / 2, then s = a y and
+  // one correction s <- s + y (a - s^2) / 2
+  double y = static_cast<double>(rsqrtf(static_cast<float>(a)));
+  y = y * fma(-0.5 * a * y, y, 1.5);
+  y = y * fma(-0.5 * a * y, y, 1.5);
+  double sq = a * y;
+  return fma(0.5 * y, fma(-sq, sq, a), sq);
+}
+
 __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
                                                       double* __restrict__ V,
                                                       double* __restrict__ tau_out,
@@ -57,10 +79,10 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     red[wrp][lane] = acc;
     __syncthreads();
     if (threadIdx.x < NB) {
-      double s = 0.0;
-#pragma unroll
-      for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
-      psum[((size_t)buf * P + b) * NB + threadIdx.x] = s;
+      const int t = threadIdx.x;
+      psum[((size_t)buf * P + b) * NB + t] =
+          ((red[0][t] + red[1][t]) + (red[2][t] + red[3][t])) +
+          ((red[4][t] + red[5][t]) + (red[6][t] + red[7][t]));
     }
     // the owner of row c publishes row c (x_0 and the y_0 of the other columns)
     if (c >= r_begin && c < r_end && (int)threadIdx.x <= nrem)
@@ -78,31 +100,38 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     // cross-CTA reduction of the partial sums: lane = column slot, the 8 warps
     // take every 8th CTA, then a fixed-order sum over the warps
     {
-      double s = 0.0;
-      if (lane <= nrem)
-        for (int q = wrp; q < P; q += 8) s += psum[((size_t)buf * P + q) * NB + lane];
-      red[wrp][lane] = s;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      if (lane <= nrem) {
+        int q = wrp;
+        for (; q + 24 < P; q += 32) {
+          s0 += psum[((size_t)buf * P + q) * NB + lane];
+          s1 += psum[((size_t)buf * P + q + 8) * NB + lane];
+          s2 += psum[((size_t)buf * P + q + 16) * NB + lane];
+          s3 += psum[((size_t)buf * P + q + 24) * NB + lane];
+        }
+        for (; q < P; q += 8) s0 += psum[((size_t)buf * P + q) * NB + lane];
+      }
+      red[wrp][lane] = (s0 + s1) + (s2 + s3);
     }
     __syncthreads();
     if ((int)threadIdx.x <= nrem) {
-      double s = 0.0;
-#pragma unroll
-      for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
-      tot[threadIdx.x] = s;
+      const int t = threadIdx.x;
+      tot[t] = ((red[0][t] + red[1][t]) + (red[2][t] + red[3][t])) +
+               ((red[4][t] + red[5][t]) + (red[6][t] + red[7][t]));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       const double x0 = rowb[buf * NB];
       const double sigma = tot[0];
-      const double mu = sqrt(x0 * x0 + sigma);
+      const double mu = sqrt_nr(x0 * x0 + sigma);
       double tau, inv_v0;
       if (sigma == 0.0) {
         tau = (x0 < 0.0) ? 2.0 : 0.0;      // v = e_1
         inv_v0 = 0.0;
       } else {
-        const double v0 = (x0 <= 0.0) ? (x0 - mu) : (-sigma / (x0 + mu));
-        tau = 2.0 * v0 * v0 / (sigma + v0 * v0);
-        inv_v0 = 1.0 / v0;
+        const double v0 = (x0 <= 0.0) ? (x0 - mu) : (-sigma * rcp_nr(x0 + mu));
+        tau = 2.0 * v0 * v0 * rcp_nr(sigma + v0 * v0);
+        inv_v0 = rcp_nr(v0);
       }
       if (!(mu == mu) || isinf(mu)) atomicOr(err, ERRF_NUMERIC);
       sc[0] = tau; sc[1] = inv_v0; sc[2] = mu;
@@ -156,8 +185,16 @@ __global__ void qr_tfactor_kernel(const double* __restrict__ G, const double* __
     double val = 0.0;
     const int i = threadIdx.x;
     if (i < j) {
-      for (int l = i; l < j; ++l) val = fma(Ts[i][l], Gs[l][j], val);
-      val *= -tau[j];
+      double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+      int l = i;
+      for (; l + 4 <= j; l += 4) {
+        v0 = fma(Ts[i][l], Gs[l][j], v0);
+        v1 = fma(Ts[i][l + 1], Gs[l + 1][j], v1);
+        v2 = fma(Ts[i][l + 2], Gs[l + 2][j], v2);
+        v3 = fma(Ts[i][l + 3], Gs[l + 3][j], v3);
+      }
+      for (; l < j; ++l) v0 = fma(Ts[i][l], Gs[l][j], v0);
+      val = -tau[j] * ((v0 + v1) + (v2 + v3));
     }
     __syncthreads();
     if (i < j) Ts[i][j] = val;

@@ -349,16 +349,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
-// out(b,m,n) = alpha * sum_z part[b][z][m][n] (in z order, FP64) + beta * out
+// out(b,m,n) = alpha * sum_z part[b][z][m][n] + beta * out: FP64 sums in a
+// fixed order (four interleaved partial sums, then their pairwise sum)
 __global__ void tc_splitk_reduce(const TcArgs a, int batch) {
   const long long MN = a.M * a.N;
   const long long tot = MN * batch;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
     const long long b = e / MN, r = e % MN, m = r / a.N, n = r % a.N;
-    double acc = 0.0;
     const float* p = a.part + b * a.ksplit * MN + r;
-    for (int z = 0; z < a.ksplit; ++z) acc += static_cast<double>(p[(long long)z * MN]);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int z = 0;
+    for (; z + 4 <= a.ksplit; z += 4) {
+      a0 += static_cast<double>(p[(long long)z * MN]);
+      a1 += static_cast<double>(p[(long long)(z + 1) * MN]);
+      a2 += static_cast<double>(p[(long long)(z + 2) * MN]);
+      a3 += static_cast<double>(p[(long long)(z + 3) * MN]);
+    }
+    for (; z < a.ksplit; ++z) a0 += static_cast<double>(p[(long long)z * MN]);
+    const double acc = (a0 + a1) + (a2 + a3);
     const long long off = map_off(a.c_b, b) + map_off(a.c_m, m) + map_off(a.c_n, n);
     double v = a.alpha * acc;
     if (a.c_fp64) {
