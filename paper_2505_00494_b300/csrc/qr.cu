@@ -22,6 +22,7 @@ namespace {
 constexpr int NB = 32;       // panel width (one warp lane per panel column)
 constexpr int PT = 256;      // threads per panel CTA (8 row lanes x 32 columns)
 constexpr int PMAX = 1024;   // upper bound on panel CTAs (scratch sizing)
+constexpr size_t kPanelTileMax = 160 * 1024;   // shared-memory panel tile limit
 
 __host__ __device__ inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -47,6 +48,13 @@ __device__ __forceinline__ double sqrt_nr(double a) {
   return fma(0.5 * y, fma(-sq, sq, a), sq);
 }
 
+// Panel factorisation.  With TILE, each CTA keeps its block of panel rows
+// (rows_per_cta x nb doubles) in shared memory for the whole factorisation, so
+// that a column step touches global memory only for the cross-CTA partial
+// sums and the published pivot row; the tile is written back (R entries,
+// reflectors) at the end.  Without TILE (very tall panels) the same steps
+// run on W in global memory.
+template <bool TILE>
 __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
                                                       double* __restrict__ V,
                                                       double* __restrict__ tau_out,
@@ -57,6 +65,7 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
   const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;   // wrp = row lane (0..7)
   const long long r_begin = (long long)j0 + (long long)b * rows_per_cta;
   const long long r_end = std::min<long long>(m, r_begin + rows_per_cta);
+  const int rows = (int)std::max<long long>(0, r_end - r_begin);
   // scratch: psum[2][P][NB], rowb[2][NB]
   double* psum = part;
   double* rowb = part + 2 * (size_t)P * NB;
@@ -64,6 +73,19 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
   __shared__ double tot[NB];
   __shared__ double sc[4];
   __shared__ double tau_s[NB];
+  extern __shared__ double tile[];                 // [rows][NB + 1]
+  // element (global row i, panel column jc)
+  auto at = [&](long long i, int jc) -> double& {
+    if (TILE) return tile[(i - r_begin) * (NB + 1) + jc];
+    return W[((long long)j0 + jc) * m + i];
+  };
+  if (TILE) {
+    for (int e = threadIdx.x; e < rows * nb; e += PT) {
+      const int r = e % rows, jc = e / rows;
+      tile[r * (NB + 1) + jc] = W[((long long)j0 + jc) * m + r_begin + r];
+    }
+    __syncthreads();
+  }
 
   // partial sums for column j (slot 0: sum x_i^2 over i > c; slot t: sum x_i y_{c+t,i})
   auto partials = [&](int j, int buf) {
@@ -71,11 +93,8 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     const int nrem = nb - j - 1;
     double acc = 0.0;
     const long long i0 = std::max<long long>(r_begin, c + 1);
-    if (lane <= nrem) {
-      const double* xc = W + c * m;
-      const double* yc = W + (c + lane) * m;
-      for (long long i = i0 + wrp; i < r_end; i += 8) acc = fma(xc[i], yc[i], acc);
-    }
+    if (lane <= nrem)
+      for (long long i = i0 + wrp; i < r_end; i += 8) acc = fma(at(i, j), at(i, j + lane), acc);
     red[wrp][lane] = acc;
     __syncthreads();
     if (threadIdx.x < NB) {
@@ -86,7 +105,7 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     }
     // the owner of row c publishes row c (x_0 and the y_0 of the other columns)
     if (c >= r_begin && c < r_end && (int)threadIdx.x <= nrem)
-      rowb[buf * NB + threadIdx.x] = W[(c + threadIdx.x) * m + c];
+      rowb[buf * NB + threadIdx.x] = at(c, j + threadIdx.x);
     __syncthreads();
   };
 
@@ -144,21 +163,17 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     if (lane >= 1 && lane <= nrem) coef = tau * (rowb[buf * NB + lane] + tot[lane] * inv_v0);
     {
       const long long i0 = std::max<long long>(r_begin, c + 1);
-      double* xc = W + c * m;
       for (long long i = i0 + wrp; i < r_end; i += 8) {
-        const double v = xc[i] * inv_v0;
-        if (lane >= 1 && lane <= nrem) W[(c + lane) * m + i] -= coef * v;
+        const double v = at(i, j) * inv_v0;
+        if (lane >= 1 && lane <= nrem) at(i, j + lane) -= coef * v;
         __syncwarp();
-        if (lane == 0) { xc[i] = v; V[c * m + i] = v; }
+        if (lane == 0) at(i, j) = v;
         __syncwarp();
       }
-      // explicit reflector column: zeros above c inside the panel rows, 1 at c
-      for (long long i = r_begin + threadIdx.x; i < std::min<long long>(r_end, c + 1); i += PT)
-        V[c * m + i] = (i == c) ? 1.0 : 0.0;
       // row c itself: the R entries
       if (c >= r_begin && c < r_end) {
-        if (lane == 0 && wrp == 0) W[c * m + c] = mu;
-        if (wrp == 0 && lane >= 1 && lane <= nrem) W[(c + lane) * m + c] -= coef;
+        if (lane == 0 && wrp == 0) at(c, j) = mu;
+        if (wrp == 0 && lane >= 1 && lane <= nrem) at(c, j + lane) -= coef;
       }
     }
     __syncthreads();
@@ -166,6 +181,15 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     if (!grid_barrier(bar, P, err)) return;
   }
 
+  // write back: panel rows of W (R above/on the diagonal, reflectors below)
+  // and the explicit reflectors V (zero above the unit diagonal)
+  for (int e = threadIdx.x; e < rows * nb; e += PT) {
+    const int r = e % rows, jc = e / rows;
+    const long long i = r_begin + r, c = (long long)j0 + jc;
+    const double x = at(i, jc);
+    if (TILE) W[c * m + i] = x;
+    V[c * m + i] = (i < c) ? 0.0 : (i == c ? 1.0 : x);
+  }
   // tau of the panel columns for the compact-WY factor (built after the kernel)
   if (b == 0 && threadIdx.x < (unsigned)nb) tau_out[threadIdx.x] = tau_s[threadIdx.x];
 }
@@ -236,8 +260,21 @@ cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t 
   GridBar* bar = w.bar; int* err = w.err;
   int m_ = m, j0_ = j0, nb_ = nbj;
   void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc};
-  cudaError_t e =
-      cudaLaunchCooperativeKernel((const void*)qr_panel_kernel, dim3(P), dim3(PT), args, 0, s);
+  const size_t tile = sizeof(double) * (size_t)rpc * (NB + 1);
+  cudaError_t e;
+  if (tile <= kPanelTileMax) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(qr_panel_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kPanelTileMax);
+      attr = true;
+    }
+    e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<true>, dim3(P), dim3(PT), args,
+                                    tile, s);
+  } else {
+    e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<false>, dim3(P), dim3(PT), args,
+                                    0, s);
+  }
   if (e != cudaSuccess) return e;
   note_launch();
   *G_out = Gp;
@@ -322,19 +359,9 @@ cudaError_t householder_qr_f64(int m, int n, const double* M, double* Q, double*
     const int j0 = p * NB;
     const int nbj = std::min(NB, n - j0);
     const int mr = m - j0;
-    const int P = qr_panel_grid(mr);
-    int rpc = (mr + P - 1) / P;
     double* Tp = w.Tf + (size_t)p * NB * NB;
-    double* W = w.W; double* V = w.V; double* part = w.part;
-    // after the panel partial sums: G (NB x NB) and tau (NB) of this panel
-    double* Gp = w.part + 2 * (size_t)PMAX * NB + 2 * NB;
-    double* taup = Gp + NB * NB;
-    GridBar* bar = w.bar; int* err = w.err;
-    int m_ = m, j0_ = j0, nb_ = nbj;
-    void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc};
-    e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel, dim3(P), dim3(PT), args, 0, s);
-    if (e != cudaSuccess) return e;
-    note_launch();
+    double *Gp, *taup;
+    if ((e = qr_panel_step(m, j0, nbj, w, s, &Gp, &taup)) != cudaSuccess) return e;
     {
       // G = V_p^T V_p over the panel rows (reflectors are zero above their
       // unit diagonal), then T from G and tau
