@@ -142,8 +142,12 @@ qrctm_status qrctm_energy(qrctm_ctx* ctx, const qrctm_model* model, double* e_ou
  * mode IMPLICIT: adjoint fixed point of two QR-CTMRG steps at the current
  * environment (the map's fixed point up to the sign gauge it alternates);
  * mode UNROLL: backpropagation through k_unroll steps started from the
- * current (detached) environment.  grad: device, d*D^4 doubles, the
- * C4v-projected gradient.  e_out: host.  Needs with_grad. */
+ * current (detached) environment (1 <= k_unroll <= 32).  grad: device,
+ * d*D^4 doubles, the C4v-projected gradient.  e_out: host, the energy at the
+ * current environment (implicit) or after the k steps (unroll).  Needs
+ * with_grad (and with_nnn when J2 != 0), d = 2, D >= 2.  All reverse passes
+ * run in FP64; the adjoint iteration stops when its update falls below
+ * grad_tol relative to dE/d(env), or after grad_max_iter iterations. */
 qrctm_status qrctm_energy_grad(qrctm_ctx* ctx, const qrctm_model* model, int mode, int k_unroll,
                                double* grad, double* e_out);
 
@@ -162,6 +166,10 @@ qrctm_status qrctm_phase_times(qrctm_ctx* ctx, double* ms_out, long long* count_
 
 /* Number of kernels this library has launched in this process so far. */
 unsigned long long qrctm_kernel_launches(void);
+
+/* Adjoint fixed-point iterations (implicit mode) or unrolled steps used by
+ * the last qrctm_energy_grad call. */
+int qrctm_grad_iterations(const qrctm_ctx* ctx);
 
 /* Steps run since qrctm_init_env. */
 int qrctm_iterations(const qrctm_ctx* ctx);

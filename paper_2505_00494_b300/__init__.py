@@ -72,6 +72,7 @@ _sig = {
                           ctypes.c_int),
     "qrctm_get_env": ([_vp, _vp, _vp, _dp], ctypes.c_int),
     "qrctm_iterations": ([_vp], ctypes.c_int),
+    "qrctm_grad_iterations": ([_vp], ctypes.c_int),
     "qrctm_set_profiling": ([_vp, ctypes.c_int], ctypes.c_int),
     "qrctm_phase_times": ([_vp, _dp, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
     "qrctm_kernel_launches": ([], ctypes.c_ulonglong),
@@ -248,6 +249,10 @@ class QRCTM:
         cnt = (ctypes.c_longlong * n)()
         self._check(_load().qrctm_phase_times(self.h, ms, cnt), "qrctm_phase_times")
         return {PHASES[i]: (ms[i], cnt[i]) for i in range(n)}
+
+    @property
+    def grad_iterations(self):
+        return _load().qrctm_grad_iterations(self.h)
 
     @property
     def iterations(self):

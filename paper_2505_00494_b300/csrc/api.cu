@@ -12,6 +12,7 @@
 
 #include "ctx.cuh"
 #include "tc_gemm.cuh"
+#include "grad.cuh"
 
 using namespace qrctm;
 
@@ -163,8 +164,6 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
   if (carve) c->split_layers = split;
   return off;
 }
-
-size_t grad_bytes(int, int, int) { return 256; }
 
 PhaseScope::PhaseScope(qrctm_ctx* c_, int ph_) : c(c_), ph(ph_), a(nullptr) {
   if (!c->prof) return;
@@ -429,10 +428,31 @@ qrctm_status qrctm_energy(qrctm_ctx* c, const qrctm_model* model, double* e_out)
   return QRCTM_OK;
 }
 
-qrctm_status qrctm_energy_grad(qrctm_ctx* c, const qrctm_model*, int, int, double*, double*) {
-  if (!c) return QRCTM_ERR_INVALID_ARG;
-  return set_err(c, QRCTM_ERR_INVALID_ARG, "energy gradient not available in this build");
+qrctm_status qrctm_energy_grad(qrctm_ctx* c, const qrctm_model* model, int mode, int k_unroll,
+                               double* grad, double* e_out) {
+  if (!c || !model || !grad || !e_out) return QRCTM_ERR_INVALID_ARG;
+  if (!c->have_env) return set_err(c, QRCTM_ERR_STATE, "qrctm_init_env not called");
+  if (c->d != 2) return set_err(c, QRCTM_ERR_INVALID_ARG, "the spin-1/2 energy needs d = 2");
+  if (!c->G) return set_err(c, QRCTM_ERR_INVALID_ARG, "qrctm_energy_grad needs with_grad = 1");
+  if (model->J2 != 0.0 && c->E3 == nullptr)
+    return set_err(c, QRCTM_ERR_INVALID_ARG, "J2 != 0 needs with_nnn = 1");
+  if (mode != QRCTM_GRAD_IMPLICIT && mode != QRCTM_GRAD_UNROLL)
+    return set_err(c, QRCTM_ERR_INVALID_ARG, "unknown gradient mode");
+  if (mode == QRCTM_GRAD_UNROLL && (k_unroll < 1 || k_unroll > kGradMaxUnroll))
+    return set_err(c, QRCTM_ERR_INVALID_ARG, "k_unroll must be in 1..32");
+  if (c->D < 2) return set_err(c, QRCTM_ERR_INVALID_ARG, "the gradient needs D >= 2");
+  cudaError_t e;
+  int iters = 0;
+  {
+    PhaseScope ps(c, QRCTM_PH_GRAD);
+    e = energy_grad_run(c, model->J1, model->J2, mode, k_unroll, grad, e_out, &iters);
+  }
+  c->grad_iters = iters;
+  if (e != cudaSuccess) return cuda_fail(c, e, "energy gradient");
+  return sync_check(c, "energy gradient");
 }
+
+int qrctm_grad_iterations(const qrctm_ctx* ctx) { return ctx ? ctx->grad_iters : 0; }
 
 qrctm_status qrctm_get_env(qrctm_ctx* c, double* C, double* T, double* spectrum_host) {
   if (!c) return QRCTM_ERR_INVALID_ARG;

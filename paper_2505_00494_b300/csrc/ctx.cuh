@@ -41,6 +41,7 @@ struct qrctm_ctx {
   qrctm::QrWork qrw;
   int* err;
   int iters;
+  int grad_iters;
   double last_delta;
   bool have_env;
   bool spec_valid;
