@@ -200,12 +200,16 @@ def main():
     ap.add_argument("--steps", type=int, default=0)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "split"])
+    ap.add_argument("--precision", default="split", choices=["fp64", "split"])
     ap.add_argument("--workload", default="d2_D6_chi144", choices=sorted(qi.WORKLOADS))
     ap.add_argument("--check-every", type=int, default=5)
     ap.add_argument("--cpu-sample", type=int, default=3, help="oracle steps in cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip time-to-convergence, dE vs FP64 and the energy gradient")
+    ap.add_argument("--conv-tol", type=float, default=0.0,
+                    help="spectrum tolerance for time-to-converged (default 1e-7 split, 1e-10 fp64)")
     args = ap.parse_args()
     w = qi.WORKLOADS[args.workload]
     if args.steps <= 0:
@@ -328,6 +332,46 @@ def main():
     h2d = (hA.numel() + hC.numel() + hT.numel()) * 8
     d2h = (oC.numel() + oT.numel()) * 8 + 8
 
+    # time to a converged environment from the bulk boundary (warm-up included),
+    # the energy error of the split path against the FP64 path from that
+    # environment, and the energy-gradient time (J1-J2 at J2/J1 = 0.5)
+    extras = {}
+    if not args.no_extras:
+        tol = args.conv_tol or (1e-7 if args.precision == "split" else 1e-10)
+        cctx = q.QRCTM(d, D, chi, precision=args.precision, check_every=ce)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cctx.init_env(A)
+        its, dl = cctx.run_to_convergence(tol=tol, max_iter=2000)
+        torch.cuda.synchronize()
+        extras["time_to_converged_s"] = time.perf_counter() - t0
+        extras["converged_iterations"] = its
+        extras["converged_delta"] = dl
+        extras["converged_tol"] = tol
+        Cc, Tc, _ = cctx.get_env(spectrum=False)
+        e_split = cctx.energy(1.0, 0.0)
+        cctx.close()
+        fctx = q.QRCTM(d, D, chi, precision="fp64", check_every=ce, with_nnn=True,
+                       with_grad=True, grad_tol=1e-10, grad_max_iter=300)
+        fctx.init_env(A, Cc, Tc)
+        fits, fdl = fctx.run_to_convergence(tol=1e-10, max_iter=400)
+        if fits % 2:
+            fctx.step(1, want_delta=False)
+        e_fp64 = fctx.energy(1.0, 0.0)
+        extras["E_per_site_J2_0"] = e_fp64
+        extras["dE_split_vs_fp64"] = (e_split - e_fp64) if args.precision == "split" else 0.0
+        extras["fp64_refine_iterations"] = fits
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Eg, g = fctx.energy_grad(1.0, 0.5, mode="implicit")
+        torch.cuda.synchronize()
+        extras["energy_grad_ms"] = 1e3 * (time.perf_counter() - t0)
+        extras["energy_grad_adjoint_iterations"] = fctx.grad_iterations
+        extras["E_per_site_J2_0.5"] = Eg
+        extras["grad_norm"] = float(g.norm().item())
+        extras["grad_dot_A"] = float((g * A).sum().item())
+        fctx.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         times, layers = oracle_sample(w, args.cpu_sample)
@@ -361,7 +405,8 @@ def main():
                     "d2h_bytes_per_step": int(d2h)},
             "energy_per_site": {"J2_0": E, "J2_0.5": E12, "energy_ms": energy_ms,
                                 "energy_j2_ms": energy_j2_ms},
-            "energy_grad_ms": None,
+            "energy_grad_ms": extras.get("energy_grad_ms"),
+            "convergence": extras,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
