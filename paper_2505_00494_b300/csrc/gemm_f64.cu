@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(Gemm g, int splits, long l
       }
     }
   }
+  }
 }
 
 // C(m,n) = alpha * sum_z part[z][m][n] + beta * C(m,n); a fixed summation
@@ -148,7 +149,8 @@ unsigned long long launches_so_far() { return __atomic_load_n(&g_launches, __ATO
 cudaError_t gemm_f64(const Gemm& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
   long long gx = (g.M + BM - 1) / BM, gy = (g.N + BN - 1) / BN;
-  if (gx > 0x7fffffffll || gy > 65535) return cudaErrorInvalidValue;
+  if (gx > 0x7fffffffll) return cudaErrorInvalidValue;
+  if (gy > 65535) gy = 65535;   // the kernel loops over the remaining N tiles
   static int nsm = 0;
   if (nsm == 0) {
     int dev = 0;
