@@ -24,8 +24,9 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(Gemm g, int splits, long l
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const long long m0 = (long long)blockIdx.x * BM;
-  const long long n0 = (long long)blockIdx.y * BN;
-
+  const long long ntiles_n = (g.N + BN - 1) / BN;
+  for (long long ny = blockIdx.y; ny < ntiles_n; ny += gridDim.y) {
+  const long long n0 = ny * BN;
   const long long kbeg = (splits > 1) ? (long long)blockIdx.z * kc : 0;
   const long long kend = (splits > 1) ? min(g.K, kbeg + kc) : g.K;
   for (long long b = (splits > 1) ? 0 : blockIdx.z; b < g.batch;
