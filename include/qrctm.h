@@ -61,8 +61,8 @@ typedef struct {
   int check_every;    /* convergence test every this many steps (>= 1)          */
   double tol;         /* default convergence tolerance on the corner spectrum   */
   int max_iter;       /* default iteration cap                                  */
-  int grad_max_iter;  /* cap on adjoint fixed-point iterations (0 = 200)        */
-  double grad_tol;    /* adjoint fixed-point tolerance (0 = 1e-12)              */
+  int grad_max_iter;  /* cap on applications of J^T in the adjoint solve (0 = 200) */
+  double grad_tol;    /* relative residual target of the adjoint solve (0 = 1e-12) */
   int with_nnn;       /* 1: reserve workspace for the J2 (2x2 patch) energy term */
   int with_grad;      /* 1: reserve workspace for qrctm_energy_grad              */
   void* stream;       /* cudaStream_t; NULL = legacy default stream             */
@@ -146,8 +146,10 @@ qrctm_status qrctm_energy(qrctm_ctx* ctx, const qrctm_model* model, double* e_ou
  * d*D^4 doubles, the C4v-projected gradient.  e_out: host, the energy at the
  * current environment (implicit) or after the k steps (unroll).  Needs
  * with_grad (and with_nnn when J2 != 0), d = 2, D >= 2.  All reverse passes
- * run in FP64; the adjoint iteration stops when its update falls below
- * grad_tol relative to dE/d(env), or after grad_max_iter iterations. */
+ * run in FP64.  Implicit mode solves (I - J^T) xbar = dE/d(env), J the
+ * Jacobian of the two steps, by restarted GMRES(40); it stops when the
+ * relative residual falls below grad_tol or after grad_max_iter
+ * applications of J^T (each one reverse pass through both steps). */
 qrctm_status qrctm_energy_grad(qrctm_ctx* ctx, const qrctm_model* model, int mode, int k_unroll,
                                double* grad, double* e_out);
 
@@ -167,9 +169,14 @@ qrctm_status qrctm_phase_times(qrctm_ctx* ctx, double* ms_out, long long* count_
 /* Number of kernels this library has launched in this process so far. */
 unsigned long long qrctm_kernel_launches(void);
 
-/* Adjoint fixed-point iterations (implicit mode) or unrolled steps used by
- * the last qrctm_energy_grad call. */
+/* Applications of J^T (implicit mode) or unrolled steps used by the last
+ * qrctm_energy_grad call. */
 int qrctm_grad_iterations(const qrctm_ctx* ctx);
+
+/* Relative residual ||b - (I - J^T) xbar|| / ||b|| of the last implicit
+ * adjoint solve, as estimated by GMRES (0 after an unrolled gradient).  This
+ * call has no counterpart in the paper; it reports solver convergence. */
+double qrctm_grad_residual(const qrctm_ctx* ctx);
 
 /* Steps run since qrctm_init_env. */
 int qrctm_iterations(const qrctm_ctx* ctx);

@@ -73,6 +73,7 @@ _sig = {
     "qrctm_get_env": ([_vp, _vp, _vp, _dp], ctypes.c_int),
     "qrctm_iterations": ([_vp], ctypes.c_int),
     "qrctm_grad_iterations": ([_vp], ctypes.c_int),
+    "qrctm_grad_residual": ([_vp], ctypes.c_double),
     "qrctm_set_profiling": ([_vp, ctypes.c_int], ctypes.c_int),
     "qrctm_phase_times": ([_vp, _dp, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
     "qrctm_kernel_launches": ([], ctypes.c_ulonglong),
@@ -253,6 +254,10 @@ class QRCTM:
     @property
     def grad_iterations(self):
         return _load().qrctm_grad_iterations(self.h)
+
+    @property
+    def grad_residual(self):
+        return _load().qrctm_grad_residual(self.h)
 
     @property
     def iterations(self):

@@ -1,0 +1,294 @@
+// Ket and bra layers of the on-site tensor absorbed into the edge, fused
+// (QR-CTMRG paragraph: T' is built with the ket and bra layers of a absorbed
+// one after the other, never forming the D^4 x D^4 double layer).
+//
+// For every (mu, b) pair -- mu the column of Q, b the third leg of T -- the
+// slice X1[mu, b] is a D^2 x D^2 matrix with rows (u_b, k_b) and columns
+// (u_k, k_k), and
+//   Z [(u_b,k_b),(s,d_k,j_k)] = sum_{u_k,k_k} X1[(u_b,k_b),(u_k,k_k)] A[s,u_k,k_k,d_k,j_k]
+//   X2[(d_k,j_k),(d_b,j_b)]   = sum_{s,u_b,k_b} Z[(u_b,k_b),(s,d_k,j_k)] A[s,u_b,k_b,d_b,j_b].
+// Both contractions of a group of slices run in one CTA with Z held in shared
+// memory, so the only HBM traffic is X1 in and X2 out.  Contractions this
+// small (K = D^2 and d D^2) and this memory-heavy stay on the FP32 cores;
+// accumulation is FP32, the precision class of the split path.
+//
+// Layouts (FP32):
+//   X1  [(mu,b)][(u_b,k_b)] x (u_k,k_k), row stride D2p
+//   Ak  [(s,d,r)] x (u,l), row stride D2p          (A[s,u,l,d,r])
+//   Ab  [(d,r)] x (s,u,l), row stride dD2p          (A[s,u,l,d,r])
+//   X2  [(mu,j_k,j_b)] x (b,d_k,d_b), row stride mp
+// Instantiated for d = 2 and D = 2, 4, 6, 8 (D^2 % 4 == 0, d D^2 % 8 == 0).
+#include "ctx.cuh"
+
+#include <algorithm>
+
+namespace qrctm {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait on an mbarrier phase
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  for (uint32_t i = 0; i < (1u << 22); ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// Slices X1[g0 .. g0+ng) (contiguous, ng*D2*D2p floats) into shared memory
+// by one bulk asynchronous copy completing on `bar`.
+__device__ __forceinline__ void issue_slices(const float* X1, float* dst, uint32_t bar,
+                                             long long g0, int ng, int D2, long long D2p) {
+  const uint32_t bytes = (uint32_t)((size_t)ng * D2 * D2p * sizeof(float));
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(X1 + g0 * D2 * D2p), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// One persistent CTA loops over batches of NG slices; the next batch is
+// copied in (bulk async copy, double buffer) while the current one is
+// contracted.  The buffer of a batch also stages its X2 block for the
+// coalesced write-out.  Shapes are template parameters, so every index
+// division is by a constant and the contraction loops unroll.
+template <int D, int d, int NG>
+struct AbsorbShape {
+  static constexpr int D2 = D * D, dD2 = d * D2;
+  static constexpr int R4 = D2 / 4, C8 = dD2 / 8;
+  static constexpr int tpg1 = R4 * C8, tpg2 = R4 * R4;
+  static constexpr int threads = NG * tpg2;
+  static constexpr size_t xbuf = (size_t)NG * D2 * D2;   // floats per slice buffer
+  static constexpr size_t smem_floats = 2 * xbuf + (size_t)NG * D2 * dD2 + 2 * (size_t)D2 * dD2;
+};
+
+template <int D, int d, int NG>
+__global__ void __launch_bounds__(AbsorbShape<D, d, NG>::threads)
+    absorb_fused_k(const float* __restrict__ X1, const float* __restrict__ Ak,
+                   const float* __restrict__ Ab, float* __restrict__ X2, int ch, long long Akp,
+                   long long Abp, long long mp, long long ngroups, int* err) {
+  using S = AbsorbShape<D, d, NG>;
+  constexpr int D2 = S::D2, dD2 = S::dD2, R4 = S::R4, C8 = S::C8, tpg1 = S::tpg1,
+                tpg2 = S::tpg2, nt = S::threads;
+  extern __shared__ __align__(128) float sm[];
+  __shared__ __align__(8) unsigned long long mbar[2];
+  __shared__ int s_ok;
+  const int tid = threadIdx.x;
+  float* Xb0 = sm;                                  // [NG][D2][D2]  slices (then X2 staging)
+  float* Xb1 = Xb0 + S::xbuf;
+  float* Zs = Xb1 + S::xbuf;                        // [NG][D2][dD2]
+  float* AkT = Zs + (size_t)NG * D2 * dD2;          // [D2][dD2]      AkT[k][c] = Ak[c][k]
+  float* AbT = AkT + (size_t)D2 * dD2;              // [dD2][D2]      AbT[k][c] = Ab[c][k]
+  const uint32_t bar0 = smem_u32(&mbar[0]), bar1 = smem_u32(&mbar[1]);
+  const long long stride = (long long)gridDim.x * NG;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const long long g0 = (long long)blockIdx.x * NG;
+    if (g0 < ngroups)
+      issue_slices(X1, Xb0, bar0, g0, (int)std::min<long long>(NG, ngroups - g0), D2, D2);
+  }
+  for (int e = tid; e < D2 * dD2; e += nt) {
+    const int c = e / D2, k = e % D2;
+    AkT[k * dD2 + c] = Ak[c * Akp + k];
+  }
+  for (int e = tid; e < D2 * dD2; e += nt) {
+    const int c = e / dD2, k = e % dD2;
+    AbT[k * D2 + c] = Ab[c * Abp + k];
+  }
+  // this thread's tiles (one of each contraction per slice group)
+  const int g1 = tid / tpg1, rem1 = tid % tpg1, rb1 = (rem1 / C8) * 4, cb1 = (rem1 % C8) * 8;
+  const int g2 = tid / tpg2, rem2 = tid % tpg2, rb2 = (rem2 / R4) * 4, cb2 = (rem2 % R4) * 4;
+  // use n of buffer it & 1 (n = it >> 1) completes phase n of its mbarrier
+  int it = 0;
+  bool next_issued = false;
+  if (tid == 0) s_ok = 1;
+  for (long long g0 = (long long)blockIdx.x * NG; g0 < ngroups; g0 += stride, ++it) {
+    const int ng = (int)std::min<long long>(NG, ngroups - g0);
+    float* Xb = (it & 1) ? Xb1 : Xb0;
+    const uint32_t bar = (it & 1) ? bar1 : bar0;
+    __syncthreads();   // the other buffer's previous batch is fully written out
+    const long long gn = g0 + stride;
+    next_issued = gn < ngroups;
+    if (tid == 0 && next_issued)
+      issue_slices(X1, (it & 1) ? Xb0 : Xb1, (it & 1) ? bar0 : bar1, gn,
+                   (int)std::min<long long>(NG, ngroups - gn), D2, D2);
+    if (!mbar_wait_bounded(bar, (uint32_t)((it >> 1) & 1))) {
+      atomicOr(err, ERRF_TIMEOUT);
+      s_ok = 0;
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    // ket: Zs[g][r][c] = sum_k X[g][r][k] AkT[k][c]   (4 x 8 tile, k in steps of 4)
+    for (int t = tid, g = g1; t < NG * tpg1; t += nt, g += nt / tpg1) {
+      if (g >= ng) break;
+      float acc[4][8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+      const float* xa = Xb + ((size_t)g * D2 + rb1) * D2;
+      const float* kb = AkT + cb1;
+#pragma unroll 3
+      for (int k = 0; k < D2; k += 4) {
+        float av[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float4 a = *reinterpret_cast<const float4*>(xa + i * D2 + k);
+          av[i][0] = a.x; av[i][1] = a.y; av[i][2] = a.z; av[i][3] = a.w;
+        }
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const float4 b0 = *reinterpret_cast<const float4*>(kb + (k + kk) * dD2);
+          const float4 b1 = *reinterpret_cast<const float4*>(kb + (k + kk) * dD2 + 4);
+          const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i][kk], bv[j], acc[i][j]);
+        }
+      }
+      float* zo = Zs + ((size_t)g * D2 + rb1) * dD2 + cb1;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        *reinterpret_cast<float4*>(zo + i * dD2) =
+            make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        *reinterpret_cast<float4*>(zo + i * dD2 + 4) =
+            make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+      }
+    }
+    __syncthreads();
+    // bra: out[g][r2][c2] = sum_{s,q} Zs[g][q][s*D2 + r2] AbT[s*D2 + q][c2]   (4 x 4 tile),
+    // staged as Xb[g][(j_k,j_b)][(d_k,d_b)]  (r2 = d_k*D + j_k, c2 = d_b*D + j_b)
+    if (g2 < ng) {
+      const int g = g2;
+      float acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll
+      for (int s = 0; s < d; ++s) {
+        const float* za = Zs + (size_t)g * D2 * dD2 + s * D2 + rb2;
+        const float* ba = AbT + (size_t)s * D2 * D2 + cb2;
+#pragma unroll 6
+        for (int q = 0; q < D2; ++q) {
+          const float4 a = *reinterpret_cast<const float4*>(za + q * dD2);
+          const float4 b = *reinterpret_cast<const float4*>(ba + q * D2);
+          const float av[4] = {a.x, a.y, a.z, a.w};
+          const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r2 = rb2 + i, dk = r2 / D, jk = r2 % D;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c2 = cb2 + j, db = c2 / D, jb = c2 % D;
+          Xb[((size_t)g * D2 + jk * D + jb) * D2 + dk * D + db] = acc[i][j];
+        }
+      }
+    }
+    __syncthreads();
+    // write out: consecutive slices of one mu are consecutive b, contiguous in X2
+    for (int e = tid; e < NG * D2 * D2; e += nt) {
+      const int dd = e % D2, g = (e / D2) % NG, jj = e / (D2 * NG);
+      if (g >= ng) continue;
+      const long long gg = g0 + g, mu = gg / ch, b = gg - mu * ch;
+      X2[(mu * D2 + jj) * mp + b * D2 + dd] = Xb[((size_t)g * D2 + jj) * D2 + dd];
+    }
+  }
+  // after an abandoned wait, let the copies still in flight land (bounded)
+  // before the CTA's shared memory is released
+  if (!s_ok && tid == 0) {
+    mbar_wait_bounded((it & 1) ? bar1 : bar0, (uint32_t)((it >> 1) & 1));
+    if (next_issued)
+      mbar_wait_bounded(((it + 1) & 1) ? bar1 : bar0, (uint32_t)(((it + 1) >> 1) & 1));
+  }
+}
+
+using AbsorbKernel = void (*)(const float*, const float*, const float*, float*, int, long long,
+                              long long, long long, long long, int*);
+
+struct AbsorbVariant {
+  AbsorbKernel k;
+  int NG, threads;
+  size_t smem;
+};
+
+// Instantiated shapes (d = 2, D = 2, 4, 6, 8); other shapes take the
+// two-contraction tensor-core path.
+template <int D, int NG>
+AbsorbVariant absorb_variant() {
+  using S = AbsorbShape<D, 2, NG>;
+  return AbsorbVariant{absorb_fused_k<D, 2, NG>, NG, S::threads, sizeof(float) * S::smem_floats};
+}
+
+bool absorb_lookup(int d, int D, AbsorbVariant* v) {
+  if (d != 2) return false;
+  switch (D) {
+    case 2: *v = absorb_variant<2, 256>(); return true;    // 256 threads
+    case 4: *v = absorb_variant<4, 16>(); return true;     // 256 threads
+    case 6: *v = absorb_variant<6, 4>(); return true;      // 324 threads
+    case 8: *v = absorb_variant<8, 2>(); return true;      // 512 threads
+    default: return false;
+  }
+}
+
+}  // namespace
+
+bool absorb_fused_ok(int d, int D) {
+  AbsorbVariant v;
+  return absorb_lookup(d, D, &v);
+}
+
+cudaError_t absorb_fused(const float* X1, const float* Ak, const float* Ab, float* X2, int ch,
+                         int D, int d, long long D2p, long long dD2p, long long mp, int* err,
+                         cudaStream_t s) {
+  AbsorbVariant v;
+  if (!absorb_lookup(d, D, &v)) return cudaErrorInvalidValue;
+  // slices are copied whole: rows must be unpadded (D^2 % 4 == 0 makes D2p == D^2)
+  // and X1 16-byte aligned for the bulk copies
+  if (D2p != (long long)D * D || (reinterpret_cast<uintptr_t>(X1) & 15) != 0)
+    return cudaErrorInvalidValue;
+  const long long ngroups = (long long)ch * ch;
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+  }
+  cudaError_t e = cudaFuncSetAttribute(v.k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)v.smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.k, v.threads, v.smem);
+  per_sm = std::max(1, per_sm);
+  const long long iters = (ngroups + v.NG - 1) / v.NG;
+  const unsigned grid = (unsigned)std::min<long long>(iters, (long long)nsm * per_sm);
+  v.k<<<grid, v.threads, v.smem, s>>>(X1, Ak, Ab, X2, ch, D2p, dD2p, mp, ngroups, err);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace qrctm

@@ -55,6 +55,8 @@ qrctm_status sync_check(qrctm_ctx* c, const char* where) {
   if (e != cudaSuccess) return cuda_fail(c, e, where);
   if (flag) {
     cudaMemsetAsync(c->err, 0, sizeof(int), c->st);
+    // an abandoned wait can leave the QR arrival counter non-zero
+    if (flag & ERRF_TIMEOUT) cudaMemsetAsync(c->qrw.bar, 0, sizeof(GridBar), c->st);
     cudaStreamSynchronize(c->st);
     if (flag & ERRF_TIMEOUT) return set_err(c, QRCTM_ERR_TIMEOUT, "device wait timed out");
     if (flag & ERRF_NUMERIC) return set_err(c, QRCTM_ERR_NUMERIC, "NaN/Inf or zero norm");
@@ -443,16 +445,20 @@ qrctm_status qrctm_energy_grad(qrctm_ctx* c, const qrctm_model* model, int mode,
   if (c->D < 2) return set_err(c, QRCTM_ERR_INVALID_ARG, "the gradient needs D >= 2");
   cudaError_t e;
   int iters = 0;
+  double resid = 0.0;
   {
     PhaseScope ps(c, QRCTM_PH_GRAD);
-    e = energy_grad_run(c, model->J1, model->J2, mode, k_unroll, grad, e_out, &iters);
+    e = energy_grad_run(c, model->J1, model->J2, mode, k_unroll, grad, e_out, &iters, &resid);
   }
   c->grad_iters = iters;
+  c->grad_resid = resid;
   if (e != cudaSuccess) return cuda_fail(c, e, "energy gradient");
   return sync_check(c, "energy gradient");
 }
 
 int qrctm_grad_iterations(const qrctm_ctx* ctx) { return ctx ? ctx->grad_iters : 0; }
+
+double qrctm_grad_residual(const qrctm_ctx* ctx) { return ctx ? ctx->grad_resid : 0.0; }
 
 qrctm_status qrctm_get_env(qrctm_ctx* c, double* C, double* T, double* spectrum_host) {
   if (!c) return QRCTM_ERR_INVALID_ARG;
@@ -551,6 +557,7 @@ qrctm_status qrctm_householder_qr(int m, int n, const double* M, double* Q, doub
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return QRCTM_ERR_CUDA;
   if (flag) {
     cudaMemsetAsync(w.err, 0, sizeof(int), s);
+    if (flag & ERRF_TIMEOUT) cudaMemsetAsync(w.bar, 0, sizeof(GridBar), s);
     cudaStreamSynchronize(s);
     return (flag & ERRF_TIMEOUT) ? QRCTM_ERR_TIMEOUT : QRCTM_ERR_NUMERIC;
   }

@@ -42,6 +42,7 @@ struct qrctm_ctx {
   int* err;
   int iters;
   int grad_iters;
+  double grad_resid;
   double last_delta;
   bool have_env;
   bool spec_valid;
@@ -89,6 +90,11 @@ cudaError_t spectrum_check(qrctm_ctx* c);
 // Split-precision step (split_step.cu)
 cudaError_t split_prepare_A(qrctm_ctx* c);
 cudaError_t qr_step_split(qrctm_ctx* c);
+// fused ket + bra absorption (FP32), see absorb.cu
+bool absorb_fused_ok(int d, int D);
+cudaError_t absorb_fused(const float* X1, const float* Ak, const float* Ab, float* X2, int ch,
+                         int D, int d, long long D2p, long long dD2p, long long mp, int* err,
+                         cudaStream_t s);
 
 // Energy (energy.cu)
 cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2);

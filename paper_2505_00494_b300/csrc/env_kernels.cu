@@ -161,123 +161,144 @@ __global__ void axpby_k(double* y, const double* x, double a, double b, long lon
 }
 
 // ---------------------------------------------------------------------------
-// Corner spectrum: one CTA of 1024 threads.
-// work: chi*chi (matrix) + 5*chi doubles.
+// Corner spectrum: Householder tridiagonalisation in one CTA of 1024 threads,
+// eigenvalues by multisection on Sturm counts, then |lambda| sorted.
+//
+// Double precision runs on a narrow pipe on this part (a warp-wide FP64
+// instruction costs tens of cycles of the SM), so every reduction folds the
+// per-warp partials in warp 0 only, the rank-2 update touches the lower
+// triangle only, and the Sturm recurrence tests signs and exponents with
+// integer instructions.
 // ---------------------------------------------------------------------------
-__device__ double block_sum(double v, double* red) {
+__device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __syncthreads();
+  return v;
+}
+
+// Sum of v over the block (fixed order).  `red` holds 32 slots, `out` one.
+__device__ double block_sum(double v, double* red, double* out) {
+  v = warp_sum(v);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  double s = 0.0;
-  const int nw = blockDim.x >> 5;
-  for (int w = 0; w < nw; ++w) s += red[w];
+  if (threadIdx.x < 32) {
+    double s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) *out = s;
+  }
   __syncthreads();
-  return s;
+  return *out;
 }
 
 // Number of eigenvalues of the symmetric tridiagonal (dg, e2 = offdiag^2)
 // below x: sign changes of the leading-minor sequence
 //   p_0 = 1, p_1 = d_0 - x, p_i = (d_{i-1} - x) p_{i-1} - e2_{i-2} p_{i-2},
 // i.e. negative pivots of T - x I (Sylvester's inertia).  No divisions: the
-// pair (p_{i-1}, p_i) is rescaled by an exact power of two when it leaves
-// [2^-400, 2^400]; an exact zero p_i is replaced by -pivmin * p_{i-1}.
+// pair (p_{i-1}, p_i) is rescaled by an exact power of two when the exponent
+// of p_i leaves [-400, 400]; an exact zero p_i is replaced by -pivmin p_{i-1}.
 __device__ int sturm_count(const double* dg, const double* e2, int n, double x, double pivmin) {
-  int cnt = 0;
   double pm = 1.0, pc = dg[0] - x;
-  if (pc == 0.0) pc = -pivmin;
-  cnt += (pc < 0.0);
+  if ((__double_as_longlong(pc) << 1) == 0) pc = -pivmin;
+  int cnt = (__double_as_longlong(pc) < 0);
   for (int i = 1; i < n; ++i) {
     double pn = fma(dg[i] - x, pc, -e2[i - 1] * pm);
-    if (pn == 0.0) pn = -pivmin * pc;
-    cnt += ((pn < 0.0) != (pc < 0.0));
+    if ((__double_as_longlong(pn) << 1) == 0) pn = -pivmin * pc;
+    const long long bn = __double_as_longlong(pn);
+    cnt += ((bn ^ __double_as_longlong(pc)) < 0);
     pm = pc;
     pc = pn;
-    const double a = fabs(pc);
-    if (a > 0x1p400) { pc *= 0x1p-400; pm *= 0x1p-400; }
-    else if (a < 0x1p-400) { pc *= 0x1p400; pm *= 0x1p400; }
+    const int ex = (int)((bn >> 52) & 0x7ff) - 1023;
+    if (ex > 400) { pc *= 0x1p-400; pm *= 0x1p-400; }
+    else if (ex < -400) { pc *= 0x1p400; pm *= 0x1p400; }
   }
   return cnt;
 }
 
-// Householder tridiagonalisation of (C + C^T)/2.  The matrix lives in shared
-// memory when it fits (n <= kSmemSpecMax), else in `work`.
+// The matrix lives in shared memory when it fits (n <= kSmemSpecMax, leading
+// dimension n + 1), else in `work` (leading dimension n).
 constexpr int kSmemSpecMax = 160;
 
 __global__ void __launch_bounds__(1024) spectrum_kernel(const double* __restrict__ C, int n,
-                                                        double* work, double* s_new,
-                                                        const double* s_old, int n_old,
-                                                        double* delta, int* err) {
+                                                        double* work, int* err) {
   __shared__ double red[32];
-  __shared__ double sc[2];
+  __shared__ double sc[4];
   extern __shared__ double spec_smem[];
-  double* Am = (n <= kSmemSpecMax) ? spec_smem : work;   // n x n
+  const bool in_smem = (n <= kSmemSpecMax);
+  const long long ld = in_smem ? n + 1 : n;
+  double* Am = in_smem ? spec_smem : work;   // lower triangle of (C + C^T)/2
   double* dg = work + (size_t)n * n; // n
   double* of = dg + n;               // n (off-diagonal)
-  double* ev = of + n;               // n
-  double* v = ev + n;                // n (squared off-diagonal, after the loop)
-  double* p = v + n;                 // n (bracket, after the loop)
+  double* v = of + 2 * n;            // n (squared off-diagonal, after the loop)
+  double* p = v + n;                 // lo, hi, pivmin
   __shared__ double sv[1024], sp[1024];   // Householder vector and A v during the loop
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wrp = tid >> 5;
   for (long long e = tid; e < (long long)n * n; e += nt) {
-    int i = (int)(e / n), j = (int)(e % n);
-    Am[e] = 0.5 * (C[e] + C[(long long)j * n + i]);
+    const int i = (int)(e / n), j = (int)(e % n);
+    if (j <= i) Am[i * ld + j] = 0.5 * (C[e] + C[(long long)j * n + i]);
   }
   __syncthreads();
   for (int k = 0; k + 2 < n; ++k) {
     const int L = n - k - 1;
-    double xi = (tid < L) ? Am[(long long)(k + 1 + tid) * n + k] : 0.0;
-    double nrm2 = block_sum(xi * xi, red);
+    double* base = Am + (k + 1) * ld + (k + 1);          // A22[i][j] = base[i*ld + j], j <= i
+    const double xi = (tid < L) ? Am[(k + 1 + tid) * ld + k] : 0.0;
+    const double nrm2 = block_sum(xi * xi, red, &sc[3]);
     if (tid == 0) {
-      double x0 = Am[(long long)(k + 1) * n + k];
-      double alpha = sqrt(nrm2);
-      double sgn = (x0 >= 0.0) ? 1.0 : -1.0;
-      sc[0] = x0 + sgn * alpha;         // v_0 (v_i = x_i for i > 0)
-      of[k] = -sgn * alpha;
-      dg[k] = Am[(long long)k * n + k];
+      const double x0 = Am[(k + 1) * ld + k];
+      dg[k] = Am[k * ld + k];
+      if (nrm2 == 0.0) {
+        of[k] = 0.0;
+        sc[1] = 0.0;
+      } else {
+        const double alpha = sqrt(nrm2);
+        const double sgn = (x0 >= 0.0) ? 1.0 : -1.0;
+        sc[0] = x0 + sgn * alpha;                        // v_0 (v_i = x_i for i > 0)
+        sc[1] = 1.0 / (alpha * (alpha + fabs(x0)));      // beta = 2 / ||v||^2
+        of[k] = -sgn * alpha;
+      }
     }
     __syncthreads();
-    if (nrm2 == 0.0) {
-      if (tid == 0) of[k] = 0.0;
-      __syncthreads();
-      continue;
-    }
+    const double beta = sc[1];
+    if (beta == 0.0) continue;                           // column already reduced
     if (tid < L) sv[tid] = (tid == 0) ? sc[0] : xi;
     __syncthreads();
-    double vv = block_sum((tid < L) ? sv[tid] * sv[tid] : 0.0, red);
-    const double beta = 2.0 / vv;
-    // p = beta * A22 v  (A22 symmetric: read columns; four independent sums)
+    // p = beta A22 v from the lower triangle: row tid up to the diagonal,
+    // then column tid below it
+    double pt = 0.0;
     if (tid < L) {
-      const double* col = Am + (long long)(k + 1) * n + k + 1 + tid;
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      const double* row = base + tid * ld;
+      double a0 = 0.0, a1 = 0.0;
       int j = 0;
-      for (; j + 4 <= L; j += 4) {
-        a0 = fma(col[(long long)j * n], sv[j], a0);
-        a1 = fma(col[(long long)(j + 1) * n], sv[j + 1], a1);
-        a2 = fma(col[(long long)(j + 2) * n], sv[j + 2], a2);
-        a3 = fma(col[(long long)(j + 3) * n], sv[j + 3], a3);
+      for (; j + 1 <= tid; j += 2) {
+        a0 = fma(row[j], sv[j], a0);
+        a1 = fma(row[j + 1], sv[j + 1], a1);
       }
-      for (; j < L; ++j) a0 = fma(col[(long long)j * n], sv[j], a0);
-      sp[tid] = beta * ((a0 + a1) + (a2 + a3));
+      if (j <= tid) a0 = fma(row[j], sv[j], a0);
+      j = tid + 1;
+      for (; j + 1 < L; j += 2) {
+        a0 = fma(base[j * ld + tid], sv[j], a0);
+        a1 = fma(base[(j + 1) * ld + tid], sv[j + 1], a1);
+      }
+      if (j < L) a0 = fma(base[j * ld + tid], sv[j], a0);
+      pt = beta * (a0 + a1);
+      sp[tid] = pt;
     }
-    __syncthreads();
-    double pv = block_sum((tid < L) ? sp[tid] * sv[tid] : 0.0, red);
+    const double pv = block_sum((tid < L) ? pt * sv[tid] : 0.0, red, &sc[3]);
     const double K = 0.5 * beta * pv;
-    if (tid < L) sp[tid] = sp[tid] - K * sv[tid];      // w
+    if (tid < L) sp[tid] = fma(-K, sv[tid], pt);          // w = p - K v
     __syncthreads();
-    for (int i = tid >> 5; i < L; i += nt >> 5) {
-      const double vi = sv[i], pi = sp[i];
-      double* row = Am + (long long)(k + 1 + i) * n + k + 1;
-      for (int j = tid & 31; j < L; j += 32) row[j] -= vi * sp[j] + pi * sv[j];
+    // A22 -= v w^T + w v^T on the lower triangle
+    for (int i = wrp; i < L; i += (nt >> 5)) {
+      const double vi = sv[i], wi = sp[i];
+      double* row = base + i * ld;
+      for (int j = lane; j <= i; j += 32) row[j] = fma(-vi, sp[j], fma(-wi, sv[j], row[j]));
     }
     __syncthreads();
   }
   if (tid == 0) {
     if (n >= 2) {
-      dg[n - 2] = Am[(long long)(n - 2) * n + n - 2];
-      of[n - 2] = Am[(long long)(n - 1) * n + n - 2];
+      dg[n - 2] = Am[(n - 2) * ld + n - 2];
+      of[n - 2] = Am[(n - 1) * ld + n - 2];
     }
-    dg[n - 1] = Am[(long long)(n - 1) * n + n - 1];
+    dg[n - 1] = Am[(n - 1) * ld + n - 1];
   }
   __syncthreads();
   // squared off-diagonals into v, Gershgorin interval into p[0..2]
@@ -295,7 +316,7 @@ __global__ void __launch_bounds__(1024) spectrum_kernel(const double* __restrict
     hi_l = fmax(hi_l, __shfl_xor_sync(0xffffffffu, hi_l, o));
     amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   }
-  if ((tid & 31) == 0) { mn[tid >> 5] = lo_l; mx[tid >> 5] = hi_l; am[tid >> 5] = amax; }
+  if (lane == 0) { mn[wrp] = lo_l; mx[wrp] = hi_l; am[wrp] = amax; }
   __syncthreads();
   if (tid == 0) {
     double lo = 1e300, hi = -1e300, big = 0.0;
@@ -305,25 +326,35 @@ __global__ void __launch_bounds__(1024) spectrum_kernel(const double* __restrict
     p[1] = hi + 1e-14 * fabs(hi) + 1e-300;
     p[2] = fmax(1e-300, big * 1e-300);       // pivot floor of the Sturm recurrence
   }
-  (void)s_new; (void)s_old; (void)n_old; (void)delta;
 }
 
 // Eigenvalue i of the tridiagonal (dg, e^2) by multisection: one warp per
-// eigenvalue, the 32 lanes evaluate Sturm counts at 32 interior points of the
-// current bracket, which shrinks 33-fold per round until it stops shrinking.
-__global__ void bisect_kernel(const double* work, int n, double* ev_out) {
+// eigenvalue (one warp per CTA, so that the Sturm recurrences of different
+// eigenvalues run on different SMs), the 32 lanes evaluate Sturm counts at 32
+// interior points of the current bracket, which shrinks 33-fold per round
+// until its width reaches the absolute resolution 4 eps max(|lo|, |hi|) of
+// the Gershgorin interval (the accuracy a backward-stable method attains).
+constexpr int kBisectMaxN = 1024;
+
+__global__ void __launch_bounds__(32) bisect_kernel(const double* work, int n, double* ev_out) {
+  __shared__ double sdg[kBisectMaxN], se2[kBisectMaxN];
   const double* dg = work + (size_t)n * n;
   const double* v = dg + 3 * (size_t)n;       // e^2
   const double* p = v + n;                    // lo, hi, pivmin
-  const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (i >= n) return;
+  const int lane = threadIdx.x;
+  const int i = blockIdx.x;
+  for (int t = lane; t < n; t += 32) {
+    sdg[t] = dg[t];
+    se2[t] = (t + 1 < n) ? v[t] : 0.0;
+  }
+  __syncwarp();
   double a = p[0], b = p[1];
   const double pivmin = p[2];
+  const double res = 4e-16 * fmax(fabs(a), fabs(b));
   for (int round = 0; round < 64; ++round) {
-    const double h = (b - a) / 33.0;
+    const double h = (b - a) * (1.0 / 33.0);
     const double x = a + h * (lane + 1);
-    const bool above = (x > a && x < b) ? (sturm_count(dg, v, n, x, pivmin) > i) : (x >= b);
+    const bool above = (x > a && x < b) ? (sturm_count(sdg, se2, n, x, pivmin) > i) : (x >= b);
     const unsigned mask = __ballot_sync(0xffffffffu, above);
     // first lane whose point lies above eigenvalue i bounds it from above
     const int first = mask ? __ffs(mask) - 1 : 32;
@@ -332,24 +363,29 @@ __global__ void bisect_kernel(const double* work, int n, double* ev_out) {
     if (!(nb < b || na > a)) break;          // no progress: bracket at resolution
     a = na;
     b = nb;
-    if (b - a <= 4e-16 * fmax(fabs(a), fabs(b))) break;
+    if (b - a <= res) break;
   }
   if (lane == 0) ev_out[i] = 0.5 * (a + b);
 }
 
-// sorted |lambda| (descending, ties by index) and the change to the previous
+// sorted |lambda| (descending, ties by index) and the change to the previous.
+// Non-negative doubles order like their bit patterns, so the ranking compares
+// integers.
 __global__ void spectrum_finish_kernel(const double* ev, int n, double* s_new, const double* s_old,
                                        int n_old, double* delta) {
-  __shared__ double red[32];
+  __shared__ double red[32], out;
+  __shared__ long long key[kBisectMaxN];
   const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < n; i += nt) key[i] = __double_as_longlong(fabs(ev[i]));
+  __syncthreads();
   for (int i = tid; i < n; i += nt) {
-    double ai = fabs(ev[i]);
+    const long long ki = key[i];
     int rank = 0;
     for (int j = 0; j < n; ++j) {
-      double aj = fabs(ev[j]);
-      rank += (aj > ai) || (aj == ai && j < i);
+      const long long kj = key[j];
+      rank += (kj > ki) || (kj == ki && j < i);
     }
-    s_new[rank] = ai;
+    s_new[rank] = __longlong_as_double(ki);
   }
   __syncthreads();
   const int nm = n > n_old ? n : n_old;
@@ -359,7 +395,7 @@ __global__ void spectrum_finish_kernel(const double* ev, int n, double* s_new, c
     double y = (s_old != nullptr && i < n_old) ? s_old[i] : 0.0;
     acc += (x - y) * (x - y);
   }
-  double tot = block_sum(acc, red);
+  double tot = block_sum(acc, red, &out);
   if (tid == 0) *delta = sqrt(tot);
 }
 
@@ -459,17 +495,17 @@ cudaError_t corner_spectrum(const double* C, int chi, double* work, double* s_ne
                             const double* s_old, int chi_old, double* delta, int* err,
                             cudaStream_t s) {
   if (chi < 1 || chi > 1024) return cudaErrorInvalidValue;
-  const size_t smem = (chi <= kSmemSpecMax) ? sizeof(double) * chi * chi : 0;
+  const size_t smem = (chi <= kSmemSpecMax) ? sizeof(double) * chi * (chi + 1) : 0;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(spectrum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(double) * kSmemSpecMax * kSmemSpecMax));
+                         (int)(sizeof(double) * kSmemSpecMax * (kSmemSpecMax + 1)));
     attr = true;
   }
-  spectrum_kernel<<<1, 1024, smem, s>>>(C, chi, work, s_new, s_old, chi_old, delta, err);
+  spectrum_kernel<<<1, 1024, smem, s>>>(C, chi, work, err);
   note_launch();
   double* ev = work + (size_t)chi * chi + 5 * (size_t)chi + 8;
-  bisect_kernel<<<(chi + 3) / 4, 128, 0, s>>>(work, chi, ev);
+  bisect_kernel<<<chi, 32, 0, s>>>(work, chi, ev);
   note_launch();
   spectrum_finish_kernel<<<1, 256, 0, s>>>(ev, chi, s_new, s_old, chi_old, delta);
   note_launch();

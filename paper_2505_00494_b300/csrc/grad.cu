@@ -4,9 +4,12 @@
 // E(A) = e(A, x*(A)) with x* = (C*, T*) a fixed point of the iteration.  The
 // QR map F alternates a sign gauge between steps, so the fixed-point equation
 // is written for two steps G = F o F, x* = G(x*, A):
-//   dE/dA = de/dA + xbar^T dG/dA,   xbar = sum_n (J_G^T)^n ebar,
-// with ebar = de/dx and J_G = dG/dx; the series converges because ebar is
-// orthogonal to the slowly contracting gauge directions of J_G.  Unrolled
+//   dE/dA = de/dA + xbar^T dG/dA,   (I - J_G^T) xbar = ebar,
+// with ebar = de/dx and J_G = dG/dx.  xbar = sum_n (J_G^T)^n ebar formally;
+// the series converges as slowly as the CTMRG iteration itself (the ratio of
+// the leading transfer-matrix eigenvalues), so the linear system is solved by
+// restarted GMRES instead, one application of J_G^T being two reverse steps.
+// Unrolled
 // mode instead backpropagates through k recorded steps started from the
 // current environment (held fixed).  The gradient is projected onto the C4v
 // subspace at the end (the function is only defined there).  All reverse
@@ -22,6 +25,7 @@ namespace qrctm {
 namespace {
 
 constexpr int kMaxUnroll = kGradMaxUnroll;
+constexpr int kGmresM = 40;   // GMRES restart length
 inline size_t al8(size_t n) { return ((n * 8) + 255) & ~size_t(255); }
 
 struct GradLayout {
@@ -32,6 +36,8 @@ struct GradLayout {
   double *ctb, *L1b, *Wb, *Z1b, *Z2b, *HLb, *rhob, *Ctb, *Pb;
   double *ckC, *ckT;   // unroll checkpoints
   double* red;         // reductions
+  double* kry;         // GMRES basis: (kGmresM + 1) env-sized vectors [C (chi^2), T]
+  double *ev0, *ev1, *evx;   // env-sized vectors: right-hand side, work, solution
 };
 
 // Lay the gradient region out (carve = false: only count bytes).
@@ -101,6 +107,10 @@ size_t layout(int d, int D, int chi, bool nnn, char* base, GradLayout* L) {
   take(L ? &L->ckC : nullptr, c2 * (kMaxUnroll + 1));
   take(L ? &L->ckT : nullptr, mc * (kMaxUnroll + 1));
   take(L ? &L->red : nullptr, 1024);
+  take(L ? &L->kry : nullptr, (c2 + mc) * (kGmresM + 1));
+  take(L ? &L->ev0 : nullptr, c2 + mc);
+  take(L ? &L->ev1 : nullptr, c2 + mc);
+  take(L ? &L->evx : nullptr, c2 + mc);
   return off;
 }
 
@@ -384,9 +394,9 @@ static cudaError_t energy_vjp(qrctm_ctx* c, const GradLayout& L, const double* C
 // ---------------------------------------------------------------------------
 // Drivers
 // ---------------------------------------------------------------------------
-static cudaError_t sumsq_host(qrctm_ctx* c, const double* x, long long n, double* red,
-                              double* out) {
-  cudaError_t e = sum_squares_partials(x, n, red, 64, c->st);
+static cudaError_t dot_host(qrctm_ctx* c, const double* x, const double* y, long long n,
+                           double* red, double* out) {
+  cudaError_t e = dot_partials(x, y, n, red, 64, c->st);
   if (e != cudaSuccess) return e;
   double h[64];
   if ((e = cudaMemcpyAsync(h, red, sizeof(h), cudaMemcpyDeviceToHost, c->st)) != cudaSuccess)
@@ -398,8 +408,103 @@ static cudaError_t sumsq_host(qrctm_ctx* c, const double* x, long long n, double
   return cudaSuccess;
 }
 
+// w = v - J_G^T v for an env-sized vector v = [C (chi^2), T (chi^2 D^2)]
+static cudaError_t adjoint_operator(qrctm_ctx* c, GradLayout& L, const double* v, double* w) {
+  const Dims k(c);
+  const long long c2 = (long long)k.ch * k.ch, n = c2 + k.m * k.ch;
+  cudaError_t e;
+  if ((e = step_vjp(c, L.tape[1], L.adj, v, v + c2, L.y2C, L.y2T, nullptr)) != cudaSuccess)
+    return e;
+  if ((e = step_vjp(c, L.tape[0], L.adj, L.y2C, L.y2T, w, w + c2, nullptr)) != cudaSuccess)
+    return e;
+  // w <- v - w
+  axpby(w, v, 1.0, -1.0, n, c->st);
+  return cudaGetLastError();
+}
+
+// Restarted GMRES for (I - J_G^T) x = b (b = L.ev0, x -> L.evx); returns the
+// number of operator applications.
+static cudaError_t adjoint_gmres(qrctm_ctx* c, GradLayout& L, double tol, int max_apply,
+                                 int* applies, double* rel_resid) {
+  const Dims k(c);
+  const long long n = (long long)k.ch * k.ch + k.m * k.ch;
+  const int M = kGmresM;
+  cudaStream_t s = c->st;
+  cudaError_t e;
+  double bnorm2;
+  if ((e = dot_host(c, L.ev0, L.ev0, n, L.red, &bnorm2)) != cudaSuccess) return e;
+  const double bnorm = std::sqrt(bnorm2);
+  if ((e = fill_zero(L.evx, n, s)) != cudaSuccess) return e;
+  *applies = 0;
+  *rel_resid = 0.0;
+  if (!(bnorm > 0.0)) return cudaSuccess;
+  std::vector<double> H((M + 1) * M), cs(M), sn(M), g(M + 1), y(M);
+  auto Vj = [&](int j) { return L.kry + (long long)j * n; };
+  double resid = bnorm;
+  while (*applies < max_apply && resid > tol * bnorm) {
+    // r = b - A x  (x = 0 on the first cycle)
+    if (*applies == 0) {
+      cudaMemcpyAsync(Vj(0), L.ev0, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+    } else {
+      if ((e = adjoint_operator(c, L, L.evx, L.ev1)) != cudaSuccess) return e;
+      ++*applies;
+      cudaMemcpyAsync(Vj(0), L.ev0, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+      axpby(Vj(0), L.ev1, -1.0, 1.0, n, s);
+    }
+    double beta2;
+    if ((e = dot_host(c, Vj(0), Vj(0), n, L.red, &beta2)) != cudaSuccess) return e;
+    const double beta = std::sqrt(beta2);
+    if (!(beta > tol * bnorm)) { resid = beta; break; }
+    axpby(Vj(0), Vj(0), 0.0, 1.0 / beta, n, s);   // v0 <- r / beta
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j = 0;
+    for (; j < M && *applies < max_apply; ++j) {
+      if ((e = adjoint_operator(c, L, Vj(j), Vj(j + 1))) != cudaSuccess) return e;
+      ++*applies;
+      for (int i = 0; i <= j; ++i) {   // modified Gram-Schmidt
+        double h;
+        if ((e = dot_host(c, Vj(j + 1), Vj(i), n, L.red, &h)) != cudaSuccess) return e;
+        H[i * M + j] = h;
+        axpby(Vj(j + 1), Vj(i), -h, 1.0, n, s);
+      }
+      double hn2;
+      if ((e = dot_host(c, Vj(j + 1), Vj(j + 1), n, L.red, &hn2)) != cudaSuccess) return e;
+      const double hn = std::sqrt(hn2);
+      H[(j + 1) * M + j] = hn;
+      if (hn > 0.0) axpby(Vj(j + 1), Vj(j + 1), 0.0, 1.0 / hn, n, s);
+      // Givens rotations on column j
+      for (int i = 0; i < j; ++i) {
+        const double a = H[i * M + j], b = H[(i + 1) * M + j];
+        H[i * M + j] = cs[i] * a + sn[i] * b;
+        H[(i + 1) * M + j] = -sn[i] * a + cs[i] * b;
+      }
+      const double a = H[j * M + j], b = H[(j + 1) * M + j];
+      const double r = std::hypot(a, b);
+      cs[j] = (r > 0) ? a / r : 1.0;
+      sn[j] = (r > 0) ? b / r : 0.0;
+      H[j * M + j] = r;
+      H[(j + 1) * M + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      resid = std::fabs(g[j + 1]);
+      if (!(resid > tol * bnorm) || hn == 0.0) { ++j; break; }
+    }
+    // y = H^{-1} g (upper triangular j x j), x += V y
+    for (int i = j - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int l = i + 1; l < j; ++l) acc -= H[i * M + l] * y[l];
+      y[i] = acc / H[i * M + i];
+    }
+    for (int i = 0; i < j; ++i) axpby(L.evx, Vj(i), y[i], 1.0, n, s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  *rel_resid = resid / bnorm;
+  return cudaSuccess;
+}
+
 cudaError_t energy_grad_run(qrctm_ctx* c, double J1, double J2, int mode, int k_unroll,
-                            double* grad, double* e_out, int* iters_out) {
+                            double* grad, double* e_out, int* iters_out, double* resid_out) {
   if (!c->G) return cudaErrorInvalidValue;
   if (mode != 0 && (k_unroll < 1 || k_unroll > kMaxUnroll)) return cudaErrorInvalidValue;
   GradLayout L;
@@ -410,37 +515,21 @@ cudaError_t energy_grad_run(qrctm_ctx* c, double J1, double J2, int mode, int k_
   const long long c2 = (long long)k.ch * k.ch, mc = k.m * k.ch, nA = (long long)k.d * k.D4;
   double* e_dev = c->e_d;
   int iters = 0;
+  double resid = 0.0;
   if (mode == 0) {
     // implicit: tapes of two steps at the current environment
     if ((e = step_fwd_tape(c, c->C, c->T, L.tape[0])) != cudaSuccess) return e;
     if ((e = step_fwd_tape(c, L.tape[0].Cout, L.tape[0].Tout, L.tape[1])) != cudaSuccess) return e;
     if ((e = energy_vjp(c, L, c->C, c->T, J1, J2, L.ebC, L.ebT, L.Abar, e_dev)) != cudaSuccess)
       return e;
-    // xbar = sum_n (J_G^T)^n ebar
-    cudaMemcpyAsync(L.xbC, L.ebC, sizeof(double) * c2, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(L.xbT, L.ebT, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(L.yC, L.ebC, sizeof(double) * c2, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(L.yT, L.ebT, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s);
-    double n0C = 0, n0T = 0;
-    if ((e = sumsq_host(c, L.ebC, c2, L.red, &n0C)) != cudaSuccess) return e;
-    if ((e = sumsq_host(c, L.ebT, mc, L.red, &n0T)) != cudaSuccess) return e;
-    const double n0 = std::sqrt(n0C + n0T);
-    const int maxit = c->cfg.grad_max_iter;
-    const double tol = c->cfg.grad_tol;
-    for (iters = 0; iters < maxit; ++iters) {
-      if ((e = step_vjp(c, L.tape[1], L.adj, L.yC, L.yT, L.y2C, L.y2T, nullptr)) != cudaSuccess)
-        return e;
-      if ((e = step_vjp(c, L.tape[0], L.adj, L.y2C, L.y2T, L.yC, L.yT, nullptr)) != cudaSuccess)
-        return e;
-      axpy_k<<<nb256(c2), 256, 0, s>>>(L.xbC, L.yC, 1.0, c2);
-      axpy_k<<<nb256(mc), 256, 0, s>>>(L.xbT, L.yT, 1.0, mc);
-      note_launch(2);
-      double nC = 0, nT = 0;
-      if ((e = sumsq_host(c, L.yC, c2, L.red, &nC)) != cudaSuccess) return e;
-      if ((e = sumsq_host(c, L.yT, mc, L.red, &nT)) != cudaSuccess) return e;
-      if (!std::isfinite(nC + nT)) return cudaErrorInvalidValue;
-      if (std::sqrt(nC + nT) < tol * n0) { ++iters; break; }
-    }
+    // xbar solves (I - J_G^T) xbar = ebar   (restarted GMRES)
+    cudaMemcpyAsync(L.ev0, L.ebC, sizeof(double) * c2, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(L.ev0 + c2, L.ebT, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s);
+    if ((e = adjoint_gmres(c, L, c->cfg.grad_tol, c->cfg.grad_max_iter, &iters, &resid)) !=
+        cudaSuccess)
+      return e;
+    cudaMemcpyAsync(L.xbC, L.evx, sizeof(double) * c2, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(L.xbT, L.evx + c2, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s);
     // A-part: xbar through both steps
     if ((e = step_vjp(c, L.tape[1], L.adj, L.xbC, L.xbT, L.y2C, L.y2T, L.Abar)) != cudaSuccess)
       return e;
@@ -481,6 +570,7 @@ cudaError_t energy_grad_run(qrctm_ctx* c, double J1, double J2, int mode, int k_
     return e;
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
   if (iters_out) *iters_out = iters;
+  if (resid_out) *resid_out = resid;
   (void)nA;
   return cudaSuccess;
 }

@@ -9,6 +9,8 @@ namespace qrctm {
 IdxMap concat_map(const IdxMap& x, long long xrange, const IdxMap& y);
 cudaError_t gemm_vjp(qrctm_ctx* c, const Gemm& f, const double* Dbar, double* Abar, double* Bbar,
                      bool accA, bool accB);
+cudaError_t dot_partials(const double* x, const double* y, long long n, double* partials,
+                         int nparts, cudaStream_t s);
 cudaError_t triu_inverse(const double* R, double* X, int n, int* err, cudaStream_t s);
 cudaError_t sym_corner_vjp(const double* X, double* Y, int chi, bool acc, cudaStream_t s);
 cudaError_t norm_vjp(const double* y, const double* ybar, double* xbar, long long n,
@@ -116,6 +118,6 @@ struct AdjWork {
 size_t grad_bytes(int d, int D, int chi);
 constexpr int kGradMaxUnroll = 32;
 cudaError_t energy_grad_run(qrctm_ctx* c, double J1, double J2, int mode, int k_unroll,
-                            double* grad, double* e_out, int* iters_out);
+                            double* grad, double* e_out, int* iters_out, double* resid_out);
 
 }  // namespace qrctm

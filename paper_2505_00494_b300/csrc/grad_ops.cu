@@ -170,6 +170,13 @@ inline unsigned nb256(long long n) { return (unsigned)std::min<long long>((n + 2
 
 }  // namespace
 
+cudaError_t dot_partials(const double* x, const double* y, long long n, double* partials,
+                         int nparts, cudaStream_t s) {
+  dot_partials_k<<<nparts, 256, 0, s>>>(x, y, n, partials);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t triu_inverse(const double* R, double* X, int n, int* err, cudaStream_t s) {
   triu_inverse_k<<<(n + 3) / 4, 128, 0, s>>>(R, X, n, err);
   note_launch();

@@ -54,6 +54,17 @@ __device__ __forceinline__ double sqrt_nr(double a) {
 // sums and the published pivot row; the tile is written back (R entries,
 // reflectors) at the end.  Without TILE (very tall panels) the same steps
 // run on W in global memory.
+//
+// Column step j (c = j0 + j the pivot row), after all CTAs have published the
+// partial sums of column j (slot 0: sum_{i>c} x_i^2, slot t: sum_{i>c} x_i
+// y_{t,i} for column j + t) and the owner of row c has published that row:
+//   sigma = sum of slot 0, mu = sqrt(x_0^2 + sigma),
+//   w = x_0 - mu  (= -sigma / (x_0 + mu) for x_0 > 0),   tau = -w / mu,
+//   v = x / w (v_0 = 1),   y_t -= tau (y_{t,0} + s_t / w) v,   R_cc = mu.
+// The same pass over a CTA's rows that applies reflector j also accumulates
+// the partial sums of column j + 1 (the updated value of column j + 1 on a
+// row reaches the other lanes by a warp shuffle), so a column costs one
+// round of the arrival counter and four block barriers.
 template <bool TILE>
 __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
                                                       double* __restrict__ V,
@@ -70,14 +81,20 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
   double* psum = part;
   double* rowb = part + 2 * (size_t)P * NB;
   __shared__ double red[8][NB];
-  __shared__ double tot[NB];
+  __shared__ double coef_s[NB];   // per lane: new y_t = y_t + coef_s[t] x on rows below c
+  __shared__ double rcoef_s[NB];  // per lane: R_{c,j+t} = y_{t,0} - rcoef_s[t]
   __shared__ double sc[4];
   __shared__ double tau_s[NB];
+  __shared__ int s_ok;
   extern __shared__ double tile[];                 // [rows][NB + 1]
   // element (global row i, panel column jc)
   auto at = [&](long long i, int jc) -> double& {
     if (TILE) return tile[(i - r_begin) * (NB + 1) + jc];
     return W[((long long)j0 + jc) * m + i];
+  };
+  auto sum8 = [&](int t) {
+    return ((red[0][t] + red[1][t]) + (red[2][t] + red[3][t])) +
+           ((red[4][t] + red[5][t]) + (red[6][t] + red[7][t]));
   };
   if (TILE) {
     for (int e = threadIdx.x; e < rows * nb; e += PT) {
@@ -86,101 +103,119 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     }
     __syncthreads();
   }
-
-  // partial sums for column j (slot 0: sum x_i^2 over i > c; slot t: sum x_i y_{c+t,i})
-  auto partials = [&](int j, int buf) {
-    const long long c = (long long)j0 + j;
-    const int nrem = nb - j - 1;
+  // partial sums of column 0 (slot t = lane) and the pivot row j0
+  {
+    const long long c = j0;
     double acc = 0.0;
-    const long long i0 = std::max<long long>(r_begin, c + 1);
-    if (lane <= nrem)
-      for (long long i = i0 + wrp; i < r_end; i += 8) acc = fma(at(i, j), at(i, j + lane), acc);
+    if (lane < nb)
+      for (long long i = std::max<long long>(r_begin, c + 1) + wrp; i < r_end; i += 8)
+        acc = fma(at(i, 0), at(i, lane), acc);
     red[wrp][lane] = acc;
+    if (c >= r_begin && c < r_end && (int)threadIdx.x < nb) rowb[threadIdx.x] = at(c, threadIdx.x);
     __syncthreads();
-    if (threadIdx.x < NB) {
-      const int t = threadIdx.x;
-      psum[((size_t)buf * P + b) * NB + t] =
-          ((red[0][t] + red[1][t]) + (red[2][t] + red[3][t])) +
-          ((red[4][t] + red[5][t]) + (red[6][t] + red[7][t]));
+    if (wrp == 0) {
+      psum[(size_t)b * NB + lane] = sum8(lane);
+      __syncwarp();
+      if (lane == 0) grid_arrive(bar);
     }
-    // the owner of row c publishes row c (x_0 and the y_0 of the other columns)
-    if (c >= r_begin && c < r_end && (int)threadIdx.x <= nrem)
-      rowb[buf * NB + threadIdx.x] = at(c, j + threadIdx.x);
-    __syncthreads();
-  };
+  }
 
-  partials(0, 0);
-  if (!grid_barrier(bar, P, err)) return;
-
-  for (int j = 0; j < nb; ++j) {
+  int j = 0;
+  for (; j < nb; ++j) {
     const int buf = j & 1;
     const long long c = (long long)j0 + j;
     const int nrem = nb - j - 1;
-    // cross-CTA reduction of the partial sums: lane = column slot, the 8 warps
-    // take every 8th CTA, then a fixed-order sum over the warps
+    if (threadIdx.x == 0) s_ok = grid_wait(bar, (unsigned)P * (unsigned)(j + 1), err) ? 1 : 0;
+    __syncthreads();
+    if (!s_ok) break;
+    // cross-CTA reduction (L2 reads): lane = slot, the 8 warps take every 8th CTA
     {
       double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
       if (lane <= nrem) {
+        const double* ps = psum + (size_t)buf * P * NB + lane;
         int q = wrp;
         for (; q + 24 < P; q += 32) {
-          s0 += psum[((size_t)buf * P + q) * NB + lane];
-          s1 += psum[((size_t)buf * P + q + 8) * NB + lane];
-          s2 += psum[((size_t)buf * P + q + 16) * NB + lane];
-          s3 += psum[((size_t)buf * P + q + 24) * NB + lane];
+          s0 += __ldcg(ps + (size_t)q * NB);
+          s1 += __ldcg(ps + (size_t)(q + 8) * NB);
+          s2 += __ldcg(ps + (size_t)(q + 16) * NB);
+          s3 += __ldcg(ps + (size_t)(q + 24) * NB);
         }
-        for (; q < P; q += 8) s0 += psum[((size_t)buf * P + q) * NB + lane];
+        for (; q < P; q += 8) s0 += __ldcg(ps + (size_t)q * NB);
       }
       red[wrp][lane] = (s0 + s1) + (s2 + s3);
     }
     __syncthreads();
-    if ((int)threadIdx.x <= nrem) {
-      const int t = threadIdx.x;
-      tot[t] = ((red[0][t] + red[1][t]) + (red[2][t] + red[3][t])) +
-               ((red[4][t] + red[5][t]) + (red[6][t] + red[7][t]));
+    if (wrp == 0) {
+      const double st = sum8(lane);                      // sigma (lane 0), s_t (lane t)
+      const double y0 = (lane <= nrem) ? __ldcg(rowb + buf * NB + lane) : 0.0;
+      double tau = 0.0, inv_w = 0.0, mu = 0.0;
+      if (lane == 0) {
+        const double x0 = y0, sigma = st;
+        mu = sqrt_nr(fma(x0, x0, sigma));
+        if (sigma == 0.0) {
+          tau = (x0 < 0.0) ? 2.0 : 0.0;                  // v = e_1
+          inv_w = 0.0;
+        } else if (x0 <= 0.0) {
+          const double w = x0 - mu;
+          tau = -w * rcp_nr(mu);
+          inv_w = rcp_nr(w);
+        } else {
+          const double xm = x0 + mu;
+          const double w = -sigma * rcp_nr(xm);
+          tau = -w * rcp_nr(mu);
+          inv_w = -xm * rcp_nr(sigma);
+        }
+        if (!(mu == mu) || isinf(mu)) atomicOr(err, ERRF_NUMERIC);
+        sc[0] = tau; sc[1] = inv_w; sc[2] = mu;
+        tau_s[j] = tau;
+      }
+      tau = __shfl_sync(0xffffffffu, tau, 0);
+      inv_w = __shfl_sync(0xffffffffu, inv_w, 0);
+      // row-update multiplier of lane t: new y_t = y_t + mult_t x  (lane 0: v = x / w)
+      double mult = 0.0, rc = 0.0;
+      if (lane == 0) {
+        mult = inv_w;
+      } else if (lane <= nrem) {
+        rc = tau * fma(st, inv_w, y0);
+        mult = -rc * inv_w;
+      }
+      coef_s[lane] = mult;
+      rcoef_s[lane] = rc;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      const double x0 = rowb[buf * NB];
-      const double sigma = tot[0];
-      const double mu = sqrt_nr(x0 * x0 + sigma);
-      double tau, inv_v0;
-      if (sigma == 0.0) {
-        tau = (x0 < 0.0) ? 2.0 : 0.0;      // v = e_1
-        inv_v0 = 0.0;
-      } else {
-        const double v0 = (x0 <= 0.0) ? (x0 - mu) : (-sigma * rcp_nr(x0 + mu));
-        tau = 2.0 * v0 * v0 * rcp_nr(sigma + v0 * v0);
-        inv_v0 = rcp_nr(v0);
-      }
-      if (!(mu == mu) || isinf(mu)) atomicOr(err, ERRF_NUMERIC);
-      sc[0] = tau; sc[1] = inv_v0; sc[2] = mu;
-      tau_s[j] = tau;
-    }
-    __syncthreads();
-    const double tau = sc[0], inv_v0 = sc[1], mu = sc[2];
-    // coefficient of column c+t (t >= 1): tau * (y_0 + s_t / v_0)
-    double coef = 0.0;
-    if (lane >= 1 && lane <= nrem) coef = tau * (rowb[buf * NB + lane] + tot[lane] * inv_v0);
-    {
-      const long long i0 = std::max<long long>(r_begin, c + 1);
-      for (long long i = i0 + wrp; i < r_end; i += 8) {
-        const double v = at(i, j) * inv_v0;
-        if (lane >= 1 && lane <= nrem) at(i, j + lane) -= coef * v;
-        __syncwarp();
-        if (lane == 0) at(i, j) = v;
-        __syncwarp();
-      }
-      // row c itself: the R entries
-      if (c >= r_begin && c < r_end) {
-        if (lane == 0 && wrp == 0) at(c, j) = mu;
-        if (wrp == 0 && lane >= 1 && lane <= nrem) at(c, j + lane) -= coef;
+    const double mult = coef_s[lane];
+    const bool active = (lane <= nrem);
+    const bool last = (j + 1 >= nb);
+    double acc = 0.0;
+    for (long long i = std::max<long long>(r_begin, c + 1) + wrp; i < r_end; i += 8) {
+      const double x = at(i, j);
+      const double old = (lane >= 1 && active) ? at(i, j + lane) : 0.0;
+      const double nv = fma(mult, x, old);
+      __syncwarp();
+      if (active) at(i, j + lane) = nv;
+      if (!last) {
+        const double xn = __shfl_sync(0xffffffffu, nv, 1);   // updated column j + 1
+        if (lane >= 1 && active) {
+          if (i > c + 1) acc = fma(xn, nv, acc);
+          else rowb[(buf ^ 1) * NB + lane - 1] = nv;       // pivot row of column j + 1
+        }
       }
     }
+    // row c itself: the R entries (R_cc = mu; y_{t,0} - tau (y_{t,0} + s_t / w))
+    if (wrp == 0 && c >= r_begin && c < r_end) {
+      if (lane == 0) at(c, j) = sc[2];
+      else if (active) at(c, j + lane) -= rcoef_s[lane];
+    }
+    if (last) break;
+    red[wrp][lane] = acc;                                  // slot lane - 1 of column j + 1
     __syncthreads();
-    if (j + 1 < nb) partials(j + 1, buf ^ 1);
-    if (!grid_barrier(bar, P, err)) return;
+    if (wrp == 0) {
+      if (lane < nrem) psum[((size_t)(buf ^ 1) * P + b) * NB + lane] = sum8(lane + 1);
+      __syncwarp();
+      if (lane == 0) grid_arrive(bar);
+    }
   }
-
+  __syncthreads();
   // write back: panel rows of W (R above/on the diagonal, reflectors below)
   // and the explicit reflectors V (zero above the unit diagonal)
   for (int e = threadIdx.x; e < rows * nb; e += PT) {
@@ -192,6 +227,7 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
   }
   // tau of the panel columns for the compact-WY factor (built after the kernel)
   if (b == 0 && threadIdx.x < (unsigned)nb) tau_out[threadIdx.x] = tau_s[threadIdx.x];
+  if (threadIdx.x == 0) grid_exit(bar, (unsigned)P);
 }
 
 // T (upper triangular, nb x nb, row stride NB): T_jj = tau_j,

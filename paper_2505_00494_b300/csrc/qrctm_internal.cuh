@@ -101,38 +101,50 @@ enum : int {
   ERRF_BOUNDS = 4,       // a size check inside a kernel failed
 };
 
-// Grid-wide barrier for cooperative launches.  The spin is bounded; on
-// timeout the flag ERRF_TIMEOUT is raised and false is returned so that the
-// caller can leave the kernel.
+// Arrival counter for cooperative launches.  `count` only grows during a
+// launch: CTA b publishes its data, then adds 1; a CTA that needs round r
+// (r = 1, 2, ...) of all P CTAs waits until count >= r P.  At exit every CTA
+// adds 1 to `exit`, and the last one puts both words back to zero, so the
+// next launch starts from zero without a host-side reset.  Waits are bounded;
+// on timeout ERRF_TIMEOUT is raised and the wait returns false.
 struct GridBar {
   unsigned int count;
-  unsigned int gen;
+  unsigned int exit;
 };
 
-__device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned int nblocks, int* err) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = &bar->gen;
-    unsigned int g = *vgen;
-    __threadfence();
-    int ok = 1;
-    if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
-      long long spins = 0;
-      while (*vgen == g) {
-        if (++spins > (1ll << 25)) { ok = 0; atomicOr(err, ERRF_TIMEOUT); break; }
-        __nanosleep(20);
-      }
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Called by one thread after the CTA's published writes (ordered before it by
+// a block or warp barrier).
+__device__ __forceinline__ void grid_arrive(GridBar* bar) {
+  __threadfence();
+  atomicAdd(&bar->count, 1u);
+}
+
+// Called by one thread; true once count >= target.
+__device__ __forceinline__ bool grid_wait(GridBar* bar, unsigned int target, int* err) {
+  long long spins = 0;
+  while (ld_acquire_gpu(&bar->count) < target) {
+    if (++spins > (1ll << 25)) {
+      atomicOr(err, ERRF_TIMEOUT);
+      return false;
     }
-    __threadfence();
-    s_ok = ok;
+    if (spins > 64) __nanosleep(32);
   }
-  __syncthreads();
-  return s_ok != 0;
+  return true;
+}
+
+// Called by one thread of every CTA as its last action.
+__device__ __forceinline__ void grid_exit(GridBar* bar, unsigned int nblocks) {
+  __threadfence();
+  if (atomicAdd(&bar->exit, 1u) == nblocks - 1) {
+    atomicExch(&bar->count, 0u);
+    atomicExch(&bar->exit, 0u);
+  }
 }
 
 // ---------------------------------------------------------------------------

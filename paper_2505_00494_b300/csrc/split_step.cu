@@ -8,6 +8,8 @@
 //   X1[m,b,ub,kb,uk,kk] = sum_a Q[(a,u),m] T[b,k,a]        (FP32)
 //   Z [m,b,dk,jk,s,ub,kb] = sum_{uk,kk} X1 A[s,uk,kk,dk,jk]  (ket layer, FP32)
 //   X2[m,jk,jb,b,dk,db]  = sum_{s,ub,kb} Z A[s,ub,kb,db,jb]  (bra layer, FP32)
+//     (for even D both layers run in one fused FP32 kernel with Z on chip;
+//      otherwise as two tensor-core contractions through Z in HBM)
 //   T'[m,j,n]    = sum_{b,d} X2[m,j,(b,d)] Q[(b,d),n]      (FP64 out)
 //   Y2[n,g,j]    = sum_m T's[n,j,m] R[m,g]                 (FP32, batched over j)
 //   C'[n,p]      = sum_{(g,j)} Y2[n,(g,j)] Q[(g,j),p]      (FP64 out)
@@ -115,6 +117,12 @@ cudaError_t qr_step_split(qrctm_ctx* c) {
   }
   {
     PhaseScope ps(c, QRCTM_PH_ABSORB);
+    if (absorb_fused_ok(d, D)) {
+      // ket and bra in one pass, Z kept on chip
+      if ((e = absorb_fused(X1, c->Aket32, c->Abra32, X2, ch, D, d, D2p, dD2p, mp, c->err, st)) !=
+          cudaSuccess)
+        return e;
+    } else {
     // ket: Z[(mu,b,u_b,k_b)][(s,d_k,j_k)] stored [(mu,b)][d_k][j_k] x (s,u_b,k_b) padded dD2p
     TcGemm g = tc0(c);
     g.A = op(X1, (long long)ch * ch * D2, D2, D2p);
@@ -133,6 +141,7 @@ cudaError_t qr_step_split(qrctm_ctx* c) {
     g.c_m = im4(D, D, ch, D * mp, D, D2, D2 * mp);
     g.c_n = im2(D, mp, 1);
     if ((e = gemm_tc(g, st)) != cudaSuccess) return e;
+    }
   }
   {
     PhaseScope ps(c, QRCTM_PH_PROJECT);
