@@ -328,6 +328,180 @@ __global__ void __launch_bounds__(1024) spectrum_kernel(const double* __restrict
   }
 }
 
+// Cluster variant of the tridiagonalisation: kSpecCluster CTAs share the
+// work.  CTA r of the cluster owns the rows i = r (mod kSpecCluster) of the
+// full symmetric matrix in its shared memory.  Per column k:
+//   (a) owners publish x_i = A[i][k] (i > k); after a cluster barrier every
+//       CTA gathers x over distributed shared memory and forms v, beta
+//       redundantly (same data, same order, same result);
+//   (b) owners publish p_i = beta (A v)_i and their partial v.p; after the
+//       second barrier every CTA forms K = beta v.p / 2 and w = p - K v,
+//       then updates its own rows, A -= v w^T + w v^T.
+constexpr int kSpecCluster = 8;
+constexpr int kSpecClusterMaxN = 360;
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ double ld_dsmem(const double* local_addr, unsigned rank) {
+  unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(local_addr)), ra;
+  double v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(ra) : "memory");
+  return v;
+}
+
+__global__ void __launch_bounds__(256) spectrum_cluster_kernel(const double* __restrict__ C, int n,
+                                                               double* work, int* err) {
+  constexpr int CS = kSpecCluster;
+  extern __shared__ double csm[];
+  __shared__ double red[32];
+  __shared__ double sc[4];
+  __shared__ double pv_part;
+  const unsigned r = cluster_rank();
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wrp = tid >> 5;
+  const int nloc = (n - (int)r + CS - 1) / CS;          // rows r, r + CS, ...
+  const int nloc_max = (n + CS - 1) / CS;
+  double* Aloc = csm;                                    // [nloc_max][n]
+  double* xs = Aloc + (size_t)nloc_max * n;              // published x (own entries)
+  double* ps = xs + n;                                   // published p (own entries)
+  double* vv = ps + n;                                   // v (all entries, local copy)
+  double* ww = vv + n;                                   // w (all entries, local copy)
+  double* dg = work + (size_t)n * n;
+  double* of = dg + n;
+  double* v2 = of + 2 * n;
+  double* pb = v2 + n;
+  for (int e = tid; e < nloc * n; e += nt) {
+    const int li = e / n, j = e % n, i = (int)r + li * CS;
+    Aloc[e] = 0.5 * (C[(size_t)i * n + j] + C[(size_t)j * n + i]);
+  }
+  cluster_sync_all();
+  for (int k = 0; k + 2 < n; ++k) {
+    const int L = n - k - 1;
+    // own rows i > k: first local row index with i > k
+    const int li0 = (k + 1 - (int)r + CS - 1 < 0) ? 0 : (k + 1 - (int)r + CS - 1) / CS;
+    for (int li = li0 + tid; li < nloc; li += nt) xs[r + li * CS] = Aloc[(size_t)li * n + k];
+    if (tid == 0 && (k % CS) == (int)r) dg[k] = Aloc[(size_t)(k / CS) * n + k];
+    cluster_sync_all();                                                     // (a)
+    for (int t = tid; t < L; t += nt) {
+      const int i = k + 1 + t;
+      vv[t] = ld_dsmem(xs + i, (unsigned)(i % CS));
+    }
+    __syncthreads();
+    double sq = 0.0;
+    for (int t = tid; t < L; t += nt) sq = fma(vv[t], vv[t], sq);
+    const double nrm2 = block_sum(sq, red, &sc[3]);
+    if (tid == 0) {
+      const double x0 = vv[0];
+      if (nrm2 == 0.0) {
+        sc[1] = 0.0;
+        if (r == 0) of[k] = 0.0;
+      } else {
+        const double alpha = sqrt(nrm2);
+        const double sgn = (x0 >= 0.0) ? 1.0 : -1.0;
+        sc[0] = x0 + sgn * alpha;
+        sc[1] = 1.0 / (alpha * (alpha + fabs(x0)));
+        if (r == 0) of[k] = -sgn * alpha;
+      }
+    }
+    __syncthreads();
+    const double beta = sc[1];
+    if (beta == 0.0) {                       // same decision in every CTA of the cluster
+      cluster_sync_all();                    // x may be republished only after every gather
+      continue;
+    }
+    if (tid == 0) vv[0] = sc[0];
+    __syncthreads();
+    // p_i = beta (A v)_i for own rows i > k: a warp per row, lanes over j
+    double pv_w = 0.0;
+    for (int li = li0 + wrp; li < nloc; li += (nt >> 5)) {
+      const double* row = Aloc + (size_t)li * n + k + 1;
+      double a0 = 0.0, a1 = 0.0;
+      int t = lane;
+      for (; t + 32 < L; t += 64) {
+        a0 = fma(row[t], vv[t], a0);
+        a1 = fma(row[t + 32], vv[t + 32], a1);
+      }
+      if (t < L) a0 = fma(row[t], vv[t], a0);
+      const double pi = beta * warp_sum(a0 + a1);
+      const int i = (int)r + li * CS;
+      if (lane == 0) ps[i] = pi;
+      pv_w += pi * vv[i - k - 1];            // identical in every lane
+    }
+    if (lane == 0) red[wrp] = pv_w;
+    __syncthreads();
+    if (tid == 0) {
+      double sacc = 0.0;
+      for (int w = 0; w < (nt >> 5); ++w) sacc += red[w];
+      pv_part = sacc;
+    }
+    cluster_sync_all();                                                     // (b)
+    for (int t = tid; t < L; t += nt) {
+      const int i = k + 1 + t;
+      ww[t] = ld_dsmem(ps + i, (unsigned)(i % CS));
+    }
+    if (tid == 0) {
+      double pv = 0.0;
+      for (int q = 0; q < CS; ++q) pv += ld_dsmem(&pv_part, (unsigned)q);
+      sc[2] = 0.5 * beta * pv;
+    }
+    __syncthreads();
+    const double K = sc[2];
+    for (int t = tid; t < L; t += nt) ww[t] = fma(-K, vv[t], ww[t]);
+    __syncthreads();
+    // own rows: A[i][j] -= v_i w_j + w_i v_j  (j > k)
+    const int rows_left = nloc - li0;
+    for (int e = tid; e < rows_left * L; e += nt) {
+      const int li = li0 + e / L, t = e % L, i = (int)r + li * CS, ti = i - k - 1;
+      double* a = Aloc + (size_t)li * n + k + 1 + t;
+      *a = fma(-vv[ti], ww[t], fma(-ww[ti], vv[t], *a));
+    }
+    __syncthreads();
+  }
+  // the last 2 x 2 block
+  if (tid == 0) {
+    for (int i = n - 2; i < n; ++i)
+      if (i >= 0 && (i % CS) == (int)r) {
+        const double* row = Aloc + (size_t)(i / CS) * n;
+        dg[i] = row[i];
+        if (i == n - 1 && n >= 2) of[n - 2] = row[n - 2];
+      }
+  }
+  cluster_sync_all();
+  if (r != 0) return;
+  // squared off-diagonals, Gershgorin interval and pivot floor (CTA 0)
+  double lo_l = 1e300, hi_l = -1e300, amax = 0.0;
+  for (int i = tid; i < n; i += nt) {
+    double rr = (i > 0 ? fabs(of[i - 1]) : 0.0) + (i + 1 < n ? fabs(of[i]) : 0.0);
+    lo_l = fmin(lo_l, dg[i] - rr);
+    hi_l = fmax(hi_l, dg[i] + rr);
+    amax = fmax(amax, fmax(fabs(dg[i]), rr));
+    if (i + 1 < n) v2[i] = of[i] * of[i];
+  }
+  __shared__ double mn[32], mx[32], am[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    lo_l = fmin(lo_l, __shfl_xor_sync(0xffffffffu, lo_l, o));
+    hi_l = fmax(hi_l, __shfl_xor_sync(0xffffffffu, hi_l, o));
+    amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  }
+  if (lane == 0) { mn[wrp] = lo_l; mx[wrp] = hi_l; am[wrp] = amax; }
+  __syncthreads();
+  if (tid == 0) {
+    double lo = 1e300, hi = -1e300, big = 0.0;
+    for (int w = 0; w < (nt >> 5); ++w) { lo = fmin(lo, mn[w]); hi = fmax(hi, mx[w]); big = fmax(big, am[w]); }
+    if (!(big == big) || isinf(big)) atomicOr(err, ERRF_NUMERIC);
+    pb[0] = lo - 1e-14 * fabs(lo) - 1e-300;
+    pb[1] = hi + 1e-14 * fabs(hi) + 1e-300;
+    pb[2] = fmax(1e-300, big * 1e-300);
+  }
+}
+
 // Eigenvalue i of the tridiagonal (dg, e^2) by multisection: one warp per
 // eigenvalue (one warp per CTA, so that the Sturm recurrences of different
 // eigenvalues run on different SMs), the 32 lanes evaluate Sturm counts at 32
@@ -502,7 +676,34 @@ cudaError_t corner_spectrum(const double* C, int chi, double* work, double* s_ne
                          (int)(sizeof(double) * kSmemSpecMax * (kSmemSpecMax + 1)));
     attr = true;
   }
-  spectrum_kernel<<<1, 1024, smem, s>>>(C, chi, work, err);
+  if (chi >= 3 && chi <= kSpecClusterMaxN) {
+    const int nloc_max = (chi + kSpecCluster - 1) / kSpecCluster;
+    const size_t csmem = sizeof(double) * ((size_t)nloc_max * chi + 4 * (size_t)chi);
+    static bool cattr = false;
+    if (!cattr) {
+      cudaFuncSetAttribute(spectrum_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(double) * (((size_t)kSpecClusterMaxN + kSpecCluster - 1) /
+                                                       kSpecCluster * kSpecClusterMaxN +
+                                                   4 * (size_t)kSpecClusterMaxN)));
+      cattr = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kSpecCluster);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = csmem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kSpecCluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, spectrum_cluster_kernel, C, chi, work, err);
+    if (e != cudaSuccess) return e;
+  } else {
+    spectrum_kernel<<<1, 1024, smem, s>>>(C, chi, work, err);
+  }
   note_launch();
   double* ev = work + (size_t)chi * chi + 5 * (size_t)chi + 8;
   bisect_kernel<<<chi, 32, 0, s>>>(work, chi, ev);

@@ -71,7 +71,8 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
                                                       double* __restrict__ tau_out,
                                                       double* __restrict__ part, GridBar* bar,
                                                       int* err, int m, int j0, int nb,
-                                                      int rows_per_cta) {
+                                                      int rows_per_cta, float* __restrict__ X32,
+                                                      long long ldx, float* __restrict__ Vr32) {
   const int P = gridDim.x, b = blockIdx.x;
   const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;   // wrp = row lane (0..7)
   const long long r_begin = (long long)j0 + (long long)b * rows_per_cta;
@@ -217,13 +218,20 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
   }
   __syncthreads();
   // write back: panel rows of W (R above/on the diagonal, reflectors below)
-  // and the explicit reflectors V (zero above the unit diagonal)
+  // and the explicit reflectors V (zero above the unit diagonal); optionally
+  // FP32 copies of V for the tensor-core WY products: X32[c][i] (row c of a
+  // K-contiguous operand, row stride ldx) and Vr32[i][jc] (row stride NB)
   for (int e = threadIdx.x; e < rows * nb; e += PT) {
     const int r = e % rows, jc = e / rows;
     const long long i = r_begin + r, c = (long long)j0 + jc;
     const double x = at(i, jc);
     if (TILE) W[c * m + i] = x;
-    V[c * m + i] = (i < c) ? 0.0 : (i == c ? 1.0 : x);
+    const double v = (i < c) ? 0.0 : (i == c ? 1.0 : x);
+    V[c * m + i] = v;
+    if (X32) {
+      X32[c * ldx + i] = static_cast<float>(v);
+      Vr32[i * NB + jc] = static_cast<float>(v);
+    }
   }
   // tau of the panel columns for the compact-WY factor (built after the kernel)
   if (b == 0 && threadIdx.x < (unsigned)nb) tau_out[threadIdx.x] = tau_s[threadIdx.x];
@@ -236,10 +244,12 @@ __global__ void qr_tfactor_kernel(const double* __restrict__ G, const double* __
                                   double* __restrict__ Tf, int nb) {
   __shared__ double Gs[NB][NB + 1];
   __shared__ double Ts[NB][NB + 1];
+  __shared__ double taus[NB];
   for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
     Gs[e / nb][e % nb] = G[(e / nb) * NB + (e % nb)];
     Ts[e / nb][e % nb] = 0.0;
   }
+  for (int e = threadIdx.x; e < nb; e += blockDim.x) taus[e] = tau[e];
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
     double val = 0.0;
@@ -254,11 +264,11 @@ __global__ void qr_tfactor_kernel(const double* __restrict__ G, const double* __
         v3 = fma(Ts[i][l + 3], Gs[l + 3][j], v3);
       }
       for (; l < j; ++l) v0 = fma(Ts[i][l], Gs[l][j], v0);
-      val = -tau[j] * ((v0 + v1) + (v2 + v3));
+      val = -taus[j] * ((v0 + v1) + (v2 + v3));
     }
     __syncthreads();
     if (i < j) Ts[i][j] = val;
-    if (i == j) Ts[j][j] = tau[j];
+    if (i == j) Ts[j][j] = taus[j];
     __syncthreads();
   }
   for (int e = threadIdx.x; e < nb * nb; e += blockDim.x)
@@ -286,7 +296,7 @@ __global__ void set_identity_cols_kernel(double* Q, int m, int n) {
 // reflectors into w.V, tau and the Gram-based T factor into w.Tf (stride NB).
 // gram_tc: compute G = V^T V with the caller's contraction (nullptr = FP64).
 cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t s, double** G_out,
-                          double** tau_out) {
+                          double** tau_out, float* X32, long long ldx, float* Vr32) {
   const int mr = m - j0;
   const int P = qr_panel_grid(mr);
   int rpc = (mr + P - 1) / P;
@@ -295,7 +305,10 @@ cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t 
   double* taup = Gp + NB * NB;
   GridBar* bar = w.bar; int* err = w.err;
   int m_ = m, j0_ = j0, nb_ = nbj;
-  void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc};
+  float* x32 = X32;
+  float* vr32 = Vr32;
+  long long ldx_ = ldx;
+  void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc, &x32, &ldx_, &vr32};
   const size_t tile = sizeof(double) * (size_t)rpc * (NB + 1);
   cudaError_t e;
   if (tile <= kPanelTileMax) {

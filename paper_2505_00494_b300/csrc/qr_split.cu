@@ -2,13 +2,23 @@
 // (QR-CTMRG paragraph: unpivoted QR, diag(R) >= 0).
 //
 // The panels are factored exactly as in the FP64 path (cooperative FP64
-// panel kernel, FP64 reflector norms, Parlett's form of v_0).  The compact-WY
-// products that dominate the flop count -- the trailing updates
-// W2 <- (I - V T V^T)^T W2, the Gram matrices V^T V of the T factors and the
-// formation of Q = H_1 ... H_n [I; 0] -- run on the TF32x3 tensor-core engine
-// from FP32 copies of V and of the blocks they act on, reading and writing
-// the FP64 matrices (FP32-class accuracy, the precision of the rest of the
-// split path).
+// panel kernel, FP64 reflector norms, Parlett's form of v_0).  The
+// compact-WY products that dominate the flop count run on the TF32x3
+// tensor-core engine from FP32 copies of V and of the blocks they act on,
+// reading and writing the FP64 matrices (FP32-class accuracy, the precision
+// of the rest of the split path).  Per panel of nb reflectors:
+//
+//   1. panel kernel: V (FP64) and its FP32 copies (K-contiguous rows of X32,
+//      and Vr32 rows for the update);
+//   2. one tensor-core product  S = V^T [V | W2]  left as K-chunk partials;
+//   3. wy_prep: sums the partials (compensated FP32 summation), builds T in
+//      FP64 from G = V^T V and tau (T_12 = -T_11 G_12 T_22 by recursive
+//      doubling) and forms Y2 = T^T (V^T W2) as FP32 rows for the update;
+//   4. W2 <- W2 - V Y2 on the tensor cores, the epilogue writing the FP64
+//      W2 and the FP32 copy that the next panel's product reads.
+// Q = H_1 ... H_n [I; 0] is formed panel by panel in reverse with the same
+// three launches (T kept from step 3, Y2 = T (V^T Q_s)); its FP32 copy
+// (rows = columns of Q) is an output as well.
 #include "qrctm_internal.cuh"
 #include "tc_gemm.cuh"
 
@@ -17,128 +27,207 @@
 namespace qrctm {
 
 namespace {
+
+constexpr int NB = kQrPanel;
+constexpr int kWyThreads = 256;
+constexpr int kQrMaxKsplit = 16;   // K chunks of the V^T [.] products
+
 inline long long pad4(long long x) { return (x + 3) & ~3ll; }
+
+// part: K-chunk partials [ksplit][nb][N] of S = V^T B.
+// mode 0 (factorisation): G = S[:, 0:nb] -> T (Tp <- T by CTA 0),
+//   Yt[c][q] = (T^T S[:, ycol0 + c])[q];
+// mode 1 (formation of Q): T = Tp, Yt[c][q] = (T S[:, ycol0 + c])[q].
+// CTA b handles columns c in [32 b, 32 b + 32) of the ncol Y columns.
+__global__ void __launch_bounds__(kWyThreads) wy_prep_kernel(const float* __restrict__ part,
+                                                             int ksplit, int nb, long long N,
+                                                             int ycol0, int ncol,
+                                                             const double* __restrict__ tau,
+                                                             double* __restrict__ Tp,
+                                                             float* __restrict__ Yt, int mode) {
+  __shared__ double Ts[NB][NB + 1];
+  __shared__ double Gs[NB][NB + 1];
+  __shared__ double Ws[NB][NB + 1];
+  __shared__ float Ys[NB][NB + 1];
+  __shared__ float Tf[NB][NB + 1];
+  const int tid = threadIdx.x;
+  const int c0 = blockIdx.x * NB;
+  const long long MN = (long long)nb * N;
+  // sum of the K-chunk partials by compensated FP32 summation (Knuth's
+  // TwoSum: s + e carries the sum exactly up to the final rounding), so that
+  // the narrow FP64 pipe only sees one conversion pair and one add
+  auto psum = [&](int q, long long col) {
+    const float* p = part + (long long)q * N + col;
+    float sh = 0.f, se = 0.f;
+    for (int z = 0; z < ksplit; ++z) {
+      const float x = p[(long long)z * MN];
+      const float t = sh + x;
+      const float bp = t - sh;
+      se += (sh - (t - bp)) + (x - bp);
+      sh = t;
+    }
+    return static_cast<double>(sh) + static_cast<double>(se);
+  };
+  for (int e = tid; e < NB * NB; e += kWyThreads) {
+    const int q = e / NB, c = e % NB;
+    Ys[q][c] = (q < nb && c0 + c < ncol) ? static_cast<float>(psum(q, ycol0 + c0 + c)) : 0.f;
+    if (mode == 0) {
+      Gs[q][c] = (q < nb && c < nb) ? psum(q, c) : 0.0;
+      Ts[q][c] = (q == c && q < nb) ? tau[q] : 0.0;
+    } else {
+      Ts[q][c] = Tp[q * NB + c];
+    }
+  }
+  __syncthreads();
+  if (mode == 0) {
+    // recursive doubling over diagonal blocks of size s:
+    //   W = G_12 T_22,  T_12 = -T_11 W   (both factors upper triangular)
+    for (int s = 1; s < NB; s <<= 1) {
+      const int cnt = (NB / (2 * s)) * s * s;
+      for (int e = tid; e < cnt; e += kWyThreads) {
+        const int k = e / (s * s), i = (e / s) % s, j = e % s, b0 = 2 * s * k;
+        double acc = 0.0;
+        for (int l = 0; l <= j; ++l) acc = fma(Gs[b0 + i][b0 + s + l], Ts[b0 + s + l][b0 + s + j], acc);
+        Ws[b0 + i][b0 + s + j] = acc;
+      }
+      __syncthreads();
+      for (int e = tid; e < cnt; e += kWyThreads) {
+        const int k = e / (s * s), i = (e / s) % s, j = e % s, b0 = 2 * s * k;
+        double acc = 0.0;
+        for (int l = i; l < s; ++l) acc = fma(Ts[b0 + i][b0 + l], Ws[b0 + l][b0 + s + j], acc);
+        Ts[b0 + i][b0 + s + j] = -acc;
+      }
+      __syncthreads();
+    }
+    if (blockIdx.x == 0)
+      for (int e = tid; e < NB * NB; e += kWyThreads) Tp[e] = Ts[e / NB][e % NB];
+  }
+  // Y2 = T^T Y (mode 0) or T Y (mode 1) in FP32 (the operand precision of
+  // the tensor-core update that consumes it), written transposed
+  for (int e = tid; e < NB * NB; e += kWyThreads) Tf[e / NB][e % NB] = static_cast<float>(Ts[e / NB][e % NB]);
+  __syncthreads();
+  for (int e = tid; e < NB * NB; e += kWyThreads) {
+    const int c = e / NB, q = e % NB;
+    if (c0 + c >= ncol) continue;
+    float acc = 0.f;
+    if (mode == 0) {
+      for (int l = 0; l <= q; ++l) acc = fmaf(Tf[l][q], Ys[l][c], acc);
+    } else {
+      for (int l = q; l < NB; ++l) acc = fmaf(Tf[q][l], Ys[l][c], acc);
+    }
+    Yt[(long long)(c0 + c) * NB + q] = acc;
+  }
+}
+
+// Q = [I; 0] (FP64, column-major m x n) and its FP32 copy Q32[c][i] (stride ldq)
+__global__ void init_q_kernel(double* Q, float* Q32, int m, int n, long long ldq) {
+  const long long tot = (long long)m * n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e / m, i = e % m;
+    const double v = (i == c) ? 1.0 : 0.0;
+    Q[e] = v;
+    Q32[c * ldq + i] = static_cast<float>(v);
+  }
+}
+
 }  // namespace
 
 size_t qr_split_floats(int m, int n) {
-  const long long mp = pad4(m), npan = (n + kQrPanel - 1) / kQrPanel;
-  return (size_t)(2 * n * mp + npan * (long long)m * kQrPanel + (long long)n * kQrPanel + 1024);
+  const long long mp = pad4(m), npan = (n + NB - 1) / NB;
+  return (size_t)(n * mp + npan * (long long)m * NB + (long long)n * NB + 1024);
 }
 
+float* qr_split_x32(float* f32) { return f32; }
+
 cudaError_t householder_qr_split(int m, int n, const double* M, double* Q, double* R,
-                                 const QrWork& w, float* f32, float* part, long long part_elems,
-                                 cudaStream_t s) {
+                                 const QrWork& w, float* f32, float* Q32, bool x32_ready,
+                                 float* part, long long part_elems, cudaStream_t s) {
   if (m < n || n <= 0) return cudaErrorInvalidValue;
-  const int NB = kQrPanel;
   const long long mp = pad4(m);
   const int npan = (n + NB - 1) / NB;
-  float* V32 = f32;                                  // [q][i]   n x mp   (reflector q, row i)
-  float* X32 = V32 + (long long)n * mp;              // [c][i]   n x mp   (W2 or Q block copy)
+  float* X32 = f32;                                  // [c][i]   n x mp  (W, then V rows)
   float* Vr32 = X32 + (long long)n * mp;             // [p][i][q] npan x m x NB
   float* Yt32 = Vr32 + (long long)npan * m * NB;     // [c][q]   n x NB
-  auto tc = [&](TcGemm g) {
-    g.err = w.err;
-    g.part = part;
-    g.part_elems = part_elems;
-    return gemm_tc(g, s);
-  };
   cudaError_t e = cudaMemcpyAsync(w.W, M, sizeof(double) * (size_t)m * n,
                                   cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
+  if (!x32_ready &&
+      (e = gather_f32(M, X32, n, m, mp, im1(m), im1(1), s)) != cudaSuccess)
+    return e;
+  // S = V^T B over rows j0.. (K-chunk partials), then wy_prep
+  auto vt_times = [&](const float* Vrows, int nbj, const float* Brows, int nrows, int mr,
+                      int* ksplit) {
+    TcGemm g{};
+    g.A = TcOperand{Vrows, nbj, mr, mp, 1, 0};
+    g.B = TcOperand{Brows, nrows, mr, mp, 1, 0};
+    g.M = nbj; g.N = nrows; g.K = mr; g.batch = 1;
+    g.c_b = im0();
+    g.err = w.err;
+    g.part = part; g.part_elems = part_elems;
+    g.partials_only = true;
+    g.ksplit_out = ksplit;
+    g.max_ksplit = kQrMaxKsplit;
+    return gemm_tc(g, s);
+  };
+  // Xs -= V Y2 (FP64 block at C, FP32 copy at C32; both column-major-like)
+  auto update = [&](const float* Vrp, int mr, int nbj, int ncols, double* C, float* C32) {
+    TcGemm g{};
+    g.A = TcOperand{Vrp, mr, nbj, NB, 1, 0};
+    g.B = TcOperand{Yt32, ncols, nbj, NB, 1, 0};
+    g.M = mr; g.N = ncols; g.K = nbj; g.batch = 1;
+    g.C = C; g.c_fp64 = true; g.c_m = im1(1); g.c_n = im1(m); g.c_b = im0();
+    g.alpha = -1.0; g.beta = 1.0;
+    g.err = w.err;
+    g.C32 = C32; g.c32_m = im1(1); g.c32_n = im1(mp);
+    return gemm_tc(g, s);
+  };
+  auto wy_prep = [&](int ksplit, int nbj, long long N, int ycol0, int ncol, const double* tau,
+                     double* Tp, int mode) {
+    const unsigned grid = (unsigned)std::max(1, (ncol + NB - 1) / NB);
+    wy_prep_kernel<<<grid, kWyThreads, 0, s>>>(part, ksplit, nbj, N, ycol0, ncol, tau, Tp, Yt32,
+                                                mode);
+    note_launch();
+    return cudaGetLastError();
+  };
   for (int p = 0; p < npan; ++p) {
     const int j0 = p * NB, nbj = std::min(NB, n - j0), mr = m - j0, n2 = n - j0 - nbj;
+    float* Vrp = Vr32 + (long long)p * m * NB;
     double *G, *tau;
-    if ((e = qr_panel_step(m, j0, nbj, w, s, &G, &tau)) != cudaSuccess) return e;
+    if ((e = qr_panel_step(m, j0, nbj, w, s, &G, &tau, X32, mp, Vrp)) != cudaSuccess) return e;
+    const float* Vrows = X32 + (long long)j0 * mp + j0;
+    int ksplit = 1;
+    if ((e = vt_times(Vrows, nbj, Vrows, n - j0, mr, &ksplit)) != cudaSuccess) return e;
     double* Tp = w.Tf + (size_t)p * NB * NB;
-    // FP32 copies of this panel's reflectors: V32[j0+q][j0+i], Vr32[p][j0+i][q]
-    float* Vp = V32 + (long long)j0 * mp + j0;
-    if ((e = gather_f32(w.V + (size_t)j0 * m + j0, Vp, nbj, mr, mp, im1(m), im1(1), s)) !=
-        cudaSuccess)
-      return e;
-    float* Vrp = Vr32 + (long long)p * m * NB + (long long)j0 * NB;
-    if ((e = gather_f32(w.V + (size_t)j0 * m + j0, Vrp, mr, nbj, NB, im1(1), im1(m), s)) !=
-        cudaSuccess)
-      return e;
-    {
-      // G = V_p^T V_p (row stride NB), then T
-      TcGemm g{};
-      g.A = TcOperand{Vp, nbj, mr, mp, 1, 0};
-      g.B = TcOperand{Vp, nbj, mr, mp, 1, 0};
-      g.M = nbj; g.N = nbj; g.K = mr; g.batch = 1;
-      g.C = G; g.c_fp64 = true; g.c_m = im1(NB); g.c_n = im1(1); g.c_b = im0();
-      g.alpha = 1.0; g.beta = 0.0;
-      if ((e = tc(g)) != cudaSuccess) return e;
-      if ((e = qr_tfactor(G, tau, Tp, nbj, s)) != cudaSuccess) return e;
-    }
+    if ((e = wy_prep(ksplit, nbj, n - j0, nbj, n2, tau, Tp, 0)) != cudaSuccess) return e;
     if (n2 > 0) {
-      // X32[c][i] = W2[i, c];   Y^T[c][q] = sum_i W2[i,c] V[i,q]  -> w.Y[q][c]
-      float* Xp = X32 + j0;
-      if ((e = gather_f32(w.W + (size_t)(j0 + nbj) * m + j0, Xp, n2, mr, mp, im1(m), im1(1), s)) !=
-          cudaSuccess)
+      if ((e = update(Vrp + (long long)j0 * NB, mr, nbj, n2, w.W + (size_t)(j0 + nbj) * m + j0,
+                      X32 + (long long)(j0 + nbj) * mp + j0)) != cudaSuccess)
         return e;
-      TcGemm g{};
-      g.A = TcOperand{Xp, n2, mr, mp, 1, 0};
-      g.B = TcOperand{Vp, nbj, mr, mp, 1, 0};
-      g.M = n2; g.N = nbj; g.K = mr; g.batch = 1;
-      g.C = w.Y; g.c_fp64 = true; g.c_m = im1(1); g.c_n = im1(n2); g.c_b = im0();
-      g.alpha = 1.0; g.beta = 0.0;
-      if ((e = tc(g)) != cudaSuccess) return e;
-      // Y2 = T^T Y  (FP64, nbj x n2)
-      Gemm h = gemm_init();
-      h.M = nbj; h.N = n2; h.K = nbj;
-      h.A = Tp; h.a_m = im1(1); h.a_k = im1(NB);
-      h.B = w.Y; h.b_k = im1(n2); h.b_n = im1(1);
-      h.C = w.Y2; h.c_m = im1(n2); h.c_n = im1(1);
-      if ((e = gemm_f64(h, s)) != cudaSuccess) return e;
-      // Yt32[c][q] = Y2[q][c];  W2[i,c] -= sum_q V[i,q] Y2[q,c]
-      if ((e = gather_f32(w.Y2, Yt32, n2, nbj, NB, im1(1), im1(n2), s)) != cudaSuccess) return e;
-      g = TcGemm{};
-      g.A = TcOperand{Vrp, mr, nbj, NB, 1, 0};
-      g.B = TcOperand{Yt32, n2, nbj, NB, 1, 0};
-      g.M = mr; g.N = n2; g.K = nbj; g.batch = 1;
-      g.C = w.W + (size_t)(j0 + nbj) * m + j0; g.c_fp64 = true;
-      g.c_m = im1(1); g.c_n = im1(m); g.c_b = im0();
-      g.alpha = -1.0; g.beta = 1.0;
-      if ((e = tc(g)) != cudaSuccess) return e;
     }
   }
   if ((e = qr_extract_r(w.W, R, m, n, s)) != cudaSuccess) return e;
   // Q = H_1 ... H_n [I; 0], panels in reverse order
-  if ((e = set_identity_cols(Q, m, n, s)) != cudaSuccess) return e;
+  {
+    const long long tot = (long long)m * n;
+    init_q_kernel<<<(unsigned)std::min<long long>((tot + 255) / 256, 8192), 256, 0, s>>>(Q, Q32, m,
+                                                                                         n, mp);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   for (int p = npan - 1; p >= 0; --p) {
     const int j0 = p * NB, nbj = std::min(NB, n - j0), mr = m - j0, nq = n - j0;
-    const double* Tp = w.Tf + (size_t)p * NB * NB;
-    const float* Vp = V32 + (long long)j0 * mp + j0;
+    const float* Vrows = X32 + (long long)j0 * mp + j0;
     const float* Vrp = Vr32 + (long long)p * m * NB + (long long)j0 * NB;
-    float* Xp = X32 + j0;
-    // X32[c][i] = Q[j0+i, j0+c];  Y^T = Qs^T V  -> w.Y[q][c]
-    if ((e = gather_f32(Q + (size_t)j0 * m + j0, Xp, nq, mr, mp, im1(m), im1(1), s)) !=
+    int ksplit = 1;
+    if ((e = vt_times(Vrows, nbj, Q32 + (long long)j0 * mp + j0, nq, mr, &ksplit)) != cudaSuccess)
+      return e;
+    if ((e = wy_prep(ksplit, nbj, nq, 0, nq, nullptr, w.Tf + (size_t)p * NB * NB, 1)) !=
         cudaSuccess)
       return e;
-    TcGemm g{};
-    g.A = TcOperand{Xp, nq, mr, mp, 1, 0};
-    g.B = TcOperand{Vp, nbj, mr, mp, 1, 0};
-    g.M = nq; g.N = nbj; g.K = mr; g.batch = 1;
-    g.C = w.Y; g.c_fp64 = true; g.c_m = im1(1); g.c_n = im1(nq); g.c_b = im0();
-    g.alpha = 1.0; g.beta = 0.0;
-    if ((e = tc(g)) != cudaSuccess) return e;
-    // Y2 = T Y
-    Gemm h = gemm_init();
-    h.M = nbj; h.N = nq; h.K = nbj;
-    h.A = Tp; h.a_m = im1(NB); h.a_k = im1(1);
-    h.B = w.Y; h.b_k = im1(nq); h.b_n = im1(1);
-    h.C = w.Y2; h.c_m = im1(nq); h.c_n = im1(1);
-    if ((e = gemm_f64(h, s)) != cudaSuccess) return e;
-    if ((e = gather_f32(w.Y2, Yt32, nq, nbj, NB, im1(1), im1(nq), s)) != cudaSuccess) return e;
-    // Qs -= V Y2
-    g = TcGemm{};
-    g.A = TcOperand{Vrp, mr, nbj, NB, 1, 0};
-    g.B = TcOperand{Yt32, nq, nbj, NB, 1, 0};
-    g.M = mr; g.N = nq; g.K = nbj; g.batch = 1;
-    g.C = Q + (size_t)j0 * m + j0; g.c_fp64 = true;
-    g.c_m = im1(1); g.c_n = im1(m); g.c_b = im0();
-    g.alpha = -1.0; g.beta = 1.0;
-    if ((e = tc(g)) != cudaSuccess) return e;
+    if ((e = update(Vrp, mr, nbj, nq, Q + (size_t)j0 * m + j0, Q32 + (long long)j0 * mp + j0)) !=
+        cudaSuccess)
+      return e;
   }
   return cudaSuccess;
 }

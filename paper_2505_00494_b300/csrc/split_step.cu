@@ -88,17 +88,19 @@ cudaError_t qr_step_split(qrctm_ctx* c) {
     g.M = ch; g.N = m; g.K = ch;
     g.C = c->Mcm; g.c_fp64 = true;
     g.c_m = im1(D2); g.c_n = im2(D2, 1, m);
+    // FP32 copy for the QR's tensor-core products: row b, K index (a, i)
+    g.C32 = qr_split_x32(c->qr32);
+    g.c32_m = im1(D2); g.c32_n = im2(D2, 1, mp);
     if ((e = gemm_tc(g, st)) != cudaSuccess) return e;
   }
   {
     PhaseScope ps(c, QRCTM_PH_QR);
-    if ((e = householder_qr_split((int)m, ch, c->Mcm, c->Q, c->R, c->qrw, c->qr32, c->tc_part,
-                                  c->tc_part_elems, st)) != cudaSuccess)
+    // Q, R in FP64 and Qc32[n][(b,d)] = Q[(b,d),n] from the QR itself
+    if ((e = householder_qr_split((int)m, ch, c->Mcm, c->Q, c->R, c->qrw, c->qr32, Qc32, true,
+                                  c->tc_part, c->tc_part_elems, st)) != cudaSuccess)
       return e;
-    // Qt32[(mu,u)][a] = Q[(a,u),mu];  Qc32[n][(b,d)] = Q[(b,d),n]
+    // Qt32[(mu,u)][a] = Q[(a,u),mu]
     if ((e = gather_f32(c->Q, Qt32, m, ch, chp, im2(D2, 1, m), im1(D2), st)) != cudaSuccess)
-      return e;
-    if ((e = gather_f32(c->Q, Qc32, ch, (int)m, mp, im1(m), im1(1), st)) != cudaSuccess)
       return e;
   }
   {

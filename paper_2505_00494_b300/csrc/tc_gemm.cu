@@ -148,7 +148,7 @@ struct Cfg {
   // main accumulator at column 0, correction accumulator at column HALF
   static constexpr int HALF = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
   static constexpr int TMEM_COLS = 2 * HALF;
-  static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + 1024 + BN * 8;
+  static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + 1024 + 2 * BN * 8;
 };
 
 template <int BN>
@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ctrl + 8 * (3 * S + 1));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(ctrl + 8 * (3 * S + 1) + 8);
   long long* col_off = reinterpret_cast<long long*>(ctrl + 1024);
+  long long* col_off32 = col_off + BN;
 
   auto xA = [&](int s) { return tiles + s * C::STAGE_BYTES; };
   auto loA = [&](int s) { return tiles + s * C::STAGE_BYTES + C::A_BYTES; };
@@ -280,6 +281,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int j = t; j < BN; j += 128) {
       const long long n = (long long)n0 + j;
       col_off[j] = (n < args.N) ? map_off(args.c_n, n) : 0;
+      if (args.C32) col_off32[j] = (n < args.N) ? map_off(args.c32_n, n) : 0;
     }
     asm volatile("bar.sync 1, 128;" ::: "memory");
     const bool ok = mbar_wait(accf, 0, abort_flag, args.err);
@@ -289,10 +291,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int row = q * 32 + lane;
       const long long m = (long long)m0 + row;
       const bool mvalid = m < args.M;
-      const bool split = args.ksplit > 1;
+      const bool split = args.ksplit > 1 || args.partials_only;
       const long long base_off =
           split ? (((long long)z * args.ksplit + kz) * args.M + (mvalid ? m : 0)) * args.N
                 : map_off(args.c_b, z) + (mvalid ? map_off(args.c_m, m) : 0);
+      const long long row32 = (args.C32 && mvalid) ? map_off(args.c32_m, m) : 0;
 #pragma unroll 1
       for (int c = 0; c < (BN + 31) / 32; ++c) {
         float v[32], w[32];
@@ -309,23 +312,43 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           continue;
         }
+        // all loads of the old values first (they would otherwise wait on
+        // the stores before them), then the results
+        const int nv = min(32, min(BN - c * 32, (int)(args.N - n0 - c * 32)));
+        double r[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          v[j] += w[j];
-          const int jj = c * 32 + j;
-          if (jj >= BN || (long long)n0 + jj >= args.N) continue;
-          const long long off = base_off + col_off[jj];
+        for (int j = 0; j < 32; ++j) r[j] = args.alpha * static_cast<double>(v[j] + w[j]);
+        if (args.beta != 0.0) {
+          double old[32];
           if (args.c_fp64) {
-            double* p = static_cast<double*>(args.C) + off;
-            double r = args.alpha * static_cast<double>(v[j]);
-            if (args.beta != 0.0) r += args.beta * *p;
-            *p = r;
+            const double* p = static_cast<const double*>(args.C) + base_off;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) old[j] = (j < nv) ? p[col_off[c * 32 + j]] : 0.0;
           } else {
-            float* p = static_cast<float*>(args.C) + off;
-            double r = args.alpha * static_cast<double>(v[j]);
-            if (args.beta != 0.0) r += args.beta * static_cast<double>(*p);
-            *p = static_cast<float>(r);
+            const float* p = static_cast<const float*>(args.C) + base_off;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              old[j] = (j < nv) ? static_cast<double>(p[col_off[c * 32 + j]]) : 0.0;
           }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) r[j] = fma(args.beta, old[j], r[j]);
+        }
+        if (args.c_fp64) {
+          double* p = static_cast<double*>(args.C) + base_off;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (j < nv) p[col_off[c * 32 + j]] = r[j];
+          if (args.C32) {
+            float* p32 = args.C32 + row32;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < nv) p32[col_off32[c * 32 + j]] = static_cast<float>(r[j]);
+          }
+        } else {
+          float* p = static_cast<float*>(args.C) + base_off;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (j < nv) p[col_off[c * 32 + j]] = static_cast<float>(r[j]);
         }
       }
     }
@@ -374,6 +397,7 @@ __global__ void tc_splitk_reduce(const TcArgs a, int batch) {
       double* o = static_cast<double*>(a.C) + off;
       if (a.beta != 0.0) v += a.beta * *o;
       *o = v;
+      if (a.C32) a.C32[map_off(a.c32_m, m) + map_off(a.c32_n, n)] = static_cast<float>(v);
     } else {
       float* o = static_cast<float*>(a.C) + off;
       if (a.beta != 0.0) v += a.beta * static_cast<double>(*o);
@@ -460,20 +484,32 @@ cudaError_t launch_bn(const TcGemm& g, cudaStream_t s) {
     want = std::min<long long>(want, nkb / 2);
     const long long cap = g.part_elems / (g.M * g.N * std::max(1, g.batch));
     want = std::min<long long>(want, cap);
+    if (g.max_ksplit > 0) want = std::min<long long>(want, g.max_ksplit);
     if (want > 1) {
       kbps = (int)((nkb + want - 1) / want);
       ksplit = (nkb + kbps - 1) / kbps;
     }
   }
+  if (g.partials_only) {
+    if (g.part == nullptr ||
+        (long long)ksplit * g.M * g.N * std::max(1, g.batch) > g.part_elems)
+      return cudaErrorInvalidValue;
+    if (g.ksplit_out) *g.ksplit_out = ksplit;
+  }
+  if (g.C32 != nullptr && (!g.c_fp64 || g.batch > 1)) return cudaErrorInvalidValue;
   a.ksplit = ksplit;
   a.kb_per_split = kbps;
   a.part = g.part;
+  a.partials_only = g.partials_only ? 1 : 0;
+  a.C32 = g.C32;
+  a.c32_m = g.c32_m;
+  a.c32_n = g.c32_n;
   if ((long long)std::max(1, g.batch) * ksplit > 65535) return cudaErrorInvalidValue;
   dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + BN - 1) / BN),
             (unsigned)(std::max(1, g.batch) * ksplit));
   tc_tf32x3_kernel<BN><<<grid, NTHREADS, C::SMEM, s>>>(ta, tb, a);
   note_launch();
-  if (ksplit > 1) {
+  if (ksplit > 1 && !g.partials_only) {
     const long long tot = g.M * g.N * std::max(1, g.batch);
     tc_splitk_reduce<<<(unsigned)std::min<long long>((tot + 255) / 256, 4096), 256, 0, s>>>(
         a, std::max(1, g.batch));

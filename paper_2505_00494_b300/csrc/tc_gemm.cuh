@@ -32,6 +32,16 @@ struct TcGemm {
   // ranges are cut into chunks of at most 512 that are summed in FP64
   float* part;
   long long part_elems;
+  // partials_only: write the raw K-chunk partials part[b][z][m][n] (always,
+  // even for one chunk) and skip the reduction; *ksplit_out gets the number
+  // of chunks.  The consumer sums them.  C, alpha, beta are ignored.
+  bool partials_only;
+  int* ksplit_out;
+  int max_ksplit;      // cap on the number of K chunks (0 = no cap)
+  // optional FP32 copy of the final FP64 result (c_fp64 only, no batch):
+  // C32[c32_m(m) + c32_n(n)] = (float) D(m, n)
+  float* C32;
+  IdxMap c32_m, c32_n;
 };
 
 // Kernel arguments (device side).
@@ -45,7 +55,10 @@ struct TcArgs {
   int* err;
   int ksplit;          // K chunks per output tile (1 = no split)
   int kb_per_split;    // 32-wide K blocks per chunk
-  float* part;         // ksplit > 1: partials [batch][ksplit][M][N]
+  float* part;         // ksplit > 1 or partials_only: partials [batch][ksplit][M][N]
+  int partials_only;
+  float* C32;          // optional FP32 copy of the FP64 result
+  IdxMap c32_m, c32_n;
 };
 
 cudaError_t gemm_tc(const TcGemm& g, cudaStream_t s);
