@@ -163,7 +163,21 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
   } else if (carve) {
     c->G = nullptr; c->G_bytes = 0;
   }
-  if (carve) c->split_layers = split;
+  // FP32 operand copies for the split-precision energy and adjoint
+  // contractions: the largest one pairs a d^2-batched (chi D^2)^2 operand
+  // with an unbatched one
+  if (cfg.precision == QRCTM_SPLIT) {
+    const size_t mm = m * m, floats = (d * d + 2) * mm + (size_t(1) << 20);
+    size_t o = off;
+    off += al(sizeof(float) * floats);
+    if (carve) { c->mm32 = reinterpret_cast<float*>(c->ws + o); c->mm32_floats = floats; }
+  } else if (carve) {
+    c->mm32 = nullptr; c->mm32_floats = 0;
+  }
+  if (carve) {
+    c->split_layers = split;
+    c->mm_split = false;   // set for the duration of a split-precision gradient
+  }
   return off;
 }
 
@@ -448,7 +462,11 @@ qrctm_status qrctm_energy_grad(qrctm_ctx* c, const qrctm_model* model, int mode,
   double resid = 0.0;
   {
     PhaseScope ps(c, QRCTM_PH_GRAD);
+    // a split-precision context runs the contractions of the taped steps, of
+    // the energy and of every reverse pass on the TF32x3 engine
+    c->mm_split = c->split_prec && c->mm32 != nullptr;
     e = energy_grad_run(c, model->J1, model->J2, mode, k_unroll, grad, e_out, &iters, &resid);
+    c->mm_split = false;
   }
   c->grad_iters = iters;
   c->grad_resid = resid;

@@ -43,6 +43,10 @@ struct qrctm_ctx {
   int iters;
   int grad_iters;
   double grad_resid;
+  // split-precision contractions of the energy and adjoint passes
+  bool mm_split;
+  float* mm32;
+  size_t mm32_floats;
   double last_delta;
   bool have_env;
   bool spec_valid;
@@ -74,6 +78,11 @@ inline Gemm gemm_ctx(qrctm_ctx* c) {
   g.part_elems = kSplitKElems;
   return g;
 }
+
+// Contraction of the energy / adjoint passes: split precision (TF32x3 on the
+// tensor cores from gathered FP32 operands) when c->mm_split, else FP64.
+cudaError_t gemm_run(qrctm_ctx* c, const Gemm& g);
+size_t mm_split_floats(const Gemm& g);
 
 // Workspace plan (api.cu); 256-byte aligned regions.
 size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* ctx);

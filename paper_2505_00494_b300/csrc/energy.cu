@@ -84,7 +84,7 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
     g.A = c->Mcm; g.a_m = im1(1); g.a_k = im1(m);
     g.B = c->C; g.b_k = im1(ch); g.b_n = im1(1);
     g.C = c->Y2; g.c_m = im1(ch); g.c_n = im1(1);
-    if ((e = gemm_f64(g, st)) != cudaSuccess) return e;
+    if ((e = gemm_run(c, g)) != cudaSuccess) return e;
   }
   // W[(q,z1),(p,X)] = sum_x1 L1[x1,q,z1] T[x1,p,X]
   {
@@ -93,7 +93,7 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
     g.A = c->Y2; g.a_m = im1(1); g.a_k = im1(m);
     g.B = c->T; g.b_k = im1(m); g.b_n = im1(1);
     g.C = c->X1; g.c_m = im1(m); g.c_n = im1(1);
-    if ((e = gemm_f64(g, st)) != cudaSuccess) return e;
+    if ((e = gemm_run(c, g)) != cudaSuccess) return e;
   }
   // ket: Z1[(z1,X,q_b,p_b),(s,d_k,h_k)] = sum_{p_k,q_k} W A[s,p_k,q_k,d_k,h_k]
   {
@@ -102,7 +102,7 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
     g.A = c->X1; g.a_m = im4(D, D, ch, ch, Sq, 1, m); g.a_k = im2(D, D * Sq, (long long)D * ch);
     g.B = c->A; g.b_k = im2(D, D2, D3); g.b_n = im3(D, D, 1, D, D4);
     g.C = c->Z; g.c_m = im1(dD2); g.c_n = im1(1);
-    if ((e = gemm_f64(g, st)) != cudaSuccess) return e;
+    if ((e = gemm_run(c, g)) != cudaSuccess) return e;
   }
   // bra (physical index t open): Z2 stored [X][s][t][h_k][h_b][z1][d_k][d_b]
   {
@@ -115,7 +115,7 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
     g.c_m = im5(D, D, d, ch, (long long)D * D2c, D, (long long)d * D4c,
                 (long long)d * d * D4c, D2);
     g.c_n = im3(D, D, D2c, 1, D4c);
-    if ((e = gemm_f64(g, st)) != cudaSuccess) return e;
+    if ((e = gemm_run(c, g)) != cudaSuccess) return e;
   }
   // HL[(X,s,t,h),Z] = sum_{(z1,d)} Z2[X,s,t,h,(z1,d)] T[(z1,d),Z]
   {
@@ -124,7 +124,7 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
     g.A = c->E1; g.a_m = im1(m); g.a_k = im1(1);
     g.B = c->T; g.b_k = im1(ch); g.b_n = im1(1);
     g.C = c->E2; g.c_m = im1(ch); g.c_n = im1(1);
-    if ((e = gemm_f64(g, st)) != cudaSuccess) return e;
+    if ((e = gemm_run(c, g)) != cudaSuccess) return e;
   }
   // rho_nn[(s1,t1),(s2,t2)] = sum_{X,h,Z} HL[X,s1,t1,h,Z] HL[X,s2,t2,h,Z]
   {
@@ -134,7 +134,7 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
     g.A = c->E2; g.a_m = im1(st_str); g.a_k = im3(ch, D2, 1, ch, (long long)d * d * D2 * ch);
     g.B = c->E2; g.b_k = im3(ch, D2, 1, ch, (long long)d * d * D2 * ch); g.b_n = im1(st_str);
     g.C = c->rho; g.c_m = im1(d * d); g.c_n = im1(1);
-    if ((e = gemm_f64(g, st)) != cudaSuccess) return e;
+    if ((e = gemm_run(c, g)) != cudaSuccess) return e;
   }
   double* rho_nnn = nullptr;
   if (J2 != 0.0) {
@@ -148,13 +148,13 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
       g.A = c->Mcm; g.a_m = im2(ch, m, 1); g.a_k = im1(D2);
       g.B = c->T; g.b_k = im1(m); g.b_n = im1(1);
       g.C = c->X1; g.c_m = im1(m); g.c_n = im1(1);
-      if ((e = gemm_f64(g, st)) != cudaSuccess) return e;
+      if ((e = gemm_run(c, g)) != cudaSuccess) return e;
       g = gemm_ctx(c);
       g.M = (long long)ch * ch * D2; g.N = dD2; g.K = D2;
       g.A = c->X1; g.a_m = im4(D, D, ch, Sk, Su, 1, Smu); g.a_k = im2(D, D * Sk, D * Su);
       g.B = c->A; g.b_k = im2(D, D2, D3); g.b_n = im3(D, D, 1, D, D4);
       g.C = c->Z; g.c_m = im1(dD2); g.c_n = im1(1);
-      if ((e = gemm_f64(g, st)) != cudaSuccess) return e;
+      if ((e = gemm_run(c, g)) != cudaSuccess) return e;
     }
     // bra with t open: Ct_open stored [s][t][b][l_k][l_b][r][j_k][j_b]
     {
@@ -166,7 +166,7 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
       g.C = c->E1;
       g.c_m = im5(D, D, d, ch, D, D * m, (long long)d * mm, (long long)D2 * m, D2);
       g.c_n = im3(D, D, 1, m, mm);
-      if ((e = gemm_f64(g, st)) != cudaSuccess) return e;
+      if ((e = gemm_run(c, g)) != cudaSuccess) return e;
       trace_phys_k<<<1184, 256, 0, st>>>(c->E1, c->X2, d, mm);
       note_launch();
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -176,14 +176,14 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
       g.A = c->E1; g.a_m = im1(m); g.a_k = im1(1); g.a_b = im1(mm);
       g.B = c->X2; g.b_k = im1(m); g.b_n = im1(1); g.b_b = im0();
       g.C = c->E3; g.c_m = im1(m); g.c_n = im1(1); g.c_b = im1(mm);
-      if ((e = gemm_f64(g, st)) != cudaSuccess) return e;
+      if ((e = gemm_run(c, g)) != cudaSuccess) return e;
       // rho_nnn[(s1,t1),(s4,t4)] = sum_{a,c} P(s1,t1)[a,c] P(s4,t4)[c,a]
       g = gemm_ctx(c);
       g.M = d * d; g.N = d * d; g.K = mm;
       g.A = c->E3; g.a_m = im1(mm); g.a_k = im1(1);
       g.B = c->E3; g.b_k = im2((int)m, m, 1); g.b_n = im1(mm);
       g.C = rho_nnn; g.c_m = im1(d * d); g.c_n = im1(1);
-      if ((e = gemm_f64(g, st)) != cudaSuccess) return e;
+      if ((e = gemm_run(c, g)) != cudaSuccess) return e;
     }
   }
   energy_k<<<1, 1, 0, st>>>(c->rho, rho_nnn, J1, J2, c->e_d, c->err);

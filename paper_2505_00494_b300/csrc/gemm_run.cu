@@ -1,0 +1,92 @@
+// Contraction dispatch for the energy and the adjoint passes.
+//
+// Every contraction of the reduced density matrices and of the reverse
+// passes is described once, as an FP64 descriptor with index maps (Gemm).
+// A context in split precision runs them on the TF32x3 tensor-core engine:
+// each operand is gathered through its maps into a K-contiguous FP32 copy
+// (row stride padded to 16 bytes, batch-major), the product accumulates on
+// the tensor cores, and the epilogue writes the FP64 result through the
+// descriptor's output maps with alpha and beta.  Traces and the energy
+// reduction that follow stay in FP64, and so do contractions with a thin
+// output (fewer than 16 rows or columns: long reductions into a few numbers,
+// memory bound).  An FP64 context runs every descriptor on the FP64
+// CUDA-core engine.
+#include "ctx.cuh"
+#include "tc_gemm.cuh"
+
+#include <algorithm>
+
+namespace qrctm {
+
+namespace {
+
+inline long long pad4(long long x) { return (x + 3) & ~3ll; }
+
+bool zero_map(const IdxMap& m) {
+  for (int t = 0; t < m.nd; ++t)
+    if (m.str[t] != 0) return false;
+  return true;
+}
+
+// out[b][r][k] (row stride ldk, batch stride ldb) = in[bm(b) + rm(r) + km(k)]
+__global__ void gather3_f32_k(const double* __restrict__ in, float* __restrict__ out, long long nb,
+                              long long nr, long long nk, long long ldk, long long ldb,
+                              IdxMap bm, IdxMap rm, IdxMap km) {
+  const long long tot = nb * nr * nk;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long k = e % nk, rb = e / nk, r = rb % nr, b = rb / nr;
+    out[b * ldb + r * ldk + k] =
+        static_cast<float>(in[map_off(bm, b) + map_off(rm, r) + map_off(km, k)]);
+  }
+}
+
+cudaError_t gather3(const double* in, float* out, long long nb, long long nr, long long nk,
+                    long long ldk, const IdxMap& bm, const IdxMap& rm, const IdxMap& km,
+                    cudaStream_t s) {
+  const long long tot = nb * nr * nk;
+  if (tot <= 0) return cudaSuccess;
+  gather3_f32_k<<<(unsigned)std::min<long long>((tot + 255) / 256, 16384), 256, 0, s>>>(
+      in, out, nb, nr, nk, ldk, nr * ldk, bm, rm, km);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t mm_split_floats(const Gemm& g) {
+  const long long Ka = pad4(g.K), B = std::max(1, g.batch);
+  const long long nbA = zero_map(g.a_b) ? 1 : B, nbB = zero_map(g.b_b) ? 1 : B;
+  return (size_t)(Ka * (nbA * g.M + nbB * g.N));
+}
+
+cudaError_t gemm_run(qrctm_ctx* c, const Gemm& g) {
+  // contractions with a thin output (a reduction over a long index into a
+  // few numbers, memory bound) or whose operand copies would not fit the
+  // scratch stay on the FP64 engine
+  if (!c->mm_split || std::min(g.M, g.N) < 16 || mm_split_floats(g) > c->mm32_floats)
+    return gemm_f64(g, c->st);
+  if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
+  const long long Ka = pad4(g.K), B = std::max(1, g.batch);
+  const bool shA = zero_map(g.a_b), shB = zero_map(g.b_b);
+  const long long nbA = shA ? 1 : B, nbB = shB ? 1 : B;
+  float* A32 = c->mm32;
+  float* B32 = A32 + pad4(nbA * g.M * Ka);
+  cudaError_t e;
+  if ((e = gather3(g.A, A32, nbA, g.M, g.K, Ka, g.a_b, g.a_m, g.a_k, c->st)) != cudaSuccess)
+    return e;
+  if ((e = gather3(g.B, B32, nbB, g.N, g.K, Ka, g.b_b, g.b_n, g.b_k, c->st)) != cudaSuccess)
+    return e;
+  TcGemm t{};
+  t.A = TcOperand{A32, g.M, g.K, Ka, (int)nbA, g.M * Ka};
+  t.B = TcOperand{B32, g.N, g.K, Ka, (int)nbB, g.N * Ka};
+  t.M = g.M; t.N = g.N; t.K = g.K; t.batch = (int)B;
+  t.C = g.C; t.c_fp64 = true;
+  t.c_m = g.c_m; t.c_n = g.c_n; t.c_b = g.c_b;
+  t.alpha = g.alpha; t.beta = g.beta;
+  t.err = c->err;
+  t.part = c->tc_part; t.part_elems = c->tc_part_elems;
+  return gemm_tc(t, c->st);
+}
+
+}  // namespace qrctm

@@ -116,11 +116,6 @@ size_t layout(int d, int D, int chi, bool nnn, char* base, GradLayout* L) {
 
 inline unsigned nb256(long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 8192); }
 
-__global__ void axpy_k(double* y, const double* x, double a, long long n) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    y[i] += a * x[i];
-}
 
 __global__ void add_diag_phys_k(double* Co_bar, const double* Ct_bar, int d, long long mm) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < mm;
@@ -209,16 +204,16 @@ static cudaError_t step_fwd_tape(qrctm_ctx* c, const double* Cin, const double* 
       (e = cudaMemcpyAsync(t.Tin, Tin, sizeof(double) * k.m * k.ch, cudaMemcpyDeviceToDevice,
                            s)) != cudaSuccess)
     return e;
-  if ((e = gemm_f64(g_ct(c, k, t.Cin, t.Tin, t.ct), s)) != cudaSuccess) return e;
+  if ((e = gemm_run(c, g_ct(c, k, t.Cin, t.Tin, t.ct))) != cudaSuccess) return e;
   if ((e = householder_qr_f64((int)k.m, k.ch, t.ct, t.Q, t.R, c->qrw, s)) != cudaSuccess) return e;
   if ((e = triu_inverse(t.R, t.Rinv, k.ch, c->err, s)) != cudaSuccess) return e;
-  if ((e = gemm_f64(g_x1(c, k, t.Q, t.Tin, t.X1), s)) != cudaSuccess) return e;
-  if ((e = gemm_f64(g_ket(c, k, t.X1, c->A, t.Z), s)) != cudaSuccess) return e;
-  if ((e = gemm_f64(g_bra(c, k, t.Z, c->A, t.X2), s)) != cudaSuccess) return e;
-  if ((e = gemm_f64(g_proj(c, k, t.X2, t.Q, t.Traw), s)) != cudaSuccess) return e;
+  if ((e = gemm_run(c, g_x1(c, k, t.Q, t.Tin, t.X1))) != cudaSuccess) return e;
+  if ((e = gemm_run(c, g_ket(c, k, t.X1, c->A, t.Z))) != cudaSuccess) return e;
+  if ((e = gemm_run(c, g_bra(c, k, t.Z, c->A, t.X2))) != cudaSuccess) return e;
+  if ((e = gemm_run(c, g_proj(c, k, t.X2, t.Q, t.Traw))) != cudaSuccess) return e;
   if ((e = sym_edge(t.Traw, t.Ts, k.ch, k.D2, s)) != cudaSuccess) return e;
-  if ((e = gemm_f64(g_y2(c, k, t.Ts, t.R, t.Y2), s)) != cudaSuccess) return e;
-  if ((e = gemm_f64(g_craw(c, k, t.Y2, t.Q, t.Craw), s)) != cudaSuccess) return e;
+  if ((e = gemm_run(c, g_y2(c, k, t.Ts, t.R, t.Y2))) != cudaSuccess) return e;
+  if ((e = gemm_run(c, g_craw(c, k, t.Y2, t.Q, t.Craw))) != cudaSuccess) return e;
   return sym_norm_env(t.Craw, t.Ts, t.Cout, t.Tout, k.ch, k.D2, t.parts, c->err, s);
 }
 
@@ -323,7 +318,7 @@ static cudaError_t energy_vjp(qrctm_ctx* c, const GradLayout& L, const double* C
   f_rho.C = rho; f_rho.c_m = im1(d * d); f_rho.c_n = im1(1);
   const Gemm* fwd[] = {&f_ct, &f_l1, &f_w, &f_ket, &f_bra, &f_hl, &f_rho};
   for (const Gemm* g : fwd)
-    if ((e = gemm_f64(*g, s)) != cudaSuccess) return e;
+    if ((e = gemm_run(c, *g)) != cudaSuccess) return e;
   // ---- reverse (2x1 patch): E_nn = 2 J1 Tr(rho h~)/Tr(rho) ----
   double* ctb = L.ctb;
   rho_bar_k<<<1, 32, 0, s>>>(rho, 0, 2.0 * J1, L.rhob);
@@ -363,13 +358,13 @@ static cudaError_t energy_vjp(qrctm_ctx* c, const GradLayout& L, const double* C
     f_rn.A = P; f_rn.a_m = im1(mm); f_rn.a_k = im1(1);
     f_rn.B = P; f_rn.b_k = im2((int)m, m, 1); f_rn.b_n = im1(mm);
     f_rn.C = rho_nnn; f_rn.c_m = im1(d * d); f_rn.c_n = im1(1);
-    if ((e = gemm_f64(f_x, s)) != cudaSuccess) return e;
-    if ((e = gemm_f64(f_keto, s)) != cudaSuccess) return e;
-    if ((e = gemm_f64(f_brao, s)) != cudaSuccess) return e;
+    if ((e = gemm_run(c, f_x)) != cudaSuccess) return e;
+    if ((e = gemm_run(c, f_keto)) != cudaSuccess) return e;
+    if ((e = gemm_run(c, f_brao)) != cudaSuccess) return e;
     trace_phys2_k<<<1184, 256, 0, s>>>(Co, Ct, d, mm);
     note_launch();
-    if ((e = gemm_f64(f_P, s)) != cudaSuccess) return e;
-    if ((e = gemm_f64(f_rn, s)) != cudaSuccess) return e;
+    if ((e = gemm_run(c, f_P)) != cudaSuccess) return e;
+    if ((e = gemm_run(c, f_rn)) != cudaSuccess) return e;
     // ---- reverse (2x2 patch) ----
     rho_bar_k<<<1, 32, 0, s>>>(rho_nnn, 1, 2.0 * J2, L.rhob + 16);
     note_launch();

@@ -63,7 +63,7 @@ cudaError_t gemm_vjp(qrctm_ctx* c, const Gemm& f, const double* Dbar, double* Ab
     }
     g.alpha = f.alpha;
     g.beta = accA ? 1.0 : 0.0;
-    if ((e = gemm_f64(g, c->st)) != cudaSuccess) return e;
+    if ((e = gemm_run(c, g)) != cudaSuccess) return e;
   }
   if (Bbar) {
     Gemm g = gemm_ctx(c);
@@ -82,7 +82,7 @@ cudaError_t gemm_vjp(qrctm_ctx* c, const Gemm& f, const double* Dbar, double* Ab
     }
     g.alpha = f.alpha;
     g.beta = accB ? 1.0 : 0.0;
-    if ((e = gemm_f64(g, c->st)) != cudaSuccess) return e;
+    if ((e = gemm_run(c, g)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

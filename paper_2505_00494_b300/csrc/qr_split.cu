@@ -48,8 +48,7 @@ __global__ void __launch_bounds__(kWyThreads) wy_prep_kernel(const float* __rest
   __shared__ double Ts[NB][NB + 1];
   __shared__ double Gs[NB][NB + 1];
   __shared__ double Ws[NB][NB + 1];
-  __shared__ float Ys[NB][NB + 1];
-  __shared__ float Tf[NB][NB + 1];
+  __shared__ double Ys[NB][NB + 1];
   const int tid = threadIdx.x;
   const int c0 = blockIdx.x * NB;
   const long long MN = (long long)nb * N;
@@ -70,7 +69,7 @@ __global__ void __launch_bounds__(kWyThreads) wy_prep_kernel(const float* __rest
   };
   for (int e = tid; e < NB * NB; e += kWyThreads) {
     const int q = e / NB, c = e % NB;
-    Ys[q][c] = (q < nb && c0 + c < ncol) ? static_cast<float>(psum(q, ycol0 + c0 + c)) : 0.f;
+    Ys[q][c] = (q < nb && c0 + c < ncol) ? psum(q, ycol0 + c0 + c) : 0.0;
     if (mode == 0) {
       Gs[q][c] = (q < nb && c < nb) ? psum(q, c) : 0.0;
       Ts[q][c] = (q == c && q < nb) ? tau[q] : 0.0;
@@ -102,20 +101,17 @@ __global__ void __launch_bounds__(kWyThreads) wy_prep_kernel(const float* __rest
     if (blockIdx.x == 0)
       for (int e = tid; e < NB * NB; e += kWyThreads) Tp[e] = Ts[e / NB][e % NB];
   }
-  // Y2 = T^T Y (mode 0) or T Y (mode 1) in FP32 (the operand precision of
-  // the tensor-core update that consumes it), written transposed
-  for (int e = tid; e < NB * NB; e += kWyThreads) Tf[e / NB][e % NB] = static_cast<float>(Ts[e / NB][e % NB]);
-  __syncthreads();
+  // Y2 = T^T Y (mode 0) or T Y (mode 1) in FP64, written transposed as FP32
   for (int e = tid; e < NB * NB; e += kWyThreads) {
     const int c = e / NB, q = e % NB;
     if (c0 + c >= ncol) continue;
-    float acc = 0.f;
+    double acc = 0.0;
     if (mode == 0) {
-      for (int l = 0; l <= q; ++l) acc = fmaf(Tf[l][q], Ys[l][c], acc);
+      for (int l = 0; l <= q; ++l) acc = fma(Ts[l][q], Ys[l][c], acc);
     } else {
-      for (int l = q; l < NB; ++l) acc = fmaf(Tf[q][l], Ys[l][c], acc);
+      for (int l = q; l < NB; ++l) acc = fma(Ts[q][l], Ys[l][c], acc);
     }
-    Yt[(long long)(c0 + c) * NB + q] = acc;
+    Yt[(long long)(c0 + c) * NB + q] = static_cast<float>(acc);
   }
 }
 

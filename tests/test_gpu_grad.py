@@ -89,3 +89,31 @@ def test_gradient_central_differences(q, point):
         Es.append(c2.energy(1.0, 0.5))
     fd = (Es[0] - Es[1]) / (2 * eps)
     assert abs(fd - float(np.sum(g * v))) < 1e-5 * max(1.0, abs(fd))
+
+
+@pytest.fixture(scope="module")
+def point_d3():
+    A = o.normalized_input(qi.raw_tensor(2, 3, 7, bias=0.1))
+    C, T, info = o.ctmrg(A, 12, "qr", tol=1e-13, max_iter=800)
+    return A, C, T
+
+
+@pytest.mark.parametrize("mode", ["implicit", "unroll"])
+def test_split_precision_gradient_matches_fp64(q, point_d3, mode):
+    """A split-precision context runs the contractions of the gradient call
+    (taped steps, energy, reverse passes) on the TF32x3 tensor-core engine
+    with FP32 accumulation: the energy it returns agrees with the FP64 one to
+    2e-6 relative (three chained contractions of FP32-class accuracy) and its
+    gradient to 1e-4 relative."""
+    A, C, T = point_d3
+    out = {}
+    for prec in ("fp64", "split"):
+        ctx = q.QRCTM(2, 3, 12, precision=prec, with_nnn=True, with_grad=True, grad_tol=1e-9,
+                      grad_max_iter=300)
+        ctx.init_env(cuda(A), cuda(C), cuda(T))
+        E, g = ctx.energy_grad(1.0, 0.5, mode=mode, k_unroll=8)
+        out[prec] = (E, g.cpu().numpy())
+        ctx.close()
+    (Ef, gf), (Es, gs) = out["fp64"], out["split"]
+    assert abs(Es - Ef) < 2e-6 * abs(Ef), (Es, Ef)
+    assert np.linalg.norm(gs - gf) < 1e-4 * np.linalg.norm(gf), np.linalg.norm(gs - gf)
