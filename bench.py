@@ -58,23 +58,55 @@ def algorithmic_flops(d, D, chi):
     }
 
 
+FP64_PEAK_TFLOPS = 1.25
+
+
+def fp32_simt_peak():
+    return 148 * 128 * 2 * 2.032e9 / 1e12
+
+
+def tf32_peak_sustained(peaks):
+    """Dense TF32 peak for a kernel inside a long step: the measured
+    sustained BF16 rate scaled by the nominal TF32/BF16 ratio 1.1/2.25."""
+    if "bf16_tflops_sustained" in peaks:
+        return (peaks["bf16_tflops_sustained"] * 1.1 / 2.25,
+                "tf32 = measured sustained bf16 x 1.1/2.25")
+    return 1400.0 * 1.1 / 2.25, "tf32 = fallback sustained bf16 1.4 PFLOP/s x 1.1/2.25"
+
+
+def panel_flops(d, D, chi):
+    """Average flops of one FP64 panel launch: Householder factorisation of
+    an mr x nb block, 2 mr nb^2 - 2 nb^3 / 3, over the panels of the
+    (chi D^2) x chi reduced corner (nb = 32)."""
+    m, n = chi * D * D, chi
+    tot, cnt = 0.0, 0
+    for j0 in range(0, n, 32):
+        nb = min(32, n - j0)
+        mr = m - j0
+        tot += 2.0 * mr * nb * nb - 2.0 * nb ** 3 / 3.0
+        cnt += 1
+    return tot / cnt
+
+
+def load_traffic():
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    from the committed ncu capture summary, keyed by kernel name."""
+    out = {}
+    try:
+        for line in open(os.path.join(ROOT, "profiles", "traffic_split_d2_D6_chi144.txt")):
+            parts = line.split()
+            if len(parts) >= 2 and not line.startswith("#"):
+                out[parts[0]] = float(parts[1])
+    except OSError:
+        pass
+    return out
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return {}
-
-
-def peak_for(precision, peaks):
-    """(peak TFLOP/s, bound, note).  The recipe's nominal dense rates: bf16
-    2.25, tf32 1.1, fp64 1.25 PFLOP/s -> TFLOP/s; TF32 is scaled from the
-    measured BF16 peak by the nominal ratio; FP64 runs on the CUDA cores
-    (ALU bound) against the nominal FP64 rate."""
-    if precision == "split":
-        if "bf16_tflops" in peaks:
-            return peaks["bf16_tflops"] * 1.1 / 2.25, "tensor", "tf32 = measured bf16 x 1.1/2.25"
-        return 1800.0 * 1.1 / 2.25, "tensor", "tf32 = fallback bf16 x 1.1/2.25"
-    return 1.25, "alu", "fp64 nominal 1.25 TFLOP/s (B300 FP64 pipe)"
 
 
 class ClockSampler:
@@ -317,16 +349,45 @@ def main():
     phases = ctx.phase_times()
     ctx.set_profiling(False)
 
-    # roofline of the dominant phase (largest share of the timed region)
+    # roofline of the dominant kernel.  Per-phase device times come from CUDA
+    # events on the library's stream; the phases below are one kernel each
+    # (qr_panel: the FP64 panel launches; absorb: the fused ket/bra kernel;
+    # x1, project: one tensor-core contraction)
     fl = algorithmic_flops(d, D, chi)
-    dom = max(fl, key=lambda k: phases[k][0])
-    dom_ms, dom_n = phases[dom]
-    avg_s = dom_ms / max(1, dom_n) / 1e3
-    achieved = fl[dom] / avg_s / 1e12
     peaks = load_peaks()
-    peak, bound, peak_note = peak_for(args.precision, peaks)
+    tf32_peak, tf32_note = tf32_peak_sustained(peaks)
+    traffic = load_traffic()
+    fp64_note = "fp64 nominal 1.25 TFLOP/s (CUDA-core FP64 pipe)"
+    kernels = {"qr_panel": ("qr_panel_kernel", panel_flops(d, D, chi), "alu", FP64_PEAK_TFLOPS,
+                            fp64_note)}
+    if args.precision == "split":
+        kernels.update({
+            "absorb": ("absorb_fused_k", fl["absorb"], "alu", fp32_simt_peak(),
+                       "fp32 FMA nominal: 148 SMs x 128 FMA/clk x 2 x 2.032 GHz"),
+            "x1": ("tc_tf32x3_kernel<256>", fl["x1"], "tensor", tf32_peak, tf32_note),
+            "project": ("tc_tf32x3_kernel<144>", fl["project"], "tensor", tf32_peak, tf32_note),
+        })
+    else:
+        kernels.update({
+            "x1": ("gemm_f64_kernel", fl["x1"], "alu", FP64_PEAK_TFLOPS, fp64_note),
+            "project": ("gemm_f64_kernel", fl["project"], "alu", FP64_PEAK_TFLOPS, fp64_note),
+        })
+    rows = {}
+    for ph, (kname, flops, bound_k, peak_k, note_k) in kernels.items():
+        ms_k, n_k = phases[ph]
+        if n_k == 0:
+            continue
+        avg = ms_k / n_k / 1e3
+        ach = flops / avg / 1e12
+        rows[ph] = {"kernel": kname, "bound": bound_k, "achieved": ach, "peak": peak_k,
+                    "unit": "TFLOP/s", "frac": ach / peak_k, "avg_launch_ms": avg * 1e3,
+                    "launches": n_k, "share_of_step": ms_k / prof_ms,
+                    "algorithmic_flops_per_launch": flops, "peak_source": note_k,
+                    "traffic": traffic.get(kname)}
+    dom = max(rows, key=lambda k: rows[k]["share_of_step"])
     share = {k: round(phases[k][0] / prof_ms, 4) for k in ("ct", "qr", "x1", "absorb", "project",
-                                                      "corner", "symnorm", "spectrum")}
+                                                      "corner", "symnorm", "spectrum",
+                                                      "qr_panel")}
 
     # energy per site after the timed steps (Heisenberg, J2 = 0; and J1-J2 at 0.5)
     torch.cuda.synchronize()
@@ -465,10 +526,8 @@ def main():
                        "check_every": ce, "parallelism": f"replicas{world}",
                        "l2": "per-step intermediates larger than L2 (X1 alone "
                              f"{(chi * D * D) ** 2 * 8 / 1e6:.0f} MB)"},
-            "roofline": {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "peak_source": peak_note, "algorithmic_flops_per_launch": fl[dom],
-                         "avg_launch_ms": avg_s * 1e3},
+            "roofline": rows[dom],
+            "roofline_kernels": rows,
             "phase_share": share,
             "clocks": clk.summary(),
             "gpu_launches": int(launches),

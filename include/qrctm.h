@@ -90,6 +90,7 @@ enum {
   QRCTM_PH_ENERGY = 8,    /* reduced density matrices and energy                 */
   QRCTM_PH_GRAD = 9,      /* adjoint (gradient) passes                           */
   QRCTM_PH_WARMUP = 10,   /* standard warm-up steps                              */
+  QRCTM_PH_QR_PANEL = 11, /* the FP64 panel factorisations inside QR (nested)     */
   QRCTM_NUM_PHASES = 12
 };
 

@@ -30,7 +30,7 @@ PRECISION = {"fp64": 0, "split": 1}
 LAYERS = {"auto": 0, "double": 1, "split": 2}
 GRAD_MODE = {"implicit": 0, "unroll": 1}
 PHASES = ["ct", "qr", "x1", "absorb", "project", "corner", "symnorm", "spectrum", "energy",
-          "grad", "warmup", "reserved"]
+          "grad", "warmup", "qr_panel"]
 
 
 class QRCTMError(RuntimeError):

@@ -69,6 +69,8 @@ qrctm_status sync_check(qrctm_ctx* c, const char* where) {
 
 namespace qrctm {
 
+void panel_hook(void* user, int begin);
+
 // Regions in a fixed order; the same function sizes and carves.
 size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
   const size_t d = cfg.d, D = cfg.D, D2 = D * D, chi = cfg.chi, m = chi * D2;
@@ -148,7 +150,11 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
   {
     size_t o = off;
     off += al(qr_work_bytes((int)m, (int)chi));
-    if (carve) c->qrw = qr_carve(c->ws + o, (int)m, (int)chi);
+    if (carve) {
+      c->qrw = qr_carve(c->ws + o, (int)m, (int)chi);
+      c->qrw.hook = panel_hook;
+      c->qrw.hook_user = c;
+    }
   }
   {
     size_t o = off;
@@ -181,19 +187,20 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
   return off;
 }
 
-PhaseScope::PhaseScope(qrctm_ctx* c_, int ph_) : c(c_), ph(ph_), a(nullptr) {
-  if (!c->prof) return;
+cudaEvent_t phase_begin(qrctm_ctx* c) {
+  if (!c->prof) return nullptr;
   if (c->ev_pool.empty()) {
     cudaEvent_t e;
-    if (cudaEventCreate(&e) != cudaSuccess) return;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
     c->ev_pool.push_back(e);
   }
-  a = c->ev_pool.back();
+  cudaEvent_t a = c->ev_pool.back();
   c->ev_pool.pop_back();
   cudaEventRecord(a, c->st);
+  return a;
 }
 
-PhaseScope::~PhaseScope() {
+void phase_end(qrctm_ctx* c, int ph, cudaEvent_t a) {
   if (!a) return;
   cudaEvent_t b;
   if (c->ev_pool.empty()) {
@@ -205,6 +212,17 @@ PhaseScope::~PhaseScope() {
   cudaEventRecord(b, c->st);
   c->recs.push_back({ph, a, b});
 }
+
+// panel launches of the QR, timed as the nested phase QRCTM_PH_QR_PANEL
+void panel_hook(void* user, int begin) {
+  qrctm_ctx* c = static_cast<qrctm_ctx*>(user);
+  if (begin) c->panel_ev = phase_begin(c);
+  else { phase_end(c, QRCTM_PH_QR_PANEL, c->panel_ev); c->panel_ev = nullptr; }
+}
+
+PhaseScope::PhaseScope(qrctm_ctx* c_, int ph_) : c(c_), ph(ph_), a(phase_begin(c_)) {}
+
+PhaseScope::~PhaseScope() { phase_end(c, ph, a); }
 
 }  // namespace qrctm
 

@@ -43,6 +43,7 @@ struct qrctm_ctx {
   int iters;
   int grad_iters;
   double grad_resid;
+  cudaEvent_t panel_ev;   // open panel-phase event (profiling)
   // split-precision contractions of the energy and adjoint passes
   bool mm_split;
   float* mm32;

@@ -311,6 +311,7 @@ cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t 
   void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc, &x32, &ldx_, &vr32};
   const size_t tile = sizeof(double) * (size_t)rpc * (NB + 1);
   cudaError_t e;
+  if (w.hook) w.hook(w.hook_user, 1);
   if (tile <= kPanelTileMax) {
     static bool attr = false;
     if (!attr) {
@@ -324,6 +325,7 @@ cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t 
     e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<false>, dim3(P), dim3(PT), args,
                                     0, s);
   }
+  if (w.hook) w.hook(w.hook_user, 0);
   if (e != cudaSuccess) return e;
   note_launch();
   *G_out = Gp;
@@ -375,6 +377,8 @@ QrWork qr_carve(void* base, int m, int n) {
   const int npan = (n + NB - 1) / NB;
   char* p = static_cast<char*>(base);
   QrWork w;
+  w.hook = nullptr;
+  w.hook_user = nullptr;
   w.splitk = reinterpret_cast<double*>(p); p += align_up(sizeof(double) * (size_t)kSplitKElems);
   w.W = reinterpret_cast<double*>(p); p += align_up(sizeof(double) * (size_t)m * n);
   w.V = reinterpret_cast<double*>(p); p += align_up(sizeof(double) * (size_t)m * n);

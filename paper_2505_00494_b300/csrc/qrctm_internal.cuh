@@ -160,6 +160,10 @@ struct QrWork {
   double* part;     // partial sums of the panel kernel
   GridBar* bar;
   int* err;
+  // optional host callback around every panel launch (begin = 1, end = 0),
+  // used for per-phase timing
+  void (*hook)(void* user, int begin);
+  void* hook_user;
 };
 constexpr long long kSplitKElems = 1ll << 21;   // 16 MB of split-K partials
 size_t qr_work_bytes(int m, int n);
