@@ -88,12 +88,13 @@ def panel_flops(d, D, chi):
     return tot / cnt
 
 
-def load_traffic():
+def load_traffic(precision, workload):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
-    from the committed ncu capture summary, keyed by kernel name."""
+    from the committed ncu capture summary of this precision and workload,
+    keyed by kernel name (empty when there is none)."""
     out = {}
     try:
-        for line in open(os.path.join(ROOT, "profiles", "traffic_split_d2_D6_chi144.txt")):
+        for line in open(os.path.join(ROOT, "profiles", f"traffic_{precision}_{workload}.txt")):
             parts = line.split()
             if len(parts) >= 2 and not line.startswith("#"):
                 out[parts[0]] = float(parts[1])
@@ -295,7 +296,7 @@ def main():
                      device="cuda")
     A = q.c4v_symmetrize(X, normalize=True)
     ctx = q.QRCTM(d, D, chi, precision=args.precision, check_every=args.check_every,
-                  with_nnn=True)
+                  with_nnn=chi * D * D <= 8192)
     ctx.init_env(A)
     ce = args.check_every
 
@@ -356,7 +357,7 @@ def main():
     fl = algorithmic_flops(d, D, chi)
     peaks = load_peaks()
     tf32_peak, tf32_note = tf32_peak_sustained(peaks)
-    traffic = load_traffic()
+    traffic = load_traffic(args.precision, args.workload)
     fp64_note = "fp64 nominal 1.25 TFLOP/s (CUDA-core FP64 pipe)"
     kernels = {"qr_panel": ("qr_panel_kernel", panel_flops(d, D, chi), "alu", FP64_PEAK_TFLOPS,
                             fp64_note)}
@@ -394,9 +395,13 @@ def main():
     t0 = time.perf_counter()
     E = ctx.energy(1.0, 0.0)
     energy_ms = 1e3 * (time.perf_counter() - t0)
-    t0 = time.perf_counter()
-    E12 = ctx.energy(1.0, 0.5)
-    energy_j2_ms = 1e3 * (time.perf_counter() - t0)
+    # the 2x2-patch RDM costs 2 d^2 (chi D^2)^3 FP64 flops: skipped beyond
+    # chi D^2 = 8192 (minutes at D = 8, chi = 512)
+    E12, energy_j2_ms = None, None
+    if chi * D * D <= 8192:
+        t0 = time.perf_counter()
+        E12 = ctx.energy(1.0, 0.5)
+        energy_j2_ms = 1e3 * (time.perf_counter() - t0)
 
     # end to end through the public API from pinned host buffers: per step the
     # host copies (A, C, T) in, the library re-initialises from them and runs

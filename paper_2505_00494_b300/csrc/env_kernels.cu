@@ -328,8 +328,8 @@ __global__ void __launch_bounds__(1024) spectrum_kernel(const double* __restrict
   }
 }
 
-// Cluster variant of the tridiagonalisation: kSpecCluster CTAs share the
-// work.  CTA r of the cluster owns the rows i = r (mod kSpecCluster) of the
+// Cluster variant of the tridiagonalisation: CS CTAs (8, or 16 for larger
+// chi) share the work.  CTA r of the cluster owns the rows i = r (mod CS) of the
 // full symmetric matrix in its shared memory.  Per column k:
 //   (a) owners publish x_i = A[i][k] (i > k); after a cluster barrier every
 //       CTA gathers x over distributed shared memory and forms v, beta
@@ -337,8 +337,8 @@ __global__ void __launch_bounds__(1024) spectrum_kernel(const double* __restrict
 //   (b) owners publish p_i = beta (A v)_i and their partial v.p; after the
 //       second barrier every CTA forms K = beta v.p / 2 and w = p - K v,
 //       then updates its own rows, A -= v w^T + w v^T.
-constexpr int kSpecCluster = 8;
-constexpr int kSpecClusterMaxN = 360;
+constexpr int kSpecClusterMaxN8 = 360;    // 8-CTA cluster (portable size)
+constexpr int kSpecClusterMaxN16 = 512;   // 16-CTA cluster (non-portable size)
 
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n"
@@ -357,9 +357,9 @@ __device__ __forceinline__ double ld_dsmem(const double* local_addr, unsigned ra
   return v;
 }
 
+template <int CS>
 __global__ void __launch_bounds__(256) spectrum_cluster_kernel(const double* __restrict__ C, int n,
                                                                double* work, int* err) {
-  constexpr int CS = kSpecCluster;
   extern __shared__ double csm[];
   __shared__ double red[32];
   __shared__ double sc[4];
@@ -676,34 +676,63 @@ cudaError_t corner_spectrum(const double* C, int chi, double* work, double* s_ne
                          (int)(sizeof(double) * kSmemSpecMax * (kSmemSpecMax + 1)));
     attr = true;
   }
-  if (chi >= 3 && chi <= kSpecClusterMaxN) {
-    const int nloc_max = (chi + kSpecCluster - 1) / kSpecCluster;
+  bool launched = false;
+  if (chi >= 3 && chi <= kSpecClusterMaxN16) {
+    const int cs = (chi <= kSpecClusterMaxN8) ? 8 : 16;
+    const int maxn = (cs == 8) ? kSpecClusterMaxN8 : kSpecClusterMaxN16;
+    auto kern = (cs == 8) ? spectrum_cluster_kernel<8> : spectrum_cluster_kernel<16>;
+    const int nloc_max = (chi + cs - 1) / cs;
     const size_t csmem = sizeof(double) * ((size_t)nloc_max * chi + 4 * (size_t)chi);
-    static bool cattr = false;
+    static bool cattr8 = false, cattr16 = false, ok16 = false;
+    bool& cattr = (cs == 8) ? cattr8 : cattr16;
     if (!cattr) {
-      cudaFuncSetAttribute(spectrum_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(double) * (((size_t)kSpecClusterMaxN + kSpecCluster - 1) /
-                                                       kSpecCluster * kSpecClusterMaxN +
-                                                   4 * (size_t)kSpecClusterMaxN)));
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(double) * (((size_t)maxn + cs - 1) / cs * maxn +
+                                                   4 * (size_t)maxn)));
+      if (cs == 16) {
+        // 16 CTAs per cluster is above the portable limit: allowed only where
+        // the device can place such a cluster
+        ok16 = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+               cudaSuccess;
+        if (ok16) {
+          cudaLaunchConfig_t q = {};
+          q.gridDim = dim3(16);
+          q.blockDim = dim3(256);
+          q.dynamicSmemBytes = csmem;
+          cudaLaunchAttribute qa[1];
+          qa[0].id = cudaLaunchAttributeClusterDimension;
+          qa[0].val.clusterDim.x = 16;
+          qa[0].val.clusterDim.y = 1;
+          qa[0].val.clusterDim.z = 1;
+          q.attrs = qa;
+          q.numAttrs = 1;
+          int nclusters = 0;
+          ok16 = cudaOccupancyMaxActiveClusters(&nclusters, kern, &q) == cudaSuccess &&
+                 nclusters >= 1;
+        }
+        cudaGetLastError();
+      }
       cattr = true;
     }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(kSpecCluster);
-    cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = csmem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = kSpecCluster;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, spectrum_cluster_kernel, C, chi, work, err);
-    if (e != cudaSuccess) return e;
-  } else {
-    spectrum_kernel<<<1, 1024, smem, s>>>(C, chi, work, err);
+    if (cs == 8 || ok16) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cs);
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = csmem;
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cs;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      cudaError_t e = cudaLaunchKernelEx(&cfg, kern, C, chi, work, err);
+      if (e != cudaSuccess) return e;
+      launched = true;
+    }
   }
+  if (!launched) spectrum_kernel<<<1, 1024, smem, s>>>(C, chi, work, err);
   note_launch();
   double* ev = work + (size_t)chi * chi + 5 * (size_t)chi + 8;
   bisect_kernel<<<chi, 32, 0, s>>>(work, chi, ev);
