@@ -70,7 +70,7 @@ cudaError_t qr_step_split(qrctm_ctx* c) {
   const long long mp = pad4(m);
   cudaStream_t st = c->st;
   cudaError_t e;
-  float* T32 = c->T32;      // [(b,k)][a]   rows chi*D2, stride chp
+  float* T32 = c->T32;      // [(b,k_b,k_k)][a]   rows chi*D2, stride chp (k = k_k D + k_b)
   float* C32 = c->C32;      // [a][g]       stride chp
   float* Qt32 = c->Qt32;    // [(m,u)][a]   rows chi*D2, stride chp
   float* Qc32 = c->Qc32;    // [n][(b,d)]   rows chi, stride mp
@@ -79,18 +79,23 @@ cudaError_t qr_step_split(qrctm_ctx* c) {
   float* X2 = reinterpret_cast<float*>(c->X2);
   {
     PhaseScope ps(c, QRCTM_PH_CT);
-    if ((e = gather_f32(c->T, T32, m, ch, chp, im1(ch), im1(1), st)) != cudaSuccess) return e;
+    // rows (b, k_b, k_k) with k_k fastest: the X1 product then writes runs
+    // along its lowest output digit
+    if ((e = gather_f32(c->T, T32, m, ch, chp, im3(D, D, (long long)D * ch, ch, (long long)D2 * ch),
+                        im1(1), st)) != cudaSuccess)
+      return e;
     if ((e = gather_f32(c->C, C32, ch, ch, chp, im1(ch), im1(1), st)) != cudaSuccess) return e;
     // ct(a, (b,i)) = sum_g C[a,g] T[b,i,g]  ->  Mcm[b*m + a*D2 + i]
+    // (column n = (b, i_b, i_k), i = i_k D + i_b)
     TcGemm g = tc0(c);
     g.A = op(C32, ch, ch, chp);
     g.B = op(T32, m, ch, chp);
     g.M = ch; g.N = m; g.K = ch;
     g.C = c->Mcm; g.c_fp64 = true;
-    g.c_m = im1(D2); g.c_n = im2(D2, 1, m);
+    g.c_m = im1(D2); g.c_n = im3(D, D, D, 1, m);
     // FP32 copy for the QR's tensor-core products: row b, K index (a, i)
     g.C32 = qr_split_x32(c->qr32);
-    g.c32_m = im1(D2); g.c32_n = im2(D2, 1, mp);
+    g.c32_m = im1(D2); g.c32_n = im3(D, D, D, 1, mp);
     if ((e = gemm_tc(g, st)) != cudaSuccess) return e;
   }
   {
@@ -111,10 +116,10 @@ cudaError_t qr_step_split(qrctm_ctx* c) {
     g.B = op(T32, m, ch, chp);
     g.M = m; g.N = m; g.K = ch;
     g.C = X1; g.c_fp64 = false;
-    // row (mu,u): u = u_k*D + u_b ; col (b,k): k = k_k*D + k_b
+    // row (mu,u): u = u_k*D + u_b ; col (b,k_b,k_k), k = k_k*D + k_b
     // offset = ((mu*chi + b)*D2 + u_b*D + k_b)*D2p + u_k*D + k_k
     g.c_m = im3(D, D, D * D2p, D, (long long)ch * D2 * D2p);
-    g.c_n = im3(D, D, D2p, 1, D2 * D2p);
+    g.c_n = im3(D, D, 1, D2p, D2 * D2p);
     if ((e = gemm_tc(g, st)) != cudaSuccess) return e;
   }
   {

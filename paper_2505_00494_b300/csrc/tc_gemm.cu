@@ -296,12 +296,34 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           split ? (((long long)z * args.ksplit + kz) * args.M + (mvalid ? m : 0)) * args.N
                 : map_off(args.c_b, z) + (mvalid ? map_off(args.c_m, m) : 0);
       const long long row32 = (args.C32 && mvalid) ? map_off(args.c32_m, m) : 0;
+      const bool col_unit = args.c_n.nd > 0 && args.c_n.str[0] == 1;
 #pragma unroll 1
       for (int c = 0; c < (BN + 31) / 32; ++c) {
         float v[32], w[32];
         const uint32_t ta = tmem + (static_cast<uint32_t>(q * 32) << 16) + c * 32;
         tmem_ld32(ta, v);
         tmem_ld32(ta + C::HALF, w);
+        if (!split && !args.c_fp64 && args.beta == 0.0 && col_unit) {
+          // FP32 output whose lowest column digit has unit stride: the 32 x 32
+          // chunk goes through shared memory (the idle pipeline buffers: every
+          // MMA has completed) and is written with the lanes along the columns
+          float* stg = reinterpret_cast<float*>(tiles) + (warp & 3) * (32 * 33);
+          const float al = static_cast<float>(args.alpha);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = al * (v[j] + w[j]);
+          __syncwarp();
+          const int jj = c * 32 + lane;
+          const bool cvalid = jj < BN && (long long)n0 + jj < args.N;
+          const long long co = cvalid ? col_off[jj] : 0;
+          float* outp = static_cast<float*>(args.C);
+          for (int rr = 0; rr < 32; ++rr) {
+            const long long bo = __shfl_sync(0xffffffffu, base_off, rr);
+            const int valid_r = __shfl_sync(0xffffffffu, mvalid ? 1 : 0, rr);
+            if (valid_r && cvalid) outp[bo + co] = stg[rr * 33 + lane];
+          }
+          __syncwarp();
+          continue;
+        }
         if (!mvalid) continue;
         if (split) {
           float* p = args.part + base_off + n0 + c * 32;
@@ -315,25 +337,36 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // all loads of the old values first (they would otherwise wait on
         // the stores before them), then the results
         const int nv = min(32, min(BN - c * 32, (int)(args.N - n0 - c * 32)));
+        if (!args.c_fp64) {
+          // FP32 output: FP32 arithmetic (B300's FP64 pipe would otherwise
+          // bound the epilogue)
+          const float al = static_cast<float>(args.alpha), be = static_cast<float>(args.beta);
+          float* p = static_cast<float*>(args.C) + base_off;
+          float o[32];
+          if (be != 0.f) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) o[j] = (j < nv) ? p[col_off[c * 32 + j]] : 0.f;
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            float r = al * (v[j] + w[j]);
+            if (be != 0.f) r = fmaf(be, o[j], r);
+            if (j < nv) p[col_off[c * 32 + j]] = r;
+          }
+          continue;
+        }
         double r[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) r[j] = args.alpha * static_cast<double>(v[j] + w[j]);
         if (args.beta != 0.0) {
           double old[32];
-          if (args.c_fp64) {
-            const double* p = static_cast<const double*>(args.C) + base_off;
+          const double* p = static_cast<const double*>(args.C) + base_off;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) old[j] = (j < nv) ? p[col_off[c * 32 + j]] : 0.0;
-          } else {
-            const float* p = static_cast<const float*>(args.C) + base_off;
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              old[j] = (j < nv) ? static_cast<double>(p[col_off[c * 32 + j]]) : 0.0;
-          }
+          for (int j = 0; j < 32; ++j) old[j] = (j < nv) ? p[col_off[c * 32 + j]] : 0.0;
 #pragma unroll
           for (int j = 0; j < 32; ++j) r[j] = fma(args.beta, old[j], r[j]);
         }
-        if (args.c_fp64) {
+        {
           double* p = static_cast<double*>(args.C) + base_off;
 #pragma unroll
           for (int j = 0; j < 32; ++j)
@@ -344,11 +377,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int j = 0; j < 32; ++j)
               if (j < nv) p32[col_off32[c * 32 + j]] = static_cast<float>(r[j]);
           }
-        } else {
-          float* p = static_cast<float*>(args.C) + base_off;
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (j < nv) p[col_off[c * 32 + j]] = static_cast<float>(r[j]);
         }
       }
     }
