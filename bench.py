@@ -204,6 +204,23 @@ def oracle_sample(w, n_steps):
     return times, layers
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (the job's time) when running under
+    torch.distributed, else ms."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(steps, world, ms):
+    """Whole-job iterations/s: every rank runs `steps` iterations of its own
+    replica (weak scaling), timed by the slowest rank."""
+    return world * steps / (ms / 1e3)
+
+
 def converge(ctx, tol, max_iter, floor=False, window=100):
     """Iterate until the spectrum change is below tol; with floor, also stop
     once it has not decreased by 2% over 3 windows (the precision floor).
@@ -327,13 +344,9 @@ def main():
         if dist is not None:
             dist.barrier()
     launches = q.kernel_launches() - launches0
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
     ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1e3)
+    value = job_rate(args.steps, world, ms)
 
     # per-phase device times from CUDA events around each phase, on a separate
     # pass after the timed one (the events are not part of the timed region)

@@ -17,7 +17,8 @@ from __future__ import annotations
 import ctypes
 import os
 
-__all__ = ["QRCTM", "QRCTMError", "lib", "c4v_symmetrize", "householder_qr", "LIB_PATH"]
+__all__ = ["QRCTM", "QRCTMError", "Energy", "lib", "c4v_symmetrize", "householder_qr",
+           "LIB_PATH"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libqrctm.so")
 
@@ -322,3 +323,51 @@ def householder_qr(M, stream=None, workspace=None):
     if code != 0:
         raise QRCTMError(code, "qrctm_householder_qr")
     return Qcm.t(), R
+
+
+def _energy_function():
+    torch = _torch()
+
+    class Energy(torch.autograd.Function):
+        """E(A): energy per site at the converged QR-CTMRG environment of A,
+        differentiable through the library's hand-written adjoint.
+
+            E = Energy.apply(A, ctx, J1, J2, tol, max_iter, mode, k_unroll)
+            E.backward()            # A.grad = dE/dA (C4v-projected)
+
+        ``ctx`` is a QRCTM context built with with_grad=True (and with_nnn=True
+        when J2 != 0).  Forward builds the environment from the bulk boundary
+        (qrctm_init_env), iterates to the spectrum tolerance and evaluates the
+        energy; the converged (C, T) are kept with the autograd node, so the
+        backward pass (qrctm_energy_grad, implicit fixed point or k unrolled
+        steps) does not depend on later use of the context."""
+
+        @staticmethod
+        def forward(fctx, A, ctx, J1=1.0, J2=0.0, tol=1e-10, max_iter=500, mode="implicit",
+                    k_unroll=20):
+            A = A.detach().contiguous()
+            ctx.init_env(A)
+            ctx.run_to_convergence(tol=tol, max_iter=max_iter)
+            E = ctx.energy(J1, J2)
+            C, T, _ = ctx.get_env(spectrum=False)
+            fctx.save_for_backward(A, C, T)
+            fctx.args = (ctx, J1, J2, mode, k_unroll)
+            return torch.tensor(E, dtype=torch.float64, device=A.device)
+
+        @staticmethod
+        def backward(fctx, gE):
+            A, C, T = fctx.saved_tensors
+            ctx, J1, J2, mode, k_unroll = fctx.args
+            ctx.init_env(A, C, T)
+            _, g = ctx.energy_grad(J1, J2, mode=mode, k_unroll=k_unroll)
+            return (gE * g,) + (None,) * 7
+
+    return Energy
+
+
+def __getattr__(name):
+    if name == "Energy":
+        fn = _energy_function()
+        globals()["Energy"] = fn
+        return fn
+    raise AttributeError(name)

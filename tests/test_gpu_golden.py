@@ -1,0 +1,104 @@
+"""Converged environments on the GPU against the oracle's converged fixtures
+(tests/golden/converged_*.json, written by tests/golden/make_golden.py from
+the oracle alone).  Both sides start from the bulk boundary (the GPU with its
+own warm-up; the QR-CTMRG fixed point does not depend on it) and iterate to
+their spectrum tolerance, so agreement is bounded by how far each run is
+from the common fixed point, not by rounding:
+
+* FP64 path: sorted |eig C| within 1e-9 and energies within 1e-9 per site;
+* split path (TF32x3 contractions): run to its precision floor, energy per
+  site within 1e-7 of the FP64 oracle (the split-path target), and the FP64
+  path polished from the split environment agrees with the oracle as above.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import qrctm_inputs as qi
+from oracle import qrctm_oracle as o
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden(name):
+    path = os.path.join(HERE, f"converged_{name}.json")
+    if not os.path.exists(path):
+        pytest.skip(f"fixture {path} not generated")
+    return json.load(open(path))
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch  # noqa: F401
+    from paper_2505_00494_b300 import build
+    build.build()
+    import paper_2505_00494_b300 as q
+    return q
+
+
+def tensor(q, w):
+    import torch
+    X = torch.tensor(qi.raw_tensor(w["d"], w["D"], w["seed"], w["decay"], w["bias"]),
+                     dtype=torch.float64, device="cuda")
+    return q.c4v_symmetrize(X, normalize=True)
+
+
+def run_floor(ctx, window=100, max_iter=6000):
+    """Iterate until the spectrum change stops decreasing by 2% over 3 windows."""
+    its, best, best_at, dl = 0, float("inf"), 0, float("inf")
+    while its < max_iter:
+        n, dl = ctx.run_to_convergence(tol=1e-14, max_iter=window)
+        its += n
+        if dl < 0.98 * best:
+            best, best_at = dl, its
+        elif its - best_at >= 3 * window:
+            break
+    return its, dl
+
+
+def oracle_start(w):
+    """The oracle's warmed environment (the fixtures' starting point)."""
+    import torch
+    A = o.normalized_input(qi.raw_tensor(w["d"], w["D"], w["seed"], w["decay"], w["bias"]))
+    C, T = o.warmup(A, w["chi"])
+    return (torch.tensor(C, dtype=torch.float64, device="cuda"),
+            torch.tensor(T, dtype=torch.float64, device="cuda"))
+
+
+@pytest.mark.parametrize("name,tol", [("d2_D2_chi16", 1e-13), ("d2_D4_chi64", 1e-12)])
+def test_fp64_converged_matches_oracle(q, name, tol):
+    """From the oracle's warmed environment (the runs would otherwise differ in
+    how far the slowest modes at the truncation edge have relaxed)."""
+    g = golden(name)
+    w = qi.WORKLOADS[name]
+    ctx = q.QRCTM(w["d"], w["D"], w["chi"], check_every=5, with_nnn=True)
+    C0, T0 = oracle_start(w)
+    ctx.init_env(tensor(q, w), C0, T0)
+    its, dl = ctx.run_to_convergence(tol=tol, max_iter=8000)
+    assert dl < tol
+    _, _, s = ctx.get_env(spectrum=True)
+    assert np.abs(s - np.array(g["spectrum"])).max() < 1e-9
+    assert abs(ctx.energy(1.0, 0.0) - g["E_J2_0"]) < 1e-9
+    assert abs(ctx.energy(1.0, 0.5) - g["E_J2_0.5"]) < 1e-9
+
+
+def test_split_converged_energy_matches_oracle_d2_D6_chi144(q):
+    g = golden("d2_D6_chi144")
+    w = qi.WORKLOADS["d2_D6_chi144"]
+    A = tensor(q, w)
+    ctx = q.QRCTM(2, 6, 144, precision="split", check_every=5)
+    ctx.init_env(A)
+    run_floor(ctx)
+    assert abs(ctx.energy(1.0, 0.0) - g["E_J2_0"]) < 1e-7
+    C, T, _ = ctx.get_env(spectrum=False)
+    f = q.QRCTM(2, 6, 144, check_every=5, with_nnn=True)
+    f.init_env(A, C, T)
+    its, dl = f.run_to_convergence(tol=1e-11, max_iter=3000)
+    assert dl < 1e-11
+    _, _, s = f.get_env(spectrum=True)
+    assert np.abs(s - np.array(g["spectrum"])).max() < 1e-9
+    assert abs(f.energy(1.0, 0.0) - g["E_J2_0"]) < 1e-9
+    assert abs(f.energy(1.0, 0.5) - g["E_J2_0.5"]) < 1e-9

@@ -73,22 +73,25 @@ def test_implicit_gradient_matches_complex_step(q, point, J2):
 
 
 def test_gradient_central_differences(q, point):
+    """Central differences (step 1e-6) of converged GPU energies along 16
+    seeded symmetric directions (seeds 1001..1016) against g . v, 1e-5
+    relative (J1-J2 at J2/J1 = 0.5)."""
     A, C, T = point
     ctx = make_ctx(q, A, C, T)
     _, g = ctx.energy_grad(1.0, 0.5, mode="implicit")
     g = g.cpu().numpy()
-    v = o.normalized_input(qi.raw_direction(2, 2, 1005))
-    eps = 1e-5
-    Es = []
-    for sgn in (1.0, -1.0):
-        Ap = A + sgn * eps * v
-        c2 = q.QRCTM(2, 2, 8, with_nnn=True)
-        c2.init_env(cuda(Ap), cuda(C), cuda(T))
-        c2.run_to_convergence(tol=1e-14, max_iter=600)
-        c2.step(1, want_delta=False) if c2.iterations % 2 else None
-        Es.append(c2.energy(1.0, 0.5))
-    fd = (Es[0] - Es[1]) / (2 * eps)
-    assert abs(fd - float(np.sum(g * v))) < 1e-5 * max(1.0, abs(fd))
+    c2 = q.QRCTM(2, 2, 8, with_nnn=True)
+    eps = 1e-6
+    for seed in range(1001, 1017):
+        v = o.normalized_input(qi.raw_direction(2, 2, seed))
+        Es = []
+        for sgn in (1.0, -1.0):
+            c2.init_env(cuda(A + sgn * eps * v), cuda(C), cuda(T))
+            c2.run_to_convergence(tol=1e-14, max_iter=800)
+            Es.append(c2.energy(1.0, 0.5))
+        fd = (Es[0] - Es[1]) / (2 * eps)
+        got = float(np.sum(g * v))
+        assert abs(fd - got) < 1e-5 * max(1.0, abs(fd)), (seed, fd, got)
 
 
 @pytest.fixture(scope="module")
