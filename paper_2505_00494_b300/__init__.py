@@ -112,12 +112,6 @@ def _load():
     return _LIB
 
 
-def __getattr__(name):
-    if name == "lib":
-        return _load()
-    raise AttributeError(name)
-
-
 def _torch():
     import torch
     return torch
@@ -366,6 +360,11 @@ def _energy_function():
 
 
 def __getattr__(name):
+    """Lazy attributes: ``lib`` (the loaded library) and ``Energy`` (the
+    autograd function, built on first use so that importing the package does
+    not import torch)."""
+    if name == "lib":
+        return _load()
     if name == "Energy":
         fn = _energy_function()
         globals()["Energy"] = fn
