@@ -586,7 +586,28 @@ __global__ void gather_f32_k(const double* __restrict__ in, float* __restrict__ 
   }
 }
 
+__global__ void gather_f32f_k(const float* __restrict__ in, float* __restrict__ out,
+                              long long nrows, int ncols, long long stride, IdxMap rmap,
+                              IdxMap cmap) {
+  const long long tot = nrows * ncols;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / ncols, c = e % ncols;
+    out[r * stride + c] = in[map_off(rmap, r) + map_off(cmap, c)];
+  }
+}
+
 }  // namespace
+
+cudaError_t gather_f32f(const float* in, float* out, long long nrows, int ncols, long long stride,
+                        IdxMap rmap, IdxMap cmap, cudaStream_t s) {
+  const long long tot = nrows * ncols;
+  if (tot <= 0) return cudaSuccess;
+  gather_f32f_k<<<(unsigned)std::min<long long>((tot + 255) / 256, 8192), 256, 0, s>>>(
+      in, out, nrows, ncols, stride, rmap, cmap);
+  note_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t gather_f32(const double* in, float* out, long long nrows, int ncols, long long stride,
                        IdxMap rmap, IdxMap cmap, cudaStream_t s) {

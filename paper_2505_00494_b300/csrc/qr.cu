@@ -72,7 +72,8 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
                                                       double* __restrict__ part, GridBar* bar,
                                                       int* err, int m, int j0, int nb,
                                                       int rows_per_cta, float* __restrict__ X32,
-                                                      long long ldx, float* __restrict__ Vr32) {
+                                                      long long ldx, float* __restrict__ Vr32,
+                                                      const float* __restrict__ src32) {
   const int P = gridDim.x, b = blockIdx.x;
   const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;   // wrp = row lane (0..7)
   const long long r_begin = (long long)j0 + (long long)b * rows_per_cta;
@@ -98,9 +99,13 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
            ((red[4][t] + red[5][t]) + (red[6][t] + red[7][t]));
   };
   if (TILE) {
+    // panel columns from W (FP64) or, when src32 is set, from the FP32 rows
+    // src32[c][i] (row stride ldx) of a trailing matrix kept in FP32
     for (int e = threadIdx.x; e < rows * nb; e += PT) {
       const int r = e % rows, jc = e / rows;
-      tile[r * (NB + 1) + jc] = W[((long long)j0 + jc) * m + r_begin + r];
+      tile[r * (NB + 1) + jc] =
+          src32 ? static_cast<double>(src32[((long long)j0 + jc) * ldx + r_begin + r])
+                : W[((long long)j0 + jc) * m + r_begin + r];
     }
     __syncthreads();
   }
@@ -296,7 +301,8 @@ __global__ void set_identity_cols_kernel(double* Q, int m, int n) {
 // reflectors into w.V, tau and the Gram-based T factor into w.Tf (stride NB).
 // gram_tc: compute G = V^T V with the caller's contraction (nullptr = FP64).
 cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t s, double** G_out,
-                          double** tau_out, float* X32, long long ldx, float* Vr32) {
+                          double** tau_out, float* X32, long long ldx, float* Vr32,
+                          const float* src32) {
   const int mr = m - j0;
   const int P = qr_panel_grid(mr);
   int rpc = (mr + P - 1) / P;
@@ -307,10 +313,12 @@ cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t 
   int m_ = m, j0_ = j0, nb_ = nbj;
   float* x32 = X32;
   float* vr32 = Vr32;
+  const float* s32 = src32;
   long long ldx_ = ldx;
-  void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc, &x32, &ldx_, &vr32};
+  void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc, &x32, &ldx_, &vr32, &s32};
   const size_t tile = sizeof(double) * (size_t)rpc * (NB + 1);
   cudaError_t e;
+  if (src32 != nullptr && tile > kPanelTileMax) return cudaErrorInvalidValue;   // tiled path only
   if (w.hook) w.hook(w.hook_user, 1);
   if (tile <= kPanelTileMax) {
     static bool attr = false;

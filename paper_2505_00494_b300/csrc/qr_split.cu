@@ -14,11 +14,14 @@
 //   3. wy_prep: sums the partials (compensated FP32 summation), builds T in
 //      FP64 from G = V^T V and tau (T_12 = -T_11 G_12 T_22 by recursive
 //      doubling) and forms Y2 = T^T (V^T W2) as FP32 rows for the update;
-//   4. W2 <- W2 - V Y2 on the tensor cores, the epilogue writing the FP64
-//      W2 and the FP32 copy that the next panel's product reads.
+//   4. W2 <- W2 - V Y2 on the tensor cores.
+// After a TF32x3 product the trailing matrix is FP32-class accurate, so it is
+// kept in FP32 only (X32, rows = columns of ct): each panel converts its 32
+// columns to FP64 when it loads them (the first panel reads ct itself in
+// FP64), and the entries of R above a panel's diagonal block come from X32.
 // Q = H_1 ... H_n [I; 0] is formed panel by panel in reverse with the same
-// three launches (T kept from step 3, Y2 = T (V^T Q_s)); its FP32 copy
-// (rows = columns of Q) is an output as well.
+// three launches (T kept from step 3, Y2 = T (V^T Q_s)), in FP32 only: its
+// rows Q32[c][i] (= column c of Q) are what the rest of the step consumes.
 #include "qrctm_internal.cuh"
 #include "tc_gemm.cuh"
 
@@ -49,6 +52,8 @@ __global__ void __launch_bounds__(kWyThreads) wy_prep_kernel(const float* __rest
   __shared__ double Gs[NB][NB + 1];
   __shared__ double Ws[NB][NB + 1];
   __shared__ double Ys[NB][NB + 1];
+  __shared__ float Tf[NB][NB + 1];
+  __shared__ float Yf[NB][NB + 1];
   const int tid = threadIdx.x;
   const int c0 = blockIdx.x * NB;
   const long long MN = (long long)nb * N;
@@ -101,30 +106,47 @@ __global__ void __launch_bounds__(kWyThreads) wy_prep_kernel(const float* __rest
     if (blockIdx.x == 0)
       for (int e = tid; e < NB * NB; e += kWyThreads) Tp[e] = Ts[e / NB][e % NB];
   }
-  // Y2 = T^T Y (mode 0) or T Y (mode 1) in FP64, written transposed as FP32
+  // Y2 = T^T Y (mode 0) or T Y (mode 1) in FP32 (the operand precision of
+  // the tensor-core update that consumes it), written transposed
+  for (int e = tid; e < NB * NB; e += kWyThreads) {
+    Tf[e / NB][e % NB] = static_cast<float>(Ts[e / NB][e % NB]);
+    Yf[e / NB][e % NB] = static_cast<float>(Ys[e / NB][e % NB]);
+  }
+  __syncthreads();
   for (int e = tid; e < NB * NB; e += kWyThreads) {
     const int c = e / NB, q = e % NB;
     if (c0 + c >= ncol) continue;
-    double acc = 0.0;
+    float acc = 0.f;
     if (mode == 0) {
-      for (int l = 0; l <= q; ++l) acc = fma(Ts[l][q], Ys[l][c], acc);
+      for (int l = 0; l <= q; ++l) acc = fmaf(Tf[l][q], Yf[l][c], acc);
     } else {
-      for (int l = q; l < NB; ++l) acc = fma(Ts[q][l], Ys[l][c], acc);
+      for (int l = q; l < NB; ++l) acc = fmaf(Tf[q][l], Yf[l][c], acc);
     }
-    Yt[(long long)(c0 + c) * NB + q] = static_cast<float>(acc);
+    Yt[(long long)(c0 + c) * NB + q] = acc;
   }
 }
 
-// Q = [I; 0] (FP64, column-major m x n) and its FP32 copy Q32[c][i] (stride ldq)
-__global__ void init_q_kernel(double* Q, float* Q32, int m, int n, long long ldq) {
+// Q32[c][i] = delta_ci (the FP32 rows of Q = [I; 0]), row stride ldq
+__global__ void init_q32_kernel(float* Q32, int m, int n, long long ldq) {
   const long long tot = (long long)m * n;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
     const long long c = e / m, i = e % m;
-    const double v = (i == c) ? 1.0 : 0.0;
-    Q[e] = v;
-    Q32[c * ldq + i] = static_cast<float>(v);
+    Q32[c * ldq + i] = (i == c) ? 1.f : 0.f;
   }
+}
+
+// R (row-major n x n): R[i][j] for i <= j from the FP64 panel output W when
+// row i lies in column j's panel, else from the FP32 trailing rows X32[j][i]
+__global__ void extract_r_split_kernel(const double* __restrict__ W, const float* __restrict__ X32,
+                                       double* __restrict__ R, int m, int n, long long ldx) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  const int i = (int)(e / n), j = (int)(e % n);
+  const int p0 = (j / NB) * NB;
+  R[e] = (i > j) ? 0.0
+                 : (i >= p0 ? W[(long long)j * m + i]
+                            : static_cast<double>(X32[(long long)j * ldx + i]));
 }
 
 }  // namespace
@@ -136,16 +158,17 @@ size_t qr_split_floats(int m, int n) {
 
 float* qr_split_x32(float* f32) { return f32; }
 
-cudaError_t householder_qr_split(int m, int n, const double* M, double* Q, double* R,
-                                 const QrWork& w, float* f32, float* Q32, bool x32_ready,
-                                 float* part, long long part_elems, cudaStream_t s) {
+cudaError_t householder_qr_split(int m, int n, const double* M, double* R, const QrWork& w,
+                                 float* f32, float* Q32, bool x32_ready, float* part,
+                                 long long part_elems, cudaStream_t s) {
   if (m < n || n <= 0) return cudaErrorInvalidValue;
   const long long mp = pad4(m);
   const int npan = (n + NB - 1) / NB;
   float* X32 = f32;                                  // [c][i]   n x mp  (W, then V rows)
   float* Vr32 = X32 + (long long)n * mp;             // [p][i][q] npan x m x NB
   float* Yt32 = Vr32 + (long long)npan * m * NB;     // [c][q]   n x NB
-  cudaError_t e = cudaMemcpyAsync(w.W, M, sizeof(double) * (size_t)m * n,
+  // the first panel reads ct in FP64 through w.W
+  cudaError_t e = cudaMemcpyAsync(w.W, M, sizeof(double) * (size_t)m * std::min(n, NB),
                                   cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
   if (!x32_ready &&
@@ -166,16 +189,15 @@ cudaError_t householder_qr_split(int m, int n, const double* M, double* Q, doubl
     g.max_ksplit = kQrMaxKsplit;
     return gemm_tc(g, s);
   };
-  // Xs -= V Y2 (FP64 block at C, FP32 copy at C32; both column-major-like)
-  auto update = [&](const float* Vrp, int mr, int nbj, int ncols, double* C, float* C32) {
+  // FP32 rows X[c][i] (stride mp) -= V Y2
+  auto update = [&](const float* Vrp, int mr, int nbj, int ncols, float* X) {
     TcGemm g{};
     g.A = TcOperand{Vrp, mr, nbj, NB, 1, 0};
     g.B = TcOperand{Yt32, ncols, nbj, NB, 1, 0};
     g.M = mr; g.N = ncols; g.K = nbj; g.batch = 1;
-    g.C = C; g.c_fp64 = true; g.c_m = im1(1); g.c_n = im1(m); g.c_b = im0();
+    g.C = X; g.c_fp64 = false; g.c_m = im1(1); g.c_n = im1(mp); g.c_b = im0();
     g.alpha = -1.0; g.beta = 1.0;
     g.err = w.err;
-    g.C32 = C32; g.c32_m = im1(1); g.c32_n = im1(mp);
     return gemm_tc(g, s);
   };
   auto wy_prep = [&](int ksplit, int nbj, long long N, int ycol0, int ncol, const double* tau,
@@ -190,24 +212,31 @@ cudaError_t householder_qr_split(int m, int n, const double* M, double* Q, doubl
     const int j0 = p * NB, nbj = std::min(NB, n - j0), mr = m - j0, n2 = n - j0 - nbj;
     float* Vrp = Vr32 + (long long)p * m * NB;
     double *G, *tau;
-    if ((e = qr_panel_step(m, j0, nbj, w, s, &G, &tau, X32, mp, Vrp)) != cudaSuccess) return e;
+    if ((e = qr_panel_step(m, j0, nbj, w, s, &G, &tau, X32, mp, Vrp, p == 0 ? nullptr : X32)) !=
+        cudaSuccess)
+      return e;
     const float* Vrows = X32 + (long long)j0 * mp + j0;
     int ksplit = 1;
     if ((e = vt_times(Vrows, nbj, Vrows, n - j0, mr, &ksplit)) != cudaSuccess) return e;
     double* Tp = w.Tf + (size_t)p * NB * NB;
     if ((e = wy_prep(ksplit, nbj, n - j0, nbj, n2, tau, Tp, 0)) != cudaSuccess) return e;
     if (n2 > 0) {
-      if ((e = update(Vrp + (long long)j0 * NB, mr, nbj, n2, w.W + (size_t)(j0 + nbj) * m + j0,
+      if ((e = update(Vrp + (long long)j0 * NB, mr, nbj, n2,
                       X32 + (long long)(j0 + nbj) * mp + j0)) != cudaSuccess)
         return e;
     }
   }
-  if ((e = qr_extract_r(w.W, R, m, n, s)) != cudaSuccess) return e;
-  // Q = H_1 ... H_n [I; 0], panels in reverse order
+  {
+    const long long tot = (long long)n * n;
+    extract_r_split_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(w.W, X32, R, m, n, mp);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // Q = H_1 ... H_n [I; 0] in FP32 rows, panels in reverse order
   {
     const long long tot = (long long)m * n;
-    init_q_kernel<<<(unsigned)std::min<long long>((tot + 255) / 256, 8192), 256, 0, s>>>(Q, Q32, m,
-                                                                                         n, mp);
+    init_q32_kernel<<<(unsigned)std::min<long long>((tot + 255) / 256, 8192), 256, 0, s>>>(
+        Q32, m, n, mp);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -221,9 +250,7 @@ cudaError_t householder_qr_split(int m, int n, const double* M, double* Q, doubl
     if ((e = wy_prep(ksplit, nbj, nq, 0, nq, nullptr, w.Tf + (size_t)p * NB * NB, 1)) !=
         cudaSuccess)
       return e;
-    if ((e = update(Vrp, mr, nbj, nq, Q + (size_t)j0 * m + j0, Q32 + (long long)j0 * mp + j0)) !=
-        cudaSuccess)
-      return e;
+    if ((e = update(Vrp, mr, nbj, nq, Q32 + (long long)j0 * mp + j0)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

@@ -175,23 +175,26 @@ constexpr int kQrPanel = 32;   // panel width of the blocked QR
 // Factor panel columns j0..j0+nbj of w.W in place (FP64 Householder):
 // reflectors into w.V, tau and a G-sized scratch returned.  With X32 set,
 // FP32 copies of the reflectors also go to X32[c][i] (row stride ldx) and
-// Vr32[i][q] (row stride kQrPanel).
+// Vr32[i][q] (row stride kQrPanel).  With src32 set the panel's columns are
+// read from the FP32 rows src32[c][i] (stride ldx) instead of w.W.
 cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t s, double** G_out,
                           double** tau_out, float* X32 = nullptr, long long ldx = 0,
-                          float* Vr32 = nullptr);
+                          float* Vr32 = nullptr, const float* src32 = nullptr);
 cudaError_t qr_tfactor(const double* G, const double* tau, double* Tp, int nbj, cudaStream_t s);
 cudaError_t qr_extract_r(const double* W, double* R, int m, int n, cudaStream_t s);
 // Split-precision variant (tensor-core compact-WY products); f32 holds
 // qr_split_floats(m, n) floats, part the tensor-core split-K partial sums.
 size_t qr_split_floats(int m, int n);
-cudaError_t householder_qr_split(int m, int n, const double* M, double* Q, double* R,
-                                 const QrWork& w, float* f32, float* Q32, bool x32_ready,
-                                 float* part, long long part_elems, cudaStream_t s);
+cudaError_t householder_qr_split(int m, int n, const double* M, double* R, const QrWork& w,
+                                 float* f32, float* Q32, bool x32_ready, float* part,
+                                 long long part_elems, cudaStream_t s);
 // FP32 copy of the input inside f32 (row c = column c of M, row stride
 // pad4(m)); a caller that writes it itself passes x32_ready = true.
 float* qr_split_x32(float* f32);
 
 // out[r * stride + c] = (float) in[map(rmap, r) + map(cmap, c)], 0 <= c < ncols
+cudaError_t gather_f32f(const float* in, float* out, long long nrows, int ncols, long long stride,
+                        IdxMap rmap, IdxMap cmap, cudaStream_t s);
 cudaError_t gather_f32(const double* in, float* out, long long nrows, int ncols, long long stride,
                        IdxMap rmap, IdxMap cmap, cudaStream_t s);
 

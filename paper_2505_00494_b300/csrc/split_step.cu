@@ -100,12 +100,12 @@ cudaError_t qr_step_split(qrctm_ctx* c) {
   }
   {
     PhaseScope ps(c, QRCTM_PH_QR);
-    // Q, R in FP64 and Qc32[n][(b,d)] = Q[(b,d),n] from the QR itself
-    if ((e = householder_qr_split((int)m, ch, c->Mcm, c->Q, c->R, c->qrw, c->qr32, Qc32, true,
+    // R in FP64; Q as its FP32 rows Qc32[n][(b,d)] = Q[(b,d),n]
+    if ((e = householder_qr_split((int)m, ch, c->Mcm, c->R, c->qrw, c->qr32, Qc32, true,
                                   c->tc_part, c->tc_part_elems, st)) != cudaSuccess)
       return e;
     // Qt32[(mu,u)][a] = Q[(a,u),mu]
-    if ((e = gather_f32(c->Q, Qt32, m, ch, chp, im2(D2, 1, m), im1(D2), st)) != cudaSuccess)
+    if ((e = gather_f32f(Qc32, Qt32, m, ch, chp, im2(D2, 1, mp), im1(D2), st)) != cudaSuccess)
       return e;
   }
   {
