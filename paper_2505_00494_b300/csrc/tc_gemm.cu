@@ -400,6 +400,328 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent variant (BN <= 128): one CTA per SM walks the output tiles; the
+// TMEM accumulator pair is double buffered so that four dedicated epilogue
+// warps drain tile i while the MMA warp already accumulates tile i + 1, and
+// the TMA / converter ring runs on across tile boundaries.
+//
+// Warps (320 threads): 0 = TMA producer, 1 = TMEM owner + MMA issuer,
+// 2..5 = converters, 6..9 = epilogue (warp w reads TMEM lane quarter w % 4).
+// ---------------------------------------------------------------------------
+constexpr int NTHREADS_P = 320;
+
+template <int BN>
+struct CfgP {
+  static constexpr int A_BYTES = BM * BK * 4;
+  static constexpr int B_BYTES = BN * BK * 4;
+  static constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);
+  static constexpr int STG_BYTES = 4 * 32 * 33 * 4;                 // epilogue staging
+  // as many ring stages as fit the 227 KB opt-in limit next to the rest
+  static constexpr int STAGES =
+      std::min(4, (232448 - 2048 - STG_BYTES - 2 * BN * 8) / STAGE_BYTES);
+  static constexpr int HALF = BN <= 32 ? 32 : BN <= 64 ? 64 : 128;
+  static constexpr int TMEM_COLS = 4 * HALF;                        // 2 buffers x (main, corr)
+  static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + STG_BYTES + 1024 + 2 * BN * 8;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(NTHREADS_P, 1)
+    tc_tf32x3_persist(const __grid_constant__ CUtensorMap tmA,
+                      const __grid_constant__ CUtensorMap tmB, const TcArgs args) {
+  using C = CfgP<BN>;
+  static_assert(BN <= 128, "double-buffered accumulators need BN <= 128");
+  constexpr int S = C::STAGES;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  unsigned char* tiles = base;
+  float* stg_all = reinterpret_cast<float*>(base + S * C::STAGE_BYTES);
+  unsigned char* ctrl = base + S * C::STAGE_BYTES + C::STG_BYTES;
+  // full[S], conv[S], empty[S], accf[2], acce[2]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ctrl);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ctrl + 8 * (3 * S + 4));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(ctrl + 8 * (3 * S + 4) + 8);
+  volatile int* epi_stop = reinterpret_cast<volatile int*>(ctrl + 8 * (3 * S + 4) + 16);
+  long long* col_off = reinterpret_cast<long long*>(ctrl + 1024);
+  long long* col_off32 = col_off + BN;
+
+  auto xA = [&](int s) { return tiles + s * C::STAGE_BYTES; };
+  auto loA = [&](int s) { return tiles + s * C::STAGE_BYTES + C::A_BYTES; };
+  auto xB = [&](int s) { return tiles + s * C::STAGE_BYTES + 2 * C::A_BYTES; };
+  auto loB = [&](int s) { return tiles + s * C::STAGE_BYTES + 2 * C::A_BYTES + C::B_BYTES; };
+  const uint32_t full0 = smem_u32(&bars[0]), conv0 = smem_u32(&bars[S]),
+                 empty0 = smem_u32(&bars[2 * S]), accf0 = smem_u32(&bars[3 * S]),
+                 acce0 = smem_u32(&bars[3 * S + 2]);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long mt = (args.M + BM - 1) / BM, nt = (args.N + BN - 1) / BN;
+  const long long zt = (long long)args.batch * args.ksplit;
+  const long long ntiles = mt * nt * zt;
+  const int nkb_all = (int)((args.K + BK - 1) / BK);
+  // tile t -> (z, kz, m0, n0), n fastest
+  auto tile_of = [&](long long t, int& z, int& kz, long long& m0, int& n0, int& nkb, int& kb0) {
+    const long long tn = t % nt, tm = (t / nt) % mt, tz = t / (nt * mt);
+    z = (int)(tz / args.ksplit);
+    kz = (int)(tz % args.ksplit);
+    m0 = tm * BM;
+    n0 = (int)(tn * BN);
+    kb0 = kz * args.kb_per_split;
+    nkb = max(0, min(nkb_all - kb0, args.kb_per_split));
+  };
+  int issued = 0;   // TMA k-blocks issued (producer lane only)
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(conv0 + 8 * s, 4);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, 4);
+    }
+    *abort_flag = 0;
+    *epi_stop = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      int kbg = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        int z, kz, n0, nkb, kb0;
+        long long m0;
+        tile_of(t, z, kz, m0, n0, nkb, kb0);
+        const int za = args.a_batched ? z : 0, zb = args.b_batched ? z : 0;
+        for (int kb = 0; kb < nkb; ++kb, ++kbg) {
+          const int s = kbg % S;
+          if (kbg >= S && !mbar_wait(empty0 + 8 * s, ((kbg / S) - 1) & 1, abort_flag, args.err)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(full0 + 8 * s, C::A_BYTES + C::B_BYTES);
+          tma_load(smem_u32(xA(s)), &tmA, (kb0 + kb) * BK, (int)m0, za, full0 + 8 * s);
+          tma_load(smem_u32(xB(s)), &tmB, (kb0 + kb) * BK, n0, zb, full0 + 8 * s);
+          issued = kbg + 1;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_tf32(BM, BN);
+      int kbg = 0, it = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
+        int z, kz, n0, nkb, kb0;
+        long long m0;
+        tile_of(t, z, kz, m0, n0, nkb, kb0);
+        const int ab = it & 1;
+        // the epilogue must have drained this accumulator buffer (use it - 2)
+        if (it >= 2 && !mbar_wait(acce0 + 8 * ab, ((it >> 1) - 1) & 1, abort_flag, args.err)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dmain = tmem + ab * 2 * C::HALF, dcorr = dmain + C::HALF;
+        for (int kb = 0; kb < nkb; ++kb, ++kbg) {
+          const int s = kbg % S;
+          ok = mbar_wait(conv0 + 8 * s, (kbg / S) & 1, abort_flag, args.err);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t ah = smem_u32(xA(s)), al = smem_u32(loA(s));
+          const uint32_t bh = smem_u32(xB(s)), bl = smem_u32(loB(s));
+#pragma unroll
+          for (int ks = 0; ks < BK / 8; ++ks) {
+            const uint32_t off = ks * 32;
+            const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
+            umma_tf32(dmain, desc_sw128(ah + off), desc_sw128(bh + off), idesc, acc);
+            umma_tf32(dcorr, desc_sw128(ah + off), desc_sw128(bl + off), idesc, acc);
+            umma_tf32(dcorr, desc_sw128(al + off), desc_sw128(bh + off), idesc, 1u);
+          }
+          umma_commit(empty0 + 8 * s);
+        }
+        if (ok) umma_commit(accf0 + 8 * ab);
+      }
+    }
+  } else if (warp < 6) {
+    // ---------------- converters (warps 2..5) ----------------
+    const int t4 = threadIdx.x - 64;   // 0..127
+    int kbg = 0;
+    bool ok = true;
+    for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int z, kz, n0, nkb, kb0;
+      long long m0;
+      tile_of(t, z, kz, m0, n0, nkb, kb0);
+      for (int kb = 0; kb < nkb; ++kb, ++kbg) {
+        const int s = kbg % S;
+        if (!mbar_wait(full0 + 8 * s, (kbg / S) & 1, abort_flag, args.err)) {
+          ok = false;
+          break;
+        }
+        float4* xa = reinterpret_cast<float4*>(xA(s));
+        float4* la = reinterpret_cast<float4*>(loA(s));
+#pragma unroll
+        for (int i = 0; i < (BM * BK / 4) / 128; ++i) {
+          const int idx = t4 + 128 * i;
+          float4 v = xa[idx], h, l;
+          h.x = tf32_head(v.x); h.y = tf32_head(v.y); h.z = tf32_head(v.z); h.w = tf32_head(v.w);
+          l.x = v.x - h.x; l.y = v.y - h.y; l.z = v.z - h.z; l.w = v.w - h.w;
+          xa[idx] = h;
+          la[idx] = l;
+        }
+        float4* xb = reinterpret_cast<float4*>(xB(s));
+        float4* lb = reinterpret_cast<float4*>(loB(s));
+        for (int idx = t4; idx < BN * BK / 4; idx += 128) {
+          float4 v = xb[idx], h, l;
+          h.x = tf32_head(v.x); h.y = tf32_head(v.y); h.z = tf32_head(v.z); h.w = tf32_head(v.w);
+          l.x = v.x - h.x; l.y = v.y - h.y; l.z = v.z - h.z; l.w = v.w - h.w;
+          xb[idx] = h;
+          lb[idx] = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(conv0 + 8 * s);
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 6..9) ----------------
+    const int te = threadIdx.x - 192;   // 0..127
+    const int q = warp & 3;             // TMEM lane quarter of this warp
+    float* stg = stg_all + q * (32 * 33);
+    const bool col_unit = args.c_n.nd > 0 && args.c_n.str[0] == 1;
+    const bool split = args.ksplit > 1 || args.partials_only;
+    int it = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      int z, kz, n0, nkb, kb0;
+      long long m0;
+      tile_of(t, z, kz, m0, n0, nkb, kb0);
+      const int ab = it & 1;
+      asm volatile("bar.sync 2, 128;" ::: "memory");   // previous tile's offsets are dead
+      for (int j = te; j < BN; j += 128) {
+        const long long n = (long long)n0 + j;
+        col_off[j] = (n < args.N) ? map_off(args.c_n, n) : 0;
+        if (args.C32) col_off32[j] = (n < args.N) ? map_off(args.c32_n, n) : 0;
+      }
+      asm volatile("bar.sync 2, 128;" ::: "memory");
+      // a failed wait stops all four epilogue warps together: the flag is
+      // written only before the barrier below and read only after it
+      if (!mbar_wait(accf0 + 8 * ab, (it >> 1) & 1, abort_flag, args.err) && lane == 0)
+        *epi_stop = 1;
+      asm volatile("bar.sync 2, 128;" ::: "memory");
+      if (*epi_stop) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int row = q * 32 + lane;
+      const long long m = m0 + row;
+      const bool mvalid = m < args.M;
+      const long long base_off =
+          split ? (((long long)z * args.ksplit + kz) * args.M + (mvalid ? m : 0)) * args.N
+                : map_off(args.c_b, z) + (mvalid ? map_off(args.c_m, m) : 0);
+      const long long row32 = (args.C32 && mvalid) ? map_off(args.c32_m, m) : 0;
+      const uint32_t dmain = tmem + ab * 2 * C::HALF;
+#pragma unroll 1
+      for (int c = 0; c < (BN + 31) / 32; ++c) {
+        float v[32], w[32];
+        const uint32_t ta = dmain + (static_cast<uint32_t>(q * 32) << 16) + c * 32;
+        tmem_ld32(ta, v);
+        tmem_ld32(ta + C::HALF, w);
+        const int nv = min(32, min(BN - c * 32, (int)(args.N - n0 - c * 32)));
+        if (!split && !args.c_fp64 && args.beta == 0.0 && col_unit) {
+          const float al = static_cast<float>(args.alpha);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = al * (v[j] + w[j]);
+          __syncwarp();
+          const bool cvalid = lane < nv;
+          const long long co = cvalid ? col_off[c * 32 + lane] : 0;
+          float* outp = static_cast<float*>(args.C);
+          for (int rr = 0; rr < 32; ++rr) {
+            const long long bo = __shfl_sync(0xffffffffu, base_off, rr);
+            const int valid_r = __shfl_sync(0xffffffffu, mvalid ? 1 : 0, rr);
+            if (valid_r && cvalid) outp[bo + co] = stg[rr * 33 + lane];
+          }
+          __syncwarp();
+          continue;
+        }
+        if (!mvalid) continue;
+        if (split) {
+          float* p = args.part + base_off + n0 + c * 32;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (j < nv) p[j] = v[j] + w[j];
+          continue;
+        }
+        if (!args.c_fp64) {
+          const float al = static_cast<float>(args.alpha), be = static_cast<float>(args.beta);
+          float* p = static_cast<float*>(args.C) + base_off;
+          float o[32];
+          if (be != 0.f) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) o[j] = (j < nv) ? p[col_off[c * 32 + j]] : 0.f;
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            float r = al * (v[j] + w[j]);
+            if (be != 0.f) r = fmaf(be, o[j], r);
+            if (j < nv) p[col_off[c * 32 + j]] = r;
+          }
+          continue;
+        }
+        double r[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) r[j] = args.alpha * static_cast<double>(v[j] + w[j]);
+        double* p = static_cast<double*>(args.C) + base_off;
+        if (args.beta != 0.0) {
+          double old[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) old[j] = (j < nv) ? p[col_off[c * 32 + j]] : 0.0;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) r[j] = fma(args.beta, old[j], r[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j < nv) p[col_off[c * 32 + j]] = r[j];
+        if (args.C32) {
+          float* p32 = args.C32 + row32;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (j < nv) p32[col_off32[c * 32 + j]] = static_cast<float>(r[j]);
+        }
+      }
+      // this accumulator buffer may be overwritten by tile it + 2
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acce0 + 8 * ab);
+    }
+  }
+  // teardown: the TMEM owner frees the accumulators after everyone is done
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (*abort_flag && warp == 0 && lane == 0) {
+    for (int kb = (issued > S ? issued - S : 0); kb < issued; ++kb)
+      for (uint32_t i = 0; i < (1u << 20); ++i)
+        if (mbar_try_wait(full0 + 8 * (kb % S), (kb / S) & 1)) break;
+  }
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+  }
+}
+
 // out(b,m,n) = alpha * sum_z part[b][z][m][n] + beta * out: FP64 sums in a
 // fixed order (four interleaved partial sums, then their pairwise sum)
 __global__ void tc_splitk_reduce(const TcArgs a, int batch) {
@@ -475,13 +797,17 @@ bool make_map(CUtensorMap* tm, const TcOperand& op, int box_rows) {
   return r == CUDA_SUCCESS;
 }
 
-template <int BN>
+template <int BN, bool PERSIST>
 cudaError_t launch_bn(const TcGemm& g, cudaStream_t s) {
-  using C = Cfg<BN>;
+  const int smem_bytes = PERSIST ? CfgP<BN>::SMEM : Cfg<BN>::SMEM;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(tc_tf32x3_kernel<BN>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    cudaError_t e = PERSIST ? cudaFuncSetAttribute(tc_tf32x3_persist<BN <= 128 ? BN : 128>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   smem_bytes)
+                            : cudaFuncSetAttribute(tc_tf32x3_kernel<BN>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   smem_bytes);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
@@ -533,9 +859,16 @@ cudaError_t launch_bn(const TcGemm& g, cudaStream_t s) {
   a.c32_m = g.c32_m;
   a.c32_n = g.c32_n;
   if ((long long)std::max(1, g.batch) * ksplit > 65535) return cudaErrorInvalidValue;
-  dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + BN - 1) / BN),
-            (unsigned)(std::max(1, g.batch) * ksplit));
-  tc_tf32x3_kernel<BN><<<grid, NTHREADS, C::SMEM, s>>>(ta, tb, a);
+  a.batch = std::max(1, g.batch);
+  if (PERSIST) {
+    const long long ntiles = ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN) * a.batch * ksplit;
+    const unsigned grid = (unsigned)std::min<long long>(ntiles, nsm);
+    tc_tf32x3_persist<BN <= 128 ? BN : 128><<<grid, NTHREADS_P, smem_bytes, s>>>(ta, tb, a);
+  } else {
+    dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + BN - 1) / BN),
+              (unsigned)(std::max(1, g.batch) * ksplit));
+    tc_tf32x3_kernel<BN><<<grid, NTHREADS, smem_bytes, s>>>(ta, tb, a);
+  }
   note_launch();
   if (ksplit > 1 && !g.partials_only) {
     const long long tot = g.M * g.N * std::max(1, g.batch);
@@ -552,14 +885,17 @@ cudaError_t gemm_tc(const TcGemm& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
   if (g.A.rows < 1 || g.B.rows < 1 || g.A.K != g.K || g.B.K != g.K) return cudaErrorInvalidValue;
   if (g.batch > 65535 || g.M > (1ll << 31) - BM) return cudaErrorInvalidValue;
+  // the persistent kernel (double-buffered accumulators, BN <= 128) except
+  // for 128 < N <= 256, where one wider tile avoids re-reading A per N tile
   const long long N = g.N;
-  if (N <= 32) return launch_bn<32>(g, s);
-  if (N <= 48) return launch_bn<48>(g, s);
-  if (N <= 64) return launch_bn<64>(g, s);
-  if (N <= 80) return launch_bn<80>(g, s);
-  if (N <= 144 && N > 128) return launch_bn<144>(g, s);
-  if (N <= 128) return launch_bn<128>(g, s);
-  return launch_bn<256>(g, s);
+  if (N <= 32) return launch_bn<32, true>(g, s);
+  if (N <= 48) return launch_bn<48, true>(g, s);
+  if (N <= 64) return launch_bn<64, true>(g, s);
+  if (N <= 80) return launch_bn<80, true>(g, s);
+  if (N <= 128) return launch_bn<128, true>(g, s);
+  if (N <= 144) return launch_bn<144, false>(g, s);
+  if (N <= 256) return launch_bn<256, false>(g, s);
+  return launch_bn<128, true>(g, s);
 }
 
 }  // namespace qrctm

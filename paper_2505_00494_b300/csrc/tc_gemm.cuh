@@ -57,6 +57,7 @@ struct TcArgs {
   int kb_per_split;    // 32-wide K blocks per chunk
   float* part;         // ksplit > 1 or partials_only: partials [batch][ksplit][M][N]
   int partials_only;
+  int batch;           // batch entries (persistent kernel's tile count)
   float* C32;          // optional FP32 copy of the FP64 result
   IdxMap c32_m, c32_n;
 };
