@@ -65,7 +65,57 @@ __device__ __forceinline__ double sqrt_nr(double a) {
 // the partial sums of column j + 1 (the updated value of column j + 1 on a
 // row reaches the other lanes by a warp shuffle), so a column costs one
 // round of the arrival counter and four block barriers.
-template <bool TILE>
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ unsigned dsmem_addr(const T* local, unsigned rank) {
+  unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(local)), ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  return ra;
+}
+__device__ __forceinline__ double ld_dsmem_f64(const double* local, unsigned rank) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(dsmem_addr(local, rank)) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_dsmem_s32(const int* local, unsigned rank) {
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(dsmem_addr(local, rank)) : "memory");
+  return v;
+}
+
+// Panel factorisation.  With TILE, each CTA keeps its block of panel rows
+// (rows_per_cta x nb doubles) in shared memory for the whole factorisation, so
+// that a column step touches global memory only for the cross-CTA partial
+// sums and the published pivot row; the tile is written back (R entries,
+// reflectors) at the end.  Without TILE (very tall panels) the same steps
+// run on W in global memory.
+//
+// Column step j (c = j0 + j the pivot row), after all CTAs have published the
+// partial sums of column j (slot 0: sum_{i>c} x_i^2, slot t: sum_{i>c} x_i
+// y_{t,i} for column j + t) and the owner of row c has published that row:
+//   sigma = sum of slot 0, mu = sqrt(x_0^2 + sigma),
+//   w = x_0 - mu  (= -sigma / (x_0 + mu) for x_0 > 0),   tau = -w / mu,
+//   v = x / w (v_0 = 1),   y_t -= tau (y_{t,0} + s_t / w) v,   R_cc = mu.
+// The same pass over a CTA's rows that applies reflector j also accumulates
+// the partial sums of column j + 1 (the updated value of column j + 1 on a
+// row reaches the other lanes by a warp shuffle), so a column costs one
+// round of the arrival counter and four block barriers.
+//
+// CL > 1: the CTAs form clusters of CL; a cluster first adds its CTAs'
+// partial sums over distributed shared memory and only its rank-0 CTA
+// publishes and arrives, which divides the partial sums every CTA reads (and
+// the FP64 adds on B300's narrow FP64 pipe) and the global arrivals by CL at
+// the price of one cluster barrier per column.  A CTA whose wait gives up
+// still reaches that barrier; the cluster then stops together.
+template <bool TILE, int CL>
 __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
                                                       double* __restrict__ V,
                                                       double* __restrict__ tau_out,
@@ -74,19 +124,25 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
                                                       int rows_per_cta, float* __restrict__ X32,
                                                       long long ldx, float* __restrict__ Vr32,
                                                       const float* __restrict__ src32) {
+  constexpr bool CLU = CL > 1;
   const int P = gridDim.x, b = blockIdx.x;
+  const int NG = P / CL;                 // publishers: clusters (CL > 1) or CTAs
+  const int grp = b / CL;
+  const unsigned crank = CLU ? cluster_rank() : 0u;
   const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;   // wrp = row lane (0..7)
   const long long r_begin = (long long)j0 + (long long)b * rows_per_cta;
   const long long r_end = std::min<long long>(m, r_begin + rows_per_cta);
   const int rows = (int)std::max<long long>(0, r_end - r_begin);
-  // scratch: psum[2][P][NB], rowb[2][NB]
+  // scratch: psum[2][NG][NB], rowb[2][NB]
   double* psum = part;
-  double* rowb = part + 2 * (size_t)P * NB;
+  double* rowb = part + 2 * (size_t)PMAX * NB;
   __shared__ double red[8][NB];
   __shared__ double coef_s[NB];   // per lane: new y_t = y_t + coef_s[t] x on rows below c
   __shared__ double rcoef_s[NB];  // per lane: R_{c,j+t} = y_{t,0} - rcoef_s[t]
   __shared__ double sc[4];
   __shared__ double tau_s[NB];
+  __shared__ double cpart[2][NB];  // this CTA's partial sums (CL > 1)
+  __shared__ int c_abort[2];       // this CTA gave up waiting (CL > 1), by column parity
   __shared__ int s_ok;
   extern __shared__ double tile[];                 // [rows][NB + 1]
   // element (global row i, panel column jc)
@@ -97,6 +153,33 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
   auto sum8 = [&](int t) {
     return ((red[0][t] + red[1][t]) + (red[2][t] + red[3][t])) +
            ((red[4][t] + red[5][t]) + (red[6][t] + red[7][t]));
+  };
+  // publish the partial sums held by warp 0 (value v in lane t = slot t) for
+  // the column with parity buf; returns false when the cluster must stop
+  auto publish = [&](int buf, double v, bool aborted) -> bool {
+    if constexpr (!CLU) {
+      if (wrp == 0) {
+        psum[((size_t)buf * NG + b) * NB + lane] = v;
+        __syncwarp();
+        if (lane == 0) grid_arrive(bar);
+      }
+      return true;
+    } else {
+      if (wrp == 0) cpart[buf][lane] = v;
+      if (threadIdx.x == 0) c_abort[buf] = aborted ? 1 : 0;
+      cluster_sync_all();
+      int any = 0;
+      for (int q = 0; q < CL; ++q) any |= ld_dsmem_s32(&c_abort[buf], (unsigned)q);
+      if (any) return false;
+      if (crank == 0 && wrp == 0) {
+        double acc = 0.0;
+        for (int q = 0; q < CL; ++q) acc += ld_dsmem_f64(&cpart[buf][lane], (unsigned)q);
+        psum[((size_t)buf * NG + grp) * NB + lane] = acc;
+        __syncwarp();
+        if (lane == 0) grid_arrive(bar);
+      }
+      return true;
+    }
   };
   if (TILE) {
     // panel columns from W (FP64) or, when src32 is set, from the FP32 rows
@@ -110,6 +193,7 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     __syncthreads();
   }
   // partial sums of column 0 (slot t = lane) and the pivot row j0
+  bool stop = false;
   {
     const long long c = j0;
     double acc = 0.0;
@@ -119,106 +203,107 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     red[wrp][lane] = acc;
     if (c >= r_begin && c < r_end && (int)threadIdx.x < nb) rowb[threadIdx.x] = at(c, threadIdx.x);
     __syncthreads();
-    if (wrp == 0) {
-      psum[(size_t)b * NB + lane] = sum8(lane);
-      __syncwarp();
-      if (lane == 0) grid_arrive(bar);
-    }
+    stop = !publish(0, (wrp == 0) ? sum8(lane) : 0.0, false);
   }
 
   int j = 0;
-  for (; j < nb; ++j) {
+  for (; j < nb && !stop; ++j) {
     const int buf = j & 1;
     const long long c = (long long)j0 + j;
     const int nrem = nb - j - 1;
-    if (threadIdx.x == 0) s_ok = grid_wait(bar, (unsigned)P * (unsigned)(j + 1), err) ? 1 : 0;
-    __syncthreads();
-    if (!s_ok) break;
-    // cross-CTA reduction (L2 reads): lane = slot, the 8 warps take every 8th CTA
-    {
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      if (lane <= nrem) {
-        const double* ps = psum + (size_t)buf * P * NB + lane;
-        int q = wrp;
-        for (; q + 24 < P; q += 32) {
-          s0 += __ldcg(ps + (size_t)q * NB);
-          s1 += __ldcg(ps + (size_t)(q + 8) * NB);
-          s2 += __ldcg(ps + (size_t)(q + 16) * NB);
-          s3 += __ldcg(ps + (size_t)(q + 24) * NB);
-        }
-        for (; q < P; q += 8) s0 += __ldcg(ps + (size_t)q * NB);
-      }
-      red[wrp][lane] = (s0 + s1) + (s2 + s3);
-    }
-    __syncthreads();
-    if (wrp == 0) {
-      const double st = sum8(lane);                      // sigma (lane 0), s_t (lane t)
-      const double y0 = (lane <= nrem) ? __ldcg(rowb + buf * NB + lane) : 0.0;
-      double tau = 0.0, inv_w = 0.0, mu = 0.0;
-      if (lane == 0) {
-        const double x0 = y0, sigma = st;
-        mu = sqrt_nr(fma(x0, x0, sigma));
-        if (sigma == 0.0) {
-          tau = (x0 < 0.0) ? 2.0 : 0.0;                  // v = e_1
-          inv_w = 0.0;
-        } else if (x0 <= 0.0) {
-          const double w = x0 - mu;
-          tau = -w * rcp_nr(mu);
-          inv_w = rcp_nr(w);
-        } else {
-          const double xm = x0 + mu;
-          const double w = -sigma * rcp_nr(xm);
-          tau = -w * rcp_nr(mu);
-          inv_w = -xm * rcp_nr(sigma);
-        }
-        if (!(mu == mu) || isinf(mu)) atomicOr(err, ERRF_NUMERIC);
-        sc[0] = tau; sc[1] = inv_w; sc[2] = mu;
-        tau_s[j] = tau;
-      }
-      tau = __shfl_sync(0xffffffffu, tau, 0);
-      inv_w = __shfl_sync(0xffffffffu, inv_w, 0);
-      // row-update multiplier of lane t: new y_t = y_t + mult_t x  (lane 0: v = x / w)
-      double mult = 0.0, rc = 0.0;
-      if (lane == 0) {
-        mult = inv_w;
-      } else if (lane <= nrem) {
-        rc = tau * fma(st, inv_w, y0);
-        mult = -rc * inv_w;
-      }
-      coef_s[lane] = mult;
-      rcoef_s[lane] = rc;
-    }
-    __syncthreads();
-    const double mult = coef_s[lane];
-    const bool active = (lane <= nrem);
     const bool last = (j + 1 >= nb);
+    if (threadIdx.x == 0) s_ok = grid_wait(bar, (unsigned)NG * (unsigned)(j + 1), err) ? 1 : 0;
+    __syncthreads();
+    const bool ok = s_ok != 0;
+    if constexpr (!CLU) {
+      if (!ok) break;
+    }
     double acc = 0.0;
-    for (long long i = std::max<long long>(r_begin, c + 1) + wrp; i < r_end; i += 8) {
-      const double x = at(i, j);
-      const double old = (lane >= 1 && active) ? at(i, j + lane) : 0.0;
-      const double nv = fma(mult, x, old);
-      __syncwarp();
-      if (active) at(i, j + lane) = nv;
-      if (!last) {
-        const double xn = __shfl_sync(0xffffffffu, nv, 1);   // updated column j + 1
-        if (lane >= 1 && active) {
-          if (i > c + 1) acc = fma(xn, nv, acc);
-          else rowb[(buf ^ 1) * NB + lane - 1] = nv;       // pivot row of column j + 1
+    if (ok) {
+      // cross-unit reduction (L2 reads): lane = slot, the 8 warps take every 8th unit
+      {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        if (lane <= nrem) {
+          const double* ps = psum + (size_t)buf * NG * NB + lane;
+          int q = wrp;
+          for (; q + 24 < NG; q += 32) {
+            s0 += __ldcg(ps + (size_t)q * NB);
+            s1 += __ldcg(ps + (size_t)(q + 8) * NB);
+            s2 += __ldcg(ps + (size_t)(q + 16) * NB);
+            s3 += __ldcg(ps + (size_t)(q + 24) * NB);
+          }
+          for (; q < NG; q += 8) s0 += __ldcg(ps + (size_t)q * NB);
+        }
+        red[wrp][lane] = (s0 + s1) + (s2 + s3);
+      }
+      __syncthreads();
+      if (wrp == 0) {
+        const double st = sum8(lane);                      // sigma (lane 0), s_t (lane t)
+        const double y0 = (lane <= nrem) ? __ldcg(rowb + buf * NB + lane) : 0.0;
+        double tau = 0.0, inv_w = 0.0, mu = 0.0;
+        if (lane == 0) {
+          const double x0 = y0, sigma = st;
+          mu = sqrt_nr(fma(x0, x0, sigma));
+          if (sigma == 0.0) {
+            tau = (x0 < 0.0) ? 2.0 : 0.0;                  // v = e_1
+            inv_w = 0.0;
+          } else if (x0 <= 0.0) {
+            const double w = x0 - mu;
+            tau = -w * rcp_nr(mu);
+            inv_w = rcp_nr(w);
+          } else {
+            const double xm = x0 + mu;
+            const double w = -sigma * rcp_nr(xm);
+            tau = -w * rcp_nr(mu);
+            inv_w = -xm * rcp_nr(sigma);
+          }
+          if (!(mu == mu) || isinf(mu)) atomicOr(err, ERRF_NUMERIC);
+          sc[0] = tau; sc[1] = inv_w; sc[2] = mu;
+          tau_s[j] = tau;
+        }
+        tau = __shfl_sync(0xffffffffu, tau, 0);
+        inv_w = __shfl_sync(0xffffffffu, inv_w, 0);
+        // row-update multiplier of lane t: new y_t = y_t + mult_t x  (lane 0: v = x / w)
+        double mult = 0.0, rc = 0.0;
+        if (lane == 0) {
+          mult = inv_w;
+        } else if (lane <= nrem) {
+          rc = tau * fma(st, inv_w, y0);
+          mult = -rc * inv_w;
+        }
+        coef_s[lane] = mult;
+        rcoef_s[lane] = rc;
+      }
+      __syncthreads();
+      const double mult = coef_s[lane];
+      const bool active = (lane <= nrem);
+      for (long long i = std::max<long long>(r_begin, c + 1) + wrp; i < r_end; i += 8) {
+        const double x = at(i, j);
+        const double old = (lane >= 1 && active) ? at(i, j + lane) : 0.0;
+        const double nv = fma(mult, x, old);
+        __syncwarp();
+        if (active) at(i, j + lane) = nv;
+        if (!last) {
+          const double xn = __shfl_sync(0xffffffffu, nv, 1);   // updated column j + 1
+          if (lane >= 1 && active) {
+            if (i > c + 1) acc = fma(xn, nv, acc);
+            else rowb[(buf ^ 1) * NB + lane - 1] = nv;       // pivot row of column j + 1
+          }
         }
       }
-    }
-    // row c itself: the R entries (R_cc = mu; y_{t,0} - tau (y_{t,0} + s_t / w))
-    if (wrp == 0 && c >= r_begin && c < r_end) {
-      if (lane == 0) at(c, j) = sc[2];
-      else if (active) at(c, j + lane) -= rcoef_s[lane];
+      // row c itself: the R entries (R_cc = mu; y_{t,0} - tau (y_{t,0} + s_t / w))
+      if (wrp == 0 && c >= r_begin && c < r_end) {
+        if (lane == 0) at(c, j) = sc[2];
+        else if (active) at(c, j + lane) -= rcoef_s[lane];
+      }
     }
     if (last) break;
     red[wrp][lane] = acc;                                  // slot lane - 1 of column j + 1
     __syncthreads();
-    if (wrp == 0) {
-      if (lane < nrem) psum[((size_t)(buf ^ 1) * P + b) * NB + lane] = sum8(lane + 1);
-      __syncwarp();
-      if (lane == 0) grid_arrive(bar);
+    const double v = (wrp == 0 && lane < nrem) ? sum8(lane + 1) : 0.0;
+    if (!publish(buf ^ 1, v, !ok)) break;
+    if constexpr (!CLU) {
+      (void)0;
     }
   }
   __syncthreads();
@@ -240,6 +325,8 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
   }
   // tau of the panel columns for the compact-WY factor (built after the kernel)
   if (b == 0 && threadIdx.x < (unsigned)nb) tau_out[threadIdx.x] = tau_s[threadIdx.x];
+  // no CTA of a cluster may leave while others can still read its shared memory
+  if constexpr (CLU) cluster_sync_all();
   if (threadIdx.x == 0) grid_exit(bar, (unsigned)P);
 }
 
@@ -304,8 +391,7 @@ cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t 
                           double** tau_out, float* X32, long long ldx, float* Vr32,
                           const float* src32) {
   const int mr = m - j0;
-  const int P = qr_panel_grid(mr);
-  int rpc = (mr + P - 1) / P;
+  int P = qr_panel_grid(mr);
   double* W = w.W; double* V = w.V; double* part = w.part;
   double* Gp = w.part + 2 * (size_t)PMAX * NB + 2 * NB;
   double* taup = Gp + NB * NB;
@@ -315,23 +401,82 @@ cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t 
   float* vr32 = Vr32;
   const float* s32 = src32;
   long long ldx_ = ldx;
-  void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc, &x32, &ldx_, &vr32, &s32};
-  const size_t tile = sizeof(double) * (size_t)rpc * (NB + 1);
-  cudaError_t e;
-  if (src32 != nullptr && tile > kPanelTileMax) return cudaErrorInvalidValue;   // tiled path only
+  cudaError_t e = cudaErrorUnknown;
+  bool launched = false;
   if (w.hook) w.hook(w.hook_user, 1);
-  if (tile <= kPanelTileMax) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(qr_panel_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kPanelTileMax);
-      attr = true;
+  // clusters of 4 CTAs (cooperative cluster launch) where the device allows
+  // it and the grid is large enough; else one CTA per publisher
+  static int cl_state = -1, cl_max = 0;   // -1 unknown, 0 unavailable, 1 available
+  if (P >= 8 && cl_state != 0) {
+    auto kern = qr_panel_kernel<true, 4>;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 4;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeCooperative;
+    at[1].val.cooperative = 1;
+    cfg.blockDim = dim3(PT);
+    cfg.stream = s;
+    cfg.attrs = at;
+    if (cl_state < 0) {
+      cl_state = 0;
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kPanelTileMax) == cudaSuccess) {
+        cfg.gridDim = dim3(4);
+        cfg.dynamicSmemBytes = kPanelTileMax;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) == cudaSuccess && nc >= 2) {
+          cl_state = 1;
+          cl_max = nc;
+        }
+      }
+      cudaGetLastError();
     }
-    e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<true>, dim3(P), dim3(PT), args,
-                                    tile, s);
-  } else {
-    e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<false>, dim3(P), dim3(PT), args,
-                                    0, s);
+    if (cl_state == 1) {
+      const int Pc = std::min((P / 4) * 4, 4 * cl_max);
+      int rpc = (mr + Pc - 1) / Pc;
+      const size_t tile = sizeof(double) * (size_t)rpc * (NB + 1);
+      if (tile <= kPanelTileMax) {
+        void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc, &x32, &ldx_,
+                        &vr32, &s32};
+        cfg.gridDim = dim3(Pc);
+        cfg.dynamicSmemBytes = tile;
+        cfg.numAttrs = 2;
+        e = cudaLaunchKernelExC(&cfg, (const void*)kern, args);
+        if (e == cudaSuccess) {
+          launched = true;
+        } else {
+          cudaGetLastError();   // the device refused the cooperative cluster launch
+          cl_state = 0;
+        }
+      }
+    }
+  }
+  if (!launched) {
+    int rpc = (mr + P - 1) / P;
+    void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc, &x32, &ldx_, &vr32,
+                    &s32};
+    const size_t tile = sizeof(double) * (size_t)rpc * (NB + 1);
+    if (src32 != nullptr && tile > kPanelTileMax) {
+      if (w.hook) w.hook(w.hook_user, 0);
+      return cudaErrorInvalidValue;   // an FP32 source needs the tiled path
+    }
+    if (tile <= kPanelTileMax) {
+      static bool attr = false;
+      if (!attr) {
+        cudaFuncSetAttribute(qr_panel_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kPanelTileMax);
+        attr = true;
+      }
+      e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<true, 1>, dim3(P), dim3(PT),
+                                      args, tile, s);
+    } else {
+      e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<false, 1>, dim3(P), dim3(PT),
+                                      args, 0, s);
+    }
   }
   if (w.hook) w.hook(w.hook_user, 0);
   if (e != cudaSuccess) return e;
