@@ -122,8 +122,9 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
                                                       double* __restrict__ part, GridBar* bar,
                                                       int* err, int m, int j0, int nb,
                                                       int rows_per_cta, float* __restrict__ X32,
-                                                      long long ldx, float* __restrict__ Vr32,
-                                                      const float* __restrict__ src32) {
+                                                      long long ldx, float* __restrict__ Vt32,
+                                                      const float* __restrict__ src32,
+                                                      float* __restrict__ V32, long long ldv) {
   constexpr bool CLU = CL > 1;
   const int P = gridDim.x, b = blockIdx.x;
   const int NG = P / CL;                 // publishers: clusters (CL > 1) or CTAs
@@ -309,8 +310,8 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
   __syncthreads();
   // write back: panel rows of W (R above/on the diagonal, reflectors below)
   // and the explicit reflectors V (zero above the unit diagonal); optionally
-  // FP32 copies of V for the tensor-core WY products: X32[c][i] (row c of a
-  // K-contiguous operand, row stride ldx) and Vr32[i][jc] (row stride NB)
+  // FP32 copies of V for the tensor-core WY products: X32[c][i] and V32[c][i]
+  // (rows c, row stride ldx) and Vt32[i][c] (row stride ldv)
   for (int e = threadIdx.x; e < rows * nb; e += PT) {
     const int r = e % rows, jc = e / rows;
     const long long i = r_begin + r, c = (long long)j0 + jc;
@@ -319,8 +320,10 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     const double v = (i < c) ? 0.0 : (i == c ? 1.0 : x);
     V[c * m + i] = v;
     if (X32) {
-      X32[c * ldx + i] = static_cast<float>(v);
-      Vr32[i * NB + jc] = static_cast<float>(v);
+      const float vf = static_cast<float>(v);
+      X32[c * ldx + i] = vf;
+      V32[c * ldx + i] = vf;
+      Vt32[i * ldv + c] = vf;
     }
   }
   // tau of the panel columns for the compact-WY factor (built after the kernel)
@@ -388,8 +391,8 @@ __global__ void set_identity_cols_kernel(double* Q, int m, int n) {
 // reflectors into w.V, tau and the Gram-based T factor into w.Tf (stride NB).
 // gram_tc: compute G = V^T V with the caller's contraction (nullptr = FP64).
 cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t s, double** G_out,
-                          double** tau_out, float* X32, long long ldx, float* Vr32,
-                          const float* src32) {
+                          double** tau_out, float* X32, long long ldx, float* Vt32,
+                          const float* src32, float* V32, long long ldv) {
   const int mr = m - j0;
   int P = qr_panel_grid(mr);
   double* W = w.W; double* V = w.V; double* part = w.part;
@@ -398,9 +401,10 @@ cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t 
   GridBar* bar = w.bar; int* err = w.err;
   int m_ = m, j0_ = j0, nb_ = nbj;
   float* x32 = X32;
-  float* vr32 = Vr32;
+  float* vt32 = Vt32;
+  float* v32 = V32;
   const float* s32 = src32;
-  long long ldx_ = ldx;
+  long long ldx_ = ldx, ldv_ = ldv;
   cudaError_t e = cudaErrorUnknown;
   bool launched = false;
   if (w.hook) w.hook(w.hook_user, 1);
@@ -441,7 +445,7 @@ cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t 
       const size_t tile = sizeof(double) * (size_t)rpc * (NB + 1);
       if (tile <= kPanelTileMax) {
         void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc, &x32, &ldx_,
-                        &vr32, &s32};
+                        &vt32, &s32, &v32, &ldv_};
         cfg.gridDim = dim3(Pc);
         cfg.dynamicSmemBytes = tile;
         cfg.numAttrs = 2;
@@ -457,8 +461,8 @@ cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t 
   }
   if (!launched) {
     int rpc = (mr + P - 1) / P;
-    void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc, &x32, &ldx_, &vr32,
-                    &s32};
+    void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc, &x32, &ldx_, &vt32,
+                    &s32, &v32, &ldv_};
     const size_t tile = sizeof(double) * (size_t)rpc * (NB + 1);
     if (src32 != nullptr && tile > kPanelTileMax) {
       if (w.hook) w.hook(w.hook_user, 0);

@@ -19,9 +19,13 @@
 // kept in FP32 only (X32, rows = columns of ct): each panel converts its 32
 // columns to FP64 when it loads them (the first panel reads ct itself in
 // FP64), and the entries of R above a panel's diagonal block come from X32.
-// Q = H_1 ... H_n [I; 0] is formed panel by panel in reverse with the same
-// three launches (T kept from step 3, Y2 = T (V^T Q_s)), in FP32 only: its
-// rows Q32[c][i] (= column c of Q) are what the rest of the step consumes.
+// Q = H_1 ... H_n [I; 0] comes from the aggregated compact-WY form of all n
+// reflectors, I - V T V^T with T^-1 = diag(1/tau) + striu(V^T V):
+//   Q = [I; 0] - V W,   W = T V_top^T  (V_top = the first n rows of V),
+// i.e. one tensor-core Gram product V^T V, a triangular solve U W = V_top^T
+// (U = T^-1; one warp per column of W, FP32 -- Q is FP32 in this path) and
+// one tensor-core product V W.  Its rows Q32[c][i] (= column c of Q) are
+// what the rest of the step consumes.
 #include "qrctm_internal.cuh"
 #include "tc_gemm.cuh"
 
@@ -126,6 +130,74 @@ __global__ void __launch_bounds__(kWyThreads) wy_prep_kernel(const float* __rest
   }
 }
 
+// UT[i][l] = U[l][i] for the aggregated compact-WY factor U = T^-1:
+// U[l][i] = (V^T V)[l][i] for l < i, 1/tau_i for l = i, 0 below; G = V^T V
+// from its K-chunk partials [ksplit][n][n] (compensated FP32 summation), tau
+// from the diagonals of the per-panel T factors (Tf, stride NB x NB per panel).
+__global__ void build_ut_kernel(const float* __restrict__ part, int ksplit, int n,
+                                const double* __restrict__ Tf, float* __restrict__ UT,
+                                long long ldu) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  const int i = (int)(e / n), l = (int)(e % n);
+  float v = 0.f;
+  if (l < i) {
+    const long long nn = (long long)n * n;
+    const float* p = part + (long long)l * n + i;
+    float sh = 0.f, se = 0.f;
+    for (int z = 0; z < ksplit; ++z) {
+      const float x = p[(long long)z * nn];
+      const float t = sh + x;
+      const float bp = t - sh;
+      se += (sh - (t - bp)) + (x - bp);
+      sh = t;
+    }
+    v = sh + se;
+  } else if (l == i) {
+    const double tau = Tf[(size_t)(i / NB) * NB * NB + (i % NB) * NB + (i % NB)];
+    v = static_cast<float>(1.0 / tau);
+  }
+  UT[(long long)i * ldu + l] = v;
+}
+
+// Wt[k][i] = W[i][k] with U W = V_top^T, one warp per column k: b_i =
+// V[k][i] (zero for i > k), back substitution in axpy form from i = k down:
+// x_i = b_i tau_i (= b_i / U_ii), then b_l -= U[l][i] x_i for l < i.
+constexpr int kSolveMaxPerLane = 16;   // n <= 512
+__global__ void __launch_bounds__(256) q_solve_kernel(const float* __restrict__ UT, long long ldu,
+                                                      const float* __restrict__ Vt,
+                                                      long long ldv, const double* __restrict__ Tf,
+                                                      int n, float* __restrict__ Wt) {
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (k >= n) return;
+  float b[kSolveMaxPerLane];   // b[q] holds entry i = lane + 32 q
+#pragma unroll
+  for (int qq = 0; qq < kSolveMaxPerLane; ++qq) {
+    const int i = lane + 32 * qq;
+    b[qq] = (i <= k && i < n) ? Vt[(long long)k * ldv + i] : 0.f;
+  }
+  float* out = Wt + (long long)k * ldv;
+  for (int i = lane; i < n; i += 32) out[i] = 0.f;
+  __syncwarp();
+  for (int i = k; i >= 0; --i) {
+    const int owner = i & 31, slot = i >> 5;
+    float bi = 0.f;
+#pragma unroll
+    for (int qq = 0; qq < kSolveMaxPerLane; ++qq)
+      if (qq == slot) bi = b[qq];
+    const float tau_i = static_cast<float>(Tf[(size_t)(i / NB) * NB * NB + (i % NB) * NB + (i % NB)]);
+    const float xi = __shfl_sync(0xffffffffu, bi, owner) * tau_i;
+    if (lane == 0) out[i] = xi;
+    const float* ui = UT + (long long)i * ldu;   // U[l][i] for l < i
+#pragma unroll
+    for (int qq = 0; qq < kSolveMaxPerLane; ++qq) {
+      const int l = lane + 32 * qq;
+      if (l < i) b[qq] = fmaf(-ui[l], xi, b[qq]);
+    }
+  }
+}
+
 // Q32[c][i] = delta_ci (the FP32 rows of Q = [I; 0]), row stride ldq
 __global__ void init_q32_kernel(float* Q32, int m, int n, long long ldq) {
   const long long tot = (long long)m * n;
@@ -152,8 +224,9 @@ __global__ void extract_r_split_kernel(const double* __restrict__ W, const float
 }  // namespace
 
 size_t qr_split_floats(int m, int n) {
-  const long long mp = pad4(m), npan = (n + NB - 1) / NB;
-  return (size_t)(n * mp + npan * (long long)m * NB + (long long)n * NB + 1024);
+  const long long mp = pad4(m), ldv = pad4(n);
+  return (size_t)(2 * n * mp + (long long)m * ldv + (long long)n * NB + 2 * (long long)n * ldv +
+                  1024);
 }
 
 float* qr_split_x32(float* f32) { return f32; }
@@ -162,15 +235,22 @@ cudaError_t householder_qr_split(int m, int n, const double* M, double* R, const
                                  float* f32, float* Q32, bool x32_ready, float* part,
                                  long long part_elems, cudaStream_t s) {
   if (m < n || n <= 0) return cudaErrorInvalidValue;
-  const long long mp = pad4(m);
+  if (n > 32 * kSolveMaxPerLane) return cudaErrorInvalidValue;
+  const long long mp = pad4(m), ldv = pad4(n);
   const int npan = (n + NB - 1) / NB;
   float* X32 = f32;                                  // [c][i]   n x mp  (W, then V rows)
-  float* Vr32 = X32 + (long long)n * mp;             // [p][i][q] npan x m x NB
-  float* Yt32 = Vr32 + (long long)npan * m * NB;     // [c][q]   n x NB
+  float* V32 = X32 + (long long)n * mp;              // [c][i]   n x mp  (V, zero above)
+  float* Vt32 = V32 + (long long)n * mp;             // [i][c]   m x ldv (V, zero above)
+  float* Yt32 = Vt32 + (long long)m * ldv;           // [c][q]   n x NB
+  float* UT = Yt32 + (long long)n * NB;              // [i][l]   n x ldv
+  float* Wt = UT + (long long)n * ldv;               // [k][i]   n x ldv
   // the first panel reads ct in FP64 through w.W
   cudaError_t e = cudaMemcpyAsync(w.W, M, sizeof(double) * (size_t)m * std::min(n, NB),
                                   cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
+  // reflector copies are written from their diagonal down; clear the rest
+  if ((e = cudaMemsetAsync(V32, 0, sizeof(float) * (size_t)(n * mp + m * ldv), s)) != cudaSuccess)
+    return e;
   if (!x32_ready &&
       (e = gather_f32(M, X32, n, m, mp, im1(m), im1(1), s)) != cudaSuccess)
     return e;
@@ -189,41 +269,32 @@ cudaError_t householder_qr_split(int m, int n, const double* M, double* R, const
     g.max_ksplit = kQrMaxKsplit;
     return gemm_tc(g, s);
   };
-  // FP32 rows X[c][i] (stride mp) -= V Y2
-  auto update = [&](const float* Vrp, int mr, int nbj, int ncols, float* X) {
-    TcGemm g{};
-    g.A = TcOperand{Vrp, mr, nbj, NB, 1, 0};
-    g.B = TcOperand{Yt32, ncols, nbj, NB, 1, 0};
-    g.M = mr; g.N = ncols; g.K = nbj; g.batch = 1;
-    g.C = X; g.c_fp64 = false; g.c_m = im1(1); g.c_n = im1(mp); g.c_b = im0();
-    g.alpha = -1.0; g.beta = 1.0;
-    g.err = w.err;
-    return gemm_tc(g, s);
-  };
-  auto wy_prep = [&](int ksplit, int nbj, long long N, int ycol0, int ncol, const double* tau,
-                     double* Tp, int mode) {
-    const unsigned grid = (unsigned)std::max(1, (ncol + NB - 1) / NB);
-    wy_prep_kernel<<<grid, kWyThreads, 0, s>>>(part, ksplit, nbj, N, ycol0, ncol, tau, Tp, Yt32,
-                                                mode);
-    note_launch();
-    return cudaGetLastError();
-  };
   for (int p = 0; p < npan; ++p) {
     const int j0 = p * NB, nbj = std::min(NB, n - j0), mr = m - j0, n2 = n - j0 - nbj;
-    float* Vrp = Vr32 + (long long)p * m * NB;
     double *G, *tau;
-    if ((e = qr_panel_step(m, j0, nbj, w, s, &G, &tau, X32, mp, Vrp, p == 0 ? nullptr : X32)) !=
-        cudaSuccess)
+    if ((e = qr_panel_step(m, j0, nbj, w, s, &G, &tau, X32, mp, Vt32, p == 0 ? nullptr : X32, V32,
+                           ldv)) != cudaSuccess)
       return e;
     const float* Vrows = X32 + (long long)j0 * mp + j0;
     int ksplit = 1;
     if ((e = vt_times(Vrows, nbj, Vrows, n - j0, mr, &ksplit)) != cudaSuccess) return e;
     double* Tp = w.Tf + (size_t)p * NB * NB;
-    if ((e = wy_prep(ksplit, nbj, n - j0, nbj, n2, tau, Tp, 0)) != cudaSuccess) return e;
+    const unsigned grid = (unsigned)std::max(1, (n2 + NB - 1) / NB);
+    wy_prep_kernel<<<grid, kWyThreads, 0, s>>>(part, ksplit, nbj, n - j0, nbj, n2, tau, Tp, Yt32,
+                                                0);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (n2 > 0) {
-      if ((e = update(Vrp + (long long)j0 * NB, mr, nbj, n2,
-                      X32 + (long long)(j0 + nbj) * mp + j0)) != cudaSuccess)
-        return e;
+      // FP32 trailing rows X[c][i] -= V Y2
+      TcGemm g{};
+      g.A = TcOperand{Vt32 + (long long)j0 * ldv + j0, mr, nbj, ldv, 1, 0};
+      g.B = TcOperand{Yt32, n2, nbj, NB, 1, 0};
+      g.M = mr; g.N = n2; g.K = nbj; g.batch = 1;
+      g.C = X32 + (long long)(j0 + nbj) * mp + j0; g.c_fp64 = false;
+      g.c_m = im1(1); g.c_n = im1(mp); g.c_b = im0();
+      g.alpha = -1.0; g.beta = 1.0;
+      g.err = w.err;
+      if ((e = gemm_tc(g, s)) != cudaSuccess) return e;
     }
   }
   {
@@ -232,27 +303,29 @@ cudaError_t householder_qr_split(int m, int n, const double* M, double* R, const
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  // Q = H_1 ... H_n [I; 0] in FP32 rows, panels in reverse order
+  // Q = [I; 0] - V W with U W = V_top^T
+  int ksplit = 1;
+  if ((e = vt_times(V32, n, V32, n, m, &ksplit)) != cudaSuccess) return e;   // G = V^T V
   {
-    const long long tot = (long long)m * n;
-    init_q32_kernel<<<(unsigned)std::min<long long>((tot + 255) / 256, 8192), 256, 0, s>>>(
+    const long long tot = (long long)n * n;
+    build_ut_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, ksplit, n, w.Tf, UT, ldv);
+    note_launch();
+    q_solve_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(UT, ldv, Vt32, ldv, w.Tf, n, Wt);
+    note_launch();
+    const long long totq = (long long)m * n;
+    init_q32_kernel<<<(unsigned)std::min<long long>((totq + 255) / 256, 8192), 256, 0, s>>>(
         Q32, m, n, mp);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  for (int p = npan - 1; p >= 0; --p) {
-    const int j0 = p * NB, nbj = std::min(NB, n - j0), mr = m - j0, nq = n - j0;
-    const float* Vrows = X32 + (long long)j0 * mp + j0;
-    const float* Vrp = Vr32 + (long long)p * m * NB + (long long)j0 * NB;
-    int ksplit = 1;
-    if ((e = vt_times(Vrows, nbj, Q32 + (long long)j0 * mp + j0, nq, mr, &ksplit)) != cudaSuccess)
-      return e;
-    if ((e = wy_prep(ksplit, nbj, nq, 0, nq, nullptr, w.Tf + (size_t)p * NB * NB, 1)) !=
-        cudaSuccess)
-      return e;
-    if ((e = update(Vrp, mr, nbj, nq, Q32 + (long long)j0 * mp + j0)) != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  TcGemm g{};
+  g.A = TcOperand{Vt32, m, n, ldv, 1, 0};
+  g.B = TcOperand{Wt, n, n, ldv, 1, 0};
+  g.M = m; g.N = n; g.K = n; g.batch = 1;
+  g.C = Q32; g.c_fp64 = false; g.c_m = im1(1); g.c_n = im1(mp); g.c_b = im0();
+  g.alpha = -1.0; g.beta = 1.0;
+  g.err = w.err;
+  return gemm_tc(g, s);
 }
 
 }  // namespace qrctm

@@ -174,12 +174,13 @@ cudaError_t householder_qr_f64(int m, int n, const double* M, double* Q, double*
 constexpr int kQrPanel = 32;   // panel width of the blocked QR
 // Factor panel columns j0..j0+nbj of w.W in place (FP64 Householder):
 // reflectors into w.V, tau and a G-sized scratch returned.  With X32 set,
-// FP32 copies of the reflectors also go to X32[c][i] (row stride ldx) and
-// Vr32[i][q] (row stride kQrPanel).  With src32 set the panel's columns are
-// read from the FP32 rows src32[c][i] (stride ldx) instead of w.W.
+// FP32 copies of the reflectors also go to X32[c][i] and V32[c][i] (row
+// stride ldx) and Vt32[i][c] (row stride ldv).  With src32 set the panel's
+// columns are read from the FP32 rows src32[c][i] (stride ldx) instead of w.W.
 cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t s, double** G_out,
                           double** tau_out, float* X32 = nullptr, long long ldx = 0,
-                          float* Vr32 = nullptr, const float* src32 = nullptr);
+                          float* Vt32 = nullptr, const float* src32 = nullptr,
+                          float* V32 = nullptr, long long ldv = 0);
 cudaError_t qr_tfactor(const double* G, const double* tau, double* Tp, int nbj, cudaStream_t s);
 cudaError_t qr_extract_r(const double* W, double* R, int m, int n, cudaStream_t s);
 // Split-precision variant (tensor-core compact-WY products); f32 holds
