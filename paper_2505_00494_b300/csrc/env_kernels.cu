@@ -349,6 +349,11 @@ __device__ __forceinline__ unsigned cluster_rank() {
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
   return r;
 }
+__device__ __forceinline__ unsigned cluster_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
 __device__ __forceinline__ double ld_dsmem(const double* local_addr, unsigned rank) {
   unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(local_addr)), ra;
   double v;
@@ -364,6 +369,11 @@ __global__ void __launch_bounds__(256) spectrum_cluster_kernel(const double* __r
   __shared__ double red[32];
   __shared__ double sc[4];
   __shared__ double pv_part;
+  // the row distribution needs exactly CS CTAs in one cluster
+  if (cluster_size() != (unsigned)CS || gridDim.x != (unsigned)CS) {
+    if (threadIdx.x == 0) atomicOr(err, ERRF_BOUNDS);
+    return;
+  }
   const unsigned r = cluster_rank();
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wrp = tid >> 5;
   const int nloc = (n - (int)r + CS - 1) / CS;          // rows r, r + CS, ...

@@ -74,6 +74,11 @@ __device__ __forceinline__ unsigned cluster_rank() {
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
   return r;
 }
+__device__ __forceinline__ unsigned cluster_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
 template <typename T>
 __device__ __forceinline__ unsigned dsmem_addr(const T* local, unsigned rank) {
   unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(local)), ra;
@@ -126,6 +131,14 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
                                                       const float* __restrict__ src32,
                                                       float* __restrict__ V32, long long ldv) {
   constexpr bool CLU = CL > 1;
+  if constexpr (CLU) {
+    // the distributed-shared-memory exchange needs exactly CL CTAs per
+    // cluster; any other launch shape reports an error and touches nothing
+    if (cluster_size() != (unsigned)CL || (gridDim.x % CL) != 0) {
+      if (threadIdx.x == 0) atomicOr(err, ERRF_BOUNDS);
+      return;
+    }
+  }
   const int P = gridDim.x, b = blockIdx.x;
   const int NG = P / CL;                 // publishers: clusters (CL > 1) or CTAs
   const int grp = b / CL;
@@ -408,19 +421,17 @@ cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t 
   cudaError_t e = cudaErrorUnknown;
   bool launched = false;
   if (w.hook) w.hook(w.hook_user, 1);
-  // clusters of 4 CTAs (cooperative cluster launch) where the device allows
-  // it and the grid is large enough; else one CTA per publisher
+  // clusters of 4 CTAs where the device can place them and the grid is large
+  // enough; else a cooperative launch with one CTA per publisher
   static int cl_state = -1, cl_max = 0;   // -1 unknown, 0 unavailable, 1 available
   if (P >= 8 && cl_state != 0) {
     auto kern = qr_panel_kernel<true, 4>;
     cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[2];
+    cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = 4;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
-    at[1].id = cudaLaunchAttributeCooperative;
-    at[1].val.cooperative = 1;
     cfg.blockDim = dim3(PT);
     cfg.stream = s;
     cfg.attrs = at;
@@ -446,9 +457,11 @@ cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t 
       if (tile <= kPanelTileMax) {
         void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc, &x32, &ldx_,
                         &vt32, &s32, &v32, &ldv_};
+        // every CTA must be resident at once: the grid is capped at the
+        // occupancy query's cluster count (waits are bounded regardless)
         cfg.gridDim = dim3(Pc);
         cfg.dynamicSmemBytes = tile;
-        cfg.numAttrs = 2;
+        cfg.numAttrs = 1;
         e = cudaLaunchKernelExC(&cfg, (const void*)kern, args);
         if (e == cudaSuccess) {
           launched = true;

@@ -162,12 +162,24 @@ __global__ void build_ut_kernel(const float* __restrict__ part, int ksplit, int 
 
 // Wt[k][i] = W[i][k] with U W = V_top^T, one warp per column k: b_i =
 // V[k][i] (zero for i > k), back substitution in axpy form from i = k down:
-// x_i = b_i tau_i (= b_i / U_ii), then b_l -= U[l][i] x_i for l < i.
+// x_i = b_i tau_i (= b_i / U_ii), then b_l -= U[l][i] x_i for l < i.  The
+// rows of U^T and tau are staged in shared memory (all eight warps of a CTA
+// use them) when they fit, else each row is loaded one step ahead.
 constexpr int kSolveMaxPerLane = 16;   // n <= 512
+constexpr int kSolveSmemMaxN = 200;    // U^T staged in shared memory up to n = 200
 __global__ void __launch_bounds__(256) q_solve_kernel(const float* __restrict__ UT, long long ldu,
                                                       const float* __restrict__ Vt,
                                                       long long ldv, const double* __restrict__ Tf,
                                                       int n, float* __restrict__ Wt) {
+  extern __shared__ float qs[];
+  const bool staged = n <= kSolveSmemMaxN;
+  float* taus = qs;                       // [n]
+  float* us = qs + ((n + 3) & ~3);        // [n][n] when staged
+  for (int e = threadIdx.x; e < n; e += blockDim.x)
+    taus[e] = static_cast<float>(Tf[(size_t)(e / NB) * NB * NB + (e % NB) * NB + (e % NB)]);
+  if (staged)
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) us[e] = UT[(long long)(e / n) * ldu + e % n];
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int k = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (k >= n) return;
@@ -180,21 +192,30 @@ __global__ void __launch_bounds__(256) q_solve_kernel(const float* __restrict__ 
   float* out = Wt + (long long)k * ldv;
   for (int i = lane; i < n; i += 32) out[i] = 0.f;
   __syncwarp();
+  const int nq = (k + 32) / 32;           // slots that can hold l < i <= k
+  float u[kSolveMaxPerLane], un[kSolveMaxPerLane];
+  auto load_row = [&](int i, float* dst) {
+    const float* src = staged ? us + (long long)i * n : UT + (long long)i * ldu;
+#pragma unroll
+    for (int qq = 0; qq < kSolveMaxPerLane; ++qq) {
+      const int l = lane + 32 * qq;
+      dst[qq] = (qq < nq && l < i) ? src[l] : 0.f;
+    }
+  };
+  load_row(k, un);
   for (int i = k; i >= 0; --i) {
+#pragma unroll
+    for (int qq = 0; qq < kSolveMaxPerLane; ++qq) u[qq] = un[qq];
+    if (i > 0) load_row(i - 1, un);       // next row while this one is applied
     const int owner = i & 31, slot = i >> 5;
     float bi = 0.f;
 #pragma unroll
     for (int qq = 0; qq < kSolveMaxPerLane; ++qq)
       if (qq == slot) bi = b[qq];
-    const float tau_i = static_cast<float>(Tf[(size_t)(i / NB) * NB * NB + (i % NB) * NB + (i % NB)]);
-    const float xi = __shfl_sync(0xffffffffu, bi, owner) * tau_i;
+    const float xi = __shfl_sync(0xffffffffu, bi, owner) * taus[i];
     if (lane == 0) out[i] = xi;
-    const float* ui = UT + (long long)i * ldu;   // U[l][i] for l < i
 #pragma unroll
-    for (int qq = 0; qq < kSolveMaxPerLane; ++qq) {
-      const int l = lane + 32 * qq;
-      if (l < i) b[qq] = fmaf(-ui[l], xi, b[qq]);
-    }
+    for (int qq = 0; qq < kSolveMaxPerLane; ++qq) b[qq] = fmaf(-u[qq], xi, b[qq]);
   }
 }
 
@@ -310,7 +331,15 @@ cudaError_t householder_qr_split(int m, int n, const double* M, double* R, const
     const long long tot = (long long)n * n;
     build_ut_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, ksplit, n, w.Tf, UT, ldv);
     note_launch();
-    q_solve_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(UT, ldv, Vt32, ldv, w.Tf, n, Wt);
+    const size_t qsm = sizeof(float) * (((n + 3) & ~3) + (n <= kSolveSmemMaxN ? (size_t)n * n : 0));
+    static bool qattr = false;
+    if (!qattr) {
+      cudaFuncSetAttribute(q_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(float) * (kSolveSmemMaxN * kSolveSmemMaxN +
+                                                  32 * kSolveMaxPerLane)));
+      qattr = true;
+    }
+    q_solve_kernel<<<(unsigned)((n + 7) / 8), 256, qsm, s>>>(UT, ldv, Vt32, ldv, w.Tf, n, Wt);
     note_launch();
     const long long totq = (long long)m * n;
     init_q32_kernel<<<(unsigned)std::min<long long>((totq + 255) / 256, 8192), 256, 0, s>>>(
