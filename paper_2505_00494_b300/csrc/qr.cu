@@ -182,17 +182,23 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
       if (wrp == 0) cpart[buf][lane] = v;
       if (threadIdx.x == 0) c_abort[buf] = aborted ? 1 : 0;
       cluster_sync_all();
-      int any = 0;
-      for (int q = 0; q < CL; ++q) any |= ld_dsmem_s32(&c_abort[buf], (unsigned)q);
-      if (any) return false;
+      // the leader publishes at once (after an abort the numbers are not
+      // used: every CTA stops below, with the error word already set)
       if (crank == 0 && wrp == 0) {
-        double acc = 0.0;
-        for (int q = 0; q < CL; ++q) acc += ld_dsmem_f64(&cpart[buf][lane], (unsigned)q);
+        double p[CL];
+#pragma unroll
+        for (int q = 0; q < CL; ++q) p[q] = ld_dsmem_f64(&cpart[buf][lane], (unsigned)q);
+        double acc = p[0];
+#pragma unroll
+        for (int q = 1; q < CL; ++q) acc += p[q];
         psum[((size_t)buf * NG + grp) * NB + lane] = acc;
         __syncwarp();
         if (lane == 0) grid_arrive(bar);
       }
-      return true;
+      int any = 0;
+#pragma unroll
+      for (int q = 0; q < CL; ++q) any |= ld_dsmem_s32(&c_abort[buf], (unsigned)q);
+      return any == 0;
     }
   };
   if (TILE) {
@@ -234,6 +240,8 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     }
     double acc = 0.0;
     if (ok) {
+      // pivot row (x_0 and the y_{t,0}) loaded together with the partial sums
+      const double y0 = (wrp == 0 && lane <= nrem) ? __ldcg(rowb + buf * NB + lane) : 0.0;
       // cross-unit reduction (L2 reads): lane = slot, the 8 warps take every 8th unit
       {
         double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
@@ -253,7 +261,6 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
       __syncthreads();
       if (wrp == 0) {
         const double st = sum8(lane);                      // sigma (lane 0), s_t (lane t)
-        const double y0 = (lane <= nrem) ? __ldcg(rowb + buf * NB + lane) : 0.0;
         double tau = 0.0, inv_w = 0.0, mu = 0.0;
         if (lane == 0) {
           const double x0 = y0, sigma = st;

@@ -121,8 +121,9 @@ __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
 // Called by one thread after the CTA's published writes (ordered before it by
 // a block or warp barrier).
 __device__ __forceinline__ void grid_arrive(GridBar* bar) {
-  __threadfence();
-  atomicAdd(&bar->count, 1u);
+  // release: the CTA's published writes (ordered before this by a block or
+  // warp barrier) become visible before the count does
+  asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
 }
 
 // Called by one thread; true once count >= target.
