@@ -269,6 +269,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="split", choices=["fp64", "split"])
+    ap.add_argument("--method", default="qr", choices=["qr", "eigen"],
+                    help="qr: QR-CTMRG; eigen: the standard step with a full "
+                         "eigendecomposition (comparison method, FP64)")
     ap.add_argument("--workload", default="d2_D6_chi144", choices=sorted(qi.WORKLOADS))
     ap.add_argument("--check-every", type=int, default=5)
     ap.add_argument("--cpu-sample", type=int, default=3, help="oracle steps in cpu_baseline")
@@ -283,8 +286,11 @@ def main():
                          "stops earlier at its precision floor)")
     args = ap.parse_args()
     w = qi.WORKLOADS[args.workload]
+    if args.method == "eigen":
+        args.precision = "fp64"
+        args.no_extras = True
     if args.steps <= 0:
-        args.steps = 20 if args.precision == "fp64" else 200
+        args.steps = 5 if args.method == "eigen" else (20 if args.precision == "fp64" else 200)
     args.warmup = max(3, args.warmup)
 
     rank = int(os.environ.get("RANK", "0"))
@@ -313,7 +319,7 @@ def main():
                      device="cuda")
     A = q.c4v_symmetrize(X, normalize=True)
     ctx = q.QRCTM(d, D, chi, precision=args.precision, check_every=args.check_every,
-                  with_nnn=chi * D * D <= 8192)
+                  with_nnn=chi * D * D <= 8192, method=args.method)
     ctx.init_env(A)
     ce = args.check_every
 
@@ -532,15 +538,17 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": METRIC if args.workload == "d2_D6_chi144" else
-            f"QR-CTMRG iterations/s ({args.workload})",
+            "metric": (METRIC if args.workload == "d2_D6_chi144" else
+                       f"QR-CTMRG iterations/s ({args.workload})") if args.method == "qr" else
+            f"standard C4v CTMRG (eigendecomposition) iterations/s ({args.workload})",
             "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "tf32x3+f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "d": d, "D": D, "chi": chi,
-                       "precision": args.precision, "layers": "split" if 2 * d < D * D else "double",
+                       "precision": args.precision, "method": args.method,
+                       "layers": "split" if 2 * d < D * D else "double",
                        "check_every": ce, "parallelism": f"replicas{world}",
                        "l2": "per-step intermediates larger than L2 (X1 alone "
                              f"{(chi * D * D) ** 2 * 8 / 1e6:.0f} MB)"},

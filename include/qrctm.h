@@ -45,6 +45,7 @@ typedef enum {
 typedef enum { QRCTM_FP64 = 0, QRCTM_SPLIT = 1 } qrctm_precision;
 typedef enum { QRCTM_LAYERS_AUTO = 0, QRCTM_LAYERS_DOUBLE = 1, QRCTM_LAYERS_SPLIT = 2 } qrctm_layers;
 typedef enum { QRCTM_GRAD_IMPLICIT = 0, QRCTM_GRAD_UNROLL = 1 } qrctm_grad_mode;
+typedef enum { QRCTM_METHOD_QR = 0, QRCTM_METHOD_EIGEN = 1 } qrctm_method;
 
 typedef struct {
   int d;              /* physical dimension (>= 1)                               */
@@ -66,6 +67,11 @@ typedef struct {
   int with_nnn;       /* 1: reserve workspace for the J2 (2x2 patch) energy term */
   int with_grad;      /* 1: reserve workspace for qrctm_energy_grad              */
   void* stream;       /* cudaStream_t; NULL = legacy default stream             */
+  int method;         /* qrctm_method: QR (QR-CTMRG, QR-CTMRG paragraph) or EIGEN
+                         (standard C4v CTMRG with a full eigendecomposition of the
+                         enlarged corner, Standard CTMRG paragraph; FP64 only, the
+                         comparison method; cuSOLVER's handle keeps a small device
+                         state of its own)                                      */
 } qrctm_config;
 
 typedef struct {

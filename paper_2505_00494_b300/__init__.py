@@ -30,6 +30,7 @@ STATUS = {
 PRECISION = {"fp64": 0, "split": 1}
 LAYERS = {"auto": 0, "double": 1, "split": 2}
 GRAD_MODE = {"implicit": 0, "unroll": 1}
+METHOD = {"qr": 0, "eigen": 1}
 PHASES = ["ct", "qr", "x1", "absorb", "project", "corner", "symnorm", "spectrum", "energy",
           "grad", "warmup", "qr_panel"]
 
@@ -49,7 +50,7 @@ class Config(ctypes.Structure):
         ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
         ("grad_max_iter", ctypes.c_int), ("grad_tol", ctypes.c_double),
         ("with_nnn", ctypes.c_int), ("with_grad", ctypes.c_int),
-        ("stream", ctypes.c_void_p),
+        ("stream", ctypes.c_void_p), ("method", ctypes.c_int),
     ]
 
 
@@ -148,12 +149,13 @@ class QRCTM:
 
     def __init__(self, d, D, chi, precision="fp64", layers="auto", warmup_steps=0,
                  check_every=1, tol=1e-10, max_iter=500, grad_max_iter=0, grad_tol=0.0,
-                 with_nnn=False, with_grad=False, stream=None, device="cuda"):
+                 with_nnn=False, with_grad=False, stream=None, device="cuda", method="qr"):
         torch = _torch()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.cfg = Config(d, D, chi, PRECISION[precision], LAYERS[layers], warmup_steps,
                           check_every, tol, max_iter, grad_max_iter, grad_tol, int(with_nnn),
-                          int(with_grad), ctypes.c_void_p(self.stream.cuda_stream))
+                          int(with_grad), ctypes.c_void_p(self.stream.cuda_stream),
+                          METHOD[method])
         nbytes = _load().qrctm_workspace_bytes(ctypes.byref(self.cfg))
         if nbytes == 0:
             raise QRCTMError(1, "qrctm_workspace_bytes", "invalid configuration")

@@ -61,7 +61,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if (not force and os.path.exists(LIB)
             and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs)):
         return LIB
-    cmd = [nvcc(), "-shared", "-o", LIB] + objs + ARCH + ["-lcudart", "-lcuda"]
+    cmd = [nvcc(), "-shared", "-o", LIB] + objs + ARCH + ["-lcudart", "-lcuda", "-lcusolver"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -29,6 +29,8 @@ bool cfg_valid(const qrctm_config& c) {
   if (D2 > 4096 || (long long)c.chi * D2 > (1ll << 20)) return false;
   if (c.chi < D2) return false;
   if (c.precision == QRCTM_SPLIT && c.D < 2) return false;
+  if (c.method != QRCTM_METHOD_QR && c.method != QRCTM_METHOD_EIGEN) return false;
+  if (c.method == QRCTM_METHOD_EIGEN && c.precision != QRCTM_FP64) return false;
   return true;
 }
 
@@ -180,9 +182,27 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
   } else if (carve) {
     c->mm32 = nullptr; c->mm32_floats = 0;
   }
+  // standard method: dense enlarged corner, eigenvalues, solver workspace
+  if (cfg.method == QRCTM_METHOD_EIGEN) {
+    const size_t ew = eigen_work_doubles((long long)m);
+    size_t o = off;
+    off += al(sizeof(double) * m * m);
+    if (carve) c->eig_E = reinterpret_cast<double*>(c->ws + o);
+    o = off; off += al(sizeof(double) * m);
+    if (carve) c->eig_w = reinterpret_cast<double*>(c->ws + o);
+    o = off; off += al(sizeof(double) * ew);
+    if (carve) { c->eig_work = reinterpret_cast<double*>(c->ws + o); c->eig_work_doubles = ew; }
+    o = off; off += al(sizeof(int) * (chi + 64));
+    if (carve) { c->eig_info = reinterpret_cast<int*>(c->ws + o); c->eig_idx = c->eig_info + 64; }
+  } else if (carve) {
+    c->eig_E = c->eig_w = c->eig_work = nullptr;
+    c->eig_work_doubles = 0;
+    c->eig_info = c->eig_idx = nullptr;
+  }
   if (carve) {
     c->split_layers = split;
     c->mm_split = false;   // set for the duration of a split-precision gradient
+    c->solver = nullptr;
   }
   return off;
 }
@@ -275,6 +295,7 @@ void qrctm_destroy(qrctm_ctx* ctx) {
   if (!ctx->recs.empty() || !ctx->ev_pool.empty()) cudaStreamSynchronize(ctx->st);
   for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  eigen_release(ctx);
   delete ctx;
 }
 
@@ -381,8 +402,12 @@ qrctm_status qrctm_init_env(qrctm_ctx* c, const double* A, const double* C0, con
     for (int w = 0; w < nw; ++w) {
       int ci = c->chi_cur;
       int co = (int)std::min<long long>(c->chi, (long long)ci * D2);
-      if ((e = warmup_step(c, ci, co)) != cudaSuccess) return cuda_fail(c, e, "warm-up");
+      // the standard method warms up with its own (exact) steps
+      if ((e = (c->cfg.method == QRCTM_METHOD_EIGEN) ? eigen_step(c, ci, co)
+                                                     : warmup_step(c, ci, co)) != cudaSuccess)
+        return cuda_fail(c, e, "warm-up");
     }
+    c->iters = 0;
   }
   qrctm_status s = sync_check(c, "init env");
   if (s != QRCTM_OK) return s;
@@ -398,9 +423,13 @@ qrctm_status qrctm_step(qrctm_ctx* c, int n, double* delta_out) {
   if (!c || n < 0) return QRCTM_ERR_INVALID_ARG;
   if (!c->have_env) return set_err(c, QRCTM_ERR_STATE, "qrctm_init_env not called");
   cudaError_t e;
-  for (int i = 0; i < n; ++i)
-    if ((e = c->split_prec ? qr_step_split(c) : qr_step(c)) != cudaSuccess)
-      return cuda_fail(c, e, "qr step");
+  for (int i = 0; i < n; ++i) {
+    if (c->cfg.method == QRCTM_METHOD_EIGEN)
+      e = eigen_step(c, c->chi_cur, (int)std::min<long long>(c->chi, (long long)c->chi_cur * c->D2));
+    else
+      e = c->split_prec ? qr_step_split(c) : qr_step(c);
+    if (e != cudaSuccess) return cuda_fail(c, e, "step");
+  }
   if (delta_out) {
     if ((e = spectrum_check(c)) != cudaSuccess) return cuda_fail(c, e, "spectrum");
     qrctm_status s = sync_check(c, "step");

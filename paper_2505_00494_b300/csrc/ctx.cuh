@@ -44,6 +44,14 @@ struct qrctm_ctx {
   int grad_iters;
   double grad_resid;
   cudaEvent_t panel_ev;   // open panel-phase event (profiling)
+  // standard (eigendecomposition) method
+  void* solver;            // cusolverDnHandle_t, created on first use
+  double* eig_E;           // dense symmetric enlarged corner, then its eigenvectors
+  double* eig_w;           // eigenvalues
+  double* eig_work;        // solver workspace
+  size_t eig_work_doubles;
+  int* eig_info;
+  int* eig_idx;            // kept eigenvalue indices, by rank
   // split-precision contractions of the energy and adjoint passes
   bool mm_split;
   float* mm32;
@@ -100,6 +108,10 @@ cudaError_t spectrum_check(qrctm_ctx* c);
 // Split-precision step (split_step.cu)
 cudaError_t split_prepare_A(qrctm_ctx* c);
 cudaError_t qr_step_split(qrctm_ctx* c);
+// Standard step with a full eigendecomposition (eigen_step.cu)
+cudaError_t eigen_step(qrctm_ctx* c, int ci, int co);
+size_t eigen_work_doubles(long long m);
+void eigen_release(qrctm_ctx* c);
 // fused ket + bra absorption (FP32), see absorb.cu
 bool absorb_fused_ok(int d, int D);
 cudaError_t absorb_fused(const float* X1, const float* Ak, const float* Ab, float* X2, int ch,
