@@ -246,8 +246,8 @@ def qr_step_parts(C, T, A, layers="double"):
     ct = reduced_corner(C, T)
     Q, R = householder_qr(ct)
     Q3 = Q.reshape(chi, D2, chi)
-    if layers == "double":
-        a = double_layer(A)
+    if layers in ("double", "network"):
+        a = A if layers == "network" else double_layer(A)
         T_raw = renormalize_edge(Q, T, a)
     else:
         X1 = np.tensordot(Q3, T, axes=([0], [0]))  # [u,m,k,b]
@@ -285,19 +285,24 @@ def spectrum_delta(s_new, s_old):
     return float(np.sqrt(np.sum((a - b) ** 2)))
 
 
-def warmup(A, chi, n_warmup=None, env=None):
+def warmup(A, chi, n_warmup=None, env=None, layers="double"):
     """Warm-up with standard steps, growing chi towards the target (QR-CTMRG
     paragraph: 1-4 standard steps suffice and let chi grow).  Reading: at
-    least two steps, more if chi0 * D^(2n) < chi."""
-    D = A.shape[1]
-    a = double_layer(A)
-    C, T = init_env(A) if env is None else env
+    least two steps, more if chi0 * D^(2n) < chi.  With ``layers='network'``
+    A is the network tensor a itself (bond D2 = A.shape[0])."""
+    if layers == "network":
+        a = A
+        C, T = init_env_network(a) if env is None else env
+    else:
+        a = double_layer(A)
+        C, T = init_env(A) if env is None else env
+    D2 = a.shape[0]
     if n_warmup is None:
         n_warmup, c = 0, C.shape[0]
         while c < chi:
-            c *= D * D
+            c *= D2
             n_warmup += 1
-            if D == 1:
+            if D2 == 1:
                 break
         n_warmup = max(2, n_warmup)
     for _ in range(n_warmup):
@@ -311,14 +316,16 @@ def ctmrg(A, chi, method="qr", tol=1e-12, max_iter=200, n_warmup=None,
 
     ``method='qr'``: warm-up standard steps, then QR-CTMRG steps.
     ``method='eigen'``: standard steps throughout.  ``init`` (C, T) skips the
-    warm-up.  Returns (C, T, info) with info['iters'], info['delta'],
-    info['converged'] and the spectrum history.
+    warm-up.  ``layers='network'``: A is a classical network tensor a[u,l,d,r]
+    used as it is (Discussion: classical partition functions).  Returns
+    (C, T, info) with info['iters'], info['delta'], info['converged'] and the
+    spectrum history.
     """
-    a = double_layer(A)
+    a = A if layers == "network" else double_layer(A)
     if init is not None:
         C, T = init
     else:
-        C, T = warmup(A, chi, n_warmup, env)
+        C, T = warmup(A, chi, n_warmup, env, layers)
     s_old = corner_spectrum(C)
     hist = []
     delta = np.inf
@@ -517,7 +524,12 @@ def ising_A(beta):
 
 def ising_kappa(C, T, a, a_obs=None):
     """Partition function per site kappa = Z11 Z00 / Z10^2 (normalisations of
-    C and T cancel).  With ``a_obs`` returns <O> = Z11(a_obs) / Z11(a)."""
+    C and T cancel).  With ``a_obs`` returns <O> = Z11(a_obs) / Z11(a).
+    Nothing here is specific to the Ising model: any C4v network tensor a
+    (bond = C4v edge leg of T) works; ``network_kappa`` is the same function.
+
+    Z00 = Tr C^4 (four corners), Z10 = a 2x1 ring C T C C T C, Z11 = the
+    3x3 patch (four C, four T, one a)."""
     Z00 = np.trace(C @ C @ C @ C)
     Z10 = np.einsum("yx,xkX,XY,YZ,ZkW,Wy->", C, T, C, C, T, C)
 
@@ -528,6 +540,56 @@ def ising_kappa(C, T, a, a_obs=None):
     if a_obs is not None:
         return z11(a_obs) / Z11
     return Z11 * Z00 / Z10 ** 2
+
+
+network_kappa = ising_kappa
+
+
+def spin_network(B, obs=None):
+    """Classical network tensor of spins with Boltzmann weight B[s,s'] on
+    every bond (B symmetric positive definite):
+        a[u,l,d,r] = sum_s o[s] W[s,u] W[s,l] W[s,d] W[s,r],  W = B^(1/2),
+    o = 1 (the network) or ``obs`` (the same network with o[s] inserted at
+    one site).  Neighbouring tensors share one bond index r, and
+    sum_r W[s1,r] W[s2,r] = B[s1,s2], so the contracted network is the
+    partition function; a is C4v symmetric and its bond is q = len(B).
+    B may be semidefinite (beta = 0): eigenvalues below 0 by rounding are
+    taken as 0."""
+    w, V = np.linalg.eigh(B)
+    W = (V * np.sqrt(np.maximum(w, 0.0))) @ V.T
+    o = np.ones(B.shape[0]) if obs is None else np.asarray(obs, dtype=float)
+    return np.einsum("s,su,sl,sd,sr->uldr", o, W, W, W, W), W
+
+
+def ising_network(beta):
+    """Ising network with bond 2: B = exp(beta s s'), s = +1, -1 (index 0 is
+    +1).  Returns (a, a_sigma, W)."""
+    spins = np.array([1.0, -1.0])
+    B = np.exp(beta * np.outer(spins, spins))
+    a, W = spin_network(B)
+    a_s, _ = spin_network(B, spins)
+    return a, a_s, W
+
+
+def potts_network(q, beta):
+    """q-state Potts network with bond q: B = exp(beta delta_{s s'}).
+    Returns (a, W)."""
+    B = np.exp(beta * np.eye(q))
+    return spin_network(B)
+
+
+def init_env_network(a, v=None):
+    """Boundary tensors of a network fed directly: the legs that point out of
+    the system are contracted with the vector v (all ones when None, i.e. a
+    free boundary):
+        C0[d,r]   = sum_{u,l} v[u] v[l] a[u,l,d,r],
+        T0[u,r,d] = sum_l v[l] a[u,l,d,r]
+    (the same leg assignment as ``init_env``), then sym_norm."""
+    b = a.shape[0]
+    v = np.ones(b) if v is None else np.asarray(v, dtype=float)
+    C0 = np.einsum("u,l,uldr->dr", v, v, a)
+    T0 = np.einsum("l,uldr->urd", v, a)
+    return sym_norm(C0, T0)
 
 
 def ising_observable_layer(A):

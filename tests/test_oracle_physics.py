@@ -84,6 +84,58 @@ def test_ising_against_onsager_and_yang(method, beta):
     assert abs(s @ p @ s - onsager_nn_correlation(beta)) < 1e-9
 
 
+def network_ln_kappa(a, chi, method="qr", v=None, a_obs=None):
+    env = o.init_env_network(a, v)
+    C, T, info = o.ctmrg(a, chi, method, tol=1e-12, max_iter=400, env=env, layers="network")
+    assert info["converged"]
+    lk = float(np.log(o.network_kappa(C, T, a)))
+    return (lk, float(o.network_kappa(C, T, a, a_obs))) if a_obs is not None else lk
+
+
+@pytest.mark.parametrize("method", ["qr", "eigen"])
+@pytest.mark.parametrize("beta", [0.3, 0.6])
+def test_ising_network_against_onsager_and_yang(method, beta):
+    # Discussion: classical partition functions; the network tensor (bond 2)
+    # is fed directly instead of a double layer.  Ordered phase: boundary
+    # spins fixed to +1 through the vector W[0].
+    a, a_s, W = o.ising_network(beta)
+    v = W[0] if beta > GOLD["ising_beta_c"]["value"] else None
+    lk, M = network_ln_kappa(a, 16, method, v, a_s)
+    assert abs(lk - o.onsager_free_energy(beta)) < 1e-11
+    assert abs(M - o.yang_magnetization(beta)) < 1e-9
+
+
+@pytest.mark.parametrize("beta", [0.4, 1.2])
+def test_potts2_network_reduces_to_ising(beta):
+    # delta(s,s') = (1 + s s')/2: every bond carries e^(beta/2) times the
+    # Ising weight at coupling beta/2, two bonds per site
+    a, W = o.potts_network(2, beta)
+    v = W[0] if beta / 2 > GOLD["ising_beta_c"]["value"] else None
+    lk = network_ln_kappa(a, 16, "qr", v)
+    assert abs(lk - (beta + o.onsager_free_energy(beta / 2))) < 1e-11
+
+
+def test_potts3_network_duality():
+    # Square-lattice Potts self-duality (Fortuin-Kasteleyn form
+    # Z(q, v) = q^(1-N*) v^E Z*(q, q/v), v = e^K - 1, E = 2N bonds, N* ~ N):
+    # ln kappa(K) - ln kappa(K*) = 2 ln(e^K - 1) - ln q.  K = 0.6 is
+    # disordered, its dual K* = 1.54 ordered (boundary fixed to state 0).
+    q, K = 3, 0.6
+    vK = np.exp(K) - 1
+    Kd = np.log1p(q / vK)
+    a1, _ = o.potts_network(q, K)
+    a2, W2 = o.potts_network(q, Kd)
+    lk1 = network_ln_kappa(a1, 27, "qr")
+    lk2 = network_ln_kappa(a2, 27, "qr", W2[0])
+    assert abs((lk1 - lk2) - (2 * np.log(vK) - np.log(q))) < 1e-9
+
+
+def test_network_infinite_temperature():
+    # beta = 0: every configuration weighs 1, kappa = q exactly
+    a, _ = o.potts_network(3, 0.0)
+    assert abs(network_ln_kappa(a, 9, "qr") - np.log(3.0)) < 1e-13
+
+
 def test_rdm_nnn_by_brute_force_patch():
     # the 2x2 patch written out tensor by tensor (4 C, 8 T, 4 sites), no
     # quadrant symmetry used
