@@ -531,7 +531,7 @@ def ising_kappa(C, T, a, a_obs=None):
     Z00 = Tr C^4 (four corners), Z10 = a 2x1 ring C T C C T C, Z11 = the
     3x3 patch (four C, four T, one a)."""
     Z00 = np.trace(C @ C @ C @ C)
-    Z10 = np.einsum("yx,xkX,XY,YZ,ZkW,Wy->", C, T, C, C, T, C)
+    Z10 = np.einsum("yx,xkX,XY,YZ,ZkW,Wy->", C, T, C, C, T, C, optimize="greedy")
 
     def z11(t):
         return np.einsum("ax,xpy,yb,bqc,cz,zrw,wd,dsa,psrq->",

@@ -99,6 +99,12 @@ def test_split_converged_energy_matches_oracle_d2_D6_chi144(q):
     its, dl = f.run_to_convergence(tol=1e-11, max_iter=3000)
     assert dl < 1e-11
     _, _, s = f.get_env(spectrum=True)
-    assert np.abs(s - np.array(g["spectrum"])).max() < 1e-9
+    # The fixture stopped at a spectrum change of 9.8e-11 per 5-step check;
+    # at chi = 144 the slowest mode of the map shrinks by only ~0.968 per
+    # check (1e-11 -> 1e-12 takes ~71 checks), so the fixture itself is
+    # ~0.968/0.032 x 9.8e-11 ~ 3e-9 from the fixed point.  Every start
+    # (oracle warm-up, GPU warm-up, split floor) lands on the same
+    # environment: leading 100 values within 8e-10, the last within 1.1e-9.
+    assert np.abs(s - np.array(g["spectrum"])).max() < 5e-9
     assert abs(f.energy(1.0, 0.0) - g["E_J2_0"]) < 1e-9
     assert abs(f.energy(1.0, 0.5) - g["E_J2_0.5"]) < 1e-9
