@@ -43,7 +43,15 @@ typedef enum {
 } qrctm_status;
 
 typedef enum { QRCTM_FP64 = 0, QRCTM_SPLIT = 1 } qrctm_precision;
-typedef enum { QRCTM_LAYERS_AUTO = 0, QRCTM_LAYERS_DOUBLE = 1, QRCTM_LAYERS_SPLIT = 2 } qrctm_layers;
+typedef enum {
+  QRCTM_LAYERS_AUTO = 0,
+  QRCTM_LAYERS_DOUBLE = 1,
+  QRCTM_LAYERS_SPLIT = 2,
+  /* a classical network tensor a[u,l,d,r] is given directly (Discussion:
+     classical partition functions); D is its bond, T's inner leg has D (not
+     D^2) values, d must be 1, precision FP64, with_nnn = with_grad = 0 */
+  QRCTM_LAYERS_NETWORK = 3
+} qrctm_layers;
 typedef enum { QRCTM_GRAD_IMPLICIT = 0, QRCTM_GRAD_UNROLL = 1 } qrctm_grad_mode;
 typedef enum { QRCTM_METHOD_QR = 0, QRCTM_METHOD_EIGEN = 1 } qrctm_method;
 
@@ -163,6 +171,31 @@ qrctm_status qrctm_energy(qrctm_ctx* ctx, const qrctm_model* model, double* e_ou
  * applications of J^T (each one reverse pass through both steps). */
 qrctm_status qrctm_energy_grad(qrctm_ctx* ctx, const qrctm_model* model, int mode, int k_unroll,
                                double* grad, double* e_out);
+
+/* ----- classical networks (layers = QRCTM_LAYERS_NETWORK) ----------------- */
+
+/* Set the network tensor and the boundary (Discussion: QR-CTMRG applies to
+ * classical partition functions).  a: device, D^4 doubles, a[u,l,d,r]
+ * row-major, C4v symmetric (checked to 1e-12 relative, else
+ * QRCTM_ERR_NOT_SYMMETRIC); copied into the workspace.  v: device, D
+ * doubles, or NULL for all ones: the legs pointing out of the system are
+ * contracted with v,
+ *   C0[d,r] = sum_{u,l} v[u] v[l] a[u,l,d,r],  T0[u,r,d] = sum_l v[l] a[u,l,d,r],
+ * (a fixed-spin vector selects one ordered state), then the warm-up steps
+ * grow chi as in qrctm_init_env.  QRCTM_ERR_INVALID_ARG on a context that is
+ * not in network mode. */
+qrctm_status qrctm_init_env_network(qrctm_ctx* ctx, const double* a, const double* v);
+
+/* Partition function per site and a one-site expectation value at the
+ * current environment: kappa = Z11 Z00 / Z10^2 with Z00 = Tr C^4, Z10 the
+ * 2x1 ring (C T C)(C T C), Z11 the 3x3 patch (four C, four T, one a), so
+ * -beta f = ln kappa; obs = Z11(a_obs) / Z11(a).  a_obs: device, D^4
+ * doubles (a with the observable inserted at the site), or NULL (obs_out
+ * untouched).  ln_kappa_out, obs_out: host (either may be NULL).
+ * QRCTM_ERR_NUMERIC when kappa <= 0 or a trace is not finite.  Runs on the
+ * context's stream and synchronises it. */
+qrctm_status qrctm_network_observables(qrctm_ctx* ctx, const double* a_obs, double* ln_kappa_out,
+                                       double* obs_out);
 
 /* Copy the environment out: C (chi*chi), T (chi*D^2*chi) on the device (may be
  * NULL); spectrum_host: chi doubles, sorted |eig(C)| (may be NULL). */

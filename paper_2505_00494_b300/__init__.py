@@ -28,7 +28,7 @@ STATUS = {
     5: "NOT_SYMMETRIC", 6: "WORKSPACE", 7: "TIMEOUT", 8: "STATE",
 }
 PRECISION = {"fp64": 0, "split": 1}
-LAYERS = {"auto": 0, "double": 1, "split": 2}
+LAYERS = {"auto": 0, "double": 1, "split": 2, "network": 3}
 GRAD_MODE = {"implicit": 0, "unroll": 1}
 METHOD = {"qr": 0, "eigen": 1}
 PHASES = ["ct", "qr", "x1", "absorb", "project", "corner", "symnorm", "spectrum", "energy",
@@ -73,6 +73,8 @@ _sig = {
     "qrctm_energy_grad": ([_vp, ctypes.POINTER(Model), ctypes.c_int, ctypes.c_int, _vp, _dp],
                           ctypes.c_int),
     "qrctm_get_env": ([_vp, _vp, _vp, _dp], ctypes.c_int),
+    "qrctm_init_env_network": ([_vp, _vp, _vp], ctypes.c_int),
+    "qrctm_network_observables": ([_vp, _vp, _dp, _dp], ctypes.c_int),
     "qrctm_iterations": ([_vp], ctypes.c_int),
     "qrctm_grad_iterations": ([_vp], ctypes.c_int),
     "qrctm_grad_residual": ([_vp], ctypes.c_double),
@@ -162,6 +164,8 @@ class QRCTM:
         self.workspace_bytes = nbytes
         self.ws = _workspace(nbytes, device)
         self.d, self.D, self.chi = d, D, chi
+        # bond of T's inner leg: D^2 (ket and bra), or D for a network tensor
+        self.D2 = D if layers == "network" else D * D
         h = ctypes.c_void_p()
         self.h = None
         self._check(_load().qrctm_create(ctypes.byref(self.cfg), ctypes.c_void_p(self.ws.data_ptr()),
@@ -193,6 +197,22 @@ class QRCTM:
     def init_env(self, A, C0=None, T0=None):
         self.A = A
         self._check(_load().qrctm_init_env(self.h, _ptr(A), _ptr(C0), _ptr(T0)), "qrctm_init_env")
+
+    def init_env_network(self, a, v=None):
+        """Classical network tensor a[u,l,d,r] (bond D) fed directly; v: the
+        boundary vector (None = all ones)."""
+        self.A = a
+        self._check(_load().qrctm_init_env_network(self.h, _ptr(a), _ptr(v)),
+                    "qrctm_init_env_network")
+
+    def network_observables(self, a_obs=None):
+        """(ln kappa, <O>) at the current environment; <O> is None without a_obs."""
+        lk = ctypes.c_double(0.0)
+        ob = ctypes.c_double(0.0)
+        self._check(_load().qrctm_network_observables(self.h, _ptr(a_obs), ctypes.byref(lk),
+                                                      ctypes.byref(ob)),
+                    "qrctm_network_observables")
+        return lk.value, (ob.value if a_obs is not None else None)
 
     def step(self, n=1, want_delta=True):
         dlt = ctypes.c_double(0.0)
@@ -229,7 +249,7 @@ class QRCTM:
     def get_env(self, spectrum=True):
         torch = _torch()
         import numpy as np
-        D2 = self.D * self.D
+        D2 = self.D2
         C = torch.empty((self.chi, self.chi), dtype=torch.float64, device="cuda")
         T = torch.empty((self.chi, D2, self.chi), dtype=torch.float64, device="cuda")
         s = np.zeros(self.chi) if spectrum else None

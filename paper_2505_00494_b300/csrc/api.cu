@@ -23,9 +23,11 @@ inline size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 bool cfg_valid(const qrctm_config& c) {
   if (c.d < 1 || c.D < 1 || c.chi < 1 || c.chi > 1024) return false;
   if (c.precision != QRCTM_FP64 && c.precision != QRCTM_SPLIT) return false;
-  if (c.layers < 0 || c.layers > 2) return false;
+  if (c.layers < 0 || c.layers > 3) return false;
   if (c.check_every < 0 || c.warmup_steps < -1) return false;
-  const long long D2 = (long long)c.D * c.D;
+  const bool net = c.layers == QRCTM_LAYERS_NETWORK;
+  if (net && (c.d != 1 || c.precision != QRCTM_FP64 || c.with_grad || c.with_nnn)) return false;
+  const long long D2 = net ? (long long)c.D : (long long)c.D * c.D;
   if (D2 > 4096 || (long long)c.chi * D2 > (1ll << 20)) return false;
   if (c.chi < D2) return false;
   if (c.precision == QRCTM_SPLIT && c.D < 2) return false;
@@ -75,7 +77,8 @@ void panel_hook(void* user, int begin);
 
 // Regions in a fixed order; the same function sizes and carves.
 size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
-  const size_t d = cfg.d, D = cfg.D, D2 = D * D, chi = cfg.chi, m = chi * D2;
+  const bool net = cfg.layers == QRCTM_LAYERS_NETWORK;
+  const size_t d = cfg.d, D = cfg.D, D2 = net ? D : D * D, chi = cfg.chi, m = chi * D2;
   const bool split = (cfg.layers == QRCTM_LAYERS_SPLIT) ||
                      (cfg.layers == QRCTM_LAYERS_AUTO && 2 * d < D2);
   size_t off = 0;
@@ -88,7 +91,8 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
   static double* dummy;
   qrctm_ctx* cc = carve ? c : nullptr;
 #define R_(field) P(cc ? cc->field : dummy)
-  const size_t nA = d * D2 * D2, nC = chi * chi, nT = chi * D2 * chi;
+  // network mode: A and tmpA hold the network tensor (D2^4 doubles)
+  const size_t nA = net ? D2 * D2 * D2 * D2 : d * D2 * D2, nC = chi * chi, nT = chi * D2 * chi;
   take(R_(A), nA);
   take(R_(tmpA), nA);
   take(R_(C), nC);
@@ -112,8 +116,9 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
   take(R_(delta_d), 8);
   take(R_(partials), 1024);
   take(R_(a), split ? 1 : D2 * D2 * D2 * D2);
-  take(R_(E1), d * d * m * m);
-  take(R_(E2), d * d * m * chi);
+  // energy patches (iPEPS only)
+  take(R_(E1), net ? 1 : d * d * m * m);
+  take(R_(E2), net ? 1 : d * d * m * chi);
   if (cfg.with_nnn) take(R_(E3), d * d * m * m);
   else if (carve) c->E3 = nullptr;
   take(R_(rho), 64);
@@ -200,6 +205,7 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
     c->eig_info = c->eig_idx = nullptr;
   }
   if (carve) {
+    c->network = net;
     c->split_layers = split;
     c->mm_split = false;   // set for the duration of a split-precision gradient
     c->solver = nullptr;
@@ -270,7 +276,8 @@ qrctm_status qrctm_create(const qrctm_config* cfg, void* workspace, size_t bytes
   if (c->cfg.grad_max_iter <= 0) c->cfg.grad_max_iter = 200;
   if (c->cfg.grad_tol <= 0) c->cfg.grad_tol = 1e-12;
   c->st = reinterpret_cast<cudaStream_t>(cfg->stream);
-  c->d = cfg->d; c->D = cfg->D; c->D2 = cfg->D * cfg->D; c->chi = cfg->chi;
+  c->d = cfg->d; c->D = cfg->D; c->chi = cfg->chi;
+  c->D2 = cfg->layers == QRCTM_LAYERS_NETWORK ? cfg->D : cfg->D * cfg->D;
   c->chi_cur = 0;
   c->split_prec = cfg->precision == QRCTM_SPLIT;
   c->ws = static_cast<char*>(workspace);
@@ -337,8 +344,87 @@ const char* qrctm_last_error(const qrctm_ctx* ctx) {
   return ctx ? ctx->last_error.c_str() : "null context";
 }
 
+}  // extern "C"
+
+namespace {
+
+// ||X - sym(X)|| <= 1e-12 ||X|| for X = ld rank-5 slices (d x D^4) of the
+// iPEPS tensor, or the network tensor (one slice, bond D2).
+qrctm_status check_c4v(qrctm_ctx* c, const double* X, int ld) {
+  const int bond = c->network ? c->D2 : c->D;
+  const long long n = (long long)ld * bond * bond * bond * bond;
+  cudaError_t e;
+  if ((e = c4v_symmetrize(ld, bond, X, c->tmpA, c->st)) != cudaSuccess)
+    return cuda_fail(c, e, "sym A");
+  if ((e = axpby(c->tmpA, X, 1.0, -1.0, n, c->st)) != cudaSuccess)
+    return cuda_fail(c, e, "sym A");
+  if ((e = sum_squares_partials(c->tmpA, n, c->partials, 64, c->st)) != cudaSuccess)
+    return cuda_fail(c, e, "sym A");
+  if ((e = sum_squares_partials(X, n, c->partials + 64, 64, c->st)) != cudaSuccess)
+    return cuda_fail(c, e, "sym A");
+  double h[128];
+  if ((e = cudaMemcpyAsync(h, c->partials, sizeof(h), cudaMemcpyDeviceToHost, c->st)) !=
+      cudaSuccess)
+    return cuda_fail(c, e, "sym A");
+  if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(c, e, "sym A");
+  double dsym = 0, nrm = 0;
+  for (int i = 0; i < 64; ++i) { dsym += h[i]; nrm += h[64 + i]; }
+  if (!(nrm > 0) || !std::isfinite(nrm))
+    return set_err(c, QRCTM_ERR_NUMERIC, "tensor has zero or non-finite norm");
+  if (std::sqrt(dsym) > 1e-12 * std::sqrt(nrm))
+    return set_err(c, QRCTM_ERR_NOT_SYMMETRIC, "tensor is not C4v symmetric");
+  return QRCTM_OK;
+}
+
+// (C, T) <- sym_norm of the raw boundary in (Craw, Traw) at chi = D2, then
+// the warm-up steps growing chi to the target.
+qrctm_status bulk_boundary_warmup(qrctm_ctx* c) {
+  const int D2 = c->D2;
+  cudaError_t e;
+  c->chi_cur = D2;
+  if ((e = sym_norm_env(c->Craw, c->Traw, c->C, c->T, D2, D2, c->partials, c->err, c->st)) !=
+      cudaSuccess)
+    return cuda_fail(c, e, "init env");
+  int nw = c->cfg.warmup_steps;
+  if (nw == 0) {
+    long long cc = c->chi_cur;
+    while (cc < c->chi && D2 > 1) { cc *= D2; ++nw; }
+    if (nw < 2) nw = 2;
+  }
+  PhaseScope ps(c, QRCTM_PH_WARMUP);
+  for (int w = 0; w < nw; ++w) {
+    int ci = c->chi_cur;
+    int co = (int)std::min<long long>(c->chi, (long long)ci * D2);
+    // the standard method warms up with its own (exact) steps
+    if ((e = (c->cfg.method == QRCTM_METHOD_EIGEN) ? eigen_step(c, ci, co)
+                                                   : warmup_step(c, ci, co)) != cudaSuccess)
+      return cuda_fail(c, e, "warm-up");
+  }
+  c->iters = 0;
+  return QRCTM_OK;
+}
+
+// First spectrum of the new environment; the context is ready to step.
+qrctm_status finish_init(qrctm_ctx* c) {
+  qrctm_status s = sync_check(c, "init env");
+  if (s != QRCTM_OK) return s;
+  cudaError_t e;
+  if ((e = spectrum_check(c)) != cudaSuccess) return cuda_fail(c, e, "spectrum");
+  s = sync_check(c, "spectrum");
+  if (s != QRCTM_OK) return s;
+  c->spec_valid = true;
+  c->have_env = true;
+  return QRCTM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 qrctm_status qrctm_init_env(qrctm_ctx* c, const double* A, const double* C0, const double* T0) {
   if (!c || !A) return QRCTM_ERR_INVALID_ARG;
+  if (c->network)
+    return set_err(c, QRCTM_ERR_INVALID_ARG, "NETWORK layers: use qrctm_init_env_network");
   if ((C0 == nullptr) != (T0 == nullptr))
     return set_err(c, QRCTM_ERR_INVALID_ARG, "C0 and T0 must both be given or both NULL");
   const int d = c->d, D = c->D, D2 = c->D2;
@@ -348,28 +434,8 @@ qrctm_status qrctm_init_env(qrctm_ctx* c, const double* A, const double* C0, con
   if ((e = cudaMemcpyAsync(c->A, A, sizeof(double) * nA, cudaMemcpyDeviceToDevice, c->st)) !=
       cudaSuccess)
     return cuda_fail(c, e, "copy A");
-  // C4v check: ||A - sym(A)|| <= 1e-12 ||A||
-  if ((e = c4v_symmetrize(d, D, c->A, c->tmpA, c->st)) != cudaSuccess)
-    return cuda_fail(c, e, "sym A");
-  if ((e = axpby(c->tmpA, c->A, 1.0, -1.0, nA, c->st)) != cudaSuccess)
-    return cuda_fail(c, e, "sym A");
-  if ((e = sum_squares_partials(c->tmpA, nA, c->partials, 64, c->st)) != cudaSuccess)
-    return cuda_fail(c, e, "sym A");
-  if ((e = sum_squares_partials(c->A, nA, c->partials + 64, 64, c->st)) != cudaSuccess)
-    return cuda_fail(c, e, "sym A");
-  {
-    double h[128];
-    if ((e = cudaMemcpyAsync(h, c->partials, sizeof(h), cudaMemcpyDeviceToHost, c->st)) !=
-        cudaSuccess)
-      return cuda_fail(c, e, "sym A");
-    if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(c, e, "sym A");
-    double dsym = 0, nrm = 0;
-    for (int i = 0; i < 64; ++i) { dsym += h[i]; nrm += h[64 + i]; }
-    if (!(nrm > 0) || !std::isfinite(nrm))
-      return set_err(c, QRCTM_ERR_NUMERIC, "A has zero or non-finite norm");
-    if (std::sqrt(dsym) > 1e-12 * std::sqrt(nrm))
-      return set_err(c, QRCTM_ERR_NOT_SYMMETRIC, "A is not C4v symmetric");
-  }
+  qrctm_status s0 = check_c4v(c, c->A, d);
+  if (s0 != QRCTM_OK) return s0;
   if (!c->split_layers) {
     if ((e = double_layer_kernel(d, D, c->A, c->a, c->st)) != cudaSuccess)
       return cuda_fail(c, e, "double layer");
@@ -388,34 +454,58 @@ qrctm_status qrctm_init_env(qrctm_ctx* c, const double* A, const double* C0, con
     // boundary from the bulk tensor, chi0 = D^2 (<= chi, checked in cfg_valid)
     if ((e = init_env_kernel(d, D, c->A, c->Craw, c->Traw, c->st)) != cudaSuccess)
       return cuda_fail(c, e, "init env");
-    c->chi_cur = D2;
-    if ((e = sym_norm_env(c->Craw, c->Traw, c->C, c->T, D2, D2, c->partials, c->err, c->st)) !=
-        cudaSuccess)
-      return cuda_fail(c, e, "init env");
-    int nw = c->cfg.warmup_steps;
-    if (nw == 0) {
-      long long cc = c->chi_cur;
-      while (cc < c->chi && D2 > 1) { cc *= D2; ++nw; }
-      if (nw < 2) nw = 2;
-    }
-    PhaseScope ps(c, QRCTM_PH_WARMUP);
-    for (int w = 0; w < nw; ++w) {
-      int ci = c->chi_cur;
-      int co = (int)std::min<long long>(c->chi, (long long)ci * D2);
-      // the standard method warms up with its own (exact) steps
-      if ((e = (c->cfg.method == QRCTM_METHOD_EIGEN) ? eigen_step(c, ci, co)
-                                                     : warmup_step(c, ci, co)) != cudaSuccess)
-        return cuda_fail(c, e, "warm-up");
-    }
-    c->iters = 0;
+    qrctm_status s = bulk_boundary_warmup(c);
+    if (s != QRCTM_OK) return s;
   }
-  qrctm_status s = sync_check(c, "init env");
+  return finish_init(c);
+}
+
+qrctm_status qrctm_init_env_network(qrctm_ctx* c, const double* a, const double* v) {
+  if (!c || !a) return QRCTM_ERR_INVALID_ARG;
+  if (!c->network)
+    return set_err(c, QRCTM_ERR_INVALID_ARG, "qrctm_init_env_network needs NETWORK layers");
+  const int b = c->D2;
+  const long long na = (long long)b * b * b * b;
+  c->have_env = false;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(c->a, a, sizeof(double) * na, cudaMemcpyDeviceToDevice, c->st)) !=
+      cudaSuccess)
+    return cuda_fail(c, e, "copy a");
+  qrctm_status s = check_c4v(c, c->a, 1);
   if (s != QRCTM_OK) return s;
-  if ((e = spectrum_check(c)) != cudaSuccess) return cuda_fail(c, e, "spectrum");
-  s = sync_check(c, "spectrum");
+  c->iters = 0;
+  c->spec_valid = false;
+  if ((e = network_boundary(b, c->a, v, c->Craw, c->Traw, c->st)) != cudaSuccess)
+    return cuda_fail(c, e, "init env");
+  if ((s = bulk_boundary_warmup(c)) != QRCTM_OK) return s;
+  return finish_init(c);
+}
+
+qrctm_status qrctm_network_observables(qrctm_ctx* c, const double* a_obs, double* ln_kappa_out,
+                                       double* obs_out) {
+  if (!c) return QRCTM_ERR_INVALID_ARG;
+  if (!c->network)
+    return set_err(c, QRCTM_ERR_INVALID_ARG, "network observables need NETWORK layers");
+  if (!c->have_env) return set_err(c, QRCTM_ERR_STATE, "qrctm_init_env_network not called");
+  cudaError_t e;
+  {
+    PhaseScope ps(c, QRCTM_PH_ENERGY);
+    if ((e = network_traces(c, a_obs)) != cudaSuccess) return cuda_fail(c, e, "network traces");
+  }
+  double z[4] = {0, 0, 0, 0};
+  if ((e = cudaMemcpyAsync(z, c->e_d, sizeof(z), cudaMemcpyDeviceToHost, c->st)) != cudaSuccess)
+    return cuda_fail(c, e, "network traces");
+  qrctm_status s = sync_check(c, "network traces");
   if (s != QRCTM_OK) return s;
-  c->spec_valid = true;
-  c->have_env = true;
+  const double kappa = z[2] * z[0] / (z[1] * z[1]);
+  if (!std::isfinite(kappa) || !(kappa > 0))
+    return set_err(c, QRCTM_ERR_NUMERIC, "partition function per site not positive");
+  if (ln_kappa_out) *ln_kappa_out = std::log(kappa);
+  if (a_obs && obs_out) {
+    const double o = z[3] / z[2];
+    if (!std::isfinite(o)) return set_err(c, QRCTM_ERR_NUMERIC, "observable not finite");
+    *obs_out = o;
+  }
   return QRCTM_OK;
 }
 

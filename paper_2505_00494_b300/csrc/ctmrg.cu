@@ -73,7 +73,7 @@ cudaError_t renorm_edge(qrctm_ctx* c, const double* P, int co, const double* T, 
     g.M = (long long)co * ci; g.N = D4; g.K = D4;
     g.A = c->X1; g.a_m = im2(ci, 1, Smu); g.a_k = im2(D2, Sk, Su);
     g.B = c->a; g.b_k = im1(D4); g.b_n = im1(1);
-    g.C = c->X2; g.c_m = im1(D4); g.c_n = im4(D, D, D, 1, D2, D, D3);
+    g.C = c->X2; g.c_m = im1(D4); g.c_n = x2_maps(c, ci).store_n;
     if ((e = gemm_f64(g, c->st)) != cudaSuccess) return e;
   }
   }
@@ -83,7 +83,8 @@ cudaError_t renorm_edge(qrctm_ctx* c, const double* P, int co, const double* T, 
     PhaseScope ps(c, QRCTM_PH_PROJECT);
     Gemm g = gemm_ctx(c);
     g.M = (long long)co * D2; g.N = co; g.K = mi;
-    g.A = c->X2; g.a_m = im3(D, D, 1, D2, (long long)ci * D4); g.a_k = im3(D, D, D, D3, D4);
+    const X2Maps xm = x2_maps(c, ci);
+    g.A = c->X2; g.a_m = xm.ct_col; g.a_k = xm.ct_row;
     g.B = P; g.b_k = im1(1); g.b_n = im1(mi);
     g.C = Tout; g.c_m = im1(co); g.c_n = im1(1);
     if ((e = gemm_f64(g, c->st)) != cudaSuccess) return e;
@@ -149,9 +150,9 @@ cudaError_t warmup_step(qrctm_ctx* c, int ci, int co) {
   if ((e = reduced_corner(c, c->C, c->T, ci, c->Mcm)) != cudaSuccess) return e;
   // X2 <- enlarged corner: the first half of renorm_edge with P = ct
   if ((e = renorm_edge(c, c->Mcm, ci, c->T, ci, nullptr)) != cudaSuccess) return e;
-  // Ct((b,l),(r,j)) = X2[r,b,l_k,j_k,l_b,j_b]
-  const IdxMap ct_row = im3(D, D, D, D3, D4);
-  const IdxMap ct_col = im3(D, D, 1, D2, (long long)ci * D4);
+  // Ct((b,l),(r,j)) = X2[r,b,l,j]
+  const X2Maps xm = x2_maps(c, ci);
+  const IdxMap ct_row = xm.ct_row, ct_col = xm.ct_col;
   // (every use of Ct comes before the final renorm_edge overwrites X2)
   auto apply_ct = [&](const double* X, double* Y, int ncol) -> cudaError_t {
     Gemm g = gemm_ctx(c);

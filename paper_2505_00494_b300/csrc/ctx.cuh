@@ -15,6 +15,7 @@ struct qrctm_ctx {
   int chi_cur;         // current bond (< chi only if the warm-up could not grow it)
   bool split_layers;
   bool split_prec;
+  bool network;        // a classical network tensor is given directly (bond D2 = D)
   // workspace
   char* ws;
   size_t ws_bytes;
@@ -117,6 +118,35 @@ bool absorb_fused_ok(int d, int D);
 cudaError_t absorb_fused(const float* X1, const float* Ak, const float* Ab, float* X2, int ch,
                          int D, int d, long long D2p, long long dD2p, long long mp, int* err,
                          cudaStream_t s);
+
+// Classical networks (network.cu)
+cudaError_t network_boundary(int b, const double* a, const double* v, double* C0, double* T0,
+                             cudaStream_t s);
+cudaError_t network_traces(qrctm_ctx* c, const double* a_obs);
+
+// Layout of the double-layer intermediate X2 and the enlarged corner read from
+// it.  An iPEPS double layer keeps X2[m][b][d_k][j_k][d_b][j_b] (the ket and
+// bra halves of the d and j legs apart, the order the split-layer absorption
+// produces); a network tensor has no halves and X2 is X2[m][b][d][j].
+//   store_n: column (d, j) of the absorption output -> offset in an X2 row
+//   ct_row:  (b, l) -> offset (row of Ct, contraction index of the projection)
+//   ct_col:  (r, j) -> offset (column of Ct, row of the projection output)
+struct X2Maps { IdxMap store_n, ct_row, ct_col; };
+inline X2Maps x2_maps(const qrctm_ctx* c, int ci) {
+  const int D = c->D, D2 = c->D2;
+  const long long D3 = (long long)D2 * D, D4 = (long long)D2 * D2;
+  X2Maps x;
+  if (c->network) {
+    x.store_n = im1(1);
+    x.ct_row = im2(D2, D2, D4);
+    x.ct_col = im2(D2, 1, (long long)ci * D4);
+  } else {
+    x.store_n = im4(D, D, D, 1, D2, D, D3);
+    x.ct_row = im3(D, D, D, D3, D4);
+    x.ct_col = im3(D, D, 1, D2, (long long)ci * D4);
+  }
+  return x;
+}
 
 // Energy (energy.cu)
 cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2);

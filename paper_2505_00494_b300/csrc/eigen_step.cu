@@ -81,8 +81,8 @@ cudaError_t eigen_step(qrctm_ctx* c, int ci, int co) {
   {
     PhaseScope ps(c, QRCTM_PH_QR);   // the decomposition phase of this method
     // Ct((b,l),(r,j)) = X2[r,b,l_k,j_k,l_b,j_b]
-    const IdxMap ct_row = im3(D, D, D, D3, D4);
-    const IdxMap ct_col = im3(D, D, 1, D2, (long long)ci * D4);
+    const X2Maps xm = x2_maps(c, ci);
+    const IdxMap ct_row = xm.ct_row, ct_col = xm.ct_col;
     sym_corner_dense_k<<<(unsigned)std::min<long long>((m * m + 255) / 256, 65535), 256, 0, c->st>>>(
         c->X2, c->eig_E, m, ct_row, ct_col);
     note_launch();

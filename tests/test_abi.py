@@ -75,3 +75,20 @@ def test_create_rejects_bad_arguments_without_gpu(q):
     # null context calls fail cleanly
     assert q.lib.qrctm_step(None, 1, None) == 1
     assert q.lib.qrctm_householder_qr(4, 8, None, None, None, None, 0, None) == 1
+
+
+def test_network_planning_host_only(q):
+    # classical network mode: T's inner leg has D values, d = 1, FP64 only,
+    # no energy/gradient buffers
+    c = cfg(q, d=1, D=3, chi=27, layers=3)
+    b = q.lib.qrctm_workspace_bytes(ctypes.byref(c))
+    m = 27 * 3
+    assert b > 0 and b >= 2 * m * m * 8
+    assert b < q.lib.qrctm_workspace_bytes(ctypes.byref(cfg(q, d=1, D=3, chi=81, layers=3)))
+    for bad in (cfg(q, d=2, D=3, chi=27, layers=3), cfg(q, d=1, D=3, chi=27, layers=3, precision=1),
+                cfg(q, d=1, D=3, chi=27, layers=3, with_grad=1),
+                cfg(q, d=1, D=3, chi=27, layers=3, with_nnn=1),
+                cfg(q, d=1, D=3, chi=2, layers=3), cfg(q, d=1, D=3, chi=27, layers=4)):
+        assert q.lib.qrctm_workspace_bytes(ctypes.byref(bad)) == 0
+    assert q.lib.qrctm_init_env_network(None, None, None) == 1
+    assert q.lib.qrctm_network_observables(None, None, None, None) == 1
