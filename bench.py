@@ -74,11 +74,11 @@ def tf32_peak_sustained(peaks):
     return 1400.0 * 1.1 / 2.25, "tf32 = fallback sustained bf16 1.4 PFLOP/s x 1.1/2.25"
 
 
-def panel_flops(d, D, chi):
+def panel_flops(d, D, chi, m=None):
     """Average flops of one FP64 panel launch: Householder factorisation of
     an mr x nb block, 2 mr nb^2 - 2 nb^3 / 3, over the panels of the
-    (chi D^2) x chi reduced corner (nb = 32)."""
-    m, n = chi * D * D, chi
+    m x chi reduced corner (m = chi D^2 unless given; nb = 32)."""
+    m, n = (chi * D * D if m is None else m), chi
     tot, cnt = 0.0, 0
     for j0 in range(0, n, 32):
         nb = min(32, n - j0)
@@ -239,6 +239,214 @@ def converge(ctx, tol, max_iter, floor=False, window=100):
     return its, dl, False
 
 
+def timed_region(q, one_step, steps, dist, local):
+    """Exactly `steps` calls of one_step between CUDA events on the current
+    stream, with a barrier and a device synchronisation on both sides, clocks
+    sampled meanwhile.  Returns (ms of the slowest rank, kernels launched,
+    clock summary)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    launches0 = q.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gpu_id = local
+    with ClockSampler(gpu_id) as clk:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")
+        ev0.record(stream)
+        for i in range(steps):
+            one_step(i)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        if dist is not None:
+            dist.barrier()
+    launches = q.kernel_launches() - launches0
+    return max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda"), launches, clk.summary()
+
+
+def phase_profile(ctx, one_step, steps):
+    """Per-phase device times from CUDA events around each phase, on a pass
+    after the timed one (the events are not part of the timed region).
+    Returns ({phase: (ms, count)}, ms of the pass)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ctx.set_profiling(True)
+    ctx.phase_times()                                 # reset accumulators
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    for i in range(steps):
+        one_step(i)
+    pe1.record(stream)
+    torch.cuda.synchronize()
+    prof_ms = pe0.elapsed_time(pe1)
+    phases = ctx.phase_times()
+    ctx.set_profiling(False)
+    return phases, prof_ms
+
+
+def roofline_rows(kernels, phases, prof_ms, traffic):
+    """One roofline entry per (phase -> single kernel): algorithmic flops per
+    launch over its average CUDA-event duration."""
+    rows = {}
+    for ph, (kname, flops, bound_k, peak_k, note_k) in kernels.items():
+        ms_k, n_k = phases[ph]
+        if n_k == 0:
+            continue
+        avg = ms_k / n_k / 1e3
+        ach = flops / avg / 1e12
+        rows[ph] = {"kernel": kname, "bound": bound_k, "achieved": ach, "peak": peak_k,
+                    "unit": "TFLOP/s", "frac": ach / peak_k, "avg_launch_ms": avg * 1e3,
+                    "launches": n_k, "share_of_step": ms_k / prof_ms,
+                    "algorithmic_flops_per_launch": flops, "peak_source": note_k,
+                    "traffic": traffic.get(kname)}
+    return rows
+
+
+def onsager_ln_kappa(beta, n=2048):
+    """Exact -beta f of the square-lattice Ising model (Onsager), midpoint
+    rule on the periodic square; reported beside the Ising workload."""
+    t = 2 * np.pi * (np.arange(n) + 0.5) / n
+    c = np.cos(t)
+    arg = np.cosh(2 * beta) ** 2 - np.sinh(2 * beta) * (c[:, None] + c[None, :])
+    return float(np.log(2.0) + 0.5 * np.mean(np.log(arg)))
+
+
+def oracle_network_sample(w, n_steps):
+    """Oracle QR-CTMRG iterations on a classical network (bounded sample) from
+    a random symmetric environment of the workload's shape."""
+    from oracle import qrctm_oracle as o
+    a, _, _ = qi.network_input(w["model"], w["q"], w["beta"])
+    chi, b = w["chi"], w["q"]
+    rng = np.random.default_rng(1)
+    C, T = o.sym_norm(rng.standard_normal((chi, chi)), rng.standard_normal((chi, b, chi)))
+    times = []
+    for _ in range(n_steps):
+        t0 = time.perf_counter()
+        C, T = o.qr_step(C, T, a, "network")
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def bench_network(args, w, q, dist, world, rank, local):
+    """Classical network fed directly (Discussion: classical partition
+    functions): QR-CTMRG (or the standard step) iterations/s, FP64."""
+    import torch
+    chi, b = w["chi"], w["q"]
+    a_h, aobs_h, v_h = qi.network_input(w["model"], w["q"], w["beta"])
+    a = torch.tensor(a_h, dtype=torch.float64, device="cuda")
+    a_obs = torch.tensor(aobs_h, dtype=torch.float64, device="cuda")
+    v = torch.tensor(v_h, dtype=torch.float64, device="cuda") if w["fixed"] else None
+    ce = args.check_every
+    ctx = q.QRCTM(1, b, chi, layers="network", check_every=ce, method=args.method)
+    ctx.init_env_network(a, v)
+
+    def one_step(i):
+        ctx.step(1, want_delta=(i % ce == ce - 1))
+
+    for i in range(args.warmup):
+        one_step(i)
+    torch.cuda.synchronize()
+    ms, launches, clocks = timed_region(q, one_step, args.steps, dist, local)
+    value = job_rate(args.steps, world, ms)
+    phases, prof_ms = phase_profile(ctx, one_step, max(ce, min(args.steps, 10 * ce)))
+    m = chi * b
+    fp64_note = "fp64 nominal 1.25 TFLOP/s (CUDA-core FP64 pipe)"
+    kernels = {
+        "qr_panel": ("qr_panel_kernel", panel_flops(1, 1, chi, m), "alu", FP64_PEAK_TFLOPS,
+                     fp64_note),
+        "x1": ("gemm_f64_kernel", 2.0 * chi ** 3 * b * b, "alu", FP64_PEAK_TFLOPS, fp64_note),
+        "absorb": ("gemm_f64_kernel", 2.0 * chi ** 2 * b ** 4, "alu", FP64_PEAK_TFLOPS, fp64_note),
+        "project": ("gemm_f64_kernel", 2.0 * chi ** 3 * b * b, "alu", FP64_PEAK_TFLOPS,
+                    fp64_note),
+    }
+    if args.method == "eigen":
+        kernels.pop("qr_panel")
+    rows = roofline_rows(kernels, phases, prof_ms, {})
+    dom = max(rows, key=lambda k: rows[k]["share_of_step"])
+    share = {k: round(phases[k][0] / prof_ms, 4) for k in ("ct", "qr", "x1", "absorb", "project",
+                                                      "corner", "symnorm", "spectrum",
+                                                      "qr_panel")}
+    # e2e through the public API from pinned host buffers: per step (a, C, T)
+    # in, re-initialise from them, one iteration with its convergence test,
+    # (C, T) out
+    C_d, T_d, _ = ctx.get_env(spectrum=False)
+    ha, hC, hT = a.cpu().pin_memory(), C_d.cpu().pin_memory(), T_d.cpu().pin_memory()
+    da, dC, dT = torch.empty_like(a), torch.empty_like(C_d), torch.empty_like(T_d)
+    oC, oT = torch.empty_like(hC).pin_memory(), torch.empty_like(hT).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        da.copy_(ha, non_blocking=True)
+        dC.copy_(hC, non_blocking=True)
+        dT.copy_(hT, non_blocking=True)
+        ctx.init_env_network(da, None, dC, dT)
+        ctx.step(1, want_delta=True)
+        Cn, Tn, _ = ctx.get_env(spectrum=False)
+        oC.copy_(Cn, non_blocking=True)
+        oT.copy_(Tn, non_blocking=True)
+        torch.cuda.synchronize()
+        hC, hT = oC.clone(), oT.clone()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    h2d = (ha.numel() + hC.numel() + hT.numel()) * 8
+    d2h = (oC.numel() + oT.numel()) * 8 + 8
+    extras = {}
+    if not args.no_extras:
+        cctx = q.QRCTM(1, b, chi, layers="network", check_every=ce, method=args.method)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cctx.init_env_network(a, v)
+        its, dl, _ = converge(cctx, args.conv_tol or 1e-10, 4000)
+        torch.cuda.synchronize()
+        extras["time_to_converged_s"] = time.perf_counter() - t0
+        extras["converged_iterations"] = its
+        extras["converged_delta"] = dl
+        t0 = time.perf_counter()
+        lk, mo = cctx.network_observables(a_obs)
+        extras["observables_ms"] = 1e3 * (time.perf_counter() - t0)
+        extras["ln_kappa"] = lk
+        extras["observable"] = mo
+        if w["model"] == "ising":
+            extras["ln_kappa_minus_onsager"] = lk - onsager_ln_kappa(w["beta"])
+        cctx.close()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        times = oracle_network_sample(w, args.cpu_sample)
+        cpu = {"value": len(times) / sum(times), "unit": UNIT, "cores": cpu_threads(),
+               "kind": "oracle",
+               "sample": f"{len(times)} oracle QR-CTMRG iterations on the network tensor "
+                         f"(NumPy FP64, bond {b}, chi={chi}) from a random symmetric environment"}
+    if rank == 0:
+        name = "QR-CTMRG" if args.method == "qr" else "standard C4v CTMRG (eigendecomposition)"
+        line = {
+            "metric": f"{name} iterations/s ({args.workload}, classical network)",
+            "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "model": w["model"], "q": w["q"],
+                       "beta": w["beta"], "chi": chi, "bond": b, "method": args.method,
+                       "layers": "network", "check_every": ce,
+                       "parallelism": f"replicas{world}",
+                       "l2": "per-step intermediates "
+                             f"{(chi * b) ** 2 * 8 / 1e6:.1f} MB (X1); L2 not flushed"},
+            "roofline": rows[dom],
+            "roofline_kernels": rows,
+            "phase_share": share,
+            "clocks": clocks,
+            "gpu_launches": int(launches),
+            "e2e": {"value": 1.0 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "convergence": extras,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_reference(args, w, rank):
     if rank != 0:
         return
@@ -272,7 +480,8 @@ def main():
     ap.add_argument("--method", default="qr", choices=["qr", "eigen"],
                     help="qr: QR-CTMRG; eigen: the standard step with a full "
                          "eigendecomposition (comparison method, FP64)")
-    ap.add_argument("--workload", default="d2_D6_chi144", choices=sorted(qi.WORKLOADS))
+    ap.add_argument("--workload", default="d2_D6_chi144",
+                    choices=sorted(qi.WORKLOADS) + sorted(qi.NETWORK_WORKLOADS))
     ap.add_argument("--check-every", type=int, default=5)
     ap.add_argument("--cpu-sample", type=int, default=3, help="oracle steps in cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -285,8 +494,11 @@ def main():
                     help="spectrum tolerance for time-to-converged (default 1e-10; the split path "
                          "stops earlier at its precision floor)")
     args = ap.parse_args()
-    w = qi.WORKLOADS[args.workload]
-    if args.method == "eigen":
+    network = args.workload in qi.NETWORK_WORKLOADS
+    w = qi.NETWORK_WORKLOADS[args.workload] if network else qi.WORKLOADS[args.workload]
+    if network:
+        args.precision = "fp64"
+    if args.method == "eigen" and not network:
         args.precision = "fp64"
         args.no_extras = True
     if args.steps <= 0:
@@ -297,6 +509,12 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
+        if network:
+            print(json.dumps({"impl": "reference",
+                              "unavailable": "the reference arm times the oracle on the iPEPS "
+                                             "workloads; the network workloads report their "
+                                             "oracle sample in cpu_baseline"}), flush=True)
+            return
         run_reference(args, w, rank)
         return
 
@@ -312,6 +530,11 @@ def main():
     if dist is not None:
         dist.barrier()
     import paper_2505_00494_b300 as q
+    if network:
+        bench_network(args, w, q, dist, world, rank, local)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     d, D, chi = w["d"], w["D"], w["chi"]
     # every replica runs the same seeded workload
@@ -329,45 +552,10 @@ def main():
     for i in range(args.warmup):
         one_step(i)
     torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
-    launches0 = q.kernel_launches()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    try:
-        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
-    except Exception:
-        gpu_id = local
-    with ClockSampler(gpu_id) as clk:
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_push("timed")
-        ev0.record(stream)
-        for i in range(args.steps):
-            one_step(i)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_pop()
-        if dist is not None:
-            dist.barrier()
-    launches = q.kernel_launches() - launches0
-    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
+    ms, launches, clocks = timed_region(q, one_step, args.steps, dist, local)
     ms_per_step = ms / args.steps
     value = job_rate(args.steps, world, ms)
-
-    # per-phase device times from CUDA events around each phase, on a separate
-    # pass after the timed one (the events are not part of the timed region)
-    prof_steps = max(ce, min(args.steps, 10 * ce))
-    ctx.set_profiling(True)
-    ctx.phase_times()                                 # reset accumulators
-    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    pe0.record(stream)
-    for i in range(prof_steps):
-        one_step(i)
-    pe1.record(stream)
-    torch.cuda.synchronize()
-    prof_ms = pe0.elapsed_time(pe1)
-    phases = ctx.phase_times()
-    ctx.set_profiling(False)
+    phases, prof_ms = phase_profile(ctx, one_step, max(ce, min(args.steps, 10 * ce)))
 
     # roofline of the dominant kernel.  Per-phase device times come from CUDA
     # events on the library's stream; the phases below are one kernel each
@@ -392,18 +580,7 @@ def main():
             "x1": ("gemm_f64_kernel", fl["x1"], "alu", FP64_PEAK_TFLOPS, fp64_note),
             "project": ("gemm_f64_kernel", fl["project"], "alu", FP64_PEAK_TFLOPS, fp64_note),
         })
-    rows = {}
-    for ph, (kname, flops, bound_k, peak_k, note_k) in kernels.items():
-        ms_k, n_k = phases[ph]
-        if n_k == 0:
-            continue
-        avg = ms_k / n_k / 1e3
-        ach = flops / avg / 1e12
-        rows[ph] = {"kernel": kname, "bound": bound_k, "achieved": ach, "peak": peak_k,
-                    "unit": "TFLOP/s", "frac": ach / peak_k, "avg_launch_ms": avg * 1e3,
-                    "launches": n_k, "share_of_step": ms_k / prof_ms,
-                    "algorithmic_flops_per_launch": flops, "peak_source": note_k,
-                    "traffic": traffic.get(kname)}
+    rows = roofline_rows(kernels, phases, prof_ms, traffic)
     dom = max(rows, key=lambda k: rows[k]["share_of_step"])
     share = {k: round(phases[k][0] / prof_ms, 4) for k in ("ct", "qr", "x1", "absorb", "project",
                                                       "corner", "symnorm", "spectrum",
@@ -555,7 +732,7 @@ def main():
             "roofline": rows[dom],
             "roofline_kernels": rows,
             "phase_share": share,
-            "clocks": clk.summary(),
+            "clocks": clocks,
             "gpu_launches": int(launches),
             "e2e": {"value": 1.0 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},

@@ -182,9 +182,13 @@ qrctm_status qrctm_energy_grad(qrctm_ctx* ctx, const qrctm_model* model, int mod
  * contracted with v,
  *   C0[d,r] = sum_{u,l} v[u] v[l] a[u,l,d,r],  T0[u,r,d] = sum_l v[l] a[u,l,d,r],
  * (a fixed-spin vector selects one ordered state), then the warm-up steps
- * grow chi as in qrctm_init_env.  QRCTM_ERR_INVALID_ARG on a context that is
- * not in network mode. */
-qrctm_status qrctm_init_env_network(qrctm_ctx* ctx, const double* a, const double* v);
+ * grow chi as in qrctm_init_env.  C0, T0: optional device environment
+ * (chi*chi and chi*D*chi doubles, both or neither); when given they are
+ * symmetrised, normalised and used as is (v ignored, no warm-up), e.g. the
+ * converged environment of a neighbouring coupling.  QRCTM_ERR_INVALID_ARG
+ * on a context that is not in network mode. */
+qrctm_status qrctm_init_env_network(qrctm_ctx* ctx, const double* a, const double* v,
+                                    const double* C0, const double* T0);
 
 /* Partition function per site and a one-site expectation value at the
  * current environment: kappa = Z11 Z00 / Z10^2 with Z00 = Tr C^4, Z10 the

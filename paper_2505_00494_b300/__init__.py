@@ -73,7 +73,7 @@ _sig = {
     "qrctm_energy_grad": ([_vp, ctypes.POINTER(Model), ctypes.c_int, ctypes.c_int, _vp, _dp],
                           ctypes.c_int),
     "qrctm_get_env": ([_vp, _vp, _vp, _dp], ctypes.c_int),
-    "qrctm_init_env_network": ([_vp, _vp, _vp], ctypes.c_int),
+    "qrctm_init_env_network": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "qrctm_network_observables": ([_vp, _vp, _dp, _dp], ctypes.c_int),
     "qrctm_iterations": ([_vp], ctypes.c_int),
     "qrctm_grad_iterations": ([_vp], ctypes.c_int),
@@ -198,11 +198,12 @@ class QRCTM:
         self.A = A
         self._check(_load().qrctm_init_env(self.h, _ptr(A), _ptr(C0), _ptr(T0)), "qrctm_init_env")
 
-    def init_env_network(self, a, v=None):
+    def init_env_network(self, a, v=None, C0=None, T0=None):
         """Classical network tensor a[u,l,d,r] (bond D) fed directly; v: the
-        boundary vector (None = all ones)."""
+        boundary vector (None = all ones); (C0, T0): a starting environment
+        used as it is instead of the boundary and warm-up."""
         self.A = a
-        self._check(_load().qrctm_init_env_network(self.h, _ptr(a), _ptr(v)),
+        self._check(_load().qrctm_init_env_network(self.h, _ptr(a), _ptr(v), _ptr(C0), _ptr(T0)),
                     "qrctm_init_env_network")
 
     def network_observables(self, a_obs=None):

@@ -460,10 +460,13 @@ qrctm_status qrctm_init_env(qrctm_ctx* c, const double* A, const double* C0, con
   return finish_init(c);
 }
 
-qrctm_status qrctm_init_env_network(qrctm_ctx* c, const double* a, const double* v) {
+qrctm_status qrctm_init_env_network(qrctm_ctx* c, const double* a, const double* v,
+                                    const double* C0, const double* T0) {
   if (!c || !a) return QRCTM_ERR_INVALID_ARG;
   if (!c->network)
     return set_err(c, QRCTM_ERR_INVALID_ARG, "qrctm_init_env_network needs NETWORK layers");
+  if ((C0 == nullptr) != (T0 == nullptr))
+    return set_err(c, QRCTM_ERR_INVALID_ARG, "C0 and T0 must both be given or both NULL");
   const int b = c->D2;
   const long long na = (long long)b * b * b * b;
   c->have_env = false;
@@ -475,6 +478,13 @@ qrctm_status qrctm_init_env_network(qrctm_ctx* c, const double* a, const double*
   if (s != QRCTM_OK) return s;
   c->iters = 0;
   c->spec_valid = false;
+  if (C0 != nullptr) {
+    c->chi_cur = c->chi;
+    if ((e = sym_norm_env(C0, T0, c->C, c->T, c->chi, b, c->partials, c->err, c->st)) !=
+        cudaSuccess)
+      return cuda_fail(c, e, "init env");
+    return finish_init(c);
+  }
   if ((e = network_boundary(b, c->a, v, c->Craw, c->Traw, c->st)) != cudaSuccess)
     return cuda_fail(c, e, "init env");
   if ((s = bulk_boundary_warmup(c)) != QRCTM_OK) return s;

@@ -18,12 +18,21 @@ for them; see the workload list in the iPEPS and Results paragraphs):
   ``sym(X) = sym(G) * w + bias * P``.
 * ``raw_direction(d, D, seed)`` returns ``N(0,1)`` draws for a
   finite-difference direction ``v = sym(N) / ||sym(N)||``.
+* ``network_input(model, q, beta)`` returns the classical spin model itself
+  (Discussion: classical partition functions) as the C4v network tensor
+  ``a[u,l,d,r] = sum_s W[s,u] W[s,l] W[s,d] W[s,r]`` with ``W = B^(1/2)`` and
+  ``B`` the bond Boltzmann weight (``exp(beta s s')`` for Ising, s = +-1;
+  ``exp(beta delta_{s s'})`` for q-state Potts), the tensor with the spin
+  (Ising) or ``delta_{s,0}`` (Potts) inserted, and the fixed-spin boundary
+  vector ``W[0]``.  This is the model's definition, the input both sides
+  consume; the CTMRG arithmetic stays in each side's own code.
 """
 from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["raw_tensor", "raw_direction", "decay_mask", "WORKLOADS"]
+__all__ = ["raw_tensor", "raw_direction", "decay_mask", "network_input", "WORKLOADS",
+           "NETWORK_WORKLOADS"]
 
 
 def decay_mask(d: int, D: int) -> np.ndarray:
@@ -49,6 +58,34 @@ def raw_tensor(d: int, D: int, seed: int = 0, decay: bool = False,
 def raw_direction(d: int, D: int, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return np.ascontiguousarray(rng.standard_normal((d, D, D, D, D)))
+
+
+def network_input(model: str, q: int, beta: float):
+    """(a, a_obs, v): network tensor (bond q), observable tensor, boundary vector."""
+    if model == "ising":
+        spins = np.array([1.0, -1.0])
+        B = np.exp(beta * np.outer(spins, spins))
+        o = spins
+    elif model == "potts":
+        B = np.exp(beta * np.eye(q))
+        o = (np.arange(q) == 0).astype(np.float64)
+    else:
+        raise ValueError(model)
+    lam, V = np.linalg.eigh(B)
+    W = (V * np.sqrt(np.clip(lam, 0.0, None))) @ V.T
+    a = np.einsum("su,sl,sd,sr->uldr", W, W, W, W)
+    a_obs = np.einsum("s,su,sl,sd,sr->uldr", o, W, W, W, W)
+    return (np.ascontiguousarray(a), np.ascontiguousarray(a_obs),
+            np.ascontiguousarray(W[0]))
+
+
+# Classical networks fed directly: near (below) the critical coupling, where
+# the correlation length is tens of sites (Ising beta_c = 0.4407, 3-state
+# Potts beta_c = ln(1 + sqrt 3) = 1.005).
+NETWORK_WORKLOADS = {
+    "ising_b2_chi256": dict(model="ising", q=2, beta=0.43, chi=256, fixed=False),
+    "potts3_b3_chi243": dict(model="potts", q=3, beta=0.95, chi=243, fixed=False),
+}
 
 
 # The workloads, by what they are.  ``chi`` is the environment bond,

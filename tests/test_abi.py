@@ -90,5 +90,5 @@ def test_network_planning_host_only(q):
                 cfg(q, d=1, D=3, chi=27, layers=3, with_nnn=1),
                 cfg(q, d=1, D=3, chi=2, layers=3), cfg(q, d=1, D=3, chi=27, layers=4)):
         assert q.lib.qrctm_workspace_bytes(ctypes.byref(bad)) == 0
-    assert q.lib.qrctm_init_env_network(None, None, None) == 1
+    assert q.lib.qrctm_init_env_network(None, None, None, None, None) == 1
     assert q.lib.qrctm_network_observables(None, None, None, None) == 1

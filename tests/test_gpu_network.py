@@ -99,9 +99,31 @@ def test_network_errors():
     assert ei.value.code == 8   # STATE: no environment yet
     ctx.close()
     # an iPEPS context refuses the network calls
-    A = o.normalized_input(np.ones((2, 2, 2, 2, 2)))
     ctx2 = q.QRCTM(2, 2, 8)
     with pytest.raises(q.QRCTMError):
         ctx2.init_env_network(_dev(a))
     ctx2.close()
-    del A
+
+
+def test_network_restart_from_environment():
+    # a converged environment handed back in is a fixed point: one more step
+    # keeps ln kappa, and a neighbouring coupling starts from it
+    import paper_2505_00494_b300 as q
+    a, a_s, W = o.ising_network(0.3)
+    ctx = q.QRCTM(1, 2, 16, layers="network", check_every=5)
+    ctx.init_env_network(_dev(a))
+    ctx.run_to_convergence(1e-12, 2000)
+    lk0, _ = ctx.network_observables()
+    C, T, _ = ctx.get_env(spectrum=False)
+    ctx.init_env_network(_dev(a), None, C, T)
+    ctx.step(5)
+    lk1, _ = ctx.network_observables()
+    assert abs(lk1 - lk0) < 1e-12
+    a2, _, _ = o.ising_network(0.32)
+    ctx.init_env_network(_dev(a2), None, C, T)
+    ctx.run_to_convergence(1e-12, 2000)
+    lk2, _ = ctx.network_observables()
+    assert abs(lk2 - o.onsager_free_energy(0.32)) < 1e-10
+    with pytest.raises(q.QRCTMError):
+        ctx.init_env_network(_dev(a), None, C, None)
+    ctx.close()

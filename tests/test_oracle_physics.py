@@ -168,3 +168,16 @@ def test_rdm_nn_by_brute_force_patch():
     ref = np.einsum(*ops, [40, 41, 42, 43], optimize="greedy")
     got = o.rdm_nn(C, T, A)
     assert np.abs(ref - got).max() < 1e-14 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("model,q,beta", [("ising", 2, 0.43), ("potts", 3, 0.95), ("potts", 4, 0.3)])
+def test_network_input_is_the_oracle_model(model, q, beta):
+    # the bench's input builder and the oracle's model agree exactly
+    a, a_obs, v = qi.network_input(model, q, beta)
+    if model == "ising":
+        a2, a2_obs, W = o.ising_network(beta)
+        assert np.abs(a_obs - a2_obs).max() < 1e-15
+    else:
+        a2, W = o.potts_network(q, beta)
+    assert np.abs(a - a2).max() < 1e-15
+    assert np.abs(v - W[0]).max() < 1e-15
