@@ -616,3 +616,146 @@ def yang_magnetization(beta):
     """Spontaneous magnetisation (1 - sinh(2 beta)^-4)^(1/8) below T_c."""
     s = np.sinh(2 * beta)
     return (1.0 - s ** -4) ** 0.125 if s > 1 else 0.0
+
+
+# ---------------------------------------------------------------------------
+# Variational optimisation (Automatic differentiation paragraph): L-BFGS on
+# E(A); each evaluation runs two CTMRG steps without gradient tracking, then
+# k tracked steps, the energy and its gradient; the boundary tensors of the
+# previous step are reused except during the line search.
+# ---------------------------------------------------------------------------
+
+def c4v_orbit_basis(d, D):
+    """Orthonormal basis of the C4v-invariant tensors A[s,u,l,d,r]: one
+    indicator per orbit of index tuples under the eight leg permutations,
+    divided by the square root of the orbit size.  Its length is n(D) of the
+    iPEPS footnote."""
+    seen = np.zeros((d, D, D, D, D), dtype=bool)
+    basis = []
+    for idx in np.ndindex(d, D, D, D, D):
+        if seen[idx]:
+            continue
+        s, legs = idx[0], idx[1:]
+        orbit = {(s,) + tuple(legs[p[i]] for i in range(4)) for p in C4V_PERMS}
+        v = np.zeros((d, D, D, D, D))
+        for o_idx in orbit:
+            v[o_idx] = 1.0
+            seen[o_idx] = True
+        basis.append(v / np.sqrt(len(orbit)))
+    return basis
+
+
+def unrolled_energy_grad(A, C, T, k, J1=1.0, J2=0.0, h=1e-20, layers="double"):
+    """E(A, F^k(A; C, T)) with (C, T) detached, its C4v gradient (one complex
+    step along every orbit basis vector: g = sum_O (dE . v_O) v_O = sym(dE)),
+    and the environment after the k steps."""
+    Ck, Tk = C, T
+    for _ in range(k):
+        Ck, Tk = qr_step(Ck, Tk, A, layers)
+    E = float(np.real(energy(Ck, Tk, A, J1, J2)))
+    g = np.zeros_like(A)
+    for v in c4v_orbit_basis(A.shape[0], A.shape[1]):
+        Ac = A.astype(complex) + 1j * h * v
+        Cc, Tc = C.astype(complex), T.astype(complex)
+        for _ in range(k):
+            Cc, Tc = qr_step(Cc, Tc, Ac, layers)
+        g = g + (float(np.imag(energy(Cc, Tc, Ac, J1, J2))) / h) * v
+    return E, g, Ck, Tk
+
+
+def lbfgs_direction(g, pairs):
+    """p = -H g by the L-BFGS two-loop recursion over the stored pairs
+    (s, y), oldest first, with H0 = (s.y / y.y) I from the newest pair
+    (Nocedal and Wright, Numerical Optimization, two-loop recursion)."""
+    q = g.copy()
+    alphas = []
+    for s, y in reversed(pairs):
+        a = np.sum(s * q) / np.sum(y * s)
+        alphas.append(a)
+        q = q - a * y
+    if pairs:
+        s, y = pairs[-1]
+        q = q * (np.sum(s * y) / np.sum(y * y))
+    for (s, y), a in zip(pairs, reversed(alphas)):
+        b = np.sum(y * q) / np.sum(y * s)
+        q = q + (a - b) * s
+    return -q
+
+
+def lbfgs_minimize(evaluate, x0, n_steps, history=10, step0=0.1, c1=1e-4, max_ls=10,
+                   accept=None):
+    """L-BFGS with a backtracking Armijo line search.
+
+    ``evaluate(x, trial) -> (f, g)``; ``trial`` is 0 for the starting point
+    and for the first point tried in a step, >= 1 for the later points of a
+    line search.  Readings (the paper names L-BFGS only): the first step has
+    length ``step0`` along -g, later steps start at alpha = 1; a point is
+    accepted when f <= f_k + c1 alpha g.p, else alpha is halved, at most
+    ``max_ls`` points per step; a pair (s, y) is kept when s.y > 1e-10 |s||y|;
+    a direction that is not a descent direction resets the history.
+    ``accept()`` is called after a point is accepted; the loop ends early at
+    a zero gradient.  Returns (x, energies, evaluations, line_search_failed).
+    """
+    x = x0.copy()
+    f, g = evaluate(x, 0)
+    if accept:
+        accept()
+    fs, nev, pairs = [f], 1, []
+    for _ in range(n_steps):
+        if not np.any(g):
+            break                        # stationary point: no direction
+        p = lbfgs_direction(g, pairs)
+        gp = float(np.sum(g * p))
+        if not gp < 0:
+            pairs = []
+            p = -g
+            gp = float(np.sum(g * p))
+        alpha = 1.0 if pairs else step0 / float(np.sqrt(np.sum(p * p)))
+        ok = False
+        for t in range(max_ls):
+            xt = x + alpha * p
+            ft, gt = evaluate(xt, t)
+            nev += 1
+            if ft <= f + c1 * alpha * gp:
+                ok = True
+                break
+            alpha *= 0.5
+        if not ok:
+            return x, fs, nev, True
+        if accept:
+            accept()
+        s, y = xt - x, gt - g
+        if np.sum(s * y) > 1e-10 * np.sqrt(np.sum(s * s) * np.sum(y * y)):
+            pairs = (pairs + [(s, y)])[-history:]
+        x, f, g = xt, ft, gt
+        fs.append(f)
+    return x, fs, nev, False
+
+
+def optimize_ipeps(A0, chi, J1=1.0, J2=0.0, n_steps=5, k=10, nograd=2, history=10,
+                   step0=0.1, c1=1e-4, max_ls=10, env_tol=1e-12, env_max_iter=2000):
+    """L-BFGS on the energy per site (Automatic differentiation paragraph).
+
+    An evaluation at A takes the environment of the last accepted point
+    (trial 0 of a step) or a fresh one, converged from the bulk boundary
+    (start, and the later points of a line search); runs ``nograd`` QR-CTMRG
+    steps, then the energy and gradient of ``k`` tracked steps.  The
+    environment after the tracked steps is what the next step reuses."""
+    layers = "double"
+    state = {"env": None, "cand": None}
+
+    def evaluate(A, trial):
+        if trial == 0 and state["env"] is not None:
+            C, T = state["env"]
+        else:
+            C, T, _ = ctmrg(A, chi, "qr", tol=env_tol, max_iter=env_max_iter, check_every=5)
+        for _ in range(nograd):
+            C, T = qr_step(C, T, A, layers)
+        E, g, Ck, Tk = unrolled_energy_grad(A, C, T, k, J1, J2, layers=layers)
+        state["cand"] = (Ck, Tk)
+        return E, g
+
+    def accept():
+        state["env"] = state["cand"]
+
+    return lbfgs_minimize(evaluate, A0, n_steps, history, step0, c1, max_ls, accept)
