@@ -80,6 +80,8 @@ typedef struct {
                          enlarged corner, Standard CTMRG paragraph; FP64 only, the
                          comparison method; cuSOLVER's handle keeps a small device
                          state of its own)                                      */
+  int opt_history;    /* > 0: reserve workspace for qrctm_optimize keeping up to this
+                         many L-BFGS pairs (1..32; needs with_grad)             */
 } qrctm_config;
 
 typedef struct {
@@ -200,6 +202,47 @@ qrctm_status qrctm_init_env_network(qrctm_ctx* ctx, const double* a, const doubl
  * context's stream and synchronises it. */
 qrctm_status qrctm_network_observables(qrctm_ctx* ctx, const double* a_obs, double* ln_kappa_out,
                                        double* obs_out);
+
+/* ----- variational optimisation ------------------------------------------ */
+
+/* Options of qrctm_optimize (Automatic differentiation paragraph).  Zero
+ * fields take the defaults in brackets. */
+typedef struct {
+  int history;        /* L-BFGS pairs kept [the config's opt_history]           */
+  int nograd_steps;   /* QR-CTMRG steps without gradient tracking per
+                         evaluation (the paper takes 2; 0 is allowed)           */
+  int k_unroll;       /* tracked steps of the unrolled gradient, 1..32 [10]     */
+  int max_ls;         /* points tried per line search [10]                      */
+  double c1;          /* Armijo constant [1e-4]                                 */
+  double step0;       /* length of the first step along -g [0.1]                */
+  double env_tol;     /* spectrum tolerance of a fresh environment [config tol] */
+  int env_max_iter;   /* iteration cap of a fresh environment [config max_iter] */
+} qrctm_lbfgs_options;
+
+/* Minimise the energy per site over the C4v tensor A by L-BFGS (Automatic
+ * differentiation paragraph).  Every evaluation at a point A' runs
+ * opt->nograd_steps QR-CTMRG steps, then the energy and its gradient
+ * through opt->k_unroll tracked steps (qrctm_energy_grad, UNROLL mode); it
+ * starts from the environment the previous accepted point ended with, except
+ * the start and the second and later points of a line search, which build a
+ * fresh environment (qrctm_init_env, then qrctm_run_to_convergence to
+ * env_tol).  Steps: p = -H g by the two-loop recursion (H0 = s.y/y.y), the
+ * first step of length step0 along -g, later ones from alpha = 1, halved
+ * until E' <= E + c1 alpha g.p (at most max_ls points); pairs with
+ * s.y <= 1e-10 |s||y| are skipped; a non-descent direction resets the
+ * history.  The two-loop recursion, trial points and pair updates run in
+ * device kernels.
+ * A: device, d*D^4 doubles, C4v symmetric; the start on entry, the last
+ * accepted point on return.  energies: host, n_steps + 1 doubles (E at the
+ * start and after each accepted step) or NULL.  steps_out, evaluations_out:
+ * host, accepted steps and energy+gradient evaluations (either may be NULL).
+ * Needs opt_history > 0 and with_grad (and with_nnn when J2 != 0).
+ * Returns QRCTM_ERR_NOT_CONVERGED when a line search finds no decrease (A
+ * holds the last accepted point); the loop also ends early at a zero
+ * gradient. */
+qrctm_status qrctm_optimize(qrctm_ctx* ctx, const qrctm_model* model,
+                            const qrctm_lbfgs_options* opt, int n_steps, double* A,
+                            double* energies, int* steps_out, int* evaluations_out);
 
 /* Copy the environment out: C (chi*chi), T (chi*D^2*chi) on the device (may be
  * NULL); spectrum_host: chi doubles, sorted |eig(C)| (may be NULL). */

@@ -51,11 +51,20 @@ class Config(ctypes.Structure):
         ("grad_max_iter", ctypes.c_int), ("grad_tol", ctypes.c_double),
         ("with_nnn", ctypes.c_int), ("with_grad", ctypes.c_int),
         ("stream", ctypes.c_void_p), ("method", ctypes.c_int),
+        ("opt_history", ctypes.c_int),
     ]
 
 
 class Model(ctypes.Structure):
     _fields_ = [("J1", ctypes.c_double), ("J2", ctypes.c_double)]
+
+
+class LbfgsOptions(ctypes.Structure):
+    _fields_ = [
+        ("history", ctypes.c_int), ("nograd_steps", ctypes.c_int), ("k_unroll", ctypes.c_int),
+        ("max_ls", ctypes.c_int), ("c1", ctypes.c_double), ("step0", ctypes.c_double),
+        ("env_tol", ctypes.c_double), ("env_max_iter", ctypes.c_int),
+    ]
 
 
 _vp, _dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
@@ -74,6 +83,9 @@ _sig = {
                           ctypes.c_int),
     "qrctm_get_env": ([_vp, _vp, _vp, _dp], ctypes.c_int),
     "qrctm_init_env_network": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "qrctm_optimize": ([_vp, ctypes.POINTER(Model), ctypes.POINTER(LbfgsOptions), ctypes.c_int,
+                        _vp, _dp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+                       ctypes.c_int),
     "qrctm_network_observables": ([_vp, _vp, _dp, _dp], ctypes.c_int),
     "qrctm_iterations": ([_vp], ctypes.c_int),
     "qrctm_grad_iterations": ([_vp], ctypes.c_int),
@@ -151,13 +163,14 @@ class QRCTM:
 
     def __init__(self, d, D, chi, precision="fp64", layers="auto", warmup_steps=0,
                  check_every=1, tol=1e-10, max_iter=500, grad_max_iter=0, grad_tol=0.0,
-                 with_nnn=False, with_grad=False, stream=None, device="cuda", method="qr"):
+                 with_nnn=False, with_grad=False, stream=None, device="cuda", method="qr",
+                 opt_history=0):
         torch = _torch()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.cfg = Config(d, D, chi, PRECISION[precision], LAYERS[layers], warmup_steps,
                           check_every, tol, max_iter, grad_max_iter, grad_tol, int(with_nnn),
                           int(with_grad), ctypes.c_void_p(self.stream.cuda_stream),
-                          METHOD[method])
+                          METHOD[method], opt_history)
         nbytes = _load().qrctm_workspace_bytes(ctypes.byref(self.cfg))
         if nbytes == 0:
             raise QRCTMError(1, "qrctm_workspace_bytes", "invalid configuration")
@@ -246,6 +259,27 @@ class QRCTM:
         self._check(_load().qrctm_energy_grad(self.h, ctypes.byref(m), GRAD_MODE[mode], k_unroll,
                                           _ptr(grad), ctypes.byref(e)), "qrctm_energy_grad")
         return e.value, grad
+
+    def optimize(self, A, n_steps, J1=1.0, J2=0.0, k_unroll=10, nograd_steps=2, history=0,
+                 max_ls=0, c1=0.0, step0=0.0, env_tol=0.0, env_max_iter=0,
+                 raise_on_line_search=False):
+        """L-BFGS on the energy per site; A (device, C4v) is updated in place.
+        Returns (energies of the accepted points, evaluations, line search
+        failed)."""
+        import numpy as np
+        opt = LbfgsOptions(history, nograd_steps, k_unroll, max_ls, c1, step0, env_tol,
+                           env_max_iter)
+        en = np.zeros(n_steps + 1)
+        steps, evals = ctypes.c_int(0), ctypes.c_int(0)
+        m = Model(J1, J2)
+        code = _load().qrctm_optimize(self.h, ctypes.byref(m), ctypes.byref(opt), n_steps, _ptr(A),
+                                      en.ctypes.data_as(_dp), ctypes.byref(steps),
+                                      ctypes.byref(evals))
+        failed = code == 3
+        if code != 0 and not (failed and not raise_on_line_search):
+            self._check(code, "qrctm_optimize")
+        self.A = A
+        return en[:steps.value + 1], evals.value, failed
 
     def get_env(self, spectrum=True):
         torch = _torch()

@@ -27,6 +27,8 @@ bool cfg_valid(const qrctm_config& c) {
   if (c.check_every < 0 || c.warmup_steps < -1) return false;
   const bool net = c.layers == QRCTM_LAYERS_NETWORK;
   if (net && (c.d != 1 || c.precision != QRCTM_FP64 || c.with_grad || c.with_nnn)) return false;
+  if (c.opt_history < 0 || c.opt_history > 32) return false;
+  if (c.opt_history > 0 && !c.with_grad) return false;
   const long long D2 = net ? (long long)c.D : (long long)c.D * c.D;
   if (D2 > 4096 || (long long)c.chi * D2 > (1ll << 20)) return false;
   if (c.chi < D2) return false;
@@ -187,6 +189,28 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
   } else if (carve) {
     c->mm32 = nullptr; c->mm32_floats = 0;
   }
+  // L-BFGS optimisation buffers
+  if (cfg.opt_history > 0) {
+    const size_t h = cfg.opt_history, n = d * D2 * D2;
+    take(carve ? &c->opt_S : nullptr, h * n);
+    take(carve ? &c->opt_Y : nullptr, h * n);
+    take(carve ? &c->opt_x : nullptr, n);
+    take(carve ? &c->opt_xt : nullptr, n);
+    take(carve ? &c->opt_g : nullptr, n);
+    take(carve ? &c->opt_gt : nullptr, n);
+    take(carve ? &c->opt_p : nullptr, n);
+    take(carve ? &c->opt_q : nullptr, n);
+    take(carve ? &c->opt_out : nullptr, 16);
+    take(carve ? &c->opt_Cp : nullptr, nC);
+    take(carve ? &c->opt_Tp : nullptr, nT);
+    take(carve ? &c->opt_Cc : nullptr, nC);
+    take(carve ? &c->opt_Tc : nullptr, nT);
+    if (carve) c->opt_hist = (int)h;
+  } else if (carve) {
+    c->opt_hist = 0;
+    c->opt_S = c->opt_Y = c->opt_x = c->opt_xt = c->opt_g = c->opt_gt = c->opt_p = c->opt_q =
+        c->opt_out = c->opt_Cp = c->opt_Tp = c->opt_Cc = c->opt_Tc = nullptr;
+  }
   // standard method: dense enlarged corner, eigenvalues, solver workspace
   if (cfg.method == QRCTM_METHOD_EIGEN) {
     const size_t ew = eigen_work_doubles((long long)m);
@@ -205,6 +229,7 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
     c->eig_info = c->eig_idx = nullptr;
   }
   if (carve) {
+    c->grad_keep_env = false;
     c->network = net;
     c->split_layers = split;
     c->mm_split = false;   // set for the duration of a split-precision gradient
@@ -619,6 +644,132 @@ qrctm_status qrctm_energy_grad(qrctm_ctx* c, const qrctm_model* model, int mode,
   c->grad_resid = resid;
   if (e != cudaSuccess) return cuda_fail(c, e, "energy gradient");
   return sync_check(c, "energy gradient");
+}
+
+qrctm_status qrctm_optimize(qrctm_ctx* c, const qrctm_model* model,
+                            const qrctm_lbfgs_options* opt, int n_steps, double* A,
+                            double* energies, int* steps_out, int* evaluations_out) {
+  if (!c || !model || !opt || !A || n_steps < 0) return QRCTM_ERR_INVALID_ARG;
+  if (steps_out) *steps_out = 0;
+  if (evaluations_out) *evaluations_out = 0;
+  if (c->opt_hist <= 0)
+    return set_err(c, QRCTM_ERR_INVALID_ARG, "qrctm_optimize needs opt_history > 0");
+  const int hist = opt->history > 0 ? std::min(opt->history, c->opt_hist) : c->opt_hist;
+  const int k = opt->k_unroll > 0 ? opt->k_unroll : 10;
+  const int nograd = opt->nograd_steps;
+  const int max_ls = opt->max_ls > 0 ? opt->max_ls : 10;
+  const double c1 = opt->c1 > 0 ? opt->c1 : 1e-4;
+  const double step0 = opt->step0 > 0 ? opt->step0 : 0.1;
+  const double env_tol = opt->env_tol > 0 ? opt->env_tol : (c->cfg.tol > 0 ? c->cfg.tol : 1e-10);
+  const int env_max = opt->env_max_iter > 0 ? opt->env_max_iter
+                                            : (c->cfg.max_iter > 0 ? c->cfg.max_iter : 500);
+  if (nograd < 0 || k > kGradMaxUnroll)
+    return set_err(c, QRCTM_ERR_INVALID_ARG, "nograd_steps >= 0 and k_unroll <= 32");
+  const int n = c->d * c->D2 * c->D2;
+  const long long nC = (long long)c->chi * c->chi, nT = (long long)c->chi * c->D2 * c->chi;
+  cudaStream_t st = c->st;
+  cudaError_t e;
+  int evals = 0;
+  auto dcopy = [&](double* dst, const double* src, long long cnt) {
+    return cudaMemcpyAsync(dst, src, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, st);
+  };
+  // one evaluation at X: environment (reused or fresh), untracked steps,
+  // energy and gradient through k tracked steps into opt_gt, the
+  // environment after them into (opt_Cc, opt_Tc)
+  auto evaluate = [&](const double* X, bool fresh, double* E) -> qrctm_status {
+    qrctm_status s;
+    if (fresh) {
+      if ((s = qrctm_init_env(c, X, nullptr, nullptr)) != QRCTM_OK) return s;
+      int it;
+      double dl;
+      s = qrctm_run_to_convergence(c, env_tol, env_max, &it, &dl);
+      if (s != QRCTM_OK && s != QRCTM_ERR_NOT_CONVERGED) return s;
+    } else {
+      if ((s = qrctm_init_env(c, X, c->opt_Cp, c->opt_Tp)) != QRCTM_OK) return s;
+    }
+    if (nograd > 0 && (s = qrctm_step(c, nograd, nullptr)) != QRCTM_OK) return s;
+    c->grad_keep_env = true;
+    s = qrctm_energy_grad(c, model, QRCTM_GRAD_UNROLL, k, c->opt_gt, E);
+    c->grad_keep_env = false;
+    if (s != QRCTM_OK) return s;
+    if (c->chi_cur != c->chi)
+      return set_err(c, QRCTM_ERR_INVALID_ARG, "the warm-up did not reach chi");
+    if ((e = dcopy(c->opt_Cc, c->C, nC)) != cudaSuccess) return cuda_fail(c, e, "optimize");
+    if ((e = dcopy(c->opt_Tc, c->T, nT)) != cudaSuccess) return cuda_fail(c, e, "optimize");
+    ++evals;
+    if (evaluations_out) *evaluations_out = evals;
+    return QRCTM_OK;
+  };
+  // accept the last evaluation at X (= opt_xt, or opt_x at the start)
+  auto accept = [&](bool from_trial) -> cudaError_t {
+    cudaError_t r = cudaSuccess;
+    if (from_trial) r = dcopy(c->opt_x, c->opt_xt, n);
+    if (r == cudaSuccess) r = dcopy(c->opt_g, c->opt_gt, n);
+    if (r == cudaSuccess) r = dcopy(c->opt_Cp, c->opt_Cc, nC);
+    if (r == cudaSuccess) r = dcopy(c->opt_Tp, c->opt_Tc, nT);
+    return r;
+  };
+  auto read_out = [&](double* h, int cnt) -> cudaError_t {
+    cudaError_t r = cudaMemcpyAsync(h, c->opt_out, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st);
+    return r == cudaSuccess ? cudaStreamSynchronize(st) : r;
+  };
+  if ((e = dcopy(c->opt_x, A, n)) != cudaSuccess) return cuda_fail(c, e, "optimize");
+  double E = 0.0;
+  qrctm_status s = evaluate(c->opt_x, true, &E);
+  if (s != QRCTM_OK) return s;
+  if ((e = accept(false)) != cudaSuccess) return cuda_fail(c, e, "optimize");
+  if (energies) energies[0] = E;
+  int cnt = 0, head = 0, steps = 0;
+  qrctm_status result = QRCTM_OK;
+  for (int it = 0; it < n_steps; ++it) {
+    double o[3];
+    if ((e = lbfgs_direction(n, cnt, head, hist, c->opt_S, c->opt_Y, c->opt_g, c->opt_q,
+                             c->opt_p, c->opt_out, st)) != cudaSuccess ||
+        (e = read_out(o, 2)) != cudaSuccess)
+      return cuda_fail(c, e, "optimize direction");
+    if (!(o[0] < 0.0) && cnt > 0) {
+      cnt = 0;   // not a descent direction: drop the history, steepest descent
+      if ((e = lbfgs_direction(n, 0, head, hist, c->opt_S, c->opt_Y, c->opt_g, c->opt_q,
+                               c->opt_p, c->opt_out, st)) != cudaSuccess ||
+          (e = read_out(o, 2)) != cudaSuccess)
+        return cuda_fail(c, e, "optimize direction");
+    }
+    const double gp = o[0], pp = o[1];
+    if (!(pp > 0.0)) break;   // zero gradient
+    if (!std::isfinite(gp) || !std::isfinite(pp))
+      return set_err(c, QRCTM_ERR_NUMERIC, "non-finite search direction");
+    double alpha = cnt > 0 ? 1.0 : step0 / std::sqrt(pp);
+    bool ok = false;
+    double Et = 0.0;
+    for (int t = 0; t < max_ls; ++t) {
+      if ((e = lbfgs_trial(n, c->opt_x, alpha, c->opt_p, c->opt_xt, st)) != cudaSuccess)
+        return cuda_fail(c, e, "optimize trial");
+      if ((s = evaluate(c->opt_xt, t > 0, &Et)) != QRCTM_OK) return s;
+      if (Et <= E + c1 * alpha * gp) { ok = true; break; }
+      alpha *= 0.5;
+    }
+    if (!ok) {
+      result = set_err(c, QRCTM_ERR_NOT_CONVERGED, "line search found no decrease");
+      break;
+    }
+    if ((e = lbfgs_pair(n, c->opt_xt, c->opt_x, c->opt_gt, c->opt_g,
+                        c->opt_S + (size_t)head * n, c->opt_Y + (size_t)head * n, c->opt_out,
+                        st)) != cudaSuccess ||
+        (e = read_out(o, 3)) != cudaSuccess)
+      return cuda_fail(c, e, "optimize pair");
+    if (o[0] > 1e-10 * std::sqrt(o[1] * o[2])) {
+      head = (head + 1) % hist;
+      cnt = std::min(cnt + 1, hist);
+    }
+    if ((e = accept(true)) != cudaSuccess) return cuda_fail(c, e, "optimize");
+    E = Et;
+    ++steps;
+    if (energies) energies[steps] = E;
+    if (steps_out) *steps_out = steps;
+  }
+  if ((e = dcopy(A, c->opt_x, n)) != cudaSuccess) return cuda_fail(c, e, "optimize");
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "optimize");
+  return result;
 }
 
 int qrctm_grad_iterations(const qrctm_ctx* ctx) { return ctx ? ctx->grad_iters : 0; }

@@ -53,6 +53,13 @@ struct qrctm_ctx {
   size_t eig_work_doubles;
   int* eig_info;
   int* eig_idx;            // kept eigenvalue indices, by rank
+  // L-BFGS optimisation (qrctm_optimize): pair ring S, Y (opt_hist x n),
+  // accepted / trial points and gradients, direction, scratch, the
+  // environments of the accepted point and of the last evaluation
+  int opt_hist;
+  double *opt_S, *opt_Y, *opt_x, *opt_xt, *opt_g, *opt_gt, *opt_p, *opt_q, *opt_out;
+  double *opt_Cp, *opt_Tp, *opt_Cc, *opt_Tc;
+  bool grad_keep_env;      // an unrolled gradient leaves (C, T) after its k steps
   // split-precision contractions of the energy and adjoint passes
   bool mm_split;
   float* mm32;
@@ -123,6 +130,15 @@ cudaError_t absorb_fused(const float* X1, const float* Ak, const float* Ab, floa
 cudaError_t network_boundary(int b, const double* a, const double* v, double* C0, double* T0,
                              cudaStream_t s);
 cudaError_t network_traces(qrctm_ctx* c, const double* a_obs);
+
+// L-BFGS device helpers (optimize.cu), one block each
+cudaError_t lbfgs_direction(int n, int cnt, int head, int hist, const double* S, const double* Y,
+                            const double* g, double* q, double* p, double* out, cudaStream_t s);
+cudaError_t lbfgs_trial(int n, const double* x, double a, const double* p, double* xt,
+                        cudaStream_t s);
+cudaError_t lbfgs_pair(int n, const double* xt, const double* x, const double* gt,
+                       const double* g, double* s_out, double* y_out, double* out,
+                       cudaStream_t s);
 
 // Layout of the double-layer intermediate X2 and the enlarged corner read from
 // it.  An iPEPS double layer keeps X2[m][b][d_k][j_k][d_b][j_b] (the ket and

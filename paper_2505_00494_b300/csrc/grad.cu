@@ -557,6 +557,13 @@ cudaError_t energy_grad_run(qrctm_ctx* c, double J1, double J2, int mode, int k_
       std::swap(L.yT, L.y2T);
     }
     iters = K;
+    if (c->grad_keep_env) {
+      // the optimiser continues from the environment after the k steps
+      cudaMemcpyAsync(c->C, L.ckC + K * c2, sizeof(double) * c2, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(c->T, L.ckT + K * mc, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s);
+      c->iters += K;
+      c->spec_valid = false;
+    }
   }
   // project onto the C4v subspace
   if ((e = c4v_symmetrize(k.d, k.D, L.Abar, grad, s)) != cudaSuccess) return e;

@@ -92,3 +92,16 @@ def test_network_planning_host_only(q):
         assert q.lib.qrctm_workspace_bytes(ctypes.byref(bad)) == 0
     assert q.lib.qrctm_init_env_network(None, None, None, None, None) == 1
     assert q.lib.qrctm_network_observables(None, None, None, None) == 1
+
+
+def test_optimizer_planning_host_only(q):
+    base = q.lib.qrctm_workspace_bytes(ctypes.byref(cfg(q, D=2, chi=16, with_grad=1)))
+    with_opt = q.lib.qrctm_workspace_bytes(ctypes.byref(cfg(q, D=2, chi=16, with_grad=1,
+                                                           opt_history=10)))
+    # 2 x history x n pair vectors + 6 vectors + two environments
+    n = 2 * 16
+    assert with_opt >= base + (2 * 10 * n + 6 * n + 2 * (16 * 16 + 16 * 4 * 16)) * 8
+    for bad in (cfg(q, D=2, chi=16, opt_history=10), cfg(q, D=2, chi=16, with_grad=1, opt_history=33),
+                cfg(q, D=2, chi=16, with_grad=1, opt_history=-1)):
+        assert q.lib.qrctm_workspace_bytes(ctypes.byref(bad)) == 0
+    assert q.lib.qrctm_optimize(None, None, None, 1, None, None, None, None) == 1
