@@ -447,6 +447,148 @@ def bench_network(args, w, q, dist, world, rank, local):
     ctx.close()
 
 
+# k of the tracked steps per D in the paper's timing of optimisation steps
+# (Fig. 3(b): chi = 5 D^2, k = 10, 12, 14, 16, 20, 24 for D = 2..7)
+PAPER_K = {2: 10, 3: 12, 4: 14, 5: 16, 6: 20, 7: 24}
+
+
+def opt_step_rate(q, ctx, A, C, T, k, J2, steps, warmup, dist, local, grad):
+    """Optimisation steps/s: one step = the environment of the previous point
+    handed back in, two untracked QR-CTMRG steps, then the energy and its
+    gradient through k tracked steps (the unit of Fig. 3(b))."""
+    import torch
+
+    def one_step(i):
+        ctx.init_env(A, C, T)
+        ctx.step(2, want_delta=False)
+        ctx.energy_grad(1.0, J2, mode="unroll", k_unroll=k, grad=grad)
+
+    for i in range(warmup):
+        one_step(i)
+    torch.cuda.synchronize()
+    return timed_region(q, one_step, steps, dist, local)
+
+
+def bench_opt(args, q, dist, world, rank, local):
+    """Time per variational optimisation step (Automatic differentiation
+    paragraph, Fig. 3(b)): the paper's unit through the public API, and the
+    L-BFGS loop (qrctm_optimize) per accepted step."""
+    import torch
+    J2 = args.j2
+    if args.mode == "opt":
+        w = qi.WORKLOADS[args.workload]
+        cases = [(w["D"], w["chi"], PAPER_K.get(w["D"], 20), w)]
+    else:
+        cases = [(D, 5 * D * D, PAPER_K[D], dict(d=2, D=D, chi=5 * D * D, seed=0, decay=True,
+                                                 bias=0.0)) for D in range(2, 8)]
+    rows = []
+    for D, chi, k, w in cases:
+        d = w["d"]
+        X = torch.tensor(qi.raw_tensor(d, D, w["seed"], w["decay"], w["bias"]),
+                         dtype=torch.float64, device="cuda")
+        A = q.c4v_symmetrize(X, normalize=True)
+        ctx = q.QRCTM(d, D, chi, precision=args.precision, check_every=args.check_every,
+                      with_grad=True, with_nnn=J2 != 0, opt_history=10)
+        ctx.init_env(A)
+        converge(ctx, 1e-8, 2000, floor=args.precision == "split")
+        C, T, _ = ctx.get_env(spectrum=False)
+        grad = torch.empty_like(A)
+        steps = args.steps
+        ms, launches, clocks = opt_step_rate(q, ctx, A, C, T, k, J2, steps, args.warmup
+                                             if args.mode == "opt" else 1, dist, local, grad)
+        row = {"D": D, "chi": chi, "k": k, "ms_per_step": ms / steps,
+               "steps_per_s": job_rate(steps, world, ms), "gpu_launches": int(launches),
+               "clocks": clocks}
+        if args.mode == "opt" and not args.no_extras:
+            # the L-BFGS loop itself: accepted steps, evaluations, wall time
+            A2 = A.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            en, evals, failed = ctx.optimize(A2, args.opt_steps, J2=J2, k_unroll=k,
+                                             env_tol=1e-8 if args.precision == "fp64" else 1e-6)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            row["lbfgs"] = {"accepted_steps": len(en) - 1, "evaluations": evals,
+                            "wall_s": wall, "energies": [float(x) for x in en],
+                            "line_search_failed": bool(failed)}
+        rows.append(row)
+        ctx.close()
+        del ctx
+        torch.cuda.empty_cache()
+    head = rows[-1] if args.mode == "opt" else next(r for r in rows if r["D"] == 6)
+    if rank == 0:
+        line = {
+            "metric": (f"optimisation steps/s ({args.workload}, 2 untracked + k={head['k']} "
+                       "tracked QR-CTMRG steps, energy, gradient)" if args.mode == "opt" else
+                       "optimisation steps/s (d=2, D=6, chi=180, k=20; sweep D=2..7, chi=5D^2)"),
+            "value": head["steps_per_s"], "unit": "opt-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "tf32x3+f64", "data": "synthetic",
+            "config": {"workload": args.workload if args.mode == "opt" else "D=2..7, chi=5D^2",
+                       "precision": args.precision, "J2": J2, "gradient": "unrolled",
+                       "parallelism": f"replicas{world}"},
+            "roofline": None,
+            "gpu_launches": head["gpu_launches"],
+            "clocks": head["clocks"],
+            "sweep": rows,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def bench_chi_sweep(args, q, dist, world, rank, local):
+    """Large-chi evaluations (Results: chi_eval up to 600-700 at D = 7, 8):
+    iterations/s and the energy-per-site time at each chi, split precision."""
+    import torch
+    D, d = 8, 2
+    rows = []
+    X = torch.tensor(qi.raw_tensor(d, D, 0, True, 0.0), dtype=torch.float64, device="cuda")
+    A = q.c4v_symmetrize(X, normalize=True)
+    for chi in args.chis:
+        ctx = q.QRCTM(d, D, chi, precision=args.precision, check_every=args.check_every)
+        t0 = time.perf_counter()
+        ctx.init_env(A)
+        torch.cuda.synchronize()
+        init_s = time.perf_counter() - t0
+        ce = args.check_every
+
+        def one_step(i):
+            ctx.step(1, want_delta=(i % ce == ce - 1))
+
+        for i in range(2):
+            one_step(i)
+        torch.cuda.synchronize()
+        steps = max(ce, args.steps)
+        ms, launches, clocks = timed_region(q, one_step, steps, dist, local)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        E = ctx.energy(1.0, 0.0)
+        e_ms = 1e3 * (time.perf_counter() - t0)
+        rows.append({"chi": chi, "m": chi * D * D, "iter_per_s": job_rate(steps, world, ms),
+                     "ms_per_step": ms / steps, "init_s": init_s, "energy_ms": e_ms,
+                     "E_unconverged": E, "workspace_GB": ctx.workspace_bytes / 1e9,
+                     "clocks": clocks, "gpu_launches": int(launches)})
+        ctx.close()
+        del ctx
+        torch.cuda.empty_cache()
+    if rank == 0:
+        head = rows[-1]
+        line = {
+            "metric": f"QR-CTMRG iterations/s (d=2, D=8, chi={head['chi']}; chi sweep)",
+            "value": head["iter_per_s"], "unit": UNIT, "n_gpus": world,
+            "steps": max(args.check_every, args.steps),
+            "warmup": 2, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "tf32x3+f64", "data": "synthetic",
+            "config": {"workload": "d2_D8 chi sweep", "chis": args.chis,
+                       "precision": args.precision, "parallelism": f"replicas{world}"},
+            "roofline": None, "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
+            "sweep": rows,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args, w, rank):
     if rank != 0:
         return
@@ -490,6 +632,13 @@ def main():
                     help="skip time-to-convergence, dE vs FP64 and the energy gradient")
     ap.add_argument("--grad-tol", type=float, default=1e-6,
                     help="relative residual target of the implicit adjoint solve")
+    ap.add_argument("--mode", default="step", choices=["step", "opt", "opt-sweep", "chi-sweep"],
+                    help="step: CTMRG iterations (default); opt: optimisation steps on the "
+                         "workload; opt-sweep: D = 2..7 at chi = 5 D^2; chi-sweep: D = 8 at "
+                         "large chi")
+    ap.add_argument("--j2", type=float, default=0.0, help="J2/J1 of the optimisation modes")
+    ap.add_argument("--opt-steps", type=int, default=5, help="L-BFGS steps reported in opt mode")
+    ap.add_argument("--chis", type=int, nargs="+", default=[300, 400, 500, 600, 700])
     ap.add_argument("--conv-tol", type=float, default=0.0,
                     help="spectrum tolerance for time-to-converged (default 1e-10; the split path "
                          "stops earlier at its precision floor)")
@@ -502,7 +651,12 @@ def main():
         args.precision = "fp64"
         args.no_extras = True
     if args.steps <= 0:
-        args.steps = 5 if args.method == "eigen" else (20 if args.precision == "fp64" else 200)
+        if args.mode in ("opt", "opt-sweep"):
+            args.steps = 5 if args.mode == "opt" else 3
+        elif args.mode == "chi-sweep":
+            args.steps = 10
+        else:
+            args.steps = 5 if args.method == "eigen" else (20 if args.precision == "fp64" else 200)
     args.warmup = max(3, args.warmup)
 
     rank = int(os.environ.get("RANK", "0"))
@@ -530,6 +684,16 @@ def main():
     if dist is not None:
         dist.barrier()
     import paper_2505_00494_b300 as q
+    if args.mode in ("opt", "opt-sweep"):
+        bench_opt(args, q, dist, world, rank, local)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    if args.mode == "chi-sweep":
+        bench_chi_sweep(args, q, dist, world, rank, local)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     if network:
         bench_network(args, w, q, dist, world, rank, local)
         if dist is not None:
