@@ -165,8 +165,10 @@ __global__ void build_ut_kernel(const float* __restrict__ part, int ksplit, int 
 // x_i = b_i tau_i (= b_i / U_ii), then b_l -= U[l][i] x_i for l < i.  The
 // rows of U^T and tau are staged in shared memory (all eight warps of a CTA
 // use them) when they fit, else each row is loaded one step ahead.
-constexpr int kSolveMaxPerLane = 16;   // n <= 512
+// MAXQ values per lane: n <= 32 MAXQ (16 up to n = 512, 32 up to 1024).
+constexpr int kSolveMaxPerLane = 32;   // n <= 1024
 constexpr int kSolveSmemMaxN = 200;    // U^T staged in shared memory up to n = 200
+template <int MAXQ>
 __global__ void __launch_bounds__(256) q_solve_kernel(const float* __restrict__ UT, long long ldu,
                                                       const float* __restrict__ Vt,
                                                       long long ldv, const double* __restrict__ Tf,
@@ -183,9 +185,9 @@ __global__ void __launch_bounds__(256) q_solve_kernel(const float* __restrict__ 
   const int lane = threadIdx.x & 31;
   const int k = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (k >= n) return;
-  float b[kSolveMaxPerLane];   // b[q] holds entry i = lane + 32 q
+  float b[MAXQ];   // b[q] holds entry i = lane + 32 q
 #pragma unroll
-  for (int qq = 0; qq < kSolveMaxPerLane; ++qq) {
+  for (int qq = 0; qq < MAXQ; ++qq) {
     const int i = lane + 32 * qq;
     b[qq] = (i <= k && i < n) ? Vt[(long long)k * ldv + i] : 0.f;
   }
@@ -193,11 +195,11 @@ __global__ void __launch_bounds__(256) q_solve_kernel(const float* __restrict__ 
   for (int i = lane; i < n; i += 32) out[i] = 0.f;
   __syncwarp();
   const int nq = (k + 32) / 32;           // slots that can hold l < i <= k
-  float u[kSolveMaxPerLane], un[kSolveMaxPerLane];
+  float u[MAXQ], un[MAXQ];
   auto load_row = [&](int i, float* dst) {
     const float* src = staged ? us + (long long)i * n : UT + (long long)i * ldu;
 #pragma unroll
-    for (int qq = 0; qq < kSolveMaxPerLane; ++qq) {
+    for (int qq = 0; qq < MAXQ; ++qq) {
       const int l = lane + 32 * qq;
       dst[qq] = (qq < nq && l < i) ? src[l] : 0.f;
     }
@@ -205,17 +207,17 @@ __global__ void __launch_bounds__(256) q_solve_kernel(const float* __restrict__ 
   load_row(k, un);
   for (int i = k; i >= 0; --i) {
 #pragma unroll
-    for (int qq = 0; qq < kSolveMaxPerLane; ++qq) u[qq] = un[qq];
+    for (int qq = 0; qq < MAXQ; ++qq) u[qq] = un[qq];
     if (i > 0) load_row(i - 1, un);       // next row while this one is applied
     const int owner = i & 31, slot = i >> 5;
     float bi = 0.f;
 #pragma unroll
-    for (int qq = 0; qq < kSolveMaxPerLane; ++qq)
+    for (int qq = 0; qq < MAXQ; ++qq)
       if (qq == slot) bi = b[qq];
     const float xi = __shfl_sync(0xffffffffu, bi, owner) * taus[i];
     if (lane == 0) out[i] = xi;
 #pragma unroll
-    for (int qq = 0; qq < kSolveMaxPerLane; ++qq) b[qq] = fmaf(-u[qq], xi, b[qq]);
+    for (int qq = 0; qq < MAXQ; ++qq) b[qq] = fmaf(-u[qq], xi, b[qq]);
   }
 }
 
@@ -334,12 +336,16 @@ cudaError_t householder_qr_split(int m, int n, const double* M, double* R, const
     const size_t qsm = sizeof(float) * (((n + 3) & ~3) + (n <= kSolveSmemMaxN ? (size_t)n * n : 0));
     static bool qattr = false;
     if (!qattr) {
-      cudaFuncSetAttribute(q_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      // only n <= 200 (the 16-slot variant) stages U^T in shared memory
+      cudaFuncSetAttribute(q_solve_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(sizeof(float) * (kSolveSmemMaxN * kSolveSmemMaxN +
                                                   32 * kSolveMaxPerLane)));
       qattr = true;
     }
-    q_solve_kernel<<<(unsigned)((n + 7) / 8), 256, qsm, s>>>(UT, ldv, Vt32, ldv, w.Tf, n, Wt);
+    if (n <= 32 * 16)
+      q_solve_kernel<16><<<(unsigned)((n + 7) / 8), 256, qsm, s>>>(UT, ldv, Vt32, ldv, w.Tf, n, Wt);
+    else
+      q_solve_kernel<32><<<(unsigned)((n + 7) / 8), 256, qsm, s>>>(UT, ldv, Vt32, ldv, w.Tf, n, Wt);
     note_launch();
     const long long totq = (long long)m * n;
     init_q32_kernel<<<(unsigned)std::min<long long>((totq + 255) / 256, 8192), 256, 0, s>>>(

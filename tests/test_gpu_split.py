@@ -43,6 +43,27 @@ def test_split_single_step(q, D, chi, seed):
     assert np.abs(Tg - Tn).max() < 2e-5 * np.abs(Tn).max()
 
 
+def test_split_single_step_wide_qr(q):
+    # chi = 520 > 512: the triangular solve forming Q keeps 32 values per
+    # lane.  C = I + small symmetric and a random T make the reduced corner a
+    # random 4 chi x chi matrix (condition ~3), so Q is well determined and
+    # one step compares entry by entry.
+    D, chi = 2, 520
+    rng = np.random.default_rng(11)
+    A = o.normalized_input(qi.raw_tensor(2, D, 7))
+    E = rng.standard_normal((chi, chi))
+    C, T = o.sym_norm(np.eye(chi) + 0.05 * (E + E.T) / np.sqrt(chi),
+                      rng.standard_normal((chi, D * D, chi)))
+    Cn, Tn = o.qr_step(C, T, A)
+    ctx = q.QRCTM(2, D, chi, precision="split")
+    ctx.init_env(cuda(A), cuda(C), cuda(T))
+    ctx.step(1, want_delta=False)
+    Cg, Tg, _ = ctx.get_env(spectrum=False)
+    Cg, Tg = Cg.cpu().numpy(), Tg.cpu().numpy()
+    assert np.abs(Cg - Cn).max() < 2e-5 * np.abs(Cn).max()
+    assert np.abs(Tg - Tn).max() < 2e-5 * np.abs(Tn).max()
+
+
 @pytest.mark.parametrize("D,chi,seed,decay", [(2, 16, 0, False), (3, 27, 1, True)])
 def test_split_converged_energy(q, D, chi, seed, decay):
     A = o.normalized_input(qi.raw_tensor(2, D, seed, decay))
