@@ -287,7 +287,8 @@ qrctm_status qrctm_c4v_symmetrize(int d, int D, const double* X, double* Y, int 
                                   void* workspace, size_t bytes, void* stream);
 
 /* Unpivoted Householder QR with diag(R) >= 0 (QR-CTMRG paragraph) of a
- * column-major m x n device matrix M (m >= n >= 1).  Q: m x n column-major,
+ * column-major m x n device matrix M (m >= n >= 1, n <= 2048; otherwise
+ * QRCTM_ERR_INVALID_ARG and a workspace size of 0).  Q: m x n column-major,
  * R: n x n row-major (upper triangular).  workspace: 256-byte aligned,
  * qrctm_qr_workspace_bytes(m, n) bytes, zero-filled before its first use
  * (the call leaves its control words zero again).  Synchronises. */

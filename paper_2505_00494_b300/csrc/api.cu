@@ -854,13 +854,13 @@ qrctm_status qrctm_gemm_tf32x3(int M, int N, int K, const float* A, long long ld
 }
 
 size_t qrctm_qr_workspace_bytes(int m, int n) {
-  if (m < n || n < 1) return 0;
+  if (m < n || n < 1 || n > 2048) return 0;
   return qr_work_bytes(m, n);
 }
 
 qrctm_status qrctm_householder_qr(int m, int n, const double* M, double* Q, double* R,
                                   void* workspace, size_t bytes, void* stream) {
-  if (m < n || n < 1 || !M || !Q || !R || !workspace) return QRCTM_ERR_INVALID_ARG;
+  if (m < n || n < 1 || n > 2048 || !M || !Q || !R || !workspace) return QRCTM_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return QRCTM_ERR_INVALID_ARG;
   if (bytes < qrctm_qr_workspace_bytes(m, n)) return QRCTM_ERR_WORKSPACE;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

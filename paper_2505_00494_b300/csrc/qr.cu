@@ -26,9 +26,9 @@ constexpr size_t kPanelTileMax = 160 * 1024;   // shared-memory panel tile limit
 
 __host__ __device__ inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
-// FP64 reciprocal and square root by Newton's iteration from an FP32 seed
-// (quadratic convergence: 24 -> 48 -> 96 bits), avoiding the long-latency
-// IEEE double-precision divide and square-root sequences on the scalar path.
+// FP64 reciprocal by Newton's iteration from an FP32 seed (quadratic
+// convergence: 24 -> 48 -> 96 bits), avoiding the long-latency IEEE
+// double-precision divide sequence on the scalar path.
 __device__ __forceinline__ double rcp_nr(double x) {
   const double ax = fabs(x);
   if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;   // outside the FP32 seed range
@@ -36,16 +36,6 @@ __device__ __forceinline__ double rcp_nr(double x) {
   r = fma(r, fma(-x, r, 1.0), r);
   r = fma(r, fma(-x, r, 1.0), r);
   return r;
-}
-__device__ __forceinline__ double sqrt_nr(double a) {
-  if (!(a > 1e-30 && a < 1e30)) return sqrt(a);   // zero, NaN or outside the seed range
-  // y ~ 1/sqrt(a); two Newton steps y <- y (3 - a y^2) / 2, then s = a y and
-  // one correction s <- s + y (a - s^2) / 2
-  double y = static_cast<double>(rsqrtf(static_cast<float>(a)));
-  y = y * fma(-0.5 * a * y, y, 1.5);
-  y = y * fma(-0.5 * a * y, y, 1.5);
-  double sq = a * y;
-  return fma(0.5 * y, fma(-sq, sq, a), sq);
 }
 
 // Panel factorisation.  With TILE, each CTA keeps its block of panel rows
@@ -96,6 +86,47 @@ __device__ __forceinline__ int ld_dsmem_s32(const int* local, unsigned rank) {
   return v;
 }
 
+__device__ __forceinline__ void st_dsmem_f64(double* local, unsigned rank, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(dsmem_addr(local, rank)), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_dsmem_s32(int* local, unsigned rank, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(dsmem_addr(local, rank)), "r"(v) : "memory");
+}
+
+// 1/sqrt(a) in FP64 by two Newton steps y <- y (3/2 - a y^2 / 2) from the
+// FP32 estimate (24 -> 48 -> 96 bits), for a inside the FP32 range.
+__device__ __forceinline__ double rsqrt_nr(double a) {
+  if (!(a > 1e-30 && a < 1e30)) return 1.0 / sqrt(a);
+  const double ha = 0.5 * a;
+  double y = static_cast<double>(rsqrtf(static_cast<float>(a)));
+  y = y * fma(-ha, y * y, 1.5);
+  y = y * fma(-ha, y * y, 1.5);
+  return y;
+}
+
+// Reflector scalars of a column with pivot value x0 and sigma = sum_{i>c}
+// x_i^2 > 0: mu = sqrt(x0^2 + sigma) (returned as rmu = 1/mu and mu),
+// w = x0 - mu (= -sigma / (x0 + mu) for x0 > 0, no cancellation) and
+// inv_w = 1/w.  tau = -w/mu follows when asked for.  The same code runs
+// inside the column loop and after it, so both see identical values.
+__device__ __forceinline__ void reflector(double x0, double sigma, double* rmu, double* mu,
+                                          double* inv_w, double* tau) {
+  const double a = fma(x0, x0, sigma);
+  const double y = rsqrt_nr(a);
+  const double m = a * y;
+  *rmu = y;
+  *mu = m;
+  if (x0 > 0.0) {
+    const double xm = x0 + m;
+    *inv_w = -xm * rcp_nr(sigma);
+    if (tau) *tau = sigma * y * rcp_nr(xm);       // -w/mu with w = -sigma/(x0 + mu)
+  } else {
+    const double w = x0 - m;
+    *inv_w = rcp_nr(w);
+    if (tau) *tau = -w * y;
+  }
+}
+
 // Panel factorisation.  With TILE, each CTA keeps its block of panel rows
 // (rows_per_cta x nb doubles) in shared memory for the whole factorisation, so
 // that a column step touches global memory only for the cross-CTA partial
@@ -104,23 +135,31 @@ __device__ __forceinline__ int ld_dsmem_s32(const int* local, unsigned rank) {
 // run on W in global memory.
 //
 // Column step j (c = j0 + j the pivot row), after all CTAs have published the
-// partial sums of column j (slot 0: sum_{i>c} x_i^2, slot t: sum_{i>c} x_i
-// y_{t,i} for column j + t) and the owner of row c has published that row:
-//   sigma = sum of slot 0, mu = sqrt(x_0^2 + sigma),
-//   w = x_0 - mu  (= -sigma / (x_0 + mu) for x_0 > 0),   tau = -w / mu,
-//   v = x / w (v_0 = 1),   y_t -= tau (y_{t,0} + s_t / w) v,   R_cc = mu.
-// The same pass over a CTA's rows that applies reflector j also accumulates
-// the partial sums of column j + 1 (the updated value of column j + 1 on a
-// row reaches the other lanes by a warp shuffle), so a column costs one
-// round of the arrival counter and four block barriers.
+// partial sums of column j (slot 0: sigma = sum_{i>c} x_i^2, slot t:
+// s_t = sum_{i>c} x_i y_{t,i} for column j + t) and the owner of row c has
+// published that row (x_0 and the y_{t,0}):
+//   mu = sqrt(x_0^2 + sigma), w = x_0 - mu, tau = -w / mu,
+//   v = x / w (v_0 = 1),   y_t -= tau (y_{t,0} + s_t / w) v,   R_cc = mu,
+//   R_{c,j+t} = y_{t,0} - tau (y_{t,0} + s_t / w).
+// Since tau / w = -1/mu, the rows below c need only 1/mu and 1/w:
+//   v_i = x_i / w,   y_{t,i} += (y_{t,0} + s_t / w) / mu * x_i,
+// so the scalar chain between the reduction and the row pass is one
+// reciprocal square root and one reciprocal; tau and the R entries of the
+// pivot rows are formed once after the column loop, from the saved sums
+// (sigma_j, s_{t,j}) and the pivot rows, which no later column touches.
+// The pass over a CTA's rows that applies reflector j also accumulates the
+// partial sums of column j + 1 (the updated value of column j + 1 on a row
+// reaches the other lanes by a warp shuffle), two rows at a time, so a
+// column costs one round of the arrival counter and three block barriers.
 //
-// CL > 1: the CTAs form clusters of CL; a cluster first adds its CTAs'
-// partial sums over distributed shared memory and only its rank-0 CTA
-// publishes and arrives, which divides the partial sums every CTA reads (and
+// CL > 1: the CTAs form clusters of CL; each CTA stores its partial sums
+// into the rank-0 CTA's shared memory (and its stop flag into every CTA's),
+// one cluster barrier makes them visible, and only rank 0 adds them,
+// publishes and arrives.  This divides the partial sums every CTA reads (and
 // the FP64 adds on B300's narrow FP64 pipe) and the global arrivals by CL at
 // the price of one cluster barrier per column.  A CTA whose wait gives up
 // still reaches that barrier; the cluster then stops together.
-template <bool TILE, int CL>
+template <bool TILE, int CL, bool ATOM>
 __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
                                                       double* __restrict__ V,
                                                       double* __restrict__ tau_out,
@@ -131,6 +170,8 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
                                                       const float* __restrict__ src32,
                                                       float* __restrict__ V32, long long ldv) {
   constexpr bool CLU = CL > 1;
+  constexpr int CLA = CLU ? CL : 1;
+  static_assert(!(ATOM && CLU), "the accumulating exchange runs without clusters");
   if constexpr (CLU) {
     // the distributed-shared-memory exchange needs exactly CL CTAs per
     // cluster; any other launch shape reports an error and touches nothing
@@ -152,11 +193,12 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
   double* rowb = part + 2 * (size_t)PMAX * NB;
   __shared__ double red[8][NB];
   __shared__ double coef_s[NB];   // per lane: new y_t = y_t + coef_s[t] x on rows below c
-  __shared__ double rcoef_s[NB];  // per lane: R_{c,j+t} = y_{t,0} - rcoef_s[t]
-  __shared__ double sc[4];
+  __shared__ double ssum[NB][NB]; // column j: sigma (slot 0) and s_t (slot t)
   __shared__ double tau_s[NB];
-  __shared__ double cpart[2][NB];  // this CTA's partial sums (CL > 1)
-  __shared__ int c_abort[2];       // this CTA gave up waiting (CL > 1), by column parity
+  __shared__ double iw_s[NB];     // 1/w of column j (R entries after the loop)
+  __shared__ double x0_s[NB];     // pivot value x_0 of column j as published
+  __shared__ double cpart[2][CLA][NB];   // partial sums of the cluster's CTAs (rank 0's copy)
+  __shared__ int c_abort[2][CLA];        // stop flags of the cluster's CTAs, by column parity
   __shared__ int s_ok;
   extern __shared__ double tile[];                 // [rows][NB + 1]
   // element (global row i, panel column jc)
@@ -168,10 +210,20 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     return ((red[0][t] + red[1][t]) + (red[2][t] + red[3][t])) +
            ((red[4][t] + red[5][t]) + (red[6][t] + red[7][t]));
   };
-  // publish the partial sums held by warp 0 (value v in lane t = slot t) for
-  // the column with parity buf; returns false when the cluster must stop
-  auto publish = [&](int buf, double v, bool aborted) -> bool {
-    if constexpr (!CLU) {
+  // publish the partial sums held by warp 0 (value v in lane t = slot t,
+  // nslots of them) for panel column col with parity buf; returns false when
+  // the cluster must stop
+  auto publish = [&](int col, int buf, double v, bool aborted, int nslots) -> bool {
+    if constexpr (ATOM) {
+      (void)buf; (void)aborted;
+      if (wrp == 0) {
+        if (lane < nslots) atomicAdd(part + ((size_t)j0 + col) * NB + lane, v);
+        __syncwarp();
+        if (lane == 0) grid_arrive(bar);
+      }
+      return true;
+    } else if constexpr (!CLU) {
+      (void)col; (void)nslots;
       if (wrp == 0) {
         psum[((size_t)buf * NG + b) * NB + lane] = v;
         __syncwarp();
@@ -179,25 +231,24 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
       }
       return true;
     } else {
-      if (wrp == 0) cpart[buf][lane] = v;
-      if (threadIdx.x == 0) c_abort[buf] = aborted ? 1 : 0;
+      (void)col; (void)nslots;
+      if (wrp == 0) st_dsmem_f64(&cpart[buf][crank][lane], 0u, v);
+      if (threadIdx.x < (unsigned)CL)
+        st_dsmem_s32(&c_abort[buf][crank], threadIdx.x, aborted ? 1 : 0);
       cluster_sync_all();
       // the leader publishes at once (after an abort the numbers are not
       // used: every CTA stops below, with the error word already set)
       if (crank == 0 && wrp == 0) {
-        double p[CL];
+        double acc = cpart[buf][0][lane];
 #pragma unroll
-        for (int q = 0; q < CL; ++q) p[q] = ld_dsmem_f64(&cpart[buf][lane], (unsigned)q);
-        double acc = p[0];
-#pragma unroll
-        for (int q = 1; q < CL; ++q) acc += p[q];
+        for (int q = 1; q < CL; ++q) acc += cpart[buf][q][lane];
         psum[((size_t)buf * NG + grp) * NB + lane] = acc;
         __syncwarp();
         if (lane == 0) grid_arrive(bar);
       }
       int any = 0;
 #pragma unroll
-      for (int q = 0; q < CL; ++q) any |= ld_dsmem_s32(&c_abort[buf], (unsigned)q);
+      for (int q = 0; q < CL; ++q) any |= c_abort[buf][q];
       return any == 0;
     }
   };
@@ -223,10 +274,10 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     red[wrp][lane] = acc;
     if (c >= r_begin && c < r_end && (int)threadIdx.x < nb) rowb[threadIdx.x] = at(c, threadIdx.x);
     __syncthreads();
-    stop = !publish(0, (wrp == 0) ? sum8(lane) : 0.0, false);
+    stop = !publish(0, 0, (wrp == 0) ? sum8(lane) : 0.0, false, nb);
   }
 
-  int j = 0;
+  int j = 0, done = 0;
   for (; j < nb && !stop; ++j) {
     const int buf = j & 1;
     const long long c = (long long)j0 + j;
@@ -238,12 +289,16 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     if constexpr (!CLU) {
       if (!ok) break;
     }
-    double acc = 0.0;
+    double acc = 0.0, acc2 = 0.0;
     if (ok) {
       // pivot row (x_0 and the y_{t,0}) loaded together with the partial sums
       const double y0 = (wrp == 0 && lane <= nrem) ? __ldcg(rowb + buf * NB + lane) : 0.0;
-      // cross-unit reduction (L2 reads): lane = slot, the 8 warps take every 8th unit
-      {
+      // ATOM: the sums of every CTA were added into this column's slots
+      double st_acc = 0.0;
+      if constexpr (ATOM) {
+        if (wrp == 0 && lane <= nrem) st_acc = __ldcg(part + ((size_t)j0 + j) * NB + lane);
+      } else {
+        // cross-unit reduction (L2 reads): lane = slot, the 8 warps take every 8th unit
         double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
         if (lane <= nrem) {
           const double* ps = psum + (size_t)buf * NG * NB + lane;
@@ -257,77 +312,110 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
           for (; q < NG; q += 8) s0 += __ldcg(ps + (size_t)q * NB);
         }
         red[wrp][lane] = (s0 + s1) + (s2 + s3);
+        __syncthreads();
       }
-      __syncthreads();
       if (wrp == 0) {
-        const double st = sum8(lane);                      // sigma (lane 0), s_t (lane t)
-        double tau = 0.0, inv_w = 0.0, mu = 0.0;
-        if (lane == 0) {
-          const double x0 = y0, sigma = st;
-          mu = sqrt_nr(fma(x0, x0, sigma));
-          if (sigma == 0.0) {
-            tau = (x0 < 0.0) ? 2.0 : 0.0;                  // v = e_1
-            inv_w = 0.0;
-          } else if (x0 <= 0.0) {
-            const double w = x0 - mu;
-            tau = -w * rcp_nr(mu);
-            inv_w = rcp_nr(w);
-          } else {
-            const double xm = x0 + mu;
-            const double w = -sigma * rcp_nr(xm);
-            tau = -w * rcp_nr(mu);
-            inv_w = -xm * rcp_nr(sigma);
-          }
-          if (!(mu == mu) || isinf(mu)) atomicOr(err, ERRF_NUMERIC);
-          sc[0] = tau; sc[1] = inv_w; sc[2] = mu;
-          tau_s[j] = tau;
+        const double st = ATOM ? st_acc : sum8(lane);      // sigma (lane 0), s_t (lane t)
+        ssum[j][lane] = st;
+        if (lane == 0) x0_s[j] = y0;
+        double rmu = 0.0, inv_w = 0.0;
+        if (lane == 0 && st != 0.0) {
+          double mu;
+          reflector(y0, st, &rmu, &mu, &inv_w, nullptr);
+          if (!(rmu == rmu) || isinf(rmu) || !(inv_w == inv_w) || isinf(inv_w))
+            atomicOr(err, ERRF_NUMERIC);
         }
-        tau = __shfl_sync(0xffffffffu, tau, 0);
+        // sigma = 0: x is zero below c, v = e_1 (tau = 0 or 2); the rows
+        // below c are left as they are (multipliers 0)
+        rmu = __shfl_sync(0xffffffffu, rmu, 0);
         inv_w = __shfl_sync(0xffffffffu, inv_w, 0);
-        // row-update multiplier of lane t: new y_t = y_t + mult_t x  (lane 0: v = x / w)
-        double mult = 0.0, rc = 0.0;
-        if (lane == 0) {
-          mult = inv_w;
-        } else if (lane <= nrem) {
-          rc = tau * fma(st, inv_w, y0);
-          mult = -rc * inv_w;
-        }
+        double mult = 0.0;
+        if (lane == 0) mult = inv_w;
+        else if (lane <= nrem) mult = rmu * fma(st, inv_w, y0);
         coef_s[lane] = mult;
-        rcoef_s[lane] = rc;
       }
       __syncthreads();
       const double mult = coef_s[lane];
       const bool active = (lane <= nrem);
-      for (long long i = std::max<long long>(r_begin, c + 1) + wrp; i < r_end; i += 8) {
+      const bool upd = (lane >= 1 && active);
+      long long i = std::max<long long>(r_begin, c + 1) + wrp;
+      // two rows per pass (independent FMA chains), then the odd one
+      for (; i + 8 < r_end; i += 16) {
+        const double x1 = at(i, j), x2 = at(i + 8, j);
+        const double o1 = upd ? at(i, j + lane) : 0.0;
+        const double o2 = upd ? at(i + 8, j + lane) : 0.0;
+        const double n1 = fma(mult, x1, o1), n2 = fma(mult, x2, o2);
+        __syncwarp();
+        if (active) {
+          at(i, j + lane) = n1;
+          at(i + 8, j + lane) = n2;
+        }
+        if (!last) {
+          const double xn1 = __shfl_sync(0xffffffffu, n1, 1);   // updated column j + 1
+          const double xn2 = __shfl_sync(0xffffffffu, n2, 1);
+          if (upd) {
+            if (i > c + 1) acc = fma(xn1, n1, acc);
+            else rowb[(buf ^ 1) * NB + lane - 1] = n1;       // pivot row of column j + 1
+            acc2 = fma(xn2, n2, acc2);
+          }
+        }
+      }
+      for (; i < r_end; i += 8) {
         const double x = at(i, j);
-        const double old = (lane >= 1 && active) ? at(i, j + lane) : 0.0;
+        const double old = upd ? at(i, j + lane) : 0.0;
         const double nv = fma(mult, x, old);
         __syncwarp();
         if (active) at(i, j + lane) = nv;
         if (!last) {
-          const double xn = __shfl_sync(0xffffffffu, nv, 1);   // updated column j + 1
-          if (lane >= 1 && active) {
+          const double xn = __shfl_sync(0xffffffffu, nv, 1);
+          if (upd) {
             if (i > c + 1) acc = fma(xn, nv, acc);
-            else rowb[(buf ^ 1) * NB + lane - 1] = nv;       // pivot row of column j + 1
+            else rowb[(buf ^ 1) * NB + lane - 1] = nv;
           }
         }
       }
-      // row c itself: the R entries (R_cc = mu; y_{t,0} - tau (y_{t,0} + s_t / w))
-      if (wrp == 0 && c >= r_begin && c < r_end) {
-        if (lane == 0) at(c, j) = sc[2];
-        else if (active) at(c, j + lane) -= rcoef_s[lane];
-      }
+      done = j + 1;
     }
     if (last) break;
-    red[wrp][lane] = acc;                                  // slot lane - 1 of column j + 1
+    red[wrp][lane] = acc + acc2;                           // slot lane - 1 of column j + 1
     __syncthreads();
     const double v = (wrp == 0 && lane < nrem) ? sum8(lane + 1) : 0.0;
-    if (!publish(buf ^ 1, v, !ok)) break;
-    if constexpr (!CLU) {
-      (void)0;
-    }
+    if (!publish(j + 1, buf ^ 1, v, !ok, nrem)) break;
   }
   __syncthreads();
+  // tau and the pivot rows (R_cc = mu, R_{c,j+t} = y_{t,0} - tau (y_{t,0} +
+  // s_t / w)) of the factored columns: one lane per column, from the saved
+  // sums and the pivot rows (unchanged since their column step).  CTA 0 needs
+  // tau of every column; a CTA holding pivot rows needs its own columns.
+  const bool has_pivots = r_begin < (long long)j0 + done;
+  if ((b == 0 || has_pivots) && wrp == 0 && lane < done) {
+    const long long c = (long long)j0 + lane;
+    const bool own = c >= r_begin && c < r_end;
+    const double sigma = ssum[lane][0];
+    const double x0 = x0_s[lane];        // = at(c, lane) on the owner of row c
+    double tau = 0.0, iw = 0.0, mu = fabs(x0);
+    if (sigma != 0.0) {
+      double rmu;
+      reflector(x0, sigma, &rmu, &mu, &iw, &tau);
+    } else {
+      tau = (x0 < 0.0) ? 2.0 : 0.0;
+    }
+    tau_s[lane] = tau;
+    iw_s[lane] = iw;
+    if (own) at(c, lane) = mu;
+  }
+  __syncthreads();
+  if (has_pivots) {
+    for (int e = threadIdx.x; e < done * NB; e += PT) {
+      const int jj = e / NB, t = e % NB;
+      const long long c = (long long)j0 + jj;
+      if (t >= 1 && jj + t < nb && c >= r_begin && c < r_end) {
+        const double y0 = at(c, jj + t);
+        at(c, jj + t) = y0 - tau_s[jj] * fma(ssum[jj][t], iw_s[jj], y0);
+      }
+    }
+    __syncthreads();
+  }
   // write back: panel rows of W (R above/on the diagonal, reflectors below)
   // and the explicit reflectors V (zero above the unit diagonal); optionally
   // FP32 copies of V for the tensor-core WY products: X32[c][i] and V32[c][i]
@@ -425,82 +513,38 @@ cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t 
   float* v32 = V32;
   const float* s32 = src32;
   long long ldx_ = ldx, ldv_ = ldv;
+  // one accumulator row of NB doubles per column of the whole factorisation
+  if (j0 + nbj > 2 * PMAX) return cudaErrorInvalidValue;
   cudaError_t e = cudaErrorUnknown;
-  bool launched = false;
   if (w.hook) w.hook(w.hook_user, 1);
-  // clusters of 4 CTAs where the device can place them and the grid is large
-  // enough; else a cooperative launch with one CTA per publisher
-  static int cl_state = -1, cl_max = 0;   // -1 unknown, 0 unavailable, 1 available
-  if (P >= 8 && cl_state != 0) {
-    auto kern = qr_panel_kernel<true, 4>;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 4;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(PT);
-    cfg.stream = s;
-    cfg.attrs = at;
-    if (cl_state < 0) {
-      cl_state = 0;
-      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kPanelTileMax) == cudaSuccess) {
-        cfg.gridDim = dim3(4);
-        cfg.dynamicSmemBytes = kPanelTileMax;
-        cfg.numAttrs = 1;
-        int nc = 0;
-        if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) == cudaSuccess && nc >= 2) {
-          cl_state = 1;
-          cl_max = nc;
-        }
-      }
-      cudaGetLastError();
-    }
-    if (cl_state == 1) {
-      const int Pc = std::min((P / 4) * 4, 4 * cl_max);
-      int rpc = (mr + Pc - 1) / Pc;
-      const size_t tile = sizeof(double) * (size_t)rpc * (NB + 1);
-      if (tile <= kPanelTileMax) {
-        void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc, &x32, &ldx_,
-                        &vt32, &s32, &v32, &ldv_};
-        // every CTA must be resident at once: the grid is capped at the
-        // occupancy query's cluster count (waits are bounded regardless)
-        cfg.gridDim = dim3(Pc);
-        cfg.dynamicSmemBytes = tile;
-        cfg.numAttrs = 1;
-        e = cudaLaunchKernelExC(&cfg, (const void*)kern, args);
-        if (e == cudaSuccess) {
-          launched = true;
-        } else {
-          cudaGetLastError();   // the device refused the cooperative cluster launch
-          cl_state = 0;
-        }
-      }
-    }
+  // the first panel of a factorisation clears every column's accumulator
+  if (j0 == 0 &&
+      (e = cudaMemsetAsync(part, 0, sizeof(double) * 2 * (size_t)PMAX * NB, s)) != cudaSuccess) {
+    if (w.hook) w.hook(w.hook_user, 0);
+    return e;
   }
-  if (!launched) {
-    int rpc = (mr + P - 1) / P;
-    void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc, &x32, &ldx_, &vt32,
-                    &s32, &v32, &ldv_};
-    const size_t tile = sizeof(double) * (size_t)rpc * (NB + 1);
-    if (src32 != nullptr && tile > kPanelTileMax) {
-      if (w.hook) w.hook(w.hook_user, 0);
-      return cudaErrorInvalidValue;   // an FP32 source needs the tiled path
+  // cooperative launch, one CTA per SM at most: every CTA adds its partial
+  // sums into the column's accumulator and arrives on the counter
+  int rpc = (mr + P - 1) / P;
+  void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc, &x32, &ldx_, &vt32,
+                  &s32, &v32, &ldv_};
+  const size_t tile = sizeof(double) * (size_t)rpc * (NB + 1);
+  if (src32 != nullptr && tile > kPanelTileMax) {
+    if (w.hook) w.hook(w.hook_user, 0);
+    return cudaErrorInvalidValue;   // an FP32 source needs the tiled path
+  }
+  if (tile <= kPanelTileMax) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(qr_panel_kernel<true, 1, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelTileMax);
+      attr = true;
     }
-    if (tile <= kPanelTileMax) {
-      static bool attr = false;
-      if (!attr) {
-        cudaFuncSetAttribute(qr_panel_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kPanelTileMax);
-        attr = true;
-      }
-      e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<true, 1>, dim3(P), dim3(PT),
-                                      args, tile, s);
-    } else {
-      e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<false, 1>, dim3(P), dim3(PT),
-                                      args, 0, s);
-    }
+    e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<true, 1, true>, dim3(P),
+                                    dim3(PT), args, tile, s);
+  } else {
+    e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<false, 1, true>, dim3(P),
+                                    dim3(PT), args, 0, s);
   }
   if (w.hook) w.hook(w.hook_user, 0);
   if (e != cudaSuccess) return e;

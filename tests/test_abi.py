@@ -105,3 +105,9 @@ def test_optimizer_planning_host_only(q):
                 cfg(q, D=2, chi=16, with_grad=1, opt_history=-1)):
         assert q.lib.qrctm_workspace_bytes(ctypes.byref(bad)) == 0
     assert q.lib.qrctm_optimize(None, None, None, 1, None, None, None, None) == 1
+
+
+def test_qr_width_limit_host_only(q):
+    # one accumulator row per column of the factorisation: n <= 2048
+    assert q.lib.qrctm_qr_workspace_bytes(4096, 2048) > 0
+    assert q.lib.qrctm_qr_workspace_bytes(4096, 2049) == 0
