@@ -3,7 +3,7 @@
 //
 // Layout: the m x n input is column-major (each column of ct contiguous).
 // Panels of nb <= 32 columns are factored by one cooperative kernel spread
-// over the whole GPU (one bounded grid barrier per column, FP64 reductions);
+// over the whole GPU (one bounded arrival round per column, FP64 sums);
 // the trailing matrix and the explicit Q are updated with the compact WY
 // form H_1...H_nb = I - V T V^T through the contraction engine.
 //
@@ -36,61 +36,6 @@ __device__ __forceinline__ double rcp_nr(double x) {
   r = fma(r, fma(-x, r, 1.0), r);
   r = fma(r, fma(-x, r, 1.0), r);
   return r;
-}
-
-// Panel factorisation.  With TILE, each CTA keeps its block of panel rows
-// (rows_per_cta x nb doubles) in shared memory for the whole factorisation, so
-// that a column step touches global memory only for the cross-CTA partial
-// sums and the published pivot row; the tile is written back (R entries,
-// reflectors) at the end.  Without TILE (very tall panels) the same steps
-// run on W in global memory.
-//
-// Column step j (c = j0 + j the pivot row), after all CTAs have published the
-// partial sums of column j (slot 0: sum_{i>c} x_i^2, slot t: sum_{i>c} x_i
-// y_{t,i} for column j + t) and the owner of row c has published that row:
-//   sigma = sum of slot 0, mu = sqrt(x_0^2 + sigma),
-//   w = x_0 - mu  (= -sigma / (x_0 + mu) for x_0 > 0),   tau = -w / mu,
-//   v = x / w (v_0 = 1),   y_t -= tau (y_{t,0} + s_t / w) v,   R_cc = mu.
-// The same pass over a CTA's rows that applies reflector j also accumulates
-// the partial sums of column j + 1 (the updated value of column j + 1 on a
-// row reaches the other lanes by a warp shuffle), so a column costs one
-// round of the arrival counter and four block barriers.
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n"
-               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ unsigned cluster_rank() {
-  unsigned r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ unsigned cluster_size() {
-  unsigned r;
-  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
-  return r;
-}
-template <typename T>
-__device__ __forceinline__ unsigned dsmem_addr(const T* local, unsigned rank) {
-  unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(local)), ra;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
-  return ra;
-}
-__device__ __forceinline__ double ld_dsmem_f64(const double* local, unsigned rank) {
-  double v;
-  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(dsmem_addr(local, rank)) : "memory");
-  return v;
-}
-__device__ __forceinline__ int ld_dsmem_s32(const int* local, unsigned rank) {
-  int v;
-  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(dsmem_addr(local, rank)) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_dsmem_f64(double* local, unsigned rank, double v) {
-  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(dsmem_addr(local, rank)), "d"(v) : "memory");
-}
-__device__ __forceinline__ void st_dsmem_s32(int* local, unsigned rank, int v) {
-  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(dsmem_addr(local, rank)), "r"(v) : "memory");
 }
 
 // 1/sqrt(a) in FP64 by two Newton steps y <- y (3/2 - a y^2 / 2) from the
@@ -127,39 +72,38 @@ __device__ __forceinline__ void reflector(double x0, double sigma, double* rmu, 
   }
 }
 
-// Panel factorisation.  With TILE, each CTA keeps its block of panel rows
-// (rows_per_cta x nb doubles) in shared memory for the whole factorisation, so
-// that a column step touches global memory only for the cross-CTA partial
-// sums and the published pivot row; the tile is written back (R entries,
-// reflectors) at the end.  Without TILE (very tall panels) the same steps
-// run on W in global memory.
+// Panel factorisation, one cooperative launch over the GPU.  With TILE, each
+// CTA keeps its block of panel rows (rows_per_cta x nb doubles) in shared
+// memory for the whole factorisation, so that a column step touches global
+// memory only for the cross-CTA sums and the published pivot row; the tile
+// is written back (R entries, reflectors) at the end.  Without TILE (very
+// tall panels) the same steps run on W in global memory.
 //
-// Column step j (c = j0 + j the pivot row), after all CTAs have published the
-// partial sums of column j (slot 0: sigma = sum_{i>c} x_i^2, slot t:
-// s_t = sum_{i>c} x_i y_{t,i} for column j + t) and the owner of row c has
-// published that row (x_0 and the y_{t,0}):
+// Column step j (c = j0 + j the pivot row), once every CTA has added its
+// partial sums of column j into the column's accumulator row (slot 0:
+// sigma = sum_{i>c} x_i^2, slot t: s_t = sum_{i>c} x_i y_{t,i} for column
+// j + t) and arrived, and the owner of row c has published that row (x_0
+// and the y_{t,0}):
 //   mu = sqrt(x_0^2 + sigma), w = x_0 - mu, tau = -w / mu,
 //   v = x / w (v_0 = 1),   y_t -= tau (y_{t,0} + s_t / w) v,   R_cc = mu,
 //   R_{c,j+t} = y_{t,0} - tau (y_{t,0} + s_t / w).
 // Since tau / w = -1/mu, the rows below c need only 1/mu and 1/w:
 //   v_i = x_i / w,   y_{t,i} += (y_{t,0} + s_t / w) / mu * x_i,
-// so the scalar chain between the reduction and the row pass is one
+// so the scalar chain between the arrival and the row pass is one
 // reciprocal square root and one reciprocal; tau and the R entries of the
 // pivot rows are formed once after the column loop, from the saved sums
 // (sigma_j, s_{t,j}) and the pivot rows, which no later column touches.
-// The pass over a CTA's rows that applies reflector j also accumulates the
-// partial sums of column j + 1 (the updated value of column j + 1 on a row
-// reaches the other lanes by a warp shuffle), two rows at a time, so a
-// column costs one round of the arrival counter and three block barriers.
+// Warp 0 waits, reads the accumulator and forms the multipliers; one block
+// barrier hands them to the row pass.  The pass over a CTA's rows that
+// applies reflector j also accumulates the partial sums of column j + 1 (the
+// updated value of column j + 1 on a row reaches the other lanes by a warp
+// shuffle), two rows at a time; a second block barrier gathers them and
+// warp 0 adds them into column j + 1's accumulator row (FP64 atomics; the
+// order of the additions across CTAs is not fixed) and arrives.
 //
-// CL > 1: the CTAs form clusters of CL; each CTA stores its partial sums
-// into the rank-0 CTA's shared memory (and its stop flag into every CTA's),
-// one cluster barrier makes them visible, and only rank 0 adds them,
-// publishes and arrives.  This divides the partial sums every CTA reads (and
-// the FP64 adds on B300's narrow FP64 pipe) and the global arrivals by CL at
-// the price of one cluster barrier per column.  A CTA whose wait gives up
-// still reaches that barrier; the cluster then stops together.
-template <bool TILE, int CL, bool ATOM>
+// part: accumulator rows [column][NB] (zeroed before the first panel of a
+// factorisation), then the pivot rows rowb[2][NB].
+template <bool TILE>
 __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
                                                       double* __restrict__ V,
                                                       double* __restrict__ tau_out,
@@ -169,27 +113,12 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
                                                       long long ldx, float* __restrict__ Vt32,
                                                       const float* __restrict__ src32,
                                                       float* __restrict__ V32, long long ldv) {
-  constexpr bool CLU = CL > 1;
-  constexpr int CLA = CLU ? CL : 1;
-  static_assert(!(ATOM && CLU), "the accumulating exchange runs without clusters");
-  if constexpr (CLU) {
-    // the distributed-shared-memory exchange needs exactly CL CTAs per
-    // cluster; any other launch shape reports an error and touches nothing
-    if (cluster_size() != (unsigned)CL || (gridDim.x % CL) != 0) {
-      if (threadIdx.x == 0) atomicOr(err, ERRF_BOUNDS);
-      return;
-    }
-  }
   const int P = gridDim.x, b = blockIdx.x;
-  const int NG = P / CL;                 // publishers: clusters (CL > 1) or CTAs
-  const int grp = b / CL;
-  const unsigned crank = CLU ? cluster_rank() : 0u;
   const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;   // wrp = row lane (0..7)
   const long long r_begin = (long long)j0 + (long long)b * rows_per_cta;
   const long long r_end = std::min<long long>(m, r_begin + rows_per_cta);
   const int rows = (int)std::max<long long>(0, r_end - r_begin);
-  // scratch: psum[2][NG][NB], rowb[2][NB]
-  double* psum = part;
+  double* accum = part + (size_t)j0 * NB;          // row jc: column j0 + jc
   double* rowb = part + 2 * (size_t)PMAX * NB;
   __shared__ double red[8][NB];
   __shared__ double coef_s[NB];   // per lane: new y_t = y_t + coef_s[t] x on rows below c
@@ -197,8 +126,6 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
   __shared__ double tau_s[NB];
   __shared__ double iw_s[NB];     // 1/w of column j (R entries after the loop)
   __shared__ double x0_s[NB];     // pivot value x_0 of column j as published
-  __shared__ double cpart[2][CLA][NB];   // partial sums of the cluster's CTAs (rank 0's copy)
-  __shared__ int c_abort[2][CLA];        // stop flags of the cluster's CTAs, by column parity
   __shared__ int s_ok;
   extern __shared__ double tile[];                 // [rows][NB + 1]
   // element (global row i, panel column jc)
@@ -210,46 +137,13 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     return ((red[0][t] + red[1][t]) + (red[2][t] + red[3][t])) +
            ((red[4][t] + red[5][t]) + (red[6][t] + red[7][t]));
   };
-  // publish the partial sums held by warp 0 (value v in lane t = slot t,
-  // nslots of them) for panel column col with parity buf; returns false when
-  // the cluster must stop
-  auto publish = [&](int col, int buf, double v, bool aborted, int nslots) -> bool {
-    if constexpr (ATOM) {
-      (void)buf; (void)aborted;
-      if (wrp == 0) {
-        if (lane < nslots) atomicAdd(part + ((size_t)j0 + col) * NB + lane, v);
-        __syncwarp();
-        if (lane == 0) grid_arrive(bar);
-      }
-      return true;
-    } else if constexpr (!CLU) {
-      (void)col; (void)nslots;
-      if (wrp == 0) {
-        psum[((size_t)buf * NG + b) * NB + lane] = v;
-        __syncwarp();
-        if (lane == 0) grid_arrive(bar);
-      }
-      return true;
-    } else {
-      (void)col; (void)nslots;
-      if (wrp == 0) st_dsmem_f64(&cpart[buf][crank][lane], 0u, v);
-      if (threadIdx.x < (unsigned)CL)
-        st_dsmem_s32(&c_abort[buf][crank], threadIdx.x, aborted ? 1 : 0);
-      cluster_sync_all();
-      // the leader publishes at once (after an abort the numbers are not
-      // used: every CTA stops below, with the error word already set)
-      if (crank == 0 && wrp == 0) {
-        double acc = cpart[buf][0][lane];
-#pragma unroll
-        for (int q = 1; q < CL; ++q) acc += cpart[buf][q][lane];
-        psum[((size_t)buf * NG + grp) * NB + lane] = acc;
-        __syncwarp();
-        if (lane == 0) grid_arrive(bar);
-      }
-      int any = 0;
-#pragma unroll
-      for (int q = 0; q < CL; ++q) any |= c_abort[buf][q];
-      return any == 0;
+  // warp 0: add the partial sums (lane t = slot t, nslots of them) into the
+  // accumulator row of panel column col, then arrive
+  auto publish = [&](int col, double v, int nslots) {
+    if (wrp == 0) {
+      if (lane < nslots) atomicAdd(accum + (size_t)col * NB + lane, v);
+      __syncwarp();
+      if (lane == 0) grid_arrive(bar);
     }
   };
   if (TILE) {
@@ -264,7 +158,6 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     __syncthreads();
   }
   // partial sums of column 0 (slot t = lane) and the pivot row j0
-  bool stop = false;
   {
     const long long c = j0;
     double acc = 0.0;
@@ -274,67 +167,46 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     red[wrp][lane] = acc;
     if (c >= r_begin && c < r_end && (int)threadIdx.x < nb) rowb[threadIdx.x] = at(c, threadIdx.x);
     __syncthreads();
-    stop = !publish(0, 0, (wrp == 0) ? sum8(lane) : 0.0, false, nb);
+    publish(0, (wrp == 0) ? sum8(lane) : 0.0, nb);
   }
 
-  int j = 0, done = 0;
-  for (; j < nb && !stop; ++j) {
+  int done = 0;
+  for (int j = 0; j < nb; ++j) {
     const int buf = j & 1;
     const long long c = (long long)j0 + j;
     const int nrem = nb - j - 1;
     const bool last = (j + 1 >= nb);
-    if (threadIdx.x == 0) s_ok = grid_wait(bar, (unsigned)NG * (unsigned)(j + 1), err) ? 1 : 0;
-    __syncthreads();
-    const bool ok = s_ok != 0;
-    if constexpr (!CLU) {
-      if (!ok) break;
+    if (wrp == 0) {
+      int okw = 1;
+      if (lane == 0) okw = grid_wait(bar, (unsigned)P * (unsigned)(j + 1), err) ? 1 : 0;
+      __syncwarp();                                        // orders lane 0's acquire first
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      double y0 = 0.0, st = 0.0;
+      if (okw && lane <= nrem) {
+        y0 = __ldcg(rowb + buf * NB + lane);               // x_0 (lane 0), y_{t,0} (lane t)
+        st = __ldcg(accum + (size_t)j * NB + lane);        // sigma (lane 0), s_t (lane t)
+      }
+      ssum[j][lane] = st;
+      if (lane == 0) x0_s[j] = y0;
+      double rmu = 0.0, inv_w = 0.0;
+      if (lane == 0 && st != 0.0) {
+        double mu;
+        reflector(y0, st, &rmu, &mu, &inv_w, nullptr);
+      }
+      // sigma = 0: x is zero below c, v = e_1 (tau = 0 or 2); the rows
+      // below c are left as they are (multipliers 0)
+      rmu = __shfl_sync(0xffffffffu, rmu, 0);
+      inv_w = __shfl_sync(0xffffffffu, inv_w, 0);
+      double mult = 0.0;
+      if (lane == 0) mult = inv_w;
+      else if (lane <= nrem) mult = rmu * fma(st, inv_w, y0);
+      coef_s[lane] = mult;
+      if (lane == 0) s_ok = okw;
     }
+    __syncthreads();
+    if (!s_ok) break;
     double acc = 0.0, acc2 = 0.0;
-    if (ok) {
-      // pivot row (x_0 and the y_{t,0}) loaded together with the partial sums
-      const double y0 = (wrp == 0 && lane <= nrem) ? __ldcg(rowb + buf * NB + lane) : 0.0;
-      // ATOM: the sums of every CTA were added into this column's slots
-      double st_acc = 0.0;
-      if constexpr (ATOM) {
-        if (wrp == 0 && lane <= nrem) st_acc = __ldcg(part + ((size_t)j0 + j) * NB + lane);
-      } else {
-        // cross-unit reduction (L2 reads): lane = slot, the 8 warps take every 8th unit
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        if (lane <= nrem) {
-          const double* ps = psum + (size_t)buf * NG * NB + lane;
-          int q = wrp;
-          for (; q + 24 < NG; q += 32) {
-            s0 += __ldcg(ps + (size_t)q * NB);
-            s1 += __ldcg(ps + (size_t)(q + 8) * NB);
-            s2 += __ldcg(ps + (size_t)(q + 16) * NB);
-            s3 += __ldcg(ps + (size_t)(q + 24) * NB);
-          }
-          for (; q < NG; q += 8) s0 += __ldcg(ps + (size_t)q * NB);
-        }
-        red[wrp][lane] = (s0 + s1) + (s2 + s3);
-        __syncthreads();
-      }
-      if (wrp == 0) {
-        const double st = ATOM ? st_acc : sum8(lane);      // sigma (lane 0), s_t (lane t)
-        ssum[j][lane] = st;
-        if (lane == 0) x0_s[j] = y0;
-        double rmu = 0.0, inv_w = 0.0;
-        if (lane == 0 && st != 0.0) {
-          double mu;
-          reflector(y0, st, &rmu, &mu, &inv_w, nullptr);
-          if (!(rmu == rmu) || isinf(rmu) || !(inv_w == inv_w) || isinf(inv_w))
-            atomicOr(err, ERRF_NUMERIC);
-        }
-        // sigma = 0: x is zero below c, v = e_1 (tau = 0 or 2); the rows
-        // below c are left as they are (multipliers 0)
-        rmu = __shfl_sync(0xffffffffu, rmu, 0);
-        inv_w = __shfl_sync(0xffffffffu, inv_w, 0);
-        double mult = 0.0;
-        if (lane == 0) mult = inv_w;
-        else if (lane <= nrem) mult = rmu * fma(st, inv_w, y0);
-        coef_s[lane] = mult;
-      }
-      __syncthreads();
+    {
       const double mult = coef_s[lane];
       const bool active = (lane <= nrem);
       const bool upd = (lane >= 1 && active);
@@ -374,23 +246,22 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
           }
         }
       }
-      done = j + 1;
     }
+    done = j + 1;
     if (last) break;
     red[wrp][lane] = acc + acc2;                           // slot lane - 1 of column j + 1
     __syncthreads();
-    const double v = (wrp == 0 && lane < nrem) ? sum8(lane + 1) : 0.0;
-    if (!publish(j + 1, buf ^ 1, v, !ok, nrem)) break;
+    publish(j + 1, (wrp == 0 && lane < nrem) ? sum8(lane + 1) : 0.0, nrem);
   }
   __syncthreads();
   // tau and the pivot rows (R_cc = mu, R_{c,j+t} = y_{t,0} - tau (y_{t,0} +
   // s_t / w)) of the factored columns: one lane per column, from the saved
-  // sums and the pivot rows (unchanged since their column step).  CTA 0 needs
-  // tau of every column; a CTA holding pivot rows needs its own columns.
+  // sums and the published pivot values.  CTA 0 needs tau of every column;
+  // a CTA holding pivot rows needs its own columns.  A NaN or Inf anywhere
+  // in the panel reaches tau or mu.
   const bool has_pivots = r_begin < (long long)j0 + done;
   if ((b == 0 || has_pivots) && wrp == 0 && lane < done) {
     const long long c = (long long)j0 + lane;
-    const bool own = c >= r_begin && c < r_end;
     const double sigma = ssum[lane][0];
     const double x0 = x0_s[lane];        // = at(c, lane) on the owner of row c
     double tau = 0.0, iw = 0.0, mu = fabs(x0);
@@ -400,9 +271,10 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     } else {
       tau = (x0 < 0.0) ? 2.0 : 0.0;
     }
+    if (!(tau == tau) || isinf(tau) || !(mu == mu) || isinf(mu)) atomicOr(err, ERRF_NUMERIC);
     tau_s[lane] = tau;
     iw_s[lane] = iw;
-    if (own) at(c, lane) = mu;
+    if (c >= r_begin && c < r_end) at(c, lane) = mu;
   }
   __syncthreads();
   if (has_pivots) {
@@ -436,8 +308,6 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
   }
   // tau of the panel columns for the compact-WY factor (built after the kernel)
   if (b == 0 && threadIdx.x < (unsigned)nb) tau_out[threadIdx.x] = tau_s[threadIdx.x];
-  // no CTA of a cluster may leave while others can still read its shared memory
-  if constexpr (CLU) cluster_sync_all();
   if (threadIdx.x == 0) grid_exit(bar, (unsigned)P);
 }
 
@@ -536,14 +406,14 @@ cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t 
   if (tile <= kPanelTileMax) {
     static bool attr = false;
     if (!attr) {
-      cudaFuncSetAttribute(qr_panel_kernel<true, 1, true>,
+      cudaFuncSetAttribute(qr_panel_kernel<true>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelTileMax);
       attr = true;
     }
-    e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<true, 1, true>, dim3(P),
+    e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<true>, dim3(P),
                                     dim3(PT), args, tile, s);
   } else {
-    e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<false, 1, true>, dim3(P),
+    e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<false>, dim3(P),
                                     dim3(PT), args, 0, s);
   }
   if (w.hook) w.hook(w.hook_user, 0);
