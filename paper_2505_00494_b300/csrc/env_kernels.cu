@@ -57,15 +57,21 @@ __global__ void sumsq_kernel(const double* __restrict__ x, long long n, double* 
 __global__ void scale_kernel(const double* __restrict__ x, double* __restrict__ y, long long n,
                              const double* __restrict__ partials, int nparts, int* err) {
   __shared__ double inv;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    // the block's copy of the norm: lanes take every 32nd partial, then a
+    // shuffle tree (a short dependent chain; the order is fixed)
     double s = 0.0;
-    for (int q = 0; q < nparts; ++q) s += partials[q];
-    double nrm = sqrt(s);
-    if (!(nrm > 0.0) || isinf(nrm)) {
-      if (blockIdx.x == 0) atomicOr(err, ERRF_NUMERIC);
-      inv = 0.0;
-    } else {
-      inv = 1.0 / nrm;
+    for (int q = threadIdx.x; q < nparts; q += 32) s += partials[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) {
+      const double nrm = sqrt(s);
+      if (!(nrm > 0.0) || isinf(nrm)) {
+        if (blockIdx.x == 0) atomicOr(err, ERRF_NUMERIC);
+        inv = 0.0;
+      } else {
+        inv = 1.0 / nrm;
+      }
     }
   }
   __syncthreads();
@@ -646,7 +652,7 @@ cudaError_t sum_squares_partials(const double* x, long long n, double* partials,
 cudaError_t scale_by_inv_norm(const double* x, double* y, long long n, const double* partials,
                               int nparts, int* err, cudaStream_t s) {
   long long nb = (n + 255) / 256;
-  if (nb > 1184) nb = 1184;
+  if (nb > 296) nb = 296;   // 2 x 148 SMs, grid-stride: each block reduces the partials once
   if (nb < 1) nb = 1;
   scale_kernel<<<(unsigned)nb, 256, 0, s>>>(x, y, n, partials, nparts, err);
   note_launch();

@@ -731,16 +731,18 @@ __global__ void tc_splitk_reduce(const TcArgs a, int batch) {
        e += (long long)gridDim.x * blockDim.x) {
     const long long b = e / MN, r = e % MN, m = r / a.N, n = r % a.N;
     const float* p = a.part + b * a.ksplit * MN + r;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int z = 0;
-    for (; z + 4 <= a.ksplit; z += 4) {
-      a0 += static_cast<double>(p[(long long)z * MN]);
-      a1 += static_cast<double>(p[(long long)(z + 1) * MN]);
-      a2 += static_cast<double>(p[(long long)(z + 2) * MN]);
-      a3 += static_cast<double>(p[(long long)(z + 3) * MN]);
+    // compensated FP32 sum (TwoSum per term, Knuth): s + c carries the sum of
+    // the partials to ~2^-48 of their magnitude, like an FP64 sum, at FP32
+    // speed (B300's FP64 pipe would bound this pass)
+    float sh = 0.f, se = 0.f;
+    for (int z = 0; z < a.ksplit; ++z) {
+      const float x = p[(long long)z * MN];
+      const float t = sh + x;
+      const float bp = t - sh;
+      se += (sh - (t - bp)) + (x - bp);
+      sh = t;
     }
-    for (; z < a.ksplit; ++z) a0 += static_cast<double>(p[(long long)z * MN]);
-    const double acc = (a0 + a1) + (a2 + a3);
+    const double acc = static_cast<double>(sh) + static_cast<double>(se);
     const long long off = map_off(a.c_b, b) + map_off(a.c_m, m) + map_off(a.c_n, n);
     double v = a.alpha * acc;
     if (a.c_fp64) {
