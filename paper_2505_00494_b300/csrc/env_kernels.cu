@@ -344,6 +344,7 @@ __global__ void __launch_bounds__(1024) spectrum_kernel(const double* __restrict
 //       second barrier every CTA forms K = beta v.p / 2 and w = p - K v,
 //       then updates its own rows, A -= v w^T + w v^T.
 constexpr int kSpecClusterMaxN8 = 360;    // 8-CTA cluster (portable size)
+constexpr int kSpecCluster16From = 97;    // 16 CTAs preferred from here (half the FP64 work per SM)
 constexpr int kSpecClusterMaxN16 = 512;   // 16-CTA cluster (non-portable size)
 
 __device__ __forceinline__ void cluster_sync_all() {
@@ -419,10 +420,12 @@ __global__ void __launch_bounds__(256) spectrum_cluster_kernel(const double* __r
         sc[1] = 0.0;
         if (r == 0) of[k] = 0.0;
       } else {
-        const double alpha = sqrt(nrm2);
+        // Newton reciprocal square root and reciprocal from FP32 seeds: the
+        // IEEE FP64 sqrt and divide are long chains on B300's FP64 pipe
+        const double alpha = nrm2 * rsqrt_nr(nrm2);
         const double sgn = (x0 >= 0.0) ? 1.0 : -1.0;
         sc[0] = x0 + sgn * alpha;
-        sc[1] = 1.0 / (alpha * (alpha + fabs(x0)));
+        sc[1] = rcp_nr(alpha * (alpha + fabs(x0)));
         if (r == 0) of[k] = -sgn * alpha;
       }
     }
@@ -714,60 +717,66 @@ cudaError_t corner_spectrum(const double* C, int chi, double* work, double* s_ne
     attr = true;
   }
   bool launched = false;
-  if (chi >= 3 && chi <= kSpecClusterMaxN16) {
-    const int cs = (chi <= kSpecClusterMaxN8) ? 8 : 16;
-    const int maxn = (cs == 8) ? kSpecClusterMaxN8 : kSpecClusterMaxN16;
+  // one-time setup of the cluster variants: shared-memory limits for their
+  // largest n, and whether the device can place a 16-CTA cluster
+  static bool cattr = false, ok16 = false;
+  if (!cattr) {
+    cudaFuncSetAttribute(spectrum_cluster_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(double) * (((size_t)kSpecClusterMaxN8 + 7) / 8 *
+                                                     kSpecClusterMaxN8 +
+                                                 4 * (size_t)kSpecClusterMaxN8)));
+    auto k16 = spectrum_cluster_kernel<16>;
+    const size_t smem16 = sizeof(double) * (((size_t)kSpecClusterMaxN16 + 15) / 16 *
+                                                kSpecClusterMaxN16 +
+                                            4 * (size_t)kSpecClusterMaxN16);
+    cudaFuncSetAttribute(k16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem16);
+    // 16 CTAs per cluster is above the portable limit: allowed only where
+    // the device can place such a cluster
+    ok16 = cudaFuncSetAttribute(k16, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+           cudaSuccess;
+    if (ok16) {
+      cudaLaunchConfig_t q = {};
+      q.gridDim = dim3(16);
+      q.blockDim = dim3(256);
+      q.dynamicSmemBytes = smem16;
+      cudaLaunchAttribute qa[1];
+      qa[0].id = cudaLaunchAttributeClusterDimension;
+      qa[0].val.clusterDim.x = 16;
+      qa[0].val.clusterDim.y = 1;
+      qa[0].val.clusterDim.z = 1;
+      q.attrs = qa;
+      q.numAttrs = 1;
+      int nclusters = 0;
+      ok16 = cudaOccupancyMaxActiveClusters(&nclusters, k16, &q) == cudaSuccess &&
+             nclusters >= 1;
+    }
+    cudaGetLastError();
+    cattr = true;
+  }
+  int cs = 0;
+  if (chi >= 3) {
+    if (ok16 && chi >= kSpecCluster16From && chi <= kSpecClusterMaxN16) cs = 16;
+    else if (chi <= kSpecClusterMaxN8) cs = 8;
+  }
+  if (cs != 0) {
     auto kern = (cs == 8) ? spectrum_cluster_kernel<8> : spectrum_cluster_kernel<16>;
     const int nloc_max = (chi + cs - 1) / cs;
     const size_t csmem = sizeof(double) * ((size_t)nloc_max * chi + 4 * (size_t)chi);
-    static bool cattr8 = false, cattr16 = false, ok16 = false;
-    bool& cattr = (cs == 8) ? cattr8 : cattr16;
-    if (!cattr) {
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(double) * (((size_t)maxn + cs - 1) / cs * maxn +
-                                                   4 * (size_t)maxn)));
-      if (cs == 16) {
-        // 16 CTAs per cluster is above the portable limit: allowed only where
-        // the device can place such a cluster
-        ok16 = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-               cudaSuccess;
-        if (ok16) {
-          cudaLaunchConfig_t q = {};
-          q.gridDim = dim3(16);
-          q.blockDim = dim3(256);
-          q.dynamicSmemBytes = csmem;
-          cudaLaunchAttribute qa[1];
-          qa[0].id = cudaLaunchAttributeClusterDimension;
-          qa[0].val.clusterDim.x = 16;
-          qa[0].val.clusterDim.y = 1;
-          qa[0].val.clusterDim.z = 1;
-          q.attrs = qa;
-          q.numAttrs = 1;
-          int nclusters = 0;
-          ok16 = cudaOccupancyMaxActiveClusters(&nclusters, kern, &q) == cudaSuccess &&
-                 nclusters >= 1;
-        }
-        cudaGetLastError();
-      }
-      cattr = true;
-    }
-    if (cs == 8 || ok16) {
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(cs);
-      cfg.blockDim = dim3(256);
-      cfg.dynamicSmemBytes = csmem;
-      cfg.stream = s;
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = cs;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      cudaError_t e = cudaLaunchKernelEx(&cfg, kern, C, chi, work, err);
-      if (e != cudaSuccess) return e;
-      launched = true;
-    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = csmem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, C, chi, work, err);
+    if (e != cudaSuccess) return e;
+    launched = true;
   }
   if (!launched) spectrum_kernel<<<1, 1024, smem, s>>>(C, chi, work, err);
   note_launch();

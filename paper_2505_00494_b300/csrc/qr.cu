@@ -26,29 +26,6 @@ constexpr size_t kPanelTileMax = 160 * 1024;   // shared-memory panel tile limit
 
 __host__ __device__ inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
-// FP64 reciprocal by Newton's iteration from an FP32 seed (quadratic
-// convergence: 24 -> 48 -> 96 bits), avoiding the long-latency IEEE
-// double-precision divide sequence on the scalar path.
-__device__ __forceinline__ double rcp_nr(double x) {
-  const double ax = fabs(x);
-  if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;   // outside the FP32 seed range
-  double r = static_cast<double>(1.0f / static_cast<float>(x));
-  r = fma(r, fma(-x, r, 1.0), r);
-  r = fma(r, fma(-x, r, 1.0), r);
-  return r;
-}
-
-// 1/sqrt(a) in FP64 by two Newton steps y <- y (3/2 - a y^2 / 2) from the
-// FP32 estimate (24 -> 48 -> 96 bits), for a inside the FP32 range.
-__device__ __forceinline__ double rsqrt_nr(double a) {
-  if (!(a > 1e-30 && a < 1e30)) return 1.0 / sqrt(a);
-  const double ha = 0.5 * a;
-  double y = static_cast<double>(rsqrtf(static_cast<float>(a)));
-  y = y * fma(-ha, y * y, 1.5);
-  y = y * fma(-ha, y * y, 1.5);
-  return y;
-}
-
 // Reflector scalars of a column with pivot value x0 and sigma = sum_{i>c}
 // x_i^2 > 0: mu = sqrt(x0^2 + sigma) (returned as rmu = 1/mu and mu),
 // w = x0 - mu (= -sigma / (x0 + mu) for x0 > 0, no cancellation) and

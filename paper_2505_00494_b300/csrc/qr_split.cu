@@ -35,6 +35,31 @@ namespace qrctm {
 
 namespace {
 
+// Compensated FP32 sum (TwoSum per term, Knuth) of ksplit partials
+// p[z * stride], z = 0, 1, ...: the loads of eight partials are issued before
+// they are added (in the same order), so the L2 round trips overlap instead
+// of following the summation chain.  Returns (sum, tail).
+__device__ __forceinline__ float2 sum_partials(const float* __restrict__ p, long long stride,
+                                               int ksplit) {
+  float sh = 0.f, se = 0.f;
+  auto add = [&](float x) {
+    const float t = sh + x;
+    const float bp = t - sh;
+    se += (sh - (t - bp)) + (x - bp);
+    sh = t;
+  };
+  int z = 0;
+  for (; z + 8 <= ksplit; z += 8) {
+    float x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x[u] = p[(long long)(z + u) * stride];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) add(x[u]);
+  }
+  for (; z < ksplit; ++z) add(p[(long long)z * stride]);
+  return make_float2(sh, se);
+}
+
 constexpr int NB = kQrPanel;
 constexpr int kWyThreads = 256;
 constexpr int kQrMaxKsplit = 16;   // K chunks of the V^T [.] products
@@ -65,16 +90,8 @@ __global__ void __launch_bounds__(kWyThreads) wy_prep_kernel(const float* __rest
   // TwoSum: s + e carries the sum exactly up to the final rounding), so that
   // the narrow FP64 pipe only sees one conversion pair and one add
   auto psum = [&](int q, long long col) {
-    const float* p = part + (long long)q * N + col;
-    float sh = 0.f, se = 0.f;
-    for (int z = 0; z < ksplit; ++z) {
-      const float x = p[(long long)z * MN];
-      const float t = sh + x;
-      const float bp = t - sh;
-      se += (sh - (t - bp)) + (x - bp);
-      sh = t;
-    }
-    return static_cast<double>(sh) + static_cast<double>(se);
+    const float2 r = sum_partials(part + (long long)q * N + col, MN, ksplit);
+    return static_cast<double>(r.x) + static_cast<double>(r.y);
   };
   for (int e = tid; e < NB * NB; e += kWyThreads) {
     const int q = e / NB, c = e % NB;
@@ -143,16 +160,8 @@ __global__ void build_ut_kernel(const float* __restrict__ part, int ksplit, int 
   float v = 0.f;
   if (l < i) {
     const long long nn = (long long)n * n;
-    const float* p = part + (long long)l * n + i;
-    float sh = 0.f, se = 0.f;
-    for (int z = 0; z < ksplit; ++z) {
-      const float x = p[(long long)z * nn];
-      const float t = sh + x;
-      const float bp = t - sh;
-      se += (sh - (t - bp)) + (x - bp);
-      sh = t;
-    }
-    v = sh + se;
+    const float2 r = sum_partials(part + (long long)l * n + i, nn, ksplit);
+    v = r.x + r.y;
   } else if (l == i) {
     const double tau = Tf[(size_t)(i / NB) * NB * NB + (i % NB) * NB + (i % NB)];
     v = static_cast<float>(1.0 / tau);
@@ -168,13 +177,15 @@ __global__ void build_ut_kernel(const float* __restrict__ part, int ksplit, int 
 // MAXQ values per lane: n <= 32 MAXQ (16 up to n = 512, 32 up to 1024).
 constexpr int kSolveMaxPerLane = 32;   // n <= 1024
 constexpr int kSolveSmemMaxN = 200;    // U^T staged in shared memory up to n = 200
-template <int MAXQ>
+// STAGED (n <= kSolveSmemMaxN) is a template parameter so that the row loads
+// of U^T compile to shared-memory loads, not generic ones.
+template <int MAXQ, bool STAGED>
 __global__ void __launch_bounds__(256) q_solve_kernel(const float* __restrict__ UT, long long ldu,
                                                       const float* __restrict__ Vt,
                                                       long long ldv, const double* __restrict__ Tf,
                                                       int n, float* __restrict__ Wt) {
   extern __shared__ float qs[];
-  const bool staged = n <= kSolveSmemMaxN;
+  constexpr bool staged = STAGED;
   float* taus = qs;                       // [n]
   float* us = qs + ((n + 3) & ~3);        // [n][n] when staged
   for (int e = threadIdx.x; e < n; e += blockDim.x)
@@ -334,18 +345,27 @@ cudaError_t householder_qr_split(int m, int n, const double* M, double* R, const
     build_ut_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, ksplit, n, w.Tf, UT, ldv);
     note_launch();
     const size_t qsm = sizeof(float) * (((n + 3) & ~3) + (n <= kSolveSmemMaxN ? (size_t)n * n : 0));
+    // the fewest values per lane that hold a column (32 MAXQ >= n); U^T
+    // staged in shared memory up to n = kSolveSmemMaxN
     static bool qattr = false;
     if (!qattr) {
-      // only n <= 200 (the 16-slot variant) stages U^T in shared memory
-      cudaFuncSetAttribute(q_solve_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(float) * (kSolveSmemMaxN * kSolveSmemMaxN +
-                                                  32 * kSolveMaxPerLane)));
+      const int mx = (int)(sizeof(float) * (kSolveSmemMaxN * kSolveSmemMaxN + 32 * 8));
+      cudaFuncSetAttribute(q_solve_kernel<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+      cudaFuncSetAttribute(q_solve_kernel<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
       qattr = true;
     }
-    if (n <= 32 * 16)
-      q_solve_kernel<16><<<(unsigned)((n + 7) / 8), 256, qsm, s>>>(UT, ldv, Vt32, ldv, w.Tf, n, Wt);
+    const unsigned qg = (unsigned)((n + 7) / 8);
+    const bool stg = n <= kSolveSmemMaxN;
+    if (n <= 128 && stg)
+      q_solve_kernel<4, true><<<qg, 256, qsm, s>>>(UT, ldv, Vt32, ldv, w.Tf, n, Wt);
+    else if (n <= 256 && stg)
+      q_solve_kernel<8, true><<<qg, 256, qsm, s>>>(UT, ldv, Vt32, ldv, w.Tf, n, Wt);
+    else if (n <= 256)
+      q_solve_kernel<8, false><<<qg, 256, qsm, s>>>(UT, ldv, Vt32, ldv, w.Tf, n, Wt);
+    else if (n <= 512)
+      q_solve_kernel<16, false><<<qg, 256, qsm, s>>>(UT, ldv, Vt32, ldv, w.Tf, n, Wt);
     else
-      q_solve_kernel<32><<<(unsigned)((n + 7) / 8), 256, qsm, s>>>(UT, ldv, Vt32, ldv, w.Tf, n, Wt);
+      q_solve_kernel<32, false><<<qg, 256, qsm, s>>>(UT, ldv, Vt32, ldv, w.Tf, n, Wt);
     note_launch();
     const long long totq = (long long)m * n;
     init_q32_kernel<<<(unsigned)std::min<long long>((totq + 255) / 256, 8192), 256, 0, s>>>(
