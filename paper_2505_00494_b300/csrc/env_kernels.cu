@@ -345,7 +345,9 @@ __global__ void __launch_bounds__(1024) spectrum_kernel(const double* __restrict
 //       then updates its own rows, A -= v w^T + w v^T.
 constexpr int kSpecClusterMaxN8 = 360;    // 8-CTA cluster (portable size)
 constexpr int kSpecCluster16From = 97;    // 16 CTAs preferred from here (half the FP64 work per SM)
-constexpr int kSpecClusterMaxN16 = 512;   // 16-CTA cluster (non-portable size)
+// 16-CTA cluster (non-portable size): ceil(n/16) rows of n doubles plus 4 n
+// doubles per CTA fit the 227 KB of shared memory up to n = 640
+constexpr int kSpecClusterMaxN16 = 640;
 
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n"

@@ -26,7 +26,7 @@ def cuda(x):
     return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
 
 
-@pytest.mark.parametrize("chi,seed", [(5, 0), (200, 1), (360, 2), (400, 3), (512, 4), (600, 5)])
+@pytest.mark.parametrize("chi,seed", [(5, 0), (200, 1), (360, 2), (400, 3), (512, 4), (600, 5), (640, 6), (700, 7)])
 def test_corner_spectrum_matches_lapack(q, chi, seed):
     rng = np.random.default_rng(seed)
     A = o.normalized_input(qi.raw_tensor(2, 2, seed))
