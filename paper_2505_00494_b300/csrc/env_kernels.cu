@@ -371,7 +371,11 @@ __device__ __forceinline__ double ld_dsmem(const double* local_addr, unsigned ra
   return v;
 }
 
-template <int CS>
+// GMEM: the rows of the symmetrised matrix stay in the work buffer (row i at
+// work + i n, n^2 doubles; L2-resident) instead of shared memory, for n
+// above what the CTAs' shared memory holds.  Each CTA touches only its own
+// rows, so the choice changes no synchronisation.
+template <int CS, bool GMEM>
 __global__ void __launch_bounds__(256) spectrum_cluster_kernel(const double* __restrict__ C, int n,
                                                                double* work, int* err) {
   extern __shared__ double csm[];
@@ -387,8 +391,11 @@ __global__ void __launch_bounds__(256) spectrum_cluster_kernel(const double* __r
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wrp = tid >> 5;
   const int nloc = (n - (int)r + CS - 1) / CS;          // rows r, r + CS, ...
   const int nloc_max = (n + CS - 1) / CS;
-  double* Aloc = csm;                                    // [nloc_max][n]
-  double* xs = Aloc + (size_t)nloc_max * n;              // published x (own entries)
+  // own row li (global row r + li CS)
+  auto rowp = [&](int li) -> double* {
+    return GMEM ? work + (size_t)((int)r + li * CS) * n : csm + (size_t)li * n;
+  };
+  double* xs = GMEM ? csm : csm + (size_t)nloc_max * n;  // published x (own entries)
   double* ps = xs + n;                                   // published p (own entries)
   double* vv = ps + n;                                   // v (all entries, local copy)
   double* ww = vv + n;                                   // w (all entries, local copy)
@@ -398,15 +405,15 @@ __global__ void __launch_bounds__(256) spectrum_cluster_kernel(const double* __r
   double* pb = v2 + n;
   for (int e = tid; e < nloc * n; e += nt) {
     const int li = e / n, j = e % n, i = (int)r + li * CS;
-    Aloc[e] = 0.5 * (C[(size_t)i * n + j] + C[(size_t)j * n + i]);
+    rowp(li)[j] = 0.5 * (C[(size_t)i * n + j] + C[(size_t)j * n + i]);
   }
   cluster_sync_all();
   for (int k = 0; k + 2 < n; ++k) {
     const int L = n - k - 1;
     // own rows i > k: first local row index with i > k
     const int li0 = (k + 1 - (int)r + CS - 1 < 0) ? 0 : (k + 1 - (int)r + CS - 1) / CS;
-    for (int li = li0 + tid; li < nloc; li += nt) xs[r + li * CS] = Aloc[(size_t)li * n + k];
-    if (tid == 0 && (k % CS) == (int)r) dg[k] = Aloc[(size_t)(k / CS) * n + k];
+    for (int li = li0 + tid; li < nloc; li += nt) xs[r + li * CS] = rowp(li)[k];
+    if (tid == 0 && (k % CS) == (int)r) dg[k] = rowp(k / CS)[k];
     cluster_sync_all();                                                     // (a)
     for (int t = tid; t < L; t += nt) {
       const int i = k + 1 + t;
@@ -442,7 +449,7 @@ __global__ void __launch_bounds__(256) spectrum_cluster_kernel(const double* __r
     // p_i = beta (A v)_i for own rows i > k: a warp per row, lanes over j
     double pv_w = 0.0;
     for (int li = li0 + wrp; li < nloc; li += (nt >> 5)) {
-      const double* row = Aloc + (size_t)li * n + k + 1;
+      const double* row = rowp(li) + k + 1;
       double a0 = 0.0, a1 = 0.0;
       int t = lane;
       for (; t + 32 < L; t += 64) {
@@ -480,7 +487,7 @@ __global__ void __launch_bounds__(256) spectrum_cluster_kernel(const double* __r
     const int rows_left = nloc - li0;
     for (int e = tid; e < rows_left * L; e += nt) {
       const int li = li0 + e / L, t = e % L, i = (int)r + li * CS, ti = i - k - 1;
-      double* a = Aloc + (size_t)li * n + k + 1 + t;
+      double* a = rowp(li) + k + 1 + t;
       *a = fma(-vv[ti], ww[t], fma(-ww[ti], vv[t], *a));
     }
     __syncthreads();
@@ -489,7 +496,7 @@ __global__ void __launch_bounds__(256) spectrum_cluster_kernel(const double* __r
   if (tid == 0) {
     for (int i = n - 2; i < n; ++i)
       if (i >= 0 && (i % CS) == (int)r) {
-        const double* row = Aloc + (size_t)(i / CS) * n;
+        const double* row = rowp(i / CS);
         dg[i] = row[i];
         if (i == n - 1 && n >= 2) of[n - 2] = row[n - 2];
       }
@@ -723,11 +730,11 @@ cudaError_t corner_spectrum(const double* C, int chi, double* work, double* s_ne
   // largest n, and whether the device can place a 16-CTA cluster
   static bool cattr = false, ok16 = false;
   if (!cattr) {
-    cudaFuncSetAttribute(spectrum_cluster_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(spectrum_cluster_kernel<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(double) * (((size_t)kSpecClusterMaxN8 + 7) / 8 *
                                                      kSpecClusterMaxN8 +
                                                  4 * (size_t)kSpecClusterMaxN8)));
-    auto k16 = spectrum_cluster_kernel<16>;
+    auto k16 = spectrum_cluster_kernel<16, false>;
     const size_t smem16 = sizeof(double) * (((size_t)kSpecClusterMaxN16 + 15) / 16 *
                                                 kSpecClusterMaxN16 +
                                             4 * (size_t)kSpecClusterMaxN16);
@@ -735,7 +742,9 @@ cudaError_t corner_spectrum(const double* C, int chi, double* work, double* s_ne
     // 16 CTAs per cluster is above the portable limit: allowed only where
     // the device can place such a cluster
     ok16 = cudaFuncSetAttribute(k16, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-           cudaSuccess;
+               cudaSuccess &&
+           cudaFuncSetAttribute(spectrum_cluster_kernel<16, true>,
+                                cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
     if (ok16) {
       cudaLaunchConfig_t q = {};
       q.gridDim = dim3(16);
@@ -756,14 +765,19 @@ cudaError_t corner_spectrum(const double* C, int chi, double* work, double* s_ne
     cattr = true;
   }
   int cs = 0;
+  bool gmem = false;
   if (chi >= 3) {
     if (ok16 && chi >= kSpecCluster16From && chi <= kSpecClusterMaxN16) cs = 16;
     else if (chi <= kSpecClusterMaxN8) cs = 8;
+    else if (ok16) { cs = 16; gmem = true; }   // rows in the work buffer
   }
   if (cs != 0) {
-    auto kern = (cs == 8) ? spectrum_cluster_kernel<8> : spectrum_cluster_kernel<16>;
+    auto kern = gmem ? spectrum_cluster_kernel<16, true>
+                     : (cs == 8) ? spectrum_cluster_kernel<8, false>
+                                 : spectrum_cluster_kernel<16, false>;
     const int nloc_max = (chi + cs - 1) / cs;
-    const size_t csmem = sizeof(double) * ((size_t)nloc_max * chi + 4 * (size_t)chi);
+    const size_t csmem =
+        sizeof(double) * ((gmem ? 0 : (size_t)nloc_max * chi) + 4 * (size_t)chi);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs);
     cfg.blockDim = dim3(256);
