@@ -734,7 +734,8 @@ def main():
                             fp64_note)}
     if args.precision == "split":
         kernels.update({
-            "absorb": ("absorb_fused_k", fl["absorb"], "alu", fp32_simt_peak(),
+            "absorb": ("absorb_d6_k" if D == 6 else "absorb_fused_k", fl["absorb"], "alu",
+                       fp32_simt_peak(),
                        "fp32 FMA nominal: 148 SMs x 128 FMA/clk x 2 x 2.032 GHz"),
             "x1": ("tc_tf32x3_persist<128>", fl["x1"], "tensor", tf32_peak, tf32_note),
             "project": ("tc_tf32x3_kernel<144>", fl["project"], "tensor", tf32_peak, tf32_note),

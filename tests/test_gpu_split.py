@@ -29,7 +29,7 @@ def cuda(x):
     return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
 
 
-@pytest.mark.parametrize("D,chi,seed", [(2, 16, 3), (3, 27, 4), (4, 32, 5)])
+@pytest.mark.parametrize("D,chi,seed", [(2, 16, 3), (3, 27, 4), (4, 32, 5), (6, 36, 6), (6, 53, 7)])
 def test_split_single_step(q, D, chi, seed):
     A = o.normalized_input(qi.raw_tensor(2, D, seed))
     C, T = o.warmup(A, chi)
