@@ -29,6 +29,15 @@ namespace {
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+// c <- a * b + c on both lanes of a pair (packed FP32 FMA, one instruction,
+// each lane rounded like fmaf)
+__device__ __forceinline__ void ffma2(float2& c, float2 a, float2 b) {
+  unsigned long long cc = *reinterpret_cast<unsigned long long*>(&c);
+  const unsigned long long aa = *reinterpret_cast<const unsigned long long*>(&a);
+  const unsigned long long bb = *reinterpret_cast<const unsigned long long*>(&b);
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(cc) : "l"(aa), "l"(bb));
+  c = *reinterpret_cast<float2*>(&cc);
+}
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -294,11 +303,11 @@ __global__ void __launch_bounds__(kD6Threads, 1)
     if (!s_ok) break;
     // ket: Zs[g][r][c] = sum_k X[g][r][k] AkT[k][c]
     if (g < ng) {
-      float acc[9][8];
+      float2 acc[9][4];   // column pairs (c0, c0+1), (c0+2, c0+3), then the s = 1 half
 #pragma unroll
       for (int i = 0; i < 9; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
       const float* xa = Xb + ((size_t)g * D2 + rb1) * D2;
 #pragma unroll 1
       for (int k = 0; k < D2; k += 4) {
@@ -312,49 +321,54 @@ __global__ void __launch_bounds__(kD6Threads, 1)
         for (int kk = 0; kk < 4; ++kk) {
           const float4 b0 = *reinterpret_cast<const float4*>(AkT + (k + kk) * dD2 + c0);
           const float4 b1 = *reinterpret_cast<const float4*>(AkT + (k + kk) * dD2 + D2 + c0);
-          const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+          const float2 bp[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w),
+                                make_float2(b1.x, b1.y), make_float2(b1.z, b1.w)};
 #pragma unroll
-          for (int i = 0; i < 9; ++i)
+          for (int i = 0; i < 9; ++i) {
+            const float2 a2 = make_float2(av[i][kk], av[i][kk]);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i][kk], bv[j], acc[i][j]);
+            for (int j = 0; j < 4; ++j) ffma2(acc[i][j], a2, bp[j]);
+          }
         }
       }
       float* zo = Zs + ((size_t)g * D2 + rb1) * dD2 + c0;
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
         *reinterpret_cast<float4*>(zo + i * dD2) =
-            make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            make_float4(acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y);
         *reinterpret_cast<float4*>(zo + i * dD2 + D2) =
-            make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+            make_float4(acc[i][2].x, acc[i][2].y, acc[i][3].x, acc[i][3].y);
       }
     }
     __syncthreads();
     // bra: out[r2][c2] = sum_{s,q} Zs[g][q][s*D2 + r2] AbT[s*D2 + q][c2], staged as
     // Xb[g][(j_k,j_b)][(d_k,d_b)]  (r2 = d_k*D + j_k, c2 = d_b*D + j_b)
     if (g < ng) {
-      float acc[6][6];
+      float2 acc[6][3];   // column pairs (cb2, cb2+1), (cb2+2, cb2+3), (cb2+4, cb2+5)
 #pragma unroll
       for (int i = 0; i < 6; ++i)
 #pragma unroll
-        for (int j = 0; j < 6; ++j) acc[i][j] = 0.f;
+        for (int j = 0; j < 3; ++j) acc[i][j] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         const float* za = Zs + (size_t)g * D2 * dD2 + s * D2 + rb2;
         const float* ba = AbT + (size_t)s * D2 * D2 + cb2;
 #pragma unroll 2
         for (int q = 0; q < D2; ++q) {
-          float av[6], bv[6];
+          float av[6];
+          float2 bp[3];
 #pragma unroll
           for (int u = 0; u < 3; ++u) {
             const float2 a = *reinterpret_cast<const float2*>(za + q * dD2 + 2 * u);
-            const float2 b = *reinterpret_cast<const float2*>(ba + q * D2 + 2 * u);
+            bp[u] = *reinterpret_cast<const float2*>(ba + q * D2 + 2 * u);
             av[2 * u] = a.x; av[2 * u + 1] = a.y;
-            bv[2 * u] = b.x; bv[2 * u + 1] = b.y;
           }
 #pragma unroll
-          for (int i = 0; i < 6; ++i)
+          for (int i = 0; i < 6; ++i) {
+            const float2 a2 = make_float2(av[i], av[i]);
 #pragma unroll
-            for (int j = 0; j < 6; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+            for (int j = 0; j < 3; ++j) ffma2(acc[i][j], a2, bp[j]);
+          }
         }
       }
 #pragma unroll
@@ -363,7 +377,8 @@ __global__ void __launch_bounds__(kD6Threads, 1)
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
           const int c2 = cb2 + j, db = c2 / D, jb = c2 % D;
-          Xb[((size_t)g * D2 + jk * D + jb) * D2 + dk * D + db] = acc[i][j];
+          Xb[((size_t)g * D2 + jk * D + jb) * D2 + dk * D + db] =
+              (j & 1) ? acc[i][j >> 1].y : acc[i][j >> 1].x;
         }
       }
     }
