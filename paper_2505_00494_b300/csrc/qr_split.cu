@@ -36,9 +36,9 @@ namespace qrctm {
 namespace {
 
 // Compensated FP32 sum (TwoSum per term, Knuth) of ksplit partials
-// p[z * stride], z = 0, 1, ...: the loads of eight partials are issued before
-// they are added (in the same order), so the L2 round trips overlap instead
-// of following the summation chain.  Returns (sum, tail).
+// p[z * stride], z = 0, 1, ...: the loads of up to sixteen partials are
+// issued before they are added (in the same order), so the L2 round trips
+// overlap instead of following the summation chain.  Returns (sum, tail).
 __device__ __forceinline__ float2 sum_partials(const float* __restrict__ p, long long stride,
                                                int ksplit) {
   float sh = 0.f, se = 0.f;
@@ -49,19 +49,29 @@ __device__ __forceinline__ float2 sum_partials(const float* __restrict__ p, long
     sh = t;
   };
   int z = 0;
-  for (; z + 8 <= ksplit; z += 8) {
-    float x[8];
+  for (; z + 16 <= ksplit; z += 16) {
+    float x[16];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) x[u] = p[(long long)(z + u) * stride];
+    for (int u = 0; u < 16; ++u) x[u] = p[(long long)(z + u) * stride];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) add(x[u]);
+    for (int u = 0; u < 16; ++u) add(x[u]);
+  }
+  if (z < ksplit) {
+    // the remaining (< 16) partials, loaded together before they are added
+    float x[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) x[u] = (z + u < ksplit) ? p[(long long)(z + u) * stride] : 0.f;
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+      if (z + u < ksplit) add(x[u]);
+    z = ksplit;
   }
   for (; z < ksplit; ++z) add(p[(long long)z * stride]);
   return make_float2(sh, se);
 }
 
 constexpr int NB = kQrPanel;
-constexpr int kWyThreads = 256;
+constexpr int kWyThreads = 1024;   // two partial sums per thread for a 32 x 32 block
 constexpr int kQrMaxKsplit = 16;   // K chunks of the V^T [.] products
 
 inline long long pad4(long long x) { return (x + 3) & ~3ll; }
