@@ -530,44 +530,56 @@ __global__ void __launch_bounds__(256) spectrum_cluster_kernel(const double* __r
   }
 }
 
-// Eigenvalue i of the tridiagonal (dg, e^2) by multisection: one warp per
-// eigenvalue (one warp per CTA, so that the Sturm recurrences of different
-// eigenvalues run on different SMs), the 32 lanes evaluate Sturm counts at 32
-// interior points of the current bracket, which shrinks 33-fold per round
-// until its width reaches the absolute resolution 4 eps max(|lo|, |hi|) of
-// the Gershgorin interval (the accuracy a backward-stable method attains).
+// Eigenvalue i of the tridiagonal (dg, e^2) by multisection: one CTA of
+// four warps per eigenvalue (one eigenvalue per SM: a single warp's Sturm
+// recurrence is bound by the FP64 latency, four fill the SM's FP64 pipe), the
+// 128 threads evaluate Sturm counts at 128 interior points of the current
+// bracket, which shrinks 129-fold per round (7 bits, against 5 bits for one
+// warp) until its width reaches the absolute resolution 4 eps max(|lo|, |hi|)
+// of the Gershgorin interval (the accuracy a backward-stable method attains).
 constexpr int kBisectMaxN = 1024;
+constexpr int kBisectThreads = 128;
 
-__global__ void __launch_bounds__(32) bisect_kernel(const double* work, int n, double* ev_out) {
+__global__ void __launch_bounds__(kBisectThreads) bisect_kernel(const double* work, int n,
+                                                                double* ev_out) {
   __shared__ double sdg[kBisectMaxN], se2[kBisectMaxN];
+  __shared__ unsigned masks[kBisectThreads / 32];
   const double* dg = work + (size_t)n * n;
   const double* v = dg + 3 * (size_t)n;       // e^2
   const double* p = v + n;                    // lo, hi, pivmin
-  const int lane = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wrp = tid >> 5;
   const int i = blockIdx.x;
-  for (int t = lane; t < n; t += 32) {
+  for (int t = tid; t < n; t += kBisectThreads) {
     sdg[t] = dg[t];
     se2[t] = (t + 1 < n) ? v[t] : 0.0;
   }
-  __syncwarp();
+  __syncthreads();
   double a = p[0], b = p[1];
   const double pivmin = p[2];
   const double res = 4e-16 * fmax(fabs(a), fabs(b));
+  constexpr int NPT = kBisectThreads;
   for (int round = 0; round < 64; ++round) {
-    const double h = (b - a) * (1.0 / 33.0);
-    const double x = a + h * (lane + 1);
+    const double h = (b - a) * (1.0 / (NPT + 1));
+    const double x = a + h * (tid + 1);
     const bool above = (x > a && x < b) ? (sturm_count(sdg, se2, n, x, pivmin) > i) : (x >= b);
     const unsigned mask = __ballot_sync(0xffffffffu, above);
-    // first lane whose point lies above eigenvalue i bounds it from above
-    const int first = mask ? __ffs(mask) - 1 : 32;
+    if (lane == 0) masks[wrp] = mask;
+    __syncthreads();
+    // the first point above eigenvalue i bounds it from above (the points
+    // above it form a suffix, the Sturm count being monotone in x)
+    int first = NPT;
+#pragma unroll
+    for (int w = NPT / 32 - 1; w >= 0; --w)
+      if (masks[w]) first = w * 32 + __ffs(masks[w]) - 1;
+    __syncthreads();                          // masks are rewritten next round
     const double na = (first == 0) ? a : a + h * first;
-    const double nb = (first == 32) ? b : a + h * (first + 1);
+    const double nb = (first == NPT) ? b : a + h * (first + 1);
     if (!(nb < b || na > a)) break;          // no progress: bracket at resolution
     a = na;
     b = nb;
     if (b - a <= res) break;
   }
-  if (lane == 0) ev_out[i] = 0.5 * (a + b);
+  if (tid == 0) ev_out[i] = 0.5 * (a + b);
 }
 
 // sorted |lambda| (descending, ties by index) and the change to the previous.
@@ -797,7 +809,7 @@ cudaError_t corner_spectrum(const double* C, int chi, double* work, double* s_ne
   if (!launched) spectrum_kernel<<<1, 1024, smem, s>>>(C, chi, work, err);
   note_launch();
   double* ev = work + (size_t)chi * chi + 5 * (size_t)chi + 8;
-  bisect_kernel<<<chi, 32, 0, s>>>(work, chi, ev);
+  bisect_kernel<<<chi, kBisectThreads, 0, s>>>(work, chi, ev);
   note_launch();
   spectrum_finish_kernel<<<1, 256, 0, s>>>(ev, chi, s_new, s_old, chi_old, delta);
   note_launch();
