@@ -474,10 +474,12 @@ __global__ void __launch_bounds__(256) spectrum_cluster_kernel(const double* __r
       const int i = k + 1 + t;
       ww[t] = ld_dsmem(ps + i, (unsigned)(i % CS));
     }
-    if (tid == 0) {
-      double pv = 0.0;
-      for (int q = 0; q < CS; ++q) pv += ld_dsmem(&pv_part, (unsigned)q);
-      sc[2] = 0.5 * beta * pv;
+    if (wrp == 0) {
+      // one lane per CTA of the cluster: the CS remote loads overlap
+      double pv = (lane < CS) ? ld_dsmem(&pv_part, (unsigned)lane) : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
+      if (lane == 0) sc[2] = 0.5 * beta * pv;
     }
     __syncthreads();
     const double K = sc[2];
