@@ -824,7 +824,8 @@ cudaError_t launch_bn(const TcGemm& g, cudaStream_t s) {
   a.b_batched = g.B.batch > 1 ? 1 : 0;
   a.err = g.err;
   // K chunks: at most 512 of K (16 blocks) per chunk, more chunks when the
-  // output grid alone cannot fill the GPU; partials are summed in FP64
+  // output grid alone cannot fill the GPU; partials are summed by compensated
+  // FP32 arithmetic
   static int nsm = 0;
   if (nsm == 0) {
     int dev = 0;
@@ -836,7 +837,12 @@ cudaError_t launch_bn(const TcGemm& g, cudaStream_t s) {
   const int nkb = (int)((g.K + BK - 1) / BK);
   int ksplit = 1, kbps = nkb;
   if (g.part != nullptr && nkb > 2) {
-    long long want = std::max<long long>((nkb + 15) / 16, (2ll * nsm + tiles - 1) / tiles);
+    // K within one 512-wide chunk: split for occupancy only when the output
+    // grid is far too small for the GPU (otherwise the reduction pass costs
+    // more than the shorter K loop saves)
+    const bool fill = nkb > 16 || tiles * 4 < nsm;
+    long long want = std::max<long long>((nkb + 15) / 16,
+                                         fill ? (2ll * nsm + tiles - 1) / tiles : 1);
     want = std::min<long long>(want, nkb / 2);
     const long long cap = g.part_elems / (g.M * g.N * std::max(1, g.batch));
     want = std::min<long long>(want, cap);
