@@ -3,21 +3,14 @@
 // D[b](m,n) = alpha * sum_k A[b](m,k) B[b](n,k) + beta * D[b](m,n)
 //
 // A and B are FP32, K-contiguous ("K-major"), read by TMA into 128-byte
-// swizzled shared-memory tiles (32 FP32 of K per row).  Four converter warps
-// split every element in place into a TF32 head hi = rna_tf32(x) and an FP32
-// tail lo = x - hi (exact), written to a second tile of the same layout.  One
-// elected thread issues, per 8-wide K slice, three kind::tf32 MMAs
-//     hi(A) hi(B) + hi(A) lo(B) + lo(A) hi(B)
-// into one FP32 accumulator in tensor memory (the lo*lo term, ~2^-22
-// relative, is dropped; the tensor core keeps 10 mantissa bits of lo, so each
-// product carries ~2^-21 relative error before FP32 accumulation).
-// The same four warps then read the accumulator (tcgen05.ld) and store it
-// through mixed-radix index maps in FP32 or FP64.
-//
-// Warp roles (192 threads): 0 = TMA producer, 1 = TMEM owner + MMA issuer,
-// 2..5 = converters, then epilogue (together they cover the four TMEM lane
-// quarters).  Every mbarrier wait is bounded; on timeout the kernel raises
-// ERRF_TIMEOUT in the error word and unwinds (TMEM is always freed).
+// swizzled shared-memory tiles (32 FP32 of K per row).  Every element is split
+// into a TF32 head and a TF32 tail, and one elected thread issues, per 8-wide
+// K slice, three kind::tf32 MMAs
+//     head(A) head(B) -> main,   head(A) tail(B) + tail(A) head(B) -> corr
+// into two FP32 accumulators in tensor memory, summed by the epilogue, which
+// stores the result through mixed-radix index maps in FP32 or FP64.  A is
+// staged into tensor memory (the MMAs read it there), B stays in shared
+// memory; the kernel below describes the split and the warp roles.
 #include <cuda.h>
 
 #include <algorithm>
@@ -32,7 +25,8 @@ namespace {
 
 constexpr int BM = 128;           // rows per tile = TMEM lanes
 constexpr int BK = 32;            // FP32 elements of K per swizzled row (128 B)
-constexpr int NTHREADS = 192;
+constexpr int NTHREADS = 320;     // 2 + 4 converter + 4 epilogue warps
+constexpr int NCONV = 4;          // converter warps
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -101,15 +95,6 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
          (static_cast<uint32_t>(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                          uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accum)
-      : "memory");
-}
-
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -133,333 +118,326 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float tf32_head(float x) {
-  uint32_t h;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-  return __uint_as_float(h);
+
+// ---------------------------------------------------------------------------
+// Epilogue (both kernels).  The 128 epilogue threads first fill the tile's
+// output offsets in shared memory (one row each, columns strided); each warp
+// then drains the 32 accumulator rows of its TMEM lane quarter in 32 x 32
+// chunks: main + correction summed, staged transposed in shared memory and
+// written one row per instruction with the lanes along the columns (coalesced
+// where the lowest column digit has unit stride; the row loop is unrolled so
+// that many stores are in flight).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void epi_offsets(const TcArgs& a, int bn, int t, long long m0, int n0,
+                                            int z, int kz, long long* col_off,
+                                            long long* col_off32, long long* row_off,
+                                            long long* row_off32) {
+  const bool split = a.ksplit > 1 || a.partials_only;
+  for (int j = t; j < bn; j += 128) {
+    const long long n = (long long)n0 + j;
+    const bool ok = n < a.N;
+    // split partials: part[b][z][m][n], the column index itself
+    col_off[j] = split ? n : (ok ? map_off(a.c_n, n) : 0);
+    if (a.C32) col_off32[j] = ok ? map_off(a.c32_n, n) : 0;
+  }
+  const long long m = m0 + t;
+  const bool ok = m < a.M;
+  row_off[t] = split ? (((long long)z * a.ksplit + kz) * a.M + (ok ? m : 0)) * a.N
+                     : map_off(a.c_b, z) + (ok ? map_off(a.c_m, m) : 0);
+  if (a.C32) row_off32[t] = ok ? map_off(a.c32_m, m) : 0;
 }
 
 template <int BN>
+__device__ __forceinline__ void epi_rows(const TcArgs& a, uint32_t acc, uint32_t half, int q,
+                                         int lane, long long m0, int n0, float* stg,
+                                         const long long* col_off, const long long* col_off32,
+                                         const long long* row_off, const long long* row_off32) {
+  const bool split = a.ksplit > 1 || a.partials_only;
+  const long long rv = a.M - m0 - q * 32;
+  if (rv <= 0) return;                      // warp-uniform: no valid row in this quarter
+  const int rows = rv < 32 ? (int)rv : 32;
+  const long long* ro = row_off + q * 32;
+  const long long* ro32 = row_off32 + q * 32;
+  // an output whose rows, not columns, are contiguous is written with the
+  // lanes along the rows (one lane = one accumulator row: no staging)
+  const bool row_major_out = split || (a.c_n.nd > 0 && a.c_n.str[0] == 1);
+  if (!row_major_out && a.c_m.nd > 0 && a.c_m.str[0] == 1) {
+    const bool rvalid = lane < rows;
+    const long long myro = rvalid ? ro[lane] : 0;
+    const long long myro32 = (rvalid && a.C32) ? ro32[lane] : 0;
+#pragma unroll 1
+    for (int c = 0; c < (BN + 31) / 32; ++c) {
+      float v[32], w[32];
+      const uint32_t ta = acc + (static_cast<uint32_t>(q * 32) << 16) + c * 32;
+      tmem_ld32(ta, v);
+      tmem_ld32(ta + half, w);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] += w[j];
+      if (!rvalid) continue;
+      const long long nrem = a.N - n0 - c * 32;
+      const int nv = (int)(nrem < BN - c * 32 ? nrem : BN - c * 32);   // valid if j < nv
+      // a one-digit column map is computed, not read from shared memory;
+      // either way each half's offsets and old values are loaded before its
+      // stores (the compiler cannot move shared-memory loads across global
+      // stores it cannot prove disjoint)
+      const bool cn1 = a.c_n.nd == 1;
+      const long long cs = a.c_n.str[0], nc0 = (long long)n0 + c * 32;
+      auto coff = [&](int j) -> long long {
+        return cn1 ? (nc0 + j) * cs : col_off[c * 32 + (j < nv ? j : 0)];
+      };
+      if (!a.c_fp64) {
+        float* p = static_cast<float*>(a.C) + myro;
+        const float al = static_cast<float>(a.alpha), be = static_cast<float>(a.beta);
+#pragma unroll
+        for (int j0 = 0; j0 < 32; j0 += 16) {   // halves: 16 loads in flight
+          long long o[16];
+          float r[16];
+#pragma unroll
+          for (int u = 0; u < 16; ++u) o[u] = coff(j0 + u);
+#pragma unroll
+          for (int u = 0; u < 16; ++u) r[u] = al * v[j0 + u];
+          if (be != 0.f) {
+            float old[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) old[u] = (j0 + u < nv) ? p[o[u]] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) r[u] = fmaf(be, old[u], r[u]);
+          }
+#pragma unroll
+          for (int u = 0; u < 16; ++u)
+            if (j0 + u < nv) p[o[u]] = r[u];
+        }
+      } else {
+        double* p = static_cast<double*>(a.C) + myro;
+#pragma unroll
+        for (int j0 = 0; j0 < 32; j0 += 16) {   // halves: 16 doubles in flight
+          long long o[16];
+          double r[16];
+#pragma unroll
+          for (int u = 0; u < 16; ++u) o[u] = coff(j0 + u);
+          if (a.beta != 0.0) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) r[u] = (j0 + u < nv) ? p[o[u]] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+              r[u] = fma(a.beta, r[u], a.alpha * static_cast<double>(v[j0 + u]));
+          } else {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) r[u] = a.alpha * static_cast<double>(v[j0 + u]);
+          }
+#pragma unroll
+          for (int u = 0; u < 16; ++u)
+            if (j0 + u < nv) p[o[u]] = r[u];
+          if (a.C32) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+              if (j0 + u < nv)
+                a.C32[myro32 + col_off32[c * 32 + j0 + u]] = static_cast<float>(r[u]);
+          }
+        }
+      }
+    }
+    return;
+  }
+#pragma unroll 1
+  for (int c = 0; c < (BN + 31) / 32; ++c) {
+    float v[32], w[32];
+    const uint32_t ta = acc + (static_cast<uint32_t>(q * 32) << 16) + c * 32;
+    tmem_ld32(ta, v);
+    tmem_ld32(ta + half, w);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = v[j] + w[j];
+    __syncwarp();
+    const int jj = c * 32 + lane;
+    const bool cvalid = jj < BN && (long long)n0 + jj < a.N;
+    // rows in groups of 8: offsets and staged values are loaded before the
+    // group's stores (the compiler cannot move shared-memory loads across
+    // global stores it cannot prove disjoint)
+    if (cvalid) {
+      const long long co = col_off[jj];
+      const long long co32 = (a.c_fp64 && a.C32) ? col_off32[jj] : 0;
+#pragma unroll 1
+      for (int r0 = 0; r0 < rows; r0 += 8) {
+        long long o[8], o32[8];
+        float x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          o[u] = ro[r0 + u] + co;
+          x[u] = stg[(r0 + u) * 33 + lane];
+          if (a.C32) o32[u] = ro32[r0 + u] + co32;
+        }
+        if (split) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (r0 + u < rows) a.part[o[u]] = x[u];
+        } else if (!a.c_fp64) {
+          // FP32 output in FP32 arithmetic (B300's FP64 pipe would bound it)
+          float* p = static_cast<float*>(a.C);
+          const float al = static_cast<float>(a.alpha), be = static_cast<float>(a.beta);
+          if (be != 0.f) {
+            float old[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) old[u] = (r0 + u < rows) ? p[o[u]] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = fmaf(be, old[u], al * x[u]);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] *= al;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (r0 + u < rows) p[o[u]] = x[u];
+        } else {
+          double* p = static_cast<double*>(a.C);
+          double r[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) r[u] = a.alpha * static_cast<double>(x[u]);
+          if (a.beta != 0.0) {
+            double old[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) old[u] = (r0 + u < rows) ? p[o[u]] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) r[u] = fma(a.beta, old[u], r[u]);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (r0 + u < rows) p[o[u]] = r[u];
+          if (a.C32) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              if (r0 + u < rows) a.C32[o32[u]] = static_cast<float>(r[u]);
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The kernel.  Tile = 128 rows (TMEM lanes) x BN columns; NBUF accumulator
+// buffers, each a (main, correction) pair of BN-wide FP32 regions in tensor
+// memory.  NBUF = 2: persistent (one CTA per SM walks the tiles; the epilogue
+// drains tile i while the MMAs accumulate tile i + 1).  NBUF = 1: one tile
+// per CTA (the wide-N shapes, whose accumulators leave no room for a second
+// buffer).
+//
+// Split of an FP32 value x (TF32x3): head = rna_tf32(x), tail = rna_tf32(x -
+// head), with x - head exact in FP32 and |tail| <= 2^-11 |x|; the two
+// roundings leave x represented to 2^-22 |x| and the dropped tail(A) tail(B)
+// term is below 2^-22 |ab|.  Rounding is an integer add and mask on the bit
+// pattern (round half away from zero at bit 13): the conversion
+// instruction's throughput would bound the kernel.  A NaN x keeps itself as
+// head, so it reaches the result.
+//
+// Operand staging: TMA brings the raw A (128 x 32) and B (BN x 32) tiles of
+// each 32-wide K block into shared memory.  Four converter warps then
+//   * split B in shared memory: head in place of the raw tile, tail plane
+//     beside it, and
+//   * move the A tile into tensor memory, head and tail side by side (each
+//     thread one row = one TMEM lane),
+// so that the three MMAs per 8-wide K slice,
+//     head(A) head(B) -> main,  head(A) tail(B) + tail(A) head(B) -> corr,
+// read A from tensor memory and only B from shared memory: the contraction
+// is bound by shared-memory bandwidth, and this removes the three reads of A
+// per K slice and the A planes from it.
+//
+// Warps (320 threads): 0 = TMA producer, 1 = TMEM owner + MMA issuer,
+// 2..5 = converters (warp w: the rows of TMEM lane quarter w % 4),
+// 6..9 = epilogue.  Every mbarrier wait is
+// bounded; on timeout the kernel raises ERRF_TIMEOUT in the error word and
+// unwinds (TMEM is always freed).
+// ---------------------------------------------------------------------------
+template <int BN, int NBUF>
 struct Cfg {
-  static constexpr int A_BYTES = BM * BK * 4;          // 16 KB
+  static constexpr int A_BYTES = BM * BK * 4;                       // 16 KB
   static constexpr int B_BYTES = BN * BK * 4;
-  static constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);   // x and lo tiles
-  static constexpr int STAGES = std::min(4, (210 * 1024) / STAGE_BYTES);
-  // main accumulator at column 0, correction accumulator at column HALF
-  static constexpr int HALF = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
-  static constexpr int TMEM_COLS = 2 * HALF;
-  static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + 1024 + 2 * BN * 8;
+  static constexpr int STAGE_BYTES = A_BYTES + 2 * B_BYTES;         // A, B, tail(B)
+  static constexpr int STG_BYTES = 4 * 32 * 33 * 4;                 // epilogue staging
+  static constexpr int OFF_BYTES = 2 * BN * 8 + 2 * BM * 8;         // column and row offsets
+  static constexpr int STAGES =
+      std::min(4, (232448 - 2048 - STG_BYTES - OFF_BYTES) / STAGE_BYTES);
+  static constexpr int HALF = (BN + 31) / 32 * 32;                  // TMEM columns per region
+  static constexpr int ACC_COLS = NBUF * 2 * HALF;
+  static constexpr int A_STAGES = std::min(4, (512 - ACC_COLS) / 64);   // (head, tail) x 32
+  static constexpr int A_COL0 = ACC_COLS;
+  static constexpr int TMEM_COLS = 512;
+  static constexpr int NBAR = 3 * STAGES + A_STAGES + 2 * NBUF;
+  static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + STG_BYTES + 1024 + OFF_BYTES;
+  static_assert(STAGES >= 2 && A_STAGES >= 2, "tile does not fit the SM");
+  static_assert(8 * NBAR + 24 <= 1024, "control block overflow");
 };
 
-template <int BN>
+__device__ __forceinline__ void umma_tf32_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t b,
+                                                 uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10,"
+      " %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28,"
+      " %29, %30, %31, %32};" ::"r"(taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]),
+      "f"(v[8]), "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]),
+      "f"(v[15]), "f"(v[16]), "f"(v[17]), "f"(v[18]), "f"(v[19]), "f"(v[20]), "f"(v[21]),
+      "f"(v[22]), "f"(v[23]), "f"(v[24]), "f"(v[25]), "f"(v[26]), "f"(v[27]), "f"(v[28]),
+      "f"(v[29]), "f"(v[30]), "f"(v[31])
+      : "memory");
+}
+
+// Nearest TF32 (ties away from zero) of a finite x: add half a TF32 unit to
+// the magnitude bits and clear the 13 dropped ones (a carry moves into the
+// exponent, as rounding up to the next binade should).
+__device__ __forceinline__ float tf32_rna_bits(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// x = head + tail (both TF32); a NaN stays the head (Inf gives a NaN tail)
+__device__ __forceinline__ void tf32_split(float x, float& head, float& tail) {
+  head = (x == x) ? tf32_rna_bits(x) : x;
+  tail = tf32_rna_bits(x - head);
+}
+
+template <int BN, int NBUF>
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_tf32x3_kernel(const __grid_constant__ CUtensorMap tmA,
                      const __grid_constant__ CUtensorMap tmB, const TcArgs args) {
-  using C = Cfg<BN>;
-  constexpr int S = C::STAGES;
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* base = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  unsigned char* tiles = base;
-  unsigned char* ctrl = base + S * C::STAGE_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(ctrl);        // full[S], conv[S], empty[S], accf
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ctrl + 8 * (3 * S + 1));
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(ctrl + 8 * (3 * S + 1) + 8);
-  long long* col_off = reinterpret_cast<long long*>(ctrl + 1024);
-  long long* col_off32 = col_off + BN;
-
-  auto xA = [&](int s) { return tiles + s * C::STAGE_BYTES; };
-  auto loA = [&](int s) { return tiles + s * C::STAGE_BYTES + C::A_BYTES; };
-  auto xB = [&](int s) { return tiles + s * C::STAGE_BYTES + 2 * C::A_BYTES; };
-  auto loB = [&](int s) { return tiles + s * C::STAGE_BYTES + 2 * C::A_BYTES + C::B_BYTES; };
-  const uint32_t full0 = smem_u32(&bars[0]), conv0 = smem_u32(&bars[S]),
-                 empty0 = smem_u32(&bars[2 * S]), accf = smem_u32(&bars[3 * S]);
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long m0 = (long long)blockIdx.x * BM;
-  const int n0 = blockIdx.y * BN;
-  const int z = blockIdx.z / args.ksplit, kz = blockIdx.z % args.ksplit;
-  int issued = 0;   // TMA k-blocks issued (producer lane only)
-  const int nkb_all = (int)((args.K + BK - 1) / BK);
-  const int kb0 = kz * args.kb_per_split;
-  const int nkb = max(0, min(nkb_all - kb0, args.kb_per_split));
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(full0 + 8 * s, 1);
-      mbar_init(conv0 + 8 * s, 4);
-      mbar_init(empty0 + 8 * s, 1);
-    }
-    mbar_init(accf, 1);
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(C::TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *tmem_slot;
-
-  if (warp == 0) {
-    // ---------------- TMA producer ----------------
-    if (lane == 0) {
-      const int za = args.a_batched ? z : 0, zb = args.b_batched ? z : 0;
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % S;
-        if (kb >= S && !mbar_wait(empty0 + 8 * s, ((kb / S) - 1) & 1, abort_flag, args.err)) break;
-        mbar_arrive_expect_tx(full0 + 8 * s, C::A_BYTES + C::B_BYTES);
-        tma_load(smem_u32(xA(s)), &tmA, (kb0 + kb) * BK, (int)m0, za, full0 + 8 * s);
-        tma_load(smem_u32(xB(s)), &tmB, (kb0 + kb) * BK, n0, zb, full0 + 8 * s);
-        issued = kb + 1;
-      }
-    }
-  } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------
-    if (lane == 0) {
-      constexpr uint32_t idesc = idesc_tf32(BM, BN);
-      bool ok = true;
-      for (int kb = 0; kb < nkb && ok; ++kb) {
-        const int s = kb % S;
-        ok = mbar_wait(conv0 + 8 * s, (kb / S) & 1, abort_flag, args.err);
-        if (!ok) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t ah = smem_u32(xA(s)), al = smem_u32(loA(s));
-        const uint32_t bh = smem_u32(xB(s)), bl = smem_u32(loB(s));
-        // head*head into the main accumulator; the two head*tail terms into
-        // a separate one, so that the tensor core's truncating accumulation
-        // never adds ~2^-11-sized terms to the large running sum
-#pragma unroll
-        for (int ks = 0; ks < BK / 8; ++ks) {
-          const uint32_t off = ks * 32;   // 8 TF32 = 32 bytes along K
-          const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
-          umma_tf32(tmem, desc_sw128(ah + off), desc_sw128(bh + off), idesc, acc);
-          umma_tf32(tmem + C::HALF, desc_sw128(ah + off), desc_sw128(bl + off), idesc, acc);
-          umma_tf32(tmem + C::HALF, desc_sw128(al + off), desc_sw128(bh + off), idesc, 1u);
-        }
-        umma_commit(empty0 + 8 * s);
-      }
-      umma_commit(accf);
-    }
-  } else {
-    // ---------------- converters (warps 2..5) ----------------
-    const int t = threadIdx.x - 64;   // 0..127
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % S;
-      if (!mbar_wait(full0 + 8 * s, (kb / S) & 1, abort_flag, args.err)) break;
-      float4* xa = reinterpret_cast<float4*>(xA(s));
-      float4* la = reinterpret_cast<float4*>(loA(s));
-#pragma unroll
-      for (int i = 0; i < (BM * BK / 4) / 128; ++i) {
-        const int idx = t + 128 * i;
-        float4 v = xa[idx], h, l;
-        h.x = tf32_head(v.x); h.y = tf32_head(v.y); h.z = tf32_head(v.z); h.w = tf32_head(v.w);
-        l.x = v.x - h.x; l.y = v.y - h.y; l.z = v.z - h.z; l.w = v.w - h.w;
-        xa[idx] = h;
-        la[idx] = l;
-      }
-      float4* xb = reinterpret_cast<float4*>(xB(s));
-      float4* lb = reinterpret_cast<float4*>(loB(s));
-      for (int idx = t; idx < BN * BK / 4; idx += 128) {
-        float4 v = xb[idx], h, l;
-        h.x = tf32_head(v.x); h.y = tf32_head(v.y); h.z = tf32_head(v.z); h.w = tf32_head(v.w);
-        l.x = v.x - h.x; l.y = v.y - h.y; l.z = v.z - h.z; l.w = v.w - h.w;
-        xb[idx] = h;
-        lb[idx] = l;
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(conv0 + 8 * s);
-    }
-    // ---------------- epilogue ----------------
-    for (int j = t; j < BN; j += 128) {
-      const long long n = (long long)n0 + j;
-      col_off[j] = (n < args.N) ? map_off(args.c_n, n) : 0;
-      if (args.C32) col_off32[j] = (n < args.N) ? map_off(args.c32_n, n) : 0;
-    }
-    asm volatile("bar.sync 1, 128;" ::: "memory");
-    const bool ok = mbar_wait(accf, 0, abort_flag, args.err);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
-      const int q = warp & 3;                 // TMEM lane quarter of this warp
-      const int row = q * 32 + lane;
-      const long long m = (long long)m0 + row;
-      const bool mvalid = m < args.M;
-      const bool split = args.ksplit > 1 || args.partials_only;
-      const long long base_off =
-          split ? (((long long)z * args.ksplit + kz) * args.M + (mvalid ? m : 0)) * args.N
-                : map_off(args.c_b, z) + (mvalid ? map_off(args.c_m, m) : 0);
-      const long long row32 = (args.C32 && mvalid) ? map_off(args.c32_m, m) : 0;
-      const bool col_unit = args.c_n.nd > 0 && args.c_n.str[0] == 1;
-#pragma unroll 1
-      for (int c = 0; c < (BN + 31) / 32; ++c) {
-        float v[32], w[32];
-        const uint32_t ta = tmem + (static_cast<uint32_t>(q * 32) << 16) + c * 32;
-        tmem_ld32(ta, v);
-        tmem_ld32(ta + C::HALF, w);
-        if (!split && !args.c_fp64 && args.beta == 0.0 && col_unit) {
-          // FP32 output whose lowest column digit has unit stride: the 32 x 32
-          // chunk goes through shared memory (the idle pipeline buffers: every
-          // MMA has completed) and is written with the lanes along the columns
-          float* stg = reinterpret_cast<float*>(tiles) + (warp & 3) * (32 * 33);
-          const float al = static_cast<float>(args.alpha);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = al * (v[j] + w[j]);
-          __syncwarp();
-          const int jj = c * 32 + lane;
-          const bool cvalid = jj < BN && (long long)n0 + jj < args.N;
-          const long long co = cvalid ? col_off[jj] : 0;
-          float* outp = static_cast<float*>(args.C);
-          for (int rr = 0; rr < 32; ++rr) {
-            const long long bo = __shfl_sync(0xffffffffu, base_off, rr);
-            const int valid_r = __shfl_sync(0xffffffffu, mvalid ? 1 : 0, rr);
-            if (valid_r && cvalid) outp[bo + co] = stg[rr * 33 + lane];
-          }
-          __syncwarp();
-          continue;
-        }
-        if (!mvalid) continue;
-        if (split) {
-          float* p = args.part + base_off + n0 + c * 32;
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int jj = c * 32 + j;
-            if (jj < BN && (long long)n0 + jj < args.N) p[j] = v[j] + w[j];
-          }
-          continue;
-        }
-        // all loads of the old values first (they would otherwise wait on
-        // the stores before them), then the results
-        const int nv = min(32, min(BN - c * 32, (int)(args.N - n0 - c * 32)));
-        if (!args.c_fp64) {
-          // FP32 output: FP32 arithmetic (B300's FP64 pipe would otherwise
-          // bound the epilogue)
-          const float al = static_cast<float>(args.alpha), be = static_cast<float>(args.beta);
-          float* p = static_cast<float*>(args.C) + base_off;
-          float o[32];
-          if (be != 0.f) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) o[j] = (j < nv) ? p[col_off[c * 32 + j]] : 0.f;
-          }
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            float r = al * (v[j] + w[j]);
-            if (be != 0.f) r = fmaf(be, o[j], r);
-            if (j < nv) p[col_off[c * 32 + j]] = r;
-          }
-          continue;
-        }
-        double r[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) r[j] = args.alpha * static_cast<double>(v[j] + w[j]);
-        if (args.beta != 0.0) {
-          double old[32];
-          const double* p = static_cast<const double*>(args.C) + base_off;
-#pragma unroll
-          for (int j = 0; j < 32; ++j) old[j] = (j < nv) ? p[col_off[c * 32 + j]] : 0.0;
-#pragma unroll
-          for (int j = 0; j < 32; ++j) r[j] = fma(args.beta, old[j], r[j]);
-        }
-        {
-          double* p = static_cast<double*>(args.C) + base_off;
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (j < nv) p[col_off[c * 32 + j]] = r[j];
-          if (args.C32) {
-            float* p32 = args.C32 + row32;
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (j < nv) p32[col_off32[c * 32 + j]] = static_cast<float>(r[j]);
-          }
-        }
-      }
-    }
-  }
-  // teardown: the TMEM owner frees the accumulator after everyone is done
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (*abort_flag && warp == 0 && lane == 0) {
-    // drain TMA copies that may still be in flight before the CTA exits:
-    // wait (bounded) for the last issued use of every stage
-    for (int kb = (issued > S ? issued - S : 0); kb < issued; ++kb)
-      for (uint32_t i = 0; i < (1u << 20); ++i)
-        if (mbar_try_wait(full0 + 8 * (kb % S), (kb / S) & 1)) break;
-  }
-  __syncthreads();
-  if (warp == 1) {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(C::TMEM_COLS)
-                 : "memory");
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Persistent variant (BN <= 128): one CTA per SM walks the output tiles; the
-// TMEM accumulator pair is double buffered so that four dedicated epilogue
-// warps drain tile i while the MMA warp already accumulates tile i + 1, and
-// the TMA / converter ring runs on across tile boundaries.
-//
-// Warps (320 threads): 0 = TMA producer, 1 = TMEM owner + MMA issuer,
-// 2..5 = converters, 6..9 = epilogue (warp w reads TMEM lane quarter w % 4).
-// ---------------------------------------------------------------------------
-constexpr int NTHREADS_P = 320;
-
-template <int BN>
-struct CfgP {
-  static constexpr int A_BYTES = BM * BK * 4;
-  static constexpr int B_BYTES = BN * BK * 4;
-  static constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);
-  static constexpr int STG_BYTES = 4 * 32 * 33 * 4;                 // epilogue staging
-  // as many ring stages as fit the 227 KB opt-in limit next to the rest
-  static constexpr int STAGES =
-      std::min(4, (232448 - 2048 - STG_BYTES - 2 * BN * 8) / STAGE_BYTES);
-  static constexpr int HALF = BN <= 32 ? 32 : BN <= 64 ? 64 : 128;
-  static constexpr int TMEM_COLS = 4 * HALF;                        // 2 buffers x (main, corr)
-  static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + STG_BYTES + 1024 + 2 * BN * 8;
-};
-
-template <int BN>
-__global__ void __launch_bounds__(NTHREADS_P, 1)
-    tc_tf32x3_persist(const __grid_constant__ CUtensorMap tmA,
-                      const __grid_constant__ CUtensorMap tmB, const TcArgs args) {
-  using C = CfgP<BN>;
-  static_assert(BN <= 128, "double-buffered accumulators need BN <= 128");
-  constexpr int S = C::STAGES;
+  using C = Cfg<BN, NBUF>;
+  constexpr int S = C::STAGES, AS = C::A_STAGES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   unsigned char* tiles = base;
   float* stg_all = reinterpret_cast<float*>(base + S * C::STAGE_BYTES);
   unsigned char* ctrl = base + S * C::STAGE_BYTES + C::STG_BYTES;
-  // full[S], conv[S], empty[S], accf[2], acce[2]
+  // full[S], conv[S], empty[S], tfree[AS], accf[NBUF], acce[NBUF]
   uint64_t* bars = reinterpret_cast<uint64_t*>(ctrl);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ctrl + 8 * (3 * S + 4));
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(ctrl + 8 * (3 * S + 4) + 8);
-  volatile int* epi_stop = reinterpret_cast<volatile int*>(ctrl + 8 * (3 * S + 4) + 16);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ctrl + 8 * C::NBAR);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(ctrl + 8 * C::NBAR + 8);
+  volatile int* epi_stop = reinterpret_cast<volatile int*>(ctrl + 8 * C::NBAR + 16);
   long long* col_off = reinterpret_cast<long long*>(ctrl + 1024);
   long long* col_off32 = col_off + BN;
+  long long* row_off = col_off32 + BN;
+  long long* row_off32 = row_off + BM;
 
   auto xA = [&](int s) { return tiles + s * C::STAGE_BYTES; };
-  auto loA = [&](int s) { return tiles + s * C::STAGE_BYTES + C::A_BYTES; };
-  auto xB = [&](int s) { return tiles + s * C::STAGE_BYTES + 2 * C::A_BYTES; };
-  auto loB = [&](int s) { return tiles + s * C::STAGE_BYTES + 2 * C::A_BYTES + C::B_BYTES; };
+  auto xB = [&](int s) { return tiles + s * C::STAGE_BYTES + C::A_BYTES; };
+  auto loB = [&](int s) { return tiles + s * C::STAGE_BYTES + C::A_BYTES + C::B_BYTES; };
   const uint32_t full0 = smem_u32(&bars[0]), conv0 = smem_u32(&bars[S]),
-                 empty0 = smem_u32(&bars[2 * S]), accf0 = smem_u32(&bars[3 * S]),
-                 acce0 = smem_u32(&bars[3 * S + 2]);
+                 empty0 = smem_u32(&bars[2 * S]), tfree0 = smem_u32(&bars[3 * S]),
+                 accf0 = smem_u32(&bars[3 * S + AS]), acce0 = smem_u32(&bars[3 * S + AS + NBUF]);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long mt = (args.M + BM - 1) / BM, nt = (args.N + BN - 1) / BN;
   const long long zt = (long long)args.batch * args.ksplit;
   const long long ntiles = mt * nt * zt;
   const int nkb_all = (int)((args.K + BK - 1) / BK);
-  // tile t -> (z, kz, m0, n0), n fastest
+  // tile t -> (z, kz, m0, n0), n fastest (neighbouring CTAs share A rows in L2)
   auto tile_of = [&](long long t, int& z, int& kz, long long& m0, int& n0, int& nkb, int& kb0) {
     const long long tn = t % nt, tm = (t / nt) % mt, tz = t / (nt * mt);
     z = (int)(tz / args.ksplit);
@@ -474,10 +452,11 @@ __global__ void __launch_bounds__(NTHREADS_P, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(full0 + 8 * s, 1);
-      mbar_init(conv0 + 8 * s, 4);
+      mbar_init(conv0 + 8 * s, NCONV);
       mbar_init(empty0 + 8 * s, 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int s = 0; s < AS; ++s) mbar_init(tfree0 + 8 * s, 1);
+    for (int b = 0; b < NBUF; ++b) {
       mbar_init(accf0 + 8 * b, 1);
       mbar_init(acce0 + 8 * b, 4);
     }
@@ -531,34 +510,41 @@ __global__ void __launch_bounds__(NTHREADS_P, 1)
         int z, kz, n0, nkb, kb0;
         long long m0;
         tile_of(t, z, kz, m0, n0, nkb, kb0);
-        const int ab = it & 1;
-        // the epilogue must have drained this accumulator buffer (use it - 2)
-        if (it >= 2 && !mbar_wait(acce0 + 8 * ab, ((it >> 1) - 1) & 1, abort_flag, args.err)) break;
+        const int ab = it % NBUF;
+        // the epilogue must have drained this accumulator buffer (use it - NBUF)
+        if (it >= NBUF &&
+            !mbar_wait(acce0 + 8 * ab, ((it / NBUF) - 1) & 1, abort_flag, args.err))
+          break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t dmain = tmem + ab * 2 * C::HALF, dcorr = dmain + C::HALF;
         for (int kb = 0; kb < nkb; ++kb, ++kbg) {
-          const int s = kbg % S;
+          const int s = kbg % S, sa = kbg % AS;
           ok = mbar_wait(conv0 + 8 * s, (kbg / S) & 1, abort_flag, args.err);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t ah = smem_u32(xA(s)), al = smem_u32(loA(s));
+          const uint32_t ah = tmem + C::A_COL0 + sa * 64, al = ah + 32;
           const uint32_t bh = smem_u32(xB(s)), bl = smem_u32(loB(s));
+          // head*head into the main accumulator; the two head*tail terms into
+          // a separate one, so that the tensor core's truncating accumulation
+          // never adds ~2^-11-sized terms to the large running sum
 #pragma unroll
           for (int ks = 0; ks < BK / 8; ++ks) {
-            const uint32_t off = ks * 32;
             const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
-            umma_tf32(dmain, desc_sw128(ah + off), desc_sw128(bh + off), idesc, acc);
-            umma_tf32(dcorr, desc_sw128(ah + off), desc_sw128(bl + off), idesc, acc);
-            umma_tf32(dcorr, desc_sw128(al + off), desc_sw128(bh + off), idesc, 1u);
+            umma_tf32_tmem_a(dmain, ah + ks * 8, desc_sw128(bh + ks * 32), idesc, acc);
+            umma_tf32_tmem_a(dcorr, ah + ks * 8, desc_sw128(bl + ks * 32), idesc, acc);
+            umma_tf32_tmem_a(dcorr, al + ks * 8, desc_sw128(bh + ks * 32), idesc, 1u);
           }
-          umma_commit(empty0 + 8 * s);
+          umma_commit(empty0 + 8 * s);    // shared-memory stage free
+          umma_commit(tfree0 + 8 * sa);   // tensor-memory A stage free
         }
         if (ok) umma_commit(accf0 + 8 * ab);
       }
     }
-  } else if (warp < 6) {
+  } else if (warp < 2 + NCONV) {
     // ---------------- converters (warps 2..5) ----------------
-    const int t4 = threadIdx.x - 64;   // 0..127
+    const int tc = threadIdx.x - 64;            // 0..127
+    const int q = warp & 3;                     // TMEM lane quarter
+    const int row = q * 32 + lane;              // A row = TMEM lane
     int kbg = 0;
     bool ok = true;
     for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -566,149 +552,89 @@ __global__ void __launch_bounds__(NTHREADS_P, 1)
       long long m0;
       tile_of(t, z, kz, m0, n0, nkb, kb0);
       for (int kb = 0; kb < nkb; ++kb, ++kbg) {
-        const int s = kbg % S;
-        if (!mbar_wait(full0 + 8 * s, (kbg / S) & 1, abort_flag, args.err)) {
+        const int s = kbg % S, sa = kbg % AS;
+        ok = mbar_wait(full0 + 8 * s, (kbg / S) & 1, abort_flag, args.err);
+        if (!__all_sync(0xffffffffu, ok)) {
           ok = false;
           break;
         }
-        float4* xa = reinterpret_cast<float4*>(xA(s));
-        float4* la = reinterpret_cast<float4*>(loA(s));
-#pragma unroll
-        for (int i = 0; i < (BM * BK / 4) / 128; ++i) {
-          const int idx = t4 + 128 * i;
-          float4 v = xa[idx], h, l;
-          h.x = tf32_head(v.x); h.y = tf32_head(v.y); h.z = tf32_head(v.z); h.w = tf32_head(v.w);
-          l.x = v.x - h.x; l.y = v.y - h.y; l.z = v.z - h.z; l.w = v.w - h.w;
-          xa[idx] = h;
-          la[idx] = l;
-        }
+        // B: head in place, tail plane in the same swizzled layout
         float4* xb = reinterpret_cast<float4*>(xB(s));
         float4* lb = reinterpret_cast<float4*>(loB(s));
-        for (int idx = t4; idx < BN * BK / 4; idx += 128) {
-          float4 v = xb[idx], h, l;
-          h.x = tf32_head(v.x); h.y = tf32_head(v.y); h.z = tf32_head(v.z); h.w = tf32_head(v.w);
-          l.x = v.x - h.x; l.y = v.y - h.y; l.z = v.z - h.z; l.w = v.w - h.w;
-          xb[idx] = h;
-          lb[idx] = l;
+#pragma unroll 2
+        for (int idx = tc; idx < BN * BK / 4; idx += 32 * NCONV) {
+          const float4 v = xb[idx];
+          float4 hd, tl;
+          tf32_split(v.x, hd.x, tl.x);
+          tf32_split(v.y, hd.y, tl.y);
+          tf32_split(v.z, hd.z, tl.z);
+          tf32_split(v.w, hd.w, tl.w);
+          xb[idx] = hd;
+          lb[idx] = tl;
         }
+        // this thread's A row: 16-byte chunk c of row r sits at chunk c ^ (r % 8)
+        float hv[32], tv[32];
+        const unsigned char* ar = xA(s) + (row >> 3) * 1024 + (row & 7) * 128;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const float4 v = *reinterpret_cast<const float4*>(ar + ((c ^ (row & 7)) << 4));
+          hv[4 * c] = v.x; hv[4 * c + 1] = v.y; hv[4 * c + 2] = v.z; hv[4 * c + 3] = v.w;
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) tf32_split(hv[i], hv[i], tv[i]);
+        // the MMAs of the K block that used this TMEM stage last must be done;
+        // the warp proceeds (tcgen05.st is warp-collective) only if every lane saw it
+        if (kbg >= AS) ok = mbar_wait(tfree0 + 8 * sa, ((kbg / AS) - 1) & 1, abort_flag, args.err);
+        if (!__all_sync(0xffffffffu, ok)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ta = tmem + (static_cast<uint32_t>(q * 32) << 16) + C::A_COL0 + sa * 64;
+        tmem_st32(ta, hv);
+        tmem_st32(ta + 32, tv);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(conv0 + 8 * s);
       }
     }
   } else {
     // ---------------- epilogue (warps 6..9) ----------------
-    const int te = threadIdx.x - 192;   // 0..127
+    const int te = threadIdx.x - 64 - 32 * NCONV;   // 0..127
     const int q = warp & 3;             // TMEM lane quarter of this warp
     float* stg = stg_all + q * (32 * 33);
-    const bool col_unit = args.c_n.nd > 0 && args.c_n.str[0] == 1;
-    const bool split = args.ksplit > 1 || args.partials_only;
     int it = 0;
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
       int z, kz, n0, nkb, kb0;
       long long m0;
       tile_of(t, z, kz, m0, n0, nkb, kb0);
-      const int ab = it & 1;
+      const int ab = it % NBUF;
       asm volatile("bar.sync 2, 128;" ::: "memory");   // previous tile's offsets are dead
-      for (int j = te; j < BN; j += 128) {
-        const long long n = (long long)n0 + j;
-        col_off[j] = (n < args.N) ? map_off(args.c_n, n) : 0;
-        if (args.C32) col_off32[j] = (n < args.N) ? map_off(args.c32_n, n) : 0;
-      }
+      epi_offsets(args, BN, te, m0, n0, z, kz, col_off, col_off32, row_off, row_off32);
       asm volatile("bar.sync 2, 128;" ::: "memory");
       // a failed wait stops all four epilogue warps together: the flag is
       // written only before the barrier below and read only after it
-      if (!mbar_wait(accf0 + 8 * ab, (it >> 1) & 1, abort_flag, args.err) && lane == 0)
+      if (!mbar_wait(accf0 + 8 * ab, (it / NBUF) & 1, abort_flag, args.err) && lane == 0)
         *epi_stop = 1;
       asm volatile("bar.sync 2, 128;" ::: "memory");
       if (*epi_stop) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int row = q * 32 + lane;
-      const long long m = m0 + row;
-      const bool mvalid = m < args.M;
-      const long long base_off =
-          split ? (((long long)z * args.ksplit + kz) * args.M + (mvalid ? m : 0)) * args.N
-                : map_off(args.c_b, z) + (mvalid ? map_off(args.c_m, m) : 0);
-      const long long row32 = (args.C32 && mvalid) ? map_off(args.c32_m, m) : 0;
-      const uint32_t dmain = tmem + ab * 2 * C::HALF;
-#pragma unroll 1
-      for (int c = 0; c < (BN + 31) / 32; ++c) {
-        float v[32], w[32];
-        const uint32_t ta = dmain + (static_cast<uint32_t>(q * 32) << 16) + c * 32;
-        tmem_ld32(ta, v);
-        tmem_ld32(ta + C::HALF, w);
-        const int nv = min(32, min(BN - c * 32, (int)(args.N - n0 - c * 32)));
-        if (!split && !args.c_fp64 && args.beta == 0.0 && col_unit) {
-          const float al = static_cast<float>(args.alpha);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = al * (v[j] + w[j]);
-          __syncwarp();
-          const bool cvalid = lane < nv;
-          const long long co = cvalid ? col_off[c * 32 + lane] : 0;
-          float* outp = static_cast<float*>(args.C);
-          for (int rr = 0; rr < 32; ++rr) {
-            const long long bo = __shfl_sync(0xffffffffu, base_off, rr);
-            const int valid_r = __shfl_sync(0xffffffffu, mvalid ? 1 : 0, rr);
-            if (valid_r && cvalid) outp[bo + co] = stg[rr * 33 + lane];
-          }
-          __syncwarp();
-          continue;
-        }
-        if (!mvalid) continue;
-        if (split) {
-          float* p = args.part + base_off + n0 + c * 32;
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (j < nv) p[j] = v[j] + w[j];
-          continue;
-        }
-        if (!args.c_fp64) {
-          const float al = static_cast<float>(args.alpha), be = static_cast<float>(args.beta);
-          float* p = static_cast<float*>(args.C) + base_off;
-          float o[32];
-          if (be != 0.f) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) o[j] = (j < nv) ? p[col_off[c * 32 + j]] : 0.f;
-          }
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            float r = al * (v[j] + w[j]);
-            if (be != 0.f) r = fmaf(be, o[j], r);
-            if (j < nv) p[col_off[c * 32 + j]] = r;
-          }
-          continue;
-        }
-        double r[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) r[j] = args.alpha * static_cast<double>(v[j] + w[j]);
-        double* p = static_cast<double*>(args.C) + base_off;
-        if (args.beta != 0.0) {
-          double old[32];
-#pragma unroll
-          for (int j = 0; j < 32; ++j) old[j] = (j < nv) ? p[col_off[c * 32 + j]] : 0.0;
-#pragma unroll
-          for (int j = 0; j < 32; ++j) r[j] = fma(args.beta, old[j], r[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (j < nv) p[col_off[c * 32 + j]] = r[j];
-        if (args.C32) {
-          float* p32 = args.C32 + row32;
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (j < nv) p32[col_off32[c * 32 + j]] = static_cast<float>(r[j]);
-        }
-      }
-      // this accumulator buffer may be overwritten by tile it + 2
+      epi_rows<BN>(args, tmem + ab * 2 * C::HALF, C::HALF, q, lane, m0, n0, stg, col_off,
+                   col_off32, row_off, row_off32);
+      // this accumulator buffer may be overwritten by tile it + NBUF
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(acce0 + 8 * ab);
     }
   }
-  // teardown: the TMEM owner frees the accumulators after everyone is done
+  // teardown: the TMEM owner frees tensor memory after everyone is done
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (*abort_flag && warp == 0 && lane == 0) {
+    // drain TMA copies that may still be in flight before the CTA exits:
+    // wait (bounded) for the last issued use of every stage
     for (int kb = (issued > S ? issued - S : 0); kb < issued; ++kb)
       for (uint32_t i = 0; i < (1u << 20); ++i)
         if (mbar_try_wait(full0 + 8 * (kb % S), (kb / S) & 1)) break;
@@ -722,26 +648,36 @@ __global__ void __launch_bounds__(NTHREADS_P, 1)
   }
 }
 
-// out(b,m,n) = alpha * sum_z part[b][z][m][n] + beta * out: FP64 sums in a
-// fixed order (four interleaved partial sums, then their pairwise sum)
+// out(b,m,n) = alpha * sum_z part[b][z][m][n] + beta * out.  The partials are
+// added in a fixed order (z = 0, 1, ...) by compensated FP32 arithmetic
+// (TwoSum per term, Knuth): sh + se carries the sum to ~2^-48 of its
+// magnitude, like an FP64 sum, at FP32 speed (B300's FP64 pipe would bound
+// this pass).  I: the flat index type (32-bit whenever batch*M*N fits).
+__device__ __forceinline__ void two_sum_add(float& sh, float& se, float x) {
+  const float t = sh + x;
+  const float bp = t - sh;
+  se += (sh - (t - bp)) + (x - bp);
+  sh = t;
+}
+
+template <typename I>
 __global__ void tc_splitk_reduce(const TcArgs a, int batch) {
-  const long long MN = a.M * a.N;
-  const long long tot = MN * batch;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long b = e / MN, r = e % MN, m = r / a.N, n = r % a.N;
-    const float* p = a.part + b * a.ksplit * MN + r;
-    // compensated FP32 sum (TwoSum per term, Knuth): s + c carries the sum of
-    // the partials to ~2^-48 of their magnitude, like an FP64 sum, at FP32
-    // speed (B300's FP64 pipe would bound this pass)
+  const I N = static_cast<I>(a.N), MN = static_cast<I>(a.M) * N, tot = MN * static_cast<I>(batch);
+  const int kz = a.ksplit;
+  for (I e = static_cast<I>(blockIdx.x) * blockDim.x + threadIdx.x; e < tot;
+       e += static_cast<I>(gridDim.x) * blockDim.x) {
+    const I b = e / MN, r = e - b * MN, m = r / N, n = r - m * N;
+    const float* p = a.part + (long long)b * kz * (long long)MN + r;
     float sh = 0.f, se = 0.f;
-    for (int z = 0; z < a.ksplit; ++z) {
-      const float x = p[(long long)z * MN];
-      const float t = sh + x;
-      const float bp = t - sh;
-      se += (sh - (t - bp)) + (x - bp);
-      sh = t;
+    int z = 0;
+    for (; z + 4 <= kz; z += 4) {
+      float x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[u] = __ldcg(p + (long long)(z + u) * MN);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) two_sum_add(sh, se, x[u]);
     }
+    for (; z < kz; ++z) two_sum_add(sh, se, __ldcg(p + (long long)z * MN));
     const double acc = static_cast<double>(sh) + static_cast<double>(se);
     const long long off = map_off(a.c_b, b) + map_off(a.c_m, m) + map_off(a.c_n, n);
     double v = a.alpha * acc;
@@ -799,17 +735,13 @@ bool make_map(CUtensorMap* tm, const TcOperand& op, int box_rows) {
   return r == CUDA_SUCCESS;
 }
 
-template <int BN, bool PERSIST>
+template <int BN, int NBUF>
 cudaError_t launch_bn(const TcGemm& g, cudaStream_t s) {
-  const int smem_bytes = PERSIST ? CfgP<BN>::SMEM : Cfg<BN>::SMEM;
+  using C = Cfg<BN, NBUF>;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = PERSIST ? cudaFuncSetAttribute(tc_tf32x3_persist<BN <= 128 ? BN : 128>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   smem_bytes)
-                            : cudaFuncSetAttribute(tc_tf32x3_kernel<BN>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   smem_bytes);
+    cudaError_t e = cudaFuncSetAttribute(tc_tf32x3_kernel<BN, NBUF>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
@@ -868,20 +800,19 @@ cudaError_t launch_bn(const TcGemm& g, cudaStream_t s) {
   a.c32_n = g.c32_n;
   if ((long long)std::max(1, g.batch) * ksplit > 65535) return cudaErrorInvalidValue;
   a.batch = std::max(1, g.batch);
-  if (PERSIST) {
-    const long long ntiles = ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN) * a.batch * ksplit;
-    const unsigned grid = (unsigned)std::min<long long>(ntiles, nsm);
-    tc_tf32x3_persist<BN <= 128 ? BN : 128><<<grid, NTHREADS_P, smem_bytes, s>>>(ta, tb, a);
-  } else {
-    dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + BN - 1) / BN),
-              (unsigned)(std::max(1, g.batch) * ksplit));
-    tc_tf32x3_kernel<BN><<<grid, NTHREADS, smem_bytes, s>>>(ta, tb, a);
-  }
+  // NBUF = 2: one CTA per SM walks the tiles; NBUF = 1: one tile per CTA
+  const long long ntiles = ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN) * a.batch * ksplit;
+  if (ntiles > (1ll << 31) - 1) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)(NBUF == 2 ? std::min<long long>(ntiles, nsm) : ntiles);
+  tc_tf32x3_kernel<BN, NBUF><<<grid, NTHREADS, C::SMEM, s>>>(ta, tb, a);
   note_launch();
   if (ksplit > 1 && !g.partials_only) {
     const long long tot = g.M * g.N * std::max(1, g.batch);
-    tc_splitk_reduce<<<(unsigned)std::min<long long>((tot + 255) / 256, 4096), 256, 0, s>>>(
-        a, std::max(1, g.batch));
+    const unsigned blocks = (unsigned)std::min<long long>((tot + 255) / 256, 4096);
+    if (tot < (1ll << 31))
+      tc_splitk_reduce<unsigned><<<blocks, 256, 0, s>>>(a, std::max(1, g.batch));
+    else
+      tc_splitk_reduce<unsigned long long><<<blocks, 256, 0, s>>>(a, std::max(1, g.batch));
     note_launch();
   }
   return cudaGetLastError();
@@ -893,17 +824,23 @@ cudaError_t gemm_tc(const TcGemm& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
   if (g.A.rows < 1 || g.B.rows < 1 || g.A.K != g.K || g.B.K != g.K) return cudaErrorInvalidValue;
   if (g.batch > 65535 || g.M > (1ll << 31) - BM) return cudaErrorInvalidValue;
-  // the persistent kernel (double-buffered accumulators, BN <= 128) except
-  // for 128 < N <= 256, where one wider tile avoids re-reading A per N tile
+  // double-buffered accumulators up to 96 columns per tile (tensor memory
+  // holds 2 x (main, correction) x 96 columns next to two A stages); N in
+  // (96, 128] as two 64-column tiles (short-K streams, whose epilogue must
+  // overlap); N in (128, 192] as one single-buffered tile (A is staged once
+  // per row block).
+  // Wider N: 192-column single-buffered tiles when K is long enough for the
+  // main loop to dwarf the exposed epilogue (half the operand traffic and
+  // conversions per output of 96-column tiles), else 96-column tiles whose
+  // epilogue overlaps the next tile.
   const long long N = g.N;
-  if (N <= 32) return launch_bn<32, true>(g, s);
-  if (N <= 48) return launch_bn<48, true>(g, s);
-  if (N <= 64) return launch_bn<64, true>(g, s);
-  if (N <= 80) return launch_bn<80, true>(g, s);
-  if (N <= 128) return launch_bn<128, true>(g, s);
-  if (N <= 144) return launch_bn<144, false>(g, s);
-  if (N <= 256) return launch_bn<256, false>(g, s);
-  return launch_bn<128, true>(g, s);
+  if (N <= 32) return launch_bn<32, 2>(g, s);
+  if (N <= 64) return launch_bn<64, 2>(g, s);
+  if (N <= 96) return launch_bn<96, 2>(g, s);
+  if (N <= 128) return launch_bn<64, 2>(g, s);    // two double-buffered tiles
+  if (N <= 144) return launch_bn<144, 1>(g, s);
+  if (N <= 192 || g.K >= 512) return launch_bn<192, 1>(g, s);
+  return launch_bn<96, 2>(g, s);
 }
 
 }  // namespace qrctm

@@ -24,7 +24,8 @@ def q():
 @pytest.mark.parametrize("split_k", [False, True])
 @pytest.mark.parametrize("M,N,K", [(128, 32, 32), (128, 48, 36), (300, 80, 72), (257, 144, 100),
                                    (1000, 256, 144), (5184, 144, 5184), (4096, 36, 72),
-                                   (333, 300, 40)])
+                                   (333, 300, 40), (260, 100, 64), (700, 192, 96),
+                                   (200, 150, 40), (300, 400, 600), (130, 520, 1100)])
 def test_tf32x3_matches_fp64(q, M, N, K, split_k):
     import torch
     rng = np.random.default_rng(M * 7 + N * 3 + K)
