@@ -91,7 +91,8 @@ def panel_flops(d, D, chi, m=None):
 def load_traffic(precision, workload):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
     from the committed ncu capture summary of this precision and workload,
-    keyed by kernel name (empty when there is none)."""
+    keyed by step phase (first column; the kernel's name follows the bytes);
+    empty when there is none."""
     out = {}
     try:
         for line in open(os.path.join(ROOT, "profiles", f"traffic_{precision}_{workload}.txt")):
@@ -289,6 +290,26 @@ def phase_profile(ctx, one_step, steps):
     return phases, prof_ms
 
 
+def tc_kernel_name(N, K):
+    """Name of the tensor-core kernel instance the engine launches for an
+    N-column, K-deep product (the tile choice of gemm_tc)."""
+    if N <= 32:
+        bn = (32, 2)
+    elif N <= 64:
+        bn = (64, 2)
+    elif N <= 96:
+        bn = (96, 2)
+    elif N <= 128:
+        bn = (64, 2)
+    elif N <= 144:
+        bn = (144, 1)
+    elif N <= 192 or K >= 512:
+        bn = (192, 1)
+    else:
+        bn = (96, 2)
+    return f"tc_tf32x3_kernel<{bn[0]}, {bn[1]}>"
+
+
 def roofline_rows(kernels, phases, prof_ms, traffic):
     """One roofline entry per (phase -> single kernel): algorithmic flops per
     launch over its average CUDA-event duration."""
@@ -303,7 +324,7 @@ def roofline_rows(kernels, phases, prof_ms, traffic):
                     "unit": "TFLOP/s", "frac": ach / peak_k, "avg_launch_ms": avg * 1e3,
                     "launches": n_k, "share_of_step": ms_k / prof_ms,
                     "algorithmic_flops_per_launch": flops, "peak_source": note_k,
-                    "traffic": traffic.get(kname)}
+                    "traffic": traffic.get(ph)}
     return rows
 
 
@@ -735,12 +756,20 @@ def main():
     kernels = {"qr_panel": ("qr_panel_kernel", panel_flops(d, D, chi), "alu", FP64_PEAK_TFLOPS,
                             fp64_note)}
     if args.precision == "split":
+        m = chi * D * D
+        if D <= 6:
+            absorb = ("absorb_d6_k" if D == 6 else "absorb_fused_k", fl["absorb"], "alu",
+                      fp32_simt_peak(), "fp32 FMA nominal: 148 SMs x 128 FMA/clk x 2 x 2.032 GHz")
+        else:
+            # two tensor-core contractions of equal flops (ket: N = d D^2, K = D^2;
+            # bra: N = D^2, K = d D^2)
+            absorb = (tc_kernel_name(d * D * D, D * D) + " (ket), " +
+                      tc_kernel_name(D * D, d * D * D) + " (bra)", fl["absorb"] / 2, "tensor",
+                      tf32_peak, tf32_note)
         kernels.update({
-            "absorb": ("absorb_d6_k" if D == 6 else "absorb_fused_k", fl["absorb"], "alu",
-                       fp32_simt_peak(),
-                       "fp32 FMA nominal: 148 SMs x 128 FMA/clk x 2 x 2.032 GHz"),
-            "x1": ("tc_tf32x3_persist<128>", fl["x1"], "tensor", tf32_peak, tf32_note),
-            "project": ("tc_tf32x3_kernel<144>", fl["project"], "tensor", tf32_peak, tf32_note),
+            "absorb": absorb,
+            "x1": (tc_kernel_name(m, chi), fl["x1"], "tensor", tf32_peak, tf32_note),
+            "project": (tc_kernel_name(chi, m), fl["project"], "tensor", tf32_peak, tf32_note),
         })
     else:
         kernels.update({
