@@ -6,8 +6,9 @@
 // * Reflection symmetrisation and FP64 Frobenius normalisation of C and T
 //   after every step (a step the paper leaves implicit).
 // * Corner spectrum |eig(C)| in FP64 for the convergence test ("repeated
-//   until convergence"): Householder tridiagonalisation followed by Sturm
-//   bisection, one CTA.
+//   until convergence"): Householder tridiagonalisation (one thread-block
+//   cluster) followed by Sturm multisection, one CTA per eigenvalue (FP32
+//   rounds narrow the bracket, FP64 rounds finish it).
 #include "qrctm_internal.cuh"
 
 #include <algorithm>
@@ -200,21 +201,44 @@ __device__ double block_sum(double v, double* red, double* out) {
 //   p_0 = 1, p_1 = d_0 - x, p_i = (d_{i-1} - x) p_{i-1} - e2_{i-2} p_{i-2},
 // i.e. negative pivots of T - x I (Sylvester's inertia).  No divisions: the
 // pair (p_{i-1}, p_i) is rescaled by an exact power of two when the exponent
-// of p_i leaves [-400, 400]; an exact zero p_i is replaced by -pivmin p_{i-1}.
+// of p_i leaves [-400, 400], tested every fourth step (four steps raise the
+// exponent by at most 4 log2(3 ||T||): under 8 for the unit-norm corner), so
+// that the dependent chain of a step is one FMA; an exact zero p_i is
+// replaced by -pivmin p_{i-1}.
+__device__ __forceinline__ void sturm_step(double dx, double me2, double& pc, double& pm,
+                                           double pivmin, int& cnt) {
+  double pn = fma(dx, pc, me2 * pm);
+  if (((__double2hiint(pn) & 0x7fffffff) | __double2loint(pn)) == 0) pn = -pivmin * pc;
+  cnt += ((__double2hiint(pn) ^ __double2hiint(pc)) < 0);
+  pm = pc;
+  pc = pn;
+}
+
+__device__ __forceinline__ void sturm_rescale(double& pc, double& pm) {
+  const int ex = (int)((__double_as_longlong(pc) >> 52) & 0x7ff) - 1023;
+  if (ex > 400) { pc *= 0x1p-400; pm *= 0x1p-400; }
+  else if (ex < -400) { pc *= 0x1p400; pm *= 0x1p400; }
+}
+
 __device__ int sturm_count(const double* dg, const double* e2, int n, double x, double pivmin) {
   double pm = 1.0, pc = dg[0] - x;
   if ((__double_as_longlong(pc) << 1) == 0) pc = -pivmin;
   int cnt = (__double_as_longlong(pc) < 0);
-  for (int i = 1; i < n; ++i) {
-    double pn = fma(dg[i] - x, pc, -e2[i - 1] * pm);
-    if ((__double_as_longlong(pn) << 1) == 0) pn = -pivmin * pc;
-    const long long bn = __double_as_longlong(pn);
-    cnt += ((bn ^ __double_as_longlong(pc)) < 0);
-    pm = pc;
-    pc = pn;
-    const int ex = (int)((bn >> 52) & 0x7ff) - 1023;
-    if (ex > 400) { pc *= 0x1p-400; pm *= 0x1p-400; }
-    else if (ex < -400) { pc *= 0x1p400; pm *= 0x1p400; }
+  int i = 1;
+  for (; i + 4 <= n; i += 4) {
+    double dx[4], me2[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      dx[u] = dg[i + u] - x;
+      me2[u] = -e2[i + u - 1];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) sturm_step(dx[u], me2[u], pc, pm, pivmin, cnt);
+    sturm_rescale(pc, pm);
+  }
+  for (; i < n; ++i) {
+    sturm_step(dg[i] - x, -e2[i - 1], pc, pm, pivmin, cnt);
+    sturm_rescale(pc, pm);
   }
   return cnt;
 }
@@ -532,54 +556,213 @@ __global__ void __launch_bounds__(256) spectrum_cluster_kernel(const double* __r
   }
 }
 
-// Eigenvalue i of the tridiagonal (dg, e^2) by multisection: one CTA of
-// four warps per eigenvalue (one eigenvalue per SM: a single warp's Sturm
-// recurrence is bound by the FP64 latency, four fill the SM's FP64 pipe), the
-// 128 threads evaluate Sturm counts at 128 interior points of the current
-// bracket, which shrinks 129-fold per round (7 bits, against 5 bits for one
-// warp) until its width reaches the absolute resolution 4 eps max(|lo|, |hi|)
-// of the Gershgorin interval (the accuracy a backward-stable method attains).
+// Eigenvalues of the tridiagonal (dg, e^2) by multisection, one CTA of four
+// warps per eigenvalue (one per SM sub-partition), down to the absolute
+// resolution 4 eps max(|lo|, |hi|) of the Gershgorin interval (the accuracy
+// a backward-stable method attains).
 constexpr int kBisectMaxN = 1024;
 constexpr int kBisectThreads = 128;
 
+// Fast Sturm counts on T scaled by a power of two so that ||T|| <= 1
+// (|d_i - x| <= 2, e2_i <= 1): the leading-minor recurrence of sturm_count
+// with one FMA per step on the dependent chain.  Every four steps the pair
+// (p_{i-1}, p_i) may be rescaled by a power of two; the decision comes from
+// the value four steps older (four steps change the exponent by at most
+// log2(3^4) < 7), and the factor is folded into the step's inputs: with
+// q = S p, a new factor s at step k gives q_k = (s dx_k) q_{k-1} + (s me2_k)
+// q_{k-2} and q_{k+1} = dx_{k+1} q_k + (s me2_{k+1}) q_{k-1}.  Sign changes
+// and exact zeros are tested off the chain; a count that met an exact zero
+// is flagged (the caller redoes it with the safe recurrence).  me2 = -e2.
+template <typename F>
+struct SturmLimits;
+template <>
+struct SturmLimits<double> {
+  static constexpr int kBits = 11, kBias = 1023, kThr = 400;
+  __device__ static double scale(int up) { return up ? 0x1p400 : 0x1p-400; }
+  __device__ static int hi(double x) { return __double2hiint(x); }
+  // on the 32-bit halves: a 64-bit shift test costs twice as much on B300
+  __device__ static bool zero(double x) {
+    return ((__double2hiint(x) & 0x7fffffff) | __double2loint(x)) == 0;
+  }
+};
+template <>
+struct SturmLimits<float> {
+  static constexpr int kBits = 8, kBias = 127, kThr = 60;
+  __device__ static float scale(int up) { return up ? 0x1p60f : 0x1p-60f; }
+  __device__ static int hi(float x) { return __float_as_int(x); }
+  __device__ static bool zero(float x) { return (__float_as_int(x) << 1) == 0; }
+};
+
+template <typename F>
+__device__ int sturm_count_fast(const F* dg, const F* me2, int n, F x, bool& hit_zero) {
+  using L = SturmLimits<F>;
+  constexpr int kShift = (L::kBits == 11) ? 20 : 23, kMask = (1 << L::kBits) - 1;
+  F pm = F(1), pc = dg[0] - x;
+  int cnt = L::hi(pc) < 0;
+  bool z = L::zero(pc);
+  int hi_old = L::hi(pc);
+  int i = 1;
+  for (; i + 4 <= n; i += 4) {
+    F dx[4], m[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      dx[u] = dg[i + u] - x;
+      m[u] = me2[i + u - 1];
+    }
+    const int ex = ((hi_old >> kShift) & kMask) - L::kBias;
+    hi_old = L::hi(pc);
+    if (ex > L::kThr || ex < -L::kThr) {
+      const F sc = L::scale(ex < 0);
+      dx[0] *= sc;
+      m[0] *= sc;
+      m[1] *= sc;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const F pn = fma(dx[u], pc, m[u] * pm);
+      z |= L::zero(pn);
+      cnt += (L::hi(pn) ^ L::hi(pc)) < 0;
+      pm = pc;
+      pc = pn;
+    }
+  }
+  for (; i < n; ++i) {
+    const F pn = fma(dg[i] - x, pc, me2[i - 1] * pm);
+    z |= L::zero(pn);
+    cnt += (L::hi(pn) ^ L::hi(pc)) < 0;
+    pm = pc;
+    pc = pn;
+  }
+  hit_zero = z;
+  return cnt;
+}
+
+// One CTA per eigenvalue i (ascending order).  Multisection: the points
+// a + h (t + 1), t < np, split [a, b] into np + 1 parts per round; the first
+// point whose count exceeds i bounds eigenvalue i from above.  The counts run
+// on T scaled by 2^-k >= 1/||T||_Gershgorin (exact).  The bracket is first
+// narrowed in FP32 (128 points, ~7 bits per round) to a few FP32 ulps of
+// ||T||, widened by a margin covering the FP32 counts' error, checked by two
+// FP64 counts (the Gershgorin interval is used instead if the check fails),
+// and refined in FP64 (128 points, 7 bits per round) down to 4e-16 ||T||.
 __global__ void __launch_bounds__(kBisectThreads) bisect_kernel(const double* work, int n,
                                                                 double* ev_out) {
-  __shared__ double sdg[kBisectMaxN], se2[kBisectMaxN];
+  __shared__ double sdg[kBisectMaxN], se2[kBisectMaxN], ndg[kBisectMaxN], nme2[kBisectMaxN];
+  __shared__ float fdg[kBisectMaxN], fme2[kBisectMaxN];
   __shared__ unsigned masks[kBisectThreads / 32];
+  __shared__ int s_cnt[2];
   const double* dg = work + (size_t)n * n;
   const double* v = dg + 3 * (size_t)n;       // e^2
   const double* p = v + n;                    // lo, hi, pivmin
   const int tid = threadIdx.x, lane = tid & 31, wrp = tid >> 5;
   const int i = blockIdx.x;
+  const double lo = p[0], hi = p[1];
+  const double pivmin = p[2];
+  const double tn = fmax(fabs(lo), fabs(hi));
+  // exact power-of-two scale with ||T|| <= sc (Gershgorin)
+  const double sc = (tn > 0.0) ? exp2(ceil(log2(tn))) : 1.0;
+  const double isc = 1.0 / sc;
   for (int t = tid; t < n; t += kBisectThreads) {
     sdg[t] = dg[t];
     se2[t] = (t + 1 < n) ? v[t] : 0.0;
+    ndg[t] = sdg[t] * isc;
+    nme2[t] = -se2[t] * (isc * isc);
+    fdg[t] = static_cast<float>(ndg[t]);
+    fme2[t] = static_cast<float>(nme2[t]);
   }
   __syncthreads();
-  double a = p[0], b = p[1];
-  const double pivmin = p[2];
-  const double res = 4e-16 * fmax(fabs(a), fabs(b));
+  const double res = 4e-16 * tn;
+  // exact count of eigenvalues below x (FP64, scaled; the safe recurrence
+  // after an exact zero)
+  auto count64 = [&](double x) {
+    bool zero;
+    int c = sturm_count_fast<double>(ndg, nme2, n, x * isc, zero);
+    if (zero) c = sturm_count(sdg, se2, n, x, pivmin);
+    return c;
+  };
+  // ---- FP32 phase ----
   constexpr int NPT = kBisectThreads;
-  for (int round = 0; round < 64; ++round) {
+  double a = lo, b = hi;
+  {
+    const double res32 = 64.0 * 1.1920928955078125e-07 * tn;
+    for (int round = 0; round < 8 && b - a > res32; ++round) {
+      const double h = (b - a) * (1.0 / (NPT + 1));
+      const double xd = a + h * (tid + 1);
+      bool zero;
+      int c = sturm_count_fast<float>(fdg, fme2, n, static_cast<float>(xd * isc), zero);
+      if (zero) c = count64(xd);
+      const unsigned mask = __ballot_sync(0xffffffffu, c > i);
+      if (lane == 0) masks[wrp] = mask;
+      __syncthreads();
+      int first = NPT;
+#pragma unroll
+      for (int w = NPT / 32 - 1; w >= 0; --w)
+        if (masks[w]) first = w * 32 + __ffs(masks[w]) - 1;
+      __syncthreads();
+      const double na = (first == 0) ? a : a + h * first;
+      const double nb = (first == NPT) ? b : a + h * (first + 1);
+      if (!(nb < b || na > a)) break;
+      a = na;
+      b = nb;
+    }
+    // margin for the FP32 counts (and the rounding of x to FP32)
+    const double mg = 16.0 * 1.1920928955078125e-07 * tn;
+    a = fmax(lo, a - mg);
+    b = fmin(hi, b + mg);
+  }
+  // ---- FP64 phase: 128 points per round (one warp per SMSP: B300 runs one
+  // FP64 instruction per sub-partition at a time, so a round costs one
+  // warp's recurrence whatever the number of warps).  The first round also
+  // counts at a and b (threads 0 and NPT - 1 take the endpoints): if the
+  // FP32 bracket does not hold eigenvalue i, it restarts from [lo, hi]. ----
+  bool checked = false;
+  for (int round = 0; round < 80; ++round) {
+    const bool chk = !checked;
+    if (!chk && b - a <= res) break;
     const double h = (b - a) * (1.0 / (NPT + 1));
-    const double x = a + h * (tid + 1);
-    const bool above = (x > a && x < b) ? (sturm_count(sdg, se2, n, x, pivmin) > i) : (x >= b);
+    // evaluation points, increasing in t
+    auto point = [&](int t) {
+      return chk ? (t == 0 ? a : (t == NPT - 1 ? b : a + h * (t + 1))) : a + h * (t + 1);
+    };
+    const double x = point(tid);
+    bool above;
+    if (chk) {
+      const int c = count64(x);
+      above = c > i;
+      if (tid == 0) s_cnt[0] = c;
+      if (tid == NPT - 1) s_cnt[1] = c;
+    } else {
+      above = (x > a && x < b) ? (count64(x) > i) : (x >= b);
+    }
     const unsigned mask = __ballot_sync(0xffffffffu, above);
     if (lane == 0) masks[wrp] = mask;
     __syncthreads();
-    // the first point above eigenvalue i bounds it from above (the points
-    // above it form a suffix, the Sturm count being monotone in x)
+    if (chk) {
+      checked = true;
+      const bool ok = s_cnt[0] <= i && s_cnt[1] > i;
+      __syncthreads();
+      if (!ok) {                             // the bracket is wrong: restart
+        a = lo;
+        b = hi;
+        continue;
+      }
+    }
     int first = NPT;
 #pragma unroll
     for (int w = NPT / 32 - 1; w >= 0; --w)
       if (masks[w]) first = w * 32 + __ffs(masks[w]) - 1;
     __syncthreads();                          // masks are rewritten next round
-    const double na = (first == 0) ? a : a + h * first;
-    const double nb = (first == NPT) ? b : a + h * (first + 1);
+    double na, nb;
+    if (chk) {                                // 1 <= first <= NPT - 1 here
+      na = point(first - 1);
+      nb = point(first);
+    } else {
+      na = (first == 0) ? a : a + h * first;
+      nb = (first == NPT) ? b : a + h * (first + 1);
+    }
     if (!(nb < b || na > a)) break;          // no progress: bracket at resolution
     a = na;
     b = nb;
-    if (b - a <= res) break;
   }
   if (tid == 0) ev_out[i] = 0.5 * (a + b);
 }
