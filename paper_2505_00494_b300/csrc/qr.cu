@@ -38,7 +38,9 @@ __device__ __forceinline__ void reflector(double x0, double sigma, double* rmu, 
   const double m = a * y;
   *rmu = y;
   *mu = m;
-  if (x0 > 0.0) {
+  // x0 > 0 from the bits (an FP64 compare would take a 64-clock FP64 slot)
+  const int x0h = __double2hiint(x0);
+  if (x0h >= 0 && (x0h | __double2loint(x0)) != 0) {
     const double xm = x0 + m;
     *inv_w = -xm * rcp_nr(sigma);
     if (tau) *tau = sigma * y * rcp_nr(xm);       // -w/mu with w = -sigma/(x0 + mu)
@@ -110,10 +112,16 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     if (TILE) return tile[(i - r_begin) * (NB + 1) + jc];
     return W[((long long)j0 + jc) * m + i];
   };
-  auto sum8 = [&](int t) {
-    return ((red[0][t] + red[1][t]) + (red[2][t] + red[3][t])) +
-           ((red[4][t] + red[5][t]) + (red[6][t] + red[7][t]));
+  // the eight row lanes' partial sums of a slot: warps 0-3 (one per SM
+  // sub-partition, whose FP64 pipes work in parallel) fold warps 4-7 in,
+  // then warp 0 adds the four (3 FP64 adds on its pipe instead of 7)
+  auto fold8 = [&]() {
+    if (wrp < 4) {
+      red[wrp][lane] += red[wrp + 4][lane];
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+    }
   };
+  auto sum4 = [&](int t) { return (red[0][t] + red[1][t]) + (red[2][t] + red[3][t]); };
   // warp 0: add the partial sums (lane t = slot t, nslots of them) into the
   // accumulator row of panel column col, then arrive
   auto publish = [&](int col, double v, int nslots) {
@@ -144,7 +152,8 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     red[wrp][lane] = acc;
     if (c >= r_begin && c < r_end && (int)threadIdx.x < nb) rowb[threadIdx.x] = at(c, threadIdx.x);
     __syncthreads();
-    publish(0, (wrp == 0) ? sum8(lane) : 0.0, nb);
+    fold8();
+    publish(0, (wrp == 0) ? sum4(lane) : 0.0, nb);
   }
 
   int done = 0;
@@ -166,7 +175,8 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
       ssum[j][lane] = st;
       if (lane == 0) x0_s[j] = y0;
       double rmu = 0.0, inv_w = 0.0;
-      if (lane == 0 && st != 0.0) {
+      // st != 0 from the bits (an FP64 compare takes a 64-clock FP64 slot)
+      if (lane == 0 && ((__double2hiint(st) & 0x7fffffff) | __double2loint(st)) != 0) {
         double mu;
         reflector(y0, st, &rmu, &mu, &inv_w, nullptr);
       }
@@ -228,7 +238,8 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     if (last) break;
     red[wrp][lane] = acc + acc2;                           // slot lane - 1 of column j + 1
     __syncthreads();
-    publish(j + 1, (wrp == 0 && lane < nrem) ? sum8(lane + 1) : 0.0, nrem);
+    fold8();
+    publish(j + 1, (wrp == 0 && lane < nrem) ? sum4(lane + 1) : 0.0, nrem);
   }
   __syncthreads();
   // tau and the pivot rows (R_cc = mu, R_{c,j+t} = y_{t,0} - tau (y_{t,0} +
