@@ -399,13 +399,46 @@ __device__ __forceinline__ double ld_dsmem(const double* local_addr, unsigned ra
 // work + i n, n^2 doubles; L2-resident) instead of shared memory, for n
 // above what the CTAs' shared memory holds.  Each CTA touches only its own
 // rows, so the choice changes no synchronisation.
+// FP64 reductions priced for B300, which issues one FP64 instruction at a time
+// per SM sub-partition: work is spread over the four sub-partitions (warps
+// 0-3 of the block) and the trees are as shallow as the data allows.
+
+// Sum over warps 0-3 (128 threads, fixed order); the result in thread 0.
+// red: 4 slots.  Named barrier 1 among the four warps.
+__device__ __forceinline__ double quad_sum(double v, double* red) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  asm volatile("bar.sync 1, 128;" ::: "memory");
+  return (red[0] + red[1]) + (red[2] + red[3]);
+}
+
+// Four per-lane partial sums (rows 0..3) reduced across the warp at once:
+// after the two exchange levels each lane carries one row (row 2 b4 + b3 of
+// its lane bits), the last three levels finish it; 6 FP64 adds for four rows
+// (5 per row one at a time).  Every lane returns the total of its row.
+__device__ __forceinline__ double warp_sum4(double a0, double a1, double a2, double a3) {
+  const int lane = threadIdx.x & 31;
+  const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+  // level 16: keep rows {0,1} (lanes < 16) or {2,3}, send the other pair
+  const double s0 = hi16 ? a0 : a2, s1 = hi16 ? a1 : a3;
+  const double r0 = __shfl_xor_sync(0xffffffffu, s0, 16);
+  const double r1 = __shfl_xor_sync(0xffffffffu, s1, 16);
+  const double c0 = (hi16 ? a2 : a0) + r0, c1 = (hi16 ? a3 : a1) + r1;
+  // level 8: keep one row of the pair
+  const double r2 = __shfl_xor_sync(0xffffffffu, hi8 ? c0 : c1, 8);
+  double v = (hi8 ? c1 : c0) + r2;
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 template <int CS, bool GMEM>
 __global__ void __launch_bounds__(256) spectrum_cluster_kernel(const double* __restrict__ C, int n,
                                                                double* work, int* err) {
   extern __shared__ double csm[];
   __shared__ double red[32];
-  __shared__ double sc[4];
-  __shared__ double pv_part;
+  __shared__ double sc[6];
+  __shared__ double pvp[2];
   // the row distribution needs exactly CS CTAs in one cluster
   if (cluster_size() != (unsigned)CS || gridDim.x != (unsigned)CS) {
     if (threadIdx.x == 0) atomicOr(err, ERRF_BOUNDS);
@@ -419,10 +452,14 @@ __global__ void __launch_bounds__(256) spectrum_cluster_kernel(const double* __r
   auto rowp = [&](int li) -> double* {
     return GMEM ? work + (size_t)((int)r + li * CS) * n : csm + (size_t)li * n;
   };
-  double* xs = GMEM ? csm : csm + (size_t)nloc_max * n;  // published x (own entries)
-  double* ps = xs + n;                                   // published p (own entries)
-  double* vv = ps + n;                                   // v (all entries, local copy)
-  double* ww = vv + n;                                   // w (all entries, local copy)
+  // published (read by the other CTAs), by column parity: p of own rows by
+  // local index, and the pivot row (its owner's copy before the update)
+  double* psb = GMEM ? csm : csm + (size_t)nloc_max * n;   // [2][nloc_max]
+  double* rpb = psb + 2 * (size_t)nloc_max;                // [2][n]
+  // local: x of the current column (turned into v in place) and of the next
+  double* xb = rpb + 2 * (size_t)n;                        // [2][n]
+  double* ww = xb + 2 * (size_t)n;                         // [n]  w
+  double* qrow = ww + n;                                   // [nloc_max]  (A x) of own rows
   double* dg = work + (size_t)n * n;
   double* of = dg + n;
   double* v2 = of + 2 * n;
@@ -431,83 +468,152 @@ __global__ void __launch_bounds__(256) spectrum_cluster_kernel(const double* __r
     const int li = e / n, j = e % n, i = (int)r + li * CS;
     rowp(li)[j] = 0.5 * (C[(size_t)i * n + j] + C[(size_t)j * n + i]);
   }
-  cluster_sync_all();
+  // x of column 0 (rows 1..n-1), in every CTA
+  for (int t = tid; t + 1 < n; t += nt) xb[t] = 0.5 * (C[(size_t)(t + 1) * n] + C[t + 1]);
+  if (tid == 0 && r == 0) dg[0] = C[0];
+  __syncthreads();
+  // Column k, with x = A[k+1.., k] already in every CTA: v and beta from x;
+  // p = beta A v on own rows (published); the owner of row k + 1 publishes
+  // that row; one cluster barrier; every CTA gathers p and the pivot row,
+  // forms w = p - (beta p^T v / 2) v and, by symmetry, the next column
+  // x' = A[k+2.., k+1] - v_{k+1} w - w_{k+1} v from the pivot row; own rows
+  // take the rank-2 update.  Published buffers alternate with the column's
+  // parity: a CTA overwrites a parity only after the next barrier, which
+  // every CTA passes only after its reads of that parity.
   for (int k = 0; k + 2 < n; ++k) {
-    const int L = n - k - 1;
+    const int L = n - k - 1, par = k & 1;
+    double* vv = xb + (size_t)par * n;                     // x, then v
+    double* xn = xb + (size_t)(par ^ 1) * n;               // next column's x
     // own rows i > k: first local row index with i > k
     const int li0 = (k + 1 - (int)r + CS - 1 < 0) ? 0 : (k + 1 - (int)r + CS - 1) / CS;
-    for (int li = li0 + tid; li < nloc; li += nt) xs[r + li * CS] = rowp(li)[k];
-    if (tid == 0 && (k % CS) == (int)r) dg[k] = rowp(k / CS)[k];
-    cluster_sync_all();                                                     // (a)
-    for (int t = tid; t < L; t += nt) {
-      const int i = k + 1 + t;
-      vv[t] = ld_dsmem(xs + i, (unsigned)(i % CS));
-    }
-    __syncthreads();
-    double sq = 0.0;
-    for (int t = tid; t < L; t += nt) sq = fma(vv[t], vv[t], sq);
-    const double nrm2 = block_sum(sq, red, &sc[3]);
-    if (tid == 0) {
-      const double x0 = vv[0];
-      if (nrm2 == 0.0) {
-        sc[1] = 0.0;
-        if (r == 0) of[k] = 0.0;
-      } else {
-        // Newton reciprocal square root and reciprocal from FP32 seeds: the
-        // IEEE FP64 sqrt and divide are long chains on B300's FP64 pipe
-        const double alpha = nrm2 * rsqrt_nr(nrm2);
-        const double sgn = (x0 >= 0.0) ? 1.0 : -1.0;
-        sc[0] = x0 + sgn * alpha;
-        sc[1] = rcp_nr(alpha * (alpha + fabs(x0)));
-        if (r == 0) of[k] = -sgn * alpha;
+    // Warps 0-3 (one per SM sub-partition): ||x||^2, then the reflector
+    // scalars in thread 0.  At the same time warps 5-7 (sub-partitions 1-3)
+    // form q = A x on own rows i > k with the unmodified x: v differs from x
+    // only in its first entry (v_0 = x_0 + sgn(x_0) alpha), so
+    // A v = q + sgn(x_0) alpha A[., k+1].  Warp 4 of the pivot row's owner
+    // publishes that row (entries k+1..n-1, before this column's update).
+    double* psw = psb + (size_t)par * nloc_max;
+    if (wrp < 4) {
+      double sq = 0.0;
+      for (int t = tid; t < L; t += 128) sq = fma(vv[t], vv[t], sq);
+      const double nrm2 = quad_sum(sq, red);
+      if (tid == 0) {
+        const double x0 = vv[0];
+        const int x0h = __double2hiint(x0), x0l = __double2loint(x0);
+        if (((__double2hiint(nrm2) & 0x7fffffff) | __double2loint(nrm2)) == 0) {
+          // x = 0: the reflector is the identity (beta = 0: p = w = 0)
+          sc[0] = x0;
+          sc[1] = 0.0;
+          sc[2] = 0.0;
+          sc[4] = 0.0;
+          if (r == 0) of[k] = 0.0;
+        } else {
+          // Newton reciprocal square root and reciprocal from FP32 seeds: the
+          // IEEE FP64 sqrt and divide are long chains on B300's FP64 pipe
+          const double alpha = nrm2 * rsqrt_nr(nrm2);
+          const double salpha =                          // sgn(x0) alpha
+              __hiloint2double(__double2hiint(alpha) ^ (x0h & (int)0x80000000),
+                               __double2loint(alpha));
+          const double ax0 = __hiloint2double(x0h & 0x7fffffff, x0l);
+          sc[0] = x0 + salpha;
+          sc[4] = salpha;
+          const double beta = rcp_nr(alpha * (alpha + ax0));
+          sc[1] = beta;
+          // beta / 2: exact, by the exponent, for a normal beta
+          const int bh = __double2hiint(beta), be = (bh >> 20) & 0x7ff;
+          sc[2] = (be > 1 && be < 0x7ff) ? __hiloint2double(bh - (1 << 20), __double2loint(beta))
+                                         : 0.5 * beta;
+          if (r == 0)
+            of[k] = __hiloint2double(__double2hiint(salpha) ^ (int)0x80000000,
+                                     __double2loint(salpha));
+        }
       }
+    } else if (wrp >= 5) {
+      // rows li0 + g + 3 q (q < 4) per warp g = wrp - 5, then the next 12
+      const int g = wrp - 5;
+      for (int g0 = li0 + g; g0 < nloc; g0 += 12) {
+        double a[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int li = g0 + 3 * q;
+          if (li < nloc) {
+            const double* row = rowp(li) + k + 1;
+            double acc = 0.0;
+            for (int t = lane; t < L; t += 32) acc = fma(row[t], vv[t], acc);
+            a[q] = acc;
+          }
+        }
+        const double tot = warp_sum4(a[0], a[1], a[2], a[3]);
+        const int q = ((lane >> 4) << 1) | ((lane >> 3) & 1);   // row slot of this lane
+        const int li = g0 + 3 * q;
+        if ((lane & 7) == 0 && li < nloc) qrow[li] = tot;
+      }
+    } else if ((int)((k + 1) % CS) == (int)r) {
+      const double* row = rowp((k + 1) / CS);
+      double* rp = rpb + (size_t)par * n;
+      for (int j = k + 1 + lane; j < n; j += 32) rp[j] = row[j];
     }
     __syncthreads();
     const double beta = sc[1];
-    if (beta == 0.0) {                       // same decision in every CTA of the cluster
-      cluster_sync_all();                    // x may be republished only after every gather
-      continue;
-    }
-    if (tid == 0) vv[0] = sc[0];
-    __syncthreads();
-    // p_i = beta (A v)_i for own rows i > k: a warp per row, lanes over j
-    double pv_w = 0.0;
-    for (int li = li0 + wrp; li < nloc; li += (nt >> 5)) {
-      const double* row = rowp(li) + k + 1;
-      double a0 = 0.0, a1 = 0.0;
-      int t = lane;
-      for (; t + 32 < L; t += 64) {
-        a0 = fma(row[t], vv[t], a0);
-        a1 = fma(row[t + 32], vv[t + 32], a1);
-      }
-      if (t < L) a0 = fma(row[t], vv[t], a0);
-      const double pi = beta * warp_sum(a0 + a1);
-      const int i = (int)r + li * CS;
-      if (lane == 0) ps[i] = pi;
-      pv_w += pi * vv[i - k - 1];            // identical in every lane
-    }
-    if (lane == 0) red[wrp] = pv_w;
-    __syncthreads();
-    if (tid == 0) {
-      double sacc = 0.0;
-      for (int w = 0; w < (nt >> 5); ++w) sacc += red[w];
-      pv_part = sacc;
-    }
-    cluster_sync_all();                                                     // (b)
-    for (int t = tid; t < L; t += nt) {
-      const int i = k + 1 + t;
-      ww[t] = ld_dsmem(ps + i, (unsigned)(i % CS));
-    }
+    // p_i = beta (q_i + sgn(x_0) alpha A[i][k+1]) on own rows; the CTA's
+    // share of p^T v (v_i = x_i below row k + 1, v_{k+1} = x_0 + sgn alpha)
     if (wrp == 0) {
-      // one lane per CTA of the cluster: the CS remote loads overlap
-      double pv = (lane < CS) ? ld_dsmem(&pv_part, (unsigned)lane) : 0.0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
-      if (lane == 0) sc[2] = 0.5 * beta * pv;
+      const double salpha = sc[4], v0 = sc[0];
+      double pv = 0.0;
+      for (int li = li0 + lane; li < nloc; li += 32) {
+        const int i = (int)r + li * CS;
+        const double pi = beta * fma(salpha, rowp(li)[k + 1], qrow[li]);
+        psw[li] = pi;
+        pv = fma(pi, (i == k + 1) ? v0 : vv[i - k - 1], pv);
+      }
+      pv = warp_sum(pv);
+      if (lane == 0) {
+        pvp[par] = pv;
+        vv[0] = v0;
+      }
     }
-    __syncthreads();
-    const double K = sc[2];
-    for (int t = tid; t < L; t += nt) ww[t] = fma(-K, vv[t], ww[t]);
+    cluster_sync_all();
+    // gather: p (own entries of every CTA), the pivot row (one CTA), the p^T v parts
+    const unsigned piv = (unsigned)((k + 1) % CS);
+    const double* rpr = rpb + (size_t)par * n;
+    double rowv[4], pvv[4];                          // entries k+1+t, t = tid + nt m
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int t = tid + nt * m;
+      const int i = k + 1 + t;
+      rowv[m] = (t < L) ? ld_dsmem(rpr + i, piv) : 0.0;
+      pvv[m] = (t < L) ? ld_dsmem(psw + i / CS, (unsigned)(i % CS)) : 0.0;
+    }
+    double p0 = ld_dsmem(psw + (k + 1) / CS, piv);   // p_{k+1}, in every thread
+    double pvs = (lane < CS) ? ld_dsmem(&pvp[par], (unsigned)lane) : 0.0;
+#pragma unroll
+    for (int o = CS / 2; o > 0; o >>= 1) pvs += __shfl_xor_sync(0xffffffffu, pvs, o);
+    pvs = __shfl_sync(0xffffffffu, pvs, 0);          // lanes >= CS hold no part
+    // K = beta p^T v / 2 (every warp has the same sum); w = p - K v; the next
+    // column x'[t'] = A'[k+2+t', k+1] = a - v_{k+1} w_i - w_{k+1} v_i from the
+    // pivot-row entry a, and the diagonal A'[k+1][k+1]
+    const double K = sc[2] * pvs;
+    const double v1 = vv[0], w1 = fma(-K, v1, p0);   // vv[0] = v0 since before the barrier
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int t = tid + nt * m;
+      if (t < L) {
+        const double wt = fma(-K, vv[t], pvv[m]);
+        ww[t] = wt;
+        const double a = fma(-v1, wt, fma(-w1, vv[t], rowv[m]));
+        if (t == 0) {
+          if (r == 0) dg[k + 1] = a;
+        } else {
+          xn[t - 1] = a;
+        }
+      }
+    }
+    for (int t = tid + nt * 4; t < L; t += nt) {      // n > 4 nt only (not reached: n <= 1024)
+      const int i = k + 1 + t;
+      const double wt = fma(-K, vv[t], ld_dsmem(psw + i / CS, (unsigned)(i % CS)));
+      ww[t] = wt;
+      xn[t - 1] = fma(-v1, wt, fma(-w1, vv[t], ld_dsmem(rpr + i, piv)));
+    }
     __syncthreads();
     // own rows: A[i][j] -= v_i w_j + w_i v_j  (j > k)
     const int rows_left = nloc - li0;
@@ -929,12 +1035,12 @@ cudaError_t corner_spectrum(const double* C, int chi, double* work, double* s_ne
   if (!cattr) {
     cudaFuncSetAttribute(spectrum_cluster_kernel<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(double) * (((size_t)kSpecClusterMaxN8 + 7) / 8 *
-                                                     kSpecClusterMaxN8 +
-                                                 4 * (size_t)kSpecClusterMaxN8)));
+                                                     (kSpecClusterMaxN8 + 3) +
+                                                 5 * (size_t)kSpecClusterMaxN8)));
     auto k16 = spectrum_cluster_kernel<16, false>;
     const size_t smem16 = sizeof(double) * (((size_t)kSpecClusterMaxN16 + 15) / 16 *
-                                                kSpecClusterMaxN16 +
-                                            4 * (size_t)kSpecClusterMaxN16);
+                                                (kSpecClusterMaxN16 + 3) +
+                                            5 * (size_t)kSpecClusterMaxN16);
     cudaFuncSetAttribute(k16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem16);
     // 16 CTAs per cluster is above the portable limit: allowed only where
     // the device can place such a cluster
@@ -973,8 +1079,8 @@ cudaError_t corner_spectrum(const double* C, int chi, double* work, double* s_ne
                      : (cs == 8) ? spectrum_cluster_kernel<8, false>
                                  : spectrum_cluster_kernel<16, false>;
     const int nloc_max = (chi + cs - 1) / cs;
-    const size_t csmem =
-        sizeof(double) * ((gmem ? 0 : (size_t)nloc_max * chi) + 4 * (size_t)chi);
+    const size_t csmem = sizeof(double) * ((gmem ? 0 : (size_t)nloc_max * chi) +
+                                           3 * (size_t)nloc_max + 5 * (size_t)chi);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs);
     cfg.blockDim = dim3(256);
