@@ -200,8 +200,22 @@ __global__ void __launch_bounds__(256) q_solve_kernel(const float* __restrict__ 
   float* us = qs + ((n + 3) & ~3);        // [n][n] when staged
   for (int e = threadIdx.x; e < n; e += blockDim.x)
     taus[e] = static_cast<float>(Tf[(size_t)(e / NB) * NB * NB + (e % NB) * NB + (e % NB)]);
-  if (staged)
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) us[e] = UT[(long long)(e / n) * ldu + e % n];
+  if (staged) {
+    // rows of U^T by warps, lanes along the row (no per-element division);
+    // 16-byte copies when rows are 16-byte aligned in both places
+    const int wid = threadIdx.x >> 5, ln = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if ((n & 3) == 0 && (ldu & 3) == 0) {
+      const int n4 = n >> 2;
+      for (int row = wid; row < n; row += nw) {
+        const float4* src = reinterpret_cast<const float4*>(UT + (long long)row * ldu);
+        float4* dst = reinterpret_cast<float4*>(us + (long long)row * n);
+        for (int c = ln; c < n4; c += 32) dst[c] = src[c];
+      }
+    } else {
+      for (int row = wid; row < n; row += nw)
+        for (int c = ln; c < n; c += 32) us[(long long)row * n + c] = UT[(long long)row * ldu + c];
+    }
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int k = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -361,6 +375,7 @@ cudaError_t householder_qr_split(int m, int n, const double* M, double* R, const
     if (!qattr) {
       const int mx = (int)(sizeof(float) * (kSolveSmemMaxN * kSolveSmemMaxN + 32 * 8));
       cudaFuncSetAttribute(q_solve_kernel<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+      cudaFuncSetAttribute(q_solve_kernel<5, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
       cudaFuncSetAttribute(q_solve_kernel<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
       qattr = true;
     }
@@ -368,6 +383,8 @@ cudaError_t householder_qr_split(int m, int n, const double* M, double* R, const
     const bool stg = n <= kSolveSmemMaxN;
     if (n <= 128 && stg)
       q_solve_kernel<4, true><<<qg, 256, qsm, s>>>(UT, ldv, Vt32, ldv, w.Tf, n, Wt);
+    else if (n <= 160 && stg)
+      q_solve_kernel<5, true><<<qg, 256, qsm, s>>>(UT, ldv, Vt32, ldv, w.Tf, n, Wt);
     else if (n <= 256 && stg)
       q_solve_kernel<8, true><<<qg, 256, qsm, s>>>(UT, ldv, Vt32, ldv, w.Tf, n, Wt);
     else if (n <= 256)
