@@ -19,7 +19,9 @@
  * All device work is queued on the stream given in the configuration; calls
  * that return host scalars synchronise that stream.  The caller owns every
  * pointer it passes; the library never frees them.  The library allocates no
- * device memory: all scratch lives in the caller's workspace.
+ * device memory for data: all scratch lives in the caller's workspace (the
+ * only driver objects a context creates are the stream and CUDA graph that
+ * qrctm_step replays, released by qrctm_destroy).
  */
 #ifndef QRCTM_H
 #define QRCTM_H
@@ -137,7 +139,10 @@ qrctm_status qrctm_init_env(qrctm_ctx* ctx, const double* A, const double* C0, c
 
 /* Run n_steps QR-CTMRG steps (Fig. 1(e,f)).  If delta_out is non-NULL the
  * corner spectrum change since the previous test is computed and returned
- * (host double; synchronises). */
+ * (host double; synchronises).  The first step at a given environment bond
+ * captures the step's launches into a CUDA graph (on a stream the context
+ * creates) that later steps replay on the configured stream; with profiling
+ * on, or where capture fails, the launches are issued one by one. */
 qrctm_status qrctm_step(qrctm_ctx* ctx, int n_steps, double* delta_out);
 
 /* Step until the change of the sorted, normalised |eig(C)| between two

@@ -324,6 +324,11 @@ qrctm_status qrctm_create(const qrctm_config* cfg, void* workspace, size_t bytes
 
 void qrctm_destroy(qrctm_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->g_exec) {
+    cudaStreamSynchronize(ctx->st);
+    cudaGraphExecDestroy(ctx->g_exec);
+  }
+  if (ctx->g_stream) cudaStreamDestroy(ctx->g_stream);
   if (!ctx->recs.empty() || !ctx->ev_pool.empty()) cudaStreamSynchronize(ctx->st);
   for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
@@ -430,6 +435,55 @@ qrctm_status bulk_boundary_warmup(qrctm_ctx* c) {
 }
 
 // First spectrum of the new environment; the context is ready to step.
+// One QR-CTMRG step, replayed from a CUDA graph: the ~45 launches of a step
+// (cooperative panel launches and memsets included) are captured once per
+// environment bond on a stream of the context and replayed on its stream, so
+// that the GPU runs them back to back without per-launch gaps.  Capture runs
+// nothing; every argument of the step (workspace pointers, shapes, tensor
+// maps) is fixed for a context and bond.  Eager launches when profiling (the
+// phase events would be captured) or when capture is not possible.
+cudaError_t qr_step_eager(qrctm_ctx* c) { return c->split_prec ? qr_step_split(c) : qr_step(c); }
+
+cudaError_t qr_step_graph(qrctm_ctx* c) {
+  if (c->prof || c->graph_off) return qr_step_eager(c);
+  if (!c->g_exec || c->g_chi != c->chi_cur) {
+    if (c->g_exec) {
+      cudaGraphExecDestroy(c->g_exec);
+      c->g_exec = nullptr;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!c->g_stream) e = cudaStreamCreateWithFlags(&c->g_stream, cudaStreamNonBlocking);
+    cudaGraph_t g = nullptr;
+    const int it0 = c->iters;
+    const unsigned long long l0 = launches_so_far();
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(c->g_stream, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      cudaStream_t saved = c->st;
+      c->st = c->g_stream;
+      const cudaError_t es = qr_step_eager(c);
+      c->st = saved;
+      e = cudaStreamEndCapture(c->g_stream, &g);
+      if (es != cudaSuccess) e = es;
+    }
+    c->iters = it0;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->g_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->g_exec = nullptr;
+      c->graph_off = true;
+      return qr_step_eager(c);
+    }
+    c->g_launches = launches_so_far() - l0;
+    c->g_chi = c->chi_cur;
+  }
+  const cudaError_t e = cudaGraphLaunch(c->g_exec, c->st);
+  if (e != cudaSuccess) return e;
+  note_launch(c->g_launches);
+  c->iters += 1;
+  return cudaSuccess;
+}
+
 qrctm_status finish_init(qrctm_ctx* c) {
   qrctm_status s = sync_check(c, "init env");
   if (s != QRCTM_OK) return s;
@@ -552,7 +606,7 @@ qrctm_status qrctm_step(qrctm_ctx* c, int n, double* delta_out) {
     if (c->cfg.method == QRCTM_METHOD_EIGEN)
       e = eigen_step(c, c->chi_cur, (int)std::min<long long>(c->chi, (long long)c->chi_cur * c->D2));
     else
-      e = c->split_prec ? qr_step_split(c) : qr_step(c);
+      e = qr_step_graph(c);
     if (e != cudaSuccess) return cuda_fail(c, e, "step");
   }
   if (delta_out) {

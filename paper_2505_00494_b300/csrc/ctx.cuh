@@ -68,6 +68,12 @@ struct qrctm_ctx {
   bool have_env;
   bool spec_valid;
   std::string last_error;
+  // one QR-CTMRG step as a CUDA graph (captured on g_stream, replayed on st)
+  cudaGraphExec_t g_exec;
+  cudaStream_t g_stream;
+  int g_chi;                       // environment bond the graph was captured for
+  unsigned long long g_launches;   // kernels in the graph
+  bool graph_off;                  // capture failed once: eager launches
   // phase timing (qrctm_set_profiling)
   bool prof;
   struct PhaseRec { int ph; cudaEvent_t a, b; };
