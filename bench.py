@@ -650,7 +650,7 @@ def main():
     ap.add_argument("--check-every", type=int, default=5)
     ap.add_argument("--cpu-sample", type=int, default=3, help="oracle steps in cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip time-to-convergence, dE vs FP64 and the energy gradient")
     ap.add_argument("--grad-tol", type=float, default=1e-6,

@@ -54,10 +54,11 @@ qrctm_status cuda_fail(qrctm_ctx* c, cudaError_t e, const char* where) {
 
 // Synchronise the stream and translate the device error word.
 qrctm_status sync_check(qrctm_ctx* c, const char* where) {
-  cudaError_t e = cudaStreamSynchronize(c->st);
-  if (e != cudaSuccess) return cuda_fail(c, e, where);
+  // one wait: a device-to-host copy into pageable memory returns once the
+  // stream's earlier work and the copy are done (and reports their errors)
   int flag = 0;
-  e = cudaMemcpy(&flag, c->err, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaError_t e = cudaMemcpyAsync(&flag, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) return cuda_fail(c, e, where);
   if (flag) {
     cudaMemsetAsync(c->err, 0, sizeof(int), c->st);
@@ -485,11 +486,11 @@ cudaError_t qr_step_graph(qrctm_ctx* c) {
 }
 
 qrctm_status finish_init(qrctm_ctx* c) {
-  qrctm_status s = sync_check(c, "init env");
-  if (s != QRCTM_OK) return s;
+  // the error word collects the set-up kernels' and the spectrum's failures:
+  // one check after both
   cudaError_t e;
   if ((e = spectrum_check(c)) != cudaSuccess) return cuda_fail(c, e, "spectrum");
-  s = sync_check(c, "spectrum");
+  qrctm_status s = sync_check(c, "init env");
   if (s != QRCTM_OK) return s;
   c->spec_valid = true;
   c->have_env = true;
@@ -611,11 +612,12 @@ qrctm_status qrctm_step(qrctm_ctx* c, int n, double* delta_out) {
   }
   if (delta_out) {
     if ((e = spectrum_check(c)) != cudaSuccess) return cuda_fail(c, e, "spectrum");
+    double dlt;
+    if ((e = cudaMemcpyAsync(&dlt, c->delta_d, sizeof(double), cudaMemcpyDeviceToHost, c->st)) !=
+        cudaSuccess)
+      return cuda_fail(c, e, "delta");
     qrctm_status s = sync_check(c, "step");
     if (s != QRCTM_OK) return s;
-    double dlt;
-    if ((e = cudaMemcpy(&dlt, c->delta_d, sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
-      return cuda_fail(c, e, "delta");
     c->last_delta = dlt;
     *delta_out = dlt;
     return QRCTM_OK;
