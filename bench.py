@@ -290,9 +290,10 @@ def phase_profile(ctx, one_step, steps):
     return phases, prof_ms
 
 
-def tc_kernel_name(N, K):
+def tc_kernel_name(N, K, pre=0):
     """Name of the tensor-core kernel instance the engine launches for an
-    N-column, K-deep product (the tile choice of gemm_tc)."""
+    N-column, K-deep product (the tile choice of gemm_tc); pre = 1 when B
+    comes pre-split, 2 when both operands do."""
     if N <= 32:
         bn = (32, 2)
     elif N <= 64:
@@ -307,7 +308,7 @@ def tc_kernel_name(N, K):
         bn = (192, 1)
     else:
         bn = (96, 2)
-    return f"tc_tf32x3_kernel<{bn[0]}, {bn[1]}>"
+    return f"tc_tf32x3_kernel<{bn[0]}, {bn[1]}, {pre}>"
 
 
 def roofline_rows(kernels, phases, prof_ms, traffic):
@@ -768,8 +769,9 @@ def main():
                       tf32_peak, tf32_note)
         kernels.update({
             "absorb": absorb,
-            "x1": (tc_kernel_name(m, chi), fl["x1"], "tensor", tf32_peak, tf32_note),
-            "project": (tc_kernel_name(chi, m), fl["project"], "tensor", tf32_peak, tf32_note),
+            "x1": (tc_kernel_name(m, chi, 2), fl["x1"], "tensor", tf32_peak, tf32_note),
+            "project": (tc_kernel_name(chi, m, 1), fl["project"], "tensor", tf32_peak,
+                        tf32_note),
         })
     else:
         kernels.update({

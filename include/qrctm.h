@@ -317,6 +317,26 @@ qrctm_status qrctm_gemm_tf32x3(int M, int N, int K, const float* A, long long ld
                                long long ldb, double* C, long long ldc, float* work,
                                long long work_elems, int* err_word, void* stream);
 
+/* The same product with pre-split operands: A (optional) and B are given as
+ * TF32 head planes (A, B) and tail planes (A_lo, B_lo) of the same layout,
+ * as qrctm_tf32_split leaves them, so the kernel splits nothing (an operand
+ * that many output tiles share is split once instead of once per tile).
+ * B_lo is required; A_lo = NULL means A is plain FP32 and split in the kernel.
+ * A pre-split A with a plain B is QRCTM_ERR_INVALID_ARG.  Same result
+ * bits as qrctm_gemm_tf32x3 on the unsplit operands.  Synchronises. */
+qrctm_status qrctm_gemm_tf32x3_presplit(int M, int N, int K, const float* A, const float* A_lo,
+                                        long long lda, const float* B, const float* B_lo,
+                                        long long ldb, double* C, long long ldc, float* work,
+                                        long long work_elems, int* err_word, void* stream);
+
+/* In-place split of the FP32 device matrix x (rows x cols, row stride ld >=
+ * cols, rows * cols < 2^32) for the TF32x3 product: x[r*ld + c] becomes its
+ * TF32 head (nearest, ties away from zero) and lo[r*ld + c] (device, same
+ * layout) the TF32 tail of the remainder; a NaN stays in the head.  Elements
+ * between cols and ld are left alone.  Synchronises `stream`. */
+qrctm_status qrctm_tf32_split(long long rows, int cols, float* x, long long ld, float* lo,
+                              void* stream);
+
 /* Householder QR that allocates nothing: the same result as
  * qrctm_householder_qr, for callers that cannot obtain device memory of their
  * own (a plug-in handed only input/output pointers by a host application that

@@ -18,7 +18,7 @@ import ctypes
 import os
 
 __all__ = ["QRCTM", "QRCTMError", "Energy", "lib", "c4v_symmetrize", "householder_qr",
-           "LIB_PATH"]
+           "gemm_tf32x3", "gemm_tf32x3_presplit", "tf32_split", "LIB_PATH"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libqrctm.so")
 
@@ -105,6 +105,12 @@ _sig = {
                            _vp], ctypes.c_int),
     "qrctm_householder_qr_noalloc": ([ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp],
                                      ctypes.c_int),
+    "qrctm_gemm_tf32x3_presplit": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
+                                    ctypes.c_longlong, _vp, _vp, ctypes.c_longlong, _vp,
+                                    ctypes.c_longlong, _vp, ctypes.c_longlong, _vp, _vp],
+                                   ctypes.c_int),
+    "qrctm_tf32_split": ([ctypes.c_longlong, ctypes.c_int, _vp, ctypes.c_longlong, _vp, _vp],
+                         ctypes.c_int),
 }
 EXPORTED = sorted(_sig)
 _LIB = None
@@ -354,6 +360,41 @@ def gemm_tf32x3(A, B, stream=None, split_k=True):
                                      ctypes.c_void_p(err.data_ptr()), _stream_ptr(stream))
     if code != 0:
         raise QRCTMError(code, "qrctm_gemm_tf32x3")
+    return C
+
+
+def tf32_split(X, stream=None):
+    """Split an FP32 CUDA matrix in place for the TF32x3 product: X becomes
+    its TF32 heads; returns the tail plane (same shape)."""
+    torch = _torch()
+    if X.dtype != torch.float32 or X.dim() != 2 or X.stride(1) != 1:
+        raise TypeError("X must be a row-contiguous float32 matrix")
+    lo = torch.empty_like(X)
+    code = _load().qrctm_tf32_split(X.shape[0], X.shape[1], ctypes.c_void_p(X.data_ptr()),
+                                    X.stride(0), ctypes.c_void_p(lo.data_ptr()),
+                                    _stream_ptr(stream))
+    if code != 0:
+        raise QRCTMError(code, "qrctm_tf32_split")
+    return lo
+
+
+def gemm_tf32x3_presplit(A, A_lo, B, B_lo, stream=None, split_k=True):
+    """gemm_tf32x3 on pre-split operands (head planes A, B and tail planes
+    A_lo, B_lo from tf32_split; A_lo may be None for a plain FP32 A)."""
+    torch = _torch()
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty((M, N), dtype=torch.float64, device=A.device)
+    err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    nwork = (1 << 22) if split_k else 0
+    work = torch.empty(max(nwork, 1), dtype=torch.float32, device=A.device)
+    vp = ctypes.c_void_p
+    code = _load().qrctm_gemm_tf32x3_presplit(
+        M, N, K, vp(A.data_ptr()), vp(A_lo.data_ptr()) if A_lo is not None else None,
+        A.stride(0), vp(B.data_ptr()), vp(B_lo.data_ptr()), B.stride(0), vp(C.data_ptr()), N,
+        vp(work.data_ptr()) if nwork else None, nwork, vp(err.data_ptr()), _stream_ptr(stream))
+    if code != 0:
+        raise QRCTMError(code, "qrctm_gemm_tf32x3_presplit")
     return C
 
 

@@ -141,6 +141,10 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
     takef(carve ? &c->C32 : &fdummy, chi * chp);
     takef(carve ? &c->Qt32 : &fdummy, m * chp);
     takef(carve ? &c->Qc32 : &fdummy, chi * mp);
+    takef(carve ? &c->T32lo : &fdummy, m * chp);
+    takef(carve ? &c->C32lo : &fdummy, chi * chp);
+    takef(carve ? &c->Qt32lo : &fdummy, m * chp);
+    takef(carve ? &c->Qc32lo : &fdummy, chi * mp);
     takef(carve ? &c->Ts32 : &fdummy, m * chp);
     takef(carve ? &c->Rt32 : &fdummy, chi * chp);
     takef(carve ? &c->Aket32 : &fdummy, d * D2 * D2p);
@@ -153,6 +157,7 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
     // names: for D >= 2 each needs at most as many bytes as its FP64 region
   } else if (carve) {
     c->T32 = c->C32 = c->Qt32 = c->Qc32 = c->Ts32 = c->Rt32 = c->Aket32 = c->Abra32 = nullptr;
+    c->T32lo = c->C32lo = c->Qt32lo = c->Qc32lo = nullptr;
     c->qr32 = nullptr;
     c->tc_part = nullptr;
     c->tc_part_elems = 0;
@@ -881,15 +886,18 @@ qrctm_status qrctm_c4v_symmetrize(int d, int D, const double* X, double* Y, int 
   return QRCTM_OK;
 }
 
-qrctm_status qrctm_gemm_tf32x3(int M, int N, int K, const float* A, long long lda, const float* B,
-                               long long ldb, double* C, long long ldc, float* work,
-                               long long work_elems, int* err_word, void* stream) {
+namespace {
+qrctm_status gemm_tf32x3_impl(int M, int N, int K, const float* A, const float* A_lo,
+                              long long lda, const float* B, const float* B_lo, long long ldb,
+                              double* C, long long ldc, float* work, long long work_elems,
+                              int* err_word, void* stream) {
   if (M < 1 || N < 1 || K < 1 || !A || !B || !C || !err_word) return QRCTM_ERR_INVALID_ARG;
   if (lda < K || ldb < K || ldc < N || (lda % 4) || (ldb % 4)) return QRCTM_ERR_INVALID_ARG;
+  if (A_lo && !B_lo) return QRCTM_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   TcGemm g{};
-  g.A = TcOperand{A, M, K, lda, 1, 0};
-  g.B = TcOperand{B, N, K, ldb, 1, 0};
+  g.A = TcOperand{A, M, K, lda, 1, 0, A_lo};
+  g.B = TcOperand{B, N, K, ldb, 1, 0, B_lo};
   g.M = M; g.N = N; g.K = K; g.batch = 1;
   g.C = C; g.c_fp64 = true;
   g.c_m = im1(ldc); g.c_n = im1(1); g.c_b = im0();
@@ -906,6 +914,33 @@ qrctm_status qrctm_gemm_tf32x3(int M, int N, int K, const float* A, long long ld
     return QRCTM_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return QRCTM_ERR_CUDA;
   if (flag) return (flag & ERRF_TIMEOUT) ? QRCTM_ERR_TIMEOUT : QRCTM_ERR_NUMERIC;
+  return QRCTM_OK;
+}
+}  // namespace
+
+qrctm_status qrctm_gemm_tf32x3(int M, int N, int K, const float* A, long long lda, const float* B,
+                               long long ldb, double* C, long long ldc, float* work,
+                               long long work_elems, int* err_word, void* stream) {
+  return gemm_tf32x3_impl(M, N, K, A, nullptr, lda, B, nullptr, ldb, C, ldc, work, work_elems,
+                          err_word, stream);
+}
+
+qrctm_status qrctm_gemm_tf32x3_presplit(int M, int N, int K, const float* A, const float* A_lo,
+                                        long long lda, const float* B, const float* B_lo,
+                                        long long ldb, double* C, long long ldc, float* work,
+                                        long long work_elems, int* err_word, void* stream) {
+  if (!B_lo) return QRCTM_ERR_INVALID_ARG;
+  return gemm_tf32x3_impl(M, N, K, A, A_lo, lda, B, B_lo, ldb, C, ldc, work, work_elems,
+                          err_word, stream);
+}
+
+qrctm_status qrctm_tf32_split(long long rows, int cols, float* x, long long ld, float* lo,
+                              void* stream) {
+  if (rows < 0 || cols < 0 || !x || !lo || ld < cols) return QRCTM_ERR_INVALID_ARG;
+  if (rows * (long long)cols >= (1ll << 32)) return QRCTM_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (split_f32(x, lo, rows, cols, ld, s) != cudaSuccess) return QRCTM_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return QRCTM_ERR_CUDA;
   return QRCTM_OK;
 }
 

@@ -35,6 +35,8 @@ struct qrctm_ctx {
   // split precision: FP32 operand copies (rows padded to 4 floats) and the
   // tensor-core split-K partial sums
   float *T32, *C32, *Qt32, *Qc32, *Ts32, *Rt32, *Aket32, *Abra32, *tc_part, *qr32;
+  // TF32 tails of the pre-split operands (T32, C32, Qt32, Qc32 then hold the heads)
+  float *T32lo, *C32lo, *Qt32lo, *Qc32lo;
   long long tc_part_elems;
   // gradient
   char* G;             // gradient region base (carved by grad.cu)

@@ -906,46 +906,79 @@ __global__ void spectrum_finish_kernel(const double* ev, int n, double* s_new, c
 
 inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+template <bool SPLIT>
 __global__ void gather_f32_k(const double* __restrict__ in, float* __restrict__ out,
-                             long long nrows, int ncols, long long stride, IdxMap rmap,
-                             IdxMap cmap) {
+                             float* __restrict__ lo, long long nrows, int ncols,
+                             long long stride, IdxMap rmap, IdxMap cmap) {
   const long long tot = nrows * ncols;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
     const long long r = e / ncols, c = e % ncols;
-    out[r * stride + c] = static_cast<float>(in[map_off(rmap, r) + map_off(cmap, c)]);
+    const float x = static_cast<float>(in[map_off(rmap, r) + map_off(cmap, c)]);
+    if (SPLIT) tf32_split(x, out[r * stride + c], lo[r * stride + c]);
+    else out[r * stride + c] = x;
   }
 }
 
+template <bool SPLIT>
 __global__ void gather_f32f_k(const float* __restrict__ in, float* __restrict__ out,
-                              long long nrows, int ncols, long long stride, IdxMap rmap,
-                              IdxMap cmap) {
+                              float* __restrict__ lo, long long nrows, int ncols,
+                              long long stride, IdxMap rmap, IdxMap cmap) {
   const long long tot = nrows * ncols;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
     const long long r = e / ncols, c = e % ncols;
-    out[r * stride + c] = in[map_off(rmap, r) + map_off(cmap, c)];
+    const float x = in[map_off(rmap, r) + map_off(cmap, c)];
+    if (SPLIT) tf32_split(x, out[r * stride + c], lo[r * stride + c]);
+    else out[r * stride + c] = x;
+  }
+}
+
+__global__ void split_f32_k(float* __restrict__ x, float* __restrict__ lo, unsigned nrows,
+                            unsigned ncols, unsigned long long stride) {
+  const unsigned tot = nrows * ncols;
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
+    const unsigned r = e / ncols, c = e - r * ncols;
+    const unsigned long long o = r * stride + c;
+    float h, t;
+    tf32_split(x[o], h, t);
+    x[o] = h;
+    lo[o] = t;
   }
 }
 
 }  // namespace
 
 cudaError_t gather_f32f(const float* in, float* out, long long nrows, int ncols, long long stride,
-                        IdxMap rmap, IdxMap cmap, cudaStream_t s) {
+                        IdxMap rmap, IdxMap cmap, cudaStream_t s, float* lo) {
   const long long tot = nrows * ncols;
   if (tot <= 0) return cudaSuccess;
-  gather_f32f_k<<<(unsigned)std::min<long long>((tot + 255) / 256, 8192), 256, 0, s>>>(
-      in, out, nrows, ncols, stride, rmap, cmap);
+  const unsigned g = (unsigned)std::min<long long>((tot + 255) / 256, 8192);
+  if (lo) gather_f32f_k<true><<<g, 256, 0, s>>>(in, out, lo, nrows, ncols, stride, rmap, cmap);
+  else gather_f32f_k<false><<<g, 256, 0, s>>>(in, out, lo, nrows, ncols, stride, rmap, cmap);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t gather_f32(const double* in, float* out, long long nrows, int ncols, long long stride,
-                       IdxMap rmap, IdxMap cmap, cudaStream_t s) {
+                       IdxMap rmap, IdxMap cmap, cudaStream_t s, float* lo) {
   const long long tot = nrows * ncols;
   if (tot <= 0) return cudaSuccess;
-  gather_f32_k<<<(unsigned)std::min<long long>((tot + 255) / 256, 8192), 256, 0, s>>>(
-      in, out, nrows, ncols, stride, rmap, cmap);
+  const unsigned g = (unsigned)std::min<long long>((tot + 255) / 256, 8192);
+  if (lo) gather_f32_k<true><<<g, 256, 0, s>>>(in, out, lo, nrows, ncols, stride, rmap, cmap);
+  else gather_f32_k<false><<<g, 256, 0, s>>>(in, out, lo, nrows, ncols, stride, rmap, cmap);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t split_f32(float* x, float* lo, long long nrows, int ncols, long long stride,
+                      cudaStream_t s) {
+  const long long tot = nrows * ncols;
+  if (tot <= 0) return cudaSuccess;
+  if (tot >= (1ll << 32)) return cudaErrorInvalidValue;
+  const unsigned g = (unsigned)std::min<long long>((tot + 255) / 256, 8192);
+  split_f32_k<<<g, 256, 0, s>>>(x, lo, (unsigned)nrows, (unsigned)ncols,
+                                (unsigned long long)stride);
   note_launch();
   return cudaGetLastError();
 }

@@ -137,6 +137,21 @@ static __device__ __forceinline__ double rsqrt_nr(double a) {
   return y;
 }
 
+// Nearest TF32 (ties away from zero) of a finite x: add half a TF32 unit to
+// the magnitude bits and clear the 13 dropped ones (a carry moves into the
+// exponent, as rounding up to the next binade should).
+static __device__ __forceinline__ float tf32_rna_bits(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// Split of an FP32 x for the TF32x3 contraction: x = head + tail, both TF32
+// (x - head is exact in FP32 and |tail| <= 2^-11 |x|); a NaN stays the head
+// (Inf gives a NaN tail).
+static __device__ __forceinline__ void tf32_split(float x, float& head, float& tail) {
+  head = (x == x) ? tf32_rna_bits(x) : x;
+  tail = tf32_rna_bits(x - head);
+}
+
 // ---------------------------------------------------------------------------
 // Device-side error flag bits (written by kernels, read by the host).
 // ---------------------------------------------------------------------------
@@ -239,11 +254,16 @@ cudaError_t householder_qr_split(int m, int n, const double* M, double* R, const
 // pad4(m)); a caller that writes it itself passes x32_ready = true.
 float* qr_split_x32(float* f32);
 
-// out[r * stride + c] = (float) in[map(rmap, r) + map(cmap, c)], 0 <= c < ncols
+// out[r * stride + c] = (float) in[map(rmap, r) + map(cmap, c)], 0 <= c < ncols.
+// With lo set, the FP32 value is split (tf32_split): out gets the TF32 head,
+// lo[r * stride + c] the TF32 tail.
 cudaError_t gather_f32f(const float* in, float* out, long long nrows, int ncols, long long stride,
-                        IdxMap rmap, IdxMap cmap, cudaStream_t s);
+                        IdxMap rmap, IdxMap cmap, cudaStream_t s, float* lo = nullptr);
 cudaError_t gather_f32(const double* in, float* out, long long nrows, int ncols, long long stride,
-                       IdxMap rmap, IdxMap cmap, cudaStream_t s);
+                       IdxMap rmap, IdxMap cmap, cudaStream_t s, float* lo = nullptr);
+// In place: x[r * stride + c] -> its TF32 head, lo[r * stride + c] = its TF32 tail.
+cudaError_t split_f32(float* x, float* lo, long long nrows, int ncols, long long stride,
+                      cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Elementwise / reduction kernels.

@@ -16,7 +16,10 @@
 //
 // Every FP32 operand is stored K-contiguous with its row length padded to a
 // multiple of 4 floats (16 bytes, the TMA stride rule); the padding is never
-// read (TMA reads the true K extent and fills beyond it with zeros).
+// read (TMA reads the true K extent and fills beyond it with zeros).  The
+// operands that many output tiles share (T, C, both layouts of Q) are split
+// into TF32 head and tail planes once, when they are formed, instead of in
+// every tile of the contraction.
 #include "ctx.cuh"
 #include "tc_gemm.cuh"
 
@@ -27,8 +30,8 @@ namespace {
 inline long long pad4(long long x) { return (x + 3) & ~3ll; }
 
 TcOperand op(const float* p, long long rows, long long K, long long stride, int batch = 1,
-             long long bstride = 0) {
-  return TcOperand{p, rows, K, stride, batch, bstride};
+             long long bstride = 0, const float* lo = nullptr) {
+  return TcOperand{p, rows, K, stride, batch, bstride, lo};
 }
 
 TcGemm tc0(qrctm_ctx* c) {
@@ -70,10 +73,11 @@ cudaError_t qr_step_split(qrctm_ctx* c) {
   const long long mp = pad4(m);
   cudaStream_t st = c->st;
   cudaError_t e;
+  // heads; the tails sit in the *lo planes of the same layout
   float* T32 = c->T32;      // [(b,k_b,k_k)][a]   rows chi*D2, stride chp (k = k_k D + k_b)
   float* C32 = c->C32;      // [a][g]       stride chp
   float* Qt32 = c->Qt32;    // [(m,u)][a]   rows chi*D2, stride chp
-  float* Qc32 = c->Qc32;    // [n][(b,d)]   rows chi, stride mp
+  float* Qc32 = c->Qc32;    // [n][(b,d)]   rows chi, stride mp (FP32 Q, split after use)
   float* X1 = reinterpret_cast<float*>(c->X1);
   float* Zf = reinterpret_cast<float*>(c->Z);
   float* X2 = reinterpret_cast<float*>(c->X2);
@@ -82,14 +86,15 @@ cudaError_t qr_step_split(qrctm_ctx* c) {
     // rows (b, k_b, k_k) with k_k fastest: the X1 product then writes runs
     // along its lowest output digit
     if ((e = gather_f32(c->T, T32, m, ch, chp, im3(D, D, (long long)D * ch, ch, (long long)D2 * ch),
-                        im1(1), st)) != cudaSuccess)
+                        im1(1), st, c->T32lo)) != cudaSuccess)
       return e;
-    if ((e = gather_f32(c->C, C32, ch, ch, chp, im1(ch), im1(1), st)) != cudaSuccess) return e;
+    if ((e = gather_f32(c->C, C32, ch, ch, chp, im1(ch), im1(1), st, c->C32lo)) != cudaSuccess)
+      return e;
     // ct(a, (b,i)) = sum_g C[a,g] T[b,i,g]  ->  Mcm[b*m + a*D2 + i]
     // (column n = (b, i_b, i_k), i = i_k D + i_b)
     TcGemm g = tc0(c);
-    g.A = op(C32, ch, ch, chp);
-    g.B = op(T32, m, ch, chp);
+    g.A = op(C32, ch, ch, chp, 1, 0, c->C32lo);
+    g.B = op(T32, m, ch, chp, 1, 0, c->T32lo);
     g.M = ch; g.N = m; g.K = ch;
     g.C = c->Mcm; g.c_fp64 = true;
     g.c_m = im1(D2); g.c_n = im3(D, D, D, 1, m);
@@ -105,15 +110,17 @@ cudaError_t qr_step_split(qrctm_ctx* c) {
                                   c->tc_part, c->tc_part_elems, st)) != cudaSuccess)
       return e;
     // Qt32[(mu,u)][a] = Q[(a,u),mu]
-    if ((e = gather_f32f(Qc32, Qt32, m, ch, chp, im2(D2, 1, mp), im1(D2), st)) != cudaSuccess)
+    if ((e = gather_f32f(Qc32, Qt32, m, ch, chp, im2(D2, 1, mp), im1(D2), st, c->Qt32lo)) !=
+        cudaSuccess)
       return e;
+    if ((e = split_f32(Qc32, c->Qc32lo, ch, (int)m, mp, st)) != cudaSuccess) return e;
   }
   {
     PhaseScope ps(c, QRCTM_PH_X1);
     // X1 stored [m][b][u_b][k_b] x (u_k,k_k) with rows padded to D2p
     TcGemm g = tc0(c);
-    g.A = op(Qt32, m, ch, chp);
-    g.B = op(T32, m, ch, chp);
+    g.A = op(Qt32, m, ch, chp, 1, 0, c->Qt32lo);
+    g.B = op(T32, m, ch, chp, 1, 0, c->T32lo);
     g.M = m; g.N = m; g.K = ch;
     g.C = X1; g.c_fp64 = false;
     // row (mu,u): u = u_k*D + u_b ; col (b,k_b,k_k), k = k_k*D + k_b
@@ -155,7 +162,7 @@ cudaError_t qr_step_split(qrctm_ctx* c) {
     // T'[(mu,j)][n] = sum_{(b,d)} X2[(mu,j)][(b,d)] Q[(b,d),n]
     TcGemm g = tc0(c);
     g.A = op(X2, m, m, mp);
-    g.B = op(Qc32, ch, m, mp);
+    g.B = op(Qc32, ch, m, mp, 1, 0, c->Qc32lo);
     g.M = m; g.N = ch; g.K = m;
     g.C = c->Traw; g.c_fp64 = true;
     g.c_m = im1(ch); g.c_n = im1(1);
@@ -181,7 +188,7 @@ cudaError_t qr_step_split(qrctm_ctx* c) {
     // C'[n][p] = sum_{(g,j)} Y2[n][(g,j)] Q[(g,j),p]
     g = tc0(c);
     g.A = op(Y2f, ch, m, mp);
-    g.B = op(Qc32, ch, m, mp);
+    g.B = op(Qc32, ch, m, mp, 1, 0, c->Qc32lo);
     g.M = ch; g.N = ch; g.K = m;
     g.C = c->Craw; g.c_fp64 = true;
     g.c_m = im1(ch); g.c_n = im1(1);

@@ -348,11 +348,15 @@ __device__ __forceinline__ void epi_rows(const TcArgs& a, uint32_t acc, uint32_t
 // bounded; on timeout the kernel raises ERRF_TIMEOUT in the error word and
 // unwinds (TMEM is always freed).
 // ---------------------------------------------------------------------------
-template <int BN, int NBUF>
+template <int BN, int NBUF, int PRE>
 struct Cfg {
+  static constexpr bool PRE_A = PRE == 2, PRE_B = PRE >= 1;
   static constexpr int A_BYTES = BM * BK * 4;                       // 16 KB
   static constexpr int B_BYTES = BN * BK * 4;
-  static constexpr int STAGE_BYTES = A_BYTES + 2 * B_BYTES;         // A, B, tail(B)
+  static constexpr int A_PLANES = PRE_A ? 2 : 1;
+  // A (and tail(A) when A comes pre-split), B, tail(B)
+  static constexpr int STAGE_BYTES = A_PLANES * A_BYTES + 2 * B_BYTES;
+  static constexpr int TX_BYTES = A_PLANES * A_BYTES + (PRE_B ? 2 : 1) * B_BYTES;
   static constexpr int STG_BYTES = 4 * 32 * 33 * 4;                 // epilogue staging
   static constexpr int OFF_BYTES = 2 * BN * 8 + 2 * BM * 8;         // column and row offsets
   static constexpr int STAGES =
@@ -377,6 +381,16 @@ __device__ __forceinline__ void umma_tf32_tmem_a(uint32_t d_tmem, uint32_t a_tme
       : "memory");
 }
 
+// MMA with both operands in shared memory (descriptors).
+__device__ __forceinline__ void umma_tf32_ss(uint32_t d_tmem, uint64_t a, uint64_t b,
+                                             uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10,"
@@ -390,24 +404,13 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
       : "memory");
 }
 
-// Nearest TF32 (ties away from zero) of a finite x: add half a TF32 unit to
-// the magnitude bits and clear the 13 dropped ones (a carry moves into the
-// exponent, as rounding up to the next binade should).
-__device__ __forceinline__ float tf32_rna_bits(float x) {
-  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
-}
-
-// x = head + tail (both TF32); a NaN stays the head (Inf gives a NaN tail)
-__device__ __forceinline__ void tf32_split(float x, float& head, float& tail) {
-  head = (x == x) ? tf32_rna_bits(x) : x;
-  tail = tf32_rna_bits(x - head);
-}
-
-template <int BN, int NBUF>
+template <int BN, int NBUF, int PRE>
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_tf32x3_kernel(const __grid_constant__ CUtensorMap tmA,
-                     const __grid_constant__ CUtensorMap tmB, const TcArgs args) {
-  using C = Cfg<BN, NBUF>;
+                     const __grid_constant__ CUtensorMap tmB,
+                     const __grid_constant__ CUtensorMap tmAlo,
+                     const __grid_constant__ CUtensorMap tmBlo, const TcArgs args) {
+  using C = Cfg<BN, NBUF, PRE>;
   constexpr int S = C::STAGES, AS = C::A_STAGES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -426,8 +429,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   long long* row_off32 = row_off + BM;
 
   auto xA = [&](int s) { return tiles + s * C::STAGE_BYTES; };
-  auto xB = [&](int s) { return tiles + s * C::STAGE_BYTES + C::A_BYTES; };
-  auto loB = [&](int s) { return tiles + s * C::STAGE_BYTES + C::A_BYTES + C::B_BYTES; };
+  auto loA = [&](int s) { return tiles + s * C::STAGE_BYTES + C::A_BYTES; };   // PRE_A only
+  auto xB = [&](int s) { return tiles + s * C::STAGE_BYTES + C::A_PLANES * C::A_BYTES; };
+  auto loB = [&](int s) {
+    return tiles + s * C::STAGE_BYTES + C::A_PLANES * C::A_BYTES + C::B_BYTES;
+  };
   const uint32_t full0 = smem_u32(&bars[0]), conv0 = smem_u32(&bars[S]),
                  empty0 = smem_u32(&bars[2 * S]), tfree0 = smem_u32(&bars[3 * S]),
                  accf0 = smem_u32(&bars[3 * S + AS]), acce0 = smem_u32(&bars[3 * S + AS + NBUF]);
@@ -493,9 +499,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             ok = false;
             break;
           }
-          mbar_arrive_expect_tx(full0 + 8 * s, C::A_BYTES + C::B_BYTES);
+          mbar_arrive_expect_tx(full0 + 8 * s, C::TX_BYTES);
           tma_load(smem_u32(xA(s)), &tmA, (kb0 + kb) * BK, (int)m0, za, full0 + 8 * s);
+          if (C::PRE_A)
+            tma_load(smem_u32(loA(s)), &tmAlo, (kb0 + kb) * BK, (int)m0, za, full0 + 8 * s);
           tma_load(smem_u32(xB(s)), &tmB, (kb0 + kb) * BK, n0, zb, full0 + 8 * s);
+          if (C::PRE_B)
+            tma_load(smem_u32(loB(s)), &tmBlo, (kb0 + kb) * BK, n0, zb, full0 + 8 * s);
           issued = kbg + 1;
         }
       }
@@ -519,29 +529,44 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint32_t dmain = tmem + ab * 2 * C::HALF, dcorr = dmain + C::HALF;
         for (int kb = 0; kb < nkb; ++kb, ++kbg) {
           const int s = kbg % S, sa = kbg % AS;
-          ok = mbar_wait(conv0 + 8 * s, (kbg / S) & 1, abort_flag, args.err);
+          // both operands pre-split: the TMA landing is all the MMAs wait for
+          ok = mbar_wait((C::PRE_A ? full0 : conv0) + 8 * s, (kbg / S) & 1, abort_flag, args.err);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t ah = tmem + C::A_COL0 + sa * 64, al = ah + 32;
           const uint32_t bh = smem_u32(xB(s)), bl = smem_u32(loB(s));
           // head*head into the main accumulator; the two head*tail terms into
           // a separate one, so that the tensor core's truncating accumulation
           // never adds ~2^-11-sized terms to the large running sum
+          if (C::PRE_A) {
+            const uint32_t ah = smem_u32(xA(s)), al = smem_u32(loA(s));
 #pragma unroll
-          for (int ks = 0; ks < BK / 8; ++ks) {
-            const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
-            umma_tf32_tmem_a(dmain, ah + ks * 8, desc_sw128(bh + ks * 32), idesc, acc);
-            umma_tf32_tmem_a(dcorr, ah + ks * 8, desc_sw128(bl + ks * 32), idesc, acc);
-            umma_tf32_tmem_a(dcorr, al + ks * 8, desc_sw128(bh + ks * 32), idesc, 1u);
+            for (int ks = 0; ks < BK / 8; ++ks) {
+              const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
+              const uint64_t dah = desc_sw128(ah + ks * 32), dbh = desc_sw128(bh + ks * 32);
+              umma_tf32_ss(dmain, dah, dbh, idesc, acc);
+              umma_tf32_ss(dcorr, dah, desc_sw128(bl + ks * 32), idesc, acc);
+              umma_tf32_ss(dcorr, desc_sw128(al + ks * 32), dbh, idesc, 1u);
+            }
+            umma_commit(empty0 + 8 * s);    // shared-memory stage free
+          } else {
+            const uint32_t ah = tmem + C::A_COL0 + sa * 64, al = ah + 32;
+#pragma unroll
+            for (int ks = 0; ks < BK / 8; ++ks) {
+              const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
+              umma_tf32_tmem_a(dmain, ah + ks * 8, desc_sw128(bh + ks * 32), idesc, acc);
+              umma_tf32_tmem_a(dcorr, ah + ks * 8, desc_sw128(bl + ks * 32), idesc, acc);
+              umma_tf32_tmem_a(dcorr, al + ks * 8, desc_sw128(bh + ks * 32), idesc, 1u);
+            }
+            umma_commit(empty0 + 8 * s);    // shared-memory stage free
+            umma_commit(tfree0 + 8 * sa);   // tensor-memory A stage free
           }
-          umma_commit(empty0 + 8 * s);    // shared-memory stage free
-          umma_commit(tfree0 + 8 * sa);   // tensor-memory A stage free
         }
         if (ok) umma_commit(accf0 + 8 * ab);
       }
     }
-  } else if (warp < 2 + NCONV) {
+  } else if (warp < 2 + NCONV && !C::PRE_A) {
     // ---------------- converters (warps 2..5) ----------------
+    // (idle when both operands come pre-split)
     const int tc = threadIdx.x - 64;            // 0..127
     const int q = warp & 3;                     // TMEM lane quarter
     const int row = q * 32 + lane;              // A row = TMEM lane
@@ -558,11 +583,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           ok = false;
           break;
         }
-        // B: head in place, tail plane in the same swizzled layout
+        // B (unless it came pre-split): head in place, tail plane in the same
+        // swizzled layout
         float4* xb = reinterpret_cast<float4*>(xB(s));
         float4* lb = reinterpret_cast<float4*>(loB(s));
 #pragma unroll 2
-        for (int idx = tc; idx < BN * BK / 4; idx += 32 * NCONV) {
+        for (int idx = tc; idx < (C::PRE_B ? 0 : BN * BK / 4); idx += 32 * NCONV) {
           const float4 v = xb[idx];
           float4 hd, tl;
           tf32_split(v.x, hd.x, tl.x);
@@ -600,7 +626,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (lane == 0) mbar_arrive(conv0 + 8 * s);
       }
     }
-  } else {
+  } else if (warp >= 2 + NCONV) {
     // ---------------- epilogue (warps 6..9) ----------------
     const int te = threadIdx.x - 64 - 32 * NCONV;   // 0..127
     const int q = warp & 3;             // TMEM lane quarter of this warp
@@ -735,18 +761,24 @@ bool make_map(CUtensorMap* tm, const TcOperand& op, int box_rows) {
   return r == CUDA_SUCCESS;
 }
 
-template <int BN, int NBUF>
+template <int BN, int NBUF, int PRE>
 cudaError_t launch_bn(const TcGemm& g, cudaStream_t s) {
-  using C = Cfg<BN, NBUF>;
+  using C = Cfg<BN, NBUF, PRE>;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(tc_tf32x3_kernel<BN, NBUF>,
+    cudaError_t e = cudaFuncSetAttribute(tc_tf32x3_kernel<BN, NBUF, PRE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  CUtensorMap ta, tb;
-  if (!make_map(&ta, g.A, BM) || !make_map(&tb, g.B, BN)) return cudaErrorInvalidValue;
+  // tail planes (pre-split operands) share the layout of their head planes
+  TcOperand alo = g.A, blo = g.B;
+  if (C::PRE_A) alo.ptr = g.A.lo;
+  if (C::PRE_B) blo.ptr = g.B.lo;
+  CUtensorMap ta, tb, tal, tbl;
+  if (!make_map(&ta, g.A, BM) || !make_map(&tb, g.B, BN) || !make_map(&tal, alo, BM) ||
+      !make_map(&tbl, blo, BN))
+    return cudaErrorInvalidValue;
   TcArgs a{};
   a.M = g.M; a.N = g.N; a.K = g.K;
   a.C = g.C; a.c_fp64 = g.c_fp64 ? 1 : 0;
@@ -804,7 +836,7 @@ cudaError_t launch_bn(const TcGemm& g, cudaStream_t s) {
   const long long ntiles = ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN) * a.batch * ksplit;
   if (ntiles > (1ll << 31) - 1) return cudaErrorInvalidValue;
   const unsigned grid = (unsigned)(NBUF == 2 ? std::min<long long>(ntiles, nsm) : ntiles);
-  tc_tf32x3_kernel<BN, NBUF><<<grid, NTHREADS, C::SMEM, s>>>(ta, tb, a);
+  tc_tf32x3_kernel<BN, NBUF, PRE><<<grid, NTHREADS, C::SMEM, s>>>(ta, tb, tal, tbl, a);
   note_launch();
   if (ksplit > 1 && !g.partials_only) {
     const long long tot = g.M * g.N * std::max(1, g.batch);
@@ -818,11 +850,21 @@ cudaError_t launch_bn(const TcGemm& g, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int BN, int NBUF>
+cudaError_t launch_pre(const TcGemm& g, cudaStream_t s) {
+  if (g.A.lo != nullptr) return launch_bn<BN, NBUF, 2>(g, s);
+  if (g.B.lo != nullptr) return launch_bn<BN, NBUF, 1>(g, s);
+  return launch_bn<BN, NBUF, 0>(g, s);
+}
+
 }  // namespace
 
 cudaError_t gemm_tc(const TcGemm& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
   if (g.A.rows < 1 || g.B.rows < 1 || g.A.K != g.K || g.B.K != g.K) return cudaErrorInvalidValue;
+  // a pre-split A is taken with a pre-split B only (A's head plane must not
+  // be split again)
+  if (g.A.lo != nullptr && g.B.lo == nullptr) return cudaErrorInvalidValue;
   if (g.batch > 65535 || g.M > (1ll << 31) - BM) return cudaErrorInvalidValue;
   // double-buffered accumulators up to 96 columns per tile (tensor memory
   // holds 2 x (main, correction) x 96 columns next to two A stages); N in
@@ -834,13 +876,13 @@ cudaError_t gemm_tc(const TcGemm& g, cudaStream_t s) {
   // conversions per output of 96-column tiles), else 96-column tiles whose
   // epilogue overlaps the next tile.
   const long long N = g.N;
-  if (N <= 32) return launch_bn<32, 2>(g, s);
-  if (N <= 64) return launch_bn<64, 2>(g, s);
-  if (N <= 96) return launch_bn<96, 2>(g, s);
-  if (N <= 128) return launch_bn<64, 2>(g, s);    // two double-buffered tiles
-  if (N <= 144) return launch_bn<144, 1>(g, s);
-  if (N <= 192 || g.K >= 512) return launch_bn<192, 1>(g, s);
-  return launch_bn<96, 2>(g, s);
+  if (N <= 32) return launch_pre<32, 2>(g, s);
+  if (N <= 64) return launch_pre<64, 2>(g, s);
+  if (N <= 96) return launch_pre<96, 2>(g, s);
+  if (N <= 128) return launch_pre<64, 2>(g, s);    // two double-buffered tiles
+  if (N <= 144) return launch_pre<144, 1>(g, s);
+  if (N <= 192 || g.K >= 512) return launch_pre<192, 1>(g, s);
+  return launch_pre<96, 2>(g, s);
 }
 
 }  // namespace qrctm

@@ -8,6 +8,10 @@ namespace qrctm {
 // A K-contiguous FP32 operand: element (b, r, k) at ptr[b*batch_stride + r*row_stride + k].
 // row_stride and batch_stride (elements) must be multiples of 4 (16 bytes)
 // and ptr 16-byte aligned (TMA rules).
+// lo != nullptr marks a pre-split operand: ptr holds the TF32 heads and lo
+// the TF32 tails (tf32_split, same layout), so the kernel splits nothing; an
+// operand reused by many output tiles is split once instead of per tile.
+// A may come pre-split only together with B.
 struct TcOperand {
   const float* ptr;
   long long rows;
@@ -15,6 +19,7 @@ struct TcOperand {
   long long row_stride;
   int batch;               // 1 = shared by every batch entry
   long long batch_stride;
+  const float* lo;
 };
 
 // D[b](m,n) = alpha * sum_k A[b](m,k) B[b](n,k) + beta * D[b](m,n), D stored
