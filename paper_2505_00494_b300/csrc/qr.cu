@@ -29,23 +29,25 @@ __host__ __device__ inline size_t align_up(size_t x) { return (x + 255) & ~size_
 // Reflector scalars of a column with pivot value x0 and sigma = sum_{i>c}
 // x_i^2 > 0: mu = sqrt(x0^2 + sigma) (returned as rmu = 1/mu and mu),
 // w = x0 - mu (= -sigma / (x0 + mu) for x0 > 0, no cancellation) and
-// inv_w = 1/w.  tau = -w/mu follows when asked for.  The same code runs
-// inside the column loop and after it, so both see identical values.
+// inv_w = 1/w.  tau = -w/mu follows when asked for.  The column loop forms
+// the same values by the same operations (1/sigma on a second warp), so both
+// agree bit for bit; the _rn intrinsics keep the compiler from contracting
+// the products into different fused operations at the two sites.
 __device__ __forceinline__ void reflector(double x0, double sigma, double* rmu, double* mu,
                                           double* inv_w, double* tau) {
   const double a = fma(x0, x0, sigma);
   const double y = rsqrt_nr(a);
-  const double m = a * y;
+  const double m = __dmul_rn(a, y);
   *rmu = y;
   *mu = m;
   // x0 > 0 from the bits (an FP64 compare would take a 64-clock FP64 slot)
   const int x0h = __double2hiint(x0);
   if (x0h >= 0 && (x0h | __double2loint(x0)) != 0) {
-    const double xm = x0 + m;
-    *inv_w = -xm * rcp_nr(sigma);
+    const double xm = __dadd_rn(x0, m);
+    *inv_w = __dmul_rn(-xm, rcp_nr(sigma));
     if (tau) *tau = sigma * y * rcp_nr(xm);       // -w/mu with w = -sigma/(x0 + mu)
   } else {
-    const double w = x0 - m;
+    const double w = __dsub_rn(x0, m);
     *inv_w = rcp_nr(w);
     if (tau) *tau = -w * y;
   }
@@ -105,6 +107,7 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
   __shared__ double tau_s[NB];
   __shared__ double iw_s[NB];     // 1/w of column j (R entries after the loop)
   __shared__ double x0_s[NB];     // pivot value x_0 of column j as published
+  __shared__ double rsig_s;       // 1/sigma of the current column (warp 1)
   __shared__ int s_ok;
   extern __shared__ double tile[];                 // [rows][NB + 1]
   // element (global row i, panel column jc)
@@ -162,7 +165,23 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
     const long long c = (long long)j0 + j;
     const int nrem = nb - j - 1;
     const bool last = (j + 1 >= nb);
-    if (wrp == 0) {
+    if (wrp == 1) {
+      // 1/sigma for a pivot x_0 > 0 (1/w = -(x_0 + mu)/sigma), formed on a
+      // second SM sub-partition while warp 0 forms 1/mu: FP64 instructions
+      // of one sub-partition do not overlap
+      int okw = 1;
+      if (lane == 0) okw = grid_wait(bar, (unsigned)P * (unsigned)(j + 1), err) ? 1 : 0;
+      __syncwarp();
+      if (lane == 0) {
+        double rs = 0.0;
+        if (okw) {
+          const double sg = __ldcg(accum + (size_t)j * NB);
+          if (((__double2hiint(sg) & 0x7fffffff) | __double2loint(sg)) != 0) rs = rcp_nr(sg);
+        }
+        rsig_s = rs;
+      }
+      asm volatile("bar.arrive 3, 64;" ::: "memory");
+    } else if (wrp == 0) {
       int okw = 1;
       if (lane == 0) okw = grid_wait(bar, (unsigned)P * (unsigned)(j + 1), err) ? 1 : 0;
       __syncwarp();                                        // orders lane 0's acquire first
@@ -174,12 +193,22 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
       }
       ssum[j][lane] = st;
       if (lane == 0) x0_s[j] = y0;
-      double rmu = 0.0, inv_w = 0.0;
-      // st != 0 from the bits (an FP64 compare takes a 64-clock FP64 slot)
-      if (lane == 0 && ((__double2hiint(st) & 0x7fffffff) | __double2loint(st)) != 0) {
-        double mu;
-        reflector(y0, st, &rmu, &mu, &inv_w, nullptr);
+      double rmu = 0.0, inv_w = 0.0, xm = 0.0;
+      // st != 0 and x_0 > 0 from the bits (an FP64 compare takes a 64-clock
+      // FP64 slot); the scalars are those of reflector(), operation for
+      // operation, so the values after the loop agree bit for bit
+      const bool nz = ((__double2hiint(st) & 0x7fffffff) | __double2loint(st)) != 0;
+      const int x0h = __double2hiint(y0);
+      const bool pos = x0h >= 0 && (x0h | __double2loint(y0)) != 0;
+      if (lane == 0 && nz) {
+        const double a = fma(y0, y0, st);
+        rmu = rsqrt_nr(a);
+        const double m = __dmul_rn(a, rmu);
+        if (pos) xm = __dadd_rn(y0, m);
+        else inv_w = rcp_nr(__dsub_rn(y0, m));
       }
+      asm volatile("bar.sync 3, 64;" ::: "memory");       // warp 1's 1/sigma
+      if (lane == 0 && nz && pos) inv_w = __dmul_rn(-xm, rsig_s);
       // sigma = 0: x is zero below c, v = e_1 (tau = 0 or 2); the rows
       // below c are left as they are (multipliers 0)
       rmu = __shfl_sync(0xffffffffu, rmu, 0);

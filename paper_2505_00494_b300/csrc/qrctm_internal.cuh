@@ -110,31 +110,31 @@ static __device__ __forceinline__ double f64_of_bits(float f) {
   return __hiloint2double(static_cast<int>(hi), static_cast<int>(fb << 29));
 }
 
-// FP64 reciprocal by Newton's iteration from an FP32 seed (quadratic
-// convergence: 22 -> 44 -> 88 bits), avoiding the long-latency IEEE
-// double-precision divide sequence on the scalar path.  The range test and
-// the seed's conversions are integer operations.
+// FP64 reciprocal from an FP32 seed r0 by one third-order step: with
+// e = 1 - x r0 (|e| <= 2^-22), 1/x = r0 (1 + e + e^2 + ...), and
+// r0 (1 + e + e^2) leaves e^3 < 2^-66 (three dependent FP64 operations, no
+// long-latency IEEE divide sequence on the scalar path; results within an
+// ulp).  The range test and the seed's conversions are integer operations.
 static __device__ __forceinline__ double rcp_nr(double x) {
   const unsigned e = (static_cast<unsigned>(__double2hiint(x)) >> 20) & 0x7ffu;
   if (e < 1023u - 100u || e > 1023u + 100u) return 1.0 / x;   // outside the seed's range
-  double r = f64_of_bits(1.0f / f32_of_bits(x));
-  r = fma(r, fma(-x, r, 1.0), r);
-  r = fma(r, fma(-x, r, 1.0), r);
-  return r;
+  const double r = f64_of_bits(1.0f / f32_of_bits(x));
+  const double d = fma(-x, r, 1.0);
+  return fma(r, fma(d, d, d), r);
 }
 
-// 1/sqrt(a) in FP64 by two Newton steps y <- y (3/2 - a y^2 / 2) from the
-// FP32 estimate (22 -> 44 -> 88 bits), for a inside [2^-100, 2^100]; a / 2
-// by decrementing the exponent.
+// 1/sqrt(a) in FP64 from the FP32 estimate y0 by one third-order step: with
+// e = 1 - a y0^2 (y0^2 exact in FP64, |e| <= 2^-20),
+// 1/sqrt(a) = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8 + ...), truncated after
+// e^2 (error 5e^3/16 < 2^-61; five dependent FP64 operations), for a inside
+// [2^-100, 2^100].
 static __device__ __forceinline__ double rsqrt_nr(double a) {
   const unsigned hi = static_cast<unsigned>(__double2hiint(a));
   const unsigned e = (hi >> 20) & 0x7ffu;
   if ((hi >> 31) || e < 1023u - 100u || e > 1023u + 100u) return 1.0 / sqrt(a);
-  const double ha = __hiloint2double(static_cast<int>(hi - (1u << 20)), __double2loint(a));
-  double y = f64_of_bits(rsqrtf(f32_of_bits(a)));
-  y = y * fma(-ha, y * y, 1.5);
-  y = y * fma(-ha, y * y, 1.5);
-  return y;
+  const double y = f64_of_bits(rsqrtf(f32_of_bits(a)));
+  const double d = fma(-a, y * y, 1.0);
+  return fma(y * d, fma(d, 0.375, 0.5), y);
 }
 
 // Nearest TF32 (ties away from zero) of a finite x: add half a TF32 unit to
