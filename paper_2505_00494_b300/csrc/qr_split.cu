@@ -72,7 +72,7 @@ __device__ __forceinline__ float2 sum_partials(const float* __restrict__ p, long
 
 constexpr int NB = kQrPanel;
 constexpr int kWyThreads = 1024;   // two partial sums per thread for a 32 x 32 block
-constexpr int kQrMaxKsplit = 16;   // K chunks of the V^T [.] products
+constexpr int kQrMaxKsplit = 48;   // K chunks of the V^T [.] products (M = 32: more CTAs)
 
 inline long long pad4(long long x) { return (x + 3) & ~3ll; }
 
@@ -81,36 +81,38 @@ inline long long pad4(long long x) { return (x + 3) & ~3ll; }
 //   Yt[c][q] = (T^T S[:, ycol0 + c])[q];
 // mode 1 (formation of Q): T = Tp, Yt[c][q] = (T S[:, ycol0 + c])[q].
 // CTA b handles columns c in [32 b, 32 b + 32) of the ncol Y columns.
+// T and Y2 are formed in FP32, the precision of the tensor-core update that
+// consumes them (and of G, whose entries are compensated FP32 sums of
+// TF32x3 products): the recursion's dependent chains then cost FP32
+// latencies instead of B300's 64-clock FP64 ones.  T's diagonal (tau) is
+// kept in FP64 in Tp for the formation of Q.
 __global__ void __launch_bounds__(kWyThreads) wy_prep_kernel(const float* __restrict__ part,
                                                              int ksplit, int nb, long long N,
                                                              int ycol0, int ncol,
                                                              const double* __restrict__ tau,
                                                              double* __restrict__ Tp,
                                                              float* __restrict__ Yt, int mode) {
-  __shared__ double Ts[NB][NB + 1];
-  __shared__ double Gs[NB][NB + 1];
-  __shared__ double Ws[NB][NB + 1];
-  __shared__ double Ys[NB][NB + 1];
-  __shared__ float Tf[NB][NB + 1];
+  __shared__ float Ts[NB][NB + 1];
+  __shared__ float Gs[NB][NB + 1];
+  __shared__ float Ws[NB][NB + 1];
   __shared__ float Yf[NB][NB + 1];
   const int tid = threadIdx.x;
   const int c0 = blockIdx.x * NB;
   const long long MN = (long long)nb * N;
   // sum of the K-chunk partials by compensated FP32 summation (Knuth's
-  // TwoSum: s + e carries the sum exactly up to the final rounding), so that
-  // the narrow FP64 pipe only sees one conversion pair and one add
+  // TwoSum: s + e carries the sum up to the final rounding)
   auto psum = [&](int q, long long col) {
     const float2 r = sum_partials(part + (long long)q * N + col, MN, ksplit);
-    return static_cast<double>(r.x) + static_cast<double>(r.y);
+    return r.x + r.y;
   };
   for (int e = tid; e < NB * NB; e += kWyThreads) {
     const int q = e / NB, c = e % NB;
-    Ys[q][c] = (q < nb && c0 + c < ncol) ? psum(q, ycol0 + c0 + c) : 0.0;
+    Yf[q][c] = (q < nb && c0 + c < ncol) ? psum(q, ycol0 + c0 + c) : 0.f;
     if (mode == 0) {
-      Gs[q][c] = (q < nb && c < nb) ? psum(q, c) : 0.0;
-      Ts[q][c] = (q == c && q < nb) ? tau[q] : 0.0;
+      Gs[q][c] = (q < nb && c < nb) ? psum(q, c) : 0.f;
+      Ts[q][c] = (q == c && q < nb) ? static_cast<float>(tau[q]) : 0.f;
     } else {
-      Ts[q][c] = Tp[q * NB + c];
+      Ts[q][c] = static_cast<float>(Tp[q * NB + c]);
     }
   }
   __syncthreads();
@@ -121,37 +123,34 @@ __global__ void __launch_bounds__(kWyThreads) wy_prep_kernel(const float* __rest
       const int cnt = (NB / (2 * s)) * s * s;
       for (int e = tid; e < cnt; e += kWyThreads) {
         const int k = e / (s * s), i = (e / s) % s, j = e % s, b0 = 2 * s * k;
-        double acc = 0.0;
-        for (int l = 0; l <= j; ++l) acc = fma(Gs[b0 + i][b0 + s + l], Ts[b0 + s + l][b0 + s + j], acc);
+        float acc = 0.f;
+        for (int l = 0; l <= j; ++l) acc = fmaf(Gs[b0 + i][b0 + s + l], Ts[b0 + s + l][b0 + s + j], acc);
         Ws[b0 + i][b0 + s + j] = acc;
       }
       __syncthreads();
       for (int e = tid; e < cnt; e += kWyThreads) {
         const int k = e / (s * s), i = (e / s) % s, j = e % s, b0 = 2 * s * k;
-        double acc = 0.0;
-        for (int l = i; l < s; ++l) acc = fma(Ts[b0 + i][b0 + l], Ws[b0 + l][b0 + s + j], acc);
+        float acc = 0.f;
+        for (int l = i; l < s; ++l) acc = fmaf(Ts[b0 + i][b0 + l], Ws[b0 + l][b0 + s + j], acc);
         Ts[b0 + i][b0 + s + j] = -acc;
       }
       __syncthreads();
     }
     if (blockIdx.x == 0)
-      for (int e = tid; e < NB * NB; e += kWyThreads) Tp[e] = Ts[e / NB][e % NB];
+      for (int e = tid; e < NB * NB; e += kWyThreads) {
+        const int q = e / NB, c = e % NB;
+        Tp[e] = (q == c && q < nb) ? tau[q] : static_cast<double>(Ts[q][c]);
+      }
   }
-  // Y2 = T^T Y (mode 0) or T Y (mode 1) in FP32 (the operand precision of
-  // the tensor-core update that consumes it), written transposed
-  for (int e = tid; e < NB * NB; e += kWyThreads) {
-    Tf[e / NB][e % NB] = static_cast<float>(Ts[e / NB][e % NB]);
-    Yf[e / NB][e % NB] = static_cast<float>(Ys[e / NB][e % NB]);
-  }
-  __syncthreads();
+  // Y2 = T^T Y (mode 0) or T Y (mode 1), written transposed
   for (int e = tid; e < NB * NB; e += kWyThreads) {
     const int c = e / NB, q = e % NB;
     if (c0 + c >= ncol) continue;
     float acc = 0.f;
     if (mode == 0) {
-      for (int l = 0; l <= q; ++l) acc = fmaf(Tf[l][q], Yf[l][c], acc);
+      for (int l = 0; l <= q; ++l) acc = fmaf(Ts[l][q], Yf[l][c], acc);
     } else {
-      for (int l = q; l < NB; ++l) acc = fmaf(Tf[q][l], Yf[l][c], acc);
+      for (int l = q; l < NB; ++l) acc = fmaf(Ts[q][l], Yf[l][c], acc);
     }
     Yt[(long long)(c0 + c) * NB + q] = acc;
   }
