@@ -114,6 +114,8 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
   take(R_(Xs), m * chi);
   take(R_(Yw), m * chi);
   take(R_(spec_work), nC + 8 * chi + 16);
+  take(R_(spec_work2), nC + 8 * chi + 16);
+  take(R_(C_init), nC);
   take(R_(s_cur), chi);
   take(R_(s_prev), chi);
   take(R_(delta_d), 8);
@@ -318,6 +320,7 @@ qrctm_status qrctm_create(const qrctm_config* cfg, void* workspace, size_t bytes
   c->last_delta = INFINITY;
   c->have_env = false;
   c->spec_valid = false;
+  c->spec_pending = false;
   // zero the control words (error flag, QR grid barrier)
   cudaError_t e = cudaMemsetAsync(c->err, 0, 256, c->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->qrw.bar, 0, sizeof(GridBar), c->st);
@@ -491,12 +494,17 @@ cudaError_t qr_step_graph(qrctm_ctx* c) {
 }
 
 qrctm_status finish_init(qrctm_ctx* c) {
-  // the error word collects the set-up kernels' and the spectrum's failures:
-  // one check after both
+  // The spectrum of the fresh corner is taken at the first convergence test,
+  // in the same launches as the then-current corner's (one tridiagonalisation
+  // latency instead of two); until then the corner waits in C_init.
   cudaError_t e;
-  if ((e = spectrum_check(c)) != cudaSuccess) return cuda_fail(c, e, "spectrum");
+  if ((e = cudaMemcpyAsync(c->C_init, c->C, sizeof(double) * (size_t)c->chi_cur * c->chi_cur,
+                           cudaMemcpyDeviceToDevice, c->st)) != cudaSuccess)
+    return cuda_fail(c, e, "init env");
+  c->chi_init = c->chi_cur;
   qrctm_status s = sync_check(c, "init env");
   if (s != QRCTM_OK) return s;
+  c->spec_pending = true;
   c->spec_valid = true;
   c->have_env = true;
   return QRCTM_OK;
@@ -530,6 +538,7 @@ qrctm_status qrctm_init_env(qrctm_ctx* c, const double* A, const double* C0, con
   }
   c->iters = 0;
   c->spec_valid = false;
+  c->spec_pending = false;
   if (C0 != nullptr) {
     c->chi_cur = c->chi;
     if ((e = sym_norm_env(C0, T0, c->C, c->T, c->chi, D2, c->partials, c->err, c->st)) !=
@@ -563,6 +572,7 @@ qrctm_status qrctm_init_env_network(qrctm_ctx* c, const double* a, const double*
   if (s != QRCTM_OK) return s;
   c->iters = 0;
   c->spec_valid = false;
+  c->spec_pending = false;
   if (C0 != nullptr) {
     c->chi_cur = c->chi;
     if ((e = sym_norm_env(C0, T0, c->C, c->T, c->chi, b, c->partials, c->err, c->st)) !=

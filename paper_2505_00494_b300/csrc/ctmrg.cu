@@ -193,6 +193,13 @@ cudaError_t warmup_step(qrctm_ctx* c, int ci, int co) {
 
 cudaError_t spectrum_check(qrctm_ctx* c) {
   PhaseScope ps(c, QRCTM_PH_SPECTRUM);
+  if (c->spec_pending) {
+    // first test after an initialisation: s_prev <- |eig(C_init)| and
+    // s_cur <- |eig(C)| in one set of launches
+    c->spec_pending = false;
+    return corner_spectrum_pair(c->C_init, c->chi_init, c->spec_work2, c->s_prev, c->C,
+                                c->chi_cur, c->spec_work, c->s_cur, c->delta_d, c->err, c->st);
+  }
   // s_prev <- s_cur, then s_cur <- |eig(C)|, delta <- ||s_cur - s_prev||
   cudaError_t e = cudaMemcpyAsync(c->s_prev, c->s_cur, sizeof(double) * c->chi,
                                   cudaMemcpyDeviceToDevice, c->st);

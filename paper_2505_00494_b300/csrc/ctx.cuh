@@ -27,6 +27,11 @@ struct qrctm_ctx {
   double *Xs, *Yw;
   // spectrum
   double *spec_work, *s_cur, *s_prev, *delta_d;
+  // corner of a fresh environment whose spectrum is still to be taken: the
+  // first convergence test reduces it beside the current corner
+  double *C_init, *spec_work2;
+  int chi_init;
+  bool spec_pending;
   double* partials;
   double* tmpA;
   double* a;           // double layer (only with DOUBLE layers)

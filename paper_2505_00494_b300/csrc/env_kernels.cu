@@ -432,18 +432,26 @@ __device__ __forceinline__ double warp_sum4(double a0, double a1, double a2, dou
   return v;
 }
 
+// njobs = 2: a second cluster reduces (C1, work1), same n, in the same launch.
 template <int CS, bool GMEM>
-__global__ void __launch_bounds__(256) spectrum_cluster_kernel(const double* __restrict__ C, int n,
-                                                               double* work, int* err) {
+__global__ void __launch_bounds__(256) spectrum_cluster_kernel(const double* __restrict__ C0, int n,
+                                                               double* work0,
+                                                               const double* __restrict__ C1,
+                                                               double* work1, int njobs,
+                                                               int* err) {
   extern __shared__ double csm[];
   __shared__ double red[32];
   __shared__ double sc[6];
   __shared__ double pvp[2];
-  // the row distribution needs exactly CS CTAs in one cluster
-  if (cluster_size() != (unsigned)CS || gridDim.x != (unsigned)CS) {
+  // the row distribution needs exactly CS CTAs per cluster, one cluster per job
+  if (cluster_size() != (unsigned)CS || (njobs != 1 && njobs != 2) ||
+      gridDim.x != (unsigned)(CS * njobs)) {
     if (threadIdx.x == 0) atomicOr(err, ERRF_BOUNDS);
     return;
   }
+  const bool second = blockIdx.x >= (unsigned)CS;
+  const double* __restrict__ C = second ? C1 : C0;
+  double* work = second ? work1 : work0;
   const unsigned r = cluster_rank();
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wrp = tid >> 5;
   const int nloc = (n - (int)r + CS - 1) / CS;          // rows r, r + CS, ...
@@ -751,8 +759,13 @@ __device__ int sturm_count_fast(const F* dg, const F* me2, int n, F x, bool& hit
 // ||T||, widened by a margin covering the FP32 counts' error, checked by two
 // FP64 counts (the Gershgorin interval is used instead if the check fails),
 // and refined in FP64 (128 points, 7 bits per round) down to 4e-16 ||T||.
-__global__ void __launch_bounds__(kBisectThreads) bisect_kernel(const double* work, int n,
-                                                                double* ev_out) {
+// blockIdx.y = 1: the second job (work1, ev1), same n.
+__global__ void __launch_bounds__(kBisectThreads) bisect_kernel(const double* work0, int n,
+                                                                double* ev0,
+                                                                const double* work1,
+                                                                double* ev1) {
+  const double* work = blockIdx.y ? work1 : work0;
+  double* ev_out = blockIdx.y ? ev1 : ev0;
   __shared__ double sdg[kBisectMaxN], se2[kBisectMaxN], ndg[kBisectMaxN], nme2[kBisectMaxN];
   __shared__ float fdg[kBisectMaxN], fme2[kBisectMaxN];
   __shared__ unsigned masks[kBisectThreads / 32];
@@ -901,7 +914,7 @@ __global__ void spectrum_finish_kernel(const double* ev, int n, double* s_new, c
     acc += (x - y) * (x - y);
   }
   double tot = block_sum(acc, red, &out);
-  if (tid == 0) *delta = sqrt(tot);
+  if (tid == 0) if (delta) *delta = sqrt(tot);
 }
 
 inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -1050,10 +1063,16 @@ cudaError_t double_layer_kernel(int d, int D, const double* A, double* a, cudaSt
 
 // work: chi*chi + 8*chi + 16 doubles: matrix, diagonal, off-diagonal, (unused),
 // squared off-diagonal, Gershgorin bracket + pivot floor, eigenvalues
-cudaError_t corner_spectrum(const double* C, int chi, double* work, double* s_new,
-                            const double* s_old, int chi_old, double* delta, int* err,
-                            cudaStream_t s) {
+// Tridiagonalisation, multisection and ranking of one corner (C1 == nullptr)
+// or of two of the same size: with C1 the two clusters and the two sets of
+// bisection CTAs share launches; s_new0 gets |eig(C0)| (no change measured),
+// s_new gets |eig(C1)| and delta its change to s_new0.
+static cudaError_t spectra(const double* C, int chi, double* work, double* s_new0,
+                           const double* C1, double* work1, double* s_new,
+                           const double* s_old, int chi_old, double* delta, int* err,
+                           cudaStream_t s) {
   if (chi < 1 || chi > 1024) return cudaErrorInvalidValue;
+  const int njobs = C1 ? 2 : 1;
   const size_t smem = (chi <= kSmemSpecMax) ? sizeof(double) * chi * (chi + 1) : 0;
   static bool attr = false;
   if (!attr) {
@@ -1115,7 +1134,7 @@ cudaError_t corner_spectrum(const double* C, int chi, double* work, double* s_ne
     const size_t csmem = sizeof(double) * ((gmem ? 0 : (size_t)nloc_max * chi) +
                                            3 * (size_t)nloc_max + 5 * (size_t)chi);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(cs);
+    cfg.gridDim = dim3(cs * njobs);
     cfg.blockDim = dim3(256);
     cfg.dynamicSmemBytes = csmem;
     cfg.stream = s;
@@ -1126,18 +1145,49 @@ cudaError_t corner_spectrum(const double* C, int chi, double* work, double* s_ne
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, C, chi, work, err);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, C, chi, work, C1 ? C1 : C, C1 ? work1 : work,
+                                       njobs, err);
     if (e != cudaSuccess) return e;
     launched = true;
   }
-  if (!launched) spectrum_kernel<<<1, 1024, smem, s>>>(C, chi, work, err);
+  if (!launched) {
+    spectrum_kernel<<<1, 1024, smem, s>>>(C, chi, work, err);
+    if (C1) {
+      note_launch();
+      spectrum_kernel<<<1, 1024, smem, s>>>(C1, chi, work1, err);
+    }
+  }
   note_launch();
   double* ev = work + (size_t)chi * chi + 5 * (size_t)chi + 8;
-  bisect_kernel<<<chi, kBisectThreads, 0, s>>>(work, chi, ev);
+  double* ev1 = C1 ? work1 + (size_t)chi * chi + 5 * (size_t)chi + 8 : ev;
+  bisect_kernel<<<dim3(chi, njobs), kBisectThreads, 0, s>>>(work, chi, ev, C1 ? work1 : work, ev1);
   note_launch();
-  spectrum_finish_kernel<<<1, 256, 0, s>>>(ev, chi, s_new, s_old, chi_old, delta);
+  if (C1) {
+    spectrum_finish_kernel<<<1, 256, 0, s>>>(ev, chi, s_new0, nullptr, 0, nullptr);
+    note_launch();
+    spectrum_finish_kernel<<<1, 256, 0, s>>>(ev1, chi, s_new, s_new0, chi, delta);
+  } else {
+    spectrum_finish_kernel<<<1, 256, 0, s>>>(ev, chi, s_new, s_old, chi_old, delta);
+  }
   note_launch();
   return cudaGetLastError();
+}
+
+cudaError_t corner_spectrum(const double* C, int chi, double* work, double* s_new,
+                            const double* s_old, int chi_old, double* delta, int* err,
+                            cudaStream_t s) {
+  return spectra(C, chi, work, nullptr, nullptr, nullptr, s_new, s_old, chi_old, delta, err, s);
+}
+
+cudaError_t corner_spectrum_pair(const double* C0, int chi0, double* work0, double* s0,
+                                 const double* C1, int chi1, double* work1, double* s1,
+                                 double* delta, int* err, cudaStream_t s) {
+  if (chi0 == chi1)
+    return spectra(C0, chi0, work0, s0, C1, work1, s1, nullptr, 0, delta, err, s);
+  cudaError_t e = spectra(C0, chi0, work0, nullptr, nullptr, nullptr, s0, nullptr, 0, nullptr,
+                          err, s);
+  if (e != cudaSuccess) return e;
+  return spectra(C1, chi1, work1, nullptr, nullptr, nullptr, s1, s0, chi0, delta, err, s);
 }
 
 cudaError_t fill_zero(double* p, long long n, cudaStream_t s) {

@@ -563,6 +563,7 @@ cudaError_t energy_grad_run(qrctm_ctx* c, double J1, double J2, int mode, int k_
       cudaMemcpyAsync(c->T, L.ckT + K * mc, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s);
       c->iters += K;
       c->spec_valid = false;
+      c->spec_pending = false;
     }
   }
   // project onto the C4v subspace

@@ -284,6 +284,12 @@ cudaError_t set_identity_cols(double* Q, int m, int n, cudaStream_t s);
 cudaError_t corner_spectrum(const double* C, int chi, double* work, double* s_new,
                             const double* s_old, int chi_old, double* delta, int* err,
                             cudaStream_t s);
+// |eig(C0)| -> s0 and |eig(C1)| -> s1 with delta = ||s1 - s0||; for equal
+// sizes the two corners share one set of launches (two clusters, two rows
+// of bisection CTAs).
+cudaError_t corner_spectrum_pair(const double* C0, int chi0, double* work0, double* s0,
+                                 const double* C1, int chi1, double* work1, double* s1,
+                                 double* delta, int* err, cudaStream_t s);
 cudaError_t fill_zero(double* p, long long n, cudaStream_t s);
 cudaError_t axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t s);
 
