@@ -91,17 +91,27 @@ def panel_flops(d, D, chi, m=None):
 def load_traffic(precision, workload):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
     from the committed ncu capture summary of this precision and workload,
-    keyed by step phase (first column; the kernel's name follows the bytes);
-    empty when there is none."""
+    keyed by step phase (first column), with the name of the kernel the
+    capture measured (the rest of the line); empty when there is none."""
     out = {}
     try:
         for line in open(os.path.join(ROOT, "profiles", f"traffic_{precision}_{workload}.txt")):
             parts = line.split()
             if len(parts) >= 2 and not line.startswith("#"):
-                out[parts[0]] = float(parts[1])
+                out[parts[0]] = (float(parts[1]), " ".join(parts[2:]))
     except OSError:
         pass
     return out
+
+
+def traffic_of(traffic, phase, kernel):
+    """Captured bytes of a phase, or None when the capture measured another
+    kernel than the one the row names (a capture older than the kernel)."""
+    t = traffic.get(phase)
+    if t is None:
+        return None
+    nbytes, name = t
+    return nbytes if name.startswith(kernel.split(" (")[0]) else None
 
 
 def load_peaks():
@@ -325,7 +335,7 @@ def roofline_rows(kernels, phases, prof_ms, traffic):
                     "unit": "TFLOP/s", "frac": ach / peak_k, "avg_launch_ms": avg * 1e3,
                     "launches": n_k, "share_of_step": ms_k / prof_ms,
                     "algorithmic_flops_per_launch": flops, "peak_source": note_k,
-                    "traffic": traffic.get(ph)}
+                    "traffic": traffic_of(traffic, ph, kname)}
     return rows
 
 
