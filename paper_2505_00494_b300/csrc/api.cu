@@ -147,6 +147,7 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
     takef(carve ? &c->C32lo : &fdummy, chi * chp);
     takef(carve ? &c->Qt32lo : &fdummy, m * chp);
     takef(carve ? &c->Qc32lo : &fdummy, chi * mp);
+    takef(carve ? &c->Rt32lo : &fdummy, chi * chp);
     takef(carve ? &c->Ts32 : &fdummy, m * chp);
     takef(carve ? &c->Rt32 : &fdummy, chi * chp);
     takef(carve ? &c->Aket32 : &fdummy, d * D2 * D2p);
@@ -159,7 +160,7 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
     // names: for D >= 2 each needs at most as many bytes as its FP64 region
   } else if (carve) {
     c->T32 = c->C32 = c->Qt32 = c->Qc32 = c->Ts32 = c->Rt32 = c->Aket32 = c->Abra32 = nullptr;
-    c->T32lo = c->C32lo = c->Qt32lo = c->Qc32lo = nullptr;
+    c->T32lo = c->C32lo = c->Qt32lo = c->Qc32lo = c->Rt32lo = nullptr;
     c->qr32 = nullptr;
     c->tc_part = nullptr;
     c->tc_part_elems = 0;

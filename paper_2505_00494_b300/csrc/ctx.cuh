@@ -41,7 +41,7 @@ struct qrctm_ctx {
   // tensor-core split-K partial sums
   float *T32, *C32, *Qt32, *Qc32, *Ts32, *Rt32, *Aket32, *Abra32, *tc_part, *qr32;
   // TF32 tails of the pre-split operands (T32, C32, Qt32, Qc32 then hold the heads)
-  float *T32lo, *C32lo, *Qt32lo, *Qc32lo;
+  float *T32lo, *C32lo, *Qt32lo, *Qc32lo, *Rt32lo;
   long long tc_part_elems;
   // gradient
   char* G;             // gradient region base (carved by grad.cu)

@@ -89,15 +89,17 @@ __global__ void sym_corner_kernel(const double* __restrict__ C, double* __restri
   Co[e] = 0.5 * (C[e] + C[(long long)j * chi + i]);
 }
 
+// I: index type (32-bit when chi D2 chi fits: 32-bit divisions)
+template <typename I>
 __global__ void sym_edge_kernel(const double* __restrict__ T, double* __restrict__ To, int chi,
                                 int D2) {
-  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  long long tot = (long long)chi * D2 * chi;
+  const I e = static_cast<I>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const I tot = static_cast<I>(chi) * D2 * chi;
   if (e >= tot) return;
-  long long a = e / ((long long)D2 * chi);
-  long long r = e % ((long long)D2 * chi);
-  long long k = r / chi, b = r % chi;
-  To[e] = 0.5 * (T[e] + T[(b * D2 + k) * chi + a]);
+  const I dc = static_cast<I>(D2) * chi;
+  const I a = e / dc, r = e - a * dc;
+  const I k = r / chi, b = r - k * chi;
+  To[e] = 0.5 * (T[e] + T[(static_cast<long long>(b) * D2 + k) * chi + a]);
 }
 
 // C0[(d d'),(r r')] = sum_{s,u,l} A[s,u,l,d,r] A[s,u,l,d',r']
@@ -919,31 +921,41 @@ __global__ void spectrum_finish_kernel(const double* ev, int n, double* s_new, c
 
 inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
-template <bool SPLIT>
+// I: the flat index type (32-bit whenever nrows * ncols fits, so that the
+// row/column split and the index maps use 32-bit divisions).
+template <typename I>
+__device__ __forceinline__ long long map_off_i(const IdxMap& m, I i) {
+  if (sizeof(I) == 4) return map_off32(m, static_cast<unsigned>(i));
+  return map_off(m, static_cast<long long>(i));
+}
+
+template <bool SPLIT, typename I>
 __global__ void gather_f32_k(const double* __restrict__ in, float* __restrict__ out,
                              float* __restrict__ lo, long long nrows, int ncols,
                              long long stride, IdxMap rmap, IdxMap cmap) {
-  const long long tot = nrows * ncols;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long r = e / ncols, c = e % ncols;
-    const float x = static_cast<float>(in[map_off(rmap, r) + map_off(cmap, c)]);
-    if (SPLIT) tf32_split(x, out[r * stride + c], lo[r * stride + c]);
-    else out[r * stride + c] = x;
+  const I tot = static_cast<I>(nrows * ncols), nc = static_cast<I>(ncols);
+  for (I e = static_cast<I>(blockIdx.x) * blockDim.x + threadIdx.x; e < tot;
+       e += static_cast<I>(gridDim.x) * blockDim.x) {
+    const I r = e / nc, c = e - r * nc;
+    const float x = static_cast<float>(in[map_off_i(rmap, r) + map_off_i(cmap, c)]);
+    const long long o = static_cast<long long>(r) * stride + static_cast<long long>(c);
+    if (SPLIT) tf32_split(x, out[o], lo[o]);
+    else out[o] = x;
   }
 }
 
-template <bool SPLIT>
+template <bool SPLIT, typename I>
 __global__ void gather_f32f_k(const float* __restrict__ in, float* __restrict__ out,
                               float* __restrict__ lo, long long nrows, int ncols,
                               long long stride, IdxMap rmap, IdxMap cmap) {
-  const long long tot = nrows * ncols;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long r = e / ncols, c = e % ncols;
-    const float x = in[map_off(rmap, r) + map_off(cmap, c)];
-    if (SPLIT) tf32_split(x, out[r * stride + c], lo[r * stride + c]);
-    else out[r * stride + c] = x;
+  const I tot = static_cast<I>(nrows * ncols), nc = static_cast<I>(ncols);
+  for (I e = static_cast<I>(blockIdx.x) * blockDim.x + threadIdx.x; e < tot;
+       e += static_cast<I>(gridDim.x) * blockDim.x) {
+    const I r = e / nc, c = e - r * nc;
+    const float x = in[map_off_i(rmap, r) + map_off_i(cmap, c)];
+    const long long o = static_cast<long long>(r) * stride + static_cast<long long>(c);
+    if (SPLIT) tf32_split(x, out[o], lo[o]);
+    else out[o] = x;
   }
 }
 
@@ -967,8 +979,16 @@ cudaError_t gather_f32f(const float* in, float* out, long long nrows, int ncols,
   const long long tot = nrows * ncols;
   if (tot <= 0) return cudaSuccess;
   const unsigned g = (unsigned)std::min<long long>((tot + 255) / 256, 8192);
-  if (lo) gather_f32f_k<true><<<g, 256, 0, s>>>(in, out, lo, nrows, ncols, stride, rmap, cmap);
-  else gather_f32f_k<false><<<g, 256, 0, s>>>(in, out, lo, nrows, ncols, stride, rmap, cmap);
+  const bool i32 = tot < (1ll << 32) - 2ll * 8192 * 256;
+  if (lo && i32)
+    gather_f32f_k<true, unsigned><<<g, 256, 0, s>>>(in, out, lo, nrows, ncols, stride, rmap, cmap);
+  else if (lo)
+    gather_f32f_k<true, long long><<<g, 256, 0, s>>>(in, out, lo, nrows, ncols, stride, rmap, cmap);
+  else if (i32)
+    gather_f32f_k<false, unsigned><<<g, 256, 0, s>>>(in, out, lo, nrows, ncols, stride, rmap, cmap);
+  else
+    gather_f32f_k<false, long long><<<g, 256, 0, s>>>(in, out, lo, nrows, ncols, stride, rmap,
+                                                      cmap);
   note_launch();
   return cudaGetLastError();
 }
@@ -978,8 +998,16 @@ cudaError_t gather_f32(const double* in, float* out, long long nrows, int ncols,
   const long long tot = nrows * ncols;
   if (tot <= 0) return cudaSuccess;
   const unsigned g = (unsigned)std::min<long long>((tot + 255) / 256, 8192);
-  if (lo) gather_f32_k<true><<<g, 256, 0, s>>>(in, out, lo, nrows, ncols, stride, rmap, cmap);
-  else gather_f32_k<false><<<g, 256, 0, s>>>(in, out, lo, nrows, ncols, stride, rmap, cmap);
+  const bool i32 = tot < (1ll << 32) - 2ll * 8192 * 256;
+  if (lo && i32)
+    gather_f32_k<true, unsigned><<<g, 256, 0, s>>>(in, out, lo, nrows, ncols, stride, rmap, cmap);
+  else if (lo)
+    gather_f32_k<true, long long><<<g, 256, 0, s>>>(in, out, lo, nrows, ncols, stride, rmap, cmap);
+  else if (i32)
+    gather_f32_k<false, unsigned><<<g, 256, 0, s>>>(in, out, lo, nrows, ncols, stride, rmap, cmap);
+  else
+    gather_f32_k<false, long long><<<g, 256, 0, s>>>(in, out, lo, nrows, ncols, stride, rmap,
+                                                     cmap);
   note_launch();
   return cudaGetLastError();
 }
@@ -1022,7 +1050,10 @@ cudaError_t scale_by_inv_norm(const double* x, double* y, long long n, const dou
 
 cudaError_t sym_edge(const double* Tin, double* Tout, int chi, int D2, cudaStream_t s) {
   long long n = (long long)chi * D2 * chi;
-  sym_edge_kernel<<<nblk(n), 256, 0, s>>>(Tin, Tout, chi, D2);
+  if (n < (1ll << 32) - 256)
+    sym_edge_kernel<unsigned><<<nblk(n), 256, 0, s>>>(Tin, Tout, chi, D2);
+  else
+    sym_edge_kernel<long long><<<nblk(n), 256, 0, s>>>(Tin, Tout, chi, D2);
   note_launch();
   return cudaGetLastError();
 }
@@ -1034,7 +1065,10 @@ cudaError_t sym_norm_env(const double* Cin, const double* Tin, double* Cout, dou
   long long nC = (long long)chi * chi, nT = (long long)chi * D2 * chi;
   sym_corner_kernel<<<nblk(nC), 256, 0, s>>>(Cin, Cout, chi);
   note_launch();
-  sym_edge_kernel<<<nblk(nT), 256, 0, s>>>(Tin, Tout, chi, D2);
+  if (nT < (1ll << 32) - 256)
+    sym_edge_kernel<unsigned><<<nblk(nT), 256, 0, s>>>(Tin, Tout, chi, D2);
+  else
+    sym_edge_kernel<long long><<<nblk(nT), 256, 0, s>>>(Tin, Tout, chi, D2);
   note_launch();
   sumsq_kernel<<<NP, 256, 0, s>>>(Cout, nC, partials);
   note_launch();

@@ -60,6 +60,24 @@ __host__ __device__ __forceinline__ long long map_off(const IdxMap& m, long long
   return off;
 }
 
+// The same for an index below 2^32: the digits come from 32-bit divisions
+// (a 64-bit division is a long instruction sequence).
+__host__ __device__ __forceinline__ long long map_off32(const IdxMap& m, unsigned i) {
+  long long off = 0;
+#pragma unroll
+  for (int t = 0; t < kMaxDigits; ++t) {
+    if (t >= m.nd) break;
+    if (t == m.nd - 1) {
+      off += (long long)i * m.str[t];
+    } else {
+      const unsigned r = static_cast<unsigned>(m.rad[t]), q = i / r;
+      off += (long long)(i - q * r) * m.str[t];
+      i = q;
+    }
+  }
+  return off;
+}
+
 // C[b](m,n) = alpha * sum_k A[b](m,k) B[b](k,n) + beta * C[b](m,n)
 // If `part` is set and the output grid is too small to fill the GPU, the K
 // range is split over CTAs; partial sums go to `part` (part_elems doubles)

@@ -17,7 +17,7 @@
 // Every FP32 operand is stored K-contiguous with its row length padded to a
 // multiple of 4 floats (16 bytes, the TMA stride rule); the padding is never
 // read (TMA reads the true K extent and fills beyond it with zeros).  The
-// operands that many output tiles share (T, C, both layouts of Q) are split
+// operands that many output tiles share (T, C, both layouts of Q, R^T) are split
 // into TF32 head and tail planes once, when they are formed, instead of in
 // every tile of the contraction.
 #include "ctx.cuh"
@@ -174,13 +174,15 @@ cudaError_t qr_step_split(qrctm_ctx* c) {
     // Ts32[n][j][mu] (mu padded), Rt32[g][mu] = R[mu][g]
     if ((e = gather_f32(c->Tn, c->Ts32, m, ch, chp, im1(ch), im1(1), st)) != cudaSuccess)
       return e;
-    if ((e = gather_f32(c->R, c->Rt32, ch, ch, chp, im1(1), im1(ch), st)) != cudaSuccess)
+    // R^T is shared by every batch entry and row block: split once
+    if ((e = gather_f32(c->R, c->Rt32, ch, ch, chp, im1(1), im1(ch), st, c->Rt32lo)) !=
+        cudaSuccess)
       return e;
     // Y2[n][(g,j)] = sum_mu Ts[n,j,mu] R[mu,g], batch j; stored [n] x (g,j) padded mp
     float* Y2f = reinterpret_cast<float*>(c->Y2);
     TcGemm g = tc0(c);
     g.A = op(c->Ts32, ch, ch, (long long)D2 * chp, D2, chp);
-    g.B = op(c->Rt32, ch, ch, chp);
+    g.B = op(c->Rt32, ch, ch, chp, 1, 0, c->Rt32lo);
     g.M = ch; g.N = ch; g.K = ch; g.batch = D2;
     g.C = Y2f; g.c_fp64 = false;
     g.c_m = im1(mp); g.c_n = im1(D2); g.c_b = im1(1);
