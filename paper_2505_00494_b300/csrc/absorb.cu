@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(AbsorbShape<D, d, NG>::threads)
   extern __shared__ __align__(128) float sm[];
   __shared__ __align__(8) unsigned long long mbar[2];
   __shared__ int s_ok;
+  __shared__ long long xbase[NG];   // X2 offset of slice g of the batch: (mu D2) mp + b D2
   const int tid = threadIdx.x;
   float* Xb0 = sm;                                  // [NG][D2][D2]  slices (then X2 staging)
   float* Xb1 = Xb0 + S::xbuf;
@@ -132,6 +133,10 @@ __global__ void __launch_bounds__(AbsorbShape<D, d, NG>::threads)
     float* Xb = (it & 1) ? Xb1 : Xb0;
     const uint32_t bar = (it & 1) ? bar1 : bar0;
     __syncthreads();   // the other buffer's previous batch is fully written out
+    if (tid < NG) {   // one 64-bit division per slice, not per element
+      const long long gg = g0 + tid, mu = gg / ch;
+      xbase[tid] = mu * D2 * mp + (gg - mu * ch) * D2;
+    }
     const long long gn = g0 + stride;
     next_issued = gn < ngroups;
     if (tid == 0 && next_issued)
@@ -222,8 +227,7 @@ __global__ void __launch_bounds__(AbsorbShape<D, d, NG>::threads)
     for (int e = tid; e < NG * D2 * D2; e += nt) {
       const int dd = e % D2, g = (e / D2) % NG, jj = e / (D2 * NG);
       if (g >= ng) continue;
-      const long long gg = g0 + g, mu = gg / ch, b = gg - mu * ch;
-      X2[(mu * D2 + jj) * mp + b * D2 + dd] = Xb[((size_t)g * D2 + jj) * D2 + dd];
+      X2[xbase[g] + (long long)jj * mp + dd] = Xb[((size_t)g * D2 + jj) * D2 + dd];
     }
   }
   // after an abandoned wait, let the copies still in flight land (bounded)
@@ -254,6 +258,7 @@ __global__ void __launch_bounds__(kD6Threads, 1)
   extern __shared__ __align__(128) float sm[];
   __shared__ __align__(8) unsigned long long mbar[2];
   __shared__ int s_ok;
+  __shared__ long long xbase[NG];   // X2 offset of slice g of the batch: (mu D2) mp + b D2
   const int tid = threadIdx.x;
   constexpr size_t xbuf = (size_t)NG * D2 * D2;
   float* Xb0 = sm;
@@ -290,6 +295,10 @@ __global__ void __launch_bounds__(kD6Threads, 1)
     float* Xb = (it & 1) ? Xb1 : Xb0;
     const uint32_t bar = (it & 1) ? bar1 : bar0;
     __syncthreads();   // the other buffer's previous batch is fully written out
+    if (tid < NG) {   // one 64-bit division per slice, not per element
+      const long long gg = g0 + tid, mu = gg / ch;
+      xbase[tid] = mu * D2 * mp + (gg - mu * ch) * D2;
+    }
     const long long gn = g0 + stride;
     next_issued = gn < ngroups;
     if (tid == 0 && next_issued)
@@ -384,11 +393,12 @@ __global__ void __launch_bounds__(kD6Threads, 1)
     }
     __syncthreads();
     // write out: consecutive slices of one mu are consecutive b, contiguous in X2
-    for (int e = tid; e < NG * D2 * D2; e += nt) {
-      const int dd = e % D2, gg_ = (e / D2) % NG, jj = e / (D2 * NG);
+    // (16-byte pieces: mp, D2 and every slice offset are multiples of 4 floats)
+    for (int e = tid; e < NG * D2 * (D2 / 4); e += nt) {
+      const int dd = (e % (D2 / 4)) * 4, gg_ = (e / (D2 / 4)) % NG, jj = e / ((D2 / 4) * NG);
       if (gg_ >= ng) continue;
-      const long long gg = g0 + gg_, mu = gg / ch, b = gg - mu * ch;
-      X2[(mu * D2 + jj) * mp + b * D2 + dd] = Xb[((size_t)gg_ * D2 + jj) * D2 + dd];
+      *reinterpret_cast<float4*>(X2 + xbase[gg_] + (long long)jj * mp + dd) =
+          *reinterpret_cast<const float4*>(Xb + ((size_t)gg_ * D2 + jj) * D2 + dd);
     }
   }
   // after an abandoned wait, let the copies still in flight land (bounded)
@@ -447,6 +457,8 @@ cudaError_t absorb_fused(const float* X1, const float* Ak, const float* Ab, floa
   // and X1 16-byte aligned for the bulk copies
   if (D2p != (long long)D * D || (reinterpret_cast<uintptr_t>(X1) & 15) != 0)
     return cudaErrorInvalidValue;
+  // X2 rows are written in 16-byte pieces
+  if ((mp & 3) != 0 || (reinterpret_cast<uintptr_t>(X2) & 15) != 0) return cudaErrorInvalidValue;
   const long long ngroups = (long long)ch * ch;
   static int nsm = 0;
   if (nsm == 0) {
