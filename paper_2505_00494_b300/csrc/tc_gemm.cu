@@ -133,18 +133,19 @@ __device__ __forceinline__ void epi_offsets(const TcArgs& a, int bn, int t, long
                                             long long* col_off32, long long* row_off,
                                             long long* row_off32) {
   const bool split = a.ksplit > 1 || a.partials_only;
+  // (M, N < 2^31: the index maps take their digits with 32-bit divisions)
   for (int j = t; j < bn; j += 128) {
     const long long n = (long long)n0 + j;
     const bool ok = n < a.N;
     // split partials: part[b][z][m][n], the column index itself
-    col_off[j] = split ? n : (ok ? map_off(a.c_n, n) : 0);
-    if (a.C32) col_off32[j] = ok ? map_off(a.c32_n, n) : 0;
+    col_off[j] = split ? n : (ok ? map_off32(a.c_n, (unsigned)n) : 0);
+    if (a.C32) col_off32[j] = ok ? map_off32(a.c32_n, (unsigned)n) : 0;
   }
   const long long m = m0 + t;
   const bool ok = m < a.M;
   row_off[t] = split ? (((long long)z * a.ksplit + kz) * a.M + (ok ? m : 0)) * a.N
-                     : map_off(a.c_b, z) + (ok ? map_off(a.c_m, m) : 0);
-  if (a.C32) row_off32[t] = ok ? map_off(a.c32_m, m) : 0;
+                     : map_off32(a.c_b, (unsigned)z) + (ok ? map_off32(a.c_m, (unsigned)m) : 0);
+  if (a.C32) row_off32[t] = ok ? map_off32(a.c32_m, (unsigned)m) : 0;
 }
 
 template <int BN>
@@ -443,12 +444,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const long long zt = (long long)args.batch * args.ksplit;
   const long long ntiles = mt * nt * zt;
   const int nkb_all = (int)((args.K + BK - 1) / BK);
-  // tile t -> (z, kz, m0, n0), n fastest (neighbouring CTAs share A rows in L2)
+  // tile t -> (z, kz, m0, n0), n fastest (neighbouring CTAs share A rows in L2);
+  // the host keeps the tile count below 2^31, so 32-bit divisions suffice
+  const unsigned ntu = (unsigned)nt, mtu = (unsigned)mt, ksu = (unsigned)args.ksplit;
   auto tile_of = [&](long long t, int& z, int& kz, long long& m0, int& n0, int& nkb, int& kb0) {
-    const long long tn = t % nt, tm = (t / nt) % mt, tz = t / (nt * mt);
-    z = (int)(tz / args.ksplit);
-    kz = (int)(tz % args.ksplit);
-    m0 = tm * BM;
+    const unsigned tu = (unsigned)t, q = tu / ntu, tn = tu - q * ntu, tz = q / mtu,
+                   tm = q - tz * mtu;
+    z = (int)(tz / ksu);
+    kz = (int)(tz - (unsigned)z * ksu);
+    m0 = (long long)tm * BM;
     n0 = (int)(tn * BN);
     kb0 = kz * args.kb_per_split;
     nkb = max(0, min(nkb_all - kb0, args.kb_per_split));
@@ -865,7 +869,8 @@ cudaError_t gemm_tc(const TcGemm& g, cudaStream_t s) {
   // a pre-split A is taken with a pre-split B only (A's head plane must not
   // be split again)
   if (g.A.lo != nullptr && g.B.lo == nullptr) return cudaErrorInvalidValue;
-  if (g.batch > 65535 || g.M > (1ll << 31) - BM) return cudaErrorInvalidValue;
+  if (g.batch > 65535 || g.M > (1ll << 31) - BM || g.N > (1ll << 31) - 256)
+    return cudaErrorInvalidValue;
   // double-buffered accumulators up to 96 columns per tile (tensor memory
   // holds 2 x (main, correction) x 96 columns next to two A stages); N in
   // (96, 128] as two 64-column tiles (short-K streams, whose epilogue must
