@@ -256,13 +256,12 @@ __global__ void __launch_bounds__(256) q_solve_kernel(const float* __restrict__ 
 }
 
 // Q32[c][i] = delta_ci (the FP32 rows of Q = [I; 0]), row stride ldq
+// one CTA row per column c (blockIdx.y), threads along the rows i
 __global__ void init_q32_kernel(float* Q32, int m, int n, long long ldq) {
-  const long long tot = (long long)m * n;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long c = e / m, i = e % m;
-    Q32[c * ldq + i] = (i == c) ? 1.f : 0.f;
-  }
+  const int c = blockIdx.y;
+  float* col = Q32 + (long long)c * ldq;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    col[i] = (i == c) ? 1.f : 0.f;
 }
 
 // R (row-major n x n): R[i][j] for i <= j from the FP64 panel output W when
@@ -393,9 +392,8 @@ cudaError_t householder_qr_split(int m, int n, const double* M, double* R, const
     else
       q_solve_kernel<32, false><<<qg, 256, qsm, s>>>(UT, ldv, Vt32, ldv, w.Tf, n, Wt);
     note_launch();
-    const long long totq = (long long)m * n;
-    init_q32_kernel<<<(unsigned)std::min<long long>((totq + 255) / 256, 8192), 256, 0, s>>>(
-        Q32, m, n, mp);
+    init_q32_kernel<<<dim3((unsigned)std::min(((long long)m + 255) / 256, 64ll), (unsigned)n), 256,
+                      0, s>>>(Q32, m, n, mp);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
