@@ -300,10 +300,12 @@ def phase_profile(ctx, one_step, steps):
     return phases, prof_ms
 
 
-def tc_kernel_name(N, K, pre=0):
+def tc_kernel_name(N, K, pre=0, M=0):
     """Name of the tensor-core kernel instance the engine launches for an
-    N-column, K-deep product (the tile choice of gemm_tc); pre = 1 when B
+    M x N, K-deep product (the tile choice of gemm_tc); pre = 1 when B
     comes pre-split, 2 when both operands do."""
+    if pre == 2 and N > 192 and K < 512 and ((M + 127) // 128) * ((N + 127) // 128) >= 296:
+        return "tc_tf32x3_kernel<128, 2, 2>"
     if N <= 32:
         bn = (32, 2)
     elif N <= 64:
@@ -779,7 +781,7 @@ def main():
                       tf32_peak, tf32_note)
         kernels.update({
             "absorb": absorb,
-            "x1": (tc_kernel_name(m, chi, 2), fl["x1"], "tensor", tf32_peak, tf32_note),
+            "x1": (tc_kernel_name(m, chi, 2, m), fl["x1"], "tensor", tf32_peak, tf32_note),
             "project": (tc_kernel_name(chi, m, 1), fl["project"], "tensor", tf32_peak,
                         tf32_note),
         })

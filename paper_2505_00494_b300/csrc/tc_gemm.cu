@@ -364,12 +364,14 @@ struct Cfg {
       std::min(4, (232448 - 2048 - STG_BYTES - OFF_BYTES) / STAGE_BYTES);
   static constexpr int HALF = (BN + 31) / 32 * 32;                  // TMEM columns per region
   static constexpr int ACC_COLS = NBUF * 2 * HALF;
-  static constexpr int A_STAGES = std::min(4, (512 - ACC_COLS) / 64);   // (head, tail) x 32
+  // (head, tail) x 32 columns per A stage; none when A comes pre-split (read from shared memory)
+  static constexpr int A_STAGES = PRE_A ? 0 : std::min(4, (512 - ACC_COLS) / 64);
   static constexpr int A_COL0 = ACC_COLS;
   static constexpr int TMEM_COLS = 512;
   static constexpr int NBAR = 3 * STAGES + A_STAGES + 2 * NBUF;
   static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + STG_BYTES + 1024 + OFF_BYTES;
-  static_assert(STAGES >= 2 && A_STAGES >= 2, "tile does not fit the SM");
+  static_assert(STAGES >= 2 && (PRE_A || A_STAGES >= 2), "tile does not fit the SM");
+  static_assert(ACC_COLS + 64 * A_STAGES <= TMEM_COLS, "tensor memory overflow");
   static_assert(8 * NBAR + 24 <= 1024, "control block overflow");
 };
 
@@ -412,7 +414,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                      const __grid_constant__ CUtensorMap tmAlo,
                      const __grid_constant__ CUtensorMap tmBlo, const TcArgs args) {
   using C = Cfg<BN, NBUF, PRE>;
-  constexpr int S = C::STAGES, AS = C::A_STAGES;
+  constexpr int S = C::STAGES, AS = C::A_STAGES, ASM = AS > 0 ? AS : 1;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -532,7 +534,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t dmain = tmem + ab * 2 * C::HALF, dcorr = dmain + C::HALF;
         for (int kb = 0; kb < nkb; ++kb, ++kbg) {
-          const int s = kbg % S, sa = kbg % AS;
+          const int s = kbg % S, sa = kbg % ASM;
           // both operands pre-split: the TMA landing is all the MMAs wait for
           ok = mbar_wait((C::PRE_A ? full0 : conv0) + 8 * s, (kbg / S) & 1, abort_flag, args.err);
           if (!ok) break;
@@ -581,7 +583,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       long long m0;
       tile_of(t, z, kz, m0, n0, nkb, kb0);
       for (int kb = 0; kb < nkb; ++kb, ++kbg) {
-        const int s = kbg % S, sa = kbg % AS;
+        const int s = kbg % S, sa = kbg % ASM;
         ok = mbar_wait(full0 + 8 * s, (kbg / S) & 1, abort_flag, args.err);
         if (!__all_sync(0xffffffffu, ok)) {
           ok = false;
@@ -614,7 +616,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int i = 0; i < 32; ++i) tf32_split(hv[i], hv[i], tv[i]);
         // the MMAs of the K block that used this TMEM stage last must be done;
         // the warp proceeds (tcgen05.st is warp-collective) only if every lane saw it
-        if (kbg >= AS) ok = mbar_wait(tfree0 + 8 * sa, ((kbg / AS) - 1) & 1, abort_flag, args.err);
+        if (kbg >= AS) ok = mbar_wait(tfree0 + 8 * sa, ((kbg / ASM) - 1) & 1, abort_flag, args.err);
         if (!__all_sync(0xffffffffu, ok)) {
           ok = false;
           break;
@@ -887,6 +889,11 @@ cudaError_t gemm_tc(const TcGemm& g, cudaStream_t s) {
   if (N <= 128) return launch_pre<64, 2>(g, s);    // two double-buffered tiles
   if (N <= 144) return launch_pre<144, 1>(g, s);
   if (N <= 192 || g.K >= 512) return launch_pre<192, 1>(g, s);
+  // both operands pre-split (no tensor-memory A stages): 128-column
+  // double-buffered tiles fill tensor memory with accumulators and cut the
+  // shared-memory operand traffic per output, when there are tiles enough
+  if (g.A.lo != nullptr && ((g.M + BM - 1) / BM) * ((N + 127) / 128) * std::max(1, g.batch) >= 296)
+    return launch_bn<128, 2, 2>(g, s);
   return launch_pre<96, 2>(g, s);
 }
 

@@ -44,7 +44,8 @@ def test_tf32x3_matches_fp64(q, M, N, K, split_k):
 @pytest.mark.parametrize("pre_a", [False, True])
 @pytest.mark.parametrize("M,N,K", [(128, 32, 32), (300, 80, 72), (257, 144, 100),
                                    (5184, 144, 5184), (333, 300, 40), (700, 192, 96),
-                                   (300, 400, 600), (130, 520, 1100), (144, 5184, 144)])
+                                   (300, 400, 600), (130, 520, 1100), (144, 5184, 144),
+                                   (2600, 3000, 144), (4100, 4200, 100)])
 def test_presplit_matches_plain(q, M, N, K, pre_a):
     """Pre-split operands (heads and tails from tf32_split) give the same
     split, hence the same products, as the in-kernel split: bit-identical
