@@ -240,6 +240,53 @@ __device__ __forceinline__ void epi_rows(const TcArgs& a, uint32_t acc, uint32_t
     }
     return;
   }
+  // FP32 rows contiguous in n (split-K partials, or an FP32 output whose
+  // column map is the identity): each thread stores its own row's 32 columns
+  // from its registers, in 16-byte pieces where the row start allows, with
+  // no staging and no per-element offsets
+  if (split || (!a.c_fp64 && a.c_n.nd == 1 && a.c_n.str[0] == 1)) {
+    const bool rvalid = lane < rows;
+    float* base = split ? a.part : static_cast<float*>(a.C);
+    const long long myro = rvalid ? ro[lane] : 0;
+    const float al = split ? 1.f : static_cast<float>(a.alpha);
+    const float be = split ? 0.f : static_cast<float>(a.beta);
+#pragma unroll 1
+    for (int c = 0; c < (BN + 31) / 32; ++c) {
+      float v[32], w[32];
+      const uint32_t ta = acc + (static_cast<uint32_t>(q * 32) << 16) + c * 32;
+      tmem_ld32(ta, v);
+      tmem_ld32(ta + half, w);
+      const long long nrem = a.N - n0 - c * 32;
+      if (!rvalid || nrem <= 0) continue;
+      const int nv = nrem < 32 ? (int)nrem : 32;
+      float* p = base + myro + n0 + c * 32;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = al * (v[j] + w[j]);
+      if (nv == 32 && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+        float4* p4 = reinterpret_cast<float4*>(p);
+        if (be != 0.f) {
+          float4 old[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) old[u] = p4[u];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            v[4 * u] = fmaf(be, old[u].x, v[4 * u]);
+            v[4 * u + 1] = fmaf(be, old[u].y, v[4 * u + 1]);
+            v[4 * u + 2] = fmaf(be, old[u].z, v[4 * u + 2]);
+            v[4 * u + 3] = fmaf(be, old[u].w, v[4 * u + 3]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          p4[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j < nv) p[j] = (be != 0.f) ? fmaf(be, p[j], v[j]) : v[j];
+      }
+    }
+    return;
+  }
 #pragma unroll 1
   for (int c = 0; c < (BN + 31) / 32; ++c) {
     float v[32], w[32];
