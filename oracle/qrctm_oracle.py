@@ -489,13 +489,15 @@ def directional_derivative_fixed_point(A, v, C, T, J1=1.0, J2=0.0,
     return float(np.imag(energy(Cc, Tc, Ac, J1, J2)) / h), info
 
 
-def directional_derivative_unrolled(A, v, C, T, k, J1=1.0, J2=0.0, h=1e-20):
+def directional_derivative_unrolled(A, v, C, T, k, J1=1.0, J2=0.0, h=1e-20, layers="double"):
     """dE/dA . v of E(A, F^k(A; C, T)) with (C, T) held fixed: the gradient of
-    k tracked CTMRG steps started from a detached environment."""
+    k tracked CTMRG steps started from a detached environment.  ``layers``
+    picks the double-layer or the ket-then-bra form of the edge update (equal
+    up to rounding; the second is cheaper for D >= 3)."""
     Ac = A.astype(complex) + 1j * h * v
     Cc, Tc = C.astype(complex), T.astype(complex)
     for _ in range(k):
-        Cc, Tc = qr_step(Cc, Tc, Ac)
+        Cc, Tc = qr_step(Cc, Tc, Ac, layers)
     return float(np.imag(energy(Cc, Tc, Ac, J1, J2)) / h)
 
 

@@ -99,6 +99,8 @@ WORKLOADS = {
                          tol=1e-10, max_iter=500),
     "d2_D6_chi600": dict(d=2, D=6, chi=600, seed=0, decay=True, bias=0.0,
                          tol=1e-10, max_iter=500),
+    "d2_D8_chi64": dict(d=2, D=8, chi=64, seed=0, decay=True, bias=0.0,
+                        tol=1e-10, max_iter=6000),
     "d2_D8_chi256": dict(d=2, D=8, chi=256, seed=0, decay=True, bias=0.0,
                          tol=1e-10, max_iter=500),
     "d2_D8_chi512": dict(d=2, D=8, chi=512, seed=0, decay=True, bias=0.0,

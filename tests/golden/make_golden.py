@@ -1,6 +1,6 @@
 """Write converged-environment fixtures computed by the oracle alone.
 
-    python tests/golden/make_golden.py d2_D2_chi16 d2_D4_chi64 d2_D6_chi144
+    python tests/golden/make_golden.py d2_D2_chi16 d2_D4_chi64 d2_D6_chi144 d2_D8_chi64
 
 For each workload (inputs from qrctm_inputs.WORKLOADS) the oracle runs its
 warm-up and QR-CTMRG steps until the corner spectrum changes by less than the
@@ -21,8 +21,8 @@ import numpy as np  # noqa: E402
 import qrctm_inputs as qi  # noqa: E402
 from oracle import qrctm_oracle as o  # noqa: E402
 
-TOL = {"d2_D2_chi16": 1e-12, "d2_D4_chi64": 1e-11, "d2_D6_chi144": 1e-10}
-MAX_ITER = {"d2_D2_chi16": 2000, "d2_D4_chi64": 4000, "d2_D6_chi144": 6000}
+TOL = {"d2_D2_chi16": 1e-12, "d2_D4_chi64": 1e-11, "d2_D6_chi144": 1e-10, "d2_D8_chi64": 1e-10}
+MAX_ITER = {"d2_D2_chi16": 2000, "d2_D4_chi64": 4000, "d2_D6_chi144": 6000, "d2_D8_chi64": 6000}
 
 
 def main(names):
