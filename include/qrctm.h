@@ -274,6 +274,17 @@ int qrctm_grad_iterations(const qrctm_ctx* ctx);
  * call has no counterpart in the paper; it reports solver convergence. */
 double qrctm_grad_residual(const qrctm_ctx* ctx);
 
+/* Elementwise distance of the environment x = (C, T) from a fixed point of
+ * two QR-CTMRG steps, ||G(x) - x|| / ||x|| with G = F o F, measured by the
+ * last implicit qrctm_energy_grad call (0 after an unrolled one).  The
+ * implicit adjoint assumes G(x) = x (Discussion: fixed-point differentiation).
+ * The spectrum test that ends qrctm_run_to_convergence is gauge invariant
+ * and can be met while the environment still rotates slowly within
+ * near-degenerate parts of the corner spectrum; the implicit gradient's
+ * error then grows with this residual, and the unrolled mode (which assumes
+ * no fixed point) is the safer choice.  No counterpart in the paper. */
+double qrctm_grad_fixed_point_residual(const qrctm_ctx* ctx);
+
 /* Steps run since qrctm_init_env. */
 int qrctm_iterations(const qrctm_ctx* ctx);
 
@@ -300,6 +311,22 @@ qrctm_status qrctm_c4v_symmetrize(int d, int D, const double* X, double* Y, int 
 size_t qrctm_qr_workspace_bytes(int m, int n);
 qrctm_status qrctm_householder_qr(int m, int n, const double* M, double* Q, double* R,
                                   void* workspace, size_t bytes, void* stream);
+
+/* qrctm_householder_qr with the bound of the panel kernel's device waits made
+ * explicit (the paper has no counterpart; this is the library's failure
+ * detection).  Each panel column ends with a grid-wide exchange: every CTA
+ * adds its partial sums and arrives on a counter, and the CTAs wait until all
+ * have arrived.  A wait gives up after wait_spins polls (0 = the default,
+ * 2^25, about a second) and the call returns QRCTM_ERR_TIMEOUT instead of
+ * hanging; Q and R are then undefined.  extra_arrivals (>= 0) raises the
+ * number of arrivals every wait expects above the CTAs launched, so that no
+ * wait can be satisfied: a value above 0 exists only to exercise the timeout
+ * path, from a test, without a fault.  Either way the call leaves its
+ * workspace's control words zero, so the next call runs normally.
+ * Synchronises `stream`. */
+qrctm_status qrctm_householder_qr_bounded(int m, int n, const double* M, double* Q, double* R,
+                                          void* workspace, size_t bytes, void* stream,
+                                          long long wait_spins, int extra_arrivals);
 
 /* Split-precision matrix product on the tensor cores (the contraction engine
  * of the QR-CTMRG split path):  C[m*ldc + n] = sum_k A[m*lda + k] B[n*ldb + k]
@@ -348,7 +375,9 @@ qrctm_status qrctm_tf32_split(long long rows, int cols, float* x, long long ld, 
  * 5184 x 144); larger sizes return QRCTM_ERR_WORKSPACE without touching the
  * device.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the array and each clears the
+ * before any stream capture.  The address is kept for the life of the
+ * process, so cudaDeviceReset (which unloads the module and may move the
+ * array) is not supported between calls.  All calls share the array and each clears the
  * words that must start at zero, so calls whose GPU work overlaps (other
  * streams, other host threads) race and must be serialised by the caller.
  * Synchronises `stream`. */

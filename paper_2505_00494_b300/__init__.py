@@ -90,6 +90,7 @@ _sig = {
     "qrctm_iterations": ([_vp], ctypes.c_int),
     "qrctm_grad_iterations": ([_vp], ctypes.c_int),
     "qrctm_grad_residual": ([_vp], ctypes.c_double),
+    "qrctm_grad_fixed_point_residual": ([_vp], ctypes.c_double),
     "qrctm_set_profiling": ([_vp, ctypes.c_int], ctypes.c_int),
     "qrctm_phase_times": ([_vp, _dp, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
     "qrctm_kernel_launches": ([], ctypes.c_ulonglong),
@@ -103,6 +104,9 @@ _sig = {
     "qrctm_gemm_tf32x3": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_longlong, _vp,
                            ctypes.c_longlong, _vp, ctypes.c_longlong, _vp, ctypes.c_longlong, _vp,
                            _vp], ctypes.c_int),
+    "qrctm_householder_qr_bounded": ([ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp,
+                                      ctypes.c_size_t, _vp, ctypes.c_longlong, ctypes.c_int],
+                                     ctypes.c_int),
     "qrctm_householder_qr_noalloc": ([ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp],
                                      ctypes.c_int),
     "qrctm_gemm_tf32x3_presplit": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
@@ -318,6 +322,11 @@ class QRCTM:
         return _load().qrctm_grad_residual(self.h)
 
     @property
+    def grad_fixed_point_residual(self):
+        """||G(x) - x|| / ||x|| of the environment at the last implicit gradient."""
+        return _load().qrctm_grad_fixed_point_residual(self.h)
+
+    @property
     def iterations(self):
         return _load().qrctm_iterations(self.h)
 
@@ -398,11 +407,14 @@ def gemm_tf32x3_presplit(A, A_lo, B, B_lo, stream=None, split_k=True):
     return C
 
 
-def householder_qr(M, stream=None, workspace=None):
+def householder_qr(M, stream=None, workspace=None, wait_spins=None, extra_arrivals=0):
     """Q, R of an m x n float64 CUDA matrix M (a row-major torch tensor).
 
     The library works on column-major storage, so M is passed as the storage
-    of M^T; Q comes back the same way and is returned as an (m, n) view."""
+    of M^T; Q comes back the same way and is returned as an (m, n) view.
+    ``wait_spins`` / ``extra_arrivals`` go to qrctm_householder_qr_bounded
+    (the bound of the panel's device waits; extra arrivals make every wait
+    run out, for testing the timeout path)."""
     torch = _torch()
     m, n = M.shape
     Mcm = M.t().contiguous()
@@ -410,8 +422,15 @@ def householder_qr(M, stream=None, workspace=None):
     R = torch.empty((n, n), dtype=torch.float64, device=M.device)
     nb = _load().qrctm_qr_workspace_bytes(m, n)
     ws = workspace if workspace is not None else _workspace(nb, M.device, zero=True)
-    code = _load().qrctm_householder_qr(m, n, _ptr(Mcm), _ptr(Qcm), _ptr(R),
-                                    ctypes.c_void_p(ws.data_ptr()), nb, _stream_ptr(stream))
+    if wait_spins is None and not extra_arrivals:
+        code = _load().qrctm_householder_qr(m, n, _ptr(Mcm), _ptr(Qcm), _ptr(R),
+                                            ctypes.c_void_p(ws.data_ptr()), nb,
+                                            _stream_ptr(stream))
+    else:
+        code = _load().qrctm_householder_qr_bounded(m, n, _ptr(Mcm), _ptr(Qcm), _ptr(R),
+                                                    ctypes.c_void_p(ws.data_ptr()), nb,
+                                                    _stream_ptr(stream), int(wait_spins or 0),
+                                                    int(extra_arrivals))
     if code != 0:
         raise QRCTMError(code, "qrctm_householder_qr")
     return Qcm.t(), R

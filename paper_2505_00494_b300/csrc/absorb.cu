@@ -460,13 +460,7 @@ cudaError_t absorb_fused(const float* X1, const float* Ak, const float* Ab, floa
   // X2 rows are written in 16-byte pieces
   if ((mp & 3) != 0 || (reinterpret_cast<uintptr_t>(X2) & 15) != 0) return cudaErrorInvalidValue;
   const long long ngroups = (long long)ch * ch;
-  static int nsm = 0;
-  if (nsm == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (nsm <= 0) nsm = 1;
-  }
+  const int nsm = device_sm_count();
   cudaError_t e = cudaFuncSetAttribute(v.k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)v.smem);
   if (e != cudaSuccess) return e;

@@ -703,17 +703,19 @@ qrctm_status qrctm_energy_grad(qrctm_ctx* c, const qrctm_model* model, int mode,
   if (c->D < 2) return set_err(c, QRCTM_ERR_INVALID_ARG, "the gradient needs D >= 2");
   cudaError_t e;
   int iters = 0;
-  double resid = 0.0;
+  double resid = 0.0, fp_resid = 0.0;
   {
     PhaseScope ps(c, QRCTM_PH_GRAD);
     // a split-precision context runs the contractions of the taped steps, of
     // the energy and of every reverse pass on the TF32x3 engine
     c->mm_split = c->split_prec && c->mm32 != nullptr;
-    e = energy_grad_run(c, model->J1, model->J2, mode, k_unroll, grad, e_out, &iters, &resid);
+    e = energy_grad_run(c, model->J1, model->J2, mode, k_unroll, grad, e_out, &iters, &resid,
+                        &fp_resid);
     c->mm_split = false;
   }
   c->grad_iters = iters;
   c->grad_resid = resid;
+  c->grad_fp_resid = fp_resid;
   if (e != cudaSuccess) return cuda_fail(c, e, "energy gradient");
   return sync_check(c, "energy gradient");
 }
@@ -848,6 +850,10 @@ int qrctm_grad_iterations(const qrctm_ctx* ctx) { return ctx ? ctx->grad_iters :
 
 double qrctm_grad_residual(const qrctm_ctx* ctx) { return ctx ? ctx->grad_resid : 0.0; }
 
+double qrctm_grad_fixed_point_residual(const qrctm_ctx* ctx) {
+  return ctx ? ctx->grad_fp_resid : 0.0;
+}
+
 qrctm_status qrctm_get_env(qrctm_ctx* c, double* C, double* T, double* spectrum_host) {
   if (!c) return QRCTM_ERR_INVALID_ARG;
   if (!c->have_env) return set_err(c, QRCTM_ERR_STATE, "qrctm_init_env not called");
@@ -962,11 +968,20 @@ size_t qrctm_qr_workspace_bytes(int m, int n) {
 
 qrctm_status qrctm_householder_qr(int m, int n, const double* M, double* Q, double* R,
                                   void* workspace, size_t bytes, void* stream) {
+  return qrctm_householder_qr_bounded(m, n, M, Q, R, workspace, bytes, stream, 0, 0);
+}
+
+qrctm_status qrctm_householder_qr_bounded(int m, int n, const double* M, double* Q, double* R,
+                                          void* workspace, size_t bytes, void* stream,
+                                          long long wait_spins, int extra_arrivals) {
   if (m < n || n < 1 || n > 2048 || !M || !Q || !R || !workspace) return QRCTM_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return QRCTM_ERR_INVALID_ARG;
+  if (wait_spins < 0 || extra_arrivals < 0 || extra_arrivals > 1024) return QRCTM_ERR_INVALID_ARG;
   if (bytes < qrctm_qr_workspace_bytes(m, n)) return QRCTM_ERR_WORKSPACE;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   QrWork w = qr_carve(workspace, m, n);
+  if (wait_spins > 0) w.wait_spins = wait_spins;
+  w.wait_extra = (unsigned)extra_arrivals;
   cudaError_t e = householder_qr_f64(m, n, M, Q, R, w, s);
   if (e != cudaSuccess) return QRCTM_ERR_CUDA;
   int flag = 0;

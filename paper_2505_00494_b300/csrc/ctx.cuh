@@ -51,6 +51,7 @@ struct qrctm_ctx {
   int iters;
   int grad_iters;
   double grad_resid;
+  double grad_fp_resid;   // ||G(x) - x|| / ||x|| at the last implicit gradient
   cudaEvent_t panel_ev;   // open panel-phase event (profiling)
   // standard (eigendecomposition) method
   void* solver;            // cusolverDnHandle_t, created on first use

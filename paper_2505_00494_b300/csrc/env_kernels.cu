@@ -1108,51 +1108,55 @@ static cudaError_t spectra(const double* C, int chi, double* work, double* s_new
   if (chi < 1 || chi > 1024) return cudaErrorInvalidValue;
   const int njobs = C1 ? 2 : 1;
   const size_t smem = (chi <= kSmemSpecMax) ? sizeof(double) * chi * (chi + 1) : 0;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(spectrum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(double) * kSmemSpecMax * (kSmemSpecMax + 1)));
-    attr = true;
-  }
+  // one-time setup per device: shared-memory limits of the one-CTA and
+  // cluster variants for their largest n, and whether the device can place a
+  // 16-CTA cluster (its result is kept as the second key's status)
+  device_once((const void*)spectrum_kernel, [] {
+    cudaError_t r = cudaFuncSetAttribute(
+        spectrum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)(sizeof(double) * kSmemSpecMax * (kSmemSpecMax + 1)));
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(spectrum_cluster_kernel<8, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(sizeof(double) * (((size_t)kSpecClusterMaxN8 + 7) / 8 *
+                                                           (kSpecClusterMaxN8 + 3) +
+                                                       5 * (size_t)kSpecClusterMaxN8)));
+    return r;
+  });
+  const bool ok16 =
+      device_once((const void*)spectrum_cluster_kernel<16, false>, [] {
+        auto k16 = spectrum_cluster_kernel<16, false>;
+        const size_t smem16 = sizeof(double) * (((size_t)kSpecClusterMaxN16 + 15) / 16 *
+                                                    (kSpecClusterMaxN16 + 3) +
+                                                5 * (size_t)kSpecClusterMaxN16);
+        cudaFuncSetAttribute(k16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem16);
+        // 16 CTAs per cluster is above the portable limit: allowed only where
+        // the device can place such a cluster
+        bool ok = cudaFuncSetAttribute(k16, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                      cudaSuccess &&
+                  cudaFuncSetAttribute(spectrum_cluster_kernel<16, true>,
+                                       cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                      cudaSuccess;
+        if (ok) {
+          cudaLaunchConfig_t q = {};
+          q.gridDim = dim3(16);
+          q.blockDim = dim3(256);
+          q.dynamicSmemBytes = smem16;
+          cudaLaunchAttribute qa[1];
+          qa[0].id = cudaLaunchAttributeClusterDimension;
+          qa[0].val.clusterDim.x = 16;
+          qa[0].val.clusterDim.y = 1;
+          qa[0].val.clusterDim.z = 1;
+          q.attrs = qa;
+          q.numAttrs = 1;
+          int nclusters = 0;
+          ok = cudaOccupancyMaxActiveClusters(&nclusters, k16, &q) == cudaSuccess &&
+               nclusters >= 1;
+        }
+        cudaGetLastError();
+        return ok ? cudaSuccess : cudaErrorNotSupported;
+      }) == cudaSuccess;
   bool launched = false;
-  // one-time setup of the cluster variants: shared-memory limits for their
-  // largest n, and whether the device can place a 16-CTA cluster
-  static bool cattr = false, ok16 = false;
-  if (!cattr) {
-    cudaFuncSetAttribute(spectrum_cluster_kernel<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(double) * (((size_t)kSpecClusterMaxN8 + 7) / 8 *
-                                                     (kSpecClusterMaxN8 + 3) +
-                                                 5 * (size_t)kSpecClusterMaxN8)));
-    auto k16 = spectrum_cluster_kernel<16, false>;
-    const size_t smem16 = sizeof(double) * (((size_t)kSpecClusterMaxN16 + 15) / 16 *
-                                                (kSpecClusterMaxN16 + 3) +
-                                            5 * (size_t)kSpecClusterMaxN16);
-    cudaFuncSetAttribute(k16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem16);
-    // 16 CTAs per cluster is above the portable limit: allowed only where
-    // the device can place such a cluster
-    ok16 = cudaFuncSetAttribute(k16, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-               cudaSuccess &&
-           cudaFuncSetAttribute(spectrum_cluster_kernel<16, true>,
-                                cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
-    if (ok16) {
-      cudaLaunchConfig_t q = {};
-      q.gridDim = dim3(16);
-      q.blockDim = dim3(256);
-      q.dynamicSmemBytes = smem16;
-      cudaLaunchAttribute qa[1];
-      qa[0].id = cudaLaunchAttributeClusterDimension;
-      qa[0].val.clusterDim.x = 16;
-      qa[0].val.clusterDim.y = 1;
-      qa[0].val.clusterDim.z = 1;
-      q.attrs = qa;
-      q.numAttrs = 1;
-      int nclusters = 0;
-      ok16 = cudaOccupancyMaxActiveClusters(&nclusters, k16, &q) == cudaSuccess &&
-             nclusters >= 1;
-    }
-    cudaGetLastError();
-    cattr = true;
-  }
   int cs = 0;
   bool gmem = false;
   if (chi >= 3) {

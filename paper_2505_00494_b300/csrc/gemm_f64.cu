@@ -8,6 +8,8 @@
 #include "qrctm_internal.cuh"
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 namespace qrctm {
 
@@ -143,6 +145,35 @@ __global__ void splitk_reduce_kernel(Gemm g, int splits) {
 
 }  // namespace
 
+cudaError_t device_once(const void* key, const std::function<cudaError_t()>& f) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, cudaError_t> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = done.find({dev, key});
+  if (it != done.end()) return it->second;
+  e = f();
+  done.emplace(std::make_pair(dev, key), e);
+  return e;
+}
+
+int device_sm_count() {
+  static std::mutex mu;
+  static std::map<int, int> count;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = count.find(dev);
+  if (it != count.end()) return it->second;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+    n = 148;
+  count[dev] = n;
+  return n;
+}
+
 static unsigned long long g_launches = 0;
 void note_launch(unsigned long long n) { __atomic_fetch_add(&g_launches, n, __ATOMIC_RELAXED); }
 unsigned long long launches_so_far() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
@@ -152,13 +183,7 @@ cudaError_t gemm_f64(const Gemm& g, cudaStream_t s) {
   long long gx = (g.M + BM - 1) / BM, gy = (g.N + BN - 1) / BN;
   if (gx > 0x7fffffffll) return cudaErrorInvalidValue;
   if (gy > 65535) gy = 65535;   // the kernel loops over the remaining N tiles
-  static int nsm = 0;
-  if (nsm == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (nsm <= 0) nsm = 148;
-  }
+  const int nsm = device_sm_count();
   const long long tiles = gx * gy;
   int splits = 1;
   if (g.part != nullptr && g.batch == 1 && tiles < 2 * nsm && g.K >= 4 * BK) {

@@ -499,7 +499,8 @@ static cudaError_t adjoint_gmres(qrctm_ctx* c, GradLayout& L, double tol, int ma
 }
 
 cudaError_t energy_grad_run(qrctm_ctx* c, double J1, double J2, int mode, int k_unroll,
-                            double* grad, double* e_out, int* iters_out, double* resid_out) {
+                            double* grad, double* e_out, int* iters_out, double* resid_out,
+                            double* fp_resid_out) {
   if (!c->G) return cudaErrorInvalidValue;
   if (mode != 0 && (k_unroll < 1 || k_unroll > kMaxUnroll)) return cudaErrorInvalidValue;
   GradLayout L;
@@ -515,6 +516,21 @@ cudaError_t energy_grad_run(qrctm_ctx* c, double J1, double J2, int mode, int k_
     // implicit: tapes of two steps at the current environment
     if ((e = step_fwd_tape(c, c->C, c->T, L.tape[0])) != cudaSuccess) return e;
     if ((e = step_fwd_tape(c, L.tape[0].Cout, L.tape[0].Tout, L.tape[1])) != cudaSuccess) return e;
+    // how far the current environment is from a fixed point of the two-step
+    // map, elementwise: ||G(x) - x|| / ||x|| with x = (C, T), each of unit
+    // norm.  The adjoint equation holds at G(x) = x; the spectrum test that
+    // ends the forward iteration is gauge invariant and can be met long
+    // before the environment stops moving elementwise.
+    {
+      const long long n = c2 + mc;
+      cudaMemcpyAsync(L.ev1, L.tape[1].Cout, sizeof(double) * c2, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(L.ev1 + c2, L.tape[1].Tout, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s);
+      axpby(L.ev1, c->C, -1.0, 1.0, c2, s);
+      axpby(L.ev1 + c2, c->T, -1.0, 1.0, mc, s);
+      double d2 = 0.0;
+      if ((e = dot_host(c, L.ev1, L.ev1, n, L.red, &d2)) != cudaSuccess) return e;
+      if (fp_resid_out) *fp_resid_out = std::sqrt(d2 / 2.0);
+    }
     if ((e = energy_vjp(c, L, c->C, c->T, J1, J2, L.ebC, L.ebT, L.Abar, e_dev)) != cudaSuccess)
       return e;
     // xbar solves (I - J_G^T) xbar = ebar   (restarted GMRES)
@@ -557,6 +573,7 @@ cudaError_t energy_grad_run(qrctm_ctx* c, double J1, double J2, int mode, int k_
       std::swap(L.yT, L.y2T);
     }
     iters = K;
+    if (fp_resid_out) *fp_resid_out = 0.0;
     if (c->grad_keep_env) {
       // the optimiser continues from the environment after the k steps
       cudaMemcpyAsync(c->C, L.ckC + K * c2, sizeof(double) * c2, cudaMemcpyDeviceToDevice, s);

@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
                                                       int rows_per_cta, float* __restrict__ X32,
                                                       long long ldx, float* __restrict__ Vt32,
                                                       const float* __restrict__ src32,
-                                                      float* __restrict__ V32, long long ldv) {
+                                                      float* __restrict__ V32, long long ldv,
+                                                      long long wait_spins, unsigned wait_extra) {
   const int P = gridDim.x, b = blockIdx.x;
   const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;   // wrp = row lane (0..7)
   const long long r_begin = (long long)j0 + (long long)b * rows_per_cta;
@@ -170,7 +171,8 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
       // second SM sub-partition while warp 0 forms 1/mu: FP64 instructions
       // of one sub-partition do not overlap
       int okw = 1;
-      if (lane == 0) okw = grid_wait(bar, (unsigned)P * (unsigned)(j + 1), err) ? 1 : 0;
+      if (lane == 0)
+        okw = grid_wait(bar, (unsigned)P * (unsigned)(j + 1) + wait_extra, err, wait_spins) ? 1 : 0;
       __syncwarp();
       if (lane == 0) {
         double rs = 0.0;
@@ -183,7 +185,8 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
       asm volatile("bar.arrive 3, 64;" ::: "memory");
     } else if (wrp == 0) {
       int okw = 1;
-      if (lane == 0) okw = grid_wait(bar, (unsigned)P * (unsigned)(j + 1), err) ? 1 : 0;
+      if (lane == 0)
+        okw = grid_wait(bar, (unsigned)P * (unsigned)(j + 1) + wait_extra, err, wait_spins) ? 1 : 0;
       __syncwarp();                                        // orders lane 0's acquire first
       okw = __shfl_sync(0xffffffffu, okw, 0);
       double y0 = 0.0, st = 0.0;
@@ -400,6 +403,8 @@ cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t 
   float* v32 = V32;
   const float* s32 = src32;
   long long ldx_ = ldx, ldv_ = ldv;
+  long long spins_ = w.wait_spins > 0 ? w.wait_spins : kGridWaitSpins;
+  unsigned extra_ = w.wait_extra;
   // one accumulator row of NB doubles per column of the whole factorisation
   if (j0 + nbj > 2 * PMAX) return cudaErrorInvalidValue;
   cudaError_t e = cudaErrorUnknown;
@@ -414,18 +419,22 @@ cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t 
   // sums into the column's accumulator and arrives on the counter
   int rpc = (mr + P - 1) / P;
   void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc, &x32, &ldx_, &vt32,
-                  &s32, &v32, &ldv_};
+                  &s32, &v32, &ldv_, &spins_, &extra_};
   const size_t tile = sizeof(double) * (size_t)rpc * (NB + 1);
   if (src32 != nullptr && tile > kPanelTileMax) {
     if (w.hook) w.hook(w.hook_user, 0);
     return cudaErrorInvalidValue;   // an FP32 source needs the tiled path
   }
   if (tile <= kPanelTileMax) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(qr_panel_kernel<true>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelTileMax);
-      attr = true;
+    // the shared-memory limit is a per-device attribute of the kernel
+    e = device_once((const void*)qr_panel_kernel<true>, [] {
+      return cudaFuncSetAttribute(qr_panel_kernel<true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kPanelTileMax);
+    });
+    if (e != cudaSuccess) {
+      if (w.hook) w.hook(w.hook_user, 0);
+      return e;
     }
     e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<true>, dim3(P),
                                     dim3(PT), args, tile, s);
@@ -455,13 +464,7 @@ cudaError_t qr_extract_r(const double* W, double* R, int m, int n, cudaStream_t 
 }
 
 int qr_panel_grid(int mrows) {
-  static int nsm = 0;
-  if (nsm == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (nsm <= 0) nsm = 1;
-  }
+  const int nsm = device_sm_count();
   int p = (mrows + 31) / 32;
   return std::max(1, std::min(std::min(p, nsm), PMAX));
 }
@@ -497,6 +500,8 @@ QrWork qr_carve(void* base, int m, int n) {
   p += align_up(sizeof(double) * ((size_t)2 * PMAX * NB + 2 * NB + (size_t)PMAX * NB * NB));
   w.bar = reinterpret_cast<GridBar*>(p); p += align_up(sizeof(GridBar));
   w.err = reinterpret_cast<int*>(p);
+  w.wait_spins = kGridWaitSpins;
+  w.wait_extra = 0;
   return w;
 }
 

@@ -369,14 +369,19 @@ cudaError_t householder_qr_split(int m, int n, const double* M, double* R, const
     const size_t qsm = sizeof(float) * (((n + 3) & ~3) + (n <= kSolveSmemMaxN ? (size_t)n * n : 0));
     // the fewest values per lane that hold a column (32 MAXQ >= n); U^T
     // staged in shared memory up to n = kSolveSmemMaxN
-    static bool qattr = false;
-    if (!qattr) {
+    // shared-memory limits are per-device attributes of the kernels
+    device_once((const void*)q_solve_kernel<4, true>, [] {
       const int mx = (int)(sizeof(float) * (kSolveSmemMaxN * kSolveSmemMaxN + 32 * 8));
-      cudaFuncSetAttribute(q_solve_kernel<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-      cudaFuncSetAttribute(q_solve_kernel<5, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-      cudaFuncSetAttribute(q_solve_kernel<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-      qattr = true;
-    }
+      cudaError_t r = cudaFuncSetAttribute(q_solve_kernel<4, true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+      if (r == cudaSuccess)
+        r = cudaFuncSetAttribute(q_solve_kernel<5, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+      if (r == cudaSuccess)
+        r = cudaFuncSetAttribute(q_solve_kernel<8, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+      return r;
+    });
     const unsigned qg = (unsigned)((n + 7) / 8);
     const bool stg = n <= kSolveSmemMaxN;
     if (n <= 128 && stg)

@@ -10,7 +10,21 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
+
 namespace qrctm {
+
+// ---------------------------------------------------------------------------
+// Per-device host state.  Kernel attributes (the dynamic shared-memory
+// limit, the non-portable cluster size) are set per device, and devices may
+// differ in SM count, so one-time setup is keyed by (current device, key).
+// device_once runs f the first time a (device, key) pair is met, under a
+// lock (a concurrent first call waits for it), and returns f's result then
+// and on every later call for that pair.
+// ---------------------------------------------------------------------------
+cudaError_t device_once(const void* key, const std::function<cudaError_t()>& f);
+// SM count of the current device (looked up once per device).
+int device_sm_count();
 
 // ---------------------------------------------------------------------------
 // Mixed-radix index map: offset(i) = sum_t digit_t(i) * str[t].
@@ -204,11 +218,17 @@ __device__ __forceinline__ void grid_arrive(GridBar* bar) {
   asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
 }
 
-// Called by one thread; true once count >= target.
-__device__ __forceinline__ bool grid_wait(GridBar* bar, unsigned int target, int* err) {
+// Default bound of a grid wait, in polls (each poll after the first 64 sleeps
+// ~32 ns on top of its L2 round trip: about a second in all).
+constexpr long long kGridWaitSpins = 1ll << 25;
+
+// Called by one thread; true once count >= target.  After `limit` polls the
+// wait gives up: ERRF_TIMEOUT is raised and false returned.
+__device__ __forceinline__ bool grid_wait(GridBar* bar, unsigned int target, int* err,
+                                          long long limit) {
   long long spins = 0;
   while (ld_acquire_gpu(&bar->count) < target) {
-    if (++spins > (1ll << 25)) {
+    if (++spins > limit) {
       atomicOr(err, ERRF_TIMEOUT);
       return false;
     }
@@ -243,6 +263,11 @@ struct QrWork {
   // used for per-phase timing
   void (*hook)(void* user, int begin);
   void* hook_user;
+  // bound of the panel's grid waits (polls) and arrivals expected beyond the
+  // CTAs launched (0; a positive value makes every wait run out, which only
+  // the timeout test asks for); qr_carve sets the defaults
+  long long wait_spins;
+  unsigned int wait_extra;
 };
 constexpr long long kSplitKElems = 1ll << 21;   // 16 MB of split-K partials
 size_t qr_work_bytes(int m, int n);

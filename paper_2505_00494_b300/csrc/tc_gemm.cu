@@ -817,13 +817,12 @@ bool make_map(CUtensorMap* tm, const TcOperand& op, int box_rows) {
 template <int BN, int NBUF, int PRE>
 cudaError_t launch_bn(const TcGemm& g, cudaStream_t s) {
   using C = Cfg<BN, NBUF, PRE>;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(tc_tf32x3_kernel<BN, NBUF, PRE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  // the shared-memory limit is a per-device attribute of the kernel
+  cudaError_t ea = device_once((const void*)tc_tf32x3_kernel<BN, NBUF, PRE>, [] {
+    return cudaFuncSetAttribute(tc_tf32x3_kernel<BN, NBUF, PRE>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  });
+  if (ea != cudaSuccess) return ea;
   // tail planes (pre-split operands) share the layout of their head planes
   TcOperand alo = g.A, blo = g.B;
   if (C::PRE_A) alo.ptr = g.A.lo;
@@ -843,13 +842,7 @@ cudaError_t launch_bn(const TcGemm& g, cudaStream_t s) {
   // K chunks: at most 512 of K (16 blocks) per chunk, more chunks when the
   // output grid alone cannot fill the GPU; partials are summed by compensated
   // FP32 arithmetic
-  static int nsm = 0;
-  if (nsm == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (nsm <= 0) nsm = 148;
-  }
+  const int nsm = device_sm_count();
   const long long tiles = ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN) * std::max(1, g.batch);
   const int nkb = (int)((g.K + BK - 1) / BK);
   int ksplit = 1, kbps = nkb;

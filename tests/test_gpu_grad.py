@@ -5,7 +5,9 @@ Tolerances: unrolled-k gradient vs the oracle's complex-step derivative of
 the same k steps (the same function): 1e-9 relative; implicit fixed-point
 gradient vs the complex-step derivative through the fixed point: 1e-8
 relative (the FP64 target); central differences of converged GPU energies
-(step 1e-5): 1e-5 relative; scale invariance <g, A> = 0: 1e-10 * |g|."""
+(step 1e-6): |fd - g.v| <= 1e-5 |g| |v| (relative to the gradient's norm, so
+that a direction along which the derivative happens to be small is not held
+to an absolute bound); scale invariance <g, A> = 0: 1e-10 * |g|."""
 import numpy as np
 import pytest
 
@@ -74,12 +76,14 @@ def test_implicit_gradient_matches_complex_step(q, point, J2):
 
 def test_gradient_central_differences(q, point):
     """Central differences (step 1e-6) of converged GPU energies along 16
-    seeded symmetric directions (seeds 1001..1016) against g . v, 1e-5
-    relative (J1-J2 at J2/J1 = 0.5)."""
+    seeded symmetric unit directions (seeds 1001..1016) against g . v, to
+    1e-5 |g| |v| (J1-J2 at J2/J1 = 0.5)."""
     A, C, T = point
     ctx = make_ctx(q, A, C, T)
     _, g = ctx.energy_grad(1.0, 0.5, mode="implicit")
     g = g.cpu().numpy()
+    gnorm = float(np.linalg.norm(g))
+    assert gnorm > 1e-3
     c2 = q.QRCTM(2, 2, 8, with_nnn=True)
     eps = 1e-6
     for seed in range(1001, 1017):
@@ -91,7 +95,7 @@ def test_gradient_central_differences(q, point):
             Es.append(c2.energy(1.0, 0.5))
         fd = (Es[0] - Es[1]) / (2 * eps)
         got = float(np.sum(g * v))
-        assert abs(fd - got) < 1e-5 * max(1.0, abs(fd)), (seed, fd, got)
+        assert abs(fd - got) < 1e-5 * gnorm * np.linalg.norm(v), (seed, fd, got, gnorm)
 
 
 @pytest.fixture(scope="module")

@@ -39,7 +39,8 @@ def test_c4v_symmetrize(q, d, D, seed):
 
 
 @pytest.mark.parametrize("m,n,seed", [(64, 16, 0), (100, 33, 1), (1024, 64, 2), (5184, 144, 3),
-                                      (77, 77, 4), (300, 1, 5), (2000, 97, 6)])
+                                      (77, 77, 4), (300, 1, 5), (2000, 97, 6),
+                                      (40000, 16, 7), (200000, 4, 8)])
 def test_householder_qr(q, m, n, seed):
     M = np.random.default_rng(seed).standard_normal((m, n))
     Q, R = q.householder_qr(cuda(M))

@@ -48,7 +48,11 @@ def test_noalloc_matches_workspace_qr_twice(q):
     rng = np.random.default_rng(2024)
     # two calls in a row with different shapes: the second must not see the
     # first call's leftovers in the shared scratch
-    for m, n in ((5184, 144), (1000, 77)):
+    # shapes: 5184 x 144 and 1000 x 77 keep each CTA's panel rows in a small
+    # shared-memory tile; 40000 x 16 in a tile between 48 and 160 KB (the
+    # raised dynamic shared-memory limit); 200000 x 4 too tall for the tile,
+    # so the panel runs on the scratch copy in global memory
+    for m, n in ((5184, 144), (1000, 77), (40000, 16), (200000, 4)):
         M = _cuda(rng.standard_normal((m, n)))
         code, Qn, Rn = _noalloc(q, M)
         assert code == 0
