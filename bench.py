@@ -215,6 +215,23 @@ def oracle_sample(w, n_steps):
     return times, layers
 
 
+def oracle_sample_threads(workload, n_steps, threads):
+    """oracle_sample in a child process whose BLAS pools have `threads`
+    threads; returns {value, unit, cores} or {unavailable}."""
+    import subprocess
+    env = dict(os.environ)
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(threads)
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample-only",
+                            "--workload", workload, "--cpu-sample", str(n_steps)],
+                           env=env, capture_output=True, text=True, timeout=600)
+        out = json.loads(r.stdout.strip().splitlines()[-1])
+        return {"value": out["value"], "unit": UNIT, "cores": out["cores"]}
+    except Exception as exc:
+        return {"unavailable": str(exc)[:160]}
+
+
 def max_over_ranks(ms, dist, device):
     """The slowest rank's time (the job's time) when running under
     torch.distributed, else ms."""
@@ -678,8 +695,19 @@ def main():
     ap.add_argument("--conv-tol", type=float, default=0.0,
                     help="spectrum tolerance for time-to-converged (default 1e-10; the split path "
                          "stops earlier at its precision floor)")
+    ap.add_argument("--fp64-ttc-max-iter", type=int, default=4000,
+                    help="iteration cap of the FP64 path's own run from the bulk boundary to the "
+                         "tolerance (time-to-converged of the plain FP64 path); 0 skips it")
+    ap.add_argument("--no-grad", action="store_true",
+                    help="skip the energy-gradient extras (automatic when chi D^2 > 8192, where "
+                         "the 2x2-patch buffers of the J2 term and the gradient tapes are large)")
+    ap.add_argument("--oracle-sample-only", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     network = args.workload in qi.NETWORK_WORKLOADS
+    if args.oracle_sample_only:
+        times, _ = oracle_sample(qi.WORKLOADS[args.workload], args.cpu_sample)
+        print(json.dumps({"value": len(times) / sum(times), "cores": cpu_threads()}), flush=True)
+        return
     w = qi.NETWORK_WORKLOADS[args.workload] if network else qi.WORKLOADS[args.workload]
     if network:
         args.precision = "fp64"
@@ -766,7 +794,9 @@ def main():
     tf32_peak, tf32_note = tf32_peak_sustained(peaks)
     traffic = load_traffic(args.precision, args.workload)
     fp64_note = "fp64 nominal 1.25 TFLOP/s (CUDA-core FP64 pipe)"
-    kernels = {"qr_panel": ("qr_panel_kernel", panel_flops(d, D, chi), "alu", FP64_PEAK_TFLOPS,
+    # the split path's panels take two columns per grid-wide exchange
+    panel_k = "qr_panel2_kernel" if args.precision == "split" else "qr_panel_kernel"
+    kernels = {"qr_panel": (panel_k, panel_flops(d, D, chi), "alu", FP64_PEAK_TFLOPS,
                             fp64_note)}
     if args.precision == "split":
         m = chi * D * D
@@ -809,28 +839,22 @@ def main():
         E12 = ctx.energy(1.0, 0.5)
         energy_j2_ms = 1e3 * (time.perf_counter() - t0)
 
-    # end to end through the public API from pinned host buffers: per step the
-    # host copies (A, C, T) in, the library re-initialises from them and runs
-    # one iteration with its convergence test, and (C, T) come back to the host.
+    # end to end through the C ABI with host buffers: per step the library
+    # copies (A, C, T) in from pinned host memory (qrctm_init_env_host),
+    # re-initialises from them, runs one iteration with its convergence test
+    # and copies (C, T) back out (qrctm_get_env_host).
     C_d, T_d, _ = ctx.get_env(spectrum=False)
     hA = A.cpu().pin_memory()
     hC = C_d.cpu().pin_memory()
     hT = T_d.cpu().pin_memory()
     ctx2 = ctx
-    dA, dC, dT = torch.empty_like(A), torch.empty_like(C_d), torch.empty_like(T_d)
     oC, oT = torch.empty_like(hC).pin_memory(), torch.empty_like(hT).pin_memory()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        dA.copy_(hA, non_blocking=True)
-        dC.copy_(hC, non_blocking=True)
-        dT.copy_(hT, non_blocking=True)
-        ctx2.init_env(dA, dC, dT)
+        ctx2.init_env_host(hA, hC, hT)
         ctx2.step(1, want_delta=True)
-        Cn, Tn, _ = ctx2.get_env(spectrum=False)
-        oC.copy_(Cn, non_blocking=True)
-        oT.copy_(Tn, non_blocking=True)
-        torch.cuda.synchronize()
+        ctx2.get_env_host(oC, oT)
         # the result becomes the next step's pinned input: swap the buffers
         hC, oC = oC, hC
         hT, oT = oT, hT
@@ -842,14 +866,16 @@ def main():
     # the energy error of the split path against the FP64 path from that
     # environment, and the energy-gradient time (J1-J2 at J2/J1 = 0.5)
     extras = {}
+    grad_extras = not args.no_grad and chi * D * D <= 8192
     if not args.no_extras:
         # time to a converged environment from the bulk boundary: until the
         # spectrum change falls below tol, or (split precision) until it stops
         # decreasing -- the FP32-class contractions leave a floor near 1e-6 at
         # this size, the summed rounding noise of the small singular values
         tol = args.conv_tol or 1e-10
-        cctx = q.QRCTM(d, D, chi, precision=args.precision, check_every=ce, with_nnn=True,
-                       with_grad=True, grad_tol=args.grad_tol, grad_max_iter=300)
+        cctx = q.QRCTM(d, D, chi, precision=args.precision, check_every=ce,
+                       with_nnn=grad_extras, with_grad=grad_extras, grad_tol=args.grad_tol,
+                       grad_max_iter=300)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         cctx.init_env(A)
@@ -862,26 +888,27 @@ def main():
         extras["converged_at_floor"] = stalled
         Cc, Tc, _ = cctx.get_env(spectrum=False)
         e_split = cctx.energy(1.0, 0.0)
-        if args.precision == "split":
+        if args.precision == "split" and grad_extras:
             # gradient with the contractions on the TF32x3 engine
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             _, gs = cctx.energy_grad(1.0, 0.5, mode="implicit")
             torch.cuda.synchronize()
-            extras["split_energy_grad_ms"] = 1e3 * (time.perf_counter() - t0)
+            extras["split_energy_grad_implicit_ms"] = 1e3 * (time.perf_counter() - t0)
             extras["split_energy_grad_applications"] = cctx.grad_iterations
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             _, gsu = cctx.energy_grad(1.0, 0.5, mode="unroll", k_unroll=20)
             torch.cuda.synchronize()
             extras["split_energy_grad_unroll20_ms"] = 1e3 * (time.perf_counter() - t0)
+            extras["split_energy_grad_ms"] = extras["split_energy_grad_unroll20_ms"]
         cctx.close()
-        fctx = q.QRCTM(d, D, chi, precision="fp64", check_every=ce, with_nnn=True,
-                       with_grad=True, grad_tol=args.grad_tol, grad_max_iter=300)
+        fctx = q.QRCTM(d, D, chi, precision="fp64", check_every=ce, with_nnn=grad_extras,
+                       with_grad=grad_extras, grad_tol=args.grad_tol, grad_max_iter=300)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         fctx.init_env(A, Cc, Tc)
-        fits, fdl = fctx.run_to_convergence(tol=1e-10, max_iter=400)
+        fits, fdl = fctx.run_to_convergence(tol=tol, max_iter=4000)
         if fits % 2:
             fctx.step(1, want_delta=False)
         torch.cuda.synchronize()
@@ -891,6 +918,41 @@ def main():
         extras["E_per_site_J2_0"] = e_fp64
         extras["dE_split_vs_fp64"] = (e_split - e_fp64) if args.precision == "split" else 0.0
         extras["fp64_refine_iterations"] = fits
+        if args.precision == "split":
+            extras["time_to_converged_split_polish_s"] = (extras["time_to_converged_s"] +
+                                                          extras["fp64_refine_s"])
+        # the plain FP64 path on its own, from the same bulk boundary to the
+        # same tolerance: the comparison of time to a converged environment
+        # at equal energy accuracy (the split path's energy at its floor is
+        # within dE_split_vs_fp64 of the converged FP64 energy)
+        if args.precision == "split" and args.fp64_ttc_max_iter > 0:
+            bctx = q.QRCTM(d, D, chi, precision="fp64", check_every=ce)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            bctx.init_env(A)
+            bits, bdl, _ = converge(bctx, tol, args.fp64_ttc_max_iter)
+            torch.cuda.synchronize()
+            tb = time.perf_counter() - t0
+            e_b = bctx.energy(1.0, 0.0)
+            bctx.close()
+            reached = bdl < tol
+            extras["fp64_time_to_converged_s"] = tb if reached else None
+            extras["fp64_converged_iterations"] = bits
+            extras["fp64_converged_delta"] = bdl
+            extras["fp64_s_per_iteration"] = tb / max(1, bits)
+            extras["dE_fp64_from_bulk_vs_polished"] = e_b - e_fp64
+            if reached:
+                extras["split_floor_speedup_vs_fp64"] = tb / extras["time_to_converged_s"]
+                extras["split_polish_speedup_vs_fp64"] = (
+                    tb / extras["time_to_converged_split_polish_s"])
+            else:
+                # capped: the same map needs about as many iterations from the
+                # bulk as the split run plus its polish took
+                extras["fp64_time_to_converged_estimate_s"] = (
+                    extras["fp64_s_per_iteration"] * (its + fits))
+        if not grad_extras:
+            fctx.close()
+    if not args.no_extras and grad_extras:
         # energy gradient at J2/J1 = 0.5 with FP64 reverse passes: the implicit
         # adjoint (GMRES on the two-step fixed point) and the unrolled
         # backpropagation through the last 20 steps
@@ -898,17 +960,22 @@ def main():
         t0 = time.perf_counter()
         Eg, g = fctx.energy_grad(1.0, 0.5, mode="implicit")
         torch.cuda.synchronize()
-        extras["energy_grad_ms"] = 1e3 * (time.perf_counter() - t0)
+        extras["energy_grad_implicit_ms"] = 1e3 * (time.perf_counter() - t0)
         extras["energy_grad_adjoint_applications"] = fctx.grad_iterations
         extras["energy_grad_adjoint_residual"] = fctx.grad_residual
+        extras["grad_fixed_point_residual"] = fctx.grad_fixed_point_residual
         extras["E_per_site_J2_0.5"] = Eg
         extras["grad_norm"] = float(g.norm().item())
         extras["grad_dot_A"] = float((g * A).sum().item())
+        # the headline gradient: backpropagation through the last 20 steps
+        # (the paper's scheme at D = 6); it needs no elementwise fixed point
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         Eu, gu = fctx.energy_grad(1.0, 0.5, mode="unroll", k_unroll=20)
         torch.cuda.synchronize()
         extras["energy_grad_unroll20_ms"] = 1e3 * (time.perf_counter() - t0)
+        extras["energy_grad_ms"] = extras["energy_grad_unroll20_ms"]
+        extras["energy_grad_mode"] = "unroll20"
         extras["grad_implicit_vs_unroll20_rel"] = float((g - gu).norm() / g.norm())
         if args.precision == "split":
             # the split gradients were taken at the split environment, the
@@ -924,6 +991,9 @@ def main():
                "kind": "oracle",
                "sample": f"{len(times)} oracle QR-CTMRG iterations ({layers} layers, NumPy FP64, "
                          f"d={d} D={D} chi={chi}) from a random symmetric environment"}
+        # the same sample on 8 BLAS threads, the paper's CPU setting (8 cores):
+        # a child process, since the BLAS pool size is fixed when NumPy loads
+        cpu["threads_8"] = oracle_sample_threads(args.workload, args.cpu_sample, 8)
 
     if rank == 0:
         line = {
@@ -952,6 +1022,7 @@ def main():
                                 "energy_j2_ms": energy_j2_ms},
             "energy_grad_ms": extras.get("energy_grad_ms"),
             "split_energy_grad_ms": extras.get("split_energy_grad_ms"),
+            "energy_grad_mode": extras.get("energy_grad_mode"),
             "convergence": extras,
             "cpu_baseline": cpu,
         }

@@ -87,8 +87,13 @@ typedef struct {
 } qrctm_config;
 
 typedef struct {
-  double J1;          /* nearest-neighbour coupling (sublattice-rotated bond)    */
+  double J1;          /* nearest-neighbour coupling                              */
   double J2;          /* next-nearest-neighbour coupling (plain bond)            */
+  int sublattice_rotation;  /* 1: the NN bond is taken with one sublattice rotated
+                         by exp(i pi sigma^y / 2) (Results, Heisenberg paragraph),
+                         h~ = (-XX + YY - ZZ)/4, so that the Neel state is the
+                         uniform C4v state; 0: the plain bond (XX + YY + ZZ)/4 on
+                         NN pairs too.  NNN pairs share a sublattice: plain bond. */
 } qrctm_model;
 
 typedef struct qrctm_ctx qrctm_ctx;
@@ -136,6 +141,15 @@ void qrctm_destroy(qrctm_ctx* ctx);
  *    dominant-|eigenvalue| subspace of the enlarged corner (block subspace
  *    iteration, Fig. 1(d)). */
 qrctm_status qrctm_init_env(qrctm_ctx* ctx, const double* A, const double* C0, const double* T0);
+
+/* qrctm_init_env from host memory: A (d*D^4 doubles) and the optional C0, T0
+ * (both or neither) are host arrays, copied to the device on the context's
+ * stream inside this call (pinned memory makes the copies asynchronous
+ * DMA).  A is staged in a per-step scratch region of the workspace, C0 and
+ * T0 in the raw environment buffers; the call then proceeds as
+ * qrctm_init_env.  Same errors; the caller keeps ownership of its arrays. */
+qrctm_status qrctm_init_env_host(qrctm_ctx* ctx, const double* A_host, const double* C0_host,
+                                 const double* T0_host);
 
 /* Run n_steps QR-CTMRG steps (Fig. 1(e,f)).  If delta_out is non-NULL the
  * corner spectrum change since the previous test is computed and returned
@@ -253,8 +267,17 @@ qrctm_status qrctm_optimize(qrctm_ctx* ctx, const qrctm_model* model,
  * NULL); spectrum_host: chi doubles, sorted |eig(C)| (may be NULL). */
 qrctm_status qrctm_get_env(qrctm_ctx* ctx, double* C, double* T, double* spectrum_host);
 
+/* qrctm_get_env into host memory: C_host (chi*chi) and T_host (chi*D^2*chi)
+ * (either may be NULL) are copied device-to-host on the context's stream;
+ * the call returns after the copies are complete. */
+qrctm_status qrctm_get_env_host(qrctm_ctx* ctx, double* C_host, double* T_host,
+                                double* spectrum_host);
+
 /* Phase timing.  With profiling on, the library records a pair of CUDA
- * events on the context's stream around every phase; qrctm_phase_times
+ * events on the context's stream around every phase and opens an NVTX range
+ * named "qrctm:<phase>" (ct, qr, x1, absorb, project, corner, symnorm,
+ * spectrum, energy, grad, warmup, qr_panel) around its launches, which run
+ * eagerly instead of from the step's CUDA graph; qrctm_phase_times
  * synchronises the stream, writes the accumulated milliseconds and the number
  * of timed occurrences of each phase since the previous call
  * (QRCTM_NUM_PHASES entries each, host arrays, either may be NULL) and resets

@@ -426,11 +426,13 @@ def bond_energy(rho4, h):
     return np.trace(rho @ h.T) / np.trace(rho)
 
 
-def energy(C, T, A, J1=1.0, J2=0.0):
+def energy(C, T, A, J1=1.0, J2=0.0, rotate=True):
     """Energy per site: 2 J1 <h~>_nn + 2 J2 <h>_nnn (two NN and two NNN bonds
     per site; NN pairs use the sublattice-rotated bond, NNN pairs share a
-    sublattice and use the plain bond)."""
-    E = 2.0 * J1 * bond_energy(rdm_nn(C, T, A), rotated_heisenberg_bond())
+    sublattice and use the plain bond).  rotate=False takes the plain bond on
+    NN pairs too (no sublattice rotation)."""
+    hnn = rotated_heisenberg_bond() if rotate else heisenberg_bond()
+    E = 2.0 * J1 * bond_energy(rdm_nn(C, T, A), hnn)
     if J2 != 0.0:
         E = E + 2.0 * J2 * bond_energy(rdm_nnn(C, T, A), heisenberg_bond())
     return E
@@ -489,7 +491,8 @@ def directional_derivative_fixed_point(A, v, C, T, J1=1.0, J2=0.0,
     return float(np.imag(energy(Cc, Tc, Ac, J1, J2)) / h), info
 
 
-def directional_derivative_unrolled(A, v, C, T, k, J1=1.0, J2=0.0, h=1e-20, layers="double"):
+def directional_derivative_unrolled(A, v, C, T, k, J1=1.0, J2=0.0, h=1e-20, layers="double",
+                                    rotate=True):
     """dE/dA . v of E(A, F^k(A; C, T)) with (C, T) held fixed: the gradient of
     k tracked CTMRG steps started from a detached environment.  ``layers``
     picks the double-layer or the ket-then-bra form of the edge update (equal
@@ -498,7 +501,7 @@ def directional_derivative_unrolled(A, v, C, T, k, J1=1.0, J2=0.0, h=1e-20, laye
     Cc, Tc = C.astype(complex), T.astype(complex)
     for _ in range(k):
         Cc, Tc = qr_step(Cc, Tc, Ac, layers)
-    return float(np.imag(energy(Cc, Tc, Ac, J1, J2)) / h)
+    return float(np.imag(energy(Cc, Tc, Ac, J1, J2, rotate)) / h)
 
 
 def energy_at(A, C, T, J1=1.0, J2=0.0, tol=1e-13, max_iter=2000):

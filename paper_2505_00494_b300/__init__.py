@@ -56,7 +56,8 @@ class Config(ctypes.Structure):
 
 
 class Model(ctypes.Structure):
-    _fields_ = [("J1", ctypes.c_double), ("J2", ctypes.c_double)]
+    _fields_ = [("J1", ctypes.c_double), ("J2", ctypes.c_double),
+                ("sublattice_rotation", ctypes.c_int)]
 
 
 class LbfgsOptions(ctypes.Structure):
@@ -82,6 +83,8 @@ _sig = {
     "qrctm_energy_grad": ([_vp, ctypes.POINTER(Model), ctypes.c_int, ctypes.c_int, _vp, _dp],
                           ctypes.c_int),
     "qrctm_get_env": ([_vp, _vp, _vp, _dp], ctypes.c_int),
+    "qrctm_init_env_host": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+    "qrctm_get_env_host": ([_vp, _vp, _vp, _dp], ctypes.c_int),
     "qrctm_init_env_network": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "qrctm_optimize": ([_vp, ctypes.POINTER(Model), ctypes.POINTER(LbfgsOptions), ctypes.c_int,
                         _vp, _dp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
@@ -159,6 +162,18 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _hptr(t):
+    """Pointer of a contiguous host float64 tensor (None passes NULL)."""
+    if t is None:
+        return None
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float64:
+        raise TypeError("expected a host (CPU) float64 tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def _workspace(nbytes, device, zero=False):
     torch = _torch()
     alloc = torch.zeros if zero else torch.empty
@@ -221,6 +236,23 @@ class QRCTM:
         self.A = A
         self._check(_load().qrctm_init_env(self.h, _ptr(A), _ptr(C0), _ptr(T0)), "qrctm_init_env")
 
+    def init_env_host(self, A, C0=None, T0=None):
+        """qrctm_init_env from host float64 tensors (pinned for asynchronous
+        copies); the copies run inside the library call."""
+        self.A = None
+        self._check(_load().qrctm_init_env_host(self.h, _hptr(A), _hptr(C0), _hptr(T0)),
+                    "qrctm_init_env_host")
+
+    def get_env_host(self, C, T, spectrum=False):
+        """Copy (C, T) into host float64 tensors C (chi, chi), T (chi, D2, chi)
+        inside the library call; optional sorted |eig C| as a NumPy array."""
+        import numpy as np
+        s = np.zeros(self.chi) if spectrum else None
+        sp = s.ctypes.data_as(_dp) if spectrum else None
+        self._check(_load().qrctm_get_env_host(self.h, _hptr(C), _hptr(T), sp),
+                    "qrctm_get_env_host")
+        return s
+
     def init_env_network(self, a, v=None, C0=None, T0=None):
         """Classical network tensor a[u,l,d,r] (bond D) fed directly; v: the
         boundary vector (None = all ones); (C0, T0): a starting environment
@@ -254,25 +286,25 @@ class QRCTM:
         self._check(code, "qrctm_run_to_convergence")
         return it.value, dlt.value
 
-    def energy(self, J1=1.0, J2=0.0):
+    def energy(self, J1=1.0, J2=0.0, rotation=True):
         e = ctypes.c_double(0.0)
-        m = Model(J1, J2)
+        m = Model(J1, J2, int(rotation))
         self._check(_load().qrctm_energy(self.h, ctypes.byref(m), ctypes.byref(e)), "qrctm_energy")
         return e.value
 
-    def energy_grad(self, J1=1.0, J2=0.0, mode="implicit", k_unroll=20, grad=None):
+    def energy_grad(self, J1=1.0, J2=0.0, mode="implicit", k_unroll=20, grad=None, rotation=True):
         torch = _torch()
         if grad is None:
             grad = torch.empty((self.d,) + (self.D,) * 4, dtype=torch.float64, device="cuda")
         e = ctypes.c_double(0.0)
-        m = Model(J1, J2)
+        m = Model(J1, J2, int(rotation))
         self._check(_load().qrctm_energy_grad(self.h, ctypes.byref(m), GRAD_MODE[mode], k_unroll,
                                           _ptr(grad), ctypes.byref(e)), "qrctm_energy_grad")
         return e.value, grad
 
     def optimize(self, A, n_steps, J1=1.0, J2=0.0, k_unroll=10, nograd_steps=2, history=0,
                  max_ls=0, c1=0.0, step0=0.0, env_tol=0.0, env_max_iter=0,
-                 raise_on_line_search=False):
+                 raise_on_line_search=False, rotation=True):
         """L-BFGS on the energy per site; A (device, C4v) is updated in place.
         Returns (energies of the accepted points, evaluations, line search
         failed)."""
@@ -281,7 +313,7 @@ class QRCTM:
                            env_max_iter)
         en = np.zeros(n_steps + 1)
         steps, evals = ctypes.c_int(0), ctypes.c_int(0)
-        m = Model(J1, J2)
+        m = Model(J1, J2, int(rotation))
         code = _load().qrctm_optimize(self.h, ctypes.byref(m), ctypes.byref(opt), n_steps, _ptr(A),
                                       en.ctypes.data_as(_dp), ctypes.byref(steps),
                                       ctypes.byref(evals))

@@ -10,6 +10,8 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ctx.cuh"
 #include "tc_gemm.cuh"
 #include "grad.cuh"
@@ -273,16 +275,35 @@ void phase_end(qrctm_ctx* c, int ph, cudaEvent_t a) {
   c->recs.push_back({ph, a, b});
 }
 
+// NVTX range names of the phases (profiling only: a tool such as ncu can
+// then select the kernels of one phase with --nvtx-include "qrctm:x1/")
+static const char* const kPhaseNames[QRCTM_NUM_PHASES] = {
+    "qrctm:ct",      "qrctm:qr",     "qrctm:x1",       "qrctm:absorb",
+    "qrctm:project", "qrctm:corner", "qrctm:symnorm",  "qrctm:spectrum",
+    "qrctm:energy",  "qrctm:grad",   "qrctm:warmup",   "qrctm:qr_panel"};
+
 // panel launches of the QR, timed as the nested phase QRCTM_PH_QR_PANEL
 void panel_hook(void* user, int begin) {
   qrctm_ctx* c = static_cast<qrctm_ctx*>(user);
-  if (begin) c->panel_ev = phase_begin(c);
-  else { phase_end(c, QRCTM_PH_QR_PANEL, c->panel_ev); c->panel_ev = nullptr; }
+  if (begin) {
+    if (c->prof) nvtxRangePushA(kPhaseNames[QRCTM_PH_QR_PANEL]);
+    c->panel_ev = phase_begin(c);
+  } else {
+    phase_end(c, QRCTM_PH_QR_PANEL, c->panel_ev);
+    c->panel_ev = nullptr;
+    if (c->prof) nvtxRangePop();
+  }
 }
 
-PhaseScope::PhaseScope(qrctm_ctx* c_, int ph_) : c(c_), ph(ph_), a(phase_begin(c_)) {}
+PhaseScope::PhaseScope(qrctm_ctx* c_, int ph_) : c(c_), ph(ph_), a(nullptr) {
+  if (c->prof && ph >= 0 && ph < QRCTM_NUM_PHASES) nvtxRangePushA(kPhaseNames[ph]);
+  a = phase_begin(c);
+}
 
-PhaseScope::~PhaseScope() { phase_end(c, ph, a); }
+PhaseScope::~PhaseScope() {
+  phase_end(c, ph, a);
+  if (c->prof && ph >= 0 && ph < QRCTM_NUM_PHASES) nvtxRangePop();
+}
 
 }  // namespace qrctm
 
@@ -669,6 +690,9 @@ qrctm_status qrctm_run_to_convergence(qrctm_ctx* c, double tol, int max_iter, in
 
 qrctm_status qrctm_energy(qrctm_ctx* c, const qrctm_model* model, double* e_out) {
   if (!c || !model || !e_out) return QRCTM_ERR_INVALID_ARG;
+  if (model->sublattice_rotation != 0 && model->sublattice_rotation != 1)
+    return set_err(c, QRCTM_ERR_INVALID_ARG, "sublattice_rotation must be 0 or 1");
+  c->nn_plain = model->sublattice_rotation == 0;
   if (!c->have_env) return set_err(c, QRCTM_ERR_STATE, "qrctm_init_env not called");
   if (c->d != 2) return set_err(c, QRCTM_ERR_INVALID_ARG, "the spin-1/2 energy needs d = 2");
   if (model->J2 != 0.0 && c->E3 == nullptr)
@@ -691,6 +715,9 @@ qrctm_status qrctm_energy(qrctm_ctx* c, const qrctm_model* model, double* e_out)
 qrctm_status qrctm_energy_grad(qrctm_ctx* c, const qrctm_model* model, int mode, int k_unroll,
                                double* grad, double* e_out) {
   if (!c || !model || !grad || !e_out) return QRCTM_ERR_INVALID_ARG;
+  if (model->sublattice_rotation != 0 && model->sublattice_rotation != 1)
+    return set_err(c, QRCTM_ERR_INVALID_ARG, "sublattice_rotation must be 0 or 1");
+  c->nn_plain = model->sublattice_rotation == 0;
   if (!c->have_env) return set_err(c, QRCTM_ERR_STATE, "qrctm_init_env not called");
   if (c->d != 2) return set_err(c, QRCTM_ERR_INVALID_ARG, "the spin-1/2 energy needs d = 2");
   if (!c->G) return set_err(c, QRCTM_ERR_INVALID_ARG, "qrctm_energy_grad needs with_grad = 1");
@@ -875,6 +902,43 @@ qrctm_status qrctm_get_env(qrctm_ctx* c, double* C, double* T, double* spectrum_
       return cuda_fail(c, e, "spectrum");
   }
   return sync_check(c, "get env");
+}
+
+qrctm_status qrctm_init_env_host(qrctm_ctx* c, const double* A, const double* C0,
+                                 const double* T0) {
+  if (!c || !A) return QRCTM_ERR_INVALID_ARG;
+  if (c->network)
+    return set_err(c, QRCTM_ERR_INVALID_ARG, "NETWORK layers: use qrctm_init_env_network");
+  if ((C0 == nullptr) != (T0 == nullptr))
+    return set_err(c, QRCTM_ERR_INVALID_ARG, "C0 and T0 must both be given or both NULL");
+  const long long nA = (long long)c->d * c->D2 * c->D2;
+  const long long nC = (long long)c->chi * c->chi, nT = (long long)c->chi * c->D2 * c->chi;
+  // staging: A in the X1 scratch (chi^2 D^4 >= d D^4 doubles, unused until a
+  // step runs), C0 and T0 in the raw environment buffers (the inputs of the
+  // symmetrise-and-normalise kernel that qrctm_init_env applies to them)
+  cudaError_t e = cudaMemcpyAsync(c->X1, A, sizeof(double) * nA, cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess && C0)
+    e = cudaMemcpyAsync(c->Craw, C0, sizeof(double) * nC, cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess && T0)
+    e = cudaMemcpyAsync(c->Traw, T0, sizeof(double) * nT, cudaMemcpyHostToDevice, c->st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copy host inputs");
+  return qrctm_init_env(c, c->X1, C0 ? c->Craw : nullptr, T0 ? c->Traw : nullptr);
+}
+
+qrctm_status qrctm_get_env_host(qrctm_ctx* c, double* C, double* T, double* spectrum_host) {
+  if (!c) return QRCTM_ERR_INVALID_ARG;
+  if (!c->have_env) return set_err(c, QRCTM_ERR_STATE, "qrctm_init_env not called");
+  cudaError_t e;
+  const long long nC = (long long)c->chi_cur * c->chi_cur;
+  const long long nT = (long long)c->chi_cur * c->D2 * c->chi_cur;
+  if (C && (e = cudaMemcpyAsync(C, c->C, sizeof(double) * nC, cudaMemcpyDeviceToHost, c->st)) !=
+               cudaSuccess)
+    return cuda_fail(c, e, "get env");
+  if (T && (e = cudaMemcpyAsync(T, c->T, sizeof(double) * nT, cudaMemcpyDeviceToHost, c->st)) !=
+               cudaSuccess)
+    return cuda_fail(c, e, "get env");
+  // the spectrum (if asked) and the synchronisation that completes the copies
+  return qrctm_get_env(c, nullptr, nullptr, spectrum_host);
 }
 
 size_t qrctm_c4v_symmetrize_workspace_bytes(void) { return 256 * sizeof(double); }

@@ -52,6 +52,7 @@ struct qrctm_ctx {
   int grad_iters;
   double grad_resid;
   double grad_fp_resid;   // ||G(x) - x|| / ||x|| at the last implicit gradient
+  bool nn_plain;          // plain NN bond (model->sublattice_rotation == 0)
   cudaEvent_t panel_ev;   // open panel-phase event (profiling)
   // standard (eigendecomposition) method
   void* solver;            // cusolverDnHandle_t, created on first use
@@ -113,6 +114,9 @@ inline Gemm gemm_ctx(qrctm_ctx* c) {
 // Contraction of the energy / adjoint passes: split precision (TF32x3 on the
 // tensor cores from gathered FP32 operands) when c->mm_split, else FP64.
 cudaError_t gemm_run(qrctm_ctx* c, const Gemm& g);
+// gemm_run with K cut into chunks of at most kchunk (a multiple of 4; 0 = one
+// pass) on the tensor-core engine, the chunk results summed in FP64.
+cudaError_t gemm_run_kchunked(qrctm_ctx* c, const Gemm& g, long long kchunk);
 size_t mm_split_floats(const Gemm& g);
 
 // Workspace plan (api.cu); 256-byte aligned regions.

@@ -10,7 +10,13 @@
 // rho_nnn: two diagonal sites of a 2x2 patch (4 C, 8 T).  The four quadrants
 //          are one enlarged corner; with its physical legs open (Ct_open) on
 //          the diagonal sites, rho = Tr(Ct_open Ct Ct_open Ct).
-// The traces and the energy are reduced in FP64 on the device.
+// The traces and the energy are reduced in FP64 on the device.  In a
+// split-precision context the one O((chi D^2)^3) product of the energy,
+// P(s,t) = Ct_open(s,t) Ct (d^2 products of (chi D^2)-square matrices, ~90%
+// of the J2 term's work), runs on the TF32x3 tensor-core engine in K chunks
+// of 512 whose FP32 results are summed in FP64 (one FP32 pass over the whole
+// K = chi D^2 moved the d2 D6 chi144 energy by 2.3e-7); every other
+// contraction and every trace stay FP64.
 #include "ctx.cuh"
 
 namespace qrctm {
@@ -50,8 +56,8 @@ __device__ double bond_expect(const double* rho4, const double* h) {
 }
 
 __global__ void energy_k(const double* rho_nn, const double* rho_nnn, double J1, double J2,
-                         double* e_out, int* err) {
-  const double enn = bond_expect(rho_nn, c_hr);
+                         int nn_plain, double* e_out, int* err) {
+  const double enn = bond_expect(rho_nn, nn_plain ? c_h : c_hr);
   double e = 2.0 * J1 * enn;
   double ennn = 0.0;
   if (rho_nnn != nullptr) {
@@ -170,13 +176,17 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
       trace_phys_k<<<1184, 256, 0, st>>>(c->E1, c->X2, d, mm);
       note_launch();
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      // P(s,t) = Ct_open(s,t) Ct
+      // P(s,t) = Ct_open(s,t) Ct  (tensor cores in a split-precision context)
       g = gemm_ctx(c);
       g.M = m; g.N = m; g.K = m; g.batch = d * d;
       g.A = c->E1; g.a_m = im1(m); g.a_k = im1(1); g.a_b = im1(mm);
       g.B = c->X2; g.b_k = im1(m); g.b_n = im1(1); g.b_b = im0();
       g.C = c->E3; g.c_m = im1(m); g.c_n = im1(1); g.c_b = im1(mm);
-      if ((e = gemm_run(c, g)) != cudaSuccess) return e;
+      const bool was = c->mm_split;
+      c->mm_split = c->split_prec && c->mm32 != nullptr;
+      e = gemm_run_kchunked(c, g, 512);
+      c->mm_split = was;
+      if (e != cudaSuccess) return e;
       // rho_nnn[(s1,t1),(s4,t4)] = sum_{a,c} P(s1,t1)[a,c] P(s4,t4)[c,a]
       g = gemm_ctx(c);
       g.M = d * d; g.N = d * d; g.K = mm;
@@ -186,7 +196,7 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
       if ((e = gemm_run(c, g)) != cudaSuccess) return e;
     }
   }
-  energy_k<<<1, 1, 0, st>>>(c->rho, rho_nnn, J1, J2, c->e_d, c->err);
+  energy_k<<<1, 1, 0, st>>>(c->rho, rho_nnn, J1, J2, c->nn_plain ? 1 : 0, c->e_d, c->err);
   note_launch();
   return cudaGetLastError();
 }

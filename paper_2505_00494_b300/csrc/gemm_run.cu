@@ -60,13 +60,16 @@ size_t mm_split_floats(const Gemm& g) {
   return (size_t)(Ka * (nbA * g.M + nbB * g.N));
 }
 
-cudaError_t gemm_run(qrctm_ctx* c, const Gemm& g) {
+cudaError_t gemm_run(qrctm_ctx* c, const Gemm& g) { return gemm_run_kchunked(c, g, 0); }
+
+cudaError_t gemm_run_kchunked(qrctm_ctx* c, const Gemm& g, long long kchunk) {
   // contractions with a thin output (a reduction over a long index into a
   // few numbers, memory bound) or whose operand copies would not fit the
   // scratch stay on the FP64 engine
   if (!c->mm_split || std::min(g.M, g.N) < 16 || mm_split_floats(g) > c->mm32_floats)
     return gemm_f64(g, c->st);
   if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
+  if (kchunk < 0 || (kchunk & 3) != 0) return cudaErrorInvalidValue;
   const long long Ka = pad4(g.K), B = std::max(1, g.batch);
   const bool shA = zero_map(g.a_b), shB = zero_map(g.b_b);
   const long long nbA = shA ? 1 : B, nbB = shB ? 1 : B;
@@ -77,16 +80,24 @@ cudaError_t gemm_run(qrctm_ctx* c, const Gemm& g) {
     return e;
   if ((e = gather3(g.B, B32, nbB, g.N, g.K, Ka, g.b_b, g.b_n, g.b_k, c->st)) != cudaSuccess)
     return e;
-  TcGemm t{};
-  t.A = TcOperand{A32, g.M, g.K, Ka, (int)nbA, g.M * Ka};
-  t.B = TcOperand{B32, g.N, g.K, Ka, (int)nbB, g.N * Ka};
-  t.M = g.M; t.N = g.N; t.K = g.K; t.batch = (int)B;
-  t.C = g.C; t.c_fp64 = true;
-  t.c_m = g.c_m; t.c_n = g.c_n; t.c_b = g.c_b;
-  t.alpha = g.alpha; t.beta = g.beta;
-  t.err = c->err;
-  t.part = c->tc_part; t.part_elems = c->tc_part_elems;
-  return gemm_tc(t, c->st);
+  // K in chunks (kchunk > 0): every chunk accumulates in FP32 on the tensor
+  // cores and is added to the FP64 result by the epilogue (beta = 1 after the
+  // first), so no FP32 sum runs over more than kchunk terms
+  const long long kc = kchunk > 0 ? kchunk : g.K;
+  for (long long k0 = 0; k0 < g.K; k0 += kc) {
+    const long long kn = std::min(kc, g.K - k0);
+    TcGemm t{};
+    t.A = TcOperand{A32 + k0, g.M, kn, Ka, (int)nbA, g.M * Ka};
+    t.B = TcOperand{B32 + k0, g.N, kn, Ka, (int)nbB, g.N * Ka};
+    t.M = g.M; t.N = g.N; t.K = kn; t.batch = (int)B;
+    t.C = g.C; t.c_fp64 = true;
+    t.c_m = g.c_m; t.c_n = g.c_n; t.c_b = g.c_b;
+    t.alpha = g.alpha; t.beta = k0 == 0 ? g.beta : 1.0;
+    t.err = c->err;
+    t.part = c->tc_part; t.part_elems = c->tc_part_elems;
+    if ((e = gemm_tc(t, c->st)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace qrctm

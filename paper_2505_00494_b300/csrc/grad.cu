@@ -166,7 +166,7 @@ __global__ void trace_phys2_k(const double* __restrict__ Co, double* __restrict_
 }
 
 __global__ void energy2_k(const double* rho_nn, const double* rho_nnn, double J1, double J2,
-                          double* e_out) {
+                          int nn_plain, double* e_out) {
   auto be = [](const double* rho4, const double* h) {
     double num = 0.0, den = 0.0;
     for (int s1 = 0; s1 < 2; ++s1)
@@ -179,7 +179,7 @@ __global__ void energy2_k(const double* rho_nn, const double* rho_nnn, double J1
           }
     return num / den;
   };
-  double e = 2.0 * J1 * be(rho_nn, g_hr);
+  double e = 2.0 * J1 * be(rho_nn, nn_plain ? g_h : g_hr);
   if (rho_nnn) e += 2.0 * J2 * be(rho_nnn, g_h);
   e_out[0] = e;
 }
@@ -321,7 +321,7 @@ static cudaError_t energy_vjp(qrctm_ctx* c, const GradLayout& L, const double* C
     if ((e = gemm_run(c, *g)) != cudaSuccess) return e;
   // ---- reverse (2x1 patch): E_nn = 2 J1 Tr(rho h~)/Tr(rho) ----
   double* ctb = L.ctb;
-  rho_bar_k<<<1, 32, 0, s>>>(rho, 0, 2.0 * J1, L.rhob);
+  rho_bar_k<<<1, 32, 0, s>>>(rho, c->nn_plain ? 1 : 0, 2.0 * J1, L.rhob);
   note_launch();
   if ((e = gemm_vjp(c, f_rho, L.rhob, L.HLb, nullptr, false, false)) != cudaSuccess) return e;
   if ((e = gemm_vjp(c, f_rho, L.rhob, nullptr, L.HLb, false, true)) != cudaSuccess) return e;
@@ -380,7 +380,7 @@ static cudaError_t energy_vjp(qrctm_ctx* c, const GradLayout& L, const double* C
   }
   // ct = C T
   if ((e = gemm_vjp(c, f_ct, ctb, Cb, Tb, true, true)) != cudaSuccess) return e;
-  energy2_k<<<1, 1, 0, s>>>(rho, rho_nnn, J1, J2, e_out_dev);
+  energy2_k<<<1, 1, 0, s>>>(rho, rho_nnn, J1, J2, c->nn_plain ? 1 : 0, e_out_dev);
   note_launch();
   (void)c2; (void)mc;
   return cudaGetLastError();

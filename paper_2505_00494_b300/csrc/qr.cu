@@ -331,6 +331,431 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
   if (threadIdx.x == 0) grid_exit(bar, (unsigned)P);
 }
 
+// Cancellation guard of a paired round: column b's reflector norm
+// sigma_b = |x_b + m_b x_a|^2 (rows below its pivot) is formed from the
+// pair's Gram sums; it is used only when it keeps at least this fraction of
+// M_b = G_bb + 2 |m_b G_ab| + m_b^2 G_aa (so its relative rounding error
+// stays below ~2^10 ulp); otherwise the round factors column a alone.
+constexpr double kPairGuard = 1.0 / 1024.0;
+
+// Panel factorisation with up to two columns per grid-wide exchange.  The
+// single-column kernel above needs one exchange of partial sums per column;
+// here a round factors columns a = j and b = j + 1 (pivot rows c, c + 1) from
+// one exchange of the pair's Gram sums over the rows below both pivots,
+//   G_at = sum x_a y_t,  G_bt = sum x_b y_t   (t >= a, resp. t >= b),
+// and the two pivot rows (published by their owners).  Column a's reflector
+// follows from sigma_a = G_aa + x_a[c+1]^2 and s_t = G_at + x_a[c+1] y_t[c+1]
+// exactly as in the single-column kernel (multipliers m_t: y_t += m_t x_a on
+// the rows below c).  After it, on the rows below c + 1,
+//   x_b' = x_b + m_b x_a,  y_t' = y_t + m_t x_a,  so
+//   sigma_b = G_bb + 2 m_b G_ab + m_b^2 G_aa,
+//   s_t'    = G_bt + m_t G_ab + m_b G_at + m_b m_t G_aa,
+// and column b's reflector (pivot value x_b[c+1] + m_b x_a[c+1], multipliers
+// n_t) is applied in the same row pass: y_t'' = y_t' + n_t x_b'.  The row
+// pass then accumulates the Gram sums of the next pair over the rows below
+// its pivots and the owners publish those two pivot rows.  When sigma_b
+// fails the cancellation guard (or only one column is left) the round
+// factors column a alone and the next pair starts at b.  Every CTA takes the
+// same decision from the same sums.  Accumulators: per round starting at
+// panel column p, two rows of NB doubles (Gram sums of columns p and p + 1);
+// pivot rows rowb[buffer][2][NB].
+template <bool TILE>
+__global__ void __launch_bounds__(PT) qr_panel2_kernel(double* __restrict__ W,
+                                                       double* __restrict__ V,
+                                                       double* __restrict__ tau_out,
+                                                       double* __restrict__ part, GridBar* bar,
+                                                       int* err, int m, int j0, int nb,
+                                                       int rows_per_cta, float* __restrict__ X32,
+                                                       long long ldx, float* __restrict__ Vt32,
+                                                       const float* __restrict__ src32,
+                                                       float* __restrict__ V32, long long ldv,
+                                                       long long wait_spins, unsigned wait_extra) {
+  const int P = gridDim.x, b = blockIdx.x;
+  const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;   // wrp = row lane (0..7)
+  const long long r_begin = (long long)j0 + (long long)b * rows_per_cta;
+  const long long r_end = std::min<long long>(m, r_begin + rows_per_cta);
+  const int rows = (int)std::max<long long>(0, r_end - r_begin);
+  double* accum = part + (size_t)j0 * 2 * NB;       // round at panel column p: accum + p * 2 NB
+  double* rowb = part + 2 * (size_t)PMAX * NB;      // [buffer][pivot row 0/1][NB]
+  __shared__ double red[8][2][NB];
+  __shared__ double cfa[NB];      // lane 0: 1/w_a; lane t >= 1: m_t
+  __shared__ double cfb[NB];      // lane 1: 1/w_b; lane t >= 2: n_t
+  __shared__ double ssum[NB][NB]; // column j: sigma (slot 0) and s_t (slot t)
+  __shared__ double tau_s[NB];
+  __shared__ double iw_s[NB];
+  __shared__ double x0_s[NB];     // pivot value of column j when its reflector was formed
+  __shared__ double rsig_s;       // 1/sigma_a (warp 1)
+  __shared__ double rsigb_s;      // 1/sigma_b (warp 2)
+  __shared__ double sc_rmu, sc_inw;    // reflector a: 1/mu_a, 1/w_a (warp 0)
+  __shared__ double sc_rmub, sc_iwb;   // reflector b: 1/mu_b, 1/w_b (warp 1)
+  __shared__ int s_ok, s_k, s_kr;
+  extern __shared__ double tile[];
+  auto at = [&](long long i, int jc) -> double& {
+    if (TILE) return tile[(i - r_begin) * (NB + 1) + jc];
+    return W[((long long)j0 + jc) * m + i];
+  };
+  auto fold8 = [&]() {
+    if (wrp < 4) {
+      red[wrp][0][lane] += red[wrp + 4][0][lane];
+      red[wrp][1][lane] += red[wrp + 4][1][lane];
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+    }
+  };
+  auto sum4 = [&](int s, int t) {
+    return (red[0][s][t] + red[1][s][t]) + (red[2][s][t] + red[3][s][t]);
+  };
+  if (TILE) {
+    for (int e = threadIdx.x; e < rows * nb; e += PT) {
+      const int r = e % rows, jc = e / rows;
+      tile[r * (NB + 1) + jc] =
+          src32 ? static_cast<double>(src32[((long long)j0 + jc) * ldx + r_begin + r])
+                : W[((long long)j0 + jc) * m + r_begin + r];
+    }
+    __syncthreads();
+  }
+  // Gram sums of the first pair over rows > j0 + 1, and pivot rows j0, j0 + 1
+  {
+    const long long c = j0;
+    double acc1 = 0.0, acc2 = 0.0;
+    if (lane < nb) {
+      for (long long i = std::max<long long>(r_begin, c + 2) + wrp; i < r_end; i += 8) {
+        const double y = at(i, lane);
+        acc1 = fma(at(i, 0), y, acc1);
+        if (nb > 1) acc2 = fma(at(i, 1), y, acc2);
+      }
+    }
+    red[wrp][0][lane] = acc1;
+    red[wrp][1][lane] = acc2;
+    for (int q = 0; q < 2; ++q)
+      if (c + q >= r_begin && c + q < r_end && (int)threadIdx.x < nb)
+        rowb[q * NB + threadIdx.x] = at(c + q, threadIdx.x);
+    __syncthreads();
+    fold8();
+    if (wrp == 0) {
+      double* acc = accum;
+      if (lane < nb) atomicAdd(acc + lane, sum4(0, lane));
+      if (lane >= 1 && lane < nb) atomicAdd(acc + NB + lane, sum4(1, lane));
+      __syncwarp();
+      if (lane == 0) grid_arrive(bar);
+    }
+  }
+
+  int done = 0, round = 0;
+  while (done < nb) {
+    const int p = done;                     // first column of this round
+    const int buf = round & 1;
+    const long long c = (long long)j0 + p;  // pivot row of column p
+    const int nrem = nb - p - 1;            // columns right of p
+    const double* acc = accum + (size_t)p * 2 * NB;
+    const double* rb = rowb + (size_t)buf * 2 * NB;
+    const unsigned target = (unsigned)P * (unsigned)(round + 1) + wait_extra;
+    // Scalars of the round, spread over three warps on three SM
+    // sub-partitions (FP64 instructions of one sub-partition do not overlap):
+    //   warp 0: reflector a (lane 0), then the per-column quantities m_t,
+    //           y_t'[c+1], s_t' (all lanes), then n_t;
+    //   warp 1: 1/sigma_a, then reflector b (from m_b, sigma_b, x_b'[c+1]);
+    //   warp 2: 1/sigma_b and the cancellation guard.
+    // Each waits on the grid barrier and loads its inputs itself, so no L2
+    // round trip follows a block barrier.  Barriers: 3 (warp 1 -> 0: 1/sigma_a),
+    // 4 (warp 0 -> 1, 2: rmu_a, 1/w_a), 6 (warp 2 -> 1: 1/sigma_b),
+    // 5 (warps 1, 2 -> 0: reflector b and the decision).
+    if (wrp == 1 || wrp == 2) {
+      int okw = 1;
+      if (lane == 0) okw = grid_wait(bar, target, err, wait_spins) ? 1 : 0;
+      // column a at row c+1, column b at rows c, c+1, and the Gram sums G_aa,
+      // G_ab, G_bb (over rows > c+1)
+      double ra1 = 0.0, g00 = 0.0, rb0 = 0.0, rb1 = 0.0, g01 = 0.0, g11 = 0.0;
+      if (lane == 0 && okw) {
+        ra1 = (c + 1 < m) ? __ldcg(rb + NB) : 0.0;
+        g00 = __ldcg(acc);
+        if (nrem >= 1) {
+          rb0 = __ldcg(rb + 1);
+          rb1 = __ldcg(rb + NB + 1);
+          g01 = __ldcg(acc + 1);
+          g11 = __ldcg(acc + NB + 1);
+        }
+      }
+      if (wrp == 1) {
+        if (lane == 0) {
+          // 1/sigma_a for a pivot x_0 > 0 (sigma_a as warp 0 forms it)
+          const double sg = fma(ra1, ra1, g00);
+          double rs = 0.0;
+          if (okw && (((__double2hiint(sg) & 0x7fffffff) | __double2loint(sg)) != 0))
+            rs = rcp_nr(sg);
+          rsig_s = rs;
+        }
+        __syncwarp();
+        asm volatile("bar.arrive 3, 64;" ::: "memory");
+      }
+      __syncwarp();
+      asm volatile("bar.sync 4, 96;" ::: "memory");        // rmu_a, 1/w_a from warp 0
+      // m_b, sigma_b and x_b'[c+1] exactly as warp 0 forms m_t, y_t'[c+1]
+      double mb = 0.0, sb = 0.0, xb0 = 0.0, rmub = 0.0, iwb = 0.0, xm = 0.0;
+      bool nzb = false, pos = false;
+      if (lane == 0 && nrem >= 1) {
+        const double st1 = fma(ra1, rb1, g01);
+        mb = sc_rmu * fma(st1, sc_inw, rb0);
+        sb = fma(mb, fma(mb, g00, 2.0 * g01), g11);
+        nzb = ((__double2hiint(sb) & 0x7fffffff) | __double2loint(sb)) != 0;
+        if (wrp == 2) {
+          rsigb_s = nzb ? rcp_nr(sb) : 0.0;
+        } else {
+          // reflector b, operation for operation as reflector() forms it
+          xb0 = fma(mb, ra1, rb1);
+          const int xh = __double2hiint(xb0);
+          pos = xh >= 0 && (xh | __double2loint(xb0)) != 0;
+          if (nzb) {
+            const double a = fma(xb0, xb0, sb);
+            rmub = rsqrt_nr(a);
+            const double mm = __dmul_rn(a, rmub);
+            if (pos) xm = __dadd_rn(xb0, mm);
+            else iwb = rcp_nr(__dsub_rn(xb0, mm));
+          }
+        }
+      }
+      if (wrp == 2) {
+        __syncwarp();
+        asm volatile("bar.arrive 6, 64;" ::: "memory");
+        if (lane == 0) {
+          bool safe = false;
+          if (nrem >= 1) {
+            const double Mb = fma(mb * mb, g00, fma(2.0 * fabs(mb), fabs(g01), g11));
+            safe = (sb >= kPairGuard * Mb) && (sb == sb) && (c + 1 < m);
+          }
+          s_k = safe ? 2 : 1;
+        }
+      } else {
+        __syncwarp();
+        asm volatile("bar.sync 6, 64;" ::: "memory");      // 1/sigma_b from warp 2
+        if (lane == 0 && nrem >= 1) {
+          if (nzb && pos) iwb = __dmul_rn(-xm, rsigb_s);
+          sc_rmub = rmub;
+          sc_iwb = iwb;
+          ssum[p + 1][0] = sb;
+          x0_s[p + 1] = xb0;
+        }
+      }
+      __syncwarp();
+      asm volatile("bar.arrive 5, 96;" ::: "memory");
+    } else if (wrp == 0) {
+      int okw = 1;
+      if (lane == 0) okw = grid_wait(bar, target, err, wait_spins) ? 1 : 0;
+      __syncwarp();                                        // orders lane 0's acquire first
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      // lane t: column p + t at rows c, c+1; Gram sums G_{p,p+t}, G_{p+1,p+t}
+      double r0 = 0.0, r1 = 0.0, g0 = 0.0, g1 = 0.0;
+      if (okw && lane <= nrem) {
+        r0 = __ldcg(rb + lane);
+        r1 = (c + 1 < m) ? __ldcg(rb + NB + lane) : 0.0;
+        g0 = __ldcg(acc + lane);
+        g1 = __ldcg(acc + NB + lane);
+      }
+      // column a's sums over rows > c: sigma (lane 0), s_t (lane t)
+      const double ra1 = __shfl_sync(0xffffffffu, r1, 0);
+      const double st = fma(ra1, r1, g0);
+      ssum[p][lane] = st;
+      if (lane == 0) x0_s[p] = r0;
+      double rmu = 0.0, inv_w = 0.0, xm = 0.0;
+      const bool nz = ((__double2hiint(st) & 0x7fffffff) | __double2loint(st)) != 0;
+      const int x0h = __double2hiint(r0);
+      const bool pos = x0h >= 0 && (x0h | __double2loint(r0)) != 0;
+      if (lane == 0 && nz) {
+        const double a = fma(r0, r0, st);
+        rmu = rsqrt_nr(a);
+        const double mm = __dmul_rn(a, rmu);
+        if (pos) xm = __dadd_rn(r0, mm);
+        else inv_w = rcp_nr(__dsub_rn(r0, mm));
+      }
+      __syncwarp();
+      asm volatile("bar.sync 3, 64;" ::: "memory");       // warp 1's 1/sigma_a
+      if (lane == 0 && nz && pos) inv_w = __dmul_rn(-xm, rsig_s);
+      if (lane == 0) {
+        sc_rmu = rmu;
+        sc_inw = inv_w;
+      }
+      __syncwarp();
+      asm volatile("bar.arrive 4, 96;" ::: "memory");
+      rmu = __shfl_sync(0xffffffffu, rmu, 0);
+      inv_w = __shfl_sync(0xffffffffu, inv_w, 0);
+      double ma = 0.0;                                    // m_t (lane t >= 1), 1/w_a (lane 0)
+      if (lane == 0) ma = inv_w;
+      else if (lane <= nrem) ma = rmu * fma(st, inv_w, r0);
+      cfa[lane] = ma;
+      // pivot row c+1 after reflector a and s_t' for lanes t >= 2
+      const double y1 = fma(ma, ra1, r1);
+      const double mb = __shfl_sync(0xffffffffu, ma, 1);
+      const double gaa = __shfl_sync(0xffffffffu, g0, 0);
+      const double gab = __shfl_sync(0xffffffffu, g0, 1);
+      const double sp = fma(ma, fma(mb, gaa, gab), fma(mb, g0, g1));
+      if (lane >= 2) ssum[p + 1][lane - 1] = sp;
+      __syncwarp();
+      asm volatile("bar.sync 5, 96;" ::: "memory");       // reflector b and the decision
+      const int k = (nrem >= 1) ? s_k : 1;
+      double nbc = 0.0;
+      if (k == 2) {
+        const double rmub = sc_rmub, iwb = sc_iwb;
+        if (lane == 1) nbc = iwb;
+        else if (lane >= 2 && lane <= nrem) nbc = rmub * fma(sp, iwb, y1);
+      }
+      cfb[lane] = nbc;
+      if (lane == 0) {
+        s_ok = okw;
+        s_kr = k;
+      }
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    const int k = s_kr;
+    const int nnext = nb - p - k;           // columns left after this round
+    double acc1 = 0.0, acc2 = 0.0;
+    {
+      const double ca = cfa[lane], cb = cfb[lane];
+      const bool active = (lane <= nrem);
+      const bool upda = (lane >= 1 && active);
+      // pivot rows of the next round: c + k, c + k + 1; Gram sums below them
+      const long long q0 = c + k, q1 = c + k + 1;
+      const int la = k, lb = k + 1;          // lanes of the next pair's columns
+      // one row: any row (the pivot rows of this and the next round included)
+      auto row1 = [&](long long i) {
+        const double xa = at(i, p);
+        const double old = upda ? at(i, p + lane) : 0.0;
+        double y = fma(ca, xa, old);        // lane 0: v_a = x_a / w_a
+        if (k == 2 && i > c + 1) {
+          // lane 1: v_b = x_b' / w_b; lanes t >= 2: y_t'' = y_t' + n_t x_b'
+          // in one instruction (cb = 0 beyond nrem: y unchanged)
+          const double xb = __shfl_sync(0xffffffffu, y, 1);
+          if (lane >= 1) y = fma(cb, xb, lane == 1 ? 0.0 : y);
+        }
+        __syncwarp();
+        if (active) at(i, p + lane) = y;
+        if (nnext > 0) {
+          const double ya = __shfl_sync(0xffffffffu, y, la & 31);
+          const double yb = __shfl_sync(0xffffffffu, y, lb & 31);
+          if (i == q0 || i == q1) {
+            if (lane >= k && active)
+              rowb[(size_t)(buf ^ 1) * 2 * NB + (i == q1 ? NB : 0) + (lane - k)] = y;
+          } else if (i > q1) {
+            if (lane >= k && active) acc1 = fma(ya, y, acc1);
+            if (lane >= k + 1 && active) acc2 = fma(yb, y, acc2);
+          }
+        }
+      };
+      long long i = std::max<long long>(r_begin, c + 1) + wrp;
+      for (; i < r_end && i <= q1; i += 8) row1(i);
+      // rows below the next pivots, two at a time (independent chains: a
+      // dependent FP64 operation costs 64 clocks on B300)
+      double acc1b = 0.0, acc2b = 0.0;
+      for (; i + 8 < r_end; i += 16) {
+        const double xa1 = at(i, p), xa2 = at(i + 8, p);
+        const double o1 = upda ? at(i, p + lane) : 0.0;
+        const double o2 = upda ? at(i + 8, p + lane) : 0.0;
+        double y1 = fma(ca, xa1, o1), y2 = fma(ca, xa2, o2);
+        if (k == 2) {
+          const double xb1 = __shfl_sync(0xffffffffu, y1, 1);
+          const double xb2 = __shfl_sync(0xffffffffu, y2, 1);
+          if (lane >= 1) {
+            y1 = fma(cb, xb1, lane == 1 ? 0.0 : y1);
+            y2 = fma(cb, xb2, lane == 1 ? 0.0 : y2);
+          }
+        }
+        __syncwarp();
+        if (active) {
+          at(i, p + lane) = y1;
+          at(i + 8, p + lane) = y2;
+        }
+        if (nnext > 0) {
+          const double ya1 = __shfl_sync(0xffffffffu, y1, la & 31);
+          const double ya2 = __shfl_sync(0xffffffffu, y2, la & 31);
+          const double yb1 = __shfl_sync(0xffffffffu, y1, lb & 31);
+          const double yb2 = __shfl_sync(0xffffffffu, y2, lb & 31);
+          if (lane >= k && active) {
+            acc1 = fma(ya1, y1, acc1);
+            acc1b = fma(ya2, y2, acc1b);
+          }
+          if (lane >= k + 1 && active) {
+            acc2 = fma(yb1, y1, acc2);
+            acc2b = fma(yb2, y2, acc2b);
+          }
+        }
+      }
+      for (; i < r_end; i += 8) row1(i);
+      acc1 += acc1b;
+      acc2 += acc2b;
+    }
+    done = p + k;
+    ++round;
+    if (done >= nb) break;
+    red[wrp][0][lane] = acc1;
+    red[wrp][1][lane] = acc2;
+    __syncthreads();
+    fold8();
+    // warp 0 adds slot row 0, warp 1 slot row 1 (two sub-partitions); warp 0
+    // arrives once warp 1's additions are issued (the barrier orders them
+    // before the release)
+    if (wrp == 0 || wrp == 1) {
+      double* an = accum + (size_t)done * 2 * NB;
+      const int t = lane + k;                // red lane of the next round's column done + lane
+      if (wrp == 0) {
+        if (lane < nnext) atomicAdd(an + lane, sum4(0, t));
+        __syncwarp();
+        asm volatile("bar.sync 7, 64;" ::: "memory");
+        if (lane == 0) grid_arrive(bar);
+      } else {
+        if (lane >= 1 && lane < nnext) atomicAdd(an + NB + lane, sum4(1, t));
+        __syncwarp();
+        asm volatile("bar.arrive 7, 64;" ::: "memory");
+      }
+    }
+  }
+  __syncthreads();
+  // tau and the pivot rows, as in the single-column kernel
+  const bool has_pivots = r_begin < (long long)j0 + done;
+  if ((b == 0 || has_pivots) && wrp == 0 && lane < done) {
+    const long long c = (long long)j0 + lane;
+    const double sigma = ssum[lane][0];
+    const double x0 = x0_s[lane];
+    double tau = 0.0, iw = 0.0, mu = fabs(x0);
+    if (sigma != 0.0) {
+      double rmu;
+      reflector(x0, sigma, &rmu, &mu, &iw, &tau);
+    } else {
+      tau = (x0 < 0.0) ? 2.0 : 0.0;
+    }
+    if (!(tau == tau) || isinf(tau) || !(mu == mu) || isinf(mu)) atomicOr(err, ERRF_NUMERIC);
+    tau_s[lane] = tau;
+    iw_s[lane] = iw;
+    if (c >= r_begin && c < r_end) at(c, lane) = mu;
+  }
+  __syncthreads();
+  if (has_pivots) {
+    for (int e = threadIdx.x; e < done * NB; e += PT) {
+      const int jj = e / NB, t = e % NB;
+      const long long c = (long long)j0 + jj;
+      if (t >= 1 && jj + t < nb && c >= r_begin && c < r_end) {
+        const double y0 = at(c, jj + t);
+        at(c, jj + t) = y0 - tau_s[jj] * fma(ssum[jj][t], iw_s[jj], y0);
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < rows * nb; e += PT) {
+    const int r = e % rows, jc = e / rows;
+    const long long i = r_begin + r, c = (long long)j0 + jc;
+    const double x = at(i, jc);
+    if (TILE) W[c * m + i] = x;
+    const double v = (i < c) ? 0.0 : (i == c ? 1.0 : x);
+    V[c * m + i] = v;
+    if (X32) {
+      const float vf = static_cast<float>(v);
+      X32[c * ldx + i] = vf;
+      V32[c * ldx + i] = vf;
+      Vt32[i * ldv + c] = vf;
+    }
+  }
+  if (b == 0 && threadIdx.x < (unsigned)nb) tau_out[threadIdx.x] = tau_s[threadIdx.x];
+  if (threadIdx.x == 0) grid_exit(bar, (unsigned)P);
+}
+
 // T (upper triangular, nb x nb, row stride NB): T_jj = tau_j,
 // T[0:j, j] = -tau_j T[0:j, 0:j] G[0:j, j], with G = V^T V of the panel.
 __global__ void qr_tfactor_kernel(const double* __restrict__ G, const double* __restrict__ tau,
@@ -394,7 +819,7 @@ cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t 
   const int mr = m - j0;
   int P = qr_panel_grid(mr);
   double* W = w.W; double* V = w.V; double* part = w.part;
-  double* Gp = w.part + 2 * (size_t)PMAX * NB + 2 * NB;
+  double* Gp = w.part + 2 * (size_t)PMAX * NB + 4 * NB;   // after the pivot rows [2][2][NB]
   double* taup = Gp + NB * NB;
   GridBar* bar = w.bar; int* err = w.err;
   int m_ = m, j0_ = j0, nb_ = nbj;
@@ -425,22 +850,24 @@ cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t 
     if (w.hook) w.hook(w.hook_user, 0);
     return cudaErrorInvalidValue;   // an FP32 source needs the tiled path
   }
+  // two columns per grid-wide exchange where the accumulator rows fit (two
+  // rows of NB per round start: j0 + nb <= PMAX); one column otherwise
+  const bool pair = w.pair_rounds && j0 + nbj <= PMAX;
+  const void* kt = pair ? (const void*)qr_panel2_kernel<true> : (const void*)qr_panel_kernel<true>;
+  const void* kg = pair ? (const void*)qr_panel2_kernel<false> : (const void*)qr_panel_kernel<false>;
   if (tile <= kPanelTileMax) {
     // the shared-memory limit is a per-device attribute of the kernel
-    e = device_once((const void*)qr_panel_kernel<true>, [] {
-      return cudaFuncSetAttribute(qr_panel_kernel<true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = device_once(kt, [kt] {
+      return cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kPanelTileMax);
     });
     if (e != cudaSuccess) {
       if (w.hook) w.hook(w.hook_user, 0);
       return e;
     }
-    e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<true>, dim3(P),
-                                    dim3(PT), args, tile, s);
+    e = cudaLaunchCooperativeKernel(kt, dim3(P), dim3(PT), args, tile, s);
   } else {
-    e = cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<false>, dim3(P),
-                                    dim3(PT), args, 0, s);
+    e = cudaLaunchCooperativeKernel(kg, dim3(P), dim3(PT), args, 0, s);
   }
   if (w.hook) w.hook(w.hook_user, 0);
   if (e != cudaSuccess) return e;
@@ -502,6 +929,7 @@ QrWork qr_carve(void* base, int m, int n) {
   w.err = reinterpret_cast<int*>(p);
   w.wait_spins = kGridWaitSpins;
   w.wait_extra = 0;
+  w.pair_rounds = false;
   return w;
 }
 

@@ -325,10 +325,14 @@ cudaError_t householder_qr_split(int m, int n, const double* M, double* R, const
     g.max_ksplit = kQrMaxKsplit;
     return gemm_tc(g, s);
   };
+  // panels with two columns per grid-wide exchange (FP32-class accuracy is
+  // all the rest of this path keeps)
+  QrWork wp = w;
+  wp.pair_rounds = true;
   for (int p = 0; p < npan; ++p) {
     const int j0 = p * NB, nbj = std::min(NB, n - j0), mr = m - j0, n2 = n - j0 - nbj;
     double *G, *tau;
-    if ((e = qr_panel_step(m, j0, nbj, w, s, &G, &tau, X32, mp, Vt32, p == 0 ? nullptr : X32, V32,
+    if ((e = qr_panel_step(m, j0, nbj, wp, s, &G, &tau, X32, mp, Vt32, p == 0 ? nullptr : X32, V32,
                            ldv)) != cudaSuccess)
       return e;
     const float* Vrows = X32 + (long long)j0 * mp + j0;

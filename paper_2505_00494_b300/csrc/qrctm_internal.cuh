@@ -268,6 +268,14 @@ struct QrWork {
   // the timeout test asks for); qr_carve sets the defaults
   long long wait_spins;
   unsigned int wait_extra;
+  // panel rounds: two columns per grid-wide exchange (guarded) when true,
+  // one column per exchange when false.  The paired round forms the second
+  // reflector's norm from Gram sums, whose rounding leaves its Householder
+  // transform orthogonal only to ~1e-13 on ill-conditioned panels (one
+  // column per exchange: ~1e-15); qr_carve chooses one column (the FP64
+  // path), the split-precision QR, whose trailing update and Q are FP32-class,
+  // two.
+  bool pair_rounds;
 };
 constexpr long long kSplitKElems = 1ll << 21;   // 16 MB of split-K partials
 size_t qr_work_bytes(int m, int n);

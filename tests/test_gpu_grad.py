@@ -44,15 +44,16 @@ def make_ctx(q, A, C, T, chi=8):
     return ctx
 
 
+@pytest.mark.parametrize("rotation", [True, False])
 @pytest.mark.parametrize("J2", [0.0, 0.5])
-def test_unrolled_gradient_matches_complex_step(q, point, J2):
+def test_unrolled_gradient_matches_complex_step(q, point, J2, rotation):
     A, C, T = point
     ctx = make_ctx(q, A, C, T)
-    E, g = ctx.energy_grad(1.0, J2, mode="unroll", k_unroll=6)
+    E, g = ctx.energy_grad(1.0, J2, mode="unroll", k_unroll=6, rotation=rotation)
     g = g.cpu().numpy()
     for seed in (1001, 1002):
         v = o.normalized_input(qi.raw_direction(2, 2, seed))
-        ref = o.directional_derivative_unrolled(A, v, C, T, 6, 1.0, J2)
+        ref = o.directional_derivative_unrolled(A, v, C, T, 6, 1.0, J2, rotate=rotation)
         got = float(np.sum(g * v))
         assert abs(got - ref) < 1e-9 * max(1.0, abs(ref)), (got, ref)
 

@@ -149,3 +149,53 @@ def test_not_symmetric_rejected(q):
     with pytest.raises(q.QRCTMError) as ei:
         ctx.init_env(cuda(X / np.linalg.norm(X)))
     assert ei.value.status == "NOT_SYMMETRIC"
+
+
+def test_host_buffer_entry_points(q):
+    """qrctm_init_env_host / qrctm_get_env_host copy inside the library call;
+    one step from host inputs equals the oracle's step (1e-11) and the
+    device-pointer path bit for bit."""
+    import torch
+    A = o.normalized_input(qi.raw_tensor(2, 3, 3))
+    C, T = o.warmup(A, 27)
+    Cn, Tn = o.qr_step(C, T, A)
+    h = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64).pin_memory()
+    ctx = q.QRCTM(2, 3, 27)
+    ctx.init_env_host(h(A), h(C), h(T))
+    ctx.step(1, want_delta=True)
+    oC = torch.empty((27, 27), dtype=torch.float64).pin_memory()
+    oT = torch.empty((27, 9, 27), dtype=torch.float64).pin_memory()
+    s = ctx.get_env_host(oC, oT, spectrum=True)
+    assert np.abs(oC.numpy() - Cn).max() < 1e-11
+    assert np.abs(oT.numpy() - Tn).max() < 1e-11
+    assert np.abs(s - o.corner_spectrum(Cn)).max() < 1e-12
+    ref = q.QRCTM(2, 3, 27)
+    ref.init_env(cuda(A), cuda(C), cuda(T))
+    ref.step(1, want_delta=True)
+    Cg, Tg, _ = ref.get_env(spectrum=False)
+    assert np.array_equal(oC.numpy(), host(Cg)) and np.array_equal(oT.numpy(), host(Tg))
+    # the bulk boundary from a host tensor alone (no C0, T0)
+    ctx.init_env_host(h(A))
+    ctx.step(2, want_delta=False)
+    ctx.close()
+    ref.close()
+
+
+def test_energy_without_sublattice_rotation(q):
+    """qrctm_model.sublattice_rotation = 0 takes the plain bond on NN pairs:
+    the oracle's energy with rotate=False from the same environment (1e-12),
+    and the product-state closed form E = J1/2 + J2/2."""
+    A = o.normalized_input(qi.raw_tensor(2, 3, 5))
+    C, T = o.warmup(A, 18)
+    ctx = q.QRCTM(2, 3, 18, with_nnn=True)
+    ctx.init_env(cuda(A), cuda(C), cuda(T))
+    for J2 in (0.0, 0.5):
+        Eo = o.energy(C, T, A, 1.0, J2, rotate=False)
+        assert abs(ctx.energy(1.0, J2, rotation=False) - Eo) < 1e-12 * max(1.0, abs(Eo))
+    v = np.array([0.6, -0.8])
+    P = np.zeros((2, 2, 2, 2, 2))
+    P[:, 0, 0, 0, 0] = v
+    pc = q.QRCTM(2, 2, 8, with_nnn=True)
+    pc.init_env(cuda(P))
+    pc.step(4, want_delta=False)
+    assert abs(pc.energy(1.0, 0.5, rotation=False) - 0.75) < 1e-12

@@ -76,3 +76,27 @@ def test_split_converged_energy(q, D, chi, seed, decay):
     Eg = ctx.energy(1.0, 0.5)
     print("split", D, chi, "iters", it, "delta", dlt, "dE", Eg - Eo)
     assert abs(Eg - Eo) < 1e-7
+
+
+@pytest.mark.parametrize("D,chi,seed,decay", [(3, 27, 1, True), (6, 144, 0, True)])
+def test_split_j2_energy_matches_fp64_from_same_env(q, D, chi, seed, decay):
+    """A split-precision context evaluates the one (chi D^2)^3 product of the
+    2x2 patch (Ct_open Ct) on the TF32x3 tensor cores; every other
+    contraction and the traces are FP64.  From the same environment its J1-J2
+    energy must match the FP64 context's (itself the oracle's to 1e-12,
+    test_gpu_parity) to 1e-7 per site, the split-path target; the J2 = 0
+    energy, which has no such product, to 1e-13."""
+    A = o.normalized_input(qi.raw_tensor(2, D, seed, decay))
+    s = q.QRCTM(2, D, chi, precision="split", with_nnn=True, check_every=5)
+    s.init_env(cuda(A))
+    s.run_to_convergence(tol=1e-9, max_iter=300)
+    C, T, _ = s.get_env(spectrum=False)
+    f = q.QRCTM(2, D, chi, with_nnn=True)
+    f.init_env(cuda(A), C, T)
+    s.init_env(cuda(A), C, T)
+    e_f, e_s = f.energy(1.0, 0.5), s.energy(1.0, 0.5)
+    print(f"D{D} chi{chi}: E(J2=0.5) split - fp64 = {e_s - e_f:.3e}")
+    assert abs(e_s - e_f) < 1e-7
+    assert abs(s.energy(1.0, 0.0) - f.energy(1.0, 0.0)) < 1e-13
+    s.close()
+    f.close()

@@ -36,6 +36,32 @@ def test_product_state_D1_energy_exact(method, seed):
         assert abs(E - (g["value_J1"] + J2 * g["value_J2"])) < 1e-14
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_product_state_energy_without_rotation(seed):
+    # plain NN bond: <h> = (<X>^2 + <Z>^2)/4 = 1/4 for a real unit v
+    v = np.random.default_rng(seed).standard_normal(2)
+    A = (v / np.linalg.norm(v)).reshape(2, 1, 1, 1, 1)
+    C, T, _ = o.ctmrg(A, 4, "qr", tol=1e-14, max_iter=5)
+    g = GOLD["product_state_energy_unrotated"]
+    for J2 in (0.0, 0.5):
+        E = o.energy(C, T, A, 1.0, J2, rotate=False)
+        assert abs(E - (g["value_J1"] + J2 * g["value_J2"])) < 1e-14
+    # a random D = 2 state: the two NN bonds differ by the rotation alone,
+    # <h~> - <h> = -(<XX> + <ZZ>)/2 on the same two-site density matrix
+    A2 = o.normalized_input(qi.raw_tensor(2, 2, seed))
+    C2, T2 = o.warmup(A2, 8)
+    rho = o.rdm_nn(C2, T2, A2)
+    d = 2
+    R = np.transpose(rho, (0, 2, 1, 3)).reshape(d * d, d * d)
+    R = R / np.trace(R)
+    X = np.array([[0.0, 1.0], [1.0, 0.0]])
+    Z = np.diag([1.0, -1.0])
+    diff = -(np.trace(R @ np.kron(X, X)) + np.trace(R @ np.kron(Z, Z))) / 2
+    E_r = o.energy(C2, T2, A2, 1.0, 0.0)
+    E_p = o.energy(C2, T2, A2, 1.0, 0.0, rotate=False)
+    assert abs((E_r - E_p) / 2 - diff) < 1e-13
+
+
 @pytest.mark.parametrize("method", ["qr", "eigen"])
 def test_product_state_embedded_D2(method):
     # rank-deficient reduced corner (R_jj = 0), exact energies survive
