@@ -706,7 +706,9 @@ def main():
     network = args.workload in qi.NETWORK_WORKLOADS
     if args.oracle_sample_only:
         times, _ = oracle_sample(qi.WORKLOADS[args.workload], args.cpu_sample)
-        print(json.dumps({"value": len(times) / sum(times), "cores": cpu_threads()}), flush=True)
+        # the BLAS pool size set by the parent (threadpoolctl may be absent)
+        cores = int(os.environ.get("OPENBLAS_NUM_THREADS") or cpu_threads())
+        print(json.dumps({"value": len(times) / sum(times), "cores": cores}), flush=True)
         return
     w = qi.NETWORK_WORKLOADS[args.workload] if network else qi.WORKLOADS[args.workload]
     if network:
