@@ -802,8 +802,11 @@ def main():
                             fp64_note)}
     if args.precision == "split":
         m = chi * D * D
-        if D <= 6:
-            absorb = ("absorb_d6_k" if D == 6 else "absorb_fused_k", fl["absorb"], "alu",
+        if D == 6:
+            # both layers on the tensor cores in one kernel
+            absorb = ("absorb_tc_kernel", fl["absorb"], "tensor", tf32_peak, tf32_note)
+        elif D < 6:
+            absorb = ("absorb_fused_k", fl["absorb"], "alu",
                       fp32_simt_peak(), "fp32 FMA nominal: 148 SMs x 128 FMA/clk x 2 x 2.032 GHz")
         else:
             # two tensor-core contractions of equal flops (ket: N = d D^2, K = D^2;

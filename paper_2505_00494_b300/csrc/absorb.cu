@@ -17,7 +17,8 @@
 //   Ak  [(s,d,r)] x (u,l), row stride D2p          (A[s,u,l,d,r])
 //   Ab  [(d,r)] x (s,u,l), row stride dD2p          (A[s,u,l,d,r])
 //   X2  [(mu,j_k,j_b)] x (b,d_k,d_b), row stride mp
-// Instantiated for d = 2 and D = 2, 4, 6, 8 (D^2 % 4 == 0, d D^2 % 8 == 0).
+// Instantiated for d = 2 and D = 2, 4 (D = 6 runs on the tensor cores,
+// absorb_tc.cu).
 #include "ctx.cuh"
 
 #include <algorithm>
@@ -28,15 +29,6 @@ namespace {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-// c <- a * b + c on both lanes of a pair (packed FP32 FMA, one instruction,
-// each lane rounded like fmaf)
-__device__ __forceinline__ void ffma2(float2& c, float2 a, float2 b) {
-  unsigned long long cc = *reinterpret_cast<unsigned long long*>(&c);
-  const unsigned long long aa = *reinterpret_cast<const unsigned long long*>(&a);
-  const unsigned long long bb = *reinterpret_cast<const unsigned long long*>(&b);
-  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(cc) : "l"(aa), "l"(bb));
-  c = *reinterpret_cast<float2*>(&cc);
 }
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
@@ -239,177 +231,6 @@ __global__ void __launch_bounds__(AbsorbShape<D, d, NG>::threads)
   }
 }
 
-// D = 6 (d = 2) with larger register tiles, because the generic 4 x 8 / 4 x 4
-// tiles are bound by shared-memory bandwidth at this shape (12 LDS.128 per
-// 128 FMAs): 8 slices per batch, 36 threads per slice in both passes.
-//   ket: 9 rows x 8 columns per thread, the columns c0..c0+3 (s = 0) and
-//        36 + c0..36 + c0 + 3 (s = 1), c0 = 4 (t mod 9): the 8 threads of an
-//        access phase read distinct banks of Ak, and Ak is reused over 9 rows;
-//   bra: 6 x 6 per thread from 8-byte-aligned pairs of Z and Ab.
-constexpr int kD6NG = 8, kD6Threads = 36 * kD6NG;
-constexpr size_t kD6Smem =
-    sizeof(float) * (2 * (size_t)kD6NG * 36 * 36 + (size_t)kD6NG * 36 * 72 + 2 * 36 * 72);
-
-__global__ void __launch_bounds__(kD6Threads, 1)
-    absorb_d6_k(const float* __restrict__ X1, const float* __restrict__ Ak,
-                const float* __restrict__ Ab, float* __restrict__ X2, int ch, long long Akp,
-                long long Abp, long long mp, long long ngroups, int* err) {
-  constexpr int D = 6, D2 = 36, dD2 = 72, NG = kD6NG, nt = kD6Threads;
-  extern __shared__ __align__(128) float sm[];
-  __shared__ __align__(8) unsigned long long mbar[2];
-  __shared__ int s_ok;
-  __shared__ long long xbase[NG];   // X2 offset of slice g of the batch: (mu D2) mp + b D2
-  const int tid = threadIdx.x;
-  constexpr size_t xbuf = (size_t)NG * D2 * D2;
-  float* Xb0 = sm;
-  float* Xb1 = Xb0 + xbuf;
-  float* Zs = Xb1 + xbuf;                           // [NG][D2][dD2]
-  float* AkT = Zs + (size_t)NG * D2 * dD2;          // [D2][dD2]
-  float* AbT = AkT + (size_t)D2 * dD2;              // [dD2][D2]
-  const uint32_t bar0 = smem_u32(&mbar[0]), bar1 = smem_u32(&mbar[1]);
-  const long long stride = (long long)gridDim.x * NG;
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    const long long g0 = (long long)blockIdx.x * NG;
-    if (g0 < ngroups)
-      issue_slices(X1, Xb0, bar0, g0, (int)std::min<long long>(NG, ngroups - g0), D2, D2);
-  }
-  for (int e = tid; e < D2 * dD2; e += nt) {
-    const int c = e / D2, k = e % D2;
-    AkT[k * dD2 + c] = Ak[c * Akp + k];
-  }
-  for (int e = tid; e < D2 * dD2; e += nt) {
-    const int c = e / dD2, k = e % dD2;
-    AbT[k * D2 + c] = Ab[c * Abp + k];
-  }
-  const int g = tid / 36, rem = tid % 36;
-  const int rb1 = (rem / 9) * 9, c0 = (rem % 9) * 4;          // ket tile
-  const int rb2 = (rem / 6) * 6, cb2 = (rem % 6) * 6;         // bra tile
-  int it = 0;
-  bool next_issued = false;
-  if (tid == 0) s_ok = 1;
-  for (long long g0 = (long long)blockIdx.x * NG; g0 < ngroups; g0 += stride, ++it) {
-    const int ng = (int)std::min<long long>(NG, ngroups - g0);
-    float* Xb = (it & 1) ? Xb1 : Xb0;
-    const uint32_t bar = (it & 1) ? bar1 : bar0;
-    __syncthreads();   // the other buffer's previous batch is fully written out
-    if (tid < NG) {   // one 64-bit division per slice, not per element
-      const long long gg = g0 + tid, mu = gg / ch;
-      xbase[tid] = mu * D2 * mp + (gg - mu * ch) * D2;
-    }
-    const long long gn = g0 + stride;
-    next_issued = gn < ngroups;
-    if (tid == 0 && next_issued)
-      issue_slices(X1, (it & 1) ? Xb0 : Xb1, (it & 1) ? bar0 : bar1, gn,
-                   (int)std::min<long long>(NG, ngroups - gn), D2, D2);
-    if (!mbar_wait_bounded(bar, (uint32_t)((it >> 1) & 1))) {
-      atomicOr(err, ERRF_TIMEOUT);
-      s_ok = 0;
-    }
-    __syncthreads();
-    if (!s_ok) break;
-    // ket: Zs[g][r][c] = sum_k X[g][r][k] AkT[k][c]
-    if (g < ng) {
-      float2 acc[9][4];   // column pairs (c0, c0+1), (c0+2, c0+3), then the s = 1 half
-#pragma unroll
-      for (int i = 0; i < 9; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
-      const float* xa = Xb + ((size_t)g * D2 + rb1) * D2;
-#pragma unroll 1
-      for (int k = 0; k < D2; k += 4) {
-        float av[9][4];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          const float4 a = *reinterpret_cast<const float4*>(xa + i * D2 + k);
-          av[i][0] = a.x; av[i][1] = a.y; av[i][2] = a.z; av[i][3] = a.w;
-        }
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const float4 b0 = *reinterpret_cast<const float4*>(AkT + (k + kk) * dD2 + c0);
-          const float4 b1 = *reinterpret_cast<const float4*>(AkT + (k + kk) * dD2 + D2 + c0);
-          const float2 bp[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w),
-                                make_float2(b1.x, b1.y), make_float2(b1.z, b1.w)};
-#pragma unroll
-          for (int i = 0; i < 9; ++i) {
-            const float2 a2 = make_float2(av[i][kk], av[i][kk]);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) ffma2(acc[i][j], a2, bp[j]);
-          }
-        }
-      }
-      float* zo = Zs + ((size_t)g * D2 + rb1) * dD2 + c0;
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        *reinterpret_cast<float4*>(zo + i * dD2) =
-            make_float4(acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y);
-        *reinterpret_cast<float4*>(zo + i * dD2 + D2) =
-            make_float4(acc[i][2].x, acc[i][2].y, acc[i][3].x, acc[i][3].y);
-      }
-    }
-    __syncthreads();
-    // bra: out[r2][c2] = sum_{s,q} Zs[g][q][s*D2 + r2] AbT[s*D2 + q][c2], staged as
-    // Xb[g][(j_k,j_b)][(d_k,d_b)]  (r2 = d_k*D + j_k, c2 = d_b*D + j_b)
-    if (g < ng) {
-      float2 acc[6][3];   // column pairs (cb2, cb2+1), (cb2+2, cb2+3), (cb2+4, cb2+5)
-#pragma unroll
-      for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) acc[i][j] = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        const float* za = Zs + (size_t)g * D2 * dD2 + s * D2 + rb2;
-        const float* ba = AbT + (size_t)s * D2 * D2 + cb2;
-#pragma unroll 2
-        for (int q = 0; q < D2; ++q) {
-          float av[6];
-          float2 bp[3];
-#pragma unroll
-          for (int u = 0; u < 3; ++u) {
-            const float2 a = *reinterpret_cast<const float2*>(za + q * dD2 + 2 * u);
-            bp[u] = *reinterpret_cast<const float2*>(ba + q * D2 + 2 * u);
-            av[2 * u] = a.x; av[2 * u + 1] = a.y;
-          }
-#pragma unroll
-          for (int i = 0; i < 6; ++i) {
-            const float2 a2 = make_float2(av[i], av[i]);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) ffma2(acc[i][j], a2, bp[j]);
-          }
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < 6; ++i) {
-        const int r2 = rb2 + i, dk = r2 / D, jk = r2 % D;
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-          const int c2 = cb2 + j, db = c2 / D, jb = c2 % D;
-          Xb[((size_t)g * D2 + jk * D + jb) * D2 + dk * D + db] =
-              (j & 1) ? acc[i][j >> 1].y : acc[i][j >> 1].x;
-        }
-      }
-    }
-    __syncthreads();
-    // write out: consecutive slices of one mu are consecutive b, contiguous in X2
-    // (16-byte pieces: mp, D2 and every slice offset are multiples of 4 floats)
-    for (int e = tid; e < NG * D2 * (D2 / 4); e += nt) {
-      const int dd = (e % (D2 / 4)) * 4, gg_ = (e / (D2 / 4)) % NG, jj = e / ((D2 / 4) * NG);
-      if (gg_ >= ng) continue;
-      *reinterpret_cast<float4*>(X2 + xbase[gg_] + (long long)jj * mp + dd) =
-          *reinterpret_cast<const float4*>(Xb + ((size_t)gg_ * D2 + jj) * D2 + dd);
-    }
-  }
-  // after an abandoned wait, let the copies still in flight land (bounded)
-  // before the CTA's shared memory is released
-  if (!s_ok && tid == 0) {
-    mbar_wait_bounded((it & 1) ? bar1 : bar0, (uint32_t)((it >> 1) & 1));
-    if (next_issued)
-      mbar_wait_bounded(((it + 1) & 1) ? bar1 : bar0, (uint32_t)(((it + 1) >> 1) & 1));
-  }
-}
-
 using AbsorbKernel = void (*)(const float*, const float*, const float*, float*, int, long long,
                               long long, long long, long long, int*);
 
@@ -419,8 +240,8 @@ struct AbsorbVariant {
   size_t smem;
 };
 
-// Instantiated shapes (d = 2, D = 2, 4, 6, 8); other shapes take the
-// two-contraction tensor-core path.
+// Instantiated shapes (d = 2, D = 2, 4); D = 6 runs in absorb_tc.cu, other
+// shapes take the two-contraction tensor-core path.
 template <int D, int NG>
 AbsorbVariant absorb_variant() {
   using S = AbsorbShape<D, 2, NG>;
@@ -432,7 +253,6 @@ bool absorb_lookup(int d, int D, AbsorbVariant* v) {
   switch (D) {
     case 2: *v = absorb_variant<2, 256>(); return true;    // 256 threads
     case 4: *v = absorb_variant<4, 16>(); return true;     // 256 threads
-    case 6: *v = AbsorbVariant{absorb_d6_k, kD6NG, kD6Threads, kD6Smem}; return true;
     case 8: *v = absorb_variant<8, 2>(); return true;      // 512 threads
     default: return false;
   }

@@ -139,6 +139,10 @@ cudaError_t eigen_step(qrctm_ctx* c, int ci, int co);
 size_t eigen_work_doubles(long long m);
 void eigen_release(qrctm_ctx* c);
 // fused ket + bra absorption (FP32), see absorb.cu
+// tensor-core absorption of both layers (d = 2, D = 6; absorb_tc.cu)
+bool absorb_tc_ok(int d, int D);
+cudaError_t absorb_tc(const float* X1, const float* Ak, const float* Ab, float* X2, int ch,
+                      long long D2p, long long dD2p, long long mp, int* err, cudaStream_t s);
 bool absorb_fused_ok(int d, int D);
 cudaError_t absorb_fused(const float* X1, const float* Ak, const float* Ab, float* X2, int ch,
                          int D, int d, long long D2p, long long dD2p, long long mp, int* err,

@@ -8,8 +8,9 @@
 //   X1[m,b,ub,kb,uk,kk] = sum_a Q[(a,u),m] T[b,k,a]        (FP32)
 //   Z [m,b,dk,jk,s,ub,kb] = sum_{uk,kk} X1 A[s,uk,kk,dk,jk]  (ket layer, FP32)
 //   X2[m,jk,jb,b,dk,db]  = sum_{s,ub,kb} Z A[s,ub,kb,db,jb]  (bra layer, FP32)
-//     (for even D both layers run in one fused FP32 kernel with Z on chip;
-//      otherwise as two tensor-core contractions through Z in HBM)
+//     (at D = 6 both layers run in one tensor-core kernel with Z on chip;
+//      for other even D in one fused FP32 kernel; otherwise as two
+//      tensor-core contractions through Z in HBM)
 //   T'[m,j,n]    = sum_{b,d} X2[m,j,(b,d)] Q[(b,d),n]      (FP64 out)
 //   Y2[n,g,j]    = sum_m T's[n,j,m] R[m,g]                 (FP32, batched over j)
 //   C'[n,p]      = sum_{(g,j)} Y2[n,(g,j)] Q[(g,j),p]      (FP64 out)
@@ -131,7 +132,12 @@ cudaError_t qr_step_split(qrctm_ctx* c) {
   }
   {
     PhaseScope ps(c, QRCTM_PH_ABSORB);
-    if (absorb_fused_ok(d, D)) {
+    if (absorb_tc_ok(d, D)) {
+      // both layers on the tensor cores in one kernel, Z kept on chip
+      if ((e = absorb_tc(X1, c->Aket32, c->Abra32, X2, ch, D2p, dD2p, mp, c->err, st)) !=
+          cudaSuccess)
+        return e;
+    } else if (absorb_fused_ok(d, D)) {
       // ket and bra in one pass, Z kept on chip
       if ((e = absorb_fused(X1, c->Aket32, c->Abra32, X2, ch, D, d, D2p, dD2p, mp, c->err, st)) !=
           cudaSuccess)

@@ -154,7 +154,8 @@ def test_not_symmetric_rejected(q):
 def test_host_buffer_entry_points(q):
     """qrctm_init_env_host / qrctm_get_env_host copy inside the library call;
     one step from host inputs equals the oracle's step (1e-11) and the
-    device-pointer path bit for bit."""
+    device-pointer path to 1e-14 (not bit for bit: the QR panel adds its
+    cross-CTA partial sums with atomics in no fixed order)."""
     import torch
     A = o.normalized_input(qi.raw_tensor(2, 3, 3))
     C, T = o.warmup(A, 27)
@@ -173,7 +174,8 @@ def test_host_buffer_entry_points(q):
     ref.init_env(cuda(A), cuda(C), cuda(T))
     ref.step(1, want_delta=True)
     Cg, Tg, _ = ref.get_env(spectrum=False)
-    assert np.array_equal(oC.numpy(), host(Cg)) and np.array_equal(oT.numpy(), host(Tg))
+    assert np.abs(oC.numpy() - host(Cg)).max() < 1e-14
+    assert np.abs(oT.numpy() - host(Tg)).max() < 1e-14
     # the bulk boundary from a host tensor alone (no C0, T0)
     ctx.init_env_host(h(A))
     ctx.step(2, want_delta=False)
