@@ -20,6 +20,7 @@
 // Instantiated for d = 2 and D = 2, 4 (D = 6 runs on the tensor cores,
 // absorb_tc.cu).
 #include "ctx.cuh"
+#include "tc_ptx.cuh"
 
 #include <algorithm>
 
@@ -27,25 +28,7 @@ namespace qrctm {
 
 namespace {
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait on an mbarrier phase
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  for (uint32_t i = 0; i < (1u << 22); ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
+using namespace ptx;
 
 // Slices X1[g0 .. g0+ng) (contiguous, ng*D2*D2p floats) into shared memory
 // by one bulk asynchronous copy completing on `bar`.
@@ -53,13 +36,8 @@ __device__ __forceinline__ void issue_slices(const float* X1, float* dst, uint32
                                              long long g0, int ng, int D2, long long D2p) {
   const uint32_t bytes = (uint32_t)((size_t)ng * D2 * D2p * sizeof(float));
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_u32(dst)),
-      "l"(X1 + g0 * D2 * D2p), "r"(bytes), "r"(bar)
-      : "memory");
+  mbar_arrive_expect_tx(bar, bytes);
+  bulk_load(smem_u32(dst), X1 + g0 * D2 * D2p, bytes, bar);
 }
 
 // One persistent CTA loops over batches of NG slices; the next batch is
@@ -98,8 +76,8 @@ __global__ void __launch_bounds__(AbsorbShape<D, d, NG>::threads)
   const uint32_t bar0 = smem_u32(&mbar[0]), bar1 = smem_u32(&mbar[1]);
   const long long stride = (long long)gridDim.x * NG;
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1) : "memory");
+    mbar_init(bar0, 1);
+    mbar_init(bar1, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     const long long g0 = (long long)blockIdx.x * NG;
     if (g0 < ngroups)

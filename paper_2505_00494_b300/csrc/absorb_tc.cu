@@ -33,6 +33,7 @@
 // hide latencies; thread 0 issues the MMAs.  Every mbarrier wait is bounded; a wait that runs out
 // raises ERRF_TIMEOUT and the CTA unwinds, freeing tensor memory.
 #include "ctx.cuh"
+#include "tc_ptx.cuh"
 
 #include <algorithm>
 
@@ -70,103 +71,7 @@ constexpr uint32_t kD1Main = 0, kD1Corr = 96, kD2Main = 192, kD2Corr = 256;
 constexpr uint32_t kAHi = 320, kALo = 384;     // X1 rows, K padded to 64
 constexpr uint32_t kTmemCols = 512;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// byte offset of element (row r, K index k) in a K-major SW128 operand whose
-// 32-wide K blocks are `block` bytes apart
-__device__ __forceinline__ uint32_t sw128_off(int r, int k, int block) {
-  const int kb = k >> 5, c = k & 31;
-  return (uint32_t)(kb * block + r * 128 + ((((c >> 2) ^ (r & 7)) & 7) << 4) + ((c & 3) << 2));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  for (uint32_t i = 0; i < (1u << 22); ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
-// 1024 bytes, tcgen05 descriptor version.
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
-  d |= static_cast<uint64_t>(1) << 16;
-  d |= static_cast<uint64_t>(1024 >> 4) << 32;
-  d |= static_cast<uint64_t>(1) << 46;
-  d |= static_cast<uint64_t>(2) << 61;
-  return d;
-}
-
-// Instruction descriptor: D = F32, A = B = TF32, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
-         (static_cast<uint32_t>(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void umma_tmem_a(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc,
-                                            uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(d),
-      "r"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ void umma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
-                                        uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11,"
-      " %12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10,"
-      " %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
-      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]),
-      "f"(v[8]), "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]),
-      "f"(v[15])
-      : "memory");
-}
+using namespace ptx;
 
 __global__ void __launch_bounds__(kThreads, 1)
     absorb_tc_kernel(const float* __restrict__ X1, const float* __restrict__ Ak,
@@ -289,9 +194,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t kb = (uint32_t)(ks >> 2) * kAkBlock + (uint32_t)(ks & 3) * 32;
         const uint64_t bh = desc_sw128(sb + kOffAkH + kb), bl = desc_sw128(sb + kOffAkL + kb);
         const uint32_t acc = ks > 0 ? 1u : 0u;
-        umma_tmem_a(tmem + kD1Main, tmem + kAHi + ks * 8, bh, idesc_ket, acc);
-        umma_tmem_a(tmem + kD1Corr, tmem + kAHi + ks * 8, bl, idesc_ket, acc);
-        umma_tmem_a(tmem + kD1Corr, tmem + kALo + ks * 8, bh, idesc_ket, 1u);
+        umma_tf32_tmem_a(tmem + kD1Main, tmem + kAHi + ks * 8, bh, idesc_ket, acc);
+        umma_tf32_tmem_a(tmem + kD1Corr, tmem + kAHi + ks * 8, bl, idesc_ket, acc);
+        umma_tf32_tmem_a(tmem + kD1Corr, tmem + kALo + ks * 8, bh, idesc_ket, 1u);
       }
       umma_commit(bar_ket);
     }
@@ -339,9 +244,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint64_t ah = desc_sw128(sb + kOffZH + za), al = desc_sw128(sb + kOffZL + za);
         const uint64_t bh = desc_sw128(sb + kOffAbH + ab), bl = desc_sw128(sb + kOffAbL + ab);
         const uint32_t acc = ks > 0 ? 1u : 0u;
-        umma_ss(tmem + kD2Main, ah, bh, idesc_bra, acc);
-        umma_ss(tmem + kD2Corr, ah, bl, idesc_bra, acc);
-        umma_ss(tmem + kD2Corr, al, bh, idesc_bra, 1u);
+        umma_tf32_ss(tmem + kD2Main, ah, bh, idesc_bra, acc);
+        umma_tf32_ss(tmem + kD2Corr, ah, bl, idesc_bra, acc);
+        umma_tf32_ss(tmem + kD2Corr, al, bh, idesc_bra, 1u);
       }
       umma_commit(bar_bra);
     }
