@@ -701,6 +701,28 @@ bool make_map(CUtensorMap* tm, const TcOperand& op, int box_rows) {
   return r == CUDA_SUCCESS;
 }
 
+}  // namespace
+
+// 2-D map over an FP32 matrix (cols x rows, row stride in elements), box
+// (box_cols, box_rows), no swizzle: the shared-memory side of a copy is a
+// dense box.
+bool make_map_2d_f32(CUtensorMap* tm, const float* base, long long cols, long long rows,
+                     long long row_stride, int box_cols, int box_rows) {
+  EncodeFn enc = encoder();
+  if (!enc) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (row_stride * 4) % 16 != 0) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)row_stride * 4};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+namespace {
+
 template <int BN, int NBUF, int PRE>
 cudaError_t launch_bn(const TcGemm& g, cudaStream_t s) {
   using C = Cfg<BN, NBUF, PRE>;

@@ -1,6 +1,8 @@
 // Split-precision (TF32x3) contraction on tcgen05 tensor cores: interface.
 #pragma once
 
+#include <cuda.h>
+
 #include "qrctm_internal.cuh"
 
 namespace qrctm {
@@ -68,5 +70,11 @@ struct TcArgs {
 };
 
 cudaError_t gemm_tc(const TcGemm& g, cudaStream_t s);
+
+// 2-D TMA map over an FP32 matrix of rows x cols (row stride in elements,
+// a multiple of 4; base 16-byte aligned), box box_cols x box_rows, no
+// swizzle.  False when the driver's encoder is unavailable or a rule fails.
+bool make_map_2d_f32(CUtensorMap* tm, const float* base, long long cols, long long rows,
+                     long long row_stride, int box_cols, int box_rows);
 
 }  // namespace qrctm
