@@ -642,6 +642,42 @@ __global__ void __launch_bounds__(PT) qr_panel2_kernel(double* __restrict__ W,
       };
       long long i = std::max<long long>(r_begin, c + 1) + wrp;
       for (; i < r_end && i <= q1; i += 8) row1(i);
+      if (nrem < 16) {
+        // at most 16 live columns: rows i (lanes 0-15) and i + 8 (lanes
+        // 16-31) share each FP64 instruction, which costs the same for any
+        // number of active lanes; rows here are below both pivots
+        const int t = lane & 15, half = lane & 16;
+        const long long off = half ? 8 : 0;
+        const double pca = cfa[t], pcb = cfb[t];
+        const bool pact = t <= nrem, pupd = t >= 1 && pact;
+        double pacc1 = 0.0, pacc2 = 0.0;
+        for (; i < r_end; i += 16) {
+          const long long ir = i + off;
+          const bool rv = ir < r_end;
+          const double xa = rv ? at(ir, p) : 0.0;
+          const double old = (rv && pupd) ? at(ir, p + t) : 0.0;
+          double y = fma(pca, xa, old);
+          if (k == 2) {
+            const double xb = __shfl_sync(0xffffffffu, y, half | 1);
+            if (t >= 1) y = fma(pcb, xb, t == 1 ? 0.0 : y);
+          }
+          __syncwarp();
+          if (rv && pact) at(ir, p + t) = y;
+          if (nnext > 0) {
+            const double ya = __shfl_sync(0xffffffffu, y, half | la);
+            const double yb = __shfl_sync(0xffffffffu, y, half | lb);
+            if (rv && pact && t >= k) pacc1 = fma(ya, y, pacc1);
+            if (rv && pact && t >= k + 1) pacc2 = fma(yb, y, pacc2);
+          }
+        }
+        // lane t (< 16) collects both halves' sums of column p + t
+        pacc1 += __shfl_down_sync(0xffffffffu, pacc1, 16);
+        pacc2 += __shfl_down_sync(0xffffffffu, pacc2, 16);
+        if (lane < 16) {
+          acc1 += pacc1;
+          acc2 += pacc2;
+        }
+      } else {
       // rows below the next pivots, two at a time (independent chains: a
       // dependent FP64 operation costs 64 clocks on B300)
       double acc1b = 0.0, acc2b = 0.0;
@@ -681,6 +717,7 @@ __global__ void __launch_bounds__(PT) qr_panel2_kernel(double* __restrict__ W,
       for (; i < r_end; i += 8) row1(i);
       acc1 += acc1b;
       acc2 += acc2b;
+      }
     }
     done = p + k;
     ++round;
