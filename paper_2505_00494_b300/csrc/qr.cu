@@ -338,6 +338,13 @@ __global__ void __launch_bounds__(PT) qr_panel_kernel(double* __restrict__ W,
 // stays below ~2^10 ulp); otherwise the round factors column a alone.
 constexpr double kPairGuard = 1.0 / 1024.0;
 
+// Placement of the pair kernel's padded Gram-sum accumulators inside the
+// panel scratch: past the accumulator rows of the one-column kernel, the
+// pivot rows, G and tau; kPairAccCap doubles are free there.
+constexpr int kPairAccStride = 16;
+constexpr size_t kPairAccOff = ((size_t)2 * PMAX * NB + 4 * NB + NB * NB + NB + 15) & ~size_t(15);
+constexpr size_t kPairAccCap = (size_t)2 * PMAX * NB + 2 * NB + (size_t)PMAX * NB * NB - kPairAccOff;
+
 // Panel factorisation with up to two columns per grid-wide exchange.  The
 // single-column kernel above needs one exchange of partial sums per column;
 // here a round factors columns a = j and b = j + 1 (pivot rows c, c + 1) from
@@ -369,13 +376,17 @@ __global__ void __launch_bounds__(PT) qr_panel2_kernel(double* __restrict__ W,
                                                        long long ldx, float* __restrict__ Vt32,
                                                        const float* __restrict__ src32,
                                                        float* __restrict__ V32, long long ldv,
-                                                       long long wait_spins, unsigned wait_extra) {
+                                                       long long wait_spins, unsigned wait_extra,
+                                                       double* __restrict__ acc_base, int as) {
   const int P = gridDim.x, b = blockIdx.x;
   const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;   // wrp = row lane (0..7)
   const long long r_begin = (long long)j0 + (long long)b * rows_per_cta;
   const long long r_end = std::min<long long>(m, r_begin + rows_per_cta);
   const int rows = (int)std::max<long long>(0, r_end - r_begin);
-  double* accum = part + (size_t)j0 * 2 * NB;       // round at panel column p: accum + p * 2 NB
+  // Gram-sum accumulators: round at panel column p, slot (r, t) at
+  // accum[((p * 2 + r) * NB + t) * as] (as = 16: one 128-byte line per sum, so
+  // the grid's atomic additions spread over the L2 slices)
+  double* accum = acc_base + (size_t)j0 * 2 * NB * as;
   double* rowb = part + 2 * (size_t)PMAX * NB;      // [buffer][pivot row 0/1][NB]
   __shared__ double red[8][2][NB];
   __shared__ double cfa[NB];      // lane 0: 1/w_a; lane t >= 1: m_t
@@ -433,8 +444,8 @@ __global__ void __launch_bounds__(PT) qr_panel2_kernel(double* __restrict__ W,
     fold8();
     if (wrp == 0) {
       double* acc = accum;
-      if (lane < nb) atomicAdd(acc + lane, sum4(0, lane));
-      if (lane >= 1 && lane < nb) atomicAdd(acc + NB + lane, sum4(1, lane));
+      if (lane < nb) atomicAdd(acc + (size_t)lane * as, sum4(0, lane));
+      if (lane >= 1 && lane < nb) atomicAdd(acc + (size_t)(NB + lane) * as, sum4(1, lane));
       __syncwarp();
       if (lane == 0) grid_arrive(bar);
     }
@@ -446,7 +457,7 @@ __global__ void __launch_bounds__(PT) qr_panel2_kernel(double* __restrict__ W,
     const int buf = round & 1;
     const long long c = (long long)j0 + p;  // pivot row of column p
     const int nrem = nb - p - 1;            // columns right of p
-    const double* acc = accum + (size_t)p * 2 * NB;
+    const double* acc = accum + (size_t)p * 2 * NB * as;
     const double* rb = rowb + (size_t)buf * 2 * NB;
     const unsigned target = (unsigned)P * (unsigned)(round + 1) + wait_extra;
     // Scalars of the round, spread over three warps on three SM
@@ -471,8 +482,8 @@ __global__ void __launch_bounds__(PT) qr_panel2_kernel(double* __restrict__ W,
         if (nrem >= 1) {
           rb0 = __ldcg(rb + 1);
           rb1 = __ldcg(rb + NB + 1);
-          g01 = __ldcg(acc + 1);
-          g11 = __ldcg(acc + NB + 1);
+          g01 = __ldcg(acc + as);
+          g11 = __ldcg(acc + (size_t)(NB + 1) * as);
         }
       }
       if (wrp == 1) {
@@ -547,8 +558,8 @@ __global__ void __launch_bounds__(PT) qr_panel2_kernel(double* __restrict__ W,
       if (okw && lane <= nrem) {
         r0 = __ldcg(rb + lane);
         r1 = (c + 1 < m) ? __ldcg(rb + NB + lane) : 0.0;
-        g0 = __ldcg(acc + lane);
-        g1 = __ldcg(acc + NB + lane);
+        g0 = __ldcg(acc + (size_t)lane * as);
+        g1 = __ldcg(acc + (size_t)(NB + lane) * as);
       }
       // column a's sums over rows > c: sigma (lane 0), s_t (lane t)
       const double ra1 = __shfl_sync(0xffffffffu, r1, 0);
@@ -730,15 +741,15 @@ __global__ void __launch_bounds__(PT) qr_panel2_kernel(double* __restrict__ W,
     // arrives once warp 1's additions are issued (the barrier orders them
     // before the release)
     if (wrp == 0 || wrp == 1) {
-      double* an = accum + (size_t)done * 2 * NB;
+      double* an = accum + (size_t)done * 2 * NB * as;
       const int t = lane + k;                // red lane of the next round's column done + lane
       if (wrp == 0) {
-        if (lane < nnext) atomicAdd(an + lane, sum4(0, t));
+        if (lane < nnext) atomicAdd(an + (size_t)lane * as, sum4(0, t));
         __syncwarp();
         asm volatile("bar.sync 7, 64;" ::: "memory");
         if (lane == 0) grid_arrive(bar);
       } else {
-        if (lane >= 1 && lane < nnext) atomicAdd(an + NB + lane, sum4(1, t));
+        if (lane >= 1 && lane < nnext) atomicAdd(an + (size_t)(NB + lane) * as, sum4(1, t));
         __syncwarp();
         asm volatile("bar.arrive 7, 64;" ::: "memory");
       }
@@ -880,16 +891,31 @@ cudaError_t qr_panel_step(int m, int j0, int nbj, const QrWork& w, cudaStream_t 
   // cooperative launch, one CTA per SM at most: every CTA adds its partial
   // sums into the column's accumulator and arrives on the counter
   int rpc = (mr + P - 1) / P;
-  void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc, &x32, &ldx_, &vt32,
-                  &s32, &v32, &ldv_, &spins_, &extra_};
+
   const size_t tile = sizeof(double) * (size_t)rpc * (NB + 1);
   if (src32 != nullptr && tile > kPanelTileMax) {
     if (w.hook) w.hook(w.hook_user, 0);
     return cudaErrorInvalidValue;   // an FP32 source needs the tiled path
   }
   // two columns per grid-wide exchange where the accumulator rows fit (two
-  // rows of NB per round start: j0 + nb <= PMAX); one column otherwise
+  // rows of NB per round start: j0 + nb <= PMAX); one column otherwise.  The
+  // pair kernel's sums sit one per 128-byte line past the pivot rows, G and
+  // tau (zeroed with the first panel), or packed when the factorisation is
+  // too wide for that region.
   const bool pair = w.pair_rounds && j0 + nbj <= PMAX;
+  double* acc_base = part;
+  int as = 1;
+  if (pair && (size_t)w.ncols * 2 * NB * kPairAccStride <= kPairAccCap) {
+    acc_base = part + kPairAccOff;
+    as = kPairAccStride;
+    if (j0 == 0 && (e = cudaMemsetAsync(acc_base, 0, sizeof(double) * (size_t)w.ncols * 2 * NB *
+                                                         kPairAccStride, s)) != cudaSuccess) {
+      if (w.hook) w.hook(w.hook_user, 0);
+      return e;
+    }
+  }
+  void* args[] = {&W, &V, &taup, &part, &bar, &err, &m_, &j0_, &nb_, &rpc, &x32, &ldx_, &vt32,
+                  &s32, &v32, &ldv_, &spins_, &extra_, &acc_base, &as};
   const void* kt = pair ? (const void*)qr_panel2_kernel<true> : (const void*)qr_panel_kernel<true>;
   const void* kg = pair ? (const void*)qr_panel2_kernel<false> : (const void*)qr_panel_kernel<false>;
   if (tile <= kPanelTileMax) {
@@ -967,6 +993,7 @@ QrWork qr_carve(void* base, int m, int n) {
   w.wait_spins = kGridWaitSpins;
   w.wait_extra = 0;
   w.pair_rounds = false;
+  w.ncols = n;
   return w;
 }
 

@@ -276,6 +276,7 @@ struct QrWork {
   // path), the split-precision QR, whose trailing update and Q are FP32-class,
   // two.
   bool pair_rounds;
+  int ncols;              // columns of the factorisation (n)
 };
 constexpr long long kSplitKElems = 1ll << 21;   // 16 MB of split-K partials
 size_t qr_work_bytes(int m, int n);
