@@ -209,6 +209,158 @@ __global__ void __launch_bounds__(AbsorbShape<D, d, NG>::threads)
   }
 }
 
+// FP64 ket + bra layers of one (mu, b) slice after another (the FP64 path,
+// split layers, d = 2): the same contraction as above in FP64, for X1 in
+// the slice-contiguous layout X1[(mu,b)][(u_b,k_b)][(u_k,k_k)] and X2 in the
+// layout the FP64 projection reads, X2[(mu,b)][(d_k,j_k)][(d_b,j_b)].
+//   Z [(u_b,k_b)][(s,d_k,j_k)] = sum_{u_k,k_k} X1 A[s,u_k,k_k,d_k,j_k]
+//   X2[(d_k,j_k)][(d_b,j_b)]   = sum_{s,u_b,k_b} Z[(u_b,k_b)][(s,d_k,j_k)] A[s,u_b,k_b,d_b,j_b]
+// Bound by the FP64 pipe (~2 FMA per clock per SM on B300): 2 d D^6 FMA per
+// slice; per CTA of 8 warps, NG slices per batch copied in by one bulk
+// asynchronous copy (double buffer), Z in shared memory, 4 x 4 register
+// tiles for the ket and 2 x 4 for the bra so that both phases have D^4/4.5
+// tiles per slice for 256 threads at D = 6.
+template <int D, int NG>
+struct Absorb64Shape {
+  static constexpr int D2 = D * D, dD2 = 2 * D2, D4 = D2 * D2;
+  static constexpr int threads = 256;
+  static constexpr int ket_tiles = (D2 / 4) * (dD2 / 4);   // 4 x 4
+  static constexpr int bra_tiles = (D2 / 2) * (D2 / 4);    // 2 x 4
+  static constexpr size_t xbuf = (size_t)NG * D4;           // doubles per slice buffer
+  static constexpr size_t smem_doubles = 2 * xbuf + (size_t)NG * D2 * dD2 + 2 * (size_t)D2 * dD2;
+};
+
+template <int D, int NG>
+__global__ void __launch_bounds__(256) absorb64_k(const double* __restrict__ X1,
+                                                  const double* __restrict__ A,
+                                                  double* __restrict__ X2, long long ngroups,
+                                                  int* err) {
+  using S = Absorb64Shape<D, NG>;
+  constexpr int D2 = S::D2, dD2 = S::dD2, D4 = S::D4, nt = S::threads;
+  constexpr int D3 = D2 * D;
+  extern __shared__ __align__(128) double smd[];
+  __shared__ __align__(8) unsigned long long mbar[2];
+  __shared__ int s_ok;
+  const int tid = threadIdx.x;
+  double* Xb0 = smd;                                 // [NG][D2][D2]
+  double* Xb1 = Xb0 + S::xbuf;
+  double* Zs = Xb1 + S::xbuf;                        // [NG][D2][dD2]
+  double* AkT = Zs + (size_t)NG * D2 * dD2;          // [D2][dD2]: AkT[(u,l)][(s,d,r)] = A[s,u,l,d,r]
+  double* Ab = AkT + (size_t)D2 * dD2;               // [dD2][D2]: Ab[(s,u,l)][(d,r)] = A[s,u,l,d,r]
+  const uint32_t bar0 = smem_u32(&mbar[0]), bar1 = smem_u32(&mbar[1]);
+  const long long stride = (long long)gridDim.x * NG;
+  auto issue = [&](double* dst, uint32_t bar, long long g0, int ng) {
+    const uint32_t bytes = (uint32_t)((size_t)ng * D4 * sizeof(double));
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_arrive_expect_tx(bar, bytes);
+    bulk_load(smem_u32(dst), X1 + g0 * D4, bytes, bar);
+  };
+  if (tid == 0) {
+    mbar_init(bar0, 1);
+    mbar_init(bar1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const long long g0 = (long long)blockIdx.x * NG;
+    if (g0 < ngroups) issue(Xb0, bar0, g0, (int)std::min<long long>(NG, ngroups - g0));
+  }
+  for (int e = tid; e < D2 * dD2; e += nt) {
+    const int kq = e / dD2, cq = e % dD2;            // kq = (u,l), cq = (s,d,r)
+    const int sq = cq / D2, dr = cq % D2;
+    AkT[e] = A[(size_t)sq * D4 + (size_t)kq * D2 + dr];
+    Ab[e] = A[e];
+  }
+  int it = 0;
+  bool next_issued = false;
+  if (tid == 0) s_ok = 1;
+  for (long long g0 = (long long)blockIdx.x * NG; g0 < ngroups; g0 += stride, ++it) {
+    const int ng = (int)std::min<long long>(NG, ngroups - g0);
+    double* Xb = (it & 1) ? Xb1 : Xb0;
+    const uint32_t bar = (it & 1) ? bar1 : bar0;
+    __syncthreads();   // the other buffer's previous batch is consumed
+    const long long gn = g0 + stride;
+    next_issued = gn < ngroups;
+    if (tid == 0 && next_issued)
+      issue((it & 1) ? Xb0 : Xb1, (it & 1) ? bar0 : bar1, gn, (int)std::min<long long>(NG, ngroups - gn));
+    if (!mbar_wait_bounded(bar, (uint32_t)((it >> 1) & 1))) {
+      atomicOr(err, ERRF_TIMEOUT);
+      s_ok = 0;
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    // ket: Zs[g][r][c] = sum_k Xb[g][r][k] AkT[k][c]   (4 x 4 tiles)
+    for (int t = tid; t < ng * S::ket_tiles; t += nt) {
+      const int g = t / S::ket_tiles, q = t % S::ket_tiles;
+      const int rb = (q / (dD2 / 4)) * 4, cb = (q % (dD2 / 4)) * 4;
+      double acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+      const double* xa = Xb + ((size_t)g * D2 + rb) * D2;
+      const double* kb = AkT + cb;
+#pragma unroll 4
+      for (int k = 0; k < D2; ++k) {
+        const double2 b01 = *reinterpret_cast<const double2*>(kb + k * dD2);
+        const double2 b23 = *reinterpret_cast<const double2*>(kb + k * dD2 + 2);
+        const double bv[4] = {b01.x, b01.y, b23.x, b23.y};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const double av = xa[i * D2 + k];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(av, bv[j], acc[i][j]);
+        }
+      }
+      double* zo = Zs + ((size_t)g * D2 + rb) * dD2 + cb;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        *reinterpret_cast<double2*>(zo + i * dD2) = make_double2(acc[i][0], acc[i][1]);
+        *reinterpret_cast<double2*>(zo + i * dD2 + 2) = make_double2(acc[i][2], acc[i][3]);
+      }
+    }
+    __syncthreads();
+    // bra: X2[g][r2][c2] = sum_{s,q} Zs[g][q][s D2 + r2] Ab[s D2 + q][c2]   (2 x 4 tiles)
+    for (int t = tid; t < ng * S::bra_tiles; t += nt) {
+      const int g = t / S::bra_tiles, q = t % S::bra_tiles;
+      const int rb = (q / (D2 / 4)) * 2, cb = (q % (D2 / 4)) * 4;
+      double acc[2][4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+#pragma unroll
+      for (int s2 = 0; s2 < 2; ++s2) {
+        const double* za = Zs + (size_t)g * D2 * dD2 + s2 * D2 + rb;
+        const double* ba = Ab + (size_t)s2 * D2 * D2 + cb;
+#pragma unroll 4
+        for (int qq = 0; qq < D2; ++qq) {
+          const double2 a = *reinterpret_cast<const double2*>(za + qq * dD2);
+          const double2 b01 = *reinterpret_cast<const double2*>(ba + qq * D2);
+          const double2 b23 = *reinterpret_cast<const double2*>(ba + qq * D2 + 2);
+          const double av[2] = {a.x, a.y};
+          const double bv[4] = {b01.x, b01.y, b23.x, b23.y};
+#pragma unroll
+          for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
+      }
+      double* xo = X2 + (size_t)(g0 + g) * D4 + (size_t)rb * D2 + cb;
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        *reinterpret_cast<double2*>(xo + i * D2) = make_double2(acc[i][0], acc[i][1]);
+        *reinterpret_cast<double2*>(xo + i * D2 + 2) = make_double2(acc[i][2], acc[i][3]);
+      }
+    }
+  }
+  // after an abandoned wait, let the copies still in flight land (bounded)
+  // before the CTA's shared memory is released
+  if (!s_ok && tid == 0) {
+    mbar_wait_bounded((it & 1) ? bar1 : bar0, (uint32_t)((it >> 1) & 1));
+    if (next_issued)
+      mbar_wait_bounded(((it + 1) & 1) ? bar1 : bar0, (uint32_t)(((it + 1) >> 1) & 1));
+  }
+  (void)D3;
+}
+
 using AbsorbKernel = void (*)(const float*, const float*, const float*, float*, int, long long,
                               long long, long long, long long, int*);
 
@@ -268,6 +420,39 @@ cudaError_t absorb_fused(const float* X1, const float* Ak, const float* Ab, floa
   const long long iters = (ngroups + v.NG - 1) / v.NG;
   const unsigned grid = (unsigned)std::min<long long>(iters, (long long)nsm * per_sm);
   v.k<<<grid, v.threads, v.smem, s>>>(X1, Ak, Ab, X2, ch, D2p, dD2p, mp, ngroups, err);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// FP64 ket + bra for the FP64 path at d = 2, D = 4 and 6 (X1 slice-contiguous,
+// X2 in the projection's layout); other shapes keep the two FP64 GEMMs.
+bool absorb64_ok(int d, int D) { return d == 2 && (D == 4 || D == 6); }
+
+cudaError_t absorb64(const double* X1, const double* A, double* X2, long long ngroups, int d, int D,
+                     int* err, cudaStream_t s) {
+  if (!absorb64_ok(d, D) || (reinterpret_cast<uintptr_t>(X1) & 15) != 0 ||
+      (reinterpret_cast<uintptr_t>(X2) & 15) != 0)
+    return cudaErrorInvalidValue;
+  const void* kf = nullptr;
+  size_t smem = 0;
+  int NG = 0;
+  if (D == 6) {
+    kf = (const void*)absorb64_k<6, 4>;
+    smem = sizeof(double) * Absorb64Shape<6, 4>::smem_doubles;
+    NG = 4;
+  } else {
+    kf = (const void*)absorb64_k<4, 8>;
+    smem = sizeof(double) * Absorb64Shape<4, 8>::smem_doubles;
+    NG = 8;
+  }
+  cudaError_t e = device_once(kf, [kf, smem] {
+    return cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (e != cudaSuccess) return e;
+  const long long iters = (ngroups + NG - 1) / NG;
+  const unsigned grid = (unsigned)std::min<long long>(iters, device_sm_count());
+  if (D == 6) absorb64_k<6, 4><<<grid, 256, smem, s>>>(X1, A, X2, ngroups, err);
+  else absorb64_k<4, 8><<<grid, 256, smem, s>>>(X1, A, X2, ngroups, err);
   note_launch();
   return cudaGetLastError();
 }

@@ -39,7 +39,10 @@ cudaError_t renorm_edge(qrctm_ctx* c, const double* P, int co, const double* T, 
   const long long mi = (long long)ci * D2;
   const long long Su = (long long)co * D2 * ci, Smu = (long long)D2 * ci, Sk = ci;
   cudaError_t e;
-  // X1[(u,m),(k,b)] = sum_a P[(a,u),m] T[a,(k,b)]
+  // X1[(u,m),(k,b)] = sum_a P[(a,u),m] T[a,(k,b)], u = (u_k,u_b), k = (k_k,k_b);
+  // for the fused FP64 absorption stored slice by slice instead,
+  // X1[(m,b)][(u_b,k_b)][(u_k,k_k)]
+  const bool fused64 = c->split_layers && absorb64_ok(d, D);
   {
     PhaseScope ps(c, QRCTM_PH_X1);
     Gemm g = gemm_ctx(c);
@@ -47,11 +50,19 @@ cudaError_t renorm_edge(qrctm_ctx* c, const double* P, int co, const double* T, 
     g.A = P; g.a_m = im2(co, mi, 1); g.a_k = im1(D2);
     g.B = T; g.b_k = im1((long long)D2 * ci); g.b_n = im1(1);
     g.C = c->X1; g.c_m = im1(g.N); g.c_n = im1(1);
+    if (fused64) {
+      g.c_m = im3(co, D, (long long)ci * D4, D3, D);
+      g.c_n = im3(ci, D, D4, D2, 1);
+    }
     if ((e = gemm_f64(g, c->st)) != cudaSuccess) return e;
   }
   {
   PhaseScope ps_abs(c, QRCTM_PH_ABSORB);
-  if (c->split_layers) {
+  if (fused64) {
+    // both layers in one FP64 kernel, Z on chip; X2 as the bra GEMM writes it
+    if ((e = absorb64(c->X1, c->A, c->X2, (long long)co * ci, d, D, c->err, c->st)) != cudaSuccess)
+      return e;
+  } else if (c->split_layers) {
     const long long dD2 = (long long)d * D2;
     // ket: Z[(m,b,u_b,k_b),(s,d_k,j_k)] = sum_{u_k,k_k} X1 A[s,u_k,k_k,d_k,j_k]
     Gemm g = gemm_ctx(c);

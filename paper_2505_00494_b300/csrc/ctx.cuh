@@ -144,6 +144,11 @@ bool absorb_tc_ok(int d, int D);
 cudaError_t absorb_tc(const float* X1, const float* Ak, const float* Ab, float* X2, int ch,
                       long long D2p, long long dD2p, long long mp, int* err, cudaStream_t s);
 bool absorb_fused_ok(int d, int D);
+// FP64 ket + bra in one kernel (FP64 path, d = 2, D = 4, 6): X1 slice-contiguous
+// [(mu,b)][(u_b,k_b)][(u_k,k_k)], X2 [(mu,b)][(d_k,j_k)][(d_b,j_b)], ngroups slices.
+bool absorb64_ok(int d, int D);
+cudaError_t absorb64(const double* X1, const double* A, double* X2, long long ngroups, int d, int D,
+                     int* err, cudaStream_t s);
 cudaError_t absorb_fused(const float* X1, const float* Ak, const float* Ab, float* X2, int ch,
                          int D, int d, long long D2p, long long dD2p, long long mp, int* err,
                          cudaStream_t s);
