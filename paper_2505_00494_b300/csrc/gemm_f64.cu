@@ -15,11 +15,14 @@ namespace qrctm {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BM = 64, BK = 16, NT = 256;
 
 // splits > 1 (batch == 1 only): CTA z handles K range [z*kc, (z+1)*kc) and
-// writes its raw sums to g.part[z][M][N].
+// writes its raw sums to g.part[z][M][N].  BN = 64 (4 x 4 per thread) or 48
+// (4 x 3: for N a multiple of 48, such as chi = 144, no column of a tile idles).
+template <int BN>
 __global__ void __launch_bounds__(NT) gemm_f64_kernel(Gemm g, int splits, long long kc) {
+  constexpr int TN = BN / 16;
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
   __shared__ long long aRow[BM], bCol[BN], aK[BK], bK[BK];
@@ -42,11 +45,11 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(Gemm g, int splits, long l
       long long n = n0 + tid - BM;
       bCol[tid - BM] = (n < g.N) ? map_off(g.b_n, n) : -1;
     }
-    double acc[4][4];
+    double acc[4][TN];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+      for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
 
     for (long long k0 = kbeg; k0 < kend; k0 += BK) {
       if (tid < BK) {
@@ -74,15 +77,15 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(Gemm g, int splits, long l
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
-        double av[4], bv[4];
+        double av[4], bv[TN];
 #pragma unroll
         for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+        for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+          for (int j = 0; j < TN; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
       }
       __syncthreads();
     }
@@ -93,7 +96,7 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(Gemm g, int splits, long l
         long long m = m0 + ty + 16 * i;
         if (m >= g.M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < TN; ++j) {
           long long n = n0 + tx + 16 * j;
           if (n < g.N) P[m * g.N + n] = acc[i][j];
         }
@@ -106,7 +109,7 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(Gemm g, int splits, long l
       if (m >= g.M) continue;
       long long ro = map_off(g.c_m, m);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < TN; ++j) {
         long long n = n0 + tx + 16 * j;
         if (n >= g.N) continue;
         double* p = g.C + cB + ro + map_off(g.c_n, n);
@@ -178,8 +181,8 @@ static unsigned long long g_launches = 0;
 void note_launch(unsigned long long n) { __atomic_fetch_add(&g_launches, n, __ATOMIC_RELAXED); }
 unsigned long long launches_so_far() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
-cudaError_t gemm_f64(const Gemm& g, cudaStream_t s) {
-  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+template <int BN>
+cudaError_t gemm_f64_launch(const Gemm& g, cudaStream_t s) {
   long long gx = (g.M + BM - 1) / BM, gy = (g.N + BN - 1) / BN;
   if (gx > 0x7fffffffll) return cudaErrorInvalidValue;
   if (gy > 65535) gy = 65535;   // the kernel loops over the remaining N tiles
@@ -197,7 +200,7 @@ cudaError_t gemm_f64(const Gemm& g, cudaStream_t s) {
     long long kc = (g.K + splits - 1) / splits;
     kc = (kc + BK - 1) / BK * BK;
     splits = (int)((g.K + kc - 1) / kc);
-    gemm_f64_kernel<<<dim3((unsigned)gx, (unsigned)gy, splits), NT, 0, s>>>(g, splits, kc);
+    gemm_f64_kernel<BN><<<dim3((unsigned)gx, (unsigned)gy, splits), NT, 0, s>>>(g, splits, kc);
     note_launch();
     long long MN = g.M * g.N;
     long long nb = std::min<long long>((MN + 255) / 256, 4096);
@@ -206,9 +209,17 @@ cudaError_t gemm_f64(const Gemm& g, cudaStream_t s) {
     return cudaGetLastError();
   }
   int gz = g.batch < 65535 ? g.batch : 65535;
-  gemm_f64_kernel<<<dim3((unsigned)gx, (unsigned)gy, gz), NT, 0, s>>>(g, 1, 0);
+  gemm_f64_kernel<BN><<<dim3((unsigned)gx, (unsigned)gy, gz), NT, 0, s>>>(g, 1, 0);
   note_launch();
   return cudaGetLastError();
+}
+
+cudaError_t gemm_f64(const Gemm& g, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+  // the narrower tile where it leaves fewer idle columns in the last N tile
+  const long long idle64 = (g.N + 63) / 64 * 64 - g.N, idle48 = (g.N + 47) / 48 * 48 - g.N;
+  if (idle48 < idle64) return gemm_f64_launch<48>(g, s);
+  return gemm_f64_launch<64>(g, s);
 }
 
 }  // namespace qrctm
