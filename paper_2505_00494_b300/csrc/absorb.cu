@@ -220,31 +220,35 @@ __global__ void __launch_bounds__(AbsorbShape<D, d, NG>::threads)
 // asynchronous copy (double buffer), Z in shared memory, 4 x 4 register
 // tiles for the ket and 2 x 4 for the bra so that both phases have D^4/4.5
 // tiles per slice for 256 threads at D = 6.
-template <int D, int NG>
+template <int D, int NG, int NBUF>
 struct Absorb64Shape {
   static constexpr int D2 = D * D, dD2 = 2 * D2, D4 = D2 * D2;
   static constexpr int threads = 256;
   static constexpr int ket_tiles = (D2 / 4) * (dD2 / 4);   // 4 x 4
   static constexpr int bra_tiles = (D2 / 2) * (D2 / 4);    // 2 x 4
   static constexpr size_t xbuf = (size_t)NG * D4;           // doubles per slice buffer
-  static constexpr size_t smem_doubles = 2 * xbuf + (size_t)NG * D2 * dD2 + 2 * (size_t)D2 * dD2;
+  static constexpr size_t smem_doubles =
+      NBUF * xbuf + (size_t)NG * D2 * dD2 + 2 * (size_t)D2 * dD2;
 };
 
-template <int D, int NG>
+// NBUF = 2: the next batch's copy overlaps this batch's contraction; NBUF = 1
+// (D = 8: one slice of 32 KB, 224 KB in all) the copy is issued once the
+// slice has been consumed -- its latency is small against the ~0.26 ms of
+// FP64 work per slice.
+template <int D, int NG, int NBUF>
 __global__ void __launch_bounds__(256) absorb64_k(const double* __restrict__ X1,
                                                   const double* __restrict__ A,
                                                   double* __restrict__ X2, long long ngroups,
                                                   int* err) {
-  using S = Absorb64Shape<D, NG>;
+  using S = Absorb64Shape<D, NG, NBUF>;
   constexpr int D2 = S::D2, dD2 = S::dD2, D4 = S::D4, nt = S::threads;
-  constexpr int D3 = D2 * D;
   extern __shared__ __align__(128) double smd[];
   __shared__ __align__(8) unsigned long long mbar[2];
   __shared__ int s_ok;
   const int tid = threadIdx.x;
   double* Xb0 = smd;                                 // [NG][D2][D2]
-  double* Xb1 = Xb0 + S::xbuf;
-  double* Zs = Xb1 + S::xbuf;                        // [NG][D2][dD2]
+  double* Xb1 = (NBUF == 2) ? Xb0 + S::xbuf : Xb0;
+  double* Zs = Xb0 + NBUF * S::xbuf;                 // [NG][D2][dD2]
   double* AkT = Zs + (size_t)NG * D2 * dD2;          // [D2][dD2]: AkT[(u,l)][(s,d,r)] = A[s,u,l,d,r]
   double* Ab = AkT + (size_t)D2 * dD2;               // [dD2][D2]: Ab[(s,u,l)][(d,r)] = A[s,u,l,d,r]
   const uint32_t bar0 = smem_u32(&mbar[0]), bar1 = smem_u32(&mbar[1]);
@@ -277,8 +281,8 @@ __global__ void __launch_bounds__(256) absorb64_k(const double* __restrict__ X1,
     const uint32_t bar = (it & 1) ? bar1 : bar0;
     __syncthreads();   // the other buffer's previous batch is consumed
     const long long gn = g0 + stride;
-    next_issued = gn < ngroups;
-    if (tid == 0 && next_issued)
+    next_issued = NBUF == 2 && gn < ngroups;   // with one buffer: set when issued below
+    if (NBUF == 2 && tid == 0 && next_issued)
       issue((it & 1) ? Xb0 : Xb1, (it & 1) ? bar0 : bar1, gn, (int)std::min<long long>(NG, ngroups - gn));
     if (!mbar_wait_bounded(bar, (uint32_t)((it >> 1) & 1))) {
       atomicOr(err, ERRF_TIMEOUT);
@@ -317,6 +321,12 @@ __global__ void __launch_bounds__(256) absorb64_k(const double* __restrict__ X1,
       }
     }
     __syncthreads();
+    // one buffer: the slices are consumed, the next batch's copy can start
+    // (it lands while the bra runs)
+    if (NBUF == 1 && gn < ngroups) {
+      next_issued = true;
+      if (tid == 0) issue(Xb0, (it & 1) ? bar0 : bar1, gn, (int)std::min<long long>(NG, ngroups - gn));
+    }
     // bra: X2[g][r2][c2] = sum_{s,q} Zs[g][q][s D2 + r2] Ab[s D2 + q][c2]   (2 x 4 tiles)
     for (int t = tid; t < ng * S::bra_tiles; t += nt) {
       const int g = t / S::bra_tiles, q = t % S::bra_tiles;
@@ -358,7 +368,6 @@ __global__ void __launch_bounds__(256) absorb64_k(const double* __restrict__ X1,
     if (next_issued)
       mbar_wait_bounded(((it + 1) & 1) ? bar1 : bar0, (uint32_t)(((it + 1) >> 1) & 1));
   }
-  (void)D3;
 }
 
 using AbsorbKernel = void (*)(const float*, const float*, const float*, float*, int, long long,
@@ -426,35 +435,33 @@ cudaError_t absorb_fused(const float* X1, const float* Ak, const float* Ab, floa
 
 // FP64 ket + bra for the FP64 path at d = 2, D = 4 and 6 (X1 slice-contiguous,
 // X2 in the projection's layout); other shapes keep the two FP64 GEMMs.
-bool absorb64_ok(int d, int D) { return d == 2 && (D == 4 || D == 6); }
+bool absorb64_ok(int d, int D) { return d == 2 && (D == 4 || D == 6 || D == 8); }
 
-cudaError_t absorb64(const double* X1, const double* A, double* X2, long long ngroups, int d, int D,
-                     int* err, cudaStream_t s) {
-  if (!absorb64_ok(d, D) || (reinterpret_cast<uintptr_t>(X1) & 15) != 0 ||
-      (reinterpret_cast<uintptr_t>(X2) & 15) != 0)
-    return cudaErrorInvalidValue;
-  const void* kf = nullptr;
-  size_t smem = 0;
-  int NG = 0;
-  if (D == 6) {
-    kf = (const void*)absorb64_k<6, 4>;
-    smem = sizeof(double) * Absorb64Shape<6, 4>::smem_doubles;
-    NG = 4;
-  } else {
-    kf = (const void*)absorb64_k<4, 8>;
-    smem = sizeof(double) * Absorb64Shape<4, 8>::smem_doubles;
-    NG = 8;
-  }
+template <int D, int NG, int NBUF>
+cudaError_t absorb64_launch(const double* X1, const double* A, double* X2, long long ngroups,
+                            int* err, cudaStream_t s) {
+  using S = Absorb64Shape<D, NG, NBUF>;
+  const void* kf = (const void*)absorb64_k<D, NG, NBUF>;
+  const size_t smem = sizeof(double) * S::smem_doubles;
   cudaError_t e = device_once(kf, [kf, smem] {
     return cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   if (e != cudaSuccess) return e;
   const long long iters = (ngroups + NG - 1) / NG;
   const unsigned grid = (unsigned)std::min<long long>(iters, device_sm_count());
-  if (D == 6) absorb64_k<6, 4><<<grid, 256, smem, s>>>(X1, A, X2, ngroups, err);
-  else absorb64_k<4, 8><<<grid, 256, smem, s>>>(X1, A, X2, ngroups, err);
+  absorb64_k<D, NG, NBUF><<<grid, S::threads, smem, s>>>(X1, A, X2, ngroups, err);
   note_launch();
   return cudaGetLastError();
+}
+
+cudaError_t absorb64(const double* X1, const double* A, double* X2, long long ngroups, int d, int D,
+                     int* err, cudaStream_t s) {
+  if (!absorb64_ok(d, D) || (reinterpret_cast<uintptr_t>(X1) & 15) != 0 ||
+      (reinterpret_cast<uintptr_t>(X2) & 15) != 0)
+    return cudaErrorInvalidValue;
+  if (D == 8) return absorb64_launch<8, 1, 1>(X1, A, X2, ngroups, err, s);   // 224 KB
+  if (D == 6) return absorb64_launch<6, 4, 2>(X1, A, X2, ngroups, err, s);   // 207 KB
+  return absorb64_launch<4, 8, 2>(X1, A, X2, ngroups, err, s);              // 74 KB
 }
 
 }  // namespace qrctm
