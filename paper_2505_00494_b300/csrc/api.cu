@@ -121,7 +121,7 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
   take(R_(s_cur), chi);
   take(R_(s_prev), chi);
   take(R_(delta_d), 8);
-  take(R_(partials), 1024);
+  take(R_(partials), std::max<size_t>(1024, (size_t)16 * kTraceParts));
   take(R_(a), split ? 1 : D2 * D2 * D2 * D2);
   // energy patches (iPEPS only)
   take(R_(E1), net ? 1 : d * d * m * m);
@@ -190,10 +190,14 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
     c->G = nullptr; c->G_bytes = 0;
   }
   // FP32 operand copies for the split-precision energy and adjoint
-  // contractions: the largest one pairs a d^2-batched (chi D^2)^2 operand
-  // with an unbatched one
+  // contractions: the energy's largest pairs a d^2-batched (chi D^2)^2
+  // operand with an unbatched one ((d^2 + 1) (chi D^2)^2 floats); with the J2
+  // gradient, the adjoint of the 2x2-patch product reads two operands of
+  // d^2 (chi D^2)^2 each, which must also fit here to run on the tensor cores
   if (cfg.precision == QRCTM_SPLIT) {
-    const size_t mm = m * m, floats = (d * d + 2) * mm + (size_t(1) << 20);
+    const size_t mm = m * m;
+    const size_t per = (cfg.with_grad && cfg.with_nnn) ? 2 * d * d + 2 : d * d + 2;
+    const size_t floats = per * mm + (size_t(1) << 20);
     size_t o = off;
     off += al(sizeof(float) * floats);
     if (carve) { c->mm32 = reinterpret_cast<float*>(c->ws + o); c->mm32_floats = floats; }

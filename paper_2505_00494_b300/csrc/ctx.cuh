@@ -193,6 +193,15 @@ inline X2Maps x2_maps(const qrctm_ctx* c, int ci) {
 
 // Energy (energy.cu)
 cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2);
+// FP64 traces Tr(P_p P_q) of nb <= 4 matrices (m x m at P + p m^2) and their
+// cotangent Pb_p = sum_q (rhob + rhob^T)[p][q] P_q^T; part: kTraceParts * 16
+// doubles of scratch (the context's partials).
+constexpr int kTraceParts = 1184;
+bool trace_pairs_ok(int nb);
+cudaError_t trace_pairs(const double* P, int nb, long long m, double* part, double* rho,
+                        cudaStream_t s);
+cudaError_t trace_pairs_vjp(const double* P, int nb, long long m, const double* rhob, double* Pb,
+                            cudaStream_t s);
 
 // Gradient (grad.cu)
 size_t grad_bytes(int d, int D, int chi);

@@ -70,10 +70,158 @@ __global__ void energy_k(const double* rho_nn, const double* rho_nnn, double J1,
   e_out[2] = ennn;
 }
 
+// Traces of pairs of the nb = d^2 matrices P_p (m x m, row-major, P_p at
+// P + p mm): rho[p][q] = sum_{i,j} P_p[i][j] P_q[j][i] = Tr(P_p P_q), and the
+// adjoint Pb_p[i][j] = sum_q W[p][q] P_q[j][i], W = rhob + rhob^T.  A
+// contraction with a d^2 x d^2 output over (chi D^2)^2 terms reads P once (and
+// once transposed) and is bound by the FP64 pipe at a few d^4 FMA per
+// element; as a general GEMM its 64 x 48 tiles were ~99% idle.  One CTA works
+// on 32 x 32 tiles (I, J): its own block P_p[I,J] in registers, the partner
+// block P_q[J,I] through shared memory read transposed.  The trace's per-CTA
+// partial sums are added in a fixed order by a second kernel.
+constexpr int kTrT = 32;          // tile edge
+constexpr int kTrThreads = 256;   // 32 x 8: four rows of a tile per thread
+constexpr int kTrMaxNb = 4;
+
+__global__ void __launch_bounds__(kTrThreads) trace_pairs_k(const double* __restrict__ P, int nb,
+                                                            long long m, double* __restrict__ part) {
+  __shared__ double Bt[kTrMaxNb][kTrT][kTrT + 1];
+  __shared__ double red[kTrThreads / 32][kTrMaxNb * kTrMaxNb];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // column b, rows ty + 8 r
+  const long long mm = m * m;
+  const long long nt = (m + kTrT - 1) / kTrT;
+  double acc[kTrMaxNb * kTrMaxNb];
+#pragma unroll
+  for (int u = 0; u < kTrMaxNb * kTrMaxNb; ++u) acc[u] = 0.0;
+  for (long long t = blockIdx.x; t < nt * nt; t += gridDim.x) {
+    const long long I = t / nt, J = t % nt;
+    __syncthreads();
+    // partner block P_q[J rows][I cols], coalesced along I, kept as Bt[q][row j][col i]
+    for (int r = ty; r < kTrT; r += 8) {
+      const long long gj = J * kTrT + r, gi = I * kTrT + tx;
+#pragma unroll
+      for (int q = 0; q < kTrMaxNb; ++q)
+        Bt[q][r][tx] = (q < nb && gj < m && gi < m) ? P[q * mm + gj * m + gi] : 0.0;
+    }
+    __syncthreads();
+    for (int r = ty; r < kTrT; r += 8) {
+      const long long gi = I * kTrT + r, gj = J * kTrT + tx;   // own element (i, j)
+      if (gi >= m || gj >= m) continue;
+      double a[kTrMaxNb];
+#pragma unroll
+      for (int p = 0; p < kTrMaxNb; ++p) a[p] = (p < nb) ? P[p * mm + gi * m + gj] : 0.0;
+#pragma unroll
+      for (int q = 0; q < kTrMaxNb; ++q) {
+        const double bq = Bt[q][tx][r];                          // P_q[j][i]
+#pragma unroll
+        for (int p = 0; p < kTrMaxNb; ++p) acc[p * kTrMaxNb + q] = fma(a[p], bq, acc[p * kTrMaxNb + q]);
+      }
+    }
+  }
+  // block reduction: warp shuffles, then the 8 warps in a fixed order
+#pragma unroll
+  for (int u = 0; u < kTrMaxNb * kTrMaxNb; ++u) {
+    double v = acc[u];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (tx == 0) red[ty][u] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kTrMaxNb * kTrMaxNb) {
+    double v = 0.0;
+    for (int w = 0; w < kTrThreads / 32; ++w) v += red[w][threadIdx.x];
+    part[(long long)blockIdx.x * kTrMaxNb * kTrMaxNb + threadIdx.x] = v;
+  }
+}
+
+__global__ void trace_pairs_sum_k(const double* __restrict__ part, int nparts, int nb,
+                                  double* __restrict__ rho) {
+  // one warp per (p, q): lanes stride over the CTA partials, then a fixed
+  // shuffle tree
+  const int u = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (u >= nb * nb) return;
+  const int p = u / nb, q = u % nb;
+  double v = 0.0;
+  for (int b = lane; b < nparts; b += 32) v += part[(long long)b * kTrMaxNb * kTrMaxNb + p * kTrMaxNb + q];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) rho[p * nb + q] = v;
+}
+
+__global__ void __launch_bounds__(kTrThreads) trace_pairs_vjp_k(const double* __restrict__ P, int nb,
+                                                                long long m,
+                                                                const double* __restrict__ rhob,
+                                                                double* __restrict__ Pb) {
+  __shared__ double Bt[kTrMaxNb][kTrT][kTrT + 1];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const long long mm = m * m;
+  const long long nt = (m + kTrT - 1) / kTrT;
+  double w[kTrMaxNb][kTrMaxNb];
+#pragma unroll
+  for (int p = 0; p < kTrMaxNb; ++p)
+#pragma unroll
+    for (int q = 0; q < kTrMaxNb; ++q)
+      w[p][q] = (p < nb && q < nb) ? rhob[p * nb + q] + rhob[q * nb + p] : 0.0;
+  for (long long t = blockIdx.x; t < nt * nt; t += gridDim.x) {
+    const long long I = t / nt, J = t % nt;
+    __syncthreads();
+    for (int r = ty; r < kTrT; r += 8) {
+      const long long gj = J * kTrT + r, gi = I * kTrT + tx;
+#pragma unroll
+      for (int q = 0; q < kTrMaxNb; ++q)
+        Bt[q][r][tx] = (q < nb && gj < m && gi < m) ? P[q * mm + gj * m + gi] : 0.0;
+    }
+    __syncthreads();
+    for (int r = ty; r < kTrT; r += 8) {
+      const long long gi = I * kTrT + r, gj = J * kTrT + tx;
+      if (gi >= m || gj >= m) continue;
+      double b[kTrMaxNb];
+#pragma unroll
+      for (int q = 0; q < kTrMaxNb; ++q) b[q] = Bt[q][tx][r];       // P_q[j][i]
+#pragma unroll
+      for (int p = 0; p < kTrMaxNb; ++p) {
+        if (p >= nb) break;
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < kTrMaxNb; ++q) v = fma(w[p][q], b[q], v);
+        Pb[p * mm + gi * m + gj] = v;
+      }
+    }
+  }
+}
+
 }  // namespace
 
 // Uses c->Mcm (ct), c->Y2 (L1), c->X1 (W / X), c->Z (ket), c->X2 (Ct),
 // c->E1 (bra / Ct_open), c->E2 (HL), c->E3 (P), c->rho, c->e_d.
+bool trace_pairs_ok(int nb) { return nb >= 1 && nb <= kTrMaxNb; }
+
+// rho[p][q] = Tr(P_p P_q) for the nb matrices P_p (m x m) at P + p m^2;
+// part: scratch of at least kTraceParts * 16 doubles.
+cudaError_t trace_pairs(const double* P, int nb, long long m, double* part, double* rho,
+                        cudaStream_t s) {
+  if (!trace_pairs_ok(nb)) return cudaErrorInvalidValue;
+  const long long nt = (m + kTrT - 1) / kTrT;
+  const int grid = (int)std::min<long long>(nt * nt, kTraceParts);
+  trace_pairs_k<<<grid, kTrThreads, 0, s>>>(P, nb, m, part);
+  note_launch();
+  trace_pairs_sum_k<<<1, 32 * kTrMaxNb * kTrMaxNb, 0, s>>>(part, grid, nb, rho);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// Pb_p = sum_q (rhob[p][q] + rhob[q][p]) P_q^T: the cotangent of every P_p
+// for rho = Tr(P_p P_q) (overwrites Pb).
+cudaError_t trace_pairs_vjp(const double* P, int nb, long long m, const double* rhob, double* Pb,
+                            cudaStream_t s) {
+  if (!trace_pairs_ok(nb)) return cudaErrorInvalidValue;
+  const long long nt = (m + kTrT - 1) / kTrT;
+  const int grid = (int)std::min<long long>(nt * nt, 8ll * device_sm_count());
+  trace_pairs_vjp_k<<<grid, kTrThreads, 0, s>>>(P, nb, m, rhob, Pb);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
   const int D = c->D, D2 = c->D2, d = c->d, ch = c->chi_cur;
   const long long D3 = (long long)D2 * D, D4 = (long long)D2 * D2;
@@ -188,12 +336,16 @@ cudaError_t energy_fp64(qrctm_ctx* c, double J1, double J2) {
       c->mm_split = was;
       if (e != cudaSuccess) return e;
       // rho_nnn[(s1,t1),(s4,t4)] = sum_{a,c} P(s1,t1)[a,c] P(s4,t4)[c,a]
-      g = gemm_ctx(c);
-      g.M = d * d; g.N = d * d; g.K = mm;
-      g.A = c->E3; g.a_m = im1(mm); g.a_k = im1(1);
-      g.B = c->E3; g.b_k = im2((int)m, m, 1); g.b_n = im1(mm);
-      g.C = rho_nnn; g.c_m = im1(d * d); g.c_n = im1(1);
-      if ((e = gemm_run(c, g)) != cudaSuccess) return e;
+      if (trace_pairs_ok(d * d)) {
+        if ((e = trace_pairs(c->E3, d * d, m, c->partials, rho_nnn, st)) != cudaSuccess) return e;
+      } else {
+        g = gemm_ctx(c);
+        g.M = d * d; g.N = d * d; g.K = mm;
+        g.A = c->E3; g.a_m = im1(mm); g.a_k = im1(1);
+        g.B = c->E3; g.b_k = im2((int)m, m, 1); g.b_n = im1(mm);
+        g.C = rho_nnn; g.c_m = im1(d * d); g.c_n = im1(1);
+        if ((e = gemm_run(c, g)) != cudaSuccess) return e;
+      }
     }
   }
   energy_k<<<1, 1, 0, st>>>(c->rho, rho_nnn, J1, J2, c->nn_plain ? 1 : 0, c->e_d, c->err);

@@ -364,12 +364,21 @@ static cudaError_t energy_vjp(qrctm_ctx* c, const GradLayout& L, const double* C
     trace_phys2_k<<<1184, 256, 0, s>>>(Co, Ct, d, mm);
     note_launch();
     if ((e = gemm_run(c, f_P)) != cudaSuccess) return e;
-    if ((e = gemm_run(c, f_rn)) != cudaSuccess) return e;
+    const bool tr = trace_pairs_ok(d * d);
+    if (tr) {
+      if ((e = trace_pairs(P, d * d, m, c->partials, rho_nnn, s)) != cudaSuccess) return e;
+    } else if ((e = gemm_run(c, f_rn)) != cudaSuccess) {
+      return e;
+    }
     // ---- reverse (2x2 patch) ----
     rho_bar_k<<<1, 32, 0, s>>>(rho_nnn, 1, 2.0 * J2, L.rhob + 16);
     note_launch();
-    if ((e = gemm_vjp(c, f_rn, L.rhob + 16, L.Pb, nullptr, false, false)) != cudaSuccess) return e;
-    if ((e = gemm_vjp(c, f_rn, L.rhob + 16, nullptr, L.Pb, false, true)) != cudaSuccess) return e;
+    if (tr) {
+      if ((e = trace_pairs_vjp(P, d * d, m, L.rhob + 16, L.Pb, s)) != cudaSuccess) return e;
+    } else {
+      if ((e = gemm_vjp(c, f_rn, L.rhob + 16, L.Pb, nullptr, false, false)) != cudaSuccess) return e;
+      if ((e = gemm_vjp(c, f_rn, L.rhob + 16, nullptr, L.Pb, false, true)) != cudaSuccess) return e;
+    }
     // Co and Ct cotangents; Ct = sum_s Co[s][s]
     if ((e = gemm_vjp(c, f_P, L.Pb, L.Z2b, L.Ctb, false, false)) != cudaSuccess) return e;
     add_diag_phys_k<<<1184, 256, 0, s>>>(L.Z2b, L.Ctb, d, mm);
