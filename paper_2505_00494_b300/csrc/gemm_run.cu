@@ -28,16 +28,41 @@ bool zero_map(const IdxMap& m) {
   return true;
 }
 
-// out[b][r][k] (row stride ldk, batch stride ldb) = in[bm(b) + rm(r) + km(k)]
+// out[b][r][k] (row stride ldk, batch stride ldb) = in[bm(b) + rm(r) + km(k)].
+// One warp per piece of an output row (up to 1024 elements, so that a few
+// long rows still spread over the GPU): the row's offset bm(b) + rm(r) is
+// formed once per piece and the K offsets with 32-bit digit divisions (a
+// per-element decomposition of the flat index in 64 bits made the gather
+// instruction bound); rows shorter than 32 are packed R = 32 / nk to a warp.
 __global__ void gather3_f32_k(const double* __restrict__ in, float* __restrict__ out, long long nb,
                               long long nr, long long nk, long long ldk, long long ldb,
                               IdxMap bm, IdxMap rm, IdxMap km) {
-  const long long tot = nb * nr * nk;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long k = e % nk, rb = e / nk, r = rb % nr, b = rb / nr;
-    out[b * ldb + r * ldk + k] =
-        static_cast<float>(in[map_off(bm, b) + map_off(rm, r) + map_off(km, k)]);
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long rows = nb * nr;
+  if (nk >= 32) {
+    constexpr long long kChunk = 1024;
+    const long long nch = (nk + kChunk - 1) / kChunk;
+    for (long long t = warp0; t < rows * nch; t += nwarps) {
+      const long long rb = t / nch, k0 = (t - rb * nch) * kChunk;
+      const long long r = rb % nr, b = rb / nr;
+      const long long base = map_off(bm, b) + map_off(rm, r);
+      float* o = out + b * ldb + r * ldk;
+      const unsigned kend = (unsigned)std::min(nk, k0 + kChunk);
+      for (unsigned k = (unsigned)k0 + lane; k < kend; k += 32)
+        o[k] = static_cast<float>(in[base + map_off32(km, k)]);
+    }
+  } else {
+    const int R = 32 / (int)nk, sub = lane / (int)nk, kk = lane % (int)nk;
+    const long long koff = map_off32(km, (unsigned)kk);
+    for (long long rb0 = warp0 * R; rb0 < rows; rb0 += nwarps * R) {
+      const long long rb = rb0 + sub;
+      if (sub >= R || rb >= rows) continue;
+      const long long r = rb % nr, b = rb / nr;
+      out[b * ldb + r * ldk + kk] =
+          static_cast<float>(in[map_off(bm, b) + map_off(rm, r) + koff]);
+    }
   }
 }
 
