@@ -15,6 +15,7 @@
 #include "tc_gemm.cuh"
 
 #include <algorithm>
+#include <cstdint>
 
 namespace qrctm {
 
@@ -28,51 +29,216 @@ bool zero_map(const IdxMap& m) {
   return true;
 }
 
-// out[b][r][k] (row stride ldk, batch stride ldb) = in[bm(b) + rm(r) + km(k)].
-// One warp per piece of an output row (up to 1024 elements, so that a few
-// long rows still spread over the GPU): the row's offset bm(b) + rm(r) is
-// formed once per piece and the K offsets with 32-bit digit divisions (a
-// per-element decomposition of the flat index in 64 bits made the gather
-// instruction bound); rows shorter than 32 are packed R = 32 / nk to a warp.
-__global__ void gather3_f32_k(const double* __restrict__ in, float* __restrict__ out, long long nb,
-                              long long nr, long long nk, long long ldk, long long ldb,
-                              IdxMap bm, IdxMap rm, IdxMap km) {
-  const int lane = threadIdx.x & 31;
-  const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const long long rows = nb * nr;
-  if (nk >= 32) {
-    constexpr long long kChunk = 1024;
-    const long long nch = (nk + kChunk - 1) / kChunk;
-    for (long long t = warp0; t < rows * nch; t += nwarps) {
-      const long long rb = t / nch, k0 = (t - rb * nch) * kChunk;
-      const long long r = rb % nr, b = rb / nr;
-      const long long base = map_off(bm, b) + map_off(rm, r);
-      float* o = out + b * ldb + r * ldk;
-      const unsigned kend = (unsigned)std::min(nk, k0 + kChunk);
-      for (unsigned k = (unsigned)k0 + lane; k < kend; k += 32)
-        o[k] = static_cast<float>(in[base + map_off32(km, k)]);
+// ---------------------------------------------------------------------------
+// Operand gathers: out[b][r][k] (row stride ldk, batch stride nr * ldk) =
+// in[bm(b) + rm(r) + km(k)], FP64 -> FP32.  Rows are numbered rb = b nr + r,
+// so that out row rb starts at out + rb * ldk.  Two tilings, chosen by which
+// index runs through the input with unit stride:
+//  * along k (the K index's lowest digit has stride 1): a block takes up to
+//    128 rows x 1024 k; the row offsets and the k offsets are formed once per
+//    block into shared memory and every element costs one load and one store,
+//    lanes along k for both;
+//  * along rows (a digit of the row index has stride 1): the rows are
+//    enumerated in an order v that makes that digit the fastest (two maps of
+//    v: the input offset and the output row); a block reads a 64 (v) x 32 (k)
+//    tile with lanes along v, transposes it through shared memory and writes
+//    it with lanes along k.
+// ---------------------------------------------------------------------------
+constexpr int kGatherThreads = 256;
+constexpr int kKRowsMax = 128, kKCols = 1024;
+constexpr int kRTileR = 64, kRTileK = 32;
+
+__global__ void __launch_bounds__(kGatherThreads)
+    gather_along_k(const double* __restrict__ in, float* __restrict__ out, long long rows,
+                   long long nr, long long nk, long long ldk, int rb_tile, int k_tile,
+                   long long nkt, IdxMap bm, IdxMap rm, IdxMap km) {
+  __shared__ long long roff[kKRowsMax];
+  __shared__ long long koff[kKCols];
+  const long long kt = blockIdx.x % nkt, rt = blockIdx.x / nkt;
+  const long long rb0 = rt * rb_tile, k0 = kt * k_tile;
+  const int nrow = (int)std::min<long long>(rb_tile, rows - rb0);
+  const int ncol = (int)std::min<long long>(k_tile, nk - k0);
+  for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
+    const long long rb = rb0 + i, b = rb / nr;
+    roff[i] = map_off(bm, b) + map_off(rm, rb - b * nr);
+  }
+  for (int j = threadIdx.x; j < ncol; j += blockDim.x)
+    koff[j] = map_off32(km, (unsigned)(k0 + j));
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i < nrow; i += kGatherThreads / 32) {
+    const double* src = in + roff[i];
+    float* dst = out + (rb0 + i) * ldk + k0;
+#pragma unroll 4
+    for (int j = lane; j < ncol; j += 32) dst[j] = static_cast<float>(src[koff[j]]);
+  }
+}
+
+__global__ void __launch_bounds__(kGatherThreads)
+    gather_along_rows(const double* __restrict__ in, float* __restrict__ out, long long rows,
+                      long long nk, long long ldk, long long nkt, IdxMap vin, IdxMap vout,
+                      IdxMap km) {
+  __shared__ float tile[kRTileK][kRTileR + 1];
+  __shared__ long long roff[kRTileR], orow[kRTileR], koff[kRTileK];
+  const long long kt = blockIdx.x % nkt, rt = blockIdx.x / nkt;
+  const long long v0 = rt * kRTileR, k0 = kt * kRTileK;
+  const int nrow = (int)std::min<long long>(kRTileR, rows - v0);
+  const int ncol = (int)std::min<long long>(kRTileK, nk - k0);
+  const int t = threadIdx.x;
+  if (t < kRTileR) {
+    if (t < nrow) {
+      roff[t] = map_off(vin, v0 + t);
+      orow[t] = map_off(vout, v0 + t);
     }
-  } else {
-    const int R = 32 / (int)nk, sub = lane / (int)nk, kk = lane % (int)nk;
-    const long long koff = map_off32(km, (unsigned)kk);
-    for (long long rb0 = warp0 * R; rb0 < rows; rb0 += nwarps * R) {
-      const long long rb = rb0 + sub;
-      if (sub >= R || rb >= rows) continue;
-      const long long r = rb % nr, b = rb / nr;
-      out[b * ldb + r * ldk + kk] =
-          static_cast<float>(in[map_off(bm, b) + map_off(rm, r) + koff]);
+  } else if (t < kRTileR + kRTileK) {
+    if (t - kRTileR < ncol) koff[t - kRTileR] = map_off32(km, (unsigned)(k0 + t - kRTileR));
+  }
+  __syncthreads();
+  const int warp = t >> 5, lane = t & 31;
+#pragma unroll
+  for (int jj = 0; jj < kRTileK / 8; ++jj) {
+    const int j = warp + 8 * jj;
+#pragma unroll
+    for (int h = 0; h < kRTileR / 32; ++h) {
+      const int i = lane + 32 * h;
+      if (j < ncol && i < nrow) tile[j][i] = static_cast<float>(in[roff[i] + koff[j]]);
     }
   }
+  __syncthreads();
+#pragma unroll
+  for (int ii = 0; ii < kRTileR / 8; ++ii) {
+    const int i = warp + 8 * ii;
+    if (i < nrow && lane < ncol) out[orow[i] * ldk + k0 + lane] = tile[lane][i];
+  }
+}
+
+// Merge neighbouring digits that continue one another (stride of the upper =
+// radix x stride of the lower) and drop inner digits of radix 1: the same
+// offsets with fewer divisions.
+IdxMap merge_digits(const IdxMap& m) {
+  IdxMap r{};
+  r.nd = 0;
+  for (int t = 0; t < m.nd; ++t) {
+    const bool last = t == m.nd - 1;
+    if (!last && m.rad[t] == 1) continue;
+    if (r.nd > 0) {
+      const int p = r.nd - 1;
+      const long long run = (long long)r.rad[p] * r.str[p];
+      if (m.str[t] == run && (last || (long long)r.rad[p] * m.rad[t] <= INT32_MAX)) {
+        if (!last) r.rad[p] *= m.rad[t];
+        continue;  // the merged digit is the last one when t is
+      }
+    }
+    r.rad[r.nd] = last ? 1 : m.rad[t];
+    r.str[r.nd] = m.str[t];
+    ++r.nd;
+  }
+  if (r.nd == 0) { r.nd = 1; r.rad[0] = 1; r.str[0] = 0; }
+  return r;
+}
+
+// Explicit digits of the combined row index rb = b nr + r: radix, input
+// stride and output place value of each.  False when a map's lower radices
+// do not divide its index range or the digits are too many for one map.
+struct RowDigits {
+  int nd;
+  long long rad[kMaxDigits], str[kMaxDigits], place[kMaxDigits];
+};
+bool row_digits(const IdxMap& bm, long long nb, const IdxMap& rm, long long nr, RowDigits& d) {
+  d.nd = 0;
+  auto add = [&](const IdxMap& m, long long n, long long place0) {
+    long long prod = 1;
+    for (int t = 0; t < m.nd; ++t) {
+      long long rad = m.rad[t];
+      if (t == m.nd - 1) {
+        if (n % prod != 0) return false;
+        rad = n / prod;
+      }
+      if (rad == 1) continue;
+      if (d.nd == kMaxDigits) return false;
+      d.rad[d.nd] = rad;
+      d.str[d.nd] = m.str[t];
+      d.place[d.nd] = place0 * prod;
+      ++d.nd;
+      prod *= rad;
+    }
+    return prod == n;
+  };
+  return add(rm, nr, 1) && (nb == 1 || add(bm, nb, nr));
+}
+
+// Length of the unit-stride run of a map's lowest digit (1 if none).
+long long unit_run(const IdxMap& m, long long n) {
+  if (m.str[0] != 1 && m.str[0] != -1) return 1;
+  return m.nd == 1 ? n : m.rad[0];
+}
+
+// How one gather runs: the tiling, its grid and the maps it takes.
+struct GatherPlan {
+  bool along_rows;
+  IdxMap bm, rm, km;  // digits merged
+  IdxMap vin, vout;   // along rows: input offset and output row of v
+  long long blocks, nkt;
+  int rb_tile, k_tile;
+};
+
+bool plan_gather(long long nb, long long nr, long long nk, const IdxMap& bm0, const IdxMap& rm0,
+                 const IdxMap& km0, GatherPlan& p) {
+  const long long rows = nb * nr;
+  if (nk > (long long)UINT32_MAX) return false;
+  p.bm = merge_digits(bm0);
+  p.rm = merge_digits(rm0);
+  p.km = merge_digits(km0);
+  // the longest unit-stride run among the row digits
+  RowDigits rd;
+  int u = -1;
+  if (row_digits(p.bm, nb, p.rm, nr, rd))
+    for (int t = 0; t < rd.nd; ++t)
+      if ((rd.str[t] == 1 || rd.str[t] == -1) && (u < 0 || rd.rad[t] > rd.rad[u])) u = t;
+  for (int t = 0; u >= 0 && t < rd.nd; ++t)
+    if (rd.rad[t] > INT32_MAX) u = -1;
+  p.nkt = (nk + kRTileK - 1) / kRTileK;
+  p.blocks = ((rows + kRTileR - 1) / kRTileR) * p.nkt;
+  p.along_rows = u >= 0 && rd.rad[u] > unit_run(p.km, nk) && p.blocks <= INT32_MAX;
+  if (p.along_rows) {
+    // rows in the order: digit u first, then the others from the lowest up
+    p.vin = IdxMap{};
+    p.vout = IdxMap{};
+    p.vin.nd = p.vout.nd = rd.nd;
+    int o = 0;
+    auto put = [&](int t) {
+      p.vin.rad[o] = p.vout.rad[o] = (int)rd.rad[t];
+      p.vin.str[o] = rd.str[t];
+      p.vout.str[o] = rd.place[t];
+      ++o;
+    };
+    put(u);
+    for (int t = 0; t < rd.nd; ++t)
+      if (t != u) put(t);
+    p.rb_tile = kRTileR;
+    p.k_tile = kRTileK;
+    return true;
+  }
+  p.k_tile = (int)std::min<long long>(nk, kKCols);
+  p.rb_tile = std::max(1, std::min(kKRowsMax, 4096 / p.k_tile));
+  p.nkt = (nk + p.k_tile - 1) / p.k_tile;
+  p.blocks = ((rows + p.rb_tile - 1) / p.rb_tile) * p.nkt;
+  return p.blocks <= INT32_MAX;
 }
 
 cudaError_t gather3(const double* in, float* out, long long nb, long long nr, long long nk,
                     long long ldk, const IdxMap& bm, const IdxMap& rm, const IdxMap& km,
                     cudaStream_t s) {
-  const long long tot = nb * nr * nk;
-  if (tot <= 0) return cudaSuccess;
-  gather3_f32_k<<<(unsigned)std::min<long long>((tot + 255) / 256, 16384), 256, 0, s>>>(
-      in, out, nb, nr, nk, ldk, nr * ldk, bm, rm, km);
+  const long long rows = nb * nr;
+  if (rows <= 0 || nk <= 0) return cudaSuccess;
+  GatherPlan p;
+  if (!plan_gather(nb, nr, nk, bm, rm, km, p)) return cudaErrorInvalidValue;
+  if (p.along_rows)
+    gather_along_rows<<<(unsigned)p.blocks, kGatherThreads, 0, s>>>(in, out, rows, nk, ldk,
+                                                                    p.nkt, p.vin, p.vout, p.km);
+  else
+    gather_along_k<<<(unsigned)p.blocks, kGatherThreads, 0, s>>>(
+        in, out, rows, nr, nk, ldk, p.rb_tile, p.k_tile, p.nkt, p.bm, p.rm, p.km);
   note_launch();
   return cudaGetLastError();
 }
