@@ -155,6 +155,16 @@ __global__ void rho_bar_k(const double* rho, int plain, double scale, double* rh
   }
 }
 
+// Q[c m + i] = Q32[c mp + i]: the split QR's FP32 columns widened for the tape.
+__global__ void q32_to_f64_k(const float* __restrict__ Q32, long long mp, double* __restrict__ Q,
+                             long long m, long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < m * n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long col = e / m;
+    Q[e] = static_cast<double>(Q32[col * mp + (e - col * m)]);
+  }
+}
+
 __global__ void trace_phys2_k(const double* __restrict__ Co, double* __restrict__ Ct, int d,
                               long long mm) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < mm;
@@ -205,7 +215,18 @@ static cudaError_t step_fwd_tape(qrctm_ctx* c, const double* Cin, const double* 
                            s)) != cudaSuccess)
     return e;
   if ((e = gemm_run(c, g_ct(c, k, t.Cin, t.Tin, t.ct))) != cudaSuccess) return e;
-  if ((e = householder_qr_f64((int)k.m, k.ch, t.ct, t.Q, t.R, c->qrw, s)) != cudaSuccess) return e;
+  if (c->split_prec) {
+    // the QR the split step itself runs: FP64 panels, TF32x3 blocked updates
+    const long long mp = (k.m + 3) & ~3ll;
+    if ((e = householder_qr_split((int)k.m, k.ch, t.ct, t.R, c->qrw, c->qr32, c->Qc32, false,
+                                  c->tc_part, c->tc_part_elems, s)) != cudaSuccess)
+      return e;
+    q32_to_f64_k<<<nb256(k.m * k.ch), 256, 0, s>>>(c->Qc32, mp, t.Q, k.m, k.ch);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else if ((e = householder_qr_f64((int)k.m, k.ch, t.ct, t.Q, t.R, c->qrw, s)) != cudaSuccess) {
+    return e;
+  }
   if ((e = triu_inverse(t.R, t.Rinv, k.ch, c->err, s)) != cudaSuccess) return e;
   if ((e = gemm_run(c, g_x1(c, k, t.Q, t.Tin, t.X1))) != cudaSuccess) return e;
   if ((e = gemm_run(c, g_ket(c, k, t.X1, c->A, t.Z))) != cudaSuccess) return e;
