@@ -16,7 +16,8 @@ namespace {
 
 // E[i + j m] = (Ct(i,j) + Ct(j,i)) / 2 with Ct(i,j) = X2[rmap(i) + cmap(j)]
 __global__ void sym_corner_dense_k(const double* __restrict__ X2, double* __restrict__ E,
-                                   long long m, IdxMap rmap, IdxMap cmap) {
+                                   long long m, const __grid_constant__ IdxMap rmap,
+                                   const __grid_constant__ IdxMap cmap) {
   const long long tot = m * m;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {

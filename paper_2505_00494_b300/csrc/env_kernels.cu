@@ -932,7 +932,8 @@ __device__ __forceinline__ long long map_off_i(const IdxMap& m, I i) {
 template <bool SPLIT, typename I>
 __global__ void gather_f32_k(const double* __restrict__ in, float* __restrict__ out,
                              float* __restrict__ lo, long long nrows, int ncols,
-                             long long stride, IdxMap rmap, IdxMap cmap) {
+                             long long stride, const __grid_constant__ IdxMap rmap,
+                             const __grid_constant__ IdxMap cmap) {
   const I tot = static_cast<I>(nrows * ncols), nc = static_cast<I>(ncols);
   for (I e = static_cast<I>(blockIdx.x) * blockDim.x + threadIdx.x; e < tot;
        e += static_cast<I>(gridDim.x) * blockDim.x) {
@@ -947,7 +948,8 @@ __global__ void gather_f32_k(const double* __restrict__ in, float* __restrict__ 
 template <bool SPLIT, typename I>
 __global__ void gather_f32f_k(const float* __restrict__ in, float* __restrict__ out,
                               float* __restrict__ lo, long long nrows, int ncols,
-                              long long stride, IdxMap rmap, IdxMap cmap) {
+                              long long stride, const __grid_constant__ IdxMap rmap,
+                              const __grid_constant__ IdxMap cmap) {
   const I tot = static_cast<I>(nrows * ncols), nc = static_cast<I>(ncols);
   for (I e = static_cast<I>(blockIdx.x) * blockDim.x + threadIdx.x; e < tot;
        e += static_cast<I>(gridDim.x) * blockDim.x) {

@@ -34,50 +34,92 @@ bool zero_map(const IdxMap& m) {
 // in[bm(b) + rm(r) + km(k)], FP64 -> FP32.  Rows are numbered rb = b nr + r,
 // so that out row rb starts at out + rb * ldk.  Two tilings, chosen by which
 // index runs through the input with unit stride:
-//  * along k (the K index's lowest digit has stride 1): a block takes up to
-//    128 rows x 1024 k; the row offsets and the k offsets are formed once per
-//    block into shared memory and every element costs one load and one store,
-//    lanes along k for both;
+//  * along k (the K index's lowest digit has stride 1): a block takes about
+//    8192 elements (up to 128 rows x 1024 k); the row offsets and the k
+//    offsets are formed once per block into shared memory and every element
+//    costs one load and one store, lanes along k for both;
 //  * along rows (a digit of the row index has stride 1): the rows are
 //    enumerated in an order v that makes that digit the fastest (two maps of
-//    v: the input offset and the output row); a block reads a 64 (v) x 32 (k)
-//    tile with lanes along v, transposes it through shared memory and writes
-//    it with lanes along k.
+//    v: the input offset and the output row); a block reads a 128 (v) x 32
+//    (k) tile with lanes along v, transposes it through shared memory and
+//    writes it with lanes along k.
+// Both are bound by the latency of their loads, not by their arithmetic: a
+// lane keeps 8 to 16 independent loads in flight, and the per-block offsets
+// use 32-bit digit divisions where the row index fits.
 // ---------------------------------------------------------------------------
 constexpr int kGatherThreads = 256;
-constexpr int kKRowsMax = 128, kKCols = 1024;
-constexpr int kRTileR = 64, kRTileK = 32;
+constexpr int kKRowsMax = 128, kKCols = 1024, kKElems = 8192, kKUnroll = 4;
+constexpr int kRTileR = 128, kRTileK = 32;
 
+// Offset of row rb = b nr + r (kNarrow: 32-bit digit divisions, rb < 2^32).
+template <bool kNarrow>
+__device__ __forceinline__ long long row_offset(const IdxMap& bm, const IdxMap& rm, long long nr,
+                                                long long rb) {
+  if (kNarrow) {
+    const unsigned r32 = (unsigned)rb, n32 = (unsigned)nr, b = r32 / n32;
+    return map_off32(bm, b) + map_off32(rm, r32 - b * n32);
+  }
+  const long long b = rb / nr;
+  return map_off(bm, b) + map_off(rm, rb - b * nr);
+}
+
+template <bool kNarrow>
+__device__ __forceinline__ long long vmap(const IdxMap& m, long long v) {
+  return kNarrow ? map_off32(m, (unsigned)v) : map_off(m, v);
+}
+
+// Lanes along k; each warp takes kKUnroll rows at a time, so that a lane has
+// that many independent loads in flight per k.
+template <bool kNarrow>
 __global__ void __launch_bounds__(kGatherThreads)
     gather_along_k(const double* __restrict__ in, float* __restrict__ out, long long rows,
                    long long nr, long long nk, long long ldk, int rb_tile, int k_tile,
-                   long long nkt, IdxMap bm, IdxMap rm, IdxMap km) {
+                   long long nkt, const __grid_constant__ IdxMap bm,
+                   const __grid_constant__ IdxMap rm, const __grid_constant__ IdxMap km) {
   __shared__ long long roff[kKRowsMax];
   __shared__ long long koff[kKCols];
   const long long kt = blockIdx.x % nkt, rt = blockIdx.x / nkt;
   const long long rb0 = rt * rb_tile, k0 = kt * k_tile;
   const int nrow = (int)std::min<long long>(rb_tile, rows - rb0);
   const int ncol = (int)std::min<long long>(k_tile, nk - k0);
-  for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
-    const long long rb = rb0 + i, b = rb / nr;
-    roff[i] = map_off(bm, b) + map_off(rm, rb - b * nr);
-  }
+  for (int i = threadIdx.x; i < nrow; i += blockDim.x)
+    roff[i] = row_offset<kNarrow>(bm, rm, nr, rb0 + i);
   for (int j = threadIdx.x; j < ncol; j += blockDim.x)
     koff[j] = map_off32(km, (unsigned)(k0 + j));
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = warp; i < nrow; i += kGatherThreads / 32) {
-    const double* src = in + roff[i];
-    float* dst = out + (rb0 + i) * ldk + k0;
-#pragma unroll 4
-    for (int j = lane; j < ncol; j += 32) dst[j] = static_cast<float>(src[koff[j]]);
+  for (int i0 = warp * kKUnroll; i0 < nrow; i0 += (kGatherThreads / 32) * kKUnroll) {
+    const int nu = nrow - i0 < kKUnroll ? nrow - i0 : kKUnroll;
+    const double* src[kKUnroll];
+    float* dst[kKUnroll];
+#pragma unroll
+    for (int u = 0; u < kKUnroll; ++u) {
+      const int i = std::min(i0 + u, nrow - 1);
+      src[u] = in + roff[i];
+      dst[u] = out + (rb0 + i) * ldk + k0;
+    }
+#pragma unroll 2
+    for (int j = lane; j < ncol; j += 32) {
+      const long long ko = koff[j];
+      double v[kKUnroll];
+#pragma unroll
+      for (int u = 0; u < kKUnroll; ++u)
+        if (u < nu) v[u] = src[u][ko];
+#pragma unroll
+      for (int u = 0; u < kKUnroll; ++u)
+        if (u < nu) dst[u][j] = static_cast<float>(v[u]);
+    }
   }
 }
 
+// Lanes along the row order v, a kRTileR x kRTileK tile transposed through
+// shared memory, written with lanes along k.
+template <bool kNarrow>
 __global__ void __launch_bounds__(kGatherThreads)
     gather_along_rows(const double* __restrict__ in, float* __restrict__ out, long long rows,
-                      long long nk, long long ldk, long long nkt, IdxMap vin, IdxMap vout,
-                      IdxMap km) {
+                      long long nk, long long ldk, long long nkt,
+                      const __grid_constant__ IdxMap vin, const __grid_constant__ IdxMap vout,
+                      const __grid_constant__ IdxMap km) {
   __shared__ float tile[kRTileK][kRTileR + 1];
   __shared__ long long roff[kRTileR], orow[kRTileR], koff[kRTileK];
   const long long kt = blockIdx.x % nkt, rt = blockIdx.x / nkt;
@@ -87,8 +129,8 @@ __global__ void __launch_bounds__(kGatherThreads)
   const int t = threadIdx.x;
   if (t < kRTileR) {
     if (t < nrow) {
-      roff[t] = map_off(vin, v0 + t);
-      orow[t] = map_off(vout, v0 + t);
+      roff[t] = vmap<kNarrow>(vin, v0 + t);
+      orow[t] = vmap<kNarrow>(vout, v0 + t);
     }
   } else if (t < kRTileR + kRTileK) {
     if (t - kRTileR < ncol) koff[t - kRTileR] = map_off32(km, (unsigned)(k0 + t - kRTileR));
@@ -105,7 +147,7 @@ __global__ void __launch_bounds__(kGatherThreads)
     }
   }
   __syncthreads();
-#pragma unroll
+#pragma unroll 4
   for (int ii = 0; ii < kRTileR / 8; ++ii) {
     const int i = warp + 8 * ii;
     if (i < nrow && lane < ncol) out[orow[i] * ldk + k0 + lane] = tile[lane][i];
@@ -180,12 +222,14 @@ struct GatherPlan {
   IdxMap vin, vout;   // along rows: input offset and output row of v
   long long blocks, nkt;
   int rb_tile, k_tile;
+  bool narrow;  // row indices below 2^32: 32-bit digit divisions
 };
 
 bool plan_gather(long long nb, long long nr, long long nk, const IdxMap& bm0, const IdxMap& rm0,
                  const IdxMap& km0, GatherPlan& p) {
   const long long rows = nb * nr;
   if (nk > (long long)UINT32_MAX) return false;
+  p.narrow = rows <= (long long)UINT32_MAX;
   p.bm = merge_digits(bm0);
   p.rm = merge_digits(rm0);
   p.km = merge_digits(km0);
@@ -220,7 +264,7 @@ bool plan_gather(long long nb, long long nr, long long nk, const IdxMap& bm0, co
     return true;
   }
   p.k_tile = (int)std::min<long long>(nk, kKCols);
-  p.rb_tile = std::max(1, std::min(kKRowsMax, 4096 / p.k_tile));
+  p.rb_tile = std::max(1, std::min(kKRowsMax, kKElems / p.k_tile));
   p.nkt = (nk + p.k_tile - 1) / p.k_tile;
   p.blocks = ((rows + p.rb_tile - 1) / p.rb_tile) * p.nkt;
   return p.blocks <= INT32_MAX;
@@ -233,12 +277,21 @@ cudaError_t gather3(const double* in, float* out, long long nb, long long nr, lo
   if (rows <= 0 || nk <= 0) return cudaSuccess;
   GatherPlan p;
   if (!plan_gather(nb, nr, nk, bm, rm, km, p)) return cudaErrorInvalidValue;
-  if (p.along_rows)
-    gather_along_rows<<<(unsigned)p.blocks, kGatherThreads, 0, s>>>(in, out, rows, nk, ldk,
-                                                                    p.nkt, p.vin, p.vout, p.km);
-  else
-    gather_along_k<<<(unsigned)p.blocks, kGatherThreads, 0, s>>>(
-        in, out, rows, nr, nk, ldk, p.rb_tile, p.k_tile, p.nkt, p.bm, p.rm, p.km);
+  const unsigned grid = (unsigned)p.blocks;
+  if (p.along_rows) {
+    if (p.narrow)
+      gather_along_rows<true><<<grid, kGatherThreads, 0, s>>>(in, out, rows, nk, ldk, p.nkt,
+                                                              p.vin, p.vout, p.km);
+    else
+      gather_along_rows<false><<<grid, kGatherThreads, 0, s>>>(in, out, rows, nk, ldk, p.nkt,
+                                                               p.vin, p.vout, p.km);
+  } else if (p.narrow) {
+    gather_along_k<true><<<grid, kGatherThreads, 0, s>>>(in, out, rows, nr, nk, ldk, p.rb_tile,
+                                                         p.k_tile, p.nkt, p.bm, p.rm, p.km);
+  } else {
+    gather_along_k<false><<<grid, kGatherThreads, 0, s>>>(in, out, rows, nr, nk, ldk, p.rb_tile,
+                                                          p.k_tile, p.nkt, p.bm, p.rm, p.km);
+  }
   note_launch();
   return cudaGetLastError();
 }

@@ -53,8 +53,9 @@ __global__ void network_boundary_k(int b, const double* __restrict__ a,
 }
 
 // part[blockIdx.x] = sum over this block's share of x[xm(i)] * y[ym(i)], i < n
-__global__ void map_dot_k(const double* __restrict__ x, IdxMap xm, const double* __restrict__ y,
-                          IdxMap ym, long long n, double* __restrict__ part) {
+__global__ void map_dot_k(const double* __restrict__ x, const __grid_constant__ IdxMap xm,
+                          const double* __restrict__ y, const __grid_constant__ IdxMap ym,
+                          long long n, double* __restrict__ part) {
   __shared__ double red[256 / 32];
   double t = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
