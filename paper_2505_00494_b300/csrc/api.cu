@@ -469,7 +469,10 @@ qrctm_status bulk_boundary_warmup(qrctm_ctx* c) {
   return QRCTM_OK;
 }
 
-// First spectrum of the new environment; the context is ready to step.
+}  // namespace
+
+namespace qrctm {
+
 // One QR-CTMRG step, replayed from a CUDA graph: the ~45 launches of a step
 // (cooperative panel launches and memsets included) are captured once per
 // environment bond on a stream of the context and replayed on its stream, so
@@ -519,6 +522,11 @@ cudaError_t qr_step_graph(qrctm_ctx* c) {
   return cudaSuccess;
 }
 
+}  // namespace qrctm
+
+namespace {
+
+// First spectrum of the new environment; the context is ready to step.
 qrctm_status finish_init(qrctm_ctx* c) {
   // The spectrum of the fresh corner is taken at the first convergence test,
   // in the same launches as the then-current corner's (one tridiagonalisation

@@ -134,6 +134,9 @@ cudaError_t spectrum_check(qrctm_ctx* c);
 // Split-precision step (split_step.cu)
 cudaError_t split_prepare_A(qrctm_ctx* c);
 cudaError_t qr_step_split(qrctm_ctx* c);
+// One QR-CTMRG step of the context's precision, in place on (C, T), replayed
+// from the context's CUDA graph (api.cu)
+cudaError_t qr_step_graph(qrctm_ctx* c);
 // Standard step with a full eigendecomposition (eigen_step.cu)
 cudaError_t eigen_step(qrctm_ctx* c, int ci, int co);
 size_t eigen_work_doubles(long long m);

@@ -581,14 +581,22 @@ cudaError_t energy_grad_run(qrctm_ctx* c, double J1, double J2, int mode, int k_
     const int K = k_unroll;
     cudaMemcpyAsync(L.ckC, c->C, sizeof(double) * c2, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(L.ckT, c->T, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s);
+    // the forward sweep keeps only the checkpoints, so it runs the plain step
+    // (the same map, without the tape's stored intermediates) in place on
+    // the context's environment
     for (int i = 1; i <= K; ++i) {
-      if ((e = step_fwd_tape(c, L.ckC + (i - 1) * c2, L.ckT + (i - 1) * mc, L.tape[0])) !=
-          cudaSuccess)
-        return e;
-      cudaMemcpyAsync(L.ckC + i * c2, L.tape[0].Cout, sizeof(double) * c2,
-                      cudaMemcpyDeviceToDevice, s);
-      cudaMemcpyAsync(L.ckT + i * mc, L.tape[0].Tout, sizeof(double) * mc,
-                      cudaMemcpyDeviceToDevice, s);
+      if ((e = qr_step_graph(c)) != cudaSuccess) return e;
+      cudaMemcpyAsync(L.ckC + i * c2, c->C, sizeof(double) * c2, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(L.ckT + i * mc, c->T, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s);
+    }
+    if (c->grad_keep_env) {
+      // the optimiser continues from the environment after the k steps
+      c->spec_valid = false;
+      c->spec_pending = false;
+    } else {
+      cudaMemcpyAsync(c->C, L.ckC, sizeof(double) * c2, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(c->T, L.ckT, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s);
+      c->iters -= K;
     }
     if ((e = energy_vjp(c, L, L.ckC + K * c2, L.ckT + K * mc, J1, J2, L.yC, L.yT, L.Abar,
                         e_dev)) != cudaSuccess)
@@ -604,14 +612,6 @@ cudaError_t energy_grad_run(qrctm_ctx* c, double J1, double J2, int mode, int k_
     }
     iters = K;
     if (fp_resid_out) *fp_resid_out = 0.0;
-    if (c->grad_keep_env) {
-      // the optimiser continues from the environment after the k steps
-      cudaMemcpyAsync(c->C, L.ckC + K * c2, sizeof(double) * c2, cudaMemcpyDeviceToDevice, s);
-      cudaMemcpyAsync(c->T, L.ckT + K * mc, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s);
-      c->iters += K;
-      c->spec_valid = false;
-      c->spec_pending = false;
-    }
   }
   // project onto the C4v subspace
   if ((e = c4v_symmetrize(k.d, k.D, L.Abar, grad, s)) != cudaSuccess) return e;

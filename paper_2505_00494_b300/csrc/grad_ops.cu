@@ -111,6 +111,57 @@ __global__ void triu_inverse_k(const double* __restrict__ R, double* __restrict_
   }
 }
 
+// The same inverse for n <= kTriuSmemMaxN: the block's part of R (rows and
+// columns up to its last column) is staged column-major in shared memory with
+// the reciprocals of its diagonal, and each warp solves R x = e_j by columns:
+// x_l = -p_l / R[l][l] for l = j, j-1, ..., 0, then p_i += R[i][l] x_l for
+// every i < l, lanes over i.  A step costs one FP64 instruction per 32 rows
+// and no reduction, where the row form above waits on global loads and a
+// shuffle tree at every step.
+constexpr int kTriuSmemMaxN = 160, kTriuNT = (kTriuSmemMaxN + 31) / 32;
+
+__global__ void triu_inverse_smem_k(const double* __restrict__ R, double* __restrict__ X, int n,
+                                    int* err) {
+  extern __shared__ double tri_sm[];
+  const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j0 = blockIdx.x * warps, jmax = min(n - 1, j0 + warps - 1), ld = jmax + 1;
+  double* sRt = tri_sm;               // [l][i] = R[i][l], i <= l <= jmax
+  double* invd = tri_sm + ld * ld;    // 1 / R[l][l]
+  for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) {
+    const int i = e / ld, l = e - i * ld;
+    if (l >= i) sRt[l * ld + i] = R[(long long)i * n + l];
+  }
+  for (int l = threadIdx.x; l < ld; l += blockDim.x) {
+    const double r = R[(long long)l * n + l];
+    if (!(r != 0.0)) atomicOr(err, ERRF_NUMERIC);
+    invd[l] = 1.0 / r;
+  }
+  __syncthreads();
+  const int j = j0 + warp;
+  if (j >= n) return;
+  for (int i = j + 1 + lane; i < n; i += 32) X[(long long)i * n + j] = 0.0;
+  double p[kTriuNT];
+#pragma unroll
+  for (int t = 0; t < kTriuNT; ++t) p[t] = 0.0;
+  for (int l = j; l >= 0; --l) {
+    const int slot = l >> 5;
+    double own = 0.0;
+#pragma unroll
+    for (int t = 0; t < kTriuNT; ++t)
+      if (t == slot) own = p[t];
+    const double xv = (l == j) ? invd[j] : -own * invd[l];
+    const double xl = __shfl_sync(0xffffffffu, xv, l & 31);
+    if (lane == 0) X[(long long)l * n + j] = xl;
+#pragma unroll
+    for (int t = 0; t < kTriuNT; ++t) {
+      if (32 * t < l) {
+        const int i = lane + 32 * t;
+        if (i < l) p[t] = fma(sRt[l * ld + i], xl, p[t]);
+      }
+    }
+  }
+}
+
 // S[i][j] = M[i][j] (i <= j), M[j][i] (i > j)
 __global__ void copyutl_k(const double* __restrict__ M, double* __restrict__ S, int n) {
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -142,11 +193,21 @@ __global__ void norm_vjp_k(const double* __restrict__ y, const double* __restric
                            double* __restrict__ xbar, long long n, const double* dot_parts,
                            const double* nrm_parts, int nparts, bool acc) {
   __shared__ double sdot, sinv;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    // one warp, the same fixed order in every block
     double d = 0.0, q = 0.0;
-    for (int i = 0; i < nparts; ++i) { d += dot_parts[i]; q += nrm_parts[i]; }
-    sdot = d;
-    sinv = 1.0 / sqrt(q);
+    for (int i = threadIdx.x; i < nparts; i += 32) {
+      d += dot_parts[i];
+      q += nrm_parts[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      d += __shfl_xor_sync(0xffffffffu, d, o);
+      q += __shfl_xor_sync(0xffffffffu, q, o);
+    }
+    if (threadIdx.x == 0) {
+      sdot = d;
+      sinv = 1.0 / sqrt(q);
+    }
   }
   __syncthreads();
   const double dt = sdot, inv = sinv;
@@ -178,7 +239,18 @@ cudaError_t dot_partials(const double* x, const double* y, long long n, double* 
 }
 
 cudaError_t triu_inverse(const double* R, double* X, int n, int* err, cudaStream_t s) {
-  triu_inverse_k<<<(n + 3) / 4, 128, 0, s>>>(R, X, n, err);
+  if (n <= kTriuSmemMaxN) {
+    const size_t smem = sizeof(double) * ((size_t)n * n + n);
+    cudaError_t e = device_once((const void*)triu_inverse_smem_k, [] {
+      return cudaFuncSetAttribute(
+          triu_inverse_smem_k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+          (int)(sizeof(double) * (kTriuSmemMaxN * kTriuSmemMaxN + kTriuSmemMaxN)));
+    });
+    if (e != cudaSuccess) return e;
+    triu_inverse_smem_k<<<(n + 3) / 4, 128, smem, s>>>(R, X, n, err);
+  } else {
+    triu_inverse_k<<<(n + 3) / 4, 128, 0, s>>>(R, X, n, err);
+  }
   note_launch();
   return cudaGetLastError();
 }
