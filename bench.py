@@ -901,6 +901,8 @@ def main():
             torch.cuda.synchronize()
             extras["split_energy_grad_implicit_ms"] = 1e3 * (time.perf_counter() - t0)
             extras["split_energy_grad_applications"] = cctx.grad_iterations
+            extras["split_energy_grad_adjoint_residual"] = cctx.grad_residual
+            extras["split_grad_fixed_point_residual"] = cctx.grad_fixed_point_residual
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             _, gsu = cctx.energy_grad(1.0, 0.5, mode="unroll", k_unroll=20)

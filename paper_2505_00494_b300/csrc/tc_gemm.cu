@@ -38,6 +38,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
 }
 
 
+// alpha * (double) x with no FP64 multiply for alpha = +-1 (alpha is the same
+// for the whole launch): on B300 the widening itself already issues at the
+// FP64 rate
+__device__ __forceinline__ double widen_scaled(double alpha, float x) {
+  if (alpha == 1.0) return static_cast<double>(x);
+  if (alpha == -1.0) return static_cast<double>(-x);
+  return alpha * static_cast<double>(x);
+}
+
 // ---------------------------------------------------------------------------
 // Epilogue (both kernels).  The 128 epilogue threads first fill the tile's
 // output offsets in shared memory (one row each, columns strided); each warp
@@ -140,10 +149,10 @@ __device__ __forceinline__ void epi_rows(const TcArgs& a, uint32_t acc, uint32_t
             for (int u = 0; u < 16; ++u) r[u] = (j0 + u < nv) ? p[o[u]] : 0.0;
 #pragma unroll
             for (int u = 0; u < 16; ++u)
-              r[u] = fma(a.beta, r[u], a.alpha * static_cast<double>(v[j0 + u]));
+              r[u] = fma(a.beta, r[u], widen_scaled(a.alpha, v[j0 + u]));
           } else {
 #pragma unroll
-            for (int u = 0; u < 16; ++u) r[u] = a.alpha * static_cast<double>(v[j0 + u]);
+            for (int u = 0; u < 16; ++u) r[u] = widen_scaled(a.alpha, v[j0 + u]);
           }
 #pragma unroll
           for (int u = 0; u < 16; ++u)
@@ -258,7 +267,7 @@ __device__ __forceinline__ void epi_rows(const TcArgs& a, uint32_t acc, uint32_t
           double* p = static_cast<double*>(a.C);
           double r[8];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) r[u] = a.alpha * static_cast<double>(x[u]);
+          for (int u = 0; u < 8; ++u) r[u] = widen_scaled(a.alpha, x[u]);
           if (a.beta != 0.0) {
             double old[8];
 #pragma unroll
@@ -614,11 +623,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
-// out(b,m,n) = alpha * sum_z part[b][z][m][n] + beta * out.  The partials are
-// added in a fixed order (z = 0, 1, ...) by compensated FP32 arithmetic
-// (TwoSum per term, Knuth): sh + se carries the sum to ~2^-48 of its
-// magnitude, like an FP64 sum, at FP32 speed (B300's FP64 pipe would bound
-// this pass).  I: the flat index type (32-bit whenever batch*M*N fits).
+// out(b,m,n) = alpha * sum_z part[b][z][m][n] + beta * out.  Lanes run along
+// 32 consecutive outputs (coalesced); the 8 warps of a block form 8 / wz
+// output groups of wz warps each, the wz warps of a group striding over z.
+// Each lane adds its terms in a fixed order by compensated FP32 arithmetic
+// (TwoSum per term, Knuth: sh + se carries the sum to ~2^-48 of its
+// magnitude without the FP64 pipe) and the group's warps meet in FP64 in
+// warp order.  wz = 1 for a large output (each warp owns its outputs, no
+// barrier); wz up to 8 for a thin output with a long K, whose few outputs
+// would otherwise leave a handful of threads walking hundreds of partials
+// each.  I: the flat index type (32-bit whenever batch*M*N fits).
+constexpr int kReduceWarps = 8;
+
 __device__ __forceinline__ void two_sum_add(float& sh, float& se, float x) {
   const float t = sh + x;
   const float bp = t - sh;
@@ -627,36 +643,64 @@ __device__ __forceinline__ void two_sum_add(float& sh, float& se, float x) {
 }
 
 template <typename I>
-__global__ void tc_splitk_reduce(const TcArgs a, int batch) {
+__device__ __forceinline__ long long out_off(const IdxMap& m, I i) {
+  return sizeof(I) == 4 ? map_off32(m, static_cast<unsigned>(i))
+                        : map_off(m, static_cast<long long>(i));
+}
+
+template <typename I>
+__device__ __forceinline__ void reduce_store(const TcArgs& a, I e, I MN, I N, double acc) {
+  const I b = e / MN, r = e - b * MN, m = r / N, n = r - m * N;
+  const long long off = out_off(a.c_b, b) + out_off(a.c_m, m) + out_off(a.c_n, n);
+  const double v = a.alpha == 1.0 ? acc : a.alpha * acc;
+  if (a.c_fp64) {
+    double* o = static_cast<double*>(a.C) + off;
+    const double w = a.beta != 0.0 ? fma(a.beta, *o, v) : v;
+    *o = w;
+    if (a.C32) a.C32[out_off(a.c32_m, m) + out_off(a.c32_n, n)] = static_cast<float>(w);
+  } else {
+    float* o = static_cast<float*>(a.C) + off;
+    *o = static_cast<float>(a.beta != 0.0 ? fma(a.beta, static_cast<double>(*o), v) : v);
+  }
+}
+
+template <typename I>
+__global__ void __launch_bounds__(32 * kReduceWarps)
+    tc_splitk_reduce(const __grid_constant__ TcArgs a, int batch, int wz) {
+  __shared__ double red[kReduceWarps][2][32];
   const I N = static_cast<I>(a.N), MN = static_cast<I>(a.M) * N, tot = MN * static_cast<I>(batch);
-  const int kz = a.ksplit;
-  for (I e = static_cast<I>(blockIdx.x) * blockDim.x + threadIdx.x; e < tot;
-       e += static_cast<I>(gridDim.x) * blockDim.x) {
-    const I b = e / MN, r = e - b * MN, m = r / N, n = r - m * N;
-    const float* p = a.part + (long long)b * kz * (long long)MN + r;
+  const int kz = a.ksplit, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int groups = kReduceWarps / wz, g = warp / wz, zw = warp - g * wz;
+  const I step = static_cast<I>(gridDim.x) * groups * 32;
+  for (I base = static_cast<I>(blockIdx.x) * groups * 32; base < tot; base += step) {
+    const I e = base + g * 32 + lane;
     float sh = 0.f, se = 0.f;
-    int z = 0;
-    for (; z + 4 <= kz; z += 4) {
-      float x[4];
+    if (e < tot) {
+      const I b = e / MN, r = e - b * MN;
+      const float* p = a.part + (long long)b * kz * (long long)MN + r;
+      int z = zw;
+      for (; z + 3 * wz < kz; z += 4 * wz) {
+        float x[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) x[u] = __ldcg(p + (long long)(z + u) * MN);
+        for (int u = 0; u < 4; ++u) x[u] = __ldcg(p + (long long)(z + u * wz) * MN);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) two_sum_add(sh, se, x[u]);
+        for (int u = 0; u < 4; ++u) two_sum_add(sh, se, x[u]);
+      }
+      for (; z < kz; z += wz) two_sum_add(sh, se, __ldcg(p + (long long)z * MN));
     }
-    for (; z < kz; ++z) two_sum_add(sh, se, __ldcg(p + (long long)z * MN));
-    const double acc = static_cast<double>(sh) + static_cast<double>(se);
-    const long long off = map_off(a.c_b, b) + map_off(a.c_m, m) + map_off(a.c_n, n);
-    double v = a.alpha * acc;
-    if (a.c_fp64) {
-      double* o = static_cast<double*>(a.C) + off;
-      if (a.beta != 0.0) v += a.beta * *o;
-      *o = v;
-      if (a.C32) a.C32[map_off(a.c32_m, m) + map_off(a.c32_n, n)] = static_cast<float>(v);
-    } else {
-      float* o = static_cast<float*>(a.C) + off;
-      if (a.beta != 0.0) v += a.beta * static_cast<double>(*o);
-      *o = static_cast<float>(v);
+    if (wz == 1) {
+      if (e < tot) reduce_store(a, e, MN, N, static_cast<double>(sh) + static_cast<double>(se));
+      continue;
     }
+    red[warp][0][lane] = static_cast<double>(sh);
+    red[warp][1][lane] = static_cast<double>(se);
+    __syncthreads();
+    if (zw == 0 && e < tot) {
+      double acc = red[warp][0][lane] + red[warp][1][lane];
+      for (int w = 1; w < wz; ++w) acc += red[warp + w][0][lane] + red[warp + w][1][lane];
+      reduce_store(a, e, MN, N, acc);
+    }
+    __syncthreads();
   }
 }
 
@@ -795,11 +839,17 @@ cudaError_t launch_bn(const TcGemm& g, cudaStream_t s) {
   note_launch();
   if (ksplit > 1 && !g.partials_only) {
     const long long tot = g.M * g.N * std::max(1, g.batch);
-    const unsigned blocks = (unsigned)std::min<long long>((tot + 255) / 256, 4096);
+    // warps over z only while the outputs alone would not fill the GPU
+    int wz = 1;
+    if (tot < 32ll * kReduceWarps * 4 * device_sm_count())
+      while (wz < kReduceWarps && wz < ksplit) wz *= 2;
+    const long long per_block = 32ll * (kReduceWarps / wz);
+    const unsigned blocks = (unsigned)std::min<long long>((tot + per_block - 1) / per_block, 8192);
     if (tot < (1ll << 31))
-      tc_splitk_reduce<unsigned><<<blocks, 256, 0, s>>>(a, std::max(1, g.batch));
+      tc_splitk_reduce<unsigned><<<blocks, 32 * kReduceWarps, 0, s>>>(a, std::max(1, g.batch), wz);
     else
-      tc_splitk_reduce<unsigned long long><<<blocks, 256, 0, s>>>(a, std::max(1, g.batch));
+      tc_splitk_reduce<unsigned long long>
+          <<<blocks, 32 * kReduceWarps, 0, s>>>(a, std::max(1, g.batch), wz);
     note_launch();
   }
   return cudaGetLastError();
