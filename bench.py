@@ -929,8 +929,12 @@ def main():
             extras["split_grad_fixed_point_residual"] = cctx.grad_fixed_point_residual
             torch.cuda.synchronize()
             t0 = time.perf_counter()
+            # an NVTX range for launch lists of the gradient alone
+            # (ncu --nvtx --nvtx-include "split_grad_unroll20/")
+            torch.cuda.nvtx.range_push("split_grad_unroll20")
             _, gsu = cctx.energy_grad(1.0, 0.5, mode="unroll", k_unroll=20)
             torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
             extras["split_energy_grad_unroll20_ms"] = 1e3 * (time.perf_counter() - t0)
             extras["split_energy_grad_ms"] = extras["split_energy_grad_unroll20_ms"]
         cctx.close()

@@ -177,6 +177,74 @@ int device_sm_count() {
   return n;
 }
 
+// Tiny outputs (M, N <= kThinMax, one batch entry, long K: a reduced density
+// matrix or its trace partner over the whole environment): the tile kernel
+// would compute a 64 x 48 tile for at most 16 useful entries.  Here each
+// thread accumulates all M x N entries over a grid-stride range of k (the m
+// and n offsets formed once), the block sums its threads in a fixed order
+// into part[block][M N], and one more block adds the blocks' sums in block
+// order and applies alpha, beta and the output maps.
+constexpr int kThinMax = 4, kThinThreads = 256;
+
+__global__ void __launch_bounds__(kThinThreads)
+    gemm_f64_thin_k(const __grid_constant__ Gemm g, double* __restrict__ part) {
+  __shared__ double red[kThinThreads / 32][kThinMax * kThinMax];
+  const int M = (int)g.M, N = (int)g.N;
+  long long am[kThinMax], bn[kThinMax];
+#pragma unroll
+  for (int i = 0; i < kThinMax; ++i) {
+    am[i] = i < M ? map_off(g.a_m, i) : 0;
+    bn[i] = i < N ? map_off(g.b_n, i) : 0;
+  }
+  double acc[kThinMax][kThinMax];
+#pragma unroll
+  for (int i = 0; i < kThinMax; ++i)
+#pragma unroll
+    for (int j = 0; j < kThinMax; ++j) acc[i][j] = 0.0;
+  const bool k32 = g.K <= (long long)UINT32_MAX;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < g.K;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long ak = k32 ? map_off32(g.a_k, (unsigned)k) : map_off(g.a_k, k);
+    const long long bk = k32 ? map_off32(g.b_k, (unsigned)k) : map_off(g.b_k, k);
+    double a[kThinMax], b[kThinMax];
+#pragma unroll
+    for (int i = 0; i < kThinMax; ++i) {
+      a[i] = i < M ? g.A[am[i] + ak] : 0.0;
+      b[i] = i < N ? g.B[bk + bn[i]] : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < kThinMax; ++i)
+#pragma unroll
+      for (int j = 0; j < kThinMax; ++j)
+        if (i < M && j < N) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < kThinMax; ++i)
+#pragma unroll
+    for (int j = 0; j < kThinMax; ++j) {
+      double v = acc[i][j];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][i * kThinMax + j] = v;
+    }
+  __syncthreads();
+  if (threadIdx.x < kThinMax * kThinMax) {
+    double v = 0.0;
+    for (int w = 0; w < kThinThreads / 32; ++w) v += red[w][threadIdx.x];
+    part[(long long)blockIdx.x * kThinMax * kThinMax + threadIdx.x] = v;
+  }
+}
+
+__global__ void gemm_f64_thin_finish_k(const __grid_constant__ Gemm g, const double* part,
+                                       int blocks) {
+  const int t = threadIdx.x, i = t / kThinMax, j = t % kThinMax;
+  if (i >= g.M || j >= g.N) return;
+  double v = 0.0;
+  for (int b = 0; b < blocks; ++b) v += part[(long long)b * kThinMax * kThinMax + t];
+  double* o = g.C + map_off(g.c_m, i) + map_off(g.c_n, j);
+  *o = g.beta != 0.0 ? fma(g.beta, *o, g.alpha * v) : g.alpha * v;
+}
+
 static unsigned long long g_launches = 0;
 void note_launch(unsigned long long n) { __atomic_fetch_add(&g_launches, n, __ATOMIC_RELAXED); }
 unsigned long long launches_so_far() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
@@ -216,6 +284,17 @@ cudaError_t gemm_f64_launch(const Gemm& g, cudaStream_t s) {
 
 cudaError_t gemm_f64(const Gemm& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+  if (g.batch == 1 && g.M <= kThinMax && g.N <= kThinMax && g.K >= 16384 && g.part != nullptr) {
+    const int blocks = (int)std::min<long long>(
+        std::min<long long>(2ll * device_sm_count(), (g.K + kThinThreads - 1) / kThinThreads),
+        g.part_elems / (kThinMax * kThinMax));
+    if (blocks >= 1) {
+      gemm_f64_thin_k<<<blocks, kThinThreads, 0, s>>>(g, g.part);
+      gemm_f64_thin_finish_k<<<1, kThinMax * kThinMax, 0, s>>>(g, g.part, blocks);
+      note_launch(2);
+      return cudaGetLastError();
+    }
+  }
   // the narrower tile where it leaves fewer idle columns in the last N tile
   const long long idle64 = (g.N + 63) / 64 * 64 - g.N, idle48 = (g.N + 47) / 48 * 48 - g.N;
   if (idle48 < idle64) return gemm_f64_launch<48>(g, s);

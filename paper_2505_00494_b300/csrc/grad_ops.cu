@@ -287,19 +287,23 @@ cudaError_t qr_vjp(qrctm_ctx* c, int m, int n, const double* Q, const double* R,
     g.B = R; g.b_k = im1(1); g.b_n = im1(n);
     g.C = Ms; g.c_m = im1(n); g.c_n = im1(1);
     if ((e = gemm_f64(g, s)) != cudaSuccess) return e;
-    // Ms -= Q^T Qbar
+    // Ms -= Q^T Qbar (on the TF32x3 engine in a split context: Q has
+    // orthonormal columns, so this product adds no more than the rounding
+    // its operands already carry)
     g = gemm_ctx(c);
     g.M = n; g.N = n; g.K = m;
     g.A = Q; g.a_m = im1(m); g.a_k = im1(1);
     g.B = Qbar; g.b_k = im1(1); g.b_n = im1(m);
     g.C = Ms; g.c_m = im1(n); g.c_n = im1(1);
     g.alpha = -1.0; g.beta = 1.0;
-    if ((e = gemm_f64(g, s)) != cudaSuccess) return e;
+    if ((e = gemm_run(c, g)) != cudaSuccess) return e;
   }
   copyutl_k<<<nb256((long long)n * n), 256, 0, s>>>(Ms, Ss, n);
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  // Bs = Qbar + Q Ss   (column-major m x n)
+  // Bs = Qbar + Q Ss   (column-major m x n; TF32x3 in a split context, as
+  // above; the product with R^{-T} below stays FP64, where the conditioning
+  // of R would amplify rounding)
   if ((e = cudaMemcpyAsync(Bs, Qbar, sizeof(double) * (size_t)m * n, cudaMemcpyDeviceToDevice,
                            s)) != cudaSuccess)
     return e;
@@ -310,7 +314,7 @@ cudaError_t qr_vjp(qrctm_ctx* c, int m, int n, const double* Q, const double* R,
     g.B = Ss; g.b_k = im1(n); g.b_n = im1(1);
     g.C = Bs; g.c_m = im1(1); g.c_n = im1(m);
     g.beta = 1.0;
-    if ((e = gemm_f64(g, s)) != cudaSuccess) return e;
+    if ((e = gemm_run(c, g)) != cudaSuccess) return e;
   }
   // Mbar[i][j] = sum_l Bs[i][l] Rinv[j][l]   (column-major m x n)
   {
