@@ -17,6 +17,25 @@ namespace {
 
 constexpr int BM = 64, BK = 16, NT = 256;
 
+// Element off of an operand stored as FP64, or as FP32 when f32 (the
+// descriptor's storage flags; uniform over a launch).
+__device__ __forceinline__ double ld_op(const double* p, bool f32, long long off) {
+  return f32 ? static_cast<double>(reinterpret_cast<const float*>(p)[off]) : p[off];
+}
+
+// C[off] = v + beta C[off] in the result's storage type.
+__device__ __forceinline__ void st_c(const Gemm& g, long long off, double v) {
+  if (g.c_f32) {
+    float* q = reinterpret_cast<float*>(g.C) + off;
+    if (g.beta != 0.0) v += g.beta * static_cast<double>(*q);
+    *q = static_cast<float>(v);
+  } else {
+    double* q = g.C + off;
+    if (g.beta != 0.0) v += g.beta * *q;
+    *q = v;
+  }
+}
+
 // splits > 1 (batch == 1 only): CTA z handles K range [z*kc, (z+1)*kc) and
 // writes its raw sums to g.part[z][M][N].  BN = 64 (4 x 4 per thread) or 48
 // (4 x 3: for N a multiple of 48, such as chi = 144, no column of a tile idles).
@@ -65,14 +84,14 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(Gemm g, int splits, long l
         int e = tid + NT * q;
         int r = e % BM, kk = e / BM;
         long long ro = aRow[r], ko = aK[kk];
-        As[kk][r] = (ro >= 0 && ko >= 0) ? g.A[aB + ro + ko] : 0.0;
+        As[kk][r] = (ro >= 0 && ko >= 0) ? ld_op(g.A, g.a_f32, aB + ro + ko) : 0.0;
       }
 #pragma unroll
       for (int q = 0; q < (BN * BK) / NT; ++q) {
         int e = tid + NT * q;
         int c = e % BN, kk = e / BN;
         long long co = bCol[c], ko = bK[kk];
-        Bs[kk][c] = (co >= 0 && ko >= 0) ? g.B[bB + co + ko] : 0.0;
+        Bs[kk][c] = (co >= 0 && ko >= 0) ? ld_op(g.B, g.b_f32, bB + co + ko) : 0.0;
       }
       __syncthreads();
 #pragma unroll
@@ -112,10 +131,7 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(Gemm g, int splits, long l
       for (int j = 0; j < TN; ++j) {
         long long n = n0 + tx + 16 * j;
         if (n >= g.N) continue;
-        double* p = g.C + cB + ro + map_off(g.c_n, n);
-        double v = g.alpha * acc[i][j];
-        if (g.beta != 0.0) v += g.beta * *p;
-        *p = v;
+        st_c(g, cB + ro + map_off(g.c_n, n), g.alpha * acc[i][j]);
       }
     }
   }
@@ -139,10 +155,7 @@ __global__ void splitk_reduce_kernel(Gemm g, int splits) {
     for (; z < splits; ++z) s0 += g.part[(long long)z * MN + e];
     const double s = (s0 + s1) + (s2 + s3);
     const long long m = e / g.N, n = e % g.N;
-    double* p = g.C + map_off(g.c_m, m) + map_off(g.c_n, n);
-    double v = g.alpha * s;
-    if (g.beta != 0.0) v += g.beta * *p;
-    *p = v;
+    st_c(g, map_off(g.c_m, m) + map_off(g.c_n, n), g.alpha * s);
   }
 }
 
@@ -209,8 +222,8 @@ __global__ void __launch_bounds__(kThinThreads)
     double a[kThinMax], b[kThinMax];
 #pragma unroll
     for (int i = 0; i < kThinMax; ++i) {
-      a[i] = i < M ? g.A[am[i] + ak] : 0.0;
-      b[i] = i < N ? g.B[bk + bn[i]] : 0.0;
+      a[i] = i < M ? ld_op(g.A, g.a_f32, am[i] + ak) : 0.0;
+      b[i] = i < N ? ld_op(g.B, g.b_f32, bk + bn[i]) : 0.0;
     }
 #pragma unroll
     for (int i = 0; i < kThinMax; ++i)
@@ -241,8 +254,7 @@ __global__ void gemm_f64_thin_finish_k(const __grid_constant__ Gemm g, const dou
   if (i >= g.M || j >= g.N) return;
   double v = 0.0;
   for (int b = 0; b < blocks; ++b) v += part[(long long)b * kThinMax * kThinMax + t];
-  double* o = g.C + map_off(g.c_m, i) + map_off(g.c_n, j);
-  *o = g.beta != 0.0 ? fma(g.beta, *o, g.alpha * v) : g.alpha * v;
+  st_c(g, map_off(g.c_m, i) + map_off(g.c_n, j), g.alpha * v);
 }
 
 static unsigned long long g_launches = 0;

@@ -70,9 +70,9 @@ __device__ __forceinline__ long long vmap(const IdxMap& m, long long v) {
 
 // Lanes along k; each warp takes kKUnroll rows at a time, so that a lane has
 // that many independent loads in flight per k.
-template <bool kNarrow>
+template <bool kNarrow, typename T>
 __global__ void __launch_bounds__(kGatherThreads)
-    gather_along_k(const double* __restrict__ in, float* __restrict__ out, long long rows,
+    gather_along_k(const T* __restrict__ in, float* __restrict__ out, long long rows,
                    long long nr, long long nk, long long ldk, int rb_tile, int k_tile,
                    long long nkt, const __grid_constant__ IdxMap bm,
                    const __grid_constant__ IdxMap rm, const __grid_constant__ IdxMap km) {
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kGatherThreads)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i0 = warp * kKUnroll; i0 < nrow; i0 += (kGatherThreads / 32) * kKUnroll) {
     const int nu = nrow - i0 < kKUnroll ? nrow - i0 : kKUnroll;
-    const double* src[kKUnroll];
+    const T* src[kKUnroll];
     float* dst[kKUnroll];
 #pragma unroll
     for (int u = 0; u < kKUnroll; ++u) {
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kGatherThreads)
 #pragma unroll 2
     for (int j = lane; j < ncol; j += 32) {
       const long long ko = koff[j];
-      double v[kKUnroll];
+      T v[kKUnroll];
 #pragma unroll
       for (int u = 0; u < kKUnroll; ++u)
         if (u < nu) v[u] = src[u][ko];
@@ -114,9 +114,9 @@ __global__ void __launch_bounds__(kGatherThreads)
 
 // Lanes along the row order v, a kRTileR x kRTileK tile transposed through
 // shared memory, written with lanes along k.
-template <bool kNarrow>
+template <bool kNarrow, typename T>
 __global__ void __launch_bounds__(kGatherThreads)
-    gather_along_rows(const double* __restrict__ in, float* __restrict__ out, long long rows,
+    gather_along_rows(const T* __restrict__ in, float* __restrict__ out, long long rows,
                       long long nk, long long ldk, long long nkt,
                       const __grid_constant__ IdxMap vin, const __grid_constant__ IdxMap vout,
                       const __grid_constant__ IdxMap km) {
@@ -270,9 +270,10 @@ bool plan_gather(long long nb, long long nr, long long nk, const IdxMap& bm0, co
   return p.blocks <= INT32_MAX;
 }
 
-cudaError_t gather3(const double* in, float* out, long long nb, long long nr, long long nk,
-                    long long ldk, const IdxMap& bm, const IdxMap& rm, const IdxMap& km,
-                    cudaStream_t s) {
+template <typename T>
+cudaError_t gather3_t(const T* in, float* out, long long nb, long long nr, long long nk,
+                      long long ldk, const IdxMap& bm, const IdxMap& rm, const IdxMap& km,
+                      cudaStream_t s) {
   const long long rows = nb * nr;
   if (rows <= 0 || nk <= 0) return cudaSuccess;
   GatherPlan p;
@@ -280,20 +281,28 @@ cudaError_t gather3(const double* in, float* out, long long nb, long long nr, lo
   const unsigned grid = (unsigned)p.blocks;
   if (p.along_rows) {
     if (p.narrow)
-      gather_along_rows<true><<<grid, kGatherThreads, 0, s>>>(in, out, rows, nk, ldk, p.nkt,
-                                                              p.vin, p.vout, p.km);
+      gather_along_rows<true, T><<<grid, kGatherThreads, 0, s>>>(in, out, rows, nk, ldk, p.nkt,
+                                                                 p.vin, p.vout, p.km);
     else
-      gather_along_rows<false><<<grid, kGatherThreads, 0, s>>>(in, out, rows, nk, ldk, p.nkt,
-                                                               p.vin, p.vout, p.km);
+      gather_along_rows<false, T><<<grid, kGatherThreads, 0, s>>>(in, out, rows, nk, ldk, p.nkt,
+                                                                  p.vin, p.vout, p.km);
   } else if (p.narrow) {
-    gather_along_k<true><<<grid, kGatherThreads, 0, s>>>(in, out, rows, nr, nk, ldk, p.rb_tile,
-                                                         p.k_tile, p.nkt, p.bm, p.rm, p.km);
+    gather_along_k<true, T><<<grid, kGatherThreads, 0, s>>>(in, out, rows, nr, nk, ldk, p.rb_tile,
+                                                            p.k_tile, p.nkt, p.bm, p.rm, p.km);
   } else {
-    gather_along_k<false><<<grid, kGatherThreads, 0, s>>>(in, out, rows, nr, nk, ldk, p.rb_tile,
-                                                          p.k_tile, p.nkt, p.bm, p.rm, p.km);
+    gather_along_k<false, T><<<grid, kGatherThreads, 0, s>>>(
+        in, out, rows, nr, nk, ldk, p.rb_tile, p.k_tile, p.nkt, p.bm, p.rm, p.km);
   }
   note_launch();
   return cudaGetLastError();
+}
+
+// in holds doubles, or floats when f32 (an operand the tape keeps in FP32)
+cudaError_t gather3(const void* in, bool f32, float* out, long long nb, long long nr,
+                    long long nk, long long ldk, const IdxMap& bm, const IdxMap& rm,
+                    const IdxMap& km, cudaStream_t s) {
+  return f32 ? gather3_t(static_cast<const float*>(in), out, nb, nr, nk, ldk, bm, rm, km, s)
+             : gather3_t(static_cast<const double*>(in), out, nb, nr, nk, ldk, bm, rm, km, s);
 }
 
 }  // namespace
@@ -320,9 +329,11 @@ cudaError_t gemm_run_kchunked(qrctm_ctx* c, const Gemm& g, long long kchunk) {
   float* A32 = c->mm32;
   float* B32 = A32 + pad4(nbA * g.M * Ka);
   cudaError_t e;
-  if ((e = gather3(g.A, A32, nbA, g.M, g.K, Ka, g.a_b, g.a_m, g.a_k, c->st)) != cudaSuccess)
+  if ((e = gather3(g.A, g.a_f32, A32, nbA, g.M, g.K, Ka, g.a_b, g.a_m, g.a_k, c->st)) !=
+      cudaSuccess)
     return e;
-  if ((e = gather3(g.B, B32, nbB, g.N, g.K, Ka, g.b_b, g.b_n, g.b_k, c->st)) != cudaSuccess)
+  if ((e = gather3(g.B, g.b_f32, B32, nbB, g.N, g.K, Ka, g.b_b, g.b_n, g.b_k, c->st)) !=
+      cudaSuccess)
     return e;
   // K in chunks (kchunk > 0): every chunk accumulates in FP32 on the tensor
   // cores and is added to the FP64 result by the epilogue (beta = 1 after the
@@ -334,7 +345,7 @@ cudaError_t gemm_run_kchunked(qrctm_ctx* c, const Gemm& g, long long kchunk) {
     t.A = TcOperand{A32 + k0, g.M, kn, Ka, (int)nbA, g.M * Ka};
     t.B = TcOperand{B32 + k0, g.N, kn, Ka, (int)nbB, g.N * Ka};
     t.M = g.M; t.N = g.N; t.K = kn; t.batch = (int)B;
-    t.C = g.C; t.c_fp64 = true;
+    t.C = g.C; t.c_fp64 = !g.c_f32;
     t.c_m = g.c_m; t.c_n = g.c_n; t.c_b = g.c_b;
     t.alpha = g.alpha; t.beta = k0 == 0 ? g.beta : 1.0;
     t.err = c->err;

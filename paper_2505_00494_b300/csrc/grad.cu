@@ -201,6 +201,33 @@ size_t grad_bytes(int d, int D, int chi) { return layout(d, D, chi, true, nullpt
 // ---------------------------------------------------------------------------
 // Forward step with tape, and its reverse pass
 // ---------------------------------------------------------------------------
+// In a split context the tape keeps X1, Z and X2 and their cotangents in
+// FP32: they feed only TF32x3 products, whose FP32 operand copies the gathers
+// would make anyway, and the FP64 values the engine would write are FP32 sums
+// widened exactly.  Half the bytes for the largest tensors of the step.
+static Gemm tape32(const qrctm_ctx* c, Gemm g, bool a, bool b, bool cc) {
+  if (c->mm_split) {
+    g.a_f32 = a;
+    g.b_f32 = b;
+    g.c_f32 = cc;
+  }
+  return g;
+}
+
+// The tape's four contractions through X1, Z, X2 (FP32 in a split context).
+static Gemm x1_t(qrctm_ctx* c, const Dims& k, const StepTape& t) {
+  return tape32(c, g_x1(c, k, t.Q, t.Tin, t.X1), false, false, true);
+}
+static Gemm ket_t(qrctm_ctx* c, const Dims& k, const StepTape& t) {
+  return tape32(c, g_ket(c, k, t.X1, c->A, t.Z), true, false, true);
+}
+static Gemm bra_t(qrctm_ctx* c, const Dims& k, const StepTape& t) {
+  return tape32(c, g_bra(c, k, t.Z, c->A, t.X2), true, false, true);
+}
+static Gemm proj_t(qrctm_ctx* c, const Dims& k, const StepTape& t) {
+  return tape32(c, g_proj(c, k, t.X2, t.Q, t.Traw), true, false, false);
+}
+
 static cudaError_t step_fwd_tape(qrctm_ctx* c, const double* Cin, const double* Tin,
                                  StepTape& t) {
   const Dims k(c);
@@ -228,10 +255,10 @@ static cudaError_t step_fwd_tape(qrctm_ctx* c, const double* Cin, const double* 
     return e;
   }
   if ((e = triu_inverse(t.R, t.Rinv, k.ch, c->err, s)) != cudaSuccess) return e;
-  if ((e = gemm_run(c, g_x1(c, k, t.Q, t.Tin, t.X1))) != cudaSuccess) return e;
-  if ((e = gemm_run(c, g_ket(c, k, t.X1, c->A, t.Z))) != cudaSuccess) return e;
-  if ((e = gemm_run(c, g_bra(c, k, t.Z, c->A, t.X2))) != cudaSuccess) return e;
-  if ((e = gemm_run(c, g_proj(c, k, t.X2, t.Q, t.Traw))) != cudaSuccess) return e;
+  if ((e = gemm_run(c, x1_t(c, k, t))) != cudaSuccess) return e;
+  if ((e = gemm_run(c, ket_t(c, k, t))) != cudaSuccess) return e;
+  if ((e = gemm_run(c, bra_t(c, k, t))) != cudaSuccess) return e;
+  if ((e = gemm_run(c, proj_t(c, k, t))) != cudaSuccess) return e;
   if ((e = sym_edge(t.Traw, t.Ts, k.ch, k.D2, s)) != cudaSuccess) return e;
   if ((e = gemm_run(c, g_y2(c, k, t.Ts, t.R, t.Y2))) != cudaSuccess) return e;
   if ((e = gemm_run(c, g_craw(c, k, t.Y2, t.Q, t.Craw))) != cudaSuccess) return e;
@@ -262,14 +289,14 @@ static cudaError_t step_vjp(qrctm_ctx* c, const StepTape& t, const AdjWork& a,
   // Ts = sym(Traw)
   if ((e = sym_edge(a.Ts, a.Traw, k.ch, k.D2, s)) != cudaSuccess) return e;
   // Traw = X2 Q ; bra ; ket ; X1 = Q^T T
-  if ((e = gemm_vjp(c, g_proj(c, k, t.X2, t.Q, t.Traw), a.Traw, a.X2, a.Q, false, true)) !=
+  if ((e = gemm_vjp(c, proj_t(c, k, t), a.Traw, a.X2, a.Q, false, true)) !=
       cudaSuccess)
     return e;
-  if ((e = gemm_vjp(c, g_bra(c, k, t.Z, c->A, t.X2), a.X2, a.Z, Abar, false, true)) != cudaSuccess)
+  if ((e = gemm_vjp(c, bra_t(c, k, t), a.X2, a.Z, Abar, false, true)) != cudaSuccess)
     return e;
-  if ((e = gemm_vjp(c, g_ket(c, k, t.X1, c->A, t.Z), a.Z, a.X1, Abar, false, true)) != cudaSuccess)
+  if ((e = gemm_vjp(c, ket_t(c, k, t), a.Z, a.X1, Abar, false, true)) != cudaSuccess)
     return e;
-  if ((e = gemm_vjp(c, g_x1(c, k, t.Q, t.Tin, t.X1), a.X1, a.Q, Tbi, true, false)) != cudaSuccess)
+  if ((e = gemm_vjp(c, x1_t(c, k, t), a.X1, a.Q, Tbi, true, false)) != cudaSuccess)
     return e;
   // QR
   if ((e = qr_vjp(c, (int)k.m, k.ch, t.Q, t.R, t.Rinv, a.Q, a.R, a.ct, a.Ms, a.Ss, a.Bs)) !=

@@ -1,7 +1,9 @@
 // Building blocks of the hand-written adjoint (Automatic differentiation
 // paragraph; fixed-point differentiation named in the Discussion).
 //
-// * gemm_vjp: the two cotangent contractions of a forward contraction
+// * gemm_vjp: the two cotangent contractions of a forward contraction (each
+//   cotangent stored like its primal: FP64, or FP32 where the descriptor
+//   says so)
 //     D[b](m,n) = alpha sum_k A[b](m,k) B[b](k,n)
 //   Abar[b](m,k) (+)= alpha sum_n Dbar[b](m,n) B[b](k,n),
 //   Bbar[b](k,n) (+)= alpha sum_m A[b](m,k) Dbar[b](m,n),
@@ -61,6 +63,8 @@ cudaError_t gemm_vjp(qrctm_ctx* c, const Gemm& f, const double* Dbar, double* Ab
       g.B = f.B; g.b_k = f.b_n; g.b_n = f.b_k; g.b_b = f.b_b;
       g.C = Abar; g.c_m = f.a_m; g.c_n = f.a_k; g.c_b = f.a_b;
     }
+    // Dbar is stored like D, Abar like A
+    g.a_f32 = f.c_f32; g.b_f32 = f.b_f32; g.c_f32 = f.a_f32;
     g.alpha = f.alpha;
     g.beta = accA ? 1.0 : 0.0;
     if ((e = gemm_run(c, g)) != cudaSuccess) return e;
@@ -80,6 +84,8 @@ cudaError_t gemm_vjp(qrctm_ctx* c, const Gemm& f, const double* Dbar, double* Ab
       g.B = Dbar; g.b_k = f.c_m; g.b_n = f.c_n; g.b_b = f.c_b;
       g.C = Bbar; g.c_m = f.b_k; g.c_n = f.b_n; g.c_b = f.b_b;
     }
+    // Bbar is stored like B
+    g.a_f32 = f.a_f32; g.b_f32 = f.c_f32; g.c_f32 = f.b_f32;
     g.alpha = f.alpha;
     g.beta = accB ? 1.0 : 0.0;
     if ((e = gemm_run(c, g)) != cudaSuccess) return e;

@@ -105,12 +105,16 @@ struct Gemm {
   double alpha, beta;
   double* part;
   long long part_elems;
+  // the operand (or result) is stored as FP32: its pointer holds floats
+  // (both engines read and write such operands; arithmetic as before)
+  bool a_f32, b_f32, c_f32;
 };
 
 static inline Gemm gemm_init() {
   Gemm g{};
   g.part = nullptr;
   g.part_elems = 0;
+  g.a_f32 = g.b_f32 = g.c_f32 = false;
   g.batch = 1;
   g.a_b = im0(); g.b_b = im0(); g.c_b = im0();
   g.alpha = 1.0; g.beta = 0.0;
