@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 namespace qrctm {
 
@@ -49,7 +50,7 @@ bool zero_map(const IdxMap& m) {
 // ---------------------------------------------------------------------------
 constexpr int kGatherThreads = 256;
 constexpr int kKRowsMax = 128, kKCols = 1024, kKElems = 8192, kKUnroll = 4;
-constexpr int kRTileR = 128, kRTileK = 32;
+constexpr int kRTileElems = 4096;   // elements per row-mode tile
 
 // Offset of row rb = b nr + r (kNarrow: 32-bit digit divisions, rb < 2^32).
 template <bool kNarrow>
@@ -112,45 +113,40 @@ __global__ void __launch_bounds__(kGatherThreads)
   }
 }
 
-// Lanes along the row order v, a kRTileR x kRTileK tile transposed through
-// shared memory, written with lanes along k.
-template <bool kNarrow, typename T>
+// Lanes along the row order v, a TR x (4096 / TR) tile transposed through
+// shared memory, written with lanes along k.  TR (16 ... 128) follows the
+// number of rows: an operand of 36 or 72 rows and a K of 746496 would leave
+// most of a 128-row tile empty.
+template <bool kNarrow, typename T, int TR>
 __global__ void __launch_bounds__(kGatherThreads)
     gather_along_rows(const T* __restrict__ in, float* __restrict__ out, long long rows,
                       long long nk, long long ldk, long long nkt,
                       const __grid_constant__ IdxMap vin, const __grid_constant__ IdxMap vout,
                       const __grid_constant__ IdxMap km) {
-  __shared__ float tile[kRTileK][kRTileR + 1];
-  __shared__ long long roff[kRTileR], orow[kRTileR], koff[kRTileK];
+  constexpr int TK = kRTileElems / TR;
+  __shared__ float tile[TK][TR + 1];
+  __shared__ long long roff[TR], orow[TR], koff[TK];
   const long long kt = blockIdx.x % nkt, rt = blockIdx.x / nkt;
-  const long long v0 = rt * kRTileR, k0 = kt * kRTileK;
-  const int nrow = (int)std::min<long long>(kRTileR, rows - v0);
-  const int ncol = (int)std::min<long long>(kRTileK, nk - k0);
+  const long long v0 = rt * TR, k0 = kt * TK;
+  const int nrow = (int)std::min<long long>(TR, rows - v0);
+  const int ncol = (int)std::min<long long>(TK, nk - k0);
   const int t = threadIdx.x;
-  if (t < kRTileR) {
-    if (t < nrow) {
-      roff[t] = vmap<kNarrow>(vin, v0 + t);
-      orow[t] = vmap<kNarrow>(vout, v0 + t);
-    }
-  } else if (t < kRTileR + kRTileK) {
-    if (t - kRTileR < ncol) koff[t - kRTileR] = map_off32(km, (unsigned)(k0 + t - kRTileR));
+  for (int i = t; i < nrow; i += kGatherThreads) {
+    roff[i] = vmap<kNarrow>(vin, v0 + i);
+    orow[i] = vmap<kNarrow>(vout, v0 + i);
   }
+  for (int j = t; j < ncol; j += kGatherThreads) koff[j] = map_off32(km, (unsigned)(k0 + j));
   __syncthreads();
-  const int warp = t >> 5, lane = t & 31;
 #pragma unroll
-  for (int jj = 0; jj < kRTileK / 8; ++jj) {
-    const int j = warp + 8 * jj;
-#pragma unroll
-    for (int h = 0; h < kRTileR / 32; ++h) {
-      const int i = lane + 32 * h;
-      if (j < ncol && i < nrow) tile[j][i] = static_cast<float>(in[roff[i] + koff[j]]);
-    }
+  for (int q = 0; q < kRTileElems / kGatherThreads; ++q) {   // rows fastest: reads along v
+    const int e = t + kGatherThreads * q, i = e % TR, j = e / TR;
+    if (i < nrow && j < ncol) tile[j][i] = static_cast<float>(in[roff[i] + koff[j]]);
   }
   __syncthreads();
 #pragma unroll 4
-  for (int ii = 0; ii < kRTileR / 8; ++ii) {
-    const int i = warp + 8 * ii;
-    if (i < nrow && lane < ncol) out[orow[i] * ldk + k0 + lane] = tile[lane][i];
+  for (int q = 0; q < kRTileElems / kGatherThreads; ++q) {   // k fastest: writes along k
+    const int e = t + kGatherThreads * q, j = e % TK, i = e / TK;
+    if (i < nrow && j < ncol) out[orow[i] * ldk + k0 + j] = tile[j][i];
   }
 }
 
@@ -222,6 +218,7 @@ struct GatherPlan {
   IdxMap vin, vout;   // along rows: input offset and output row of v
   long long blocks, nkt;
   int rb_tile, k_tile;
+  int tr;       // row-mode tile height
   bool narrow;  // row indices below 2^32: 32-bit digit divisions
 };
 
@@ -241,8 +238,12 @@ bool plan_gather(long long nb, long long nr, long long nk, const IdxMap& bm0, co
       if ((rd.str[t] == 1 || rd.str[t] == -1) && (u < 0 || rd.rad[t] > rd.rad[u])) u = t;
   for (int t = 0; u >= 0 && t < rd.nd; ++t)
     if (rd.rad[t] > INT32_MAX) u = -1;
-  p.nkt = (nk + kRTileK - 1) / kRTileK;
-  p.blocks = ((rows + kRTileR - 1) / kRTileR) * p.nkt;
+  // row-mode tile height: the least padding over the rows (the taller on a tie)
+  p.tr = 128;
+  for (int tr = 64; tr >= 16; tr /= 2)
+    if ((rows + tr - 1) / tr * tr - rows < (rows + p.tr - 1) / p.tr * p.tr - rows) p.tr = tr;
+  p.nkt = (nk + kRTileElems / p.tr - 1) / (kRTileElems / p.tr);
+  p.blocks = ((rows + p.tr - 1) / p.tr) * p.nkt;
   p.along_rows = u >= 0 && rd.rad[u] > unit_run(p.km, nk) && p.blocks <= INT32_MAX;
   if (p.along_rows) {
     // rows in the order: digit u first, then the others from the lowest up
@@ -259,8 +260,8 @@ bool plan_gather(long long nb, long long nr, long long nk, const IdxMap& bm0, co
     put(u);
     for (int t = 0; t < rd.nd; ++t)
       if (t != u) put(t);
-    p.rb_tile = kRTileR;
-    p.k_tile = kRTileK;
+    p.rb_tile = p.tr;
+    p.k_tile = kRTileElems / p.tr;
     return true;
   }
   p.k_tile = (int)std::min<long long>(nk, kKCols);
@@ -280,12 +281,21 @@ cudaError_t gather3_t(const T* in, float* out, long long nb, long long nr, long 
   if (!plan_gather(nb, nr, nk, bm, rm, km, p)) return cudaErrorInvalidValue;
   const unsigned grid = (unsigned)p.blocks;
   if (p.along_rows) {
-    if (p.narrow)
-      gather_along_rows<true, T><<<grid, kGatherThreads, 0, s>>>(in, out, rows, nk, ldk, p.nkt,
-                                                                 p.vin, p.vout, p.km);
-    else
-      gather_along_rows<false, T><<<grid, kGatherThreads, 0, s>>>(in, out, rows, nk, ldk, p.nkt,
-                                                                  p.vin, p.vout, p.km);
+    auto launch = [&](auto tr_tag) {
+      constexpr int TR = decltype(tr_tag)::value;
+      if (p.narrow)
+        gather_along_rows<true, T, TR><<<grid, kGatherThreads, 0, s>>>(in, out, rows, nk, ldk,
+                                                                       p.nkt, p.vin, p.vout, p.km);
+      else
+        gather_along_rows<false, T, TR><<<grid, kGatherThreads, 0, s>>>(
+            in, out, rows, nk, ldk, p.nkt, p.vin, p.vout, p.km);
+    };
+    switch (p.tr) {
+      case 16: launch(std::integral_constant<int, 16>{}); break;
+      case 32: launch(std::integral_constant<int, 32>{}); break;
+      case 64: launch(std::integral_constant<int, 64>{}); break;
+      default: launch(std::integral_constant<int, 128>{}); break;
+    }
   } else if (p.narrow) {
     gather_along_k<true, T><<<grid, kGatherThreads, 0, s>>>(in, out, rows, nr, nk, ldk, p.rb_tile,
                                                             p.k_tile, p.nkt, p.bm, p.rm, p.km);
