@@ -1,16 +1,17 @@
 // Contraction dispatch for the energy and the adjoint passes.
 //
 // Every contraction of the reduced density matrices and of the reverse
-// passes is described once, as an FP64 descriptor with index maps (Gemm).
-// A context in split precision runs them on the TF32x3 tensor-core engine:
-// each operand is gathered through its maps into a K-contiguous FP32 copy
-// (row stride padded to 16 bytes, batch-major), the product accumulates on
-// the tensor cores, and the epilogue writes the FP64 result through the
-// descriptor's output maps with alpha and beta.  Traces and the energy
-// reduction that follow stay in FP64, and so do contractions with a thin
-// output (fewer than 16 rows or columns: long reductions into a few numbers,
-// memory bound).  An FP64 context runs every descriptor on the FP64
-// CUDA-core engine.
+// passes is described once, as a descriptor with index maps (Gemm): operands
+// and result in FP64, or in FP32 where the descriptor's storage flags say so
+// (the gradient tape of a split context).  A context in split precision runs
+// them on the TF32x3 tensor-core engine: each operand is gathered through its
+// maps into a K-contiguous FP32 copy (row stride padded to 16 bytes,
+// batch-major), the product accumulates on the tensor cores, and the
+// epilogue writes the result through the descriptor's output maps with alpha
+// and beta.  Traces and the energy reduction that follow stay in FP64, and so
+// do contractions with a thin output (fewer than 16 rows or columns: long
+// reductions into a few numbers, memory bound).  An FP64 context runs every
+// descriptor on the FP64 CUDA-core engine.
 #include "ctx.cuh"
 #include "tc_gemm.cuh"
 
