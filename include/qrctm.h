@@ -84,6 +84,15 @@ typedef struct {
                          state of its own)                                      */
   int opt_history;    /* > 0: reserve workspace for qrctm_optimize keeping up to this
                          many L-BFGS pairs (1..32; needs with_grad)             */
+  int grad_store;     /* 0..32 (needs with_grad): reserve workspace for the tapes of
+                         this many steps.  An unrolled gradient of k <= grad_store
+                         steps then records each step's tape once on the way
+                         forward and reads it on the way back; otherwise (0, or
+                         k larger) it keeps only each step's (C, T) and re-runs
+                         the step's forward pass before its reverse pass.  The
+                         result is the same derivative either way.  Costs
+                         grad_store x (the bytes of one tape, about 4 (chi D^2)^2
+                         doubles) of workspace.                                  */
 } qrctm_config;
 
 typedef struct {

@@ -51,7 +51,7 @@ class Config(ctypes.Structure):
         ("grad_max_iter", ctypes.c_int), ("grad_tol", ctypes.c_double),
         ("with_nnn", ctypes.c_int), ("with_grad", ctypes.c_int),
         ("stream", ctypes.c_void_p), ("method", ctypes.c_int),
-        ("opt_history", ctypes.c_int),
+        ("opt_history", ctypes.c_int), ("grad_store", ctypes.c_int),
     ]
 
 
@@ -189,13 +189,27 @@ class QRCTM:
     def __init__(self, d, D, chi, precision="fp64", layers="auto", warmup_steps=0,
                  check_every=1, tol=1e-10, max_iter=500, grad_max_iter=0, grad_tol=0.0,
                  with_nnn=False, with_grad=False, stream=None, device="cuda", method="qr",
-                 opt_history=0):
+                 opt_history=0, grad_store="auto"):
+        """grad_store: tapes of this many steps kept for unrolled gradients (an
+        unrolled gradient of k <= grad_store steps records each step's tape on
+        the way forward instead of re-running the step on the way back);
+        "auto": up to 24 (the largest k of the paper's runs) within a quarter
+        of the device memory still free after the rest of the workspace, 0
+        without with_grad."""
         torch = _torch()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.cfg = Config(d, D, chi, PRECISION[precision], LAYERS[layers], warmup_steps,
                           check_every, tol, max_iter, grad_max_iter, grad_tol, int(with_nnn),
                           int(with_grad), ctypes.c_void_p(self.stream.cuda_stream),
-                          METHOD[method], opt_history)
+                          METHOD[method], opt_history, 0)
+        if with_grad and grad_store == "auto":
+            base = _load().qrctm_workspace_bytes(ctypes.byref(self.cfg))
+            self.cfg.grad_store = 1
+            tape = _load().qrctm_workspace_bytes(ctypes.byref(self.cfg)) - base
+            free = torch.cuda.mem_get_info(torch.device(device))[0] - base
+            self.cfg.grad_store = int(max(0, min(24, (free // 4) // max(tape, 1)))) if base else 0
+        elif grad_store != "auto":
+            self.cfg.grad_store = int(grad_store)
         nbytes = _load().qrctm_workspace_bytes(ctypes.byref(self.cfg))
         if nbytes == 0:
             raise QRCTMError(1, "qrctm_workspace_bytes", "invalid configuration")

@@ -31,6 +31,8 @@ bool cfg_valid(const qrctm_config& c) {
   if (net && (c.d != 1 || c.precision != QRCTM_FP64 || c.with_grad || c.with_nnn)) return false;
   if (c.opt_history < 0 || c.opt_history > 32) return false;
   if (c.opt_history > 0 && !c.with_grad) return false;
+  if (c.grad_store < 0 || c.grad_store > kGradMaxUnroll) return false;
+  if (c.grad_store > 0 && !c.with_grad) return false;
   const long long D2 = net ? (long long)c.D : (long long)c.D * c.D;
   if (D2 > 4096 || (long long)c.chi * D2 > (1ll << 20)) return false;
   if (c.chi < D2) return false;
@@ -186,8 +188,17 @@ size_t make_plan(const qrctm_config& cfg, bool carve, qrctm_ctx* c) {
     size_t o = off;
     off += al(gb);
     if (carve) { c->G = c->ws + o; c->G_bytes = gb; }
+    // tapes of the unrolled gradient's steps
+    const size_t tb = tape_bytes((int)d, (int)D, (int)chi), ts = tb * (size_t)cfg.grad_store;
+    o = off;
+    off += al(ts);
+    if (carve) {
+      c->tape_store = cfg.grad_store > 0 ? c->ws + o : nullptr;
+      c->tape_store_k = cfg.grad_store;
+    }
   } else if (carve) {
     c->G = nullptr; c->G_bytes = 0;
+    c->tape_store = nullptr; c->tape_store_k = 0;
   }
   // FP32 operand copies for the split-precision energy and adjoint
   // contractions: the energy's largest pairs a d^2-batched (chi D^2)^2

@@ -69,6 +69,8 @@ struct qrctm_ctx {
   double *opt_S, *opt_Y, *opt_x, *opt_xt, *opt_g, *opt_gt, *opt_p, *opt_q, *opt_out;
   double *opt_Cp, *opt_Tp, *opt_Cc, *opt_Tc;
   bool grad_keep_env;      // an unrolled gradient leaves (C, T) after its k steps
+  char* tape_store;        // tapes of up to tape_store_k steps (unrolled gradient)
+  int tape_store_k;
   // split-precision contractions of the energy and adjoint passes
   bool mm_split;
   float* mm32;

@@ -43,6 +43,34 @@ struct GradLayout {
   double *ev0, *ev1, *evx;   // env-sized vectors: right-hand side, work, solution
 };
 
+// Lay one step's tape out from base (base = nullptr: only count bytes).
+size_t tape_layout(int d, int D, int chi, char* base, StepTape* T) {
+  const size_t D2 = (size_t)D * D, m = (size_t)chi * D2, mm = m * m, c2 = (size_t)chi * chi,
+               mc = m * chi;
+  size_t off = 0;
+  auto take = [&](double** p, size_t n) {
+    if (base && p) *p = reinterpret_cast<double*>(base + off);
+    off += al8(n > 0 ? n : 1);
+  };
+  take(T ? &T->Cin : nullptr, c2);
+  take(T ? &T->Tin : nullptr, mc);
+  take(T ? &T->ct : nullptr, mc);
+  take(T ? &T->Q : nullptr, mc);
+  take(T ? &T->R : nullptr, c2);
+  take(T ? &T->Rinv : nullptr, c2);
+  take(T ? &T->X1 : nullptr, mm);
+  take(T ? &T->Z : nullptr, mm * d);
+  take(T ? &T->X2 : nullptr, mm);
+  take(T ? &T->Traw : nullptr, mc);
+  take(T ? &T->Ts : nullptr, mc);
+  take(T ? &T->Y2 : nullptr, mc);
+  take(T ? &T->Craw : nullptr, c2);
+  take(T ? &T->Cout : nullptr, c2);
+  take(T ? &T->Tout : nullptr, mc);
+  take(T ? &T->parts : nullptr, 512);
+  return off;
+}
+
 // Lay the gradient region out (carve = false: only count bytes).
 size_t layout(int d, int D, int chi, bool nnn, char* base, GradLayout* L) {
   const size_t D2 = (size_t)D * D, m = (size_t)chi * D2, mm = m * m, c2 = (size_t)chi * chi,
@@ -52,25 +80,8 @@ size_t layout(int d, int D, int chi, bool nnn, char* base, GradLayout* L) {
     if (base && p) *p = reinterpret_cast<double*>(base + off);
     off += al8(n > 0 ? n : 1);
   };
-  for (int t = 0; t < 2; ++t) {
-    StepTape* T = L ? &L->tape[t] : nullptr;
-    take(T ? &T->Cin : nullptr, c2);
-    take(T ? &T->Tin : nullptr, mc);
-    take(T ? &T->ct : nullptr, mc);
-    take(T ? &T->Q : nullptr, mc);
-    take(T ? &T->R : nullptr, c2);
-    take(T ? &T->Rinv : nullptr, c2);
-    take(T ? &T->X1 : nullptr, mm);
-    take(T ? &T->Z : nullptr, mm * d);
-    take(T ? &T->X2 : nullptr, mm);
-    take(T ? &T->Traw : nullptr, mc);
-    take(T ? &T->Ts : nullptr, mc);
-    take(T ? &T->Y2 : nullptr, mc);
-    take(T ? &T->Craw : nullptr, c2);
-    take(T ? &T->Cout : nullptr, c2);
-    take(T ? &T->Tout : nullptr, mc);
-    take(T ? &T->parts : nullptr, 512);
-  }
+  for (int t = 0; t < 2; ++t)
+    off += tape_layout(d, D, chi, base ? base + off : nullptr, L ? &L->tape[t] : nullptr);
   AdjWork* A = L ? &L->adj : nullptr;
   take(A ? &A->Cs : nullptr, c2);
   take(A ? &A->Craw : nullptr, c2);
@@ -200,6 +211,7 @@ __global__ void energy2_k(const double* rho_nn, const double* rho_nnn, double J1
 }  // namespace
 
 size_t grad_bytes(int d, int D, int chi) { return layout(d, D, chi, true, nullptr, nullptr); }
+size_t tape_bytes(int d, int D, int chi) { return tape_layout(d, D, chi, nullptr, nullptr); }
 
 // ---------------------------------------------------------------------------
 // Forward step with tape, and its reverse pass
@@ -611,37 +623,69 @@ cudaError_t energy_grad_run(qrctm_ctx* c, double J1, double J2, int mode, int k_
     const int K = k_unroll;
     cudaMemcpyAsync(L.ckC, c->C, sizeof(double) * c2, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(L.ckT, c->T, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s);
-    // the forward sweep keeps only the checkpoints, so it runs the plain step
-    // (the same map, without the tape's stored intermediates) in place on
-    // the context's environment
-    for (int i = 1; i <= K; ++i) {
-      if ((e = qr_step_graph(c)) != cudaSuccess) return e;
-      cudaMemcpyAsync(L.ckC + i * c2, c->C, sizeof(double) * c2, cudaMemcpyDeviceToDevice, s);
-      cudaMemcpyAsync(L.ckT + i * mc, c->T, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s);
-    }
-    if (c->grad_keep_env) {
-      // the optimiser continues from the environment after the k steps
-      c->spec_valid = false;
-      c->spec_pending = false;
+    if (c->tape_store && K <= c->tape_store_k) {
+      // every step's tape recorded once on the way forward, read on the way back
+      const size_t tb = tape_bytes(c->d, c->D, c->chi);
+      std::vector<StepTape> tp(K);
+      for (int i = 0; i < K; ++i)
+        tape_layout(c->d, c->D, c->chi, c->tape_store + (size_t)i * tb, &tp[i]);
+      for (int i = 0; i < K; ++i) {
+        const double* Cin = i == 0 ? L.ckC : tp[i - 1].Cout;
+        const double* Tin = i == 0 ? L.ckT : tp[i - 1].Tout;
+        if ((e = step_fwd_tape(c, Cin, Tin, tp[i])) != cudaSuccess) return e;
+      }
+      if ((e = energy_vjp(c, L, tp[K - 1].Cout, tp[K - 1].Tout, J1, J2, L.yC, L.yT, L.Abar,
+                          e_dev)) != cudaSuccess)
+        return e;
+      for (int i = K - 1; i >= 0; --i) {
+        if ((e = step_vjp(c, tp[i], L.adj, L.yC, L.yT, L.y2C, L.y2T, L.Abar)) != cudaSuccess)
+          return e;
+        std::swap(L.yC, L.y2C);
+        std::swap(L.yT, L.y2T);
+      }
+      iters = K;
+      if (fp_resid_out) *fp_resid_out = 0.0;
+      if (c->grad_keep_env) {
+        // the optimiser continues from the environment after the k steps
+        cudaMemcpyAsync(c->C, tp[K - 1].Cout, sizeof(double) * c2, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(c->T, tp[K - 1].Tout, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s);
+        c->iters += K;
+        c->spec_valid = false;
+        c->spec_pending = false;
+      }
     } else {
-      cudaMemcpyAsync(c->C, L.ckC, sizeof(double) * c2, cudaMemcpyDeviceToDevice, s);
-      cudaMemcpyAsync(c->T, L.ckT, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s);
-      c->iters -= K;
-    }
-    if ((e = energy_vjp(c, L, L.ckC + K * c2, L.ckT + K * mc, J1, J2, L.yC, L.yT, L.Abar,
-                        e_dev)) != cudaSuccess)
-      return e;
-    for (int i = K; i >= 1; --i) {
-      if ((e = step_fwd_tape(c, L.ckC + (i - 1) * c2, L.ckT + (i - 1) * mc, L.tape[0])) !=
-          cudaSuccess)
+      // the forward sweep keeps only the checkpoints, so it runs the plain step
+      // (the same map, without the tape's stored intermediates) in place on
+      // the context's environment
+      for (int i = 1; i <= K; ++i) {
+        if ((e = qr_step_graph(c)) != cudaSuccess) return e;
+        cudaMemcpyAsync(L.ckC + i * c2, c->C, sizeof(double) * c2, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(L.ckT + i * mc, c->T, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s);
+      }
+      if (c->grad_keep_env) {
+        // the optimiser continues from the environment after the k steps
+        c->spec_valid = false;
+        c->spec_pending = false;
+      } else {
+        cudaMemcpyAsync(c->C, L.ckC, sizeof(double) * c2, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(c->T, L.ckT, sizeof(double) * mc, cudaMemcpyDeviceToDevice, s);
+        c->iters -= K;
+      }
+      if ((e = energy_vjp(c, L, L.ckC + K * c2, L.ckT + K * mc, J1, J2, L.yC, L.yT, L.Abar,
+                          e_dev)) != cudaSuccess)
         return e;
-      if ((e = step_vjp(c, L.tape[0], L.adj, L.yC, L.yT, L.y2C, L.y2T, L.Abar)) != cudaSuccess)
-        return e;
-      std::swap(L.yC, L.y2C);
-      std::swap(L.yT, L.y2T);
+      for (int i = K; i >= 1; --i) {
+        if ((e = step_fwd_tape(c, L.ckC + (i - 1) * c2, L.ckT + (i - 1) * mc, L.tape[0])) !=
+            cudaSuccess)
+          return e;
+        if ((e = step_vjp(c, L.tape[0], L.adj, L.yC, L.yT, L.y2C, L.y2T, L.Abar)) != cudaSuccess)
+          return e;
+        std::swap(L.yC, L.y2C);
+        std::swap(L.yT, L.y2T);
+      }
+      iters = K;
+      if (fp_resid_out) *fp_resid_out = 0.0;
     }
-    iters = K;
-    if (fp_resid_out) *fp_resid_out = 0.0;
   }
   // project onto the C4v subspace
   if ((e = c4v_symmetrize(k.d, k.D, L.Abar, grad, s)) != cudaSuccess) return e;

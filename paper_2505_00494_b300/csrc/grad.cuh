@@ -116,6 +116,8 @@ struct AdjWork {
 };
 
 size_t grad_bytes(int d, int D, int chi);
+// Bytes of one step's tape (each 256-byte aligned piece of a StepTape).
+size_t tape_bytes(int d, int D, int chi);
 constexpr int kGradMaxUnroll = 32;
 cudaError_t energy_grad_run(qrctm_ctx* c, double J1, double J2, int mode, int k_unroll,
                             double* grad, double* e_out, int* iters_out, double* resid_out,

@@ -107,6 +107,19 @@ def test_optimizer_planning_host_only(q):
     assert q.lib.qrctm_optimize(None, None, None, 1, None, None, None, None) == 1
 
 
+def test_tape_store_planning_host_only(q):
+    # the tapes of grad_store steps: each holds X1, Z, X2 (4 (chi D^2)^2 doubles at
+    # d = 2) and a dozen environment-sized pieces; the reservation grows linearly
+    ws = lambda n: q.lib.qrctm_workspace_bytes(ctypes.byref(cfg(q, D=3, chi=12, with_grad=1,
+                                                                grad_store=n)))
+    m = 12 * 9
+    assert ws(1) - ws(0) >= 4 * m * m * 8
+    assert ws(3) - ws(0) == 3 * (ws(1) - ws(0))   # every piece 256-byte aligned
+    for bad in (cfg(q, D=3, chi=12, grad_store=2), cfg(q, D=3, chi=12, with_grad=1, grad_store=33),
+                cfg(q, D=3, chi=12, with_grad=1, grad_store=-1)):
+        assert q.lib.qrctm_workspace_bytes(ctypes.byref(bad)) == 0
+
+
 def test_qr_width_limit_host_only(q):
     # one accumulator row per column of the factorisation: n <= 2048
     assert q.lib.qrctm_qr_workspace_bytes(4096, 2048) > 0
