@@ -10,9 +10,11 @@
 // the leading transfer-matrix eigenvalues), so the linear system is solved by
 // restarted GMRES instead, one application of J_G^T being two reverse steps.
 // Unrolled mode instead backpropagates through k recorded steps started from
-// the current environment (held fixed): a forward sweep of plain steps keeps
-// their (C, T) checkpoints, and each step's tape is recomputed from its
-// checkpoint on the way back.  The gradient is projected onto the C4v
+// the current environment (held fixed): their tapes are recorded into the
+// workspace's tape store on the way forward and read on the way back, or,
+// without room for k tapes, a forward sweep of plain steps keeps their (C, T)
+// checkpoints and each step's tape is recomputed from its checkpoint on the
+// way back.  The gradient is projected onto the C4v
 // subspace at the end (the function is only defined there).  The passes take
 // the context's precision: FP64, or in a split context the TF32x3 engine with
 // the step's own split QR (thin-output contractions, the traces and the QR
