@@ -193,8 +193,11 @@ qrctm_status qrctm_energy(qrctm_ctx* ctx, const qrctm_model* model, double* e_ou
  * with_grad (and with_nnn when J2 != 0), d = 2, D >= 2.  All reverse passes
  * run in FP64 for an FP64 context; a split-precision context runs every
  * contraction of the taped steps, of the energy and of the reverse passes on
- * the TF32x3 tensor-core engine (FP32-class, e_out included; the QR adjoint,
- * normalisations and traces stay FP64).  Implicit mode solves
+ * the TF32x3 tensor-core engine and factors ct with the step's own split QR
+ * (FP32-class, e_out included; the QR panels, the QR adjoint's product with
+ * R^-T, normalisations and traces stay FP64).  Unroll mode keeps the k tapes
+ * in the workspace when grad_store >= k, else re-runs each step's forward
+ * pass before its reverse pass (same result).  Implicit mode solves
  * (I - J^T) xbar = dE/d(env), J the
  * Jacobian of the two steps, by restarted GMRES(40); it stops when the
  * relative residual falls below grad_tol or after grad_max_iter
