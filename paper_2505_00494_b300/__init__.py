@@ -233,6 +233,11 @@ class QRCTM:
         if getattr(self, "h", None):
             _load().qrctm_destroy(self.h)
             self.h = None
+        if getattr(self, "ws", None) is not None:
+            # the workspace (with a gradient's tape store, tens of GB) goes back
+            # to torch once the context's queued work is done
+            self.stream.synchronize()
+            self.ws = None
 
     def __del__(self):
         try:
